@@ -1,0 +1,187 @@
+/*
+ * fgt.h — C ABI of the GB300 machine fast Gauss transform library (libfgt.so).
+ *
+ * The library evaluates the continuous Gauss transform of Greengard, Jiang,
+ * Rachh and Wang, "A new version of the adaptive fast Gauss transform for
+ * discrete and continuous sources" (arXiv 2305.07165):
+ *
+ *     u(x) = \int_B G(x - y; delta) sigma(y) dy,    B = [-1/2, 1/2]^d,
+ *
+ * Section 1, eq. (bgt), with the free-space kernel G(x) = exp(-|x|^2/delta)
+ * (eq. (gkernel)) or its periodic image sum (eq. (gper_kernel)), d = 2 or 3.
+ * sigma is given, and u is returned, at the k^d tensor-product Gauss-Legendre
+ * nodes of the leaves of a level-restricted adaptive tree (Section 4,
+ * Algorithm 3 output; Definition treedefs).  The transform itself is the box
+ * FGT of Section 4.2, Algorithm 4, with the periodic variant of Section 5.
+ *
+ * Layout (all calls):
+ *   - A tree is a list of leaves.  Leaf i has level leaf_level[i] >= 0 and
+ *     integer box index leaf_coord[i*d + a] in [0, 2^level) along axis a
+ *     (a = 0 is x_1).  Its centre is -1/2 + (coord + 1/2) 2^-level, its side
+ *     L = 2^-level.  The leaves must tile B exactly and be 2:1 balanced across
+ *     shared boundary points, corners included (Definition treedefs); with
+ *     periodic boundary conditions the balance must also hold across the wrap.
+ *   - sigma and u are FP64 arrays [n_leaves][k^d] in the caller's leaf order.
+ *     Node t = (t_1..t_d) of a leaf sits at centre + (L/2)(eta_{t_1}, ...),
+ *     eta the ascending k-point Gauss-Legendre nodes on [-1, 1]; inside a
+ *     leaf t_1 is the fastest index.
+ *
+ * Errors: every call returns an fgt_status; nothing throws across the ABI.
+ * fgt_last_error() gives a human-readable message for the calling thread's
+ * most recent failure.  All entry points are thread-safe for distinct plans;
+ * one plan must not be used from two threads at once.
+ */
+#ifndef FGT_H
+#define FGT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FGT_OK = 0,
+  FGT_ERR_ARG = 1,      /* bad argument (d, k, delta, tol, sizes, null pointers) */
+  FGT_ERR_TREE = 2,     /* leaves do not tile B, overlap, or are not 2:1 balanced */
+  FGT_ERR_OOM = 3,      /* device or host allocation failed */
+  FGT_ERR_CUDA = 4,     /* a CUDA call failed (message has the CUDA error string) */
+  FGT_ERR_TIMEOUT = 5,  /* a bounded device wait gave up (reserved for batched execution) */
+  FGT_ERR_STATE = 6     /* call not valid in the plan's current state */
+} fgt_status;
+
+typedef enum { FGT_BC_FREE = 0, FGT_BC_PERIODIC = 1 } fgt_bc;
+
+/* Arithmetic of the plane-wave contractions (form / shift / evaluate).
+ * FGT_PREC_FP64: everything in FP64.
+ * FGT_PREC_SPLIT: contractions and stored expansions in FP32 (accepted only
+ *   when tol >= 1e-7); the near-field 1D tables, the tables' construction and
+ *   the final per-leaf accumulation stay FP64. */
+typedef enum { FGT_PREC_FP64 = 0, FGT_PREC_SPLIT = 1 } fgt_prec;
+
+/* How the plane-wave hierarchy of Algorithm 4 is executed.
+ * FGT_MODE_FUSED (default): the child-to-parent (T_c->p) and parent-to-child
+ *   (T_p->c) diagonal shifts are separable, so they are folded into the 1D form
+ *   and evaluation matrices; leaves (or whole uniform subtrees) form their
+ *   outgoing expansion directly at their cutoff-level ancestor and evaluate
+ *   its incoming expansion directly.  Same arithmetic, reassociated.
+ * FGT_MODE_HIERARCHICAL: the literal order of Algorithm 4 — form at each
+ *   leaf's own centre, merge level by level with T_c->p, gather with
+ *   T_out->in at the cutoff level, push level by level with T_p->c, evaluate
+ *   at each leaf.  Needs an expansion slot for every box with f(B) = 1. */
+typedef enum { FGT_MODE_FUSED = 0, FGT_MODE_HIERARCHICAL = 1 } fgt_mode;
+
+typedef struct {
+  int32_t d;                  /* 2 or 3 */
+  int32_t k;                  /* Gauss-Legendre nodes per dimension per leaf, 1..16 */
+  int64_t n_leaves;           /* >= 1 */
+  const int32_t *leaf_level;  /* [n_leaves], host memory, copied by fgt_plan_create */
+  const int32_t *leaf_coord;  /* [n_leaves * d], host memory, copied */
+} fgt_tree;
+
+typedef struct fgt_plan fgt_plan;
+
+/* Plan parameters chosen at creation (host values, for inspection and tests). */
+typedef struct {
+  int32_t d, k, bc;
+  int32_t cutoff_level;       /* l_c: boxes at l_c have side 2^-l_c >= D0 sqrt(delta) (Section 3) */
+  int32_t fourier;            /* 1: periodic with l_c <= 1, root Fourier series (Section 5) */
+  int32_t max_level;          /* deepest leaf level */
+  int32_t n_f;                /* paper's n_f = 2M (Theorem 1, eq. (pwterms)); 0 when fourier */
+  int32_t n_p;                /* periodic Fourier terms (Section 2.2); 0 unless fourier */
+  int32_t modes_1d;           /* modes per dimension actually used: 2M-1, or 2 n_p + 1 */
+  int32_t modes_half;         /* stored modes along the last dimension (conjugate symmetry) */
+  double delta, tol, eps_pw;  /* eps_pw: the epsilon plugged into Theorem 1 / n_p */
+  double D0, R, h;            /* Theorem 1 quantities (R*sqrt(delta) is the covered range) */
+  int64_t n_leaves, n_boxes;
+  int64_t n_pw_leaves;        /* leaves with f = 1 (evaluated from plane waves) */
+  int64_t n_anchor_boxes;     /* boxes at l_c with f = 1 (outgoing/incoming expansion owners) */
+  int64_t n_form_blocks;      /* uniform subtrees formed / evaluated as one dense transform */
+  int64_t n_direct_pairs;     /* near-field (D-list) leaf pairs, images counted separately */
+  int64_t n_gather_pairs;     /* out->in translations at the cutoff level */
+  int64_t form_flops, eval_flops, gather_flops, direct_flops; /* per execute, real flops */
+  int64_t device_bytes;       /* tables + lists + expansion workspace (excludes host-path staging) */
+  int32_t prec, mode;
+} fgt_plan_info;
+
+/* Build a plan: validate the tree, choose l_c, n_f (or n_p), build the lists
+ * and the FP64 1D tables (Section 4.1), upload them, size the workspace.
+ * delta > 0; tol in [1e-14, 1e-1].  Returns FGT_ERR_TREE for invalid trees. */
+fgt_status fgt_plan_create(int d, double delta, double tol, int bc, const fgt_tree *tree, fgt_plan **out);
+
+/* Same, with the plane-wave epsilon given explicitly (eps_pw <= 0 means tol). */
+fgt_status fgt_plan_create_ex(int d, double delta, double tol, double eps_pw, int bc, int prec, int mode,
+                              const fgt_tree *tree, fgt_plan **out);
+
+/* Host-only dry run of fgt_plan_create_ex: validates the tree, builds the lists and
+ * tables and fills `info` (including device_bytes, for admission by HBM footprint)
+ * without touching the GPU.  Same error behaviour as plan creation. */
+fgt_status fgt_plan_analyze(int d, double delta, double tol, double eps_pw, int bc, int prec, int mode,
+                            const fgt_tree *tree, fgt_plan_info *info);
+
+/* Host-only plan (no GPU is touched): the lists and tables are built and kept in host memory
+ * for inspection through fgt_plan_host_array(); executing it returns FGT_ERR_STATE. */
+fgt_status fgt_plan_create_host(int d, double delta, double tol, double eps_pw, int bc, int prec, int mode,
+                                const fgt_tree *tree, fgt_plan **out);
+
+/* Borrow a host-only plan's array by name ("blocks", "block_leaves", "Ff", "Fh", "Ef", "Eh",
+ * "gather_dst", "gather_ptr", "gather_src", "Pf", "Ph", "near_tgt", "near_flags", "near_ptr",
+ * "near_src", "near_tab", "merge<i>_items|qf|qh", "push<i>_items|qf|qh").  The pointer stays
+ * valid until the plan is destroyed or re-planned.  FGT_ERR_STATE for device plans. */
+fgt_status fgt_plan_host_array(const fgt_plan *plan, const char *name, const void **data, size_t *bytes);
+
+fgt_status fgt_plan_set_precision(fgt_plan *plan, int prec);  /* fgt_prec; SPLIT needs tol >= 1e-7 */
+fgt_status fgt_plan_set_mode(fgt_plan *plan, int mode);       /* fgt_mode */
+fgt_status fgt_plan_get_info(const fgt_plan *plan, fgt_plan_info *info);
+
+/* Device bytes the plan holds (tables, lists, expansion workspace). */
+size_t fgt_plan_device_bytes(const fgt_plan *plan);
+
+/* Evaluate u from sigma (Algorithm 4).  sigma_dev, u_dev: device pointers to
+ * FP64 [n_leaves][k^d]; u is overwritten (not accumulated into); sigma is not
+ * modified.  fgt_execute runs on the legacy default stream and returns after
+ * the result is complete; fgt_execute_async only enqueues on `stream` (a
+ * cudaStream_t, NULL = legacy default stream).  A plan runs one transform at a
+ * time: do not overlap two executions of the same plan. */
+fgt_status fgt_execute(fgt_plan *plan, const double *sigma_dev, double *u_dev);
+fgt_status fgt_execute_async(fgt_plan *plan, const double *sigma_dev, double *u_dev, void *stream);
+
+/* End to end: sigma_host, u_host are host arrays (pinned for full copy speed);
+ * copies in, transforms, copies out on `stream` and synchronises it. */
+fgt_status fgt_execute_host(fgt_plan *plan, const double *sigma_host, double *u_host, void *stream);
+
+void fgt_destroy(fgt_plan *plan);
+
+const char *fgt_last_error(void);
+
+/* ---- Host-side building blocks of the 1D tables (Section 2.4), exposed for tests ---- */
+
+/* k-point Gauss-Legendre rule on [-1,1], ascending nodes. 1 <= k <= 64. */
+fgt_status fgt_gauss_legendre(int k, double *nodes, double *weights);
+
+/* Theorem 1 / Section 3 parameters for (delta, eps, bc): cutoff level l_c,
+ * D0 = sqrt(log(3/eps)), range R, step h, n_f = 2M; n_p of Section 2.2. */
+fgt_status fgt_params(double delta, double eps, int bc, int32_t *cutoff_level, double *D0, double *R,
+                      double *h, int32_t *n_f, int32_t *n_p);
+
+/* n_f(R) = 2 ceil(D0 (R + D0) / pi) for a given R (Theorem 1, eq. (pwterms)). */
+int32_t fgt_nf_for_range(double eps, double R);
+
+/* J_lambda[P_n](t) = int_{-1}^{1} exp(-(t-x)^2/lambda^2) P_n(x) dx, n = 0..nmax
+ * (Section 2.4, eq. (gsintegrals)): erf seeds plus the five-term recurrence
+ * (eq. (Jnrecurrence)) when lambda <= 1/8, Gauss-Legendre quadrature above. */
+fgt_status fgt_legendre_gauss_integrals(double lambda, double t, int nmax, double *out);
+
+/* Spherical Bessel j_n(x), n = 0..nmax (backward recurrence, normalised). */
+fgt_status fgt_spherical_bessel(double x, int nmax, double *out);
+
+/* I[P_n](t) = int_{-1}^{1} exp(i t x) P_n(x) dx = 2 i^n j_n(t), n = 0..nmax
+ * (Section 2.4, eq. (pwintegrals2)); real and imaginary parts. */
+fgt_status fgt_legendre_fourier_integrals(double t, int nmax, double *re, double *im);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FGT_H */

@@ -1,0 +1,272 @@
+"""GB300 machine fast Gauss transform: thin Python binding of libfgt.so.
+
+The transform (paper Section 4.2, Algorithm 4; periodic variant Section 5)
+runs entirely in the library's CUDA kernels; this module only marshals
+arguments through the C ABI declared in ``include/fgt.h``.  PyTorch supplies
+device memory and streams.  There is no CPU fallback: every call that needs
+the GPU raises if the library or the device is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Plan", "FGTError", "lib", "BC_FREE", "BC_PERIODIC", "PREC_FP64", "PREC_SPLIT", "MODE_FUSED",
+           "MODE_HIERARCHICAL", "gauss_legendre", "params", "nf_for_range", "legendre_gauss_integrals",
+           "spherical_bessel", "legendre_fourier_integrals", "analyze", "HostPlan"]
+
+BC_FREE, BC_PERIODIC = 0, 1
+PREC_FP64, PREC_SPLIT = 0, 1
+MODE_FUSED, MODE_HIERARCHICAL = 0, 1
+_STATUS = {0: "FGT_OK", 1: "FGT_ERR_ARG", 2: "FGT_ERR_TREE", 3: "FGT_ERR_OOM", 4: "FGT_ERR_CUDA",
+           5: "FGT_ERR_TIMEOUT", 6: "FGT_ERR_STATE"}
+
+
+class FGTError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Tree(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("k", ctypes.c_int32), ("n_leaves", ctypes.c_int64),
+                ("leaf_level", ctypes.c_void_p), ("leaf_coord", ctypes.c_void_p)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("d", "k", "bc", "cutoff_level", "fourier", "max_level", "n_f",
+                                              "n_p", "modes_1d", "modes_half")] + \
+               [(n, ctypes.c_double) for n in ("delta", "tol", "eps_pw", "D0", "R", "h")] + \
+               [(n, ctypes.c_int64) for n in ("n_leaves", "n_boxes", "n_pw_leaves", "n_anchor_boxes",
+                                              "n_form_blocks", "n_direct_pairs", "n_gather_pairs", "form_flops",
+                                              "eval_flops", "gather_flops", "direct_flops", "device_bytes")] + \
+               [("prec", ctypes.c_int32), ("mode", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load (building first if the sources are newer) the in-tree libfgt.so."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+            L.fgt_plan_create_ex.argtypes = [i32, dbl, dbl, dbl, i32, i32, i32, ctypes.POINTER(_Tree), vp]
+            L.fgt_plan_create_host.argtypes = [i32, dbl, dbl, dbl, i32, i32, i32, ctypes.POINTER(_Tree), vp]
+            L.fgt_plan_host_array.argtypes = [vp, ctypes.c_char_p, vp, vp]
+            L.fgt_plan_analyze.argtypes = [i32, dbl, dbl, dbl, i32, i32, i32, ctypes.POINTER(_Tree),
+                                           ctypes.POINTER(PlanInfo)]
+            L.fgt_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+            L.fgt_plan_set_precision.argtypes = [vp, i32]
+            L.fgt_plan_set_mode.argtypes = [vp, i32]
+            L.fgt_plan_device_bytes.argtypes = [vp]
+            L.fgt_plan_device_bytes.restype = ctypes.c_size_t
+            L.fgt_execute.argtypes = [vp, vp, vp]
+            L.fgt_execute_async.argtypes = [vp, vp, vp, vp]
+            L.fgt_execute_host.argtypes = [vp, vp, vp, vp]
+            L.fgt_destroy.argtypes = [vp]
+            L.fgt_destroy.restype = None
+            L.fgt_last_error.restype = ctypes.c_char_p
+            L.fgt_gauss_legendre.argtypes = [i32, vp, vp]
+            L.fgt_params.argtypes = [dbl, dbl, i32, vp, vp, vp, vp, vp, vp]
+            L.fgt_nf_for_range.argtypes = [dbl, dbl]
+            L.fgt_nf_for_range.restype = ctypes.c_int32
+            L.fgt_legendre_gauss_integrals.argtypes = [dbl, dbl, i32, vp]
+            L.fgt_spherical_bessel.argtypes = [dbl, i32, vp]
+            L.fgt_legendre_fourier_integrals.argtypes = [dbl, i32, vp, vp]
+            for name in ("fgt_plan_create_ex", "fgt_plan_create_host", "fgt_plan_host_array", "fgt_plan_analyze", "fgt_plan_get_info", "fgt_plan_set_precision",
+                         "fgt_plan_set_mode", "fgt_execute", "fgt_execute_async", "fgt_execute_host",
+                         "fgt_gauss_legendre", "fgt_params", "fgt_legendre_gauss_integrals",
+                         "fgt_spherical_bessel", "fgt_legendre_fourier_integrals"):
+                getattr(L, name).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        raise FGTError(status, lib().fgt_last_error().decode(errors="replace"))
+
+
+def _tree_struct(d, k, level, coord):
+    lev = np.ascontiguousarray(level, dtype=np.int32)
+    crd = np.ascontiguousarray(coord, dtype=np.int32).reshape(-1)
+    if crd.size != lev.size * d:
+        raise ValueError("coord must have n_leaves * d entries")
+    t = _Tree(d, k, lev.size, lev.ctypes.data, crd.ctypes.data)
+    return t, (lev, crd)
+
+
+def analyze(d, k, delta, tol, level, coord, bc=BC_FREE, prec=PREC_FP64, mode=MODE_FUSED, eps_pw=0.0) -> dict:
+    """Host-only planning (no GPU): validates the tree and returns the plan info."""
+    t, keep = _tree_struct(d, k, level, coord)
+    info = PlanInfo()
+    _check(lib().fgt_plan_analyze(d, delta, tol, eps_pw, bc, prec, mode, ctypes.byref(t), ctypes.byref(info)))
+    return info.as_dict()
+
+
+class HostPlan:
+    """A plan built without a GPU: lists and tables kept in host memory for inspection."""
+
+    def __init__(self, d, k, delta, tol, level, coord, bc=BC_FREE, prec=PREC_FP64, mode=MODE_FUSED, eps_pw=0.0):
+        self.d, self.k = d, k
+        t, keep = _tree_struct(d, k, level, coord)
+        self._h = ctypes.c_void_p()
+        _check(lib().fgt_plan_create_host(d, delta, tol, eps_pw, bc, prec, mode, ctypes.byref(t),
+                                          ctypes.byref(self._h)))
+
+    def info(self) -> dict:
+        info = PlanInfo()
+        _check(lib().fgt_plan_get_info(self._h, ctypes.byref(info)))
+        return info.as_dict()
+
+    def array(self, name, dtype):
+        p, n = ctypes.c_void_p(), ctypes.c_size_t()
+        _check(lib().fgt_plan_host_array(self._h, name.encode(), ctypes.byref(p), ctypes.byref(n)))
+        if n.value == 0:
+            return np.zeros(0, dtype=dtype)
+        buf = (ctypes.c_char * n.value).from_address(p.value)
+        return np.frombuffer(bytes(buf), dtype=dtype).copy()
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().fgt_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """A box-FGT plan on the current CUDA device.
+
+    level: int32 [n_leaves]; coord: int32 [n_leaves, d]; k: nodes per dimension.
+    ``plan(sigma)`` takes a CUDA float64 tensor [n_leaves, k**d] and returns u.
+    """
+
+    def __init__(self, d, k, delta, tol, level, coord, bc=BC_FREE, prec=PREC_FP64, mode=MODE_FUSED, eps_pw=0.0):
+        import torch
+        if not torch.cuda.is_available():
+            raise FGTError(4, "no CUDA device: the box FGT runs only on the GPU")
+        torch.cuda.current_device()  # make sure the primary context exists before the library uses it
+        self.d, self.k, self.delta, self.tol, self.bc = d, k, delta, tol, bc
+        t, keep = _tree_struct(d, k, level, coord)
+        self.n_leaves = int(keep[0].size)
+        self._h = ctypes.c_void_p()
+        _check(lib().fgt_plan_create_ex(d, delta, tol, eps_pw, bc, prec, mode, ctypes.byref(t),
+                                        ctypes.byref(self._h)))
+
+    @property
+    def n_points(self):
+        return self.n_leaves * self.k ** self.d
+
+    def info(self) -> dict:
+        info = PlanInfo()
+        _check(lib().fgt_plan_get_info(self._h, ctypes.byref(info)))
+        return info.as_dict()
+
+    def set_precision(self, prec):
+        _check(lib().fgt_plan_set_precision(self._h, prec))
+
+    def set_mode(self, mode):
+        _check(lib().fgt_plan_set_mode(self._h, mode))
+
+    def device_bytes(self) -> int:
+        return int(lib().fgt_plan_device_bytes(self._h))
+
+    def _check_tensor(self, x, name):
+        import torch
+        if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous CUDA float64 tensor")
+        if x.numel() != self.n_points:
+            raise ValueError(f"{name} must hold n_leaves * k**d = {self.n_points} values")
+
+    def execute(self, sigma, out=None, stream=None):
+        """Enqueue u = transform(sigma) on `stream` (default: torch's current stream)."""
+        import torch
+        self._check_tensor(sigma, "sigma")
+        if out is None:
+            out = torch.empty_like(sigma)
+        self._check_tensor(out, "out")
+        s = stream if stream is not None else torch.cuda.current_stream(sigma.device)
+        _check(lib().fgt_execute_async(self._h, sigma.data_ptr(), out.data_ptr(), ctypes.c_void_p(s.cuda_stream)))
+        return out
+
+    __call__ = execute
+
+    def execute_host(self, sigma, out, stream=None):
+        """End to end through the C ABI: host (ideally pinned) float64 arrays in and out."""
+        import torch
+        for x, n in ((sigma, "sigma"), (out, "out")):
+            if isinstance(x, torch.Tensor):
+                if x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous() or x.numel() != self.n_points:
+                    raise TypeError(f"{n} must be a contiguous host float64 tensor of n_points values")
+            else:
+                raise TypeError(f"{n} must be a host torch tensor")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(lib().fgt_execute_host(self._h, sigma.data_ptr(), out.data_ptr(), ctypes.c_void_p(s.cuda_stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().fgt_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- host-side table helpers (no GPU)
+
+def gauss_legendre(k):
+    x, w = np.zeros(k), np.zeros(k)
+    _check(lib().fgt_gauss_legendre(k, x.ctypes.data, w.ctypes.data))
+    return x, w
+
+
+def params(delta, eps, bc=BC_FREE):
+    lc, nf, npp = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    D0, R, h = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().fgt_params(delta, eps, bc, ctypes.byref(lc), ctypes.byref(D0), ctypes.byref(R), ctypes.byref(h),
+                            ctypes.byref(nf), ctypes.byref(npp)))
+    return dict(cutoff_level=lc.value, D0=D0.value, R=R.value, h=h.value, n_f=nf.value, n_p=npp.value)
+
+
+def nf_for_range(eps, R):
+    return int(lib().fgt_nf_for_range(eps, R))
+
+
+def legendre_gauss_integrals(lam, t, nmax):
+    out = np.zeros(nmax + 1)
+    _check(lib().fgt_legendre_gauss_integrals(lam, t, nmax, out.ctypes.data))
+    return out
+
+
+def spherical_bessel(x, nmax):
+    out = np.zeros(nmax + 1)
+    _check(lib().fgt_spherical_bessel(x, nmax, out.ctypes.data))
+    return out
+
+
+def legendre_fourier_integrals(t, nmax):
+    re, im = np.zeros(nmax + 1), np.zeros(nmax + 1)
+    _check(lib().fgt_legendre_fourier_integrals(t, nmax, re.ctypes.data, im.ctypes.data))
+    return re + 1j * im

@@ -1,0 +1,62 @@
+// Device-side execution descriptor: everything one transform launch sequence
+// needs, filled by the planner and consumed by fgt_kernels.cu.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "fgt_internal.h"
+
+namespace fgt {
+
+// One level of the hierarchical merge (child -> parent) or push (parent -> child).
+struct ShiftStep {
+  const TreeShift *items = nullptr;  // device
+  int64_t n = 0;
+  const void *qf = nullptr;          // [2][n1] phase per child half (bit 0 / 1), full-range axes
+  const void *qh = nullptr;          // [2][nh] same for the last (half-range) axis
+};
+
+struct ExecDesc {
+  int d = 0, k = 0, n1 = 0, nh = 0;
+  int prec = 0;                      // 0: FP64 expansions, 1: FP32 expansions
+  int fourier = 0;                   // 1: no out->in gather, evaluation reads the outgoing slot
+  int64_t slot_size = 0;             // complex elements per expansion slot
+  int64_t n_phi_slots = 0, n_psi_slots = 0;
+  void *phi = nullptr, *psi = nullptr;
+
+  // dense block form / evaluation
+  const Block *blocks = nullptr;     // device
+  int64_t n_blocks = 0;
+  int Kmax = 0;
+  const int64_t *block_leaves = nullptr;
+  const void *Ff = nullptr, *Fh = nullptr, *Ef = nullptr, *Eh = nullptr;
+
+  // out->in gather at the cutoff level
+  int64_t n_gather = 0;
+  const int32_t *gather_dst = nullptr;
+  const int64_t *gather_ptr = nullptr;
+  const GatherSrc *gather_src = nullptr;
+  const void *Pf = nullptr, *Ph = nullptr;   // [3][n1], [3][nh]
+
+  // hierarchical mode (empty in fused mode); merge in execution order (fine -> coarse)
+  std::vector<ShiftStep> merge, push;
+
+  // near field (D-list)
+  int64_t n_near = 0;
+  const int64_t *near_tgt = nullptr;
+  const int32_t *near_flags = nullptr;
+  const int64_t *near_ptr = nullptr;
+  const NearSrc *near_src = nullptr;
+  const double *near_tab = nullptr;
+};
+
+// Enqueue the whole transform on `stream`.  sigma, u: device FP64 [n_leaves][k^d].
+cudaError_t run_transform(const ExecDesc &e, const double *sigma, double *u, cudaStream_t stream);
+
+// Shared-memory bytes the form / evaluation kernels need for a block size K.
+size_t form_smem_bytes(int d, int K, int n1, int prec);
+size_t eval_smem_bytes(int d, int K, int n1, int prec);
+int max_dynamic_smem();
+
+}  // namespace fgt

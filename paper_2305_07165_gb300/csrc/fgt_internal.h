@@ -1,0 +1,44 @@
+// Internal structures shared by the host planner (fgt_plan.cpp) and the CUDA
+// kernels (fgt_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+namespace fgt {
+
+constexpr int kMaxK = 16;        // Gauss-Legendre nodes per dimension per leaf
+constexpr int kMaxLevel = 19;    // deepest supported tree level (box keys pack 19 bits per axis)
+constexpr int kNearTypes = 11;   // near-field table kinds per source level (Section 4.1)
+
+// A uniform subtree (or single leaf) that is formed / evaluated as one dense
+// separable transform against the expansion of its anchor box.
+struct Block {
+  int32_t slot;      // anchor expansion slot (outgoing for form, incoming for evaluation)
+  int32_t K;         // nodes per dimension of the block: (1 << dl) * k
+  int32_t dl;        // depth of the uniform subtree; (1 << dl) leaves per dimension
+  int32_t flags;     // evaluation: bit 0 = accumulate into u instead of storing
+  int32_t mat[3];    // per dimension: first 1D matrix id; ids mat..mat+(1<<dl)-1 follow offsets
+  int32_t pad;
+  int64_t leaf0;     // offset into the block-leaf index array; leaves ordered (o_d,..,o_1), o_1 fastest
+};
+
+// One out->in translation source at the cutoff level.
+struct GatherSrc {
+  int32_t slot;      // source outgoing slot
+  int32_t code;      // (o1+1) + 3 (o2+1) + 9 (o3+1), o = S - T in box units
+};
+
+// One near-field (D-list) source for a target leaf.
+struct NearSrc {
+  int64_t leaf;      // source leaf index
+  int32_t tab[3];    // per dimension: table id = source_level * kNearTypes + kind
+  int32_t pad;
+};
+
+// Merge (child -> parent) or push (parent -> child) item of the hierarchical mode.
+struct TreeShift {
+  int32_t parent;    // parent slot
+  int32_t child[8];  // child slots, child c has bit a of c = child's half along axis a
+};
+
+}  // namespace fgt

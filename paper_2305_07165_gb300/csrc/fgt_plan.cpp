@@ -1,0 +1,1107 @@
+// Host planner and C ABI of the box FGT (Algorithm 4, Section 4.2; periodic
+// variant Section 5).  Builds, once per (tree, delta, tol, bc):
+//   - the validated box tree (leaves tile B, 2:1 balance with corners,
+//     Definition treedefs; across the wrap for periodic problems),
+//   - the cutoff level l_c and the plane-wave parameters of Theorem 1
+//     (eqs. (D0), (pwterms)) or the Fourier parameters of Section 2.2,
+//   - the flags f(B) (Definition fflagdef), the P-list (out->in gather at
+//     l_c) and the D-list (near-field pairs) work lists,
+//   - the FP64 1D tables of Section 4.1 (T_val->pw, T_pw->pot with the
+//     separable shift phases folded in, T_val->pot for the 11 neighbour
+//     offsets, the diagonal shift phase vectors),
+// uploads them and sizes the expansion workspace.  Execution is enqueued by
+// fgt_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/fgt.h"
+#include "fgt_exec.h"
+#include "fgt_internal.h"
+#include "fgt_tables.h"
+
+using cd = std::complex<double>;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+thread_local std::string g_err;
+
+fgt_status fail(fgt_status s, const std::string &msg) {
+  g_err = msg;
+  return s;
+}
+
+fgt_status cuda_fail(cudaError_t e, const char *what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return FGT_ERR_CUDA;
+}
+
+inline uint64_t box_key(int level, const int32_t *c) {
+  return ((uint64_t)level << 57) | (uint64_t)c[0] | ((uint64_t)c[1] << 19) | ((uint64_t)c[2] << 38);
+}
+
+struct Box {
+  int32_t level = 0;
+  int32_t c[3] = {0, 0, 0};
+  int32_t parent = -1;
+  int32_t child0 = -1;   // first of 2^d consecutive entries in Plan::children, -1 for a leaf
+  int64_t leaf = -1;     // leaf index, -1 for an internal box
+  int32_t f = 0;         // Definition fflagdef
+  int32_t slot = -1;     // expansion slot
+  int32_t mind = 0, maxd = 0;  // min / max depth of the leaves below, relative to this box
+};
+
+// Bump allocator over one device allocation.
+struct DevPack {
+  std::vector<std::pair<size_t, std::vector<unsigned char>>> parts;
+  std::vector<std::string> names;
+  size_t size = 0;
+  size_t add(const std::string &name, const void *p, size_t bytes) {
+    size_t off = (size + 255) & ~(size_t)255;
+    std::vector<unsigned char> v(bytes);
+    if (bytes) std::memcpy(v.data(), p, bytes);
+    parts.emplace_back(off, std::move(v));
+    names.push_back(name);
+    size = off + bytes;
+    return off;
+  }
+  template <typename T>
+  size_t add(const std::string &name, const std::vector<T> &v) {
+    return add(name, v.data(), v.size() * sizeof(T));
+  }
+};
+
+}  // namespace
+
+struct fgt_plan {
+  int d = 0, k = 0, bc = 0, prec = FGT_PREC_FP64, mode = FGT_MODE_FUSED;
+  double delta = 0, tol = 0, eps_pw = 0;
+  // parameters
+  int lc = 0, fourier = 0, n_f = 0, n_p = 0, M = 0, n1 = 0, nh = 0, lmax = 0;
+  double D0 = 0, R = 0, h = 0, kappa = 0;
+  std::vector<double> wmode;  // weight of mode index a in [0, n1), m = a - (M - 1)
+  // tree
+  int64_t n_leaves = 0;
+  std::vector<int32_t> leaf_level, leaf_coord;
+  std::vector<Box> boxes;
+  std::vector<int32_t> children;
+  std::unordered_map<uint64_t, int32_t> index;
+  std::vector<int32_t> leaf_box;
+  std::vector<std::vector<int32_t>> by_level;
+  // quadrature
+  std::vector<double> eta, weta, Tvp;
+  // device state
+  bool dirty = true;
+  void *dev = nullptr;
+  size_t dev_bytes = 0;
+  void *work = nullptr;
+  size_t work_bytes = 0;
+  double *stage = nullptr;  // host-path staging [2][n_leaves k^d]
+  bool host_only = false;   // planned without a device (inspection only)
+  DevPack host_pack;        // host copy of the uploaded lists and tables (kept for host-only plans)
+  fgt::ExecDesc ex;
+  fgt_plan_info info{};
+  // host copies kept for flop accounting
+  int64_t n_near_pairs = 0, n_gather_pairs = 0, n_blocks = 0;
+
+  int32_t find(int level, const int32_t *c) const {
+    auto it = index.find(box_key(level, c));
+    return it == index.end() ? -1 : it->second;
+  }
+  int np() const { return d == 3 ? k * k * k : k * k; }
+  ~fgt_plan() {
+    if (dev) cudaFree(dev);
+    if (work) cudaFree(work);
+    if (stage) cudaFree(stage);
+  }
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------- parameters
+
+void choose_params(double delta, double eps, int bc, int &lc, double &D0, double &R, double &h, int &M,
+                   int &n_p, int &fourier) {
+  D0 = std::sqrt(std::log(3.0 / eps));
+  const double cut = D0 * std::sqrt(delta);
+  // l_c: the finest level whose boxes are still at least D0 sqrt(delta) wide, so that only
+  // neighbouring boxes interact above the tolerance (Section 3, cutoff level)
+  lc = 0;
+  while (lc < fgt::kMaxLevel && std::ldexp(1.0, -(lc + 1)) >= cut) ++lc;
+  // range covered by the plane waves: |x_i - y_i| <= 2 L_c between colleagues (just L_0 = 1
+  // for the lone root when l_c = 0); Theorem 1 needs R >= D0
+  const double span = (lc == 0) ? 1.0 : 2.0 * std::ldexp(1.0, -lc);
+  R = std::max(span / std::sqrt(delta), D0);
+  h = 2.0 * kPi / (R + D0);
+  M = (int)std::ceil(D0 * (R + D0) / kPi);
+  n_p = (int)std::ceil(std::sqrt(std::log(1.0 / eps)) / (kPi * std::sqrt(delta)));
+  fourier = (bc == FGT_BC_PERIODIC && lc <= 1) ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------- tree
+
+fgt_status build_tree(fgt_plan &P) {
+  const int d = P.d;
+  const int64_t n = P.n_leaves;
+  P.boxes.reserve((size_t)(n * 1.2) + 16);
+  P.leaf_box.assign(n, -1);
+  for (int64_t i = 0; i < n; ++i) {
+    const int lev = P.leaf_level[i];
+    if (lev < 0 || lev > fgt::kMaxLevel)
+      return fail(FGT_ERR_TREE, "leaf " + std::to_string(i) + ": level out of range");
+    Box b;
+    b.level = lev;
+    for (int a = 0; a < d; ++a) {
+      const int32_t c = P.leaf_coord[i * d + a];
+      if (c < 0 || c >= (1 << lev)) return fail(FGT_ERR_TREE, "leaf " + std::to_string(i) + ": coordinate out of range");
+      b.c[a] = c;
+    }
+    b.leaf = i;
+    const uint64_t key = box_key(lev, b.c);
+    if (P.index.count(key)) return fail(FGT_ERR_TREE, "leaf " + std::to_string(i) + " duplicates another leaf");
+    P.index[key] = (int32_t)P.boxes.size();
+    P.leaf_box[i] = (int32_t)P.boxes.size();
+    P.boxes.push_back(b);
+  }
+  // ancestors
+  for (int64_t i = 0; i < n; ++i) {
+    Box cur = P.boxes[P.leaf_box[i]];
+    while (cur.level > 0) {
+      Box par;
+      par.level = cur.level - 1;
+      for (int a = 0; a < d; ++a) par.c[a] = cur.c[a] >> 1;
+      const uint64_t key = box_key(par.level, par.c);
+      auto it = P.index.find(key);
+      if (it != P.index.end()) {
+        if (P.boxes[it->second].leaf >= 0)
+          return fail(FGT_ERR_TREE, "leaf " + std::to_string(i) + " overlaps leaf " +
+                                        std::to_string(P.boxes[it->second].leaf));
+        break;
+      }
+      P.index[key] = (int32_t)P.boxes.size();
+      P.boxes.push_back(par);
+      cur = par;
+    }
+  }
+  // parent / child links
+  const int nc = 1 << d;
+  std::vector<int> nkids(P.boxes.size(), 0);
+  for (size_t b = 0; b < P.boxes.size(); ++b) {
+    Box &bx = P.boxes[b];
+    if (bx.level == 0) continue;
+    int32_t pc[3] = {0, 0, 0};
+    for (int a = 0; a < d; ++a) pc[a] = bx.c[a] >> 1;
+    bx.parent = P.find(bx.level - 1, pc);
+    nkids[bx.parent]++;
+  }
+  const int32_t root_c[3] = {0, 0, 0};
+  if (P.find(0, root_c) < 0) return fail(FGT_ERR_TREE, "empty tree");
+  for (size_t b = 0; b < P.boxes.size(); ++b) {
+    if (P.boxes[b].leaf >= 0) continue;
+    if (nkids[b] != nc) return fail(FGT_ERR_TREE, "leaves do not tile B (a box has missing children)");
+    P.boxes[b].child0 = (int32_t)P.children.size();
+    for (int c = 0; c < nc; ++c) {
+      int32_t cc[3] = {0, 0, 0};
+      for (int a = 0; a < d; ++a) cc[a] = 2 * P.boxes[b].c[a] + ((c >> a) & 1);
+      P.children.push_back(P.find(P.boxes[b].level + 1, cc));
+    }
+  }
+  // levels, depth ranges
+  P.lmax = 0;
+  for (const Box &b : P.boxes) P.lmax = std::max(P.lmax, b.level);
+  P.by_level.assign(P.lmax + 1, {});
+  for (size_t b = 0; b < P.boxes.size(); ++b) P.by_level[P.boxes[b].level].push_back((int32_t)b);
+  for (int l = P.lmax; l >= 0; --l)
+    for (int32_t b : P.by_level[l]) {
+      Box &bx = P.boxes[b];
+      if (bx.leaf >= 0) { bx.mind = bx.maxd = 0; continue; }
+      int mn = 1 << 30, mx = 0;
+      for (int c = 0; c < nc; ++c) {
+        const Box &ch = P.boxes[P.children[bx.child0 + c]];
+        mn = std::min(mn, ch.mind + 1);
+        mx = std::max(mx, ch.maxd + 1);
+      }
+      bx.mind = mn;
+      bx.maxd = mx;
+    }
+  // 2:1 balance across shared boundary points, corners included
+  const bool per = P.bc == FGT_BC_PERIODIC;
+  int noff = 1;
+  for (int a = 0; a < d; ++a) noff *= 3;
+  for (int64_t i = 0; i < n; ++i) {
+    const Box &T = P.boxes[P.leaf_box[i]];
+    const int l = T.level, nb = 1 << l;
+    for (int oc = 0; oc < noff; ++oc) {
+      int o[3] = {0, 0, 0}, q[3] = {0, 0, 0};
+      bool ok = true, zero = true;
+      for (int a = 0, r = oc; a < d; ++a, r /= 3) {
+        o[a] = r % 3 - 1;
+        if (o[a]) zero = false;
+        int v = T.c[a] + o[a];
+        if (v < 0 || v >= nb) {
+          if (!per) { ok = false; break; }
+          v = (v + nb) % nb;
+        }
+        q[a] = v;
+      }
+      if (!ok || zero) continue;
+      const int32_t nbx = P.find(l, q);
+      if (nbx >= 0) {
+        const Box &N = P.boxes[nbx];
+        if (N.leaf >= 0) continue;
+        for (int c = 0; c < nc; ++c) {
+          bool touch = true;
+          for (int a = 0; a < d; ++a) {
+            const int bit = (c >> a) & 1;
+            if ((o[a] == 1 && bit != 0) || (o[a] == -1 && bit != 1)) touch = false;
+          }
+          if (touch && P.boxes[P.children[N.child0 + c]].leaf < 0)
+            return fail(FGT_ERR_TREE, "tree is not 2:1 balanced (leaf " + std::to_string(i) +
+                                          " touches leaves two or more levels finer)");
+        }
+      } else {
+        int32_t pq[3] = {0, 0, 0};
+        for (int a = 0; a < d; ++a) pq[a] = q[a] >> 1;
+        const int32_t pb = (l >= 1) ? P.find(l - 1, pq) : -1;
+        if (pb < 0 || P.boxes[pb].leaf < 0)
+          return fail(FGT_ERR_TREE, "tree is not 2:1 balanced (leaf " + std::to_string(i) +
+                                        " touches a leaf two or more levels coarser)");
+      }
+    }
+  }
+  return FGT_OK;
+}
+
+// ---------------------------------------------------------------------------- tables
+
+// Form matrix of a leaf at level l whose expansion centre is offset by `shift` from the leaf
+// centre: F[a][j] = w_a (L/2) exp(-i kappa m_a shift) sum_n I[P_n](-kappa m_a L/2) Tvp[n][j]
+// (Lemma pwbox with the separable T_c->p shift folded in).
+void form_matrix(const fgt_plan &P, int l, double shift, cd *F) {
+  const int k = P.k;
+  const double L = std::ldexp(1.0, -l);
+  double re[72], im[72];
+  for (int a = 0; a < P.n1; ++a) {
+    const int m = a - (P.M - 1);
+    const double t = -P.kappa * m * 0.5 * L;
+    fgt::legendre_fourier_integrals(t, k - 1, re, im);
+    const cd ph = std::polar(P.wmode[a] * 0.5 * L, -P.kappa * m * shift);
+    for (int j = 0; j < k; ++j) {
+      cd s = 0;
+      for (int nn = 0; nn < k; ++nn) s += cd(re[nn], im[nn]) * P.Tvp[nn * k + j];
+      F[a * k + j] = ph * s;
+    }
+  }
+}
+
+// Evaluation matrix: E[t][a] = exp(i kappa m_a ((L/2) eta_t + shift)) (Lemma thm:pweval, T_pw->pot
+// with T_p->c folded in).
+void eval_matrix(const fgt_plan &P, int l, double shift, cd *E) {
+  const double L = std::ldexp(1.0, -l);
+  for (int t = 0; t < P.k; ++t)
+    for (int a = 0; a < P.n1; ++a) {
+      const int m = a - (P.M - 1);
+      E[t * P.n1 + a] = std::polar(1.0, P.kappa * m * (0.5 * L * P.eta[t] + shift));
+    }
+}
+
+// Near-field table (Lemma directbox): K[t][j] = int_S exp(-(x_t - y)^2/delta) l_j(y) dy for a
+// source of level ls and a target whose centre is offset by o4/4 source sides and whose side is
+// ratio times the source side; = (L/2) sum_n J_lambda[P_n](tau_t) Tvp[n][j], lambda = 2 sqrt(delta)/L.
+void near_table(const fgt_plan &P, int ls, int o4, double ratio, double *K) {
+  const int k = P.k;
+  const double L = std::ldexp(1.0, -ls);
+  const double lam = 2.0 * std::sqrt(P.delta) / L;
+  double J[72];
+  for (int t = 0; t < k; ++t) {
+    const double tau = 0.5 * o4 + ratio * P.eta[t];
+    fgt::gauss_legendre_integrals(lam, tau, k - 1, J);
+    for (int j = 0; j < k; ++j) {
+      double s = 0;
+      for (int nn = 0; nn < k; ++nn) s += J[nn] * P.Tvp[nn * k + j];
+      K[t * k + j] = 0.5 * L * s;
+    }
+  }
+}
+
+// kind of a near-field table from the level difference and the centre offset in quarter source sides
+int near_kind(int ldiff, int o4) {
+  if (ldiff == 0) return o4 == -4 ? 0 : (o4 == 0 ? 1 : (o4 == 4 ? 2 : -1));
+  if (ldiff == 1) return o4 == -3 ? 3 : (o4 == -1 ? 4 : (o4 == 1 ? 5 : (o4 == 3 ? 6 : -1)));
+  if (ldiff == -1) return o4 == -6 ? 7 : (o4 == -2 ? 8 : (o4 == 2 ? 9 : (o4 == 6 ? 10 : -1)));
+  return -1;
+}
+
+void kind_geometry(int kind, int &o4, int &ldiff, double &ratio) {
+  static const int o4s[11] = {-4, 0, 4, -3, -1, 1, 3, -6, -2, 2, 6};
+  o4 = o4s[kind];
+  ldiff = kind < 3 ? 0 : (kind < 7 ? 1 : -1);
+  ratio = ldiff == 0 ? 1.0 : (ldiff == 1 ? 0.5 : 2.0);
+}
+
+template <typename C>
+void push_complex(std::vector<C> &dst, const cd *src, size_t n) {
+  for (size_t i = 0; i < n; ++i) dst.push_back(C{(decltype(C::x))src[i].real(), (decltype(C::x))src[i].imag()});
+}
+
+// ---------------------------------------------------------------------------- device state
+
+struct MatKey {
+  int l, la, obase, dl;
+  bool operator<(const MatKey &o) const { return std::tie(l, la, obase, dl) < std::tie(o.l, o.la, o.obase, o.dl); }
+};
+
+// Algorithmic flop counts of one execution (real flops; complex MAC = 8, real x complex = 4).
+void fill_flops(fgt_plan &P, const fgt::ExecDesc &ex, const std::vector<fgt::Block> &blocks, int64_t shift_flops,
+                size_t n_anchor) {
+  const int d = P.d, k = P.k;
+  const int64_t n1 = P.n1, nh = P.nh;
+  fgt_plan_info &I = P.info;
+  I.n_anchor_boxes = P.fourier ? 1 : (int64_t)n_anchor;
+  I.n_form_blocks = ex.n_blocks;
+  I.n_direct_pairs = P.n_near_pairs;
+  I.n_gather_pairs = P.n_gather_pairs;
+  int64_t ff = 0, ef = 0;
+  for (const fgt::Block &b : blocks) {
+    const int64_t K = b.K;
+    if (d == 3) {
+      ff += 4 * nh * K * K * K + 8 * nh * n1 * K * K + 8 * nh * n1 * n1 * K;
+      ef += K * (8 * nh * n1 * n1 + 8 * K * n1 * n1 + 4 * K * K * n1);
+    } else {
+      ff += 4 * nh * K * K + 8 * nh * n1 * K;
+      ef += K * (8 * nh * n1 + 4 * K * n1);
+    }
+  }
+  I.form_flops = ff;
+  I.eval_flops = ef;
+  I.gather_flops = 8 * P.n_gather_pairs * ex.slot_size + shift_flops;
+  I.direct_flops = P.n_near_pairs * 2 * d * (int64_t)P.np() * k;
+  I.prec = P.prec;
+  I.mode = P.mode;
+}
+
+template <typename C>
+fgt_status prepare_typed(fgt_plan &P, bool upload) {
+  const int d = P.d, k = P.k, n1 = P.n1, nh = P.nh, nc = 1 << d;
+  const bool hier = P.mode == FGT_MODE_HIERARCHICAL && !P.fourier;
+  DevPack pack;
+  fgt::ExecDesc ex;
+  ex.d = d; ex.k = k; ex.n1 = n1; ex.nh = nh; ex.prec = P.prec; ex.fourier = P.fourier;
+  ex.slot_size = (int64_t)nh * (d == 3 ? (int64_t)n1 * n1 : (int64_t)n1);
+
+  // ---- slots and anchors
+  for (Box &b : P.boxes) b.slot = -1;
+  std::vector<int32_t> anchors;  // boxes owning an expansion at the cutoff level (root in Fourier mode)
+  int32_t nslots = 0;
+  if (P.fourier) {
+    const int32_t rc[3] = {0, 0, 0};
+    const int32_t root = P.find(0, rc);
+    P.boxes[root].slot = nslots++;
+    anchors.push_back(root);
+  } else {
+    if (P.lc <= P.lmax)
+      for (int32_t b : P.by_level[P.lc])
+        if (P.boxes[b].f) anchors.push_back(b);
+    if (hier) {
+      for (int l = P.lc; l <= P.lmax; ++l)
+        for (int32_t b : P.by_level[l])
+          if (P.boxes[b].f) P.boxes[b].slot = nslots++;
+    } else {
+      for (int32_t a : anchors) P.boxes[a].slot = nslots++;
+    }
+  }
+  ex.n_phi_slots = nslots;
+  ex.n_psi_slots = P.fourier ? 0 : nslots;
+
+  // ---- smem-limited block size
+  const int smax = upload ? fgt::max_dynamic_smem() : 232448;  // sm_103 opt-in limit without a device
+  int dlcap = 0;
+  while (((2 << dlcap) * k) <= 64) ++dlcap;  // K = 2^dl k <= 64
+  auto fits = [&](int dl) {
+    const int K = (1 << dl) * k;
+    return fgt::form_smem_bytes(d, K, n1, P.prec) <= (size_t)smax &&
+           fgt::eval_smem_bytes(d, K, n1, P.prec) <= (size_t)smax;
+  };
+  while (dlcap > 0 && !fits(dlcap)) --dlcap;
+  if (!fits(0)) return fail(FGT_ERR_ARG, "expansion too large for shared memory (n_f too big for this k)");
+  if (hier) dlcap = 0;
+
+  // ---- blocks
+  std::vector<fgt::Block> blocks;
+  std::vector<int64_t> bleaves;
+  std::map<MatKey, int32_t> matid;
+  std::vector<C> Ff, Fh, Ef, Eh;
+  int32_t nmat = 0;
+  std::vector<cd> Fb((size_t)n1 * k), Eb((size_t)k * n1);
+  auto get_mat = [&](int l, int la, int obase, int dl, double anchor_lo) -> int32_t {
+    MatKey key{l, la, obase, dl};
+    auto it = matid.find(key);
+    if (it != matid.end()) return it->second;
+    const int32_t id = nmat;
+    const double L = std::ldexp(1.0, -l), La = std::ldexp(1.0, -la);
+    for (int o = obase; o < obase + (1 << dl); ++o) {
+      // leaf centre minus anchor centre along this axis (anchor_lo is unused: offsets are relative)
+      const double shift = (o + 0.5) * L - 0.5 * La;
+      (void)anchor_lo;
+      form_matrix(P, l, shift, Fb.data());
+      eval_matrix(P, l, shift, Eb.data());
+      push_complex(Ff, Fb.data(), Fb.size());
+      for (int b = 0; b < nh; ++b)
+        for (int j = 0; j < k; ++j) {
+          const cd v = Fb[(size_t)(P.M - 1 + b) * k + j] * (b == 0 ? 1.0 : 2.0);
+          Fh.push_back(C{(decltype(C::x))v.real(), (decltype(C::x))v.imag()});
+        }
+      push_complex(Ef, Eb.data(), Eb.size());
+      for (int t = 0; t < k; ++t)
+        for (int b = 0; b < nh; ++b) {
+          const cd v = Eb[(size_t)t * n1 + P.M - 1 + b];
+          Eh.push_back(C{(decltype(C::x))v.real(), (decltype(C::x))v.imag()});
+        }
+      ++nmat;
+    }
+    matid[key] = id;
+    return id;
+  };
+  std::vector<int32_t> stack;
+  int Kmax = 0;
+  auto add_block = [&](int32_t bb, int32_t anchor, int dl) {
+    const Box &B = P.boxes[bb];
+    const Box &A = P.boxes[anchor];
+    fgt::Block blk{};
+    blk.slot = A.slot;
+    blk.dl = dl;
+    blk.K = (1 << dl) * k;
+    blk.flags = 0;
+    const int l = B.level + dl, nl = 1 << dl;
+    for (int a = 0; a < d; ++a) {
+      const int obase = (B.c[a] << dl) - (A.c[a] << (l - A.level));
+      blk.mat[a] = get_mat(l, A.level, obase, dl, 0.0);
+    }
+    blk.leaf0 = (int64_t)bleaves.size();
+    int32_t q[3] = {0, 0, 0};
+    const int tot = d == 3 ? nl * nl * nl : nl * nl;
+    for (int idx = 0; idx < tot; ++idx) {
+      int r = idx;
+      for (int a = 0; a < d; ++a) { q[a] = (B.c[a] << dl) + (r % nl); r /= nl; }
+      const int32_t lb = P.find(l, q);
+      bleaves.push_back(P.boxes[lb].leaf);
+    }
+    Kmax = std::max(Kmax, blk.K);
+    blocks.push_back(blk);
+  };
+  if (hier) {
+    for (int64_t i = 0; i < P.n_leaves; ++i) {
+      const int32_t b = P.leaf_box[i];
+      if (P.boxes[b].f) add_block(b, b, 0);
+    }
+  } else {
+    for (int32_t a : anchors) {
+      stack.assign(1, a);
+      while (!stack.empty()) {
+        const int32_t b = stack.back();
+        stack.pop_back();
+        const Box &B = P.boxes[b];
+        if (B.mind == B.maxd && B.maxd <= dlcap) {
+          add_block(b, a, B.maxd);
+        } else {
+          for (int c = nc - 1; c >= 0; --c) stack.push_back(P.children[B.child0 + c]);
+        }
+      }
+    }
+  }
+  ex.n_blocks = (int64_t)blocks.size();
+  ex.Kmax = Kmax;
+  P.n_blocks = ex.n_blocks;
+
+  // ---- out->in gather at the cutoff level (P-list)
+  std::vector<int32_t> gdst;
+  std::vector<int64_t> gptr(1, 0);
+  std::vector<fgt::GatherSrc> gsrc;
+  const bool per = P.bc == FGT_BC_PERIODIC;
+  int noff = 1;
+  for (int a = 0; a < d; ++a) noff *= 3;
+  if (!P.fourier) {
+    const int nb = 1 << P.lc;
+    for (int32_t T : anchors) {
+      const Box &Tb = P.boxes[T];
+      for (int oc = 0; oc < noff; ++oc) {
+        int32_t q[3] = {0, 0, 0};
+        bool ok = true;
+        int code = 0, mul = 1;
+        for (int a = 0, r = oc; a < d; ++a, r /= 3) {
+          const int o = r % 3 - 1;
+          int v = Tb.c[a] + o;
+          if (v < 0 || v >= nb) {
+            if (!per) { ok = false; break; }
+            v = (v + nb) % nb;
+          }
+          q[a] = v;
+          code += (o + 1) * mul;
+          mul *= 3;
+        }
+        if (!ok) continue;
+        const int32_t S = P.find(P.lc, q);
+        if (S < 0 || !P.boxes[S].f) continue;
+        gsrc.push_back(fgt::GatherSrc{P.boxes[S].slot, code});
+      }
+      gdst.push_back(Tb.slot);
+      gptr.push_back((int64_t)gsrc.size());
+    }
+  }
+  ex.n_gather = (int64_t)gdst.size();
+  P.n_gather_pairs = (int64_t)gsrc.size();
+  // phase vectors of T_out->in: S = T + o (box units) gives c_T - c_S = -o L_c
+  std::vector<C> Pf, Ph;
+  {
+    const double Lc = std::ldexp(1.0, -P.lc);
+    for (int o = -1; o <= 1; ++o)
+      for (int a = 0; a < n1; ++a) {
+        const cd v = std::polar(1.0, -P.kappa * (a - (P.M - 1)) * o * Lc);
+        Pf.push_back(C{(decltype(C::x))v.real(), (decltype(C::x))v.imag()});
+      }
+    for (int o = -1; o <= 1; ++o)
+      for (int b = 0; b < nh; ++b) {
+        const cd v = std::polar(1.0, -P.kappa * b * o * Lc);
+        Ph.push_back(C{(decltype(C::x))v.real(), (decltype(C::x))v.imag()});
+      }
+  }
+
+  // ---- hierarchical merge / push lists and phases
+  struct StepHost { std::vector<fgt::TreeShift> items; std::vector<C> qf, qh; };
+  std::vector<StepHost> merge_h, push_h;
+  if (hier) {
+    auto phases = [&](int child_level, double sign, std::vector<C> &qf, std::vector<C> &qh) {
+      const double Lch = std::ldexp(1.0, -child_level);
+      for (int bit = 0; bit < 2; ++bit)
+        for (int a = 0; a < n1; ++a) {
+          const cd v = std::polar(1.0, sign * P.kappa * (a - (P.M - 1)) * (bit - 0.5) * Lch);
+          qf.push_back(C{(decltype(C::x))v.real(), (decltype(C::x))v.imag()});
+        }
+      for (int bit = 0; bit < 2; ++bit)
+        for (int b = 0; b < nh; ++b) {
+          const cd v = std::polar(1.0, sign * P.kappa * b * (bit - 0.5) * Lch);
+          qh.push_back(C{(decltype(C::x))v.real(), (decltype(C::x))v.imag()});
+        }
+    };
+    auto items_at = [&](int l) {
+      std::vector<fgt::TreeShift> v;
+      for (int32_t b : P.by_level[l]) {
+        const Box &B = P.boxes[b];
+        if (B.leaf >= 0 || !B.f) continue;
+        fgt::TreeShift it{};
+        it.parent = B.slot;
+        for (int c = 0; c < nc; ++c) it.child[c] = P.boxes[P.children[B.child0 + c]].slot;
+        v.push_back(it);
+      }
+      return v;
+    };
+    for (int l = P.lmax - 1; l >= P.lc; --l) {
+      StepHost s;
+      s.items = items_at(l);
+      phases(l + 1, -1.0, s.qf, s.qh);  // T_c->p = exp(-i k (c_child - c_parent))
+      merge_h.push_back(std::move(s));
+    }
+    for (int l = P.lc; l <= P.lmax - 1; ++l) {
+      StepHost s;
+      s.items = items_at(l);
+      phases(l + 1, +1.0, s.qf, s.qh);  // T_p->c = exp(+i k (c_child - c_parent))
+      push_h.push_back(std::move(s));
+    }
+  }
+
+  // ---- near field (D-list)
+  std::vector<int64_t> ntgt, nptr(1, 0);
+  std::vector<int32_t> nflags;
+  std::vector<fgt::NearSrc> nsrc;
+  std::vector<double> ntab;
+  if (!P.fourier) {
+    const int ltab = std::min(P.lc, P.lmax);
+    std::vector<char> level_used(ltab + 1, 0);
+    struct Cand { int32_t box; int n[3]; };
+    std::vector<Cand> cands;
+    for (int64_t i = 0; i < P.n_leaves; ++i) {
+      const int32_t T = P.leaf_box[i];
+      const Box &Tb = P.boxes[T];
+      if (Tb.level > P.lc) continue;
+      const int l = Tb.level, nb = 1 << l;
+      cands.clear();
+      for (int oc = 0; oc < noff; ++oc) {
+        int o[3] = {0, 0, 0}, q[3] = {0, 0, 0}, img[3] = {0, 0, 0};
+        bool ok = true;
+        for (int a = 0, r = oc; a < d; ++a, r /= 3) {
+          o[a] = r % 3 - 1;
+          int v = Tb.c[a] + o[a];
+          if (v < 0 || v >= nb) {
+            if (!per) { ok = false; break; }
+            img[a] = v < 0 ? -1 : 1;
+            v -= img[a] * nb;
+          }
+          q[a] = v;
+        }
+        if (!ok) continue;
+        const int32_t N = P.find(l, q);
+        auto add = [&](int32_t s) {
+          for (const Cand &c : cands)
+            if (c.box == s && c.n[0] == img[0] && c.n[1] == img[1] && c.n[2] == img[2]) return;
+          cands.push_back(Cand{s, {img[0], img[1], img[2]}});
+        };
+        if (N >= 0) {
+          const Box &Nb = P.boxes[N];
+          if (Nb.leaf >= 0) {
+            add(N);
+          } else if (l < P.lc) {
+            for (int c = 0; c < nc; ++c) {
+              bool touch = true;
+              for (int a = 0; a < d; ++a) {
+                const int bit = (c >> a) & 1;
+                if ((o[a] == 1 && bit != 0) || (o[a] == -1 && bit != 1)) touch = false;
+              }
+              if (touch) add(P.children[Nb.child0 + c]);
+            }
+          }
+        } else {
+          int32_t pq[3] = {0, 0, 0};
+          for (int a = 0; a < d; ++a) pq[a] = q[a] >> 1;
+          const int32_t cb = (l >= 1) ? P.find(l - 1, pq) : -1;
+          if (cb < 0) return fail(FGT_ERR_TREE, "internal: missing coarse neighbour");
+          add(cb);
+        }
+      }
+      const size_t before = nsrc.size();
+      for (const Cand &c : cands) {
+        const Box &Sb = P.boxes[c.box];
+        if (Tb.level == P.lc && Sb.level == P.lc && Tb.f && Sb.f) continue;  // plane-wave pair
+        fgt::NearSrc ns{};
+        ns.leaf = Sb.leaf;
+        const double Ls = std::ldexp(1.0, -Sb.level), Lt = std::ldexp(1.0, -Tb.level);
+        for (int a = 0; a < d; ++a) {
+          const double ct = -0.5 + (Tb.c[a] + 0.5) * Lt;
+          const double cs = -0.5 + (Sb.c[a] + 0.5) * Ls + c.n[a];
+          const int o4 = (int)std::lround(4.0 * (ct - cs) / Ls);
+          const int kind = near_kind(Tb.level - Sb.level, o4);
+          if (kind < 0) return fail(FGT_ERR_TREE, "internal: unexpected neighbour geometry");
+          ns.tab[a] = Sb.level * fgt::kNearTypes + kind;
+        }
+        level_used[Sb.level] = 1;
+        nsrc.push_back(ns);
+      }
+      if (nsrc.size() > before) {
+        ntgt.push_back(i);
+        nflags.push_back(Tb.f ? 1 : 0);
+        nptr.push_back((int64_t)nsrc.size());
+      }
+    }
+    ntab.assign((size_t)(ltab + 1) * fgt::kNearTypes * k * k, 0.0);
+    for (int l = 0; l <= ltab; ++l) {
+      if (!level_used[l]) continue;
+      for (int kind = 0; kind < fgt::kNearTypes; ++kind) {
+        int o4, ldiff;
+        double ratio;
+        kind_geometry(kind, o4, ldiff, ratio);
+        near_table(P, l, o4, ratio, ntab.data() + ((size_t)l * fgt::kNearTypes + kind) * k * k);
+      }
+    }
+  }
+  ex.n_near = (int64_t)ntgt.size();
+  P.n_near_pairs = (int64_t)nsrc.size();
+
+  // ---- upload
+  const size_t o_blocks = pack.add("blocks", blocks), o_bleaves = pack.add("block_leaves", bleaves);
+  const size_t o_Ff = pack.add("Ff", Ff), o_Fh = pack.add("Fh", Fh), o_Ef = pack.add("Ef", Ef),
+               o_Eh = pack.add("Eh", Eh);
+  const size_t o_gdst = pack.add("gather_dst", gdst), o_gptr = pack.add("gather_ptr", gptr),
+               o_gsrc = pack.add("gather_src", gsrc);
+  const size_t o_Pf = pack.add("Pf", Pf), o_Ph = pack.add("Ph", Ph);
+  const size_t o_ntgt = pack.add("near_tgt", ntgt), o_nflags = pack.add("near_flags", nflags),
+               o_nptr = pack.add("near_ptr", nptr), o_nsrc = pack.add("near_src", nsrc),
+               o_ntab = pack.add("near_tab", ntab);
+  std::vector<std::tuple<size_t, size_t, size_t, int64_t>> step_off;  // items, qf, qh, n
+  for (size_t i = 0; i < merge_h.size(); ++i) {
+    auto &s = merge_h[i];
+    const std::string b = "merge" + std::to_string(i) + "_";
+    step_off.emplace_back(pack.add(b + "items", s.items), pack.add(b + "qf", s.qf), pack.add(b + "qh", s.qh),
+                          (int64_t)s.items.size());
+  }
+  for (size_t i = 0; i < push_h.size(); ++i) {
+    auto &s = push_h[i];
+    const std::string b = "push" + std::to_string(i) + "_";
+    step_off.emplace_back(pack.add(b + "items", s.items), pack.add(b + "qf", s.qf), pack.add(b + "qh", s.qh),
+                          (int64_t)s.items.size());
+  }
+
+  const size_t slot_bytes = sizeof(C) * (size_t)ex.slot_size;
+  const size_t phi_bytes = slot_bytes * (size_t)ex.n_phi_slots, psi_bytes = slot_bytes * (size_t)ex.n_psi_slots;
+  fill_flops(P, ex, blocks, merge_h.size() + push_h.size() ? [&] {
+    int64_t sf = 0;
+    for (auto &s : merge_h) sf += 8 * (int64_t)s.items.size() * nc * ex.slot_size;
+    for (auto &s : push_h) sf += 8 * (int64_t)s.items.size() * nc * ex.slot_size;
+    return sf;
+  }() : 0, anchors.size());
+  P.info.device_bytes = (int64_t)(pack.size + phi_bytes + psi_bytes);
+  if (!upload) {
+    P.ex = ex;
+    P.host_pack = std::move(pack);
+    P.dirty = false;
+    return FGT_OK;
+  }
+  if (P.dev) { cudaFree(P.dev); P.dev = nullptr; P.dev_bytes = 0; }
+  if (P.work) { cudaFree(P.work); P.work = nullptr; P.work_bytes = 0; }
+  cudaError_t e = cudaMalloc(&P.dev, std::max<size_t>(pack.size, 256));
+  if (e != cudaSuccess) { P.dev = nullptr; return e == cudaErrorMemoryAllocation ? fail(FGT_ERR_OOM, "device tables") : cuda_fail(e, "cudaMalloc"); }
+  P.dev_bytes = pack.size;
+  for (auto &pt : pack.parts)
+    if (!pt.second.empty()) {
+      e = cudaMemcpy((char *)P.dev + pt.first, pt.second.data(), pt.second.size(), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return cuda_fail(e, "upload");
+    }
+  P.work_bytes = phi_bytes + psi_bytes;
+  if (P.work_bytes) {
+    e = cudaMalloc(&P.work, P.work_bytes);
+    if (e != cudaSuccess) {
+      P.work = nullptr;
+      P.work_bytes = 0;
+      cudaGetLastError();
+      return fail(FGT_ERR_OOM, "expansion workspace of " + std::to_string(phi_bytes + psi_bytes) + " bytes");
+    }
+  }
+  auto at = [&](size_t off) { return (const void *)((const char *)P.dev + off); };
+  ex.phi = P.work;
+  ex.psi = (char *)P.work + phi_bytes;
+  ex.blocks = (const fgt::Block *)at(o_blocks);
+  ex.block_leaves = (const int64_t *)at(o_bleaves);
+  ex.Ff = at(o_Ff); ex.Fh = at(o_Fh); ex.Ef = at(o_Ef); ex.Eh = at(o_Eh);
+  ex.gather_dst = (const int32_t *)at(o_gdst);
+  ex.gather_ptr = (const int64_t *)at(o_gptr);
+  ex.gather_src = (const fgt::GatherSrc *)at(o_gsrc);
+  ex.Pf = at(o_Pf); ex.Ph = at(o_Ph);
+  ex.near_tgt = (const int64_t *)at(o_ntgt);
+  ex.near_flags = (const int32_t *)at(o_nflags);
+  ex.near_ptr = (const int64_t *)at(o_nptr);
+  ex.near_src = (const fgt::NearSrc *)at(o_nsrc);
+  ex.near_tab = (const double *)at(o_ntab);
+  size_t si = 0;
+  for (size_t s = 0; s < merge_h.size(); ++s, ++si) {
+    fgt::ShiftStep st;
+    st.items = (const fgt::TreeShift *)at(std::get<0>(step_off[si]));
+    st.qf = at(std::get<1>(step_off[si]));
+    st.qh = at(std::get<2>(step_off[si]));
+    st.n = std::get<3>(step_off[si]);
+    ex.merge.push_back(st);
+  }
+  for (size_t s = 0; s < push_h.size(); ++s, ++si) {
+    fgt::ShiftStep st;
+    st.items = (const fgt::TreeShift *)at(std::get<0>(step_off[si]));
+    st.qf = at(std::get<1>(step_off[si]));
+    st.qh = at(std::get<2>(step_off[si]));
+    st.n = std::get<3>(step_off[si]);
+    ex.push.push_back(st);
+  }
+  P.ex = ex;
+
+  P.dirty = false;
+  return FGT_OK;
+}
+
+fgt_status prepare(fgt_plan &P, bool upload = true) {
+  if (P.prec == FGT_PREC_SPLIT) return prepare_typed<float2>(P, upload);
+  return prepare_typed<double2>(P, upload);
+}
+
+fgt_status create_impl(int d, double delta, double tol, double eps_pw, int bc, int prec, int mode,
+                       const fgt_tree *tree, fgt_plan **out, bool upload = true) {
+  if (!out) return fail(FGT_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (d != 2 && d != 3) return fail(FGT_ERR_ARG, "d must be 2 or 3");
+  if (!tree || tree->d != d) return fail(FGT_ERR_ARG, "tree missing or tree->d != d");
+  if (tree->k < 1 || tree->k > fgt::kMaxK) return fail(FGT_ERR_ARG, "k must be in [1, 16]");
+  if (tree->n_leaves < 1 || !tree->leaf_level || !tree->leaf_coord) return fail(FGT_ERR_ARG, "empty tree");
+  if (!(delta > 0) || !std::isfinite(delta)) return fail(FGT_ERR_ARG, "delta must be positive");
+  if (!(tol >= 1e-14 && tol <= 1e-1)) return fail(FGT_ERR_ARG, "tol must be in [1e-14, 1e-1]");
+  if (bc != FGT_BC_FREE && bc != FGT_BC_PERIODIC) return fail(FGT_ERR_ARG, "bad bc");
+  if (prec != FGT_PREC_FP64 && prec != FGT_PREC_SPLIT) return fail(FGT_ERR_ARG, "bad precision");
+  if (prec == FGT_PREC_SPLIT && tol < 1e-7) return fail(FGT_ERR_ARG, "split precision needs tol >= 1e-7");
+  if (mode != FGT_MODE_FUSED && mode != FGT_MODE_HIERARCHICAL) return fail(FGT_ERR_ARG, "bad mode");
+  fgt_plan *P = new (std::nothrow) fgt_plan();
+  if (!P) return fail(FGT_ERR_OOM, "host allocation");
+  P->d = d; P->k = tree->k; P->bc = bc; P->prec = prec; P->mode = mode;
+  P->delta = delta; P->tol = tol; P->eps_pw = eps_pw > 0 ? eps_pw : tol;
+  P->n_leaves = tree->n_leaves;
+  P->leaf_level.assign(tree->leaf_level, tree->leaf_level + tree->n_leaves);
+  P->leaf_coord.assign(tree->leaf_coord, tree->leaf_coord + tree->n_leaves * d);
+  fgt_status s = build_tree(*P);
+  if (s != FGT_OK) { delete P; return s; }
+  // parameters
+  choose_params(delta, P->eps_pw, bc, P->lc, P->D0, P->R, P->h, P->M, P->n_p, P->fourier);
+  P->n_f = 2 * P->M;
+  if (P->fourier) {
+    P->M = P->n_p + 1;     // modes -n_p..n_p
+    P->kappa = 2.0 * kPi;
+    P->n_f = 0;
+  } else {
+    P->kappa = P->h / std::sqrt(delta);
+    P->n_p = 0;
+  }
+  P->n1 = 2 * P->M - 1;
+  P->nh = P->M;
+  P->wmode.resize(P->n1);
+  for (int a = 0; a < P->n1; ++a) {
+    const int m = a - (P->M - 1);
+    P->wmode[a] = P->fourier ? std::sqrt(kPi * delta) * std::exp(-kPi * kPi * delta * m * m)
+                             : P->h / (2.0 * std::sqrt(kPi)) * std::exp(-0.25 * m * m * P->h * P->h);
+  }
+  // f flags (Definition fflagdef); Fourier mode: every leaf is evaluated from the root series
+  for (Box &b : P->boxes) b.f = 0;
+  if (P->fourier) {
+    for (Box &b : P->boxes) b.f = 1;
+  } else {
+    const int nb = 1 << P->lc;
+    int noff = 1;
+    for (int a = 0; a < d; ++a) noff *= 3;
+    for (Box &b : P->boxes) {
+      if (b.level > P->lc) { b.f = 1; continue; }
+      if (b.level < P->lc) continue;
+      for (int oc = 0; oc < noff && !b.f; ++oc) {
+        int32_t q[3] = {0, 0, 0};
+        bool ok = true;
+        for (int a = 0, r = oc; a < d; ++a, r /= 3) {
+          int v = b.c[a] + r % 3 - 1;
+          if (v < 0 || v >= nb) {
+            if (bc != FGT_BC_PERIODIC) { ok = false; break; }
+            v = (v + nb) % nb;
+          }
+          q[a] = v;
+        }
+        if (!ok) continue;
+        const int32_t S = P->find(P->lc, q);
+        if (S >= 0 && P->boxes[S].leaf < 0) b.f = 1;
+      }
+    }
+  }
+  // quadrature and values -> coefficients
+  P->eta.resize(P->k);
+  P->weta.resize(P->k);
+  fgt::gl_rule(P->k, P->eta.data(), P->weta.data());
+  P->Tvp.resize((size_t)P->k * P->k);
+  fgt::val_to_pol(P->k, P->eta.data(), P->weta.data(), P->Tvp.data());
+  s = prepare(*P, upload);
+  if (s != FGT_OK) { delete P; return s; }
+  *out = P;
+  return FGT_OK;
+}
+
+void fill_info(const fgt_plan &P, fgt_plan_info &I) {
+  I.d = P.d; I.k = P.k; I.bc = P.bc;
+  I.cutoff_level = P.lc; I.fourier = P.fourier; I.max_level = P.lmax;
+  I.n_f = P.n_f; I.n_p = P.n_p; I.modes_1d = P.n1; I.modes_half = P.nh;
+  I.delta = P.delta; I.tol = P.tol; I.eps_pw = P.eps_pw;
+  I.D0 = P.D0; I.R = P.R; I.h = P.h;
+  I.n_leaves = P.n_leaves; I.n_boxes = (int64_t)P.boxes.size();
+  int64_t npw = 0;
+  for (int64_t i = 0; i < P.n_leaves; ++i) npw += P.boxes[P.leaf_box[i]].f ? 1 : 0;
+  I.n_pw_leaves = npw;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+
+extern "C" {
+
+fgt_status fgt_plan_create_ex(int d, double delta, double tol, double eps_pw, int bc, int prec, int mode,
+                              const fgt_tree *tree, fgt_plan **out) {
+  try {
+    return create_impl(d, delta, tol, eps_pw, bc, prec, mode, tree, out);
+  } catch (const std::bad_alloc &) {
+    return fail(FGT_ERR_OOM, "host allocation");
+  } catch (...) {
+    return fail(FGT_ERR_ARG, "unexpected host exception");
+  }
+}
+
+fgt_status fgt_plan_analyze(int d, double delta, double tol, double eps_pw, int bc, int prec, int mode,
+                            const fgt_tree *tree, fgt_plan_info *info) {
+  if (!info) return fail(FGT_ERR_ARG, "info is NULL");
+  try {
+    fgt_plan *P = nullptr;
+    fgt_status s = create_impl(d, delta, tol, eps_pw, bc, prec, mode, tree, &P, false);
+    if (s != FGT_OK) return s;
+    *info = P->info;
+    fill_info(*P, *info);
+    delete P;
+    return FGT_OK;
+  } catch (const std::bad_alloc &) {
+    return fail(FGT_ERR_OOM, "host allocation");
+  }
+}
+
+fgt_status fgt_plan_create_host(int d, double delta, double tol, double eps_pw, int bc, int prec, int mode,
+                                const fgt_tree *tree, fgt_plan **out) {
+  try {
+    fgt_status s = create_impl(d, delta, tol, eps_pw, bc, prec, mode, tree, out, false);
+    if (s == FGT_OK) (*out)->host_only = true;
+    return s;
+  } catch (const std::bad_alloc &) {
+    return fail(FGT_ERR_OOM, "host allocation");
+  }
+}
+
+fgt_status fgt_plan_host_array(const fgt_plan *plan, const char *name, const void **data, size_t *bytes) {
+  if (!plan || !name || !data || !bytes) return fail(FGT_ERR_ARG, "NULL argument");
+  if (!plan->host_only) return fail(FGT_ERR_STATE, "host arrays are kept only by host-only plans");
+  const DevPack &pk = plan->host_pack;
+  for (size_t i = 0; i < pk.names.size(); ++i)
+    if (pk.names[i] == name) {
+      *data = pk.parts[i].second.data();
+      *bytes = pk.parts[i].second.size();
+      return FGT_OK;
+    }
+  return fail(FGT_ERR_ARG, std::string("no host array named ") + name);
+}
+
+fgt_status fgt_plan_create(int d, double delta, double tol, int bc, const fgt_tree *tree, fgt_plan **out) {
+  return fgt_plan_create_ex(d, delta, tol, 0.0, bc, FGT_PREC_FP64, FGT_MODE_FUSED, tree, out);
+}
+
+fgt_status fgt_plan_set_precision(fgt_plan *plan, int prec) {
+  if (!plan) return fail(FGT_ERR_ARG, "plan is NULL");
+  if (prec != FGT_PREC_FP64 && prec != FGT_PREC_SPLIT) return fail(FGT_ERR_ARG, "bad precision");
+  if (prec == FGT_PREC_SPLIT && plan->tol < 1e-7) return fail(FGT_ERR_ARG, "split precision needs tol >= 1e-7");
+  if (plan->prec != prec) { plan->prec = prec; plan->dirty = true; }
+  return FGT_OK;
+}
+
+fgt_status fgt_plan_set_mode(fgt_plan *plan, int mode) {
+  if (!plan) return fail(FGT_ERR_ARG, "plan is NULL");
+  if (mode != FGT_MODE_FUSED && mode != FGT_MODE_HIERARCHICAL) return fail(FGT_ERR_ARG, "bad mode");
+  if (plan->mode != mode) { plan->mode = mode; plan->dirty = true; }
+  return FGT_OK;
+}
+
+fgt_status fgt_plan_get_info(const fgt_plan *plan, fgt_plan_info *info) {
+  if (!plan || !info) return fail(FGT_ERR_ARG, "NULL argument");
+  if (plan->dirty) {
+    try {
+      fgt_status s = prepare(*const_cast<fgt_plan *>(plan), !plan->host_only);
+      if (s != FGT_OK) return s;
+    } catch (...) {
+      return fail(FGT_ERR_OOM, "host allocation");
+    }
+  }
+  *info = plan->info;
+  fill_info(*plan, *info);
+  return FGT_OK;
+}
+
+size_t fgt_plan_device_bytes(const fgt_plan *plan) {
+  if (!plan) return 0;
+  return plan->dev_bytes + plan->work_bytes + (plan->stage ? sizeof(double) * 2 * plan->n_leaves * plan->np() : 0);
+}
+
+fgt_status fgt_execute_async(fgt_plan *plan, const double *sigma_dev, double *u_dev, void *stream) {
+  if (!plan || !sigma_dev || !u_dev) return fail(FGT_ERR_ARG, "NULL argument");
+  if (plan->host_only) return fail(FGT_ERR_STATE, "host-only plan cannot execute");
+  if (plan->dirty) {
+    fgt_status s;
+    try {
+      s = prepare(*plan);
+    } catch (...) {
+      return fail(FGT_ERR_OOM, "host allocation");
+    }
+    if (s != FGT_OK) return s;
+  }
+  cudaError_t e = fgt::run_transform(plan->ex, sigma_dev, u_dev, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "transform launch");
+  return FGT_OK;
+}
+
+fgt_status fgt_execute(fgt_plan *plan, const double *sigma_dev, double *u_dev) {
+  fgt_status s = fgt_execute_async(plan, sigma_dev, u_dev, nullptr);
+  if (s != FGT_OK) return s;
+  cudaError_t e = cudaStreamSynchronize(nullptr);
+  if (e != cudaSuccess) return cuda_fail(e, "transform");
+  return FGT_OK;
+}
+
+fgt_status fgt_execute_host(fgt_plan *plan, const double *sigma_host, double *u_host, void *stream) {
+  if (!plan || !sigma_host || !u_host) return fail(FGT_ERR_ARG, "NULL argument");
+  if (plan->host_only) return fail(FGT_ERR_STATE, "host-only plan cannot execute");
+  const size_t n = (size_t)plan->n_leaves * plan->np();
+  if (!plan->stage) {
+    cudaError_t e = cudaMalloc(&plan->stage, sizeof(double) * 2 * n);
+    if (e != cudaSuccess) { plan->stage = nullptr; cudaGetLastError(); return fail(FGT_ERR_OOM, "staging buffers"); }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  double *sd = plan->stage, *ud = plan->stage + n;
+  cudaError_t e = cudaMemcpyAsync(sd, sigma_host, sizeof(double) * n, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "copy in");
+  fgt_status s = fgt_execute_async(plan, sd, ud, stream);
+  if (s != FGT_OK) return s;
+  e = cudaMemcpyAsync(u_host, ud, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e, "copy out");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "transform");
+  return FGT_OK;
+}
+
+void fgt_destroy(fgt_plan *plan) { delete plan; }
+
+const char *fgt_last_error(void) { return g_err.c_str(); }
+
+fgt_status fgt_gauss_legendre(int k, double *nodes, double *weights) {
+  if (k < 1 || k > 64 || !nodes || !weights) return fail(FGT_ERR_ARG, "k must be in [1, 64]");
+  fgt::gl_rule(k, nodes, weights);
+  return FGT_OK;
+}
+
+fgt_status fgt_params(double delta, double eps, int bc, int32_t *cutoff_level, double *D0, double *R, double *h,
+                      int32_t *n_f, int32_t *n_p) {
+  if (!(delta > 0) || !(eps > 0 && eps < 1)) return fail(FGT_ERR_ARG, "bad delta or eps");
+  int lc, M, np, fourier;
+  double d0, r, hh;
+  choose_params(delta, eps, bc, lc, d0, r, hh, M, np, fourier);
+  if (cutoff_level) *cutoff_level = lc;
+  if (D0) *D0 = d0;
+  if (R) *R = r;
+  if (h) *h = hh;
+  if (n_f) *n_f = 2 * M;
+  if (n_p) *n_p = np;
+  return FGT_OK;
+}
+
+int32_t fgt_nf_for_range(double eps, double R) {
+  const double D0 = std::sqrt(std::log(3.0 / eps));
+  return 2 * (int32_t)std::ceil(D0 * (R + D0) / kPi);
+}
+
+fgt_status fgt_legendre_gauss_integrals(double lambda, double t, int nmax, double *out) {
+  if (!(lambda > 0) || nmax < 0 || nmax > 70 || !out) return fail(FGT_ERR_ARG, "bad argument");
+  fgt::gauss_legendre_integrals(lambda, t, nmax, out);
+  return FGT_OK;
+}
+
+fgt_status fgt_spherical_bessel(double x, int nmax, double *out) {
+  if (nmax < 0 || nmax > 70 || !out || !std::isfinite(x) || std::fabs(x) > 1e4)
+    return fail(FGT_ERR_ARG, "bad argument");
+  fgt::spherical_bessel(x, nmax, out);
+  return FGT_OK;
+}
+
+fgt_status fgt_legendre_fourier_integrals(double t, int nmax, double *re, double *im) {
+  if (nmax < 0 || nmax > 70 || !re || !im || !std::isfinite(t) || std::fabs(t) > 1e4)
+    return fail(FGT_ERR_ARG, "bad argument");
+  fgt::legendre_fourier_integrals(t, nmax, re, im);
+  return FGT_OK;
+}
+
+}  // extern "C"
