@@ -1,0 +1,293 @@
+"""Benchmark: box fast Gauss transform throughput on one GB300 (or N replicas).
+
+One step = one full transform (Algorithm 4: form, gather, evaluate, near field)
+of a seeded 3D free-space density on an adaptive 2:1-balanced tree refined
+around 8 Gaussians (p = 8, about 2.1M target points), delta = 1e-3.
+
+Printed value: target points/s of the split-precision form at tol 1e-6, next to
+the plain FP64 form at tol 1e-6 and 1e-10 (all on the same GPU), with p50/p99
+step latency, the dominant kernel's roofline fraction, an end-to-end number
+through the host-buffer entry point, and the CPU oracle timed on a bounded
+sample of target leaves.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Multi-GPU: the transform does not shard across GPUs here; N ranks run N
+independent replicas (weak scaling) and rank 0 reports the whole-job rate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 / FP32 CUDA-core peaks of GB300 from unit counts and the maximum SM clock:
+# 152 SMs x 2 FP64 FMA/clk (x2 flops) x 2.07 GHz, and 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload():
+    import workloads as W
+    return W.config_3d_free_adaptive(seed=0, p=8, delta=1e-3)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while active."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+
+    def summary(self):
+        rows = getattr(self, "rows", [])
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def time_steps(plan, sigma, out, steps, warmup, flush):
+    """Per-step device times (ms) with an L2 flush before every step (not timed)."""
+    import torch
+    st = torch.cuda.current_stream()
+    for _ in range(warmup):
+        flush.zero_()
+        plan(sigma, out=out)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record(st)
+        plan(sigma, out=out)
+        e1.record(st)
+    torch.cuda.synchronize()
+    return np.array([e0.elapsed_time(e1) for e0, e1 in ev])
+
+
+def cpu_oracle_rate(w, budget_s=15.0, threads=0):
+    """Oracle points/s on a seeded sample of target leaves sized to about budget_s."""
+    import oracle
+    rng = np.random.default_rng(123)
+    n = w.tree.n_leaves
+    probe = np.sort(rng.choice(n, size=min(n, 8), replace=False))
+    t0 = time.perf_counter()
+    oracle.box_fgt(3, w.p, w.delta, w.periodic, w.tree.level, w.tree.coord, w.sigma, targets=probe, threads=threads)
+    t_probe = max(time.perf_counter() - t0, 1e-3)
+    m = int(np.clip(len(probe) * budget_s / t_probe, 8, n))
+    sample = np.sort(rng.choice(n, size=m, replace=False))
+    t0 = time.perf_counter()
+    oracle.box_fgt(3, w.p, w.delta, w.periodic, w.tree.level, w.tree.coord, w.sigma, targets=sample, threads=threads)
+    dt = time.perf_counter() - t0
+    cores = threads if threads > 0 else oracle.default_threads()
+    return m * w.p ** 3 / dt, cores, m, dt
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm: each step a bounded sample of target leaves."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    w = workload()
+    rng = np.random.default_rng(7)
+    n = w.tree.n_leaves
+    probe = np.sort(rng.choice(n, size=4, replace=False))
+    t0 = time.perf_counter()
+    oracle.box_fgt(3, w.p, w.delta, False, w.tree.level, w.tree.coord, w.sigma, targets=probe)
+    t_leaf = max((time.perf_counter() - t0) / len(probe), 1e-4)
+    per_step = 120.0 / max(args.steps + args.warmup, 1)
+    m = int(np.clip(per_step / t_leaf, 1, n))
+    samples = [np.sort(rng.choice(n, size=m, replace=False)) for _ in range(args.steps + args.warmup)]
+    for s in samples[: args.warmup]:
+        oracle.box_fgt(3, w.p, w.delta, False, w.tree.level, w.tree.coord, w.sigma, targets=s)
+    t0 = time.perf_counter()
+    for s in samples[args.warmup:]:
+        oracle.box_fgt(3, w.p, w.delta, False, w.tree.level, w.tree.coord, w.sigma, targets=s)
+    dt = time.perf_counter() - t0
+    value = args.steps * m * w.p ** 3 / dt
+    cores = oracle.default_threads()
+    line = {
+        "impl": "reference", "metric": "target points/s (box FGT, 3D free space, delta=1e-3)", "value": value,
+        "unit": "points/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{w.name}: {w.tree.n_leaves} leaves, {w.n_points} points, delta=1e-3",
+                   "sample_leaves_per_step": m},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{m} seeded target leaves per step of {n}"},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2305_07165_gb300 as F
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    w = workload()
+    sigma = torch.from_numpy(w.sigma).cuda()
+    out = torch.empty_like(sigma)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    forms = [("split_tol1e-6", 1e-6, F.PREC_SPLIT), ("fp64_tol1e-6", 1e-6, F.PREC_FP64),
+             ("fp64_tol1e-10", 1e-10, F.PREC_FP64)]
+    results = {}
+    head = None
+    for name, tol, prec in forms:
+        plan = F.Plan(3, w.p, w.delta, tol, w.tree.level, w.tree.coord, prec=prec)
+        info = plan.info()
+        is_head = head is None
+        if is_head:
+            plan.set_profiling(True)
+            with ClockSampler(local) as cs:
+                if world > 1:
+                    dist.barrier()
+                torch.cuda.synchronize()
+                times = time_steps(plan, sigma, out, args.steps, args.warmup, flush)
+                torch.cuda.synchronize()
+            prof, nprof = plan.read_profile()
+            plan.set_profiling(False)
+            clocks = cs.summary()
+            head = dict(name=name, plan=plan, info=info, prof=prof, nprof=nprof, times=times, tol=tol, prec=prec)
+        else:
+            times = time_steps(plan, sigma, out, args.steps, args.warmup, flush)
+            plan.close()
+        tot = float(times.sum())
+        if world > 1:
+            t = torch.tensor([tot], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = float(t.item())
+        results[name] = dict(points_per_s=world * w.n_points * args.steps / (tot / 1e3),
+                             ms_per_step=tot / args.steps, p50_ms=float(np.percentile(times, 50)),
+                             p99_ms=float(np.percentile(times, 99)), cutoff_level=info["cutoff_level"],
+                             n_f=info["n_f"], launches=info["launches"])
+
+    # end to end through the host-buffer entry point (pinned host memory, copies timed)
+    plan = head["plan"]
+    sh = torch.from_numpy(w.sigma).pin_memory()
+    uh = torch.empty_like(sh).pin_memory()
+    for _ in range(args.warmup):
+        plan.execute_host(sh, uh)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.execute_host(sh, uh)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # roofline of the dominant kernel (per-phase CUDA events over the timed region)
+    info, prof = head["info"], head["prof"]
+    phase_flops = {"form": info["form_flops"], "evaluate": info["eval_flops"], "gather": info["gather_flops"],
+                   "near": info["direct_flops"], "merge": 0, "push": 0}
+    dom = max(prof, key=lambda k: prof[k])
+    per_launch_ms = prof[dom] / max(head["nprof"], 1)
+    achieved = phase_flops[dom] / (per_launch_ms / 1e3) / 1e12
+    peak = FP32_PEAK_TFLOPS if head["prec"] == F.PREC_SPLIT else FP64_PEAK_TFLOPS
+    if dom == "near":
+        peak = FP64_PEAK_TFLOPS
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x lanes x 2 x 2.07 GHz (FP32 CUDA cores for split, FP64 units otherwise)",
+                "phase_ms_per_step": {k: v / max(head["nprof"], 1) for k, v in prof.items()}}
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            rate, cores, m, dt = cpu_oracle_rate(w)
+            cpu = {"value": rate, "unit": "points/s", "cores": cores, "kind": "oracle",
+                   "sample": f"{m} seeded target leaves of {w.tree.n_leaves} ({m * w.p ** 3} points), {dt:.1f} s"}
+        hr = results[head["name"]]
+        line = {
+            "metric": "target points/s (box FGT, 3D free space, delta=1e-3, tol 1e-6 split form)",
+            "value": hr["points_per_s"], "unit": "points/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": hr["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{w.name}: 3D free space, {w.tree.n_leaves} leaves (levels "
+                                   f"{int(w.tree.level.min())}-{int(w.tree.level.max())}), p=8, {w.n_points} points, "
+                                   f"delta=1e-3, 8 Gaussians", "tol": head["tol"],
+                       "cache": "L2 flushed (256 MiB write) before every step, outside the timed events",
+                       "parallelism": f"replicas x{world}"},
+            "latency_ms": {"p50": hr["p50_ms"], "p99": hr["p99_ms"]},
+            "forms": results,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * w.n_points * args.steps / e2e_s, "unit": "points/s",
+                    "h2d_bytes_per_step": int(w.n_points * 8), "d2h_bytes_per_step": int(w.n_points * 8)},
+            "gpu_launches": int(info["launches"] * args.steps),
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    plan.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

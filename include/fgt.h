@@ -103,6 +103,7 @@ typedef struct {
   int64_t form_flops, eval_flops, gather_flops, direct_flops; /* per execute, real flops */
   int64_t device_bytes;       /* tables + lists + expansion workspace (excludes host-path staging) */
   int32_t prec, mode;
+  int32_t launches;           /* CUDA kernels one execution launches */
 } fgt_plan_info;
 
 /* Build a plan: validate the tree, choose l_c, n_f (or n_p), build the lists
@@ -150,6 +151,14 @@ fgt_status fgt_execute_async(fgt_plan *plan, const double *sigma_dev, double *u_
 /* End to end: sigma_host, u_host are host arrays (pinned for full copy speed);
  * copies in, transforms, copies out on `stream` and synchronises it. */
 fgt_status fgt_execute_host(fgt_plan *plan, const double *sigma_host, double *u_host, void *stream);
+
+/* Per-phase device timing (CUDA events on the launching stream) for the executions
+ * enqueued while profiling is on.  Phases: 0 form, 1 child->parent merge, 2 out->in
+ * gather, 3 parent->child push, 4 evaluate, 5 near field.  fgt_plan_read_profile
+ * waits for the recorded events, returns the summed milliseconds per phase in
+ * ms[0..5] and the number of executions covered, and starts a new accumulation. */
+fgt_status fgt_plan_set_profiling(fgt_plan *plan, int on);
+fgt_status fgt_plan_read_profile(fgt_plan *plan, double *ms, int *n_transforms);
 
 void fgt_destroy(fgt_plan *plan);
 

@@ -45,7 +45,7 @@ class PlanInfo(ctypes.Structure):
                [(n, ctypes.c_int64) for n in ("n_leaves", "n_boxes", "n_pw_leaves", "n_anchor_boxes",
                                               "n_form_blocks", "n_direct_pairs", "n_gather_pairs", "form_flops",
                                               "eval_flops", "gather_flops", "direct_flops", "device_bytes")] + \
-               [("prec", ctypes.c_int32), ("mode", ctypes.c_int32)]
+               [("prec", ctypes.c_int32), ("mode", ctypes.c_int32), ("launches", ctypes.c_int32)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -76,6 +76,8 @@ def lib():
             L.fgt_execute.argtypes = [vp, vp, vp]
             L.fgt_execute_async.argtypes = [vp, vp, vp, vp]
             L.fgt_execute_host.argtypes = [vp, vp, vp, vp]
+            L.fgt_plan_set_profiling.argtypes = [vp, i32]
+            L.fgt_plan_read_profile.argtypes = [vp, vp, vp]
             L.fgt_destroy.argtypes = [vp]
             L.fgt_destroy.restype = None
             L.fgt_last_error.restype = ctypes.c_char_p
@@ -89,7 +91,8 @@ def lib():
             for name in ("fgt_plan_create_ex", "fgt_plan_create_host", "fgt_plan_host_array", "fgt_plan_analyze", "fgt_plan_get_info", "fgt_plan_set_precision",
                          "fgt_plan_set_mode", "fgt_execute", "fgt_execute_async", "fgt_execute_host",
                          "fgt_gauss_legendre", "fgt_params", "fgt_legendre_gauss_integrals",
-                         "fgt_spherical_bessel", "fgt_legendre_fourier_integrals"):
+                         "fgt_spherical_bessel", "fgt_legendre_fourier_integrals", "fgt_plan_set_profiling",
+                         "fgt_plan_read_profile"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -185,6 +188,18 @@ class Plan:
 
     def set_mode(self, mode):
         _check(lib().fgt_plan_set_mode(self._h, mode))
+
+    PHASES = ("form", "merge", "gather", "push", "evaluate", "near")
+
+    def set_profiling(self, on=True):
+        _check(lib().fgt_plan_set_profiling(self._h, int(bool(on))))
+
+    def read_profile(self):
+        """(summed ms per phase, number of executions) since profiling was switched on / last read."""
+        ms = np.zeros(6)
+        n = ctypes.c_int()
+        _check(lib().fgt_plan_read_profile(self._h, ms.ctypes.data, ctypes.byref(n)))
+        return dict(zip(self.PHASES, ms.tolist())), n.value
 
     def device_bytes(self) -> int:
         return int(lib().fgt_plan_device_bytes(self._h))

@@ -42,6 +42,10 @@ struct ExecDesc {
   // hierarchical mode (empty in fused mode); merge in execution order (fine -> coarse)
   std::vector<ShiftStep> merge, push;
 
+  // optional per-phase timing: events[2p] / events[2p+1] recorded around phase p
+  // (p: 0 form, 1 merge, 2 gather, 3 push, 4 evaluate, 5 near field); nullptr = off
+  cudaEvent_t *events = nullptr;
+
   // near field (D-list)
   int64_t n_near = 0;
   const int64_t *near_tgt = nullptr;
@@ -50,6 +54,11 @@ struct ExecDesc {
   const NearSrc *near_src = nullptr;
   const double *near_tab = nullptr;
 };
+
+constexpr int kPhases = 6;
+
+// Number of kernel launches one transform makes.
+int launches_per_transform(const ExecDesc &e);
 
 // Enqueue the whole transform on `stream`.  sigma, u: device FP64 [n_leaves][k^d].
 cudaError_t run_transform(const ExecDesc &e, const double *sigma, double *u, cudaStream_t stream);

@@ -436,6 +436,10 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
   const int64_t ss = e.slot_size;
   const unsigned tiles = (unsigned)((ss + 255) / 256);
 
+  auto mark = [&](int ph, int end) {
+    if (e.events) cudaEventRecord(e.events[2 * ph + end], st);
+  };
+  mark(0, 0);
   if (e.n_blocks > 0) {
     // outgoing expansions: zero, then every block adds its contribution
     if ((err = cudaMemsetAsync(phi, 0, sizeof(C) * ss * e.n_phi_slots, st)) != cudaSuccess) return err;
@@ -448,12 +452,16 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
         e.k, n1, nh, ss, e.Kmax);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
+  mark(0, 1);
+  mark(1, 0);
   for (const ShiftStep &s : e.merge) {
     if (s.n == 0) continue;
     merge_kernel<D, R><<<dim3((unsigned)s.n, tiles), 256, 0, st>>>(
         s.items, reinterpret_cast<const C *>(s.qf), reinterpret_cast<const C *>(s.qh), phi, n1, nh, ss);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
+  mark(1, 1);
+  mark(2, 0);
   const C *eval_src = phi;
   if (!e.fourier && e.n_gather > 0) {
     gather_kernel<D, R><<<dim3((unsigned)e.n_gather, tiles), 256, 0, st>>>(
@@ -462,12 +470,16 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     eval_src = psi;
   }
+  mark(2, 1);
+  mark(3, 0);
   for (const ShiftStep &s : e.push) {
     if (s.n == 0) continue;
     push_kernel<D, R><<<dim3((unsigned)s.n, tiles), 256, 0, st>>>(
         s.items, reinterpret_cast<const C *>(s.qf), reinterpret_cast<const C *>(s.qh), psi, n1, nh, ss);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
+  mark(3, 1);
+  mark(4, 0);
   if (e.n_blocks > 0) {
     const size_t esm = eval_smem_bytes(D, e.Kmax, n1, sizeof(R) == 4);
     if ((err = cudaFuncSetAttribute(eval_kernel<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm)) !=
@@ -478,6 +490,8 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
         e.k, n1, nh, ss);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
+  mark(4, 1);
+  mark(5, 0);
   if (e.n_near > 0) {
     const int np = D == 3 ? e.k * e.k * e.k : e.k * e.k;
     const size_t nsm = sizeof(double) * (3 * (size_t)np + (size_t)D * e.k * e.k);
@@ -488,7 +502,18 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
                                                          sigma, u, e.k);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
+  mark(5, 1);
   return cudaSuccess;
+}
+
+int launches_per_transform(const ExecDesc &e) {
+  int n = 0;
+  if (e.n_blocks > 0) n += 2;  // form + evaluate
+  for (const ShiftStep &s : e.merge) n += s.n > 0;
+  for (const ShiftStep &s : e.push) n += s.n > 0;
+  if (!e.fourier && e.n_gather > 0) n += 1;
+  if (e.n_near > 0) n += 1;
+  return n;
 }
 
 cudaError_t run_transform(const ExecDesc &e, const double *sigma, double *u, cudaStream_t stream) {

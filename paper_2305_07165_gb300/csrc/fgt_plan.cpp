@@ -112,6 +112,10 @@ struct fgt_plan {
   DevPack host_pack;        // host copy of the uploaded lists and tables (kept for host-only plans)
   fgt::ExecDesc ex;
   fgt_plan_info info{};
+  // per-phase profiling
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
   // host copies kept for flop accounting
   int64_t n_near_pairs = 0, n_gather_pairs = 0, n_blocks = 0;
 
@@ -121,6 +125,7 @@ struct fgt_plan {
   }
   int np() const { return d == 3 ? k * k * k : k * k; }
   ~fgt_plan() {
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     if (dev) cudaFree(dev);
     if (work) cudaFree(work);
     if (stage) cudaFree(stage);
@@ -389,6 +394,7 @@ void fill_flops(fgt_plan &P, const fgt::ExecDesc &ex, const std::vector<fgt::Blo
   I.direct_flops = P.n_near_pairs * 2 * d * (int64_t)P.np() * k;
   I.prec = P.prec;
   I.mode = P.mode;
+  I.launches = fgt::launches_per_transform(ex);
 }
 
 template <typename C>
@@ -1020,8 +1026,47 @@ fgt_status fgt_execute_async(fgt_plan *plan, const double *sigma_dev, double *u_
     }
     if (s != FGT_OK) return s;
   }
+  plan->ex.events = nullptr;
+  if (plan->profiling) {
+    const size_t need = plan->ev_used + 2 * fgt::kPhases;
+    while (plan->ev_pool.size() < need) {
+      cudaEvent_t ev;
+      cudaError_t ce = cudaEventCreate(&ev);
+      if (ce != cudaSuccess) return cuda_fail(ce, "cudaEventCreate");
+      plan->ev_pool.push_back(ev);
+    }
+    plan->ex.events = plan->ev_pool.data() + plan->ev_used;
+    plan->ev_used = need;
+  }
   cudaError_t e = fgt::run_transform(plan->ex, sigma_dev, u_dev, (cudaStream_t)stream);
+  plan->ex.events = nullptr;
   if (e != cudaSuccess) return cuda_fail(e, "transform launch");
+  return FGT_OK;
+}
+
+fgt_status fgt_plan_set_profiling(fgt_plan *plan, int on) {
+  if (!plan) return fail(FGT_ERR_ARG, "plan is NULL");
+  plan->profiling = on != 0;
+  plan->ev_used = 0;
+  return FGT_OK;
+}
+
+fgt_status fgt_plan_read_profile(fgt_plan *plan, double *ms, int *n_transforms) {
+  if (!plan || !ms) return fail(FGT_ERR_ARG, "NULL argument");
+  for (int p = 0; p < fgt::kPhases; ++p) ms[p] = 0.0;
+  const size_t nt = plan->ev_used / (2 * fgt::kPhases);
+  for (size_t t = 0; t < nt; ++t)
+    for (int p = 0; p < fgt::kPhases; ++p) {
+      float v = 0.f;
+      cudaEvent_t *ev = plan->ev_pool.data() + t * 2 * fgt::kPhases;
+      cudaError_t ce = cudaEventSynchronize(ev[2 * p + 1]);
+      if (ce != cudaSuccess) return cuda_fail(ce, "profile");
+      ce = cudaEventElapsedTime(&v, ev[2 * p], ev[2 * p + 1]);
+      if (ce != cudaSuccess) return cuda_fail(ce, "profile");
+      ms[p] += v;
+    }
+  if (n_transforms) *n_transforms = (int)nt;
+  plan->ev_used = 0;
   return FGT_OK;
 }
 

@@ -118,7 +118,8 @@ def test_linearity_and_repeat():
     ua, ub, uab = plan(a).clone(), plan(b).clone(), plan(2 * a - 3 * b).clone()
     ua2 = plan(a)
     torch.cuda.synchronize()
-    assert torch.equal(ua, ua2)  # deterministic up to atomics order: same inputs, same plan
+    # repeatable up to the order of the atomic additions into the anchor expansions
+    assert (ua - ua2).abs().max().item() <= 1e-13 * ua.abs().max().item()
     assert (uab - (2 * ua - 3 * ub)).abs().max().item() <= 1e-12 * uab.abs().max().item()
     plan.close()
 
