@@ -175,17 +175,16 @@ def node_positions(tree: Tree, p: int) -> np.ndarray:
 
 
 def gaussian_sum(x, centers, alphas, amps=None, periodic=False):
-    """sum_i a_i exp(-|x - c_i|^2 / alpha_i); periodic adds the nearest images."""
+    """sum_i a_i exp(-|x - c_i|^2 / alpha_i); periodic: minimum-image distance to each centre."""
     centers = np.asarray(centers, dtype=np.float64)
     alphas = np.asarray(alphas, dtype=np.float64)
     amps = np.ones(len(centers)) if amps is None else np.asarray(amps, dtype=np.float64)
     out = np.zeros(x.shape[:-1])
-    d = x.shape[-1]
-    shifts = list(itertools.product((-1, 0, 1), repeat=d)) if periodic else [(0,) * d]
     for c, a, w in zip(centers, alphas, amps):
-        for s in shifts:
-            r2 = np.sum((x - c - np.asarray(s, dtype=np.float64)) ** 2, axis=-1)
-            out += w * np.exp(-r2 / a)
+        dx = x - c
+        if periodic:
+            dx = dx - np.round(dx)
+        out += w * np.exp(-np.sum(dx * dx, axis=-1) / a)
     return out
 
 
