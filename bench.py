@@ -37,9 +37,18 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 
 
-def workload():
+WORKLOADS = {
+    "adaptive3d": lambda W: W.config_3d_free_adaptive(seed=0, p=8, delta=1e-3),
+    "periodic3d": lambda W: W.config_3d_periodic_uniform(seed=0),
+    "uniform2d": lambda W: W.config_2d_free_uniform(seed=0),
+}
+FORMS = {"split": ("split_tol1e-6", 1e-6, 1), "fp64": ("fp64_tol1e-6", 1e-6, 0),
+         "fp64_1e-10": ("fp64_tol1e-10", 1e-10, 0)}
+
+
+def workload(name="adaptive3d"):
     import workloads as W
-    return W.config_3d_free_adaptive(seed=0, p=8, delta=1e-3)
+    return WORKLOADS[name](W)
 
 
 class ClockSampler:
@@ -113,15 +122,27 @@ def cpu_oracle_rate(w, budget_s=15.0, threads=0):
     n = w.tree.n_leaves
     probe = np.sort(rng.choice(n, size=min(n, 8), replace=False))
     t0 = time.perf_counter()
-    oracle.box_fgt(3, w.p, w.delta, w.periodic, w.tree.level, w.tree.coord, w.sigma, targets=probe, threads=threads)
+    oracle.box_fgt(w.d, w.p, w.delta, w.periodic, w.tree.level, w.tree.coord, w.sigma, targets=probe,
+                   threads=threads)
     t_probe = max(time.perf_counter() - t0, 1e-3)
     m = int(np.clip(len(probe) * budget_s / t_probe, 8, n))
     sample = np.sort(rng.choice(n, size=m, replace=False))
     t0 = time.perf_counter()
-    oracle.box_fgt(3, w.p, w.delta, w.periodic, w.tree.level, w.tree.coord, w.sigma, targets=sample, threads=threads)
+    oracle.box_fgt(w.d, w.p, w.delta, w.periodic, w.tree.level, w.tree.coord, w.sigma, targets=sample,
+                   threads=threads)
     dt = time.perf_counter() - t0
     cores = threads if threads > 0 else oracle.default_threads()
-    return m * w.p ** 3 / dt, cores, m, dt
+    return m * w.p ** w.d / dt, cores, m, dt
+
+
+def metric_name(w):
+    return (f"target points/s (box FGT, {w.d}D {'periodic' if w.periodic else 'free space'}, "
+            f"delta={w.delta:g}, tol 1e-6 split form)")
+
+
+def workload_text(w):
+    return (f"{w.name}: {w.d}D {'periodic' if w.periodic else 'free space'}, {w.tree.n_leaves} leaves (levels "
+            f"{int(w.tree.level.min())}-{int(w.tree.level.max())}), p={w.p}, {w.n_points} points, delta={w.delta:g}")
 
 
 def run_reference(args):
@@ -130,31 +151,30 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    w = workload()
+    w = workload(args.workload)
     rng = np.random.default_rng(7)
     n = w.tree.n_leaves
     probe = np.sort(rng.choice(n, size=4, replace=False))
     t0 = time.perf_counter()
-    oracle.box_fgt(3, w.p, w.delta, False, w.tree.level, w.tree.coord, w.sigma, targets=probe)
+    oracle.box_fgt(w.d, w.p, w.delta, w.periodic, w.tree.level, w.tree.coord, w.sigma, targets=probe)
     t_leaf = max((time.perf_counter() - t0) / len(probe), 1e-4)
     per_step = 120.0 / max(args.steps + args.warmup, 1)
     m = int(np.clip(per_step / t_leaf, 1, n))
     samples = [np.sort(rng.choice(n, size=m, replace=False)) for _ in range(args.steps + args.warmup)]
     for s in samples[: args.warmup]:
-        oracle.box_fgt(3, w.p, w.delta, False, w.tree.level, w.tree.coord, w.sigma, targets=s)
+        oracle.box_fgt(w.d, w.p, w.delta, w.periodic, w.tree.level, w.tree.coord, w.sigma, targets=s)
     t0 = time.perf_counter()
     for s in samples[args.warmup:]:
-        oracle.box_fgt(3, w.p, w.delta, False, w.tree.level, w.tree.coord, w.sigma, targets=s)
+        oracle.box_fgt(w.d, w.p, w.delta, w.periodic, w.tree.level, w.tree.coord, w.sigma, targets=s)
     dt = time.perf_counter() - t0
-    value = args.steps * m * w.p ** 3 / dt
+    value = args.steps * m * w.p ** w.d / dt
     cores = oracle.default_threads()
     line = {
-        "impl": "reference", "metric": "target points/s (box FGT, 3D free space, delta=1e-3)", "value": value,
+        "impl": "reference", "metric": metric_name(w), "value": value,
         "unit": "points/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{w.name}: {w.tree.n_leaves} leaves, {w.n_points} points, delta=1e-3",
-                   "sample_leaves_per_step": m},
+        "config": {"workload": workload_text(w), "sample_leaves_per_step": m},
         "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
                          "sample": f"{m} seeded target leaves per step of {n}"},
         "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -170,6 +190,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="adaptive3d", choices=sorted(WORKLOADS))
+    ap.add_argument("--forms", default="split,fp64,fp64_1e-10",
+                    help="comma list of split, fp64, fp64_1e-10; the first one is the headline")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -185,16 +208,15 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-    w = workload()
+    w = workload(args.workload)
     sigma = torch.from_numpy(w.sigma).cuda()
     out = torch.empty_like(sigma)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    forms = [("split_tol1e-6", 1e-6, F.PREC_SPLIT), ("fp64_tol1e-6", 1e-6, F.PREC_FP64),
-             ("fp64_tol1e-10", 1e-10, F.PREC_FP64)]
+    forms = [FORMS[f] for f in args.forms.split(",")]
     results = {}
     head = None
     for name, tol, prec in forms:
-        plan = F.Plan(3, w.p, w.delta, tol, w.tree.level, w.tree.coord, prec=prec)
+        plan = F.Plan(w.d, w.p, w.delta, tol, w.tree.level, w.tree.coord, bc=int(w.periodic), prec=prec)
         info = plan.info()
         is_head = head is None
         if is_head:
@@ -260,16 +282,14 @@ def main():
         if not args.no_cpu_baseline and world == 1:
             rate, cores, m, dt = cpu_oracle_rate(w)
             cpu = {"value": rate, "unit": "points/s", "cores": cores, "kind": "oracle",
-                   "sample": f"{m} seeded target leaves of {w.tree.n_leaves} ({m * w.p ** 3} points), {dt:.1f} s"}
+                   "sample": f"{m} seeded target leaves of {w.tree.n_leaves} ({m * w.p ** w.d} points), {dt:.1f} s"}
         hr = results[head["name"]]
         line = {
-            "metric": "target points/s (box FGT, 3D free space, delta=1e-3, tol 1e-6 split form)",
+            "metric": metric_name(w),
             "value": hr["points_per_s"], "unit": "points/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": hr["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{w.name}: 3D free space, {w.tree.n_leaves} leaves (levels "
-                                   f"{int(w.tree.level.min())}-{int(w.tree.level.max())}), p=8, {w.n_points} points, "
-                                   f"delta=1e-3, 8 Gaussians", "tol": head["tol"],
+            "vs_baseline": None, "dtype": "f32" if head["prec"] == 1 else "f64", "data": "synthetic",
+            "config": {"workload": workload_text(w), "tol": head["tol"], "form": head["name"],
                        "cache": "L2 flushed (256 MiB write) before every step, outside the timed events",
                        "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": hr["p50_ms"], "p99": hr["p99_ms"]},

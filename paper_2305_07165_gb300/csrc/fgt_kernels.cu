@@ -237,7 +237,10 @@ __device__ __forceinline__ void mode_index(int64_t idx, int n1, int &m1, int &m2
   }
 }
 
-// psi[dst] = sum_S T_out->in(S) phi[S]; the phase is a product of one 1D factor per axis.
+// psi[dst] = sum_S T_out->in(S) phi[S].  The phase is a product of one 1D factor per axis,
+// so the sum is taken axis by axis: sources arrive sorted by code (o_1 fastest), the x_1
+// factor multiplies each source, the x_2 factor each run of equal (o_2, o_3), the x_3 factor
+// each run of equal o_3 -- 27 + 9 + 3 complex products per mode in 3D instead of 27 x 3.
 template <int D, typename R>
 __global__ void gather_kernel(const int32_t *__restrict__ dst, const int64_t *__restrict__ ptr,
                               const GatherSrc *__restrict__ src, const typename C2T<R>::T *__restrict__ Pf,
@@ -249,20 +252,37 @@ __global__ void gather_kernel(const int32_t *__restrict__ dst, const int64_t *__
   const int i = blockIdx.x;
   int m1, m2, m3;
   mode_index<D>(idx, n1, m1, m2, m3);
-  R ar = 0, ai = 0;
+  // factors of the second and last axes (the last axis stores m >= 0 only)
+  const C* P2 = (D == 3) ? Pf : Ph;
+  const int s2 = (D == 3) ? n1 : nh, i2 = m2;
+  R a1r = 0, a1i = 0, a2r = 0, a2i = 0, a3r = 0, a3i = 0;
+  int g1 = -1, g2 = -1;  // current (o_2, o_3) run and o_3 run
   for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) {
     const GatherSrc g = src[q];
-    const int o1 = g.code % 3, o2 = (g.code / 3) % 3, o3 = g.code / 9;
-    C ph = Pf[o1 * n1 + m1];
-    if (D == 3) {
-      ph = cmul(ph, Pf[o2 * n1 + m2]);
-      ph = cmul(ph, Ph[o3 * nh + m3]);
-    } else {
-      ph = cmul(ph, Ph[o2 * nh + m2]);
+    const int run1 = g.code / 3, run2 = g.code / 9;
+    if (run1 != g1) {
+      if (g1 >= 0) {
+        cfma(a2r, a2i, P2[(g1 % 3) * s2 + i2], C{a1r, a1i});
+        a1r = a1i = 0;
+      }
+      g1 = run1;
     }
-    cfma(ar, ai, ph, phi[(int64_t)g.slot * slot_size + idx]);
+    if (D == 3 && run2 != g2) {
+      if (g2 >= 0) {
+        cfma(a3r, a3i, Ph[g2 * nh + m3], C{a2r, a2i});
+        a2r = a2i = 0;
+      }
+      g2 = run2;
+    }
+    cfma(a1r, a1i, Pf[(g.code % 3) * n1 + m1], phi[(int64_t)g.slot * slot_size + idx]);
   }
-  psi[(int64_t)dst[i] * slot_size + idx] = C{ar, ai};
+  if (g1 >= 0) cfma(a2r, a2i, P2[(g1 % 3) * s2 + i2], C{a1r, a1i});
+  if (D == 3) {
+    if (g2 >= 0) cfma(a3r, a3i, Ph[g2 * nh + m3], C{a2r, a2i});
+    psi[(int64_t)dst[i] * slot_size + idx] = C{a3r, a3i};
+  } else {
+    psi[(int64_t)dst[i] * slot_size + idx] = C{a2r, a2i};
+  }
 }
 
 // phi[parent] = sum_children T_c->p(child) phi[child]
