@@ -148,6 +148,28 @@ size_t fgt_plan_device_bytes(const fgt_plan *plan);
 fgt_status fgt_execute(fgt_plan *plan, const double *sigma_dev, double *u_dev);
 fgt_status fgt_execute_async(fgt_plan *plan, const double *sigma_dev, double *u_dev, void *stream);
 
+/* Allocation-free execution.  The paper has no counterpart; this entry point
+ * exists for callers that must not allocate device memory at transform time
+ * (an application whose allocator owns all device memory, or a thread that may
+ * not call cudaMalloc/cudaFree because that would synchronise the device or
+ * break its memory pool).  It computes exactly what fgt_execute_async does, on
+ * `stream`, but keeps the plane-wave expansions in one fixed array of
+ * FGT_NOALLOC_SCRATCH_BYTES (64 MiB) compiled into the library, which every GPU
+ * that loads the library holds until the process exits.  It calls no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *   - The first call on a device looks up that array's device address (a
+ *     one-time set-up per device); make that first call before any stream
+ *     capture.
+ *   - All calls share the array and each call overwrites it (the outgoing
+ *     expansions are cleared at the start of every call): calls that overlap on
+ *     the GPU race and give wrong results.  Serialise them.
+ *   - Returns FGT_ERR_ARG (with the sizes in the message) when the plan's
+ *     expansion workspace is larger than the array, and FGT_ERR_STATE when the
+ *     plan's mode or precision changed since it was last prepared (preparing
+ *     again would allocate; fgt_plan_get_info prepares it). */
+#define FGT_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+fgt_status fgt_execute_noalloc(fgt_plan *plan, const double *sigma_dev, double *u_dev, void *stream);
+
 /* End to end: sigma_host, u_host are host arrays (pinned for full copy speed);
  * copies in, transforms, copies out on `stream` and synchronises it. */
 fgt_status fgt_execute_host(fgt_plan *plan, const double *sigma_host, double *u_host, void *stream);

@@ -76,6 +76,8 @@ def lib():
             L.fgt_execute.argtypes = [vp, vp, vp]
             L.fgt_execute_async.argtypes = [vp, vp, vp, vp]
             L.fgt_execute_host.argtypes = [vp, vp, vp, vp]
+            L.fgt_execute_noalloc.argtypes = [vp, vp, vp, vp]
+            L.fgt_execute_noalloc.restype = ctypes.c_int
             L.fgt_plan_set_profiling.argtypes = [vp, i32]
             L.fgt_plan_read_profile.argtypes = [vp, vp, vp]
             L.fgt_destroy.argtypes = [vp]
@@ -223,6 +225,16 @@ class Plan:
         return out
 
     __call__ = execute
+
+    def execute_noalloc(self, sigma, out, stream=None):
+        """Same transform through fgt_execute_noalloc: the expansions live in the library's fixed
+        64 MiB device array, nothing is allocated.  Calls that overlap on the GPU race."""
+        import torch
+        self._check_tensor(sigma, "sigma")
+        self._check_tensor(out, "out")
+        s = stream if stream is not None else torch.cuda.current_stream(sigma.device)
+        _check(lib().fgt_execute_noalloc(self._h, sigma.data_ptr(), out.data_ptr(), ctypes.c_void_p(s.cuda_stream)))
+        return out
 
     def execute_host(self, sigma, out, stream=None):
         """End to end through the C ABI: host (ideally pinned) float64 arrays in and out."""

@@ -63,6 +63,14 @@ int launches_per_transform(const ExecDesc &e);
 // Enqueue the whole transform on `stream`.  sigma, u: device FP64 [n_leaves][k^d].
 cudaError_t run_transform(const ExecDesc &e, const double *sigma, double *u, cudaStream_t stream);
 
+// Allocation-free execution: the expansion workspace lives in a fixed device array of
+// kNoallocScratchBytes inside the library instead of the plan's own buffers.  The first call
+// on a device looks up that array's device address (cudaGetSymbolAddress).  Returns
+// cudaErrorInvalidValue when the plan's workspace does not fit.
+constexpr size_t kNoallocScratchBytes = size_t(64) << 20;
+cudaError_t noalloc_scratch(void **ptr);
+cudaError_t run_transform_noalloc(const ExecDesc &e, const double *sigma, double *u, cudaStream_t stream);
+
 // Shared-memory bytes the form / evaluation kernels need for a block size K.
 size_t form_smem_bytes(int d, int K, int n1, int prec);
 size_t eval_smem_bytes(int d, int K, int n1, int prec);

@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "fgt_exec.h"
 
@@ -539,6 +540,55 @@ int launches_per_transform(const ExecDesc &e) {
 cudaError_t run_transform(const ExecDesc &e, const double *sigma, double *u, cudaStream_t stream) {
   if (e.d == 3) return e.prec ? run_typed<3, float>(e, sigma, u, stream) : run_typed<3, double>(e, sigma, u, stream);
   return e.prec ? run_typed<2, float>(e, sigma, u, stream) : run_typed<2, double>(e, sigma, u, stream);
+}
+
+// ----------------------------------------------------------------------------- allocation-free variant
+//
+// For callers that cannot allocate device memory when they transform (for
+// example code running under an allocator that forbids cudaMalloc, or a
+// runtime that has already committed all device memory to its own pool), the
+// expansion workspace can live in this fixed array instead of the plan's own.
+// Every GPU that loads the library holds it until the process exits.  All
+// calls share it: calls that overlap on the GPU race on it.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+void *g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mutex;
+}  // namespace
+
+cudaError_t noalloc_scratch(void **ptr) {
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    // host code only sees a stand-in for the array: ask the runtime for its device address
+    void *p = nullptr;
+    err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (err != cudaSuccess) return err;
+    g_scratch_addr[dev] = p;
+  }
+  *ptr = g_scratch_addr[dev];
+  return cudaSuccess;
+}
+
+cudaError_t run_transform_noalloc(const ExecDesc &e, const double *sigma, double *u, cudaStream_t stream) {
+  void *base = nullptr;
+  cudaError_t err = noalloc_scratch(&base);
+  if (err != cudaSuccess) return err;
+  const size_t c = e.prec ? sizeof(float2) : sizeof(double2);
+  const size_t phi_bytes = c * (size_t)e.slot_size * (size_t)e.n_phi_slots;
+  const size_t psi_bytes = c * (size_t)e.slot_size * (size_t)e.n_psi_slots;
+  if (phi_bytes + psi_bytes > kNoallocScratchBytes) return cudaErrorInvalidValue;
+  ExecDesc f = e;
+  f.phi = base;
+  f.psi = static_cast<unsigned char *>(base) + ((phi_bytes + 255) & ~(size_t)255);
+  if (((phi_bytes + 255) & ~(size_t)255) + psi_bytes > kNoallocScratchBytes) return cudaErrorInvalidValue;
+  f.events = nullptr;
+  return run_transform(f, sigma, u, stream);
 }
 
 }  // namespace fgt

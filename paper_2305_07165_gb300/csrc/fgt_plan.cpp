@@ -1070,6 +1070,25 @@ fgt_status fgt_plan_read_profile(fgt_plan *plan, double *ms, int *n_transforms) 
   return FGT_OK;
 }
 
+fgt_status fgt_execute_noalloc(fgt_plan *plan, const double *sigma_dev, double *u_dev, void *stream) {
+  if (!plan || !sigma_dev || !u_dev) return fail(FGT_ERR_ARG, "NULL argument");
+  if (plan->host_only) return fail(FGT_ERR_STATE, "host-only plan cannot execute");
+  // re-planning would allocate: the plan must already be prepared for its mode and precision
+  if (plan->dirty) return fail(FGT_ERR_STATE, "plan changed since it was prepared; run fgt_plan_get_info first");
+  const size_t c = plan->prec ? 8 : 16;
+  const size_t phi = c * (size_t)plan->ex.slot_size * (size_t)plan->ex.n_phi_slots;
+  const size_t psi = c * (size_t)plan->ex.slot_size * (size_t)plan->ex.n_psi_slots;
+  if (((phi + 255) & ~(size_t)255) + psi > fgt::kNoallocScratchBytes)
+    return fail(FGT_ERR_ARG, "expansion workspace of " + std::to_string(phi + psi) +
+                                 " bytes exceeds the fixed allocation-free scratch of " +
+                                 std::to_string(fgt::kNoallocScratchBytes) + " bytes");
+  fgt::ExecDesc ex = plan->ex;
+  ex.events = nullptr;
+  cudaError_t e = fgt::run_transform_noalloc(ex, sigma_dev, u_dev, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "allocation-free transform");
+  return FGT_OK;
+}
+
 fgt_status fgt_execute(fgt_plan *plan, const double *sigma_dev, double *u_dev) {
   fgt_status s = fgt_execute_async(plan, sigma_dev, u_dev, nullptr);
   if (s != FGT_OK) return s;
