@@ -174,6 +174,23 @@ fgt_status fgt_execute_noalloc(fgt_plan *plan, const double *sigma_dev, double *
  * copies in, transforms, copies out on `stream` and synchronises it. */
 fgt_status fgt_execute_host(fgt_plan *plan, const double *sigma_host, double *u_host, void *stream);
 
+/* ---- Batched execution: many independent transforms in one launch ----
+ * The paper transforms one density at a time; batching is how the GPU is kept busy with many
+ * small transforms of uneven depth, k and delta.  fgt_batch_create takes n prepared device
+ * plans (any mix of d, k, delta, tol, bc, precision; the batch keeps pointers to them, so they
+ * must outlive it and must not change mode or precision).  fgt_batch_execute enqueues all n
+ * transforms on `stream` as ONE CUDA graph launch in which every transform is an independent
+ * branch, so their kernels run concurrently; sigma_dev[i], u_dev[i] are device FP64 arrays of
+ * plan i's size.  The graph is captured on the first call and again only when a pointer
+ * changes.  Executions of one batch must not overlap each other or other executions of its
+ * plans.  fgt_execute_batch = create + execute + synchronise `stream` + destroy. */
+typedef struct fgt_batch fgt_batch;
+fgt_status fgt_batch_create(fgt_plan *const *plans, int n, fgt_batch **out);
+fgt_status fgt_batch_execute(fgt_batch *batch, const double *const *sigma_dev, double *const *u_dev, void *stream);
+void fgt_batch_destroy(fgt_batch *batch);
+fgt_status fgt_execute_batch(fgt_plan *const *plans, const double *const *sigma_dev, double *const *u_dev, int n,
+                             void *stream);
+
 /* Per-phase device timing (CUDA events on the launching stream) for the executions
  * enqueued while profiling is on.  Phases: 0 form, 1 child->parent merge, 2 out->in
  * gather, 3 parent->child push, 4 evaluate, 5 near field.  fgt_plan_read_profile

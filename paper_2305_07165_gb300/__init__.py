@@ -18,7 +18,7 @@ from . import build as _build
 
 __all__ = ["Plan", "FGTError", "lib", "BC_FREE", "BC_PERIODIC", "PREC_FP64", "PREC_SPLIT", "MODE_FUSED",
            "MODE_HIERARCHICAL", "gauss_legendre", "params", "nf_for_range", "legendre_gauss_integrals",
-           "spherical_bessel", "legendre_fourier_integrals", "analyze", "HostPlan"]
+           "spherical_bessel", "legendre_fourier_integrals", "analyze", "HostPlan", "Batch"]
 
 BC_FREE, BC_PERIODIC = 0, 1
 PREC_FP64, PREC_SPLIT = 0, 1
@@ -78,6 +78,13 @@ def lib():
             L.fgt_execute_host.argtypes = [vp, vp, vp, vp]
             L.fgt_execute_noalloc.argtypes = [vp, vp, vp, vp]
             L.fgt_execute_noalloc.restype = ctypes.c_int
+            L.fgt_batch_create.argtypes = [vp, i32, vp]
+            L.fgt_batch_execute.argtypes = [vp, vp, vp, vp]
+            L.fgt_batch_destroy.argtypes = [vp]
+            L.fgt_batch_destroy.restype = None
+            L.fgt_execute_batch.argtypes = [vp, vp, vp, i32, vp]
+            for name in ("fgt_batch_create", "fgt_batch_execute", "fgt_execute_batch"):
+                getattr(L, name).restype = ctypes.c_int
             L.fgt_plan_set_profiling.argtypes = [vp, i32]
             L.fgt_plan_read_profile.argtypes = [vp, vp, vp]
             L.fgt_destroy.argtypes = [vp]
@@ -252,6 +259,47 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             lib().fgt_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent transforms run as one CUDA graph launch (each transform a parallel branch).
+
+    ``batch(sigmas, outs)`` enqueues all transforms on the current stream; the graph is
+    captured on the first call and recaptured only when a tensor pointer changes.
+    """
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        self._h = ctypes.c_void_p()
+        _check(lib().fgt_batch_create(arr, len(self.plans), ctypes.byref(self._h)))
+
+    def execute(self, sigmas, outs, stream=None):
+        import torch
+        if len(sigmas) != len(self.plans) or len(outs) != len(self.plans):
+            raise ValueError("one sigma and one output per plan")
+        for p, s, o in zip(self.plans, sigmas, outs):
+            p._check_tensor(s, "sigma")
+            p._check_tensor(o, "out")
+        n = len(self.plans)
+        sp = (ctypes.c_void_p * n)(*[s.data_ptr() for s in sigmas])
+        up = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+        st = stream if stream is not None else torch.cuda.current_stream()
+        _check(lib().fgt_batch_execute(self._h, sp, up, ctypes.c_void_p(st.cuda_stream)))
+        return outs
+
+    __call__ = execute
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().fgt_batch_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

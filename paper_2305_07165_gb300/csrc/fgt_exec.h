@@ -9,6 +9,12 @@
 
 namespace fgt {
 
+// One launch of a kernel over a contiguous range of items that share a block size K.
+struct LaunchRange {
+  int first = 0, count = 0, K = 0;
+  size_t smem = 0;
+};
+
 // One level of the hierarchical merge (child -> parent) or push (parent -> child).
 struct ShiftStep {
   const TreeShift *items = nullptr;  // device
@@ -25,10 +31,23 @@ struct ExecDesc {
   int64_t n_phi_slots = 0, n_psi_slots = 0;
   void *phi = nullptr, *psi = nullptr;
 
-  // dense block form / evaluation
+  // dense block form / evaluation: all blocks, then the per-kernel lists
   const Block *blocks = nullptr;     // device
   int64_t n_blocks = 0;
   int Kmax = 0;
+  const Block *f1_blocks = nullptr;  // per-(block, m_d) form kernel
+  int64_t n_f1 = 0;
+  int Kmax_f1 = 0;
+  const Block *f2_blocks = nullptr;  // grouped form kernel; group g = f2_blocks[gptr[g] .. gptr[g+1])
+  const int32_t *f2_gptr = nullptr;
+  int64_t n_f2_groups = 0;
+  std::vector<LaunchRange> f2_ranges;  // groups by K
+  const Block *e1_blocks = nullptr;  // per-(block, row) evaluation kernel
+  int64_t n_e1 = 0;
+  int Kmax_e1 = 0;
+  const Block *e2_blocks = nullptr;  // whole-block evaluation kernel
+  int64_t n_e2 = 0;
+  std::vector<LaunchRange> e2_ranges;  // blocks by K
   const int64_t *block_leaves = nullptr;
   const void *Ff = nullptr, *Fh = nullptr, *Ef = nullptr, *Eh = nullptr;
 
@@ -53,6 +72,9 @@ struct ExecDesc {
   const int64_t *near_ptr = nullptr;
   const NearSrc *near_src = nullptr;
   const double *near_tab = nullptr;
+  const NearPair *near_pairs = nullptr;  // flattened D-list, one CTA per pair
+  int64_t n_near_pairs = 0;
+  int64_t n_points = 0;                  // n_leaves * k^d
 };
 
 constexpr int kPhases = 6;
@@ -70,6 +92,26 @@ cudaError_t run_transform(const ExecDesc &e, const double *sigma, double *u, cud
 constexpr size_t kNoallocScratchBytes = size_t(64) << 20;
 cudaError_t noalloc_scratch(void **ptr);
 cudaError_t run_transform_noalloc(const ExecDesc &e, const double *sigma, double *u, cudaStream_t stream);
+
+// Shared-memory bytes of the grouped form kernel (G blocks of K nodes per axis; r, c: real and
+// complex element sizes) and of the whole-block evaluation kernel.
+inline size_t form2_bytes(int d, int G, int K, int n1, int nh, size_t r, size_t c) {
+  const size_t npb = (d == 3) ? (size_t)K * K * K : (size_t)K * K;
+  size_t b = npb * r + (size_t)n1 * K * c + (size_t)nh * K * c + (d == 3 ? (size_t)K * K : (size_t)K) * c;
+  if (d == 3) b += 2 * (size_t)n1 * K * c;  // second-axis matrices and Z2
+  return (size_t)G * b + 16;                // padding that keeps the complex arrays aligned
+}
+// Register-tiled 3D form: G blocks of K nodes per axis, planes m_3 in chunks of 4.
+inline size_t form3_bytes(int G, int K, int n1, size_t r, size_t c) {
+  const size_t GK = (size_t)G * K, Sc = 4;
+  const size_t sig = (((size_t)G * K * K * K * r) + 15) & ~(size_t)15;
+  return sig + c * (GK * n1 + (size_t)G * n1 * K + (size_t)G * Sc * K + Sc * G * (size_t)K * K +
+                    Sc * (size_t)n1 * (GK + 1));
+}
+inline size_t eval2_bytes(int d, int K, int n1, int nh, size_t c) {
+  if (d == 3) return c * ((size_t)K * n1 * n1 + (size_t)K * K * n1 + 2 * (size_t)K * n1 + (size_t)K * nh);
+  return c * ((size_t)K * n1 + (size_t)K * n1 + (size_t)K * nh);
+}
 
 // Shared-memory bytes the form / evaluation kernels need for a block size K.
 size_t form_smem_bytes(int d, int K, int n1, int prec);

@@ -35,6 +35,14 @@ struct NearSrc {
   int32_t pad;
 };
 
+// One near-field (D-list) pair: source leaf S acting on target leaf T.
+struct NearPair {
+  int64_t tgt;       // target leaf index
+  int64_t src;       // source leaf index
+  int32_t tab[3];    // per dimension: table id = source_level * kNearTypes + kind
+  int32_t pad;
+};
+
 // Merge (child -> parent) or push (parent -> child) item of the hierarchical mode.
 struct TreeShift {
   int32_t parent;    // parent slot

@@ -223,6 +223,404 @@ __global__ void __launch_bounds__(256) eval_kernel(const Block *__restrict__ blo
   }
 }
 
+// ----------------------------------------------------------------------------- grouped form
+
+// A CTA takes up to G blocks of one anchor (same K) and one m_d plane: their sigma (converted
+// to R) and 1D matrices are staged in shared memory, the three contractions run for all its
+// blocks, and their summed contribution goes to the anchor slot with one atomic per
+// coefficient (G times fewer atomics than one CTA per block).  The x_1 matrices are stored transposed ([J][m]) so that
+// threads reading consecutive modes hit consecutive banks.
+template <int D, typename R>
+__global__ void __launch_bounds__(256) form2_kernel(const Block *__restrict__ blocks, const int32_t *__restrict__ gptr,
+                                                    const int64_t *__restrict__ bleaves,
+                                                    const double *__restrict__ sigma,
+                                                    const typename C2T<R>::T *__restrict__ Ff,
+                                                    const typename C2T<R>::T *__restrict__ Fh,
+                                                    typename C2T<R>::T *__restrict__ phi, int k, int n1, int nh,
+                                                    int64_t slot_size) {
+  using C = typename C2T<R>::T;
+  extern __shared__ unsigned char smem_raw[];
+  const int b0 = gptr[blockIdx.x], G = gptr[blockIdx.x + 1] - b0;
+  const Block B0 = blocks[b0];
+  const int K = B0.K, nl = 1 << B0.dl;
+  const int KK = K * K, npb = (D == 3) ? KK * K : KK, kp = (D == 3) ? k * k * k : k * k;
+  // layout
+  R *sig = reinterpret_cast<R *>(smem_raw);
+  const size_t sig_bytes = ((size_t)G * npb * sizeof(R) + 15) & ~(size_t)15;  // keep C aligned
+  C *F1t = reinterpret_cast<C *>(smem_raw + sig_bytes);         // [G][K][n1]
+  C *Fd = F1t + (size_t)G * K * n1;                             // [G][nh][K]
+  C *Z1 = Fd + (size_t)G * nh * K;                              // [G][K^(D-1)]
+  C *F2 = Z1 + (size_t)G * (D == 3 ? KK : K);                   // [G][n1][K]   (3D)
+  C *Z2 = F2 + (size_t)G * n1 * K;                              // [G][n1][K]   (3D)
+  for (int g = 0; g < G; ++g) {
+    const Block b = blocks[b0 + g];
+    const int64_t *lv = bleaves + b.leaf0;
+    for (int e = threadIdx.x; e < npb; e += blockDim.x) {
+      int J1 = e % K, rest = e / K, J2 = (D == 3) ? rest % K : rest, J3 = (D == 3) ? rest / K : 0;
+      const int o1 = J1 / k, o2 = J2 / k, o3 = J3 / k;
+      const int64_t leaf = (D == 3) ? lv[(o3 * nl + o2) * nl + o1] : lv[o2 * nl + o1];
+      const int node = (D == 3) ? ((J3 - o3 * k) * k + (J2 - o2 * k)) * k + (J1 - o1 * k) : (J2 - o2 * k) * k + (J1 - o1 * k);
+      sig[(size_t)g * npb + e] = (R)__ldg(sigma + leaf * kp + node);
+    }
+    for (int e = threadIdx.x; e < K * n1; e += blockDim.x) {
+      const int J = e / n1, m = e - J * n1;
+      F1t[(size_t)g * K * n1 + e] = Ff[((int64_t)(b.mat[0] + J / k) * n1 + m) * k + J % k];
+    }
+    for (int e = threadIdx.x; e < nh * K; e += blockDim.x) {
+      const int m = e / K, J = e - m * K;
+      Fd[(size_t)g * nh * K + e] = Fh[((int64_t)(b.mat[D - 1] + J / k) * nh + m) * k + J % k];
+    }
+    if (D == 3)
+      for (int e = threadIdx.x; e < n1 * K; e += blockDim.x) {
+        const int m = e / K, J = e - m * K;
+        F2[(size_t)g * n1 * K + e] = Ff[((int64_t)(b.mat[1] + J / k) * n1 + m) * k + J % k];
+      }
+  }
+  __syncthreads();
+  C *out = phi + (int64_t)B0.slot * slot_size;
+  {
+    const int s = blockIdx.y;  // one m_d plane per CTA
+    if (D == 3) {
+      // Z1[g][J2][J1] = sum_J3 Fd[g][s][J3] sig[g][J3][J2][J1]
+      for (int e = threadIdx.x; e < G * KK; e += blockDim.x) {
+        const int g = e / KK, rem = e - g * KK;
+        const R *sp = sig + (size_t)g * npb + rem;
+        const C *fp = Fd + ((size_t)g * nh + s) * K;
+        R ar = 0, ai = 0;
+        for (int J3 = 0; J3 < K; ++J3) {
+          const R v = sp[(size_t)J3 * KK];
+          const C f = fp[J3];
+          ar = fma(f.x, v, ar);
+          ai = fma(f.y, v, ai);
+        }
+        Z1[e] = C{ar, ai};
+      }
+      __syncthreads();
+      // Z2[g][m2][J1] = sum_J2 F2[g][m2][J2] Z1[g][J2][J1]
+      for (int e = threadIdx.x; e < G * n1 * K; e += blockDim.x) {
+        const int g = e / (n1 * K), rem = e - g * n1 * K, m2 = rem / K, J1 = rem - m2 * K;
+        const C *fp = F2 + ((size_t)g * n1 + m2) * K;
+        const C *zp = Z1 + (size_t)g * KK + J1;
+        R ar = 0, ai = 0;
+        for (int J2 = 0; J2 < K; ++J2) cfma(ar, ai, fp[J2], zp[J2 * K]);
+        Z2[e] = C{ar, ai};
+      }
+      __syncthreads();
+      // out[s][m2][m1] += sum_g sum_J1 F1[g][m1][J1] Z2[g][m2][J1]
+      C *o = out + (int64_t)s * n1 * n1;
+      for (int idx = threadIdx.x; idx < n1 * n1; idx += blockDim.x) {
+        const int m2 = idx / n1, m1 = idx - m2 * n1;
+        R ar = 0, ai = 0;
+        for (int g = 0; g < G; ++g) {
+          const C *fp = F1t + (size_t)g * K * n1 + m1;
+          const C *zp = Z2 + ((size_t)g * n1 + m2) * K;
+          for (int J1 = 0; J1 < K; ++J1) cfma(ar, ai, fp[J1 * n1], zp[J1]);
+        }
+        atomicAdd(&o[idx].x, ar);
+        atomicAdd(&o[idx].y, ai);
+      }
+      __syncthreads();
+    } else {
+      // Z1[g][J1] = sum_J2 Fd[g][s][J2] sig[g][J2][J1]
+      for (int e = threadIdx.x; e < G * K; e += blockDim.x) {
+        const int g = e / K, J1 = e - g * K;
+        const R *sp = sig + (size_t)g * npb + J1;
+        const C *fp = Fd + ((size_t)g * nh + s) * K;
+        R ar = 0, ai = 0;
+        for (int J2 = 0; J2 < K; ++J2) {
+          const R v = sp[(size_t)J2 * K];
+          const C f = fp[J2];
+          ar = fma(f.x, v, ar);
+          ai = fma(f.y, v, ai);
+        }
+        Z1[e] = C{ar, ai};
+      }
+      __syncthreads();
+      C *o = out + (int64_t)s * n1;
+      for (int m1 = threadIdx.x; m1 < n1; m1 += blockDim.x) {
+        R ar = 0, ai = 0;
+        for (int g = 0; g < G; ++g) {
+          const C *fp = F1t + (size_t)g * K * n1 + m1;
+          const C *zp = Z1 + (size_t)g * K;
+          for (int J1 = 0; J1 < K; ++J1) cfma(ar, ai, fp[J1 * n1], zp[J1]);
+        }
+        atomicAdd(&o[m1].x, ar);
+        atomicAdd(&o[m1].y, ai);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- register-tiled form (3D)
+//
+// A CTA takes a group of G blocks of one anchor (same K) and a chunk of up to kSc planes m_3.
+// Stage 1 (J3 -> m3) keeps kSc outputs per thread, stages 2 (J2 -> m2) and 3 (J1 -> m1) run as
+// small complex GEMMs with 4 x 4 register tiles, so every operand read from shared memory
+// feeds four complex multiply-adds.  The group's contributions are summed before one atomic
+// add per coefficient.
+constexpr int kSc = 4;
+
+__host__ __device__ inline int pad_gk(int GK) { return GK + 1; }  // row stride of Z2 (bank spread)
+
+template <typename R>
+__global__ void __launch_bounds__(256) form3_kernel(const Block *__restrict__ blocks, const int32_t *__restrict__ gptr,
+                                                    const int64_t *__restrict__ bleaves,
+                                                    const double *__restrict__ sigma,
+                                                    const typename C2T<R>::T *__restrict__ Ff,
+                                                    const typename C2T<R>::T *__restrict__ Fh,
+                                                    typename C2T<R>::T *__restrict__ phi, int k, int n1, int nh,
+                                                    int64_t slot_size) {
+  using C = typename C2T<R>::T;
+  extern __shared__ unsigned char smem_raw[];
+  const int b0 = gptr[blockIdx.x], G = gptr[blockIdx.x + 1] - b0;
+  const Block B0 = blocks[b0];
+  const int K = B0.K, nl = 1 << B0.dl;
+  const int KK = K * K, npb = KK * K, kp = k * k * k, GK = G * K, ldz = pad_gk(GK);
+  const int s0 = blockIdx.y * kSc, ns = min(kSc, nh - s0);
+  R *sig = reinterpret_cast<R *>(smem_raw);                                   // [G][K^3]
+  const size_t sig_bytes = ((size_t)G * npb * sizeof(R) + 15) & ~(size_t)15;
+  C *F1t = reinterpret_cast<C *>(smem_raw + sig_bytes);                       // [G K][n1]
+  C *F2 = F1t + (size_t)GK * n1;                                              // [G][n1][K]
+  C *Fd = F2 + (size_t)G * n1 * K;                                            // [G][kSc][K]
+  C *Z1 = Fd + (size_t)G * kSc * K;                                           // [kSc][G][K][K]
+  C *Z2 = Z1 + (size_t)kSc * G * KK;                                          // [kSc][n1][ldz]
+  for (int g = 0; g < G; ++g) {
+    const Block b = blocks[b0 + g];
+    const int64_t *lv = bleaves + b.leaf0;
+    // sigma of the block, leaf by leaf (k^3 contiguous values per leaf)
+    for (int e = threadIdx.x; e < npb; e += blockDim.x) {
+      const int leafi = e / kp, node = e - leafi * kp;
+      const int o1 = leafi % nl, o2 = (leafi / nl) % nl, o3 = leafi / (nl * nl);
+      const int j1 = node % k, j2 = (node / k) % k, j3 = node / (k * k);
+      sig[(size_t)g * npb + ((o3 * k + j3) * K + (o2 * k + j2)) * K + (o1 * k + j1)] =
+          (R)__ldg(sigma + lv[leafi] * kp + node);
+    }
+    for (int e = threadIdx.x; e < K * n1; e += blockDim.x) {
+      const int J = e / n1, m = e - J * n1;
+      F1t[(size_t)(g * K + J) * n1 + m] = Ff[((int64_t)(b.mat[0] + J / k) * n1 + m) * k + J % k];
+    }
+    for (int e = threadIdx.x; e < n1 * K; e += blockDim.x) {
+      const int m = e / K, J = e - m * K;
+      F2[(size_t)g * n1 * K + e] = Ff[((int64_t)(b.mat[1] + J / k) * n1 + m) * k + J % k];
+    }
+    for (int e = threadIdx.x; e < kSc * K; e += blockDim.x) {
+      const int q = e / K, J = e - q * K;
+      Fd[((size_t)g * kSc + q) * K + J] =
+          (q < ns) ? Fh[((int64_t)(b.mat[2] + J / k) * nh + s0 + q) * k + J % k] : C{0, 0};
+    }
+  }
+  __syncthreads();
+  // stage 1: Z1[q][g][J2][J1] = sum_J3 Fd[g][q][J3] sig[g][J3][J2][J1], all kSc planes per thread
+  for (int e = threadIdx.x; e < G * KK; e += blockDim.x) {
+    const int g = e / KK, rem = e - g * KK;
+    const R *sp = sig + (size_t)g * npb + rem;
+    const C *fp = Fd + (size_t)g * kSc * K;
+    R ar[kSc], ai[kSc];
+#pragma unroll
+    for (int q = 0; q < kSc; ++q) ar[q] = ai[q] = 0;
+    for (int J3 = 0; J3 < K; ++J3) {
+      const R v = sp[(size_t)J3 * KK];
+#pragma unroll
+      for (int q = 0; q < kSc; ++q) {
+        const C f = fp[q * K + J3];
+        ar[q] = fma(f.x, v, ar[q]);
+        ai[q] = fma(f.y, v, ai[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kSc; ++q) Z1[((size_t)q * G + g) * KK + rem] = C{ar[q], ai[q]};
+  }
+  __syncthreads();
+  // stage 2: Z2[q][m2][g K + J1] = sum_J2 F2[g][m2][J2] Z1[q][g][J2][J1]; 4 x 4 tiles over (m2, J1)
+  {
+    const int tm = (n1 + 3) / 4, tj = (K + 3) / 4, ntile = ns * G * tm * tj;
+    for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
+      int r = t;
+      const int bj = r % tj; r /= tj;
+      const int bm = r % tm; r /= tm;
+      const int g = r % G, q = r / G;
+      R ar[4][4], ai[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ar[i][j] = ai[i][j] = 0;
+      const C *fp = F2 + (size_t)g * n1 * K;
+      const C *zp = Z1 + ((size_t)q * G + g) * KK;
+      for (int J2 = 0; J2 < K; ++J2) {
+        C a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int m = bm * 4 + i;
+          a[i] = (m < n1) ? fp[m * K + J2] : C{0, 0};
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int J1 = bj * 4 + j;
+          b[j] = (J1 < K) ? zp[J2 * K + J1] : C{0, 0};
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) cfma(ar[i][j], ai[i][j], a[i], b[j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int m = bm * 4 + i, J1 = bj * 4 + j;
+          if (m < n1 && J1 < K) Z2[((size_t)q * n1 + m) * ldz + g * K + J1] = C{ar[i][j], ai[i][j]};
+        }
+    }
+  }
+  __syncthreads();
+  // stage 3: out[s0+q][m2][m1] += sum_{gJ} Z2[q][m2][gJ] F1t[gJ][m1]; 4 x 4 tiles over (m2, m1)
+  C *out = phi + (int64_t)B0.slot * slot_size;
+  {
+    const int tm = (n1 + 3) / 4, ntile = ns * tm * tm;
+    for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
+      const int b1 = t % tm, rest = t / tm, b2 = rest % tm, q = rest / tm;
+      R ar[4][4], ai[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ar[i][j] = ai[i][j] = 0;
+      const C *zq = Z2 + (size_t)q * n1 * ldz;
+      for (int J = 0; J < GK; ++J) {
+        C a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int m2 = b2 * 4 + i;
+          a[i] = (m2 < n1) ? zq[(size_t)m2 * ldz + J] : C{0, 0};
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int m1 = b1 * 4 + j;
+          b[j] = (m1 < n1) ? F1t[(size_t)J * n1 + m1] : C{0, 0};
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) cfma(ar[i][j], ai[i][j], a[i], b[j]);
+      }
+      C *o = out + (int64_t)(s0 + q) * n1 * n1;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int m2 = b2 * 4 + i, m1 = b1 * 4 + j;
+          if (m2 < n1 && m1 < n1) {
+            atomicAdd(&o[m2 * n1 + m1].x, ar[i][j]);
+            atomicAdd(&o[m2 * n1 + m1].y, ai[i][j]);
+          }
+        }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- whole-block evaluation
+
+// A CTA evaluates one whole block (K <= KM nodes per axis): the anchor's incoming expansion is
+// read once (each thread keeps K accumulators for its mode column), then the two remaining
+// contractions run from shared memory.
+template <int D, typename R, int KM>
+__global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256) eval2_kernel(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
+                                                    const typename C2T<R>::T *__restrict__ Ef,
+                                                    const typename C2T<R>::T *__restrict__ Eh,
+                                                    const typename C2T<R>::T *__restrict__ psi, double *__restrict__ u,
+                                                    int k, int n1, int nh, int64_t slot_size) {
+  using C = typename C2T<R>::T;
+  extern __shared__ unsigned char smem_raw[];
+  const Block blk = blocks[blockIdx.x];
+  const int K = blk.K, nl = 1 << blk.dl;
+  const int64_t *lv = bleaves + blk.leaf0;
+  const C *ps = psi + (int64_t)blk.slot * slot_size;
+  const bool acc_u = (blk.flags & 1) != 0;
+  const int nn = (D == 3) ? n1 * n1 : n1;
+  C *Y1 = reinterpret_cast<C *>(smem_raw);            // [K][nn]
+  C *Y2 = Y1 + (size_t)K * nn;                         // [K][K][n1] (3D)
+  C *E1 = Y2 + (D == 3 ? (size_t)K * K * n1 : 0);      // [K][n1]
+  C *E2 = E1 + (size_t)K * n1;                         // [K][n1] (3D)
+  C *Ed = E2 + (D == 3 ? (size_t)K * n1 : 0);          // [K][nh]
+  for (int e = threadIdx.x; e < K * n1; e += blockDim.x) {
+    const int I = e / n1, m = e - I * n1;
+    E1[e] = Ef[((int64_t)(blk.mat[0] + I / k) * k + I % k) * n1 + m];
+    if (D == 3) E2[e] = Ef[((int64_t)(blk.mat[1] + I / k) * k + I % k) * n1 + m];
+  }
+  for (int e = threadIdx.x; e < K * nh; e += blockDim.x) {
+    const int I = e / nh, m = e - I * nh;
+    Ed[e] = Eh[((int64_t)(blk.mat[D - 1] + I / k) * k + I % k) * nh + m];
+  }
+  __syncthreads();
+  // Y1[r][mode] = sum_{m_d} Ed[r][m_d] psi[m_d][mode]; psi fetched 8 planes at a time so that
+  // eight loads are in flight per thread
+  for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+    R ar[KM], ai[KM];
+#pragma unroll
+    for (int r = 0; r < KM; ++r) ar[r] = ai[r] = 0;
+    for (int md0 = 0; md0 < nh; md0 += 8) {
+      C v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = (md0 + q < nh) ? ps[(int64_t)(md0 + q) * nn + idx] : C{0, 0};
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (md0 + q < nh) {
+#pragma unroll
+          for (int r = 0; r < KM; ++r)
+            if (r < K) cfma(ar[r], ai[r], Ed[r * nh + md0 + q], v[q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < KM; ++r)
+      if (r < K) Y1[(size_t)r * nn + idx] = C{ar[r], ai[r]};
+  }
+  __syncthreads();
+  const int kp = (D == 3) ? k * k * k : k * k;
+  if (D == 3) {
+    // Y2[r][I2][m1] = sum_m2 E2[I2][m2] Y1[r][m2][m1]
+    for (int e = threadIdx.x; e < K * K * n1; e += blockDim.x) {
+      const int m1 = e % n1, rest = e / n1, I2 = rest % K, r = rest / K;
+      const C *ep = E2 + (size_t)I2 * n1;
+      const C *yp = Y1 + (size_t)r * nn + m1;
+      R ar = 0, ai = 0;
+      for (int m2 = 0; m2 < n1; ++m2) cfma(ar, ai, ep[m2], yp[m2 * n1]);
+      Y2[e] = C{ar, ai};
+    }
+    __syncthreads();
+    // u(r, I2, I1) = Re sum_m1 E1[I1][m1] Y2[r][I2][m1]
+    for (int e = threadIdx.x; e < K * K * K; e += blockDim.x) {
+      const int I1 = e % K, rest = e / K, I2 = rest % K, r = rest / K;
+      const C *ep = E1 + (size_t)I1 * n1;
+      const C *yp = Y2 + ((size_t)r * K + I2) * n1;
+      R acc = 0;
+      for (int m1 = 0; m1 < n1; ++m1) {
+        const C a = ep[m1], y = yp[m1];
+        acc = fma(a.x, y.x, acc);
+        acc = fma(-a.y, y.y, acc);
+      }
+      const int o1 = I1 / k, o2 = I2 / k, o3 = r / k;
+      double *up = u + lv[(o3 * nl + o2) * nl + o1] * kp + ((r - o3 * k) * k + (I2 - o2 * k)) * k + (I1 - o1 * k);
+      if (acc_u) *up += (double)acc; else *up = (double)acc;
+    }
+  } else {
+    for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+      const int I1 = e % K, r = e / K;
+      const C *ep = E1 + (size_t)I1 * n1;
+      const C *yp = Y1 + (size_t)r * nn;
+      R acc = 0;
+      for (int m1 = 0; m1 < n1; ++m1) {
+        const C a = ep[m1], y = yp[m1];
+        acc = fma(a.x, y.x, acc);
+        acc = fma(-a.y, y.y, acc);
+      }
+      const int o1 = I1 / k, o2 = r / k;
+      double *up = u + lv[o2 * nl + o1] * kp + (r - o2 * k) * k + (I1 - o1 * k);
+      if (acc_u) *up += (double)acc; else *up = (double)acc;
+    }
+  }
+}
+
 // ----------------------------------------------------------------------------- diagonal shifts
 
 template <int D>
@@ -338,6 +736,69 @@ __global__ void push_kernel(const TreeShift *__restrict__ items, const typename 
 }
 
 // ----------------------------------------------------------------------------- near field
+
+// One D-list pair per CTA: u_T += (K_d x ... x K_1) sigma_S with the three k x k tables of the
+// pair, added to u with FP64 atomics (u is cleared before the evaluation step stores into it).
+// Pair-parallel so that many pairs are in flight at once; the tables and sigma_S are staged in
+// shared memory.
+template <int D>
+__global__ void __launch_bounds__(128) near2_kernel(const NearPair *__restrict__ pairs, const double *__restrict__ tab,
+                                                    const double *__restrict__ sigma, double *__restrict__ u, int k) {
+  extern __shared__ double sm[];
+  const int kk = k * k;
+  const int np = (D == 3) ? kk * k : kk;
+  double *s0 = sm, *A = sm + np, *B = A + np, *T = B + np;
+  const NearPair pr = pairs[blockIdx.x];
+  const double *sg = sigma + pr.src * np;
+  for (int e = threadIdx.x; e < np; e += blockDim.x) s0[e] = __ldg(sg + e);
+  for (int e = threadIdx.x; e < D * kk; e += blockDim.x) {
+    const int a = e / kk;
+    T[e] = __ldg(tab + (int64_t)pr.tab[a] * kk + (e - a * kk));
+  }
+  __syncthreads();
+  double *ut = u + pr.tgt * np;
+  if (D == 3) {
+    for (int e = threadIdx.x; e < np; e += blockDim.x) {  // A[j3][j2][t1] = sum_j1 T1[t1][j1] s0[j3][j2][j1]
+      const int row = e / k, t1 = e - row * k;
+      const double *sp = s0 + row * k, *tp = T + t1 * k;
+      double a = 0;
+      for (int j = 0; j < k; ++j) a = fma(tp[j], sp[j], a);
+      A[e] = a;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < np; e += blockDim.x) {  // B[j3][t2][t1] = sum_j2 T2[t2][j2] A[j3][j2][t1]
+      const int j3 = e / kk, rem = e - j3 * kk, t2 = rem / k, t1 = rem - t2 * k;
+      const double *tp = T + kk + t2 * k, *ap = A + j3 * kk + t1;
+      double a = 0;
+      for (int j = 0; j < k; ++j) a = fma(tp[j], ap[j * k], a);
+      B[e] = a;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < np; e += blockDim.x) {  // u[t3][t2][t1] += sum_j3 T3[t3][j3] B[j3][t2][t1]
+      const int t3 = e / kk, rem = e - t3 * kk;
+      const double *tp = T + 2 * kk + t3 * k, *bp = B + rem;
+      double a = 0;
+      for (int j = 0; j < k; ++j) a = fma(tp[j], bp[j * kk], a);
+      atomicAdd(ut + e, a);
+    }
+  } else {
+    for (int e = threadIdx.x; e < np; e += blockDim.x) {  // A[j2][t1] = sum_j1 T1[t1][j1] s0[j2][j1]
+      const int j2 = e / k, t1 = e - j2 * k;
+      const double *sp = s0 + j2 * k, *tp = T + t1 * k;
+      double a = 0;
+      for (int j = 0; j < k; ++j) a = fma(tp[j], sp[j], a);
+      A[e] = a;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < np; e += blockDim.x) {  // u[t2][t1] += sum_j2 T2[t2][j2] A[j2][t1]
+      const int t2 = e / k, t1 = e - t2 * k;
+      const double *tp = T + kk + t2 * k, *ap = A + t1;
+      double a = 0;
+      for (int j = 0; j < k; ++j) a = fma(tp[j], ap[j * k], a);
+      atomicAdd(ut + e, a);
+    }
+  }
+}
 
 template <int D>
 __global__ void __launch_bounds__(256) near_kernel(const int64_t *__restrict__ tgt, const int32_t *__restrict__ flags,
@@ -461,17 +922,41 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
     if (e.events) cudaEventRecord(e.events[2 * ph + end], st);
   };
   mark(0, 0);
+  if (e.n_near_pairs > 0) {
+    // the near field adds into u with atomics: clear it first (evaluation then stores its leaves)
+    if ((err = cudaMemsetAsync(u, 0, sizeof(double) * (size_t)e.n_points, st)) != cudaSuccess) return err;
+  }
   if (e.n_blocks > 0) {
     // outgoing expansions: zero, then every block adds its contribution
     if ((err = cudaMemsetAsync(phi, 0, sizeof(C) * ss * e.n_phi_slots, st)) != cudaSuccess) return err;
-    const size_t fsm = form_smem_bytes(D, e.Kmax, n1, sizeof(R) == 4);
-    if ((err = cudaFuncSetAttribute(form_kernel<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm)) !=
-        cudaSuccess)
-      return err;
-    form_kernel<D, R><<<dim3((unsigned)e.n_blocks, (unsigned)nh), 256, fsm, st>>>(
-        e.blocks, e.block_leaves, sigma, reinterpret_cast<const C *>(e.Ff), reinterpret_cast<const C *>(e.Fh), phi,
-        e.k, n1, nh, ss, e.Kmax);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if (e.n_f1 > 0) {
+      const size_t fsm = form_smem_bytes(D, e.Kmax_f1, n1, sizeof(R) == 4);
+      if ((err = cudaFuncSetAttribute(form_kernel<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm)) !=
+          cudaSuccess)
+        return err;
+      form_kernel<D, R><<<dim3((unsigned)e.n_f1, (unsigned)nh), 256, fsm, st>>>(
+          e.f1_blocks, e.block_leaves, sigma, reinterpret_cast<const C *>(e.Ff), reinterpret_cast<const C *>(e.Fh),
+          phi, e.k, n1, nh, ss, e.Kmax_f1);
+      if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    for (const LaunchRange &lr : e.f2_ranges) {  // one launch per block size K
+      if (D == 3) {
+        if ((err = cudaFuncSetAttribute(form3_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)lr.smem)) != cudaSuccess)
+          return err;
+        form3_kernel<R><<<dim3((unsigned)lr.count, (unsigned)((nh + kSc - 1) / kSc)), 256, lr.smem, st>>>(
+            e.f2_blocks, e.f2_gptr + lr.first, e.block_leaves, sigma, reinterpret_cast<const C *>(e.Ff),
+            reinterpret_cast<const C *>(e.Fh), phi, e.k, n1, nh, ss);
+      } else {
+        if ((err = cudaFuncSetAttribute(form2_kernel<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)lr.smem)) != cudaSuccess)
+          return err;
+        form2_kernel<D, R><<<dim3((unsigned)lr.count, (unsigned)nh), 256, lr.smem, st>>>(
+            e.f2_blocks, e.f2_gptr + lr.first, e.block_leaves, sigma, reinterpret_cast<const C *>(e.Ff),
+            reinterpret_cast<const C *>(e.Fh), phi, e.k, n1, nh, ss);
+      }
+      if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
   }
   mark(0, 1);
   mark(1, 0);
@@ -501,26 +986,35 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
   }
   mark(3, 1);
   mark(4, 0);
-  if (e.n_blocks > 0) {
-    const size_t esm = eval_smem_bytes(D, e.Kmax, n1, sizeof(R) == 4);
+  if (e.n_e1 > 0) {
+    const size_t esm = eval_smem_bytes(D, e.Kmax_e1, n1, sizeof(R) == 4);
     if ((err = cudaFuncSetAttribute(eval_kernel<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm)) !=
         cudaSuccess)
       return err;
-    eval_kernel<D, R><<<dim3((unsigned)e.n_blocks, (unsigned)e.Kmax), 256, esm, st>>>(
-        e.blocks, e.block_leaves, reinterpret_cast<const C *>(e.Ef), reinterpret_cast<const C *>(e.Eh), eval_src, u,
-        e.k, n1, nh, ss);
+    eval_kernel<D, R><<<dim3((unsigned)e.n_e1, (unsigned)e.Kmax_e1), 256, esm, st>>>(
+        e.e1_blocks, e.block_leaves, reinterpret_cast<const C *>(e.Ef), reinterpret_cast<const C *>(e.Eh), eval_src,
+        u, e.k, n1, nh, ss);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  for (const LaunchRange &lr : e.e2_ranges) {  // one launch per block size K
+    auto kern = lr.K <= 8 ? eval2_kernel<D, R, 8> : eval2_kernel<D, R, 16>;
+    if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) !=
+        cudaSuccess)
+      return err;
+    kern<<<(unsigned)lr.count, sizeof(R) == 4 ? 512 : 256, lr.smem, st>>>(
+        e.e2_blocks + lr.first, e.block_leaves, reinterpret_cast<const C *>(e.Ef), reinterpret_cast<const C *>(e.Eh),
+        eval_src, u, e.k, n1, nh, ss);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   mark(4, 1);
   mark(5, 0);
-  if (e.n_near > 0) {
+  if (e.n_near_pairs > 0) {
     const int np = D == 3 ? e.k * e.k * e.k : e.k * e.k;
     const size_t nsm = sizeof(double) * (3 * (size_t)np + (size_t)D * e.k * e.k);
-    if ((err = cudaFuncSetAttribute(near_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nsm)) !=
+    if ((err = cudaFuncSetAttribute(near2_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nsm)) !=
         cudaSuccess)
       return err;
-    near_kernel<D><<<(unsigned)e.n_near, 256, nsm, st>>>(e.near_tgt, e.near_flags, e.near_ptr, e.near_src, e.near_tab,
-                                                         sigma, u, e.k);
+    near2_kernel<D><<<(unsigned)e.n_near_pairs, 128, nsm, st>>>(e.near_pairs, e.near_tab, sigma, u, e.k);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   mark(5, 1);
@@ -529,11 +1023,11 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
 
 int launches_per_transform(const ExecDesc &e) {
   int n = 0;
-  if (e.n_blocks > 0) n += 2;  // form + evaluate
+  n += (e.n_f1 > 0) + (int)e.f2_ranges.size() + (e.n_e1 > 0) + (int)e.e2_ranges.size();  // form + evaluate
   for (const ShiftStep &s : e.merge) n += s.n > 0;
   for (const ShiftStep &s : e.push) n += s.n > 0;
   if (!e.fourier && e.n_gather > 0) n += 1;
-  if (e.n_near > 0) n += 1;
+  if (e.n_near_pairs > 0) n += 1;
   return n;
 }
 

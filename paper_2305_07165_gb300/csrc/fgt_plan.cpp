@@ -530,6 +530,89 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   ex.Kmax = Kmax;
   P.n_blocks = ex.n_blocks;
 
+  // ---- kernel choice per block.  Form: blocks whose sigma and matrices fit in shared memory go
+  // to the grouped kernel, up to 8 blocks of one anchor and one size per CTA (fewer when they
+  // would not leave room for two CTAs per SM); the rest to the per-(block, m_d) kernel.
+  // Evaluation: blocks with K <= 16 whose whole-block intermediates fit go to the whole-block
+  // kernel; the rest to the per-(block, row) kernel.
+  std::vector<fgt::Block> f1, f2, e1, e2;
+  std::vector<int32_t> f2ptr(1, 0);
+  int Kf1 = 0, Ke1 = 0;
+  {
+    const size_t rsz = P.prec ? sizeof(float) : sizeof(double), csz = sizeof(C);
+    const size_t three_per_sm = 72 * 1024;
+    // 3D uses the register-tiled kernel (planes in chunks of 4), 2D the plain grouped one
+    auto gbytes = [&](int g, int K) {
+      return d == 3 ? fgt::form3_bytes(g, K, n1, rsz, csz) : fgt::form2_bytes(d, g, K, n1, nh, rsz, csz);
+    };
+    auto gmax = [&](int K) {
+      int G = 0;
+      if (K > 16) return 0;  // large blocks: staging sigma would leave one CTA per SM
+      for (int g = 1; g <= 8; ++g)
+        if (gbytes(g, K) <= three_per_sm) G = g;
+      if (G == 0 && gbytes(1, K) <= (size_t)smax) G = 1;
+      return G;
+    };
+    // form: groups of one anchor and one K, ordered by K so that each K gets its own launch
+    // (and its own shared-memory size)
+    std::vector<fgt::Block> sorted = blocks;
+    std::stable_sort(sorted.begin(), sorted.end(), [](const fgt::Block &a, const fgt::Block &b) {
+      return a.K != b.K ? a.K < b.K : a.slot < b.slot;
+    });
+    size_t q = 0;
+    while (q < sorted.size()) {
+      const int K = sorted[q].K, G = gmax(K);
+      if (G == 0) {
+        f1.push_back(sorted[q]);
+        Kf1 = std::max(Kf1, K);
+        ++q;
+        continue;
+      }
+      const int first_group = (int)f2ptr.size() - 1;
+      while (q < sorted.size() && sorted[q].K == K) {
+        const int32_t slot = sorted[q].slot;
+        int n = 0;
+        while (q < sorted.size() && sorted[q].K == K && sorted[q].slot == slot && n < G) {
+          f2.push_back(sorted[q]);
+          ++q;
+          ++n;
+        }
+        f2ptr.push_back((int32_t)f2.size());
+      }
+      fgt::LaunchRange lr;
+      lr.first = first_group;
+      lr.count = (int)f2ptr.size() - 1 - first_group;
+      lr.K = K;
+      lr.smem = gbytes(G, K);
+      ex.f2_ranges.push_back(lr);
+    }
+    // evaluation: whole-block kernel for K <= 16 when it fits, one launch per K
+    for (const fgt::Block &b : sorted) {
+      const size_t eb = fgt::eval2_bytes(d, b.K, n1, nh, csz);
+      if (b.K <= 16 && eb <= (size_t)smax) {
+        if (ex.e2_ranges.empty() || ex.e2_ranges.back().K != b.K) {
+          fgt::LaunchRange lr;
+          lr.first = (int)e2.size();
+          lr.count = 0;
+          lr.K = b.K;
+          lr.smem = eb;
+          ex.e2_ranges.push_back(lr);
+        }
+        e2.push_back(b);
+        ex.e2_ranges.back().count++;
+      } else {
+        e1.push_back(b);
+        Ke1 = std::max(Ke1, b.K);
+      }
+    }
+  }
+  ex.n_f1 = (int64_t)f1.size();
+  ex.Kmax_f1 = Kf1;
+  ex.n_f2_groups = (int64_t)f2ptr.size() - 1;
+  ex.n_e1 = (int64_t)e1.size();
+  ex.Kmax_e1 = Ke1;
+  ex.n_e2 = (int64_t)e2.size();
+
   // ---- out->in gather at the cutoff level (P-list)
   std::vector<int32_t> gdst;
   std::vector<int64_t> gptr(1, 0);
@@ -721,9 +804,24 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   }
   ex.n_near = (int64_t)ntgt.size();
   P.n_near_pairs = (int64_t)nsrc.size();
+  std::vector<fgt::NearPair> npairs;
+  npairs.reserve(nsrc.size());
+  for (size_t i = 0; i < ntgt.size(); ++i)
+    for (int64_t q = nptr[i]; q < nptr[i + 1]; ++q) {
+      fgt::NearPair pr{};
+      pr.tgt = ntgt[i];
+      pr.src = nsrc[q].leaf;
+      for (int a = 0; a < 3; ++a) pr.tab[a] = nsrc[q].tab[a];
+      npairs.push_back(pr);
+    }
+  ex.n_near_pairs = (int64_t)npairs.size();
+  ex.n_points = P.n_leaves * (int64_t)P.np();
 
   // ---- upload
   const size_t o_blocks = pack.add("blocks", blocks), o_bleaves = pack.add("block_leaves", bleaves);
+  const size_t o_f1 = pack.add("form1_blocks", f1), o_f2 = pack.add("form2_blocks", f2),
+               o_f2p = pack.add("form2_groups", f2ptr), o_e1 = pack.add("eval1_blocks", e1),
+               o_e2 = pack.add("eval2_blocks", e2);
   const size_t o_Ff = pack.add("Ff", Ff), o_Fh = pack.add("Fh", Fh), o_Ef = pack.add("Ef", Ef),
                o_Eh = pack.add("Eh", Eh);
   const size_t o_gdst = pack.add("gather_dst", gdst), o_gptr = pack.add("gather_ptr", gptr),
@@ -731,7 +829,7 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   const size_t o_Pf = pack.add("Pf", Pf), o_Ph = pack.add("Ph", Ph);
   const size_t o_ntgt = pack.add("near_tgt", ntgt), o_nflags = pack.add("near_flags", nflags),
                o_nptr = pack.add("near_ptr", nptr), o_nsrc = pack.add("near_src", nsrc),
-               o_ntab = pack.add("near_tab", ntab);
+               o_ntab = pack.add("near_tab", ntab), o_npairs = pack.add("near_pairs", npairs);
   std::vector<std::tuple<size_t, size_t, size_t, int64_t>> step_off;  // items, qf, qh, n
   for (size_t i = 0; i < merge_h.size(); ++i) {
     auto &s = merge_h[i];
@@ -785,6 +883,11 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   ex.phi = P.work;
   ex.psi = (char *)P.work + phi_bytes;
   ex.blocks = (const fgt::Block *)at(o_blocks);
+  ex.f1_blocks = (const fgt::Block *)at(o_f1);
+  ex.f2_blocks = (const fgt::Block *)at(o_f2);
+  ex.f2_gptr = (const int32_t *)at(o_f2p);
+  ex.e1_blocks = (const fgt::Block *)at(o_e1);
+  ex.e2_blocks = (const fgt::Block *)at(o_e2);
   ex.block_leaves = (const int64_t *)at(o_bleaves);
   ex.Ff = at(o_Ff); ex.Fh = at(o_Fh); ex.Ef = at(o_Ef); ex.Eh = at(o_Eh);
   ex.gather_dst = (const int32_t *)at(o_gdst);
@@ -796,6 +899,7 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   ex.near_ptr = (const int64_t *)at(o_nptr);
   ex.near_src = (const fgt::NearSrc *)at(o_nsrc);
   ex.near_tab = (const double *)at(o_ntab);
+  ex.near_pairs = (const fgt::NearPair *)at(o_npairs);
   size_t si = 0;
   for (size_t s = 0; s < merge_h.size(); ++s, ++si) {
     fgt::ShiftStep st;
@@ -1165,6 +1269,143 @@ fgt_status fgt_legendre_fourier_integrals(double t, int nmax, double *re, double
   if (nmax < 0 || nmax > 70 || !re || !im || !std::isfinite(t) || std::fabs(t) > 1e4)
     return fail(FGT_ERR_ARG, "bad argument");
   fgt::legendre_fourier_integrals(t, nmax, re, im);
+  return FGT_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================ batched execution
+//
+// Many independent transforms in one launch: the kernel sequence of every plan is captured
+// once into a CUDA graph in which each transform is its own branch (branches rotate over a
+// small pool of capture streams), so the device runs the transforms' kernels concurrently and
+// the host issues a single graph launch.  The graph is rebuilt only when the input / output
+// pointers change.
+
+struct fgt_batch {
+  std::vector<fgt_plan *> plans;
+  std::vector<cudaStream_t> streams;   // branch streams used while capturing
+  cudaStream_t cap = nullptr;          // capture origin
+  std::vector<cudaEvent_t> events;     // [0] fork, [1..n] joins
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const double *> sig;
+  std::vector<double *> u;
+  ~fgt_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+    for (cudaStream_t s : streams) cudaStreamDestroy(s);
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
+namespace {
+
+fgt_status batch_capture(fgt_batch *b) {
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return cuda_fail(e, "batch capture");
+  cudaError_t first = cudaEventRecord(b->events[0], b->cap);
+  for (size_t i = 0; i < b->plans.size() && first == cudaSuccess; ++i) {
+    cudaStream_t s = b->streams[i % b->streams.size()];
+    first = cudaStreamWaitEvent(s, b->events[0], 0);
+    if (first != cudaSuccess) break;
+    fgt::ExecDesc ex = b->plans[i]->ex;
+    ex.events = nullptr;
+    first = fgt::run_transform(ex, b->sig[i], b->u[i], s);
+    if (first != cudaSuccess) break;
+    first = cudaEventRecord(b->events[1 + i], s);
+    if (first != cudaSuccess) break;
+    first = cudaStreamWaitEvent(b->cap, b->events[1 + i], 0);
+  }
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(b->cap, &g);
+  if (first != cudaSuccess || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return cuda_fail(first != cudaSuccess ? first : e, "batch capture");
+  }
+  e = cudaGraphInstantiate(&b->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    b->exec = nullptr;
+    return cuda_fail(e, "batch graph instantiate");
+  }
+  return FGT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fgt_status fgt_batch_create(fgt_plan *const *plans, int n, fgt_batch **out) {
+  if (!out || !plans || n < 1) return fail(FGT_ERR_ARG, "bad batch arguments");
+  *out = nullptr;
+  fgt_batch *b = new (std::nothrow) fgt_batch();
+  if (!b) return fail(FGT_ERR_OOM, "host allocation");
+  for (int i = 0; i < n; ++i) {
+    fgt_plan *p = plans[i];
+    if (!p || p->host_only) { delete b; return fail(FGT_ERR_ARG, "batch plan " + std::to_string(i) + " is not a device plan"); }
+    if (p->dirty) {
+      fgt_status s = prepare(*p);
+      if (s != FGT_OK) { delete b; return s; }
+    }
+    b->plans.push_back(p);
+  }
+  const int nstreams = std::min(n, 16);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  for (int i = 0; i < nstreams && e == cudaSuccess; ++i) {
+    cudaStream_t s;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->streams.push_back(s);
+  }
+  for (int i = 0; i <= n && e == cudaSuccess; ++i) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->events.push_back(ev);
+  }
+  if (e != cudaSuccess) { delete b; return cuda_fail(e, "batch streams/events"); }
+  b->sig.assign(n, nullptr);
+  b->u.assign(n, nullptr);
+  *out = b;
+  return FGT_OK;
+}
+
+fgt_status fgt_batch_execute(fgt_batch *b, const double *const *sigma_dev, double *const *u_dev, void *stream) {
+  if (!b || !sigma_dev || !u_dev) return fail(FGT_ERR_ARG, "NULL argument");
+  bool same = b->exec != nullptr;
+  for (size_t i = 0; i < b->plans.size(); ++i) {
+    if (!sigma_dev[i] || !u_dev[i]) return fail(FGT_ERR_ARG, "NULL buffer in batch");
+    if (b->plans[i]->dirty) return fail(FGT_ERR_STATE, "a batch plan changed mode or precision; rebuild the batch");
+    if (b->sig[i] != sigma_dev[i] || b->u[i] != u_dev[i]) same = false;
+  }
+  if (!same) {
+    for (size_t i = 0; i < b->plans.size(); ++i) {
+      b->sig[i] = sigma_dev[i];
+      b->u[i] = u_dev[i];
+    }
+    fgt_status s = batch_capture(b);
+    if (s != FGT_OK) return s;
+  }
+  cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch launch");
+  return FGT_OK;
+}
+
+void fgt_batch_destroy(fgt_batch *b) { delete b; }
+
+fgt_status fgt_execute_batch(fgt_plan *const *plans, const double *const *sigma_dev, double *const *u_dev, int n,
+                             void *stream) {
+  fgt_batch *b = nullptr;
+  fgt_status s = fgt_batch_create(plans, n, &b);
+  if (s != FGT_OK) return s;
+  s = fgt_batch_execute(b, sigma_dev, u_dev, stream);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  fgt_batch_destroy(b);
+  if (s != FGT_OK) return s;
+  if (e != cudaSuccess) return cuda_fail(e, "batch");
   return FGT_OK;
 }
 

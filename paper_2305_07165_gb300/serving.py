@@ -1,0 +1,180 @@
+"""Continuous-batching request loop for box Gauss transforms on one GPU.
+
+Requests (a tree, a density, delta, tol, boundary condition) arrive at any
+time.  The loop admits them while their device footprint fits a budget
+(``fgt_plan_analyze`` reports a plan's bytes before anything is allocated),
+builds plans on a host thread pool while the GPU works, and launches every
+admitted, planned request as soon as it is ready -- each on its own CUDA stream
+so that transforms overlap on the device -- without waiting for earlier
+launches to finish.  Completed requests free their memory, which admits the
+next ones.  Trees, tables and expansions stay resident on the device for the
+life of a request; results come back to pinned host memory.
+
+Reports per-request latency (arrival -> result on the host) and the points/s
+achieved over the run.
+"""
+from __future__ import annotations
+
+import queue
+import threading
+import time
+from concurrent.futures import Future, ThreadPoolExecutor
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import BC_FREE, PREC_FP64, PREC_SPLIT, Plan, analyze
+
+
+@dataclass
+class Request:
+    d: int
+    k: int
+    delta: float
+    tol: float
+    level: np.ndarray
+    coord: np.ndarray
+    sigma: np.ndarray               # float64 [n_leaves, k**d] (host)
+    bc: int = BC_FREE
+    prec: int | None = None         # default: split when tol >= 1e-7, else FP64
+    rid: int = -1
+    t_arrival: float = 0.0
+    t_done: float = 0.0
+    footprint: int = 0
+    future: Future = field(default_factory=Future)
+
+    @property
+    def n_points(self):
+        return int(self.sigma.size)
+
+
+class Server:
+    """Admission by device-memory footprint, host-side planning overlapped with GPU work,
+    one stream per in-flight request, completion by CUDA events."""
+
+    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 32, planner_threads: int = 4,
+                 device: int = 0):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.budget = int(hbm_budget_bytes)
+        self.used = 0
+        self.max_inflight = max_inflight
+        self.pending: "queue.Queue[Request]" = queue.Queue()
+        self.pool = ThreadPoolExecutor(max_workers=planner_threads)
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(max_inflight)]
+        self.free_streams = list(range(max_inflight))
+        self.lock = threading.Lock()
+        self.stop = False
+        self.completed: list[Request] = []
+        self.thread = threading.Thread(target=self._loop, daemon=True)
+        self.next_id = 0
+
+    # ---------------------------------------------------------------- client side
+    def submit(self, req: Request) -> Future:
+        req.t_arrival = time.perf_counter()
+        with self.lock:
+            req.rid = self.next_id
+            self.next_id += 1
+        if req.prec is None:
+            req.prec = PREC_SPLIT if req.tol >= 1e-7 else PREC_FP64
+        info = analyze(req.d, req.k, req.delta, req.tol, req.level, req.coord, bc=req.bc, prec=req.prec)
+        req.footprint = int(info["device_bytes"]) + 2 * 8 * req.n_points
+        if req.footprint > self.budget:
+            req.future.set_exception(MemoryError(f"request needs {req.footprint} bytes, budget {self.budget}"))
+            return req.future
+        self.pending.put(req)
+        return req.future
+
+    def start(self):
+        self.thread.start()
+        return self
+
+    def shutdown(self):
+        self.stop = True
+        self.thread.join()
+        self.pool.shutdown()
+
+    # ---------------------------------------------------------------- loop
+    def _plan(self, req: Request):
+        torch = self.torch
+        torch.cuda.set_device(self.device)
+        plan = Plan(req.d, req.k, req.delta, req.tol, req.level, req.coord, bc=req.bc, prec=req.prec)
+        sig_h = torch.from_numpy(np.ascontiguousarray(req.sigma)).pin_memory()
+        out_h = torch.empty_like(sig_h).pin_memory()
+        return plan, sig_h, out_h
+
+    def _loop(self):
+        torch = self.torch
+        torch.cuda.set_device(self.device)
+        waiting: list[Request] = []          # admitted, not yet planned
+        planning: list[tuple[Request, Future]] = []
+        inflight: list[tuple] = []
+        while True:
+            # admit by footprint
+            while True:
+                if not waiting:
+                    try:
+                        waiting.append(self.pending.get_nowait())
+                    except queue.Empty:
+                        break
+                r = waiting[0]
+                if self.used + r.footprint > self.budget or len(planning) + len(inflight) >= self.max_inflight:
+                    break
+                waiting.pop(0)
+                self.used += r.footprint
+                planning.append((r, self.pool.submit(self._plan, r)))
+            # launch everything that finished planning
+            still = []
+            for r, f in planning:
+                if f.done() and self.free_streams:
+                    try:
+                        plan, sig_h, out_h = f.result()
+                    except Exception as e:  # planning failed: report and release
+                        self.used -= r.footprint
+                        r.future.set_exception(e)
+                        continue
+                    si = self.free_streams.pop()
+                    st = self.streams[si]
+                    with torch.cuda.stream(st):
+                        sig_d = sig_h.to(f"cuda:{self.device}", non_blocking=True)
+                        u_d = torch.empty_like(sig_d)
+                        plan.execute(sig_d, out=u_d, stream=st)
+                        out_h.copy_(u_d, non_blocking=True)
+                        ev = torch.cuda.Event()
+                        ev.record(st)
+                    inflight.append((r, plan, sig_d, u_d, out_h, ev, si))
+                else:
+                    still.append((r, f))
+            planning = still
+            # complete
+            rest = []
+            for item in inflight:
+                r, plan, sig_d, u_d, out_h, ev, si = item
+                if ev.query():
+                    r.t_done = time.perf_counter()
+                    r.future.set_result(out_h.numpy().reshape(r.sigma.shape))
+                    plan.close()
+                    self.free_streams.append(si)
+                    self.used -= r.footprint
+                    self.completed.append(r)
+                else:
+                    rest.append(item)
+            inflight = rest
+            if self.stop and not waiting and not planning and not inflight and self.pending.empty():
+                break
+            if not (planning or inflight):
+                time.sleep(1e-4)
+
+    # ---------------------------------------------------------------- statistics
+    def stats(self, t0=None, t1=None):
+        done = self.completed
+        if not done:
+            return {}
+        lat = np.array([r.t_done - r.t_arrival for r in done]) * 1e3
+        t0 = min(r.t_arrival for r in done) if t0 is None else t0
+        t1 = max(r.t_done for r in done) if t1 is None else t1
+        pts = sum(r.n_points for r in done)
+        return {"requests": len(done), "points": pts, "points_per_s": pts / max(t1 - t0, 1e-9),
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean())}

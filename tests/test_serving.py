@@ -1,0 +1,70 @@
+"""Continuous-batching request loop: results in the mix equal results alone.
+
+Requests of mixed dimension, boundary condition and tolerance arrive while
+others are on the GPU; the loop admits them by device-memory footprint and
+overlaps their work on separate streams.  Each result must match the same
+request transformed alone, within the request's tolerance.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+F = pytest.importorskip("paper_2305_07165_gb300")
+S = pytest.importorskip("paper_2305_07165_gb300.serving")
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(n, seed=0):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        d = int(rng.choice([2, 3]))
+        per = bool(rng.integers(2))
+        tol = float(rng.choice([1e-6, 1e-10]))
+        delta = float(10 ** rng.uniform(-3.5, -1.5))
+        k = 6 if d == 2 else 4
+        tr = W.random_balanced_tree(d, int(rng.integers(1 << 30)), max_level=5 if d == 2 else 3,
+                                    min_level=1, split_prob=0.4, periodic=per)
+        sig = W.random_sigma(tr, k, int(rng.integers(1 << 30)))
+        reqs.append(S.Request(d=d, k=k, delta=delta, tol=tol, level=tr.level, coord=tr.coord, sigma=sig,
+                              bc=int(per)))
+    return reqs
+
+
+def _alone(r):
+    plan = F.Plan(r.d, r.k, r.delta, r.tol, r.level, r.coord, bc=r.bc, prec=r.prec)
+    u = plan(torch.from_numpy(r.sigma).cuda()).cpu().numpy()
+    plan.close()
+    return u
+
+
+def test_results_in_the_mix_equal_results_alone():
+    reqs = _requests(16)
+    srv = S.Server(hbm_budget_bytes=2 << 30, max_inflight=6).start()
+    futs = []
+    for i, r in enumerate(reqs):
+        futs.append(srv.submit(r))
+        if i % 3 == 2:
+            time.sleep(0.002)  # arrivals spread over time, some while others run
+    outs = [f.result(timeout=120) for f in futs]
+    srv.shutdown()
+    st = srv.stats()
+    assert st["requests"] == len(reqs) and st["p99_ms"] >= st["p50_ms"] > 0
+    for r, u in zip(reqs, outs):
+        ua = _alone(r)
+        scale = np.abs(ua).max()
+        assert np.abs(u - ua).max() <= 10 * r.tol * scale
+
+
+def test_admission_refuses_requests_larger_than_the_budget():
+    r = _requests(1, seed=3)[0]
+    srv = S.Server(hbm_budget_bytes=1024, max_inflight=2).start()
+    f = srv.submit(r)
+    with pytest.raises(MemoryError):
+        f.result(timeout=10)
+    srv.shutdown()
