@@ -135,6 +135,64 @@ def cpu_oracle_rate(w, budget_s=15.0, threads=0):
     return m * w.p ** w.d / dt, cores, m, dt
 
 
+def run_batched_and_serving(args, F, torch):
+    """256 independent free-space transforms (d 2/3, depth 2-7, p 8/12/16, delta 1e-5..1e-1):
+    one after another on one stream vs one batched graph launch, split form at tol 1e-6 (FP64
+    at 1e-6 too); then a Poisson-arrival serving run over the same requests."""
+    import workloads as W
+    from paper_2305_07165_gb300 import serving as S
+    ws = W.batched_configs(seed=0, n=256)
+    npts = sum(w.n_points for w in ws)
+    sig = [torch.from_numpy(w.sigma).cuda() for w in ws]
+    out = [torch.empty_like(s) for s in sig]
+    res = {"transforms": len(ws), "points": int(npts),
+           "mix": "d 2/3, tree depth 2-7, p 8/12/16, delta log-U[1e-5,1e-1], 1-8 Gaussians, free space"}
+    st = torch.cuda.current_stream()
+    for name, prec in (("split_tol1e-6", F.PREC_SPLIT), ("fp64_tol1e-6", F.PREC_FP64)):
+        plans = [F.Plan(w.d, w.p, w.delta, 1e-6, w.tree.level, w.tree.coord, prec=prec) for w in ws]
+        batch = F.Batch(plans)
+        reps = max(2, args.steps // 4)
+        for _ in range(2):
+            batch(sig, out)
+            for p, s, o in zip(plans, sig, out):
+                p(s, out=o)
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(st)
+        for _ in range(reps):
+            for p, s, o in zip(plans, sig, out):
+                p(s, out=o)
+        e1.record(st)
+        for _ in range(reps):
+            batch(sig, out)
+        e2.record(st)
+        torch.cuda.synchronize()
+        t_serial = e0.elapsed_time(e1) / reps
+        t_graph = e1.elapsed_time(e2) / reps
+        res[name] = {"serial_ms": t_serial, "serial_points_per_s": npts / t_serial * 1e3,
+                     "batched_ms": t_graph, "batched_points_per_s": npts / t_graph * 1e3}
+        batch.close()
+        for p in plans:
+            p.close()
+    # serving: Poisson arrivals (200 requests/s) of the same transforms, admitted by footprint
+    rate = 200.0
+    rng = np.random.default_rng(5)
+    srv = S.Server(hbm_budget_bytes=16 << 30, max_inflight=32).start()
+    t0 = time.perf_counter()
+    futs = []
+    for w in ws[:128]:
+        futs.append(srv.submit(S.Request(d=w.d, k=w.p, delta=w.delta, tol=1e-6, level=w.tree.level,
+                                         coord=w.tree.coord, sigma=w.sigma)))
+        time.sleep(rng.exponential(1.0 / rate))
+    for f in futs:
+        f.result(timeout=300)
+    srv.shutdown()
+    serving = srv.stats(t0=t0)
+    serving["arrival_rate_per_s"] = rate
+    serving["admission_budget_bytes"] = 16 << 30
+    return res, serving
+
+
 def metric_name(w):
     return (f"target points/s (box FGT, {w.d}D {'periodic' if w.periodic else 'free space'}, "
             f"delta={w.delta:g}, tol 1e-6 split form)")
@@ -191,6 +249,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="adaptive3d", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched and serving sections")
     ap.add_argument("--forms", default="split,fp64,fp64_1e-10",
                     help="comma list of split, fp64, fp64_1e-10; the first one is the headline")
     args = ap.parse_args()
@@ -243,6 +302,10 @@ def main():
                              ms_per_step=tot / args.steps, p50_ms=float(np.percentile(times, 50)),
                              p99_ms=float(np.percentile(times, 99)), cutoff_level=info["cutoff_level"],
                              n_f=info["n_f"], launches=info["launches"])
+
+    batched = serving = None
+    if not args.no_batch and rank == 0:
+        batched, serving = run_batched_and_serving(args, F, torch)
 
     # end to end through the host-buffer entry point (pinned host memory, copies timed)
     plan = head["plan"]
@@ -300,6 +363,8 @@ def main():
                     "h2d_bytes_per_step": int(w.n_points * 8), "d2h_bytes_per_step": int(w.n_points * 8)},
             "gpu_launches": int(info["launches"] * args.steps),
             "clocks": clocks,
+            "batched": batched,
+            "serving": serving,
         }
         print(json.dumps(line))
     plan.close()

@@ -137,7 +137,8 @@ def balance_leaves(d, leaves, periodic=False):
     return list(leafset)
 
 
-def gaussian_refined_tree(d, centers, widths, rho, beta=4.0, max_level=12, periodic=False, min_level=0):
+def gaussian_refined_tree(d, centers, widths, rho, beta=4.0, max_level=12, periodic=False, min_level=0,
+                          balance=True):
     """Split a box while it is wider than rho*w_i and lies within beta*w_i of centre c_i."""
     centers = np.asarray(centers, dtype=np.float64)
     widths = np.asarray(widths, dtype=np.float64)
@@ -151,7 +152,7 @@ def gaussian_refined_tree(d, centers, widths, rho, beta=4.0, max_level=12, perio
                 return True
         return False
 
-    return refine_tree(d, should_split, max_level, periodic)
+    return refine_tree(d, should_split, max_level, periodic, balance=balance)
 
 
 # ----------------------------------------------------------------------------- nodes / densities
@@ -255,6 +256,33 @@ def config_3d_periodic_uniform(seed=0, p=8, level=5, delta=1e-3, n_gauss=16, noi
         sigma = sigma + rng.uniform(-noise, noise, size=sigma.shape)
     return Workload(f"3d-periodic-uniform-l{level}-p{p}", 3, p, delta, True, tree, sigma,
                     dict(seed=seed, centers=centers, alphas=widths ** 2, noise=noise))
+
+
+def batched_configs(seed=0, n=256, max_points=1 << 18):
+    """n independent free-space transforms: d in {2,3}, tree depth U{2..7}, p in {8,12,16},
+    delta log-U[1e-5, 1e-1], sigma a sum of 1..8 Gaussians (widths log-U[1e-2, 2e-1]).  Each
+    transform is capped at max_points (the depth is lowered until the tree fits)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        d = int(rng.choice([2, 3]))
+        depth = int(rng.integers(2, 8))
+        p = int(rng.choice([8, 12, 16]))
+        delta = float(np.exp(rng.uniform(np.log(1e-5), np.log(1e-1))))
+        ng = int(rng.integers(1, 9))
+        centers = rng.uniform(-0.4, 0.4, size=(ng, d))
+        widths = np.exp(rng.uniform(np.log(1e-2), np.log(2e-1), size=ng))
+        while True:  # size the depth on the unbalanced tree, balance only the final one
+            tree = gaussian_refined_tree(d, centers, widths, rho=1.0, beta=3.0, max_level=depth, min_level=1,
+                                         balance=False)
+            if tree.n_leaves * p ** d * 1.5 <= max_points or depth <= 1:
+                break
+            depth -= 1
+        tree = gaussian_refined_tree(d, centers, widths, rho=1.0, beta=3.0, max_level=depth, min_level=1)
+        sigma = gaussian_sum(node_positions(tree, p), centers, widths ** 2)
+        out.append(Workload(f"batch{i}-{d}d-p{p}-L{depth}", d, p, delta, False, tree, sigma,
+                            dict(seed=seed, index=i)))
+    return out
 
 
 def random_balanced_tree(d, seed, max_level=4, split_prob=0.45, periodic=False, min_level=0):
