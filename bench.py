@@ -97,6 +97,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(x, world, device):
+    """The slowest rank's value (replicas finish when the last one does)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(points_per_replica, steps, world, seconds):
+    """Weak scaling: every rank transforms its own copy of the workload each step."""
+    return world * points_per_replica * steps / seconds
+
+
 def time_steps(plan, sigma, out, steps, warmup, flush):
     """Per-step device times (ms) with an L2 flush before every step (not timed)."""
     import torch
@@ -293,12 +309,8 @@ def main():
         else:
             times = time_steps(plan, sigma, out, args.steps, args.warmup, flush)
             plan.close()
-        tot = float(times.sum())
-        if world > 1:
-            t = torch.tensor([tot], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
-        results[name] = dict(points_per_s=world * w.n_points * args.steps / (tot / 1e3),
+        tot = max_over_ranks(float(times.sum()), world, "cuda")
+        results[name] = dict(points_per_s=whole_job_rate(w.n_points, args.steps, world, tot / 1e3),
                              ms_per_step=tot / args.steps, p50_ms=float(np.percentile(times, 50)),
                              p99_ms=float(np.percentile(times, 99)), cutoff_level=info["cutoff_level"],
                              n_f=info["n_f"], launches=info["launches"])
@@ -318,11 +330,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         plan.execute_host(sh, uh)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, "cuda")
 
     # roofline of the dominant kernel (per-phase CUDA events over the timed region)
     info, prof = head["info"], head["prof"]

@@ -13,6 +13,7 @@ namespace fgt {
 struct LaunchRange {
   int first = 0, count = 0, K = 0;
   size_t smem = 0;
+  int tensor = 0;  // 1: the tensor-core (3xTF32) variant of the kernel
 };
 
 // One level of the hierarchical merge (child -> parent) or push (parent -> child).
@@ -107,6 +108,16 @@ inline size_t form3_bytes(int G, int K, int n1, size_t r, size_t c) {
   const size_t sig = (((size_t)G * K * K * K * r) + 15) & ~(size_t)15;
   return sig + c * (GK * n1 + (size_t)G * n1 * K + (size_t)G * Sc * K + Sc * G * (size_t)K * K +
                     Sc * (size_t)n1 * (GK + 1));
+}
+// Tensor-core 3D form (FP32 only): form3's layout plus the split B operands (2 x 2 n1p x (2GK+4)).
+inline size_t form4_bytes(int G, int K, int n1) {
+  const size_t GK = (size_t)G * K, n1p = ((size_t)n1 + 7) / 8 * 8;
+  // form3's Z2 rows are GK + 1 complex wide, form4's GK + 2
+  return form3_bytes(G, K, n1, 4, 8) + 4 * (size_t)n1 * 8 + 2 * (2 * n1p) * (2 * GK + 4) * 4;
+}
+// Tensor-core 3D evaluation (FP32 only): 8 output rows per CTA.
+inline size_t eval3_bytes(int K, int n1, int nh) {
+  return 8 * (8 * (size_t)n1 * n1 + 8 * (size_t)K * n1 + 2 * (size_t)K * n1 + 8 * (size_t)nh);
 }
 inline size_t eval2_bytes(int d, int K, int n1, int nh, size_t c) {
   if (d == 3) return c * ((size_t)K * n1 * n1 + (size_t)K * K * n1 + 2 * (size_t)K * n1 + (size_t)K * nh);

@@ -518,6 +518,237 @@ __global__ void __launch_bounds__(256) form3_kernel(const Block *__restrict__ bl
   }
 }
 
+// ----------------------------------------------------------------------------- 3xTF32 tensor-core helpers
+//
+// Split-precision contractions on the tensor cores: every FP32 operand x is split into
+// x_hi = tf32(x) and x_lo = tf32(x - x_hi), and a product is accumulated as
+// a_lo b_hi + a_hi b_lo + a_hi b_hi in FP32 (the a_lo b_lo term is below FP32 rounding).
+// A complex product C = A B is embedded in one real product over an interleaved (re, im)
+// contraction index: C_re = sum_k A~[k] Bre~[k], C_im = sum_k A~[k] Bim~[k] with
+// A~[2j] = Re A_j, A~[2j+1] = Im A_j, Bre~[2j] = Re B_j, Bre~[2j+1] = -Im B_j,
+// Bim~[2j] = Im B_j, Bim~[2j+1] = Re B_j.
+// Fragments of mma.m16n8k8 (TF32, A row-major, B column-major), g = lane / 4, t = lane % 4:
+// a = {A[g][t], A[g+8][t], A[g][t+4], A[g+8][t+4]}, b = {B[t][g], B[t+4][g]},
+// c = {C[g][2t], C[g][2t+1], C[g+8][2t], C[g+8][2t+1]}.
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// c += a b in 3xTF32 (small terms first)
+__device__ __forceinline__ void mma3(float (&c)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4], uint32_t bh0,
+                                     uint32_t bh1, uint32_t bl0, uint32_t bl1) {
+  mma_tf32(c, al, bh0, bh1);
+  mma_tf32(c, ah, bl0, bl1);
+  mma_tf32(c, ah, bh0, bh1);
+}
+
+// ----------------------------------------------------------------------------- tensor-core form (3D, FP32)
+//
+// Same work split as form3_kernel; stages 1-2 on the CUDA cores, stage 3 (the largest,
+// Z2 (n1 x GK) times F1 (GK x n1) per plane) on the tensor cores in 3xTF32.  F1 is embedded
+// once per CTA into split B operands Bh / Bl of 2*n1p columns (re outputs, then im outputs)
+// by 2*GK interleaved rows.
+constexpr int kNbtMax = 14;  // n-tiles of 8 columns: 2 * n1p / 8 <= 14 (n1 <= 56)
+
+__host__ __device__ inline int n1_pad8(int n1) { return (n1 + 7) / 8 * 8; }
+__host__ __device__ inline int ldz4(int GK) { return GK + 2; }       // complex row stride of Z2
+__host__ __device__ inline int ldb4(int GK) { return 2 * GK + 4; }   // uint32 row stride of Bh / Bl
+
+template <int NBT>  // n-tiles of 8 output columns held in registers (>= 2 n1p / 8)
+__global__ void __launch_bounds__(256) form4_kernel(const Block *__restrict__ blocks, const int32_t *__restrict__ gptr,
+                                                    const int64_t *__restrict__ bleaves,
+                                                    const double *__restrict__ sigma, const float2 *__restrict__ Ff,
+                                                    const float2 *__restrict__ Fh, float2 *__restrict__ phi, int k,
+                                                    int n1, int nh, int64_t slot_size) {
+  using R = float;
+  using C = float2;
+  extern __shared__ unsigned char smem_raw[];
+  const int b0 = gptr[blockIdx.x], G = gptr[blockIdx.x + 1] - b0;
+  const Block B0 = blocks[b0];
+  const int K = B0.K, nl = 1 << B0.dl;
+  const int KK = K * K, npb = KK * K, kp = k * k * k, GK = G * K, ldz = ldz4(GK), ldb = ldb4(GK);
+  const int n1p = n1_pad8(n1), NB = 2 * n1p;
+  const int s0 = blockIdx.y * kSc, ns = min(kSc, nh - s0);
+  R *sig = reinterpret_cast<R *>(smem_raw);                                   // [G][K^3]
+  const size_t sig_bytes = ((size_t)G * npb * sizeof(R) + 15) & ~(size_t)15;
+  C *F1t = reinterpret_cast<C *>(smem_raw + sig_bytes);                       // [G K][n1]
+  C *F2 = F1t + (size_t)GK * n1;                                              // [G][n1][K]
+  C *Fd = F2 + (size_t)G * n1 * K;                                            // [G][kSc][K]
+  C *Z1 = Fd + (size_t)G * kSc * K;                                           // [kSc][G][K][K]
+  C *Z2 = Z1 + (size_t)kSc * G * KK;                                          // [kSc][n1][ldz]
+  uint32_t *Bh = reinterpret_cast<uint32_t *>(Z2 + (size_t)kSc * n1 * ldz);   // [NB][ldb]
+  uint32_t *Bl = Bh + (size_t)NB * ldb;
+  for (int g = 0; g < G; ++g) {
+    const Block b = blocks[b0 + g];
+    const int64_t *lv = bleaves + b.leaf0;
+    for (int e = threadIdx.x; e < npb; e += blockDim.x) {
+      const int leafi = e / kp, node = e - leafi * kp;
+      const int o1 = leafi % nl, o2 = (leafi / nl) % nl, o3 = leafi / (nl * nl);
+      const int j1 = node % k, j2 = (node / k) % k, j3 = node / (k * k);
+      sig[(size_t)g * npb + ((o3 * k + j3) * K + (o2 * k + j2)) * K + (o1 * k + j1)] =
+          (R)__ldg(sigma + lv[leafi] * kp + node);
+    }
+    for (int e = threadIdx.x; e < K * n1; e += blockDim.x) {
+      const int J = e / n1, m = e - J * n1;
+      F1t[(size_t)(g * K + J) * n1 + m] = Ff[((int64_t)(b.mat[0] + J / k) * n1 + m) * k + J % k];
+    }
+    for (int e = threadIdx.x; e < n1 * K; e += blockDim.x) {
+      const int m = e / K, J = e - m * K;
+      F2[(size_t)g * n1 * K + e] = Ff[((int64_t)(b.mat[1] + J / k) * n1 + m) * k + J % k];
+    }
+    for (int e = threadIdx.x; e < kSc * K; e += blockDim.x) {
+      const int q = e / K, J = e - q * K;
+      Fd[((size_t)g * kSc + q) * K + J] =
+          (q < ns) ? Fh[((int64_t)(b.mat[2] + J / k) * nh + s0 + q) * k + J % k] : C{0, 0};
+    }
+  }
+  __syncthreads();
+  // split B operands from F1t: column n < n1p -> real part of output m1 = n, else imaginary part
+  for (int e = threadIdx.x; e < NB * 2 * GK; e += blockDim.x) {
+    // columns in 16-wide pairs: 8 real-part columns of modes 8 jt .. 8 jt + 7, then their 8
+    // imaginary-part columns (so a tile and its partner sit at compile-time indices 2j, 2j+1)
+    const int n = e / (2 * GK), kr = e - n * 2 * GK, J = kr >> 1, odd = kr & 1;
+    const bool im = ((n >> 3) & 1) != 0;
+    const int m1 = (n >> 4) * 8 + (n & 7);
+    float v = 0.f;
+    if (m1 < n1) {
+      const C f = F1t[(size_t)J * n1 + m1];
+      v = im ? (odd ? f.x : f.y) : (odd ? -f.y : f.x);
+    }
+    uint32_t h, l;
+    split_tf32(v, h, l);
+    Bh[(size_t)n * ldb + kr] = h;
+    Bl[(size_t)n * ldb + kr] = l;
+  }
+  // stage 1: Z1[q][g][J2][J1] = sum_J3 Fd[g][q][J3] sig[g][J3][J2][J1]
+  for (int e = threadIdx.x; e < G * KK; e += blockDim.x) {
+    const int g = e / KK, rem = e - g * KK;
+    const R *sp = sig + (size_t)g * npb + rem;
+    const C *fp = Fd + (size_t)g * kSc * K;
+    R ar[kSc], ai[kSc];
+#pragma unroll
+    for (int q = 0; q < kSc; ++q) ar[q] = ai[q] = 0;
+    for (int J3 = 0; J3 < K; ++J3) {
+      const R v = sp[(size_t)J3 * KK];
+#pragma unroll
+      for (int q = 0; q < kSc; ++q) {
+        const C f = fp[q * K + J3];
+        ar[q] = fmaf(f.x, v, ar[q]);
+        ai[q] = fmaf(f.y, v, ai[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kSc; ++q) Z1[((size_t)q * G + g) * KK + rem] = C{ar[q], ai[q]};
+  }
+  __syncthreads();
+  // stage 2 (CUDA cores, 4 x 4 tiles): Z2[q][m2][g K + J1] = sum_J2 F2[g][m2][J2] Z1[q][g][J2][J1]
+  {
+    const int tm = (n1 + 3) / 4, tj = (K + 3) / 4, ntile = ns * G * tm * tj;
+    for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
+      int r = t;
+      const int bj = r % tj; r /= tj;
+      const int bm = r % tm; r /= tm;
+      const int g = r % G, q = r / G;
+      R ar[4][4], ai[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ar[i][j] = ai[i][j] = 0;
+      const C *fp = F2 + (size_t)g * n1 * K;
+      const C *zp = Z1 + ((size_t)q * G + g) * KK;
+      for (int J2 = 0; J2 < K; ++J2) {
+        C a[4], bb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int m = bm * 4 + i;
+          a[i] = (m < n1) ? fp[m * K + J2] : C{0, 0};
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int J1 = bj * 4 + j;
+          bb[j] = (J1 < K) ? zp[J2 * K + J1] : C{0, 0};
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) cfma(ar[i][j], ai[i][j], a[i], bb[j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int m = bm * 4 + i, J1 = bj * 4 + j;
+          if (m < n1 && J1 < K) Z2[((size_t)q * n1 + m) * ldz + g * K + J1] = C{ar[i][j], ai[i][j]};
+        }
+    }
+  }
+  __syncthreads();
+  // stage 3 (tensor cores): per plane q and 16-row tile of m2, all 2*n1p output columns
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+  const int mt = (n1 + 15) / 16, nbt = NB / 8, ksteps = (2 * GK) / 8;
+  C *out = phi + (int64_t)B0.slot * slot_size;
+  for (int job = warp; job < ns * mt; job += blockDim.x >> 5) {
+    const int q = job / mt, i0 = (job - q * mt) * 16;
+    const float *za = reinterpret_cast<const float *>(Z2 + (size_t)q * n1 * ldz);  // row stride 2 ldz floats
+    float acc[NBT][4];
+#pragma unroll
+    for (int j = 0; j < NBT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    const int r0 = i0 + gq, r1 = r0 + 8;
+    for (int ks = 0; ks < ksteps; ++ks) {
+      const int k0 = ks * 8;
+      float av[4];
+      av[0] = (r0 < n1) ? za[(size_t)r0 * 2 * ldz + k0 + tq] : 0.f;
+      av[1] = (r1 < n1) ? za[(size_t)r1 * 2 * ldz + k0 + tq] : 0.f;
+      av[2] = (r0 < n1) ? za[(size_t)r0 * 2 * ldz + k0 + tq + 4] : 0.f;
+      av[3] = (r1 < n1) ? za[(size_t)r1 * 2 * ldz + k0 + tq + 4] : 0.f;
+      uint32_t ah[4], al[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) split_tf32(av[x], ah[x], al[x]);
+#pragma unroll
+      for (int j = 0; j < NBT; ++j) {
+        if (j < nbt) {
+          const size_t base = (size_t)(j * 8 + gq) * ldb + k0 + tq;
+          mma3(acc[j], ah, al, Bh[base], Bh[base + 4], Bl[base], Bl[base + 4]);
+        }
+      }
+    }
+    C *o = out + (int64_t)(s0 + q) * n1 * n1;
+#pragma unroll
+    for (int j = 0; j < NBT / 2; ++j) {
+      if (2 * j < nbt) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int m2 = h ? r1 : r0;
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const int m1 = j * 8 + 2 * tq + c;
+            if (m2 < n1 && m1 < n1) {
+              atomicAdd(&o[m2 * n1 + m1].x, acc[2 * j][2 * h + c]);
+              atomicAdd(&o[m2 * n1 + m1].y, acc[2 * j + 1][2 * h + c]);
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
 // ----------------------------------------------------------------------------- whole-block evaluation
 
 // A CTA evaluates one whole block (K <= KM nodes per axis): the anchor's incoming expansion is
@@ -621,6 +852,119 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256) eval2_kernel(const
   }
 }
 
+// ----------------------------------------------------------------------------- tensor-core evaluation (3D, FP32)
+//
+// eval2_kernel with its first contraction, Y1 (K x n1^2) = Ed (K x nh) psi (nh x n1^2), on the
+// tensor cores in 3xTF32: Ed is the A operand (16 rows, kept in registers for the whole CTA),
+// psi streams in as B fragments straight from the slot, 8 mode columns per tile.
+// A CTA evaluates rows [8 y, 8 y + 8) of one block (K <= 16), so that its shared memory
+// (Y1 for 8 rows) leaves room for two or more CTAs per SM.
+constexpr int kEvalRows = 8;
+
+template <int KST>  // k-steps of 8 over the interleaved 2 nh contraction: 2 nh <= 8 KST
+__global__ void __launch_bounds__(256) eval3_kernel(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
+                                                    const float2 *__restrict__ Ef, const float2 *__restrict__ Eh,
+                                                    const float2 *__restrict__ psi, double *__restrict__ u, int k,
+                                                    int n1, int nh, int64_t slot_size) {
+  using R = float;
+  using C = float2;
+  extern __shared__ unsigned char smem_raw[];
+  const Block blk = blocks[blockIdx.x];
+  const int K = blk.K, nl = 1 << blk.dl;
+  const int rbase = blockIdx.y * kEvalRows;
+  if (rbase >= K) return;
+  const int RB = min(kEvalRows, K - rbase);
+  const int64_t *lv = bleaves + blk.leaf0;
+  const C *ps = psi + (int64_t)blk.slot * slot_size;
+  const bool acc_u = (blk.flags & 1) != 0;
+  const int nn = n1 * n1;
+  C *Y1 = reinterpret_cast<C *>(smem_raw);            // [RB][nn]
+  C *Y2 = Y1 + (size_t)kEvalRows * nn;                 // [RB][K][n1]
+  C *E1 = Y2 + (size_t)kEvalRows * K * n1;             // [K][n1]
+  C *E2 = E1 + (size_t)K * n1;                         // [K][n1]
+  C *Ed = E2 + (size_t)K * n1;                         // [RB][nh]
+  for (int e = threadIdx.x; e < K * n1; e += blockDim.x) {
+    const int I = e / n1, m = e - I * n1;
+    E1[e] = Ef[((int64_t)(blk.mat[0] + I / k) * k + I % k) * n1 + m];
+    E2[e] = Ef[((int64_t)(blk.mat[1] + I / k) * k + I % k) * n1 + m];
+  }
+  for (int e = threadIdx.x; e < RB * nh; e += blockDim.x) {
+    const int I = rbase + e / nh, m = e % nh;
+    Ed[e] = Eh[((int64_t)(blk.mat[2] + I / k) * k + I % k) * nh + m];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, gq = lane >> 2, tq = lane & 3;
+  const int ksteps = (2 * nh + 7) / 8;
+  // A operand: row gq of this CTA's Ed rows (rows 8..15 of the tile are zero), interleaved
+  // (re, im) contraction index; kept in registers for the whole CTA
+  uint32_t ah[KST][4], al[KST][4];
+#pragma unroll
+  for (int ks = 0; ks < KST; ++ks) {
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const int kr = ks * 8 + tq + ((x & 2) ? 4 : 0), md = kr >> 1;
+      float v = 0.f;
+      if (!(x & 1) && ks < ksteps && gq < RB && md < nh) {
+        const C e = Ed[gq * nh + md];
+        v = (kr & 1) ? e.y : e.x;
+      }
+      split_tf32(v, ah[ks][x], al[ks][x]);
+    }
+  }
+  const int ntiles = (nn + 7) / 8;
+  for (int tile = warp; tile < ntiles; tile += blockDim.x >> 5) {
+    const int p = tile * 8 + gq;  // this lane's B column (mode index)
+    float cre[4] = {0.f, 0.f, 0.f, 0.f}, cim[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int ks = 0; ks < KST; ++ks) {
+      if (ks < ksteps) {
+        const int md0 = (ks * 8 + tq) >> 1, md1 = md0 + 2, odd = tq & 1;
+        const C v0 = (p < nn && md0 < nh) ? ps[(int64_t)md0 * nn + p] : C{0.f, 0.f};
+        const C v1 = (p < nn && md1 < nh) ? ps[(int64_t)md1 * nn + p] : C{0.f, 0.f};
+        uint32_t rh0, rl0, rh1, rl1, ih0, il0, ih1, il1;
+        split_tf32(odd ? -v0.y : v0.x, rh0, rl0);
+        split_tf32(odd ? -v1.y : v1.x, rh1, rl1);
+        split_tf32(odd ? v0.x : v0.y, ih0, il0);
+        split_tf32(odd ? v1.x : v1.y, ih1, il1);
+        mma3(cre, ah[ks], al[ks], rh0, rh1, rl0, rl1);
+        mma3(cim, ah[ks], al[ks], ih0, ih1, il0, il1);
+      }
+    }
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {  // rows gq (c0, c1); rows gq + 8 are padding
+      const int col = tile * 8 + 2 * tq + x;
+      if (gq < RB && col < nn) Y1[(size_t)gq * nn + col] = C{cre[x], cim[x]};
+    }
+  }
+  __syncthreads();
+  const int kp = k * k * k;
+  // Y2[r][I2][m1] = sum_m2 E2[I2][m2] Y1[r][m2][m1]
+  for (int e = threadIdx.x; e < RB * K * n1; e += blockDim.x) {
+    const int m1 = e % n1, rest = e / n1, I2 = rest % K, r = rest / K;
+    const C *ep = E2 + (size_t)I2 * n1;
+    const C *yp = Y1 + (size_t)r * nn + m1;
+    R ar = 0, ai = 0;
+    for (int m2 = 0; m2 < n1; ++m2) cfma(ar, ai, ep[m2], yp[m2 * n1]);
+    Y2[e] = C{ar, ai};
+  }
+  __syncthreads();
+  // u(rbase + r, I2, I1) = Re sum_m1 E1[I1][m1] Y2[r][I2][m1]
+  for (int e = threadIdx.x; e < RB * K * K; e += blockDim.x) {
+    const int I1 = e % K, rest = e / K, I2 = rest % K, r = rest / K, rg = rbase + r;
+    const C *ep = E1 + (size_t)I1 * n1;
+    const C *yp = Y2 + ((size_t)r * K + I2) * n1;
+    R acc = 0;
+    for (int m1 = 0; m1 < n1; ++m1) {
+      const C a = ep[m1], y = yp[m1];
+      acc = fmaf(a.x, y.x, acc);
+      acc = fmaf(-a.y, y.y, acc);
+    }
+    const int o1 = I1 / k, o2 = I2 / k, o3 = rg / k;
+    double *up = u + lv[(o3 * nl + o2) * nl + o1] * kp + ((rg - o3 * k) * k + (I2 - o2 * k)) * k + (I1 - o1 * k);
+    if (acc_u) *up += (double)acc; else *up = (double)acc;
+  }
+}
+
 // ----------------------------------------------------------------------------- diagonal shifts
 
 template <int D>
@@ -640,47 +984,74 @@ __device__ __forceinline__ void mode_index(int64_t idx, int n1, int &m1, int &m2
 // so the sum is taken axis by axis: sources arrive sorted by code (o_1 fastest), the x_1
 // factor multiplies each source, the x_2 factor each run of equal (o_2, o_3), the x_3 factor
 // each run of equal o_3 -- 27 + 9 + 3 complex products per mode in 3D instead of 27 x 3.
+// Each thread handles kGatherMpt modes, blockDim apart (coalesced), sharing the per-source
+// bookkeeping; a CTA covers kGatherMpt * blockDim consecutive modes of one anchor.
+constexpr int kGatherMpt = 4;
+
 template <int D, typename R>
-__global__ void gather_kernel(const int32_t *__restrict__ dst, const int64_t *__restrict__ ptr,
+__global__ void __launch_bounds__(256) gather_kernel(const int32_t *__restrict__ dst, const int64_t *__restrict__ ptr,
                               const GatherSrc *__restrict__ src, const typename C2T<R>::T *__restrict__ Pf,
                               const typename C2T<R>::T *__restrict__ Ph, const typename C2T<R>::T *__restrict__ phi,
                               typename C2T<R>::T *__restrict__ psi, int n1, int nh, int64_t slot_size) {
   using C = typename C2T<R>::T;
-  const int64_t idx = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
-  if (idx >= slot_size) return;
+  constexpr int MPT = kGatherMpt;
   const int i = blockIdx.x;
-  int m1, m2, m3;
-  mode_index<D>(idx, n1, m1, m2, m3);
+  const int64_t base = (int64_t)blockIdx.y * blockDim.x * MPT + threadIdx.x;
+  int m1[MPT], m2[MPT], m3[MPT];
+  bool ok[MPT];
+#pragma unroll
+  for (int j = 0; j < MPT; ++j) {
+    const int64_t idx = base + (int64_t)j * blockDim.x;
+    ok[j] = idx < slot_size;
+    mode_index<D>(ok[j] ? idx : 0, n1, m1[j], m2[j], m3[j]);
+  }
   // factors of the second and last axes (the last axis stores m >= 0 only)
-  const C* P2 = (D == 3) ? Pf : Ph;
-  const int s2 = (D == 3) ? n1 : nh, i2 = m2;
-  R a1r = 0, a1i = 0, a2r = 0, a2i = 0, a3r = 0, a3i = 0;
+  const C *P2 = (D == 3) ? Pf : Ph;
+  const int s2 = (D == 3) ? n1 : nh;
+  R a1r[MPT], a1i[MPT], a2r[MPT], a2i[MPT], a3r[MPT], a3i[MPT];
+#pragma unroll
+  for (int j = 0; j < MPT; ++j) a1r[j] = a1i[j] = a2r[j] = a2i[j] = a3r[j] = a3i[j] = 0;
   int g1 = -1, g2 = -1;  // current (o_2, o_3) run and o_3 run
   for (int64_t q = ptr[i]; q < ptr[i + 1]; ++q) {
     const GatherSrc g = src[q];
     const int run1 = g.code / 3, run2 = g.code / 9;
     if (run1 != g1) {
       if (g1 >= 0) {
-        cfma(a2r, a2i, P2[(g1 % 3) * s2 + i2], C{a1r, a1i});
-        a1r = a1i = 0;
+#pragma unroll
+        for (int j = 0; j < MPT; ++j) {
+          cfma(a2r[j], a2i[j], P2[(g1 % 3) * s2 + m2[j]], C{a1r[j], a1i[j]});
+          a1r[j] = a1i[j] = 0;
+        }
       }
       g1 = run1;
     }
     if (D == 3 && run2 != g2) {
       if (g2 >= 0) {
-        cfma(a3r, a3i, Ph[g2 * nh + m3], C{a2r, a2i});
-        a2r = a2i = 0;
+#pragma unroll
+        for (int j = 0; j < MPT; ++j) {
+          cfma(a3r[j], a3i[j], Ph[g2 * nh + m3[j]], C{a2r[j], a2i[j]});
+          a2r[j] = a2i[j] = 0;
+        }
       }
       g2 = run2;
     }
-    cfma(a1r, a1i, Pf[(g.code % 3) * n1 + m1], phi[(int64_t)g.slot * slot_size + idx]);
+    const C *ph = phi + (int64_t)g.slot * slot_size + base;
+    C v[MPT];
+#pragma unroll
+    for (int j = 0; j < MPT; ++j) v[j] = ok[j] ? ph[(int64_t)j * blockDim.x] : C{0, 0};
+#pragma unroll
+    for (int j = 0; j < MPT; ++j) cfma(a1r[j], a1i[j], Pf[(g.code % 3) * n1 + m1[j]], v[j]);
   }
-  if (g1 >= 0) cfma(a2r, a2i, P2[(g1 % 3) * s2 + i2], C{a1r, a1i});
-  if (D == 3) {
-    if (g2 >= 0) cfma(a3r, a3i, Ph[g2 * nh + m3], C{a2r, a2i});
-    psi[(int64_t)dst[i] * slot_size + idx] = C{a3r, a3i};
-  } else {
-    psi[(int64_t)dst[i] * slot_size + idx] = C{a2r, a2i};
+  C *out = psi + (int64_t)dst[i] * slot_size + base;
+#pragma unroll
+  for (int j = 0; j < MPT; ++j) {
+    if (g1 >= 0) cfma(a2r[j], a2i[j], P2[(g1 % 3) * s2 + m2[j]], C{a1r[j], a1i[j]});
+    if (D == 3) {
+      if (g2 >= 0) cfma(a3r[j], a3i[j], Ph[g2 * nh + m3[j]], C{a2r[j], a2i[j]});
+      if (ok[j]) out[(int64_t)j * blockDim.x] = C{a3r[j], a3i[j]};
+    } else {
+      if (ok[j]) out[(int64_t)j * blockDim.x] = C{a2r[j], a2i[j]};
+    }
   }
 }
 
@@ -940,7 +1311,15 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     for (const LaunchRange &lr : e.f2_ranges) {  // one launch per block size K
-      if (D == 3) {
+      if (D == 3 && lr.tensor && sizeof(R) == 4) {
+        auto fk = (n1_pad8(n1) / 4 <= 8) ? form4_kernel<8> : form4_kernel<kNbtMax>;
+        if ((err = cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) !=
+            cudaSuccess)
+          return err;
+        fk<<<dim3((unsigned)lr.count, (unsigned)((nh + kSc - 1) / kSc)), 256, lr.smem, st>>>(
+            e.f2_blocks, e.f2_gptr + lr.first, e.block_leaves, sigma, reinterpret_cast<const float2 *>(e.Ff),
+            reinterpret_cast<const float2 *>(e.Fh), reinterpret_cast<float2 *>(phi), e.k, n1, nh, ss);
+      } else if (D == 3) {
         if ((err = cudaFuncSetAttribute(form3_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)lr.smem)) != cudaSuccess)
           return err;
@@ -970,7 +1349,8 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
   mark(2, 0);
   const C *eval_src = phi;
   if (!e.fourier && e.n_gather > 0) {
-    gather_kernel<D, R><<<dim3((unsigned)e.n_gather, tiles), 256, 0, st>>>(
+    const unsigned gtiles = (unsigned)((ss + 256 * kGatherMpt - 1) / (256 * kGatherMpt));
+    gather_kernel<D, R><<<dim3((unsigned)e.n_gather, gtiles), 256, 0, st>>>(
         e.gather_dst, e.gather_ptr, e.gather_src, reinterpret_cast<const C *>(e.Pf),
         reinterpret_cast<const C *>(e.Ph), phi, psi, n1, nh, ss);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
@@ -997,6 +1377,18 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   for (const LaunchRange &lr : e.e2_ranges) {  // one launch per block size K
+    if (D == 3 && lr.tensor && sizeof(R) == 4) {
+      auto tk = (2 * nh <= 32) ? eval3_kernel<4> : eval3_kernel<8>;
+      if ((err = cudaFuncSetAttribute(tk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) != cudaSuccess)
+        return err;
+      tk<<<dim3((unsigned)lr.count, (unsigned)((lr.K + kEvalRows - 1) / kEvalRows)), 256, lr.smem, st>>>(
+          e.e2_blocks + lr.first, e.block_leaves,
+                                                   reinterpret_cast<const float2 *>(e.Ef),
+                                                   reinterpret_cast<const float2 *>(e.Eh),
+                                                   reinterpret_cast<const float2 *>(eval_src), u, e.k, n1, nh, ss);
+      if ((err = cudaGetLastError()) != cudaSuccess) return err;
+      continue;
+    }
     auto kern = lr.K <= 8 ? eval2_kernel<D, R, 8> : eval2_kernel<D, R, 16>;
     if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) !=
         cudaSuccess)

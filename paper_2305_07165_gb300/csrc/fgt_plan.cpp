@@ -17,6 +17,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -109,6 +110,7 @@ struct fgt_plan {
   size_t work_bytes = 0;
   double *stage = nullptr;  // host-path staging [2][n_leaves k^d]
   bool host_only = false;   // planned without a device (inspection only)
+  bool tc_eval = false;     // split precision: evaluate with the tensor-core kernel (FGT_TC_EVAL=1)
   DevPack host_pack;        // host copy of the uploaded lists and tables (kept for host-only plans)
   fgt::ExecDesc ex;
   fgt_plan_info info{};
@@ -433,7 +435,8 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   // ---- smem-limited block size
   const int smax = upload ? fgt::max_dynamic_smem() : 232448;  // sm_103 opt-in limit without a device
   int dlcap = 0;
-  while (((2 << dlcap) * k) <= 64) ++dlcap;  // K = 2^dl k <= 64
+  // K = 2^dl k <= 64 (blocks of K > 16 use the per-plane form and per-row evaluation kernels)
+  while (((2 << dlcap) * k) <= 64) ++dlcap;
   auto fits = [&](int dl) {
     const int K = (1 << dl) * k;
     return fgt::form_smem_bytes(d, K, n1, P.prec) <= (size_t)smax &&
@@ -542,7 +545,16 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
     const size_t rsz = P.prec ? sizeof(float) : sizeof(double), csz = sizeof(C);
     const size_t three_per_sm = 72 * 1024;
     // 3D uses the register-tiled kernel (planes in chunks of 4), 2D the plain grouped one
+    // split precision in 3D: the last contraction of the form and the first of the evaluation
+    // run on the tensor cores (3xTF32) when the shapes fit the kernels' register tiles
+    auto tensor_form = [&](int K) {
+      return d == 3 && P.prec == FGT_PREC_SPLIT && K % 4 == 0 && 2 * ((n1 + 7) / 8 * 8) / 8 <= 14;
+    };
+    // the tensor-core evaluation kernel measured slower than the whole-block CUDA-core one on
+    // GB300 (its stages 2-3 dominate once stage 1 is on the tensor cores), so it is off by default
+    const bool tensor_eval = d == 3 && P.prec == FGT_PREC_SPLIT && nh <= 32 && P.tc_eval;
     auto gbytes = [&](int g, int K) {
+      if (tensor_form(K)) return fgt::form4_bytes(g, K, n1);
       return d == 3 ? fgt::form3_bytes(g, K, n1, rsz, csz) : fgt::form2_bytes(d, g, K, n1, nh, rsz, csz);
     };
     auto gmax = [&](int K) {
@@ -584,11 +596,12 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
       lr.count = (int)f2ptr.size() - 1 - first_group;
       lr.K = K;
       lr.smem = gbytes(G, K);
+      lr.tensor = tensor_form(K) ? 1 : 0;
       ex.f2_ranges.push_back(lr);
     }
     // evaluation: whole-block kernel for K <= 16 when it fits, one launch per K
     for (const fgt::Block &b : sorted) {
-      const size_t eb = fgt::eval2_bytes(d, b.K, n1, nh, csz);
+      const size_t eb = tensor_eval ? fgt::eval3_bytes(b.K, n1, nh) : fgt::eval2_bytes(d, b.K, n1, nh, csz);
       if (b.K <= 16 && eb <= (size_t)smax) {
         if (ex.e2_ranges.empty() || ex.e2_ranges.back().K != b.K) {
           fgt::LaunchRange lr;
@@ -596,6 +609,7 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
           lr.count = 0;
           lr.K = b.K;
           lr.smem = eb;
+          lr.tensor = tensor_eval ? 1 : 0;
           ex.e2_ranges.push_back(lr);
         }
         e2.push_back(b);
@@ -946,6 +960,10 @@ fgt_status create_impl(int d, double delta, double tol, double eps_pw, int bc, i
   if (!P) return fail(FGT_ERR_OOM, "host allocation");
   P->d = d; P->k = tree->k; P->bc = bc; P->prec = prec; P->mode = mode;
   P->delta = delta; P->tol = tol; P->eps_pw = eps_pw > 0 ? eps_pw : tol;
+  {
+    const char *tc = std::getenv("FGT_TC_EVAL");
+    P->tc_eval = tc && tc[0] == '1';
+  }
   P->n_leaves = tree->n_leaves;
   P->leaf_level.assign(tree->leaf_level, tree->leaf_level + tree->n_leaves);
   P->leaf_coord.assign(tree->leaf_coord, tree->leaf_coord + tree->n_leaves * d);

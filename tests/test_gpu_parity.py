@@ -142,3 +142,12 @@ def test_invalid_tree_rejected_on_gpu_plan():
     with pytest.raises(F.FGTError) as e:
         F.Plan(2, 4, 1e-3, 1e-6, lev, crd)
     assert e.value.status == 2
+
+
+def test_split_precision_tensor_core_evaluation(monkeypatch):
+    """The tensor-core (3xTF32) evaluation kernel, off by default, selected with FGT_TC_EVAL=1."""
+    monkeypatch.setenv("FGT_TC_EVAL", "1")
+    tr = W.random_balanced_tree(3, 21, max_level=4, min_level=2, split_prob=0.2)
+    sig = W.random_sigma(tr, 8, 16)
+    check(3, 8, 1e-3, 1e-6, tr, sig, prec=1)
+    check(3, 8, 1e-2, 1e-6, tr, sig, prec=1)
