@@ -97,6 +97,24 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def roofline_of(info, prof, nprof, prec):
+    """Dominant phase of one form (per-phase CUDA events over the timed region) against the
+    ALU peak it is bound by: algorithmic flops of the phase / its average time per step."""
+    phase_flops = {"form": info["form_flops"], "evaluate": info["eval_flops"], "gather": info["gather_flops"],
+                   "near": info["direct_flops"], "merge": 0, "push": 0}
+    n = max(nprof, 1)
+    dom = max(prof, key=lambda k: prof[k])
+    ms = prof[dom] / n
+    achieved = phase_flops[dom] / (ms / 1e3) / 1e12
+    fp32 = prec == 1 and dom in ("form", "evaluate", "gather")
+    peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
+    return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if fp32 else
+                            "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"),
+            "phase_ms_per_step": {k: v / n for k, v in prof.items()}}
+
+
 def max_over_ranks(x, world, device):
     """The slowest rank's value (replicas finish when the last one does)."""
     if world <= 1:
@@ -294,26 +312,30 @@ def main():
         plan = F.Plan(w.d, w.p, w.delta, tol, w.tree.level, w.tree.coord, bc=int(w.periodic), prec=prec)
         info = plan.info()
         is_head = head is None
+        plan.set_profiling(True)
         if is_head:
-            plan.set_profiling(True)
             with ClockSampler(local) as cs:
                 if world > 1:
                     dist.barrier()
                 torch.cuda.synchronize()
                 times = time_steps(plan, sigma, out, args.steps, args.warmup, flush)
                 torch.cuda.synchronize()
-            prof, nprof = plan.read_profile()
-            plan.set_profiling(False)
             clocks = cs.summary()
-            head = dict(name=name, plan=plan, info=info, prof=prof, nprof=nprof, times=times, tol=tol, prec=prec)
         else:
             times = time_steps(plan, sigma, out, args.steps, args.warmup, flush)
+        prof, nprof = plan.read_profile()
+        plan.set_profiling(False)
+        form_roofline = roofline_of(info, prof, nprof, prec)
+        if is_head:
+            head = dict(name=name, plan=plan, info=info, prof=prof, nprof=nprof, times=times, tol=tol, prec=prec,
+                        roofline=form_roofline)
+        else:
             plan.close()
         tot = max_over_ranks(float(times.sum()), world, "cuda")
         results[name] = dict(points_per_s=whole_job_rate(w.n_points, args.steps, world, tot / 1e3),
                              ms_per_step=tot / args.steps, p50_ms=float(np.percentile(times, 50)),
                              p99_ms=float(np.percentile(times, 99)), cutoff_level=info["cutoff_level"],
-                             n_f=info["n_f"], launches=info["launches"])
+                             n_f=info["n_f"], launches=info["launches"], roofline=form_roofline)
 
     batched = serving = None
     if not args.no_batch and rank == 0:
@@ -332,20 +354,7 @@ def main():
         plan.execute_host(sh, uh)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, "cuda")
 
-    # roofline of the dominant kernel (per-phase CUDA events over the timed region)
-    info, prof = head["info"], head["prof"]
-    phase_flops = {"form": info["form_flops"], "evaluate": info["eval_flops"], "gather": info["gather_flops"],
-                   "near": info["direct_flops"], "merge": 0, "push": 0}
-    dom = max(prof, key=lambda k: prof[k])
-    per_launch_ms = prof[dom] / max(head["nprof"], 1)
-    achieved = phase_flops[dom] / (per_launch_ms / 1e3) / 1e12
-    peak = FP32_PEAK_TFLOPS if head["prec"] == F.PREC_SPLIT else FP64_PEAK_TFLOPS
-    if dom == "near":
-        peak = FP64_PEAK_TFLOPS
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": "derived: 152 SMs x lanes x 2 x 2.07 GHz (FP32 CUDA cores for split, FP64 units otherwise)",
-                "phase_ms_per_step": {k: v / max(head["nprof"], 1) for k, v in prof.items()}}
+    roofline = head["roofline"]
 
     line = None
     if rank == 0:

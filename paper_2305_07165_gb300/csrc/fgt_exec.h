@@ -76,6 +76,10 @@ struct ExecDesc {
   const NearPair *near_pairs = nullptr;  // flattened D-list, one CTA per pair
   int64_t n_near_pairs = 0;
   int64_t n_points = 0;                  // n_leaves * k^d
+  int zero_u = 0;                        // clear u first (near field or accumulating evaluation)
+  cudaStream_t aux = nullptr;            // second stream for the near field (nullptr: same stream)
+  int near_phase = 0;                    // phase the near field is forked before (0 form, 2 gather, 4 evaluate)
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 constexpr int kPhases = 6;

@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(256) eval_kernel(const Block *__restrict__ blo
         acc = fma(-e.y, y.y, acc);
       }
       double *up = u + lv[(od * nl + o2) * nl + o1] * k3 + (td * k + t2) * k + t1;
-      if (acc_u) *up += (double)acc; else *up = (double)acc;
+      if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc;
     }
   } else {
     const int kk = k * k;
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(256) eval_kernel(const Block *__restrict__ blo
         acc = fma(-e.y, y.y, acc);
       }
       double *up = u + lv[od * nl + o1] * kk + td * k + t1;
-      if (acc_u) *up += (double)acc; else *up = (double)acc;
+      if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc;
     }
   }
 }
@@ -832,7 +832,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256) eval2_kernel(const
       }
       const int o1 = I1 / k, o2 = I2 / k, o3 = r / k;
       double *up = u + lv[(o3 * nl + o2) * nl + o1] * kp + ((r - o3 * k) * k + (I2 - o2 * k)) * k + (I1 - o1 * k);
-      if (acc_u) *up += (double)acc; else *up = (double)acc;
+      if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc;
     }
   } else {
     for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
@@ -847,7 +847,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256) eval2_kernel(const
       }
       const int o1 = I1 / k, o2 = r / k;
       double *up = u + lv[o2 * nl + o1] * kp + (r - o2 * k) * k + (I1 - o1 * k);
-      if (acc_u) *up += (double)acc; else *up = (double)acc;
+      if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc;
     }
   }
 }
@@ -961,7 +961,7 @@ __global__ void __launch_bounds__(256) eval3_kernel(const Block *__restrict__ bl
     }
     const int o1 = I1 / k, o2 = I2 / k, o3 = rg / k;
     double *up = u + lv[(o3 * nl + o2) * nl + o1] * kp + ((rg - o3 * k) * k + (I2 - o2 * k)) * k + (I1 - o1 * k);
-    if (acc_u) *up += (double)acc; else *up = (double)acc;
+    if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc;
   }
 }
 
@@ -1293,10 +1293,37 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
     if (e.events) cudaEventRecord(e.events[2 * ph + end], st);
   };
   mark(0, 0);
-  if (e.n_near_pairs > 0) {
-    // the near field adds into u with atomics: clear it first (evaluation then stores its leaves)
+  if (e.zero_u) {
+    // the near field (and the evaluation of cutoff-level leaves) add into u: clear it first
     if ((err = cudaMemsetAsync(u, 0, sizeof(double) * (size_t)e.n_points, st)) != cudaSuccess) return err;
   }
+  // near field: D-list pairs, FP64; independent of the plane-wave phases, so it runs on the
+  // plan's second stream (forked after the clear of u, joined before returning) when one exists
+  auto launch_near = [&](cudaStream_t ns) -> cudaError_t {
+    const int np = D == 3 ? e.k * e.k * e.k : e.k * e.k;
+    const size_t nsm = sizeof(double) * (3 * (size_t)np + (size_t)D * e.k * e.k);
+    cudaError_t r = cudaFuncSetAttribute(near2_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nsm);
+    if (r != cudaSuccess) return r;
+    if (e.events) cudaEventRecord(e.events[10], ns);
+    near2_kernel<D><<<(unsigned)e.n_near_pairs, 128, nsm, ns>>>(e.near_pairs, e.near_tab, sigma, u, e.k);
+    r = cudaGetLastError();
+    if (e.events) cudaEventRecord(e.events[11], ns);
+    return r;
+  };
+  const bool near_aside = e.n_near_pairs > 0 && e.aux != nullptr;
+  if (!(e.n_near_pairs > 0) && e.events) {
+    cudaEventRecord(e.events[10], st);
+    cudaEventRecord(e.events[11], st);
+  }
+  auto fork_near = [&](int phase) -> cudaError_t {
+    if (!near_aside || e.near_phase != phase) return cudaSuccess;
+    cudaError_t r;
+    if ((r = cudaEventRecord(e.fork, st)) != cudaSuccess) return r;
+    if ((r = cudaStreamWaitEvent(e.aux, e.fork, 0)) != cudaSuccess) return r;
+    if ((r = launch_near(e.aux)) != cudaSuccess) return r;
+    return cudaEventRecord(e.join, e.aux);
+  };
+  if ((err = fork_near(0)) != cudaSuccess) return err;
   if (e.n_blocks > 0) {
     // outgoing expansions: zero, then every block adds its contribution
     if ((err = cudaMemsetAsync(phi, 0, sizeof(C) * ss * e.n_phi_slots, st)) != cudaSuccess) return err;
@@ -1346,6 +1373,7 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   mark(1, 1);
+  if ((err = fork_near(2)) != cudaSuccess) return err;
   mark(2, 0);
   const C *eval_src = phi;
   if (!e.fourier && e.n_gather > 0) {
@@ -1365,6 +1393,7 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   mark(3, 1);
+  if ((err = fork_near(4)) != cudaSuccess) return err;
   mark(4, 0);
   if (e.n_e1 > 0) {
     const size_t esm = eval_smem_bytes(D, e.Kmax_e1, n1, sizeof(R) == 4);
@@ -1399,17 +1428,10 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   mark(4, 1);
-  mark(5, 0);
-  if (e.n_near_pairs > 0) {
-    const int np = D == 3 ? e.k * e.k * e.k : e.k * e.k;
-    const size_t nsm = sizeof(double) * (3 * (size_t)np + (size_t)D * e.k * e.k);
-    if ((err = cudaFuncSetAttribute(near2_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nsm)) !=
-        cudaSuccess)
-      return err;
-    near2_kernel<D><<<(unsigned)e.n_near_pairs, 128, nsm, st>>>(e.near_pairs, e.near_tab, sigma, u, e.k);
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  if (e.n_near_pairs > 0 && !near_aside) {
+    if ((err = launch_near(st)) != cudaSuccess) return err;
   }
-  mark(5, 1);
+  if (near_aside && (err = cudaStreamWaitEvent(st, e.join, 0)) != cudaSuccess) return err;
   return cudaSuccess;
 }
 

@@ -111,6 +111,8 @@ struct fgt_plan {
   double *stage = nullptr;  // host-path staging [2][n_leaves k^d]
   bool host_only = false;   // planned without a device (inspection only)
   bool tc_eval = false;     // split precision: evaluate with the tensor-core kernel (FGT_TC_EVAL=1)
+  cudaStream_t aux = nullptr;              // near-field stream
+  cudaEvent_t fork = nullptr, join = nullptr;
   DevPack host_pack;        // host copy of the uploaded lists and tables (kept for host-only plans)
   fgt::ExecDesc ex;
   fgt_plan_info info{};
@@ -128,6 +130,9 @@ struct fgt_plan {
   int np() const { return d == 3 ? k * k * k : k * k; }
   ~fgt_plan() {
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (aux) cudaStreamDestroy(aux);
     if (dev) cudaFree(dev);
     if (work) cudaFree(work);
     if (stage) cudaFree(stage);
@@ -491,8 +496,10 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
     blk.slot = A.slot;
     blk.dl = dl;
     blk.K = (1 << dl) * k;
-    blk.flags = 0;
     const int l = B.level + dl, nl = 1 << dl;
+    // leaves at the cutoff level may also receive near-field terms, which run concurrently on a
+    // second stream: their evaluation adds atomically into the cleared u instead of storing
+    blk.flags = (l == P.lc && !P.fourier) ? 1 : 0;
     for (int a = 0; a < d; ++a) {
       const int obase = (B.c[a] << dl) - (A.c[a] << (l - A.level));
       blk.mat[a] = get_mat(l, A.level, obase, dl, 0.0);
@@ -829,6 +836,11 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
       npairs.push_back(pr);
     }
   ex.n_near_pairs = (int64_t)npairs.size();
+  {
+    bool acc_blocks = false;
+    for (const fgt::Block &b : blocks) acc_blocks = acc_blocks || (b.flags & 1);
+    ex.zero_u = (ex.n_near_pairs > 0 || acc_blocks) ? 1 : 0;
+  }
   ex.n_points = P.n_leaves * (int64_t)P.np();
 
   // ---- upload
@@ -930,6 +942,20 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
     st.qh = at(std::get<2>(step_off[si]));
     st.n = std::get<3>(step_off[si]);
     ex.push.push_back(st);
+  }
+  if (ex.n_near_pairs > 0) {  // second stream for the near field, made once per plan
+    if (!P.aux) {
+      e = cudaStreamCreateWithFlags(&P.aux, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P.join, cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_fail(e, "near-field stream");
+    }
+    ex.aux = P.aux;
+    // forked before the gather: the near field's FP64 work then overlaps the L2-bound gather and
+    // the evaluation rather than the form, which measured fastest of the three fork points
+    ex.near_phase = 2;
+    ex.fork = P.fork;
+    ex.join = P.join;
   }
   P.ex = ex;
 

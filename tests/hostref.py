@@ -174,7 +174,10 @@ class HostState:
 
     def transform(self, sigma):
         sigma = np.asarray(sigma, dtype=np.float64).reshape(-1, self.k ** self.d)
-        u = np.full(sigma.shape, np.nan)
+        # the device clears u first when the near field or a cutoff-level block adds into it;
+        # otherwise every entry must be stored by exactly one writer (NaN shows a missed one)
+        zero_u = len(self.ntgt) > 0 or any(int(b["flags"]) & 1 for b in self.blocks)
+        u = np.zeros(sigma.shape) if zero_u else np.full(sigma.shape, np.nan)
         if len(self.blocks):
             phi = self.merge_up(self.form(sigma))
             psi = self.push_down(self.gather(phi))
