@@ -14,6 +14,7 @@ struct LaunchRange {
   int first = 0, count = 0, K = 0;
   size_t smem = 0;
   int tensor = 0;  // 1: the tensor-core (3xTF32) variant of the kernel
+  int big = 0;     // 1: single blocks of K > 16, sigma streamed from global memory in stage 1
 };
 
 // One level of the hierarchical merge (child -> parent) or push (parent -> child).
@@ -50,6 +51,11 @@ struct ExecDesc {
   int64_t n_e2 = 0;
   std::vector<LaunchRange> e2_ranges;  // blocks by K
   const int64_t *block_leaves = nullptr;
+  // split precision, 3D: sigma converted to FP32 once per transform, block by block (block b's
+  // K^3 values at sigp + b.leaf0 k^3, in (J3, J2, J1) order); nullptr: kernels read sigma itself
+  float *sigp = nullptr;
+  const int32_t *pack_block = nullptr;  // index into blocks of every block_leaves entry
+  int64_t n_pack = 0;                   // block_leaves entries
   const void *Ff = nullptr, *Fh = nullptr, *Ef = nullptr, *Eh = nullptr;
 
   // out->in gather at the cutoff level
@@ -118,6 +124,10 @@ inline size_t form4_bytes(int G, int K, int n1) {
   const size_t GK = (size_t)G * K, n1p = ((size_t)n1 + 7) / 8 * 8;
   // form3's Z2 rows are GK + 1 complex wide, form4's GK + 2
   return form3_bytes(G, K, n1, 4, 8) + 4 * (size_t)n1 * 8 + 2 * (2 * n1p) * (2 * GK + 4) * 4;
+}
+// form4 over one block of K > 16 whose sigma is read from global memory in stage 1: no sigma tile.
+inline size_t form4b_bytes(int K, int n1) {
+  return form4_bytes(1, K, n1) - ((((size_t)K * K * K * 4) + 15) & ~(size_t)15);
 }
 // Tensor-core 3D evaluation (FP32 only): 8 output rows per CTA.
 inline size_t eval3_bytes(int K, int n1, int nh) {

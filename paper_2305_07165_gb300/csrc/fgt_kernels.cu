@@ -558,6 +558,29 @@ __device__ __forceinline__ void mma3(float (&c)[4], const uint32_t (&ah)[4], con
   mma_tf32(c, ah, bh0, bh1);
 }
 
+// ----------------------------------------------------------------------------- packed FP32 sigma (3D)
+//
+// One CTA per block_leaves entry: the leaf's k^3 values, converted to FP32, go to their place in
+// the block's (J3, J2, J1) tile at sigp + block.leaf0 k^3, so that every form CTA that needs
+// the block reads it as one contiguous run.
+__global__ void __launch_bounds__(256) sigma_pack_kernel(const Block *__restrict__ blocks,
+                                                         const int32_t *__restrict__ pack_block,
+                                                         const int64_t *__restrict__ bleaves,
+                                                         const double *__restrict__ sigma, float *__restrict__ sigp,
+                                                         int k) {
+  const int64_t i = blockIdx.x;
+  const Block b = blocks[pack_block[i]];
+  const int kp = k * k * k, nl = 1 << b.dl, K = b.K;
+  const int leafi = (int)(i - b.leaf0);
+  const int o1 = leafi % nl, o2 = (leafi / nl) % nl, o3 = leafi / (nl * nl);
+  const double *src = sigma + bleaves[i] * kp;
+  float *dst = sigp + b.leaf0 * kp;
+  for (int node = threadIdx.x; node < kp; node += blockDim.x) {
+    const int j1 = node % k, j2 = (node / k) % k, j3 = node / (k * k);
+    dst[((o3 * k + j3) * K + (o2 * k + j2)) * K + (o1 * k + j1)] = (float)__ldg(src + node);
+  }
+}
+
 // ----------------------------------------------------------------------------- tensor-core form (3D, FP32)
 //
 // Same work split as form3_kernel; stages 1-2 on the CUDA cores, stage 3 (the largest,
@@ -570,24 +593,26 @@ __host__ __device__ inline int n1_pad8(int n1) { return (n1 + 7) / 8 * 8; }
 __host__ __device__ inline int ldz4(int GK) { return GK + 2; }       // complex row stride of Z2
 __host__ __device__ inline int ldb4(int GK) { return 2 * GK + 4; }   // uint32 row stride of Bh / Bl
 
-template <int NBT>  // n-tiles of 8 output columns held in registers (>= 2 n1p / 8)
+template <int NBT, bool BIG>  // NBT: n-tiles of 8 output columns held in registers (>= 2 n1p / 8)
 __global__ void __launch_bounds__(256) form4_kernel(const Block *__restrict__ blocks, const int32_t *__restrict__ gptr,
                                                     const int64_t *__restrict__ bleaves,
-                                                    const double *__restrict__ sigma, const float2 *__restrict__ Ff,
-                                                    const float2 *__restrict__ Fh, float2 *__restrict__ phi, int k,
-                                                    int n1, int nh, int64_t slot_size) {
+                                                    const double *__restrict__ sigma, const float *__restrict__ sigp,
+                                                    const float2 *__restrict__ Ff, const float2 *__restrict__ Fh,
+                                                    float2 *__restrict__ phi, int k, int n1, int nh,
+                                                    int64_t slot_size) {
   using R = float;
   using C = float2;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem4[];
   const int b0 = gptr[blockIdx.x], G = gptr[blockIdx.x + 1] - b0;
   const Block B0 = blocks[b0];
   const int K = B0.K, nl = 1 << B0.dl;
   const int KK = K * K, npb = KK * K, kp = k * k * k, GK = G * K, ldz = ldz4(GK), ldb = ldb4(GK);
   const int n1p = n1_pad8(n1), NB = 2 * n1p;
   const int s0 = blockIdx.y * kSc, ns = min(kSc, nh - s0);
-  R *sig = reinterpret_cast<R *>(smem_raw);                                   // [G][K^3]
-  const size_t sig_bytes = ((size_t)G * npb * sizeof(R) + 15) & ~(size_t)15;
-  C *F1t = reinterpret_cast<C *>(smem_raw + sig_bytes);                       // [G K][n1]
+  // BIG (one block of K > 16): no sigma tile, stage 1 streams it from global memory
+  R *sig = reinterpret_cast<R *>(smem4);                                      // [G][K^3]
+  const size_t sig_bytes = BIG ? 0 : ((size_t)G * npb * sizeof(R) + 15) & ~(size_t)15;
+  C *F1t = reinterpret_cast<C *>(smem4 + sig_bytes);                          // [G K][n1]
   C *F2 = F1t + (size_t)GK * n1;                                              // [G][n1][K]
   C *Fd = F2 + (size_t)G * n1 * K;                                            // [G][kSc][K]
   C *Z1 = Fd + (size_t)G * kSc * K;                                           // [kSc][G][K][K]
@@ -596,13 +621,27 @@ __global__ void __launch_bounds__(256) form4_kernel(const Block *__restrict__ bl
   uint32_t *Bl = Bh + (size_t)NB * ldb;
   for (int g = 0; g < G; ++g) {
     const Block b = blocks[b0 + g];
-    const int64_t *lv = bleaves + b.leaf0;
-    for (int e = threadIdx.x; e < npb; e += blockDim.x) {
-      const int leafi = e / kp, node = e - leafi * kp;
-      const int o1 = leafi % nl, o2 = (leafi / nl) % nl, o3 = leafi / (nl * nl);
-      const int j1 = node % k, j2 = (node / k) % k, j3 = node / (k * k);
-      sig[(size_t)g * npb + ((o3 * k + j3) * K + (o2 * k + j2)) * K + (o1 * k + j1)] =
-          (R)__ldg(sigma + lv[leafi] * kp + node);
+    if (!BIG) {
+      if (sigp != nullptr) {
+        // packed FP32 sigma: the block's K^3 values are contiguous and already in tile order
+        const float *src = sigp + b.leaf0 * kp;
+        if ((kp & 3) == 0) {
+          const float4 *s4 = reinterpret_cast<const float4 *>(src);
+          float4 *d4 = reinterpret_cast<float4 *>(sig + (size_t)g * npb);
+          for (int e = threadIdx.x; e < (npb >> 2); e += blockDim.x) d4[e] = __ldg(s4 + e);
+        } else {
+          for (int e = threadIdx.x; e < npb; e += blockDim.x) sig[(size_t)g * npb + e] = __ldg(src + e);
+        }
+      } else {
+        const int64_t *lv = bleaves + b.leaf0;
+        for (int e = threadIdx.x; e < npb; e += blockDim.x) {
+          const int leafi = e / kp, node = e - leafi * kp;
+          const int o1 = leafi % nl, o2 = (leafi / nl) % nl, o3 = leafi / (nl * nl);
+          const int j1 = node % k, j2 = (node / k) % k, j3 = node / (k * k);
+          sig[(size_t)g * npb + ((o3 * k + j3) * K + (o2 * k + j2)) * K + (o1 * k + j1)] =
+              (R)__ldg(sigma + lv[leafi] * kp + node);
+        }
+      }
     }
     for (int e = threadIdx.x; e < K * n1; e += blockDim.x) {
       const int J = e / n1, m = e - J * n1;
@@ -637,24 +676,64 @@ __global__ void __launch_bounds__(256) form4_kernel(const Block *__restrict__ bl
     Bl[(size_t)n * ldb + kr] = l;
   }
   // stage 1: Z1[q][g][J2][J1] = sum_J3 Fd[g][q][J3] sig[g][J3][J2][J1]
-  for (int e = threadIdx.x; e < G * KK; e += blockDim.x) {
-    const int g = e / KK, rem = e - g * KK;
-    const R *sp = sig + (size_t)g * npb + rem;
-    const C *fp = Fd + (size_t)g * kSc * K;
-    R ar[kSc], ai[kSc];
+  if (BIG) {
+    // one block, sigma from global memory: packed (coalesced along J1), else leaf by leaf
+    const int64_t *lv = bleaves + B0.leaf0;
+    for (int rem = threadIdx.x; rem < KK; rem += blockDim.x) {
+      R ar[kSc], ai[kSc];
 #pragma unroll
-    for (int q = 0; q < kSc; ++q) ar[q] = ai[q] = 0;
-    for (int J3 = 0; J3 < K; ++J3) {
-      const R v = sp[(size_t)J3 * KK];
+      for (int q = 0; q < kSc; ++q) ar[q] = ai[q] = 0;
+      if (sigp != nullptr) {
+        const float *sp = sigp + B0.leaf0 * kp + rem;
+#pragma unroll 4
+        for (int J3 = 0; J3 < K; ++J3) {
+          const R v = __ldg(sp + (size_t)J3 * KK);
 #pragma unroll
-      for (int q = 0; q < kSc; ++q) {
-        const C f = fp[q * K + J3];
-        ar[q] = fmaf(f.x, v, ar[q]);
-        ai[q] = fmaf(f.y, v, ai[q]);
+          for (int q = 0; q < kSc; ++q) {
+            const C f = Fd[q * K + J3];
+            ar[q] = fmaf(f.x, v, ar[q]);
+            ai[q] = fmaf(f.y, v, ai[q]);
+          }
+        }
+      } else {
+        const int J2 = rem / K, J1 = rem - J2 * K;
+        const int o2 = J2 / k, j2 = J2 - o2 * k, o1 = J1 / k, j1 = J1 - o1 * k;
+        for (int o3 = 0; o3 < nl; ++o3) {
+          const double *sp = sigma + lv[(o3 * nl + o2) * nl + o1] * kp + j2 * k + j1;
+          for (int j3 = 0; j3 < k; ++j3) {
+            const R v = (R)__ldg(sp + j3 * k * k);
+#pragma unroll
+            for (int q = 0; q < kSc; ++q) {
+              const C f = Fd[q * K + o3 * k + j3];
+              ar[q] = fmaf(f.x, v, ar[q]);
+              ai[q] = fmaf(f.y, v, ai[q]);
+            }
+          }
+        }
       }
-    }
 #pragma unroll
-    for (int q = 0; q < kSc; ++q) Z1[((size_t)q * G + g) * KK + rem] = C{ar[q], ai[q]};
+      for (int q = 0; q < kSc; ++q) Z1[(size_t)q * KK + rem] = C{ar[q], ai[q]};
+    }
+  } else {
+    for (int e = threadIdx.x; e < G * KK; e += blockDim.x) {
+      const int g = e / KK, rem = e - g * KK;
+      const R *sp = sig + (size_t)g * npb + rem;
+      const C *fp = Fd + (size_t)g * kSc * K;
+      R ar[kSc], ai[kSc];
+#pragma unroll
+      for (int q = 0; q < kSc; ++q) ar[q] = ai[q] = 0;
+      for (int J3 = 0; J3 < K; ++J3) {
+        const R v = sp[(size_t)J3 * KK];
+#pragma unroll
+        for (int q = 0; q < kSc; ++q) {
+          const C f = fp[q * K + J3];
+          ar[q] = fmaf(f.x, v, ar[q]);
+          ai[q] = fmaf(f.y, v, ai[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kSc; ++q) Z1[((size_t)q * G + g) * KK + rem] = C{ar[q], ai[q]};
+    }
   }
   __syncthreads();
   // stage 2 (CUDA cores, 4 x 4 tiles): Z2[q][m2][g K + J1] = sum_J2 F2[g][m2][J2] Z1[q][g][J2][J1]
@@ -738,10 +817,7 @@ __global__ void __launch_bounds__(256) form4_kernel(const Block *__restrict__ bl
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             const int m1 = j * 8 + 2 * tq + c;
-            if (m2 < n1 && m1 < n1) {
-              atomicAdd(&o[m2 * n1 + m1].x, acc[2 * j][2 * h + c]);
-              atomicAdd(&o[m2 * n1 + m1].y, acc[2 * j + 1][2 * h + c]);
-            }
+            if (m2 < n1 && m1 < n1) atomicAdd(&o[m2 * n1 + m1], make_float2(acc[2 * j][2 * h + c], acc[2 * j + 1][2 * h + c]));
           }
         }
       }
@@ -1327,6 +1403,11 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
   if (e.n_blocks > 0) {
     // outgoing expansions: zero, then every block adds its contribution
     if ((err = cudaMemsetAsync(phi, 0, sizeof(C) * ss * e.n_phi_slots, st)) != cudaSuccess) return err;
+    if (D == 3 && sizeof(R) == 4 && e.sigp != nullptr && e.n_pack > 0) {
+      sigma_pack_kernel<<<(unsigned)e.n_pack, 256, 0, st>>>(e.blocks, e.pack_block, e.block_leaves, sigma, e.sigp,
+                                                            e.k);
+      if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
     if (e.n_f1 > 0) {
       const size_t fsm = form_smem_bytes(D, e.Kmax_f1, n1, sizeof(R) == 4);
       if ((err = cudaFuncSetAttribute(form_kernel<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm)) !=
@@ -1339,12 +1420,14 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
     }
     for (const LaunchRange &lr : e.f2_ranges) {  // one launch per block size K
       if (D == 3 && lr.tensor && sizeof(R) == 4) {
-        auto fk = (n1_pad8(n1) / 4 <= 8) ? form4_kernel<8> : form4_kernel<kNbtMax>;
+        const bool small_n = n1_pad8(n1) / 4 <= 8;
+        auto fk = lr.big ? (small_n ? form4_kernel<8, true> : form4_kernel<kNbtMax, true>)
+                         : (small_n ? form4_kernel<8, false> : form4_kernel<kNbtMax, false>);
         if ((err = cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) !=
             cudaSuccess)
           return err;
         fk<<<dim3((unsigned)lr.count, (unsigned)((nh + kSc - 1) / kSc)), 256, lr.smem, st>>>(
-            e.f2_blocks, e.f2_gptr + lr.first, e.block_leaves, sigma, reinterpret_cast<const float2 *>(e.Ff),
+            e.f2_blocks, e.f2_gptr + lr.first, e.block_leaves, sigma, e.sigp, reinterpret_cast<const float2 *>(e.Ff),
             reinterpret_cast<const float2 *>(e.Fh), reinterpret_cast<float2 *>(phi), e.k, n1, nh, ss);
       } else if (D == 3) {
         if ((err = cudaFuncSetAttribute(form3_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1437,6 +1520,7 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
 
 int launches_per_transform(const ExecDesc &e) {
   int n = 0;
+  n += (e.d == 3 && e.prec == 1 && e.n_pack > 0);  // sigma packing
   n += (e.n_f1 > 0) + (int)e.f2_ranges.size() + (e.n_e1 > 0) + (int)e.e2_ranges.size();  // form + evaluate
   for (const ShiftStep &s : e.merge) n += s.n > 0;
   for (const ShiftStep &s : e.push) n += s.n > 0;
@@ -1491,10 +1575,12 @@ cudaError_t run_transform_noalloc(const ExecDesc &e, const double *sigma, double
   const size_t phi_bytes = c * (size_t)e.slot_size * (size_t)e.n_phi_slots;
   const size_t psi_bytes = c * (size_t)e.slot_size * (size_t)e.n_psi_slots;
   if (phi_bytes + psi_bytes > kNoallocScratchBytes) return cudaErrorInvalidValue;
+  const size_t psi_off = (phi_bytes + 255) & ~(size_t)255;
+  if (psi_off + psi_bytes > kNoallocScratchBytes) return cudaErrorInvalidValue;
   ExecDesc f = e;
   f.phi = base;
-  f.psi = static_cast<unsigned char *>(base) + ((phi_bytes + 255) & ~(size_t)255);
-  if (((phi_bytes + 255) & ~(size_t)255) + psi_bytes > kNoallocScratchBytes) return cudaErrorInvalidValue;
+  f.psi = static_cast<unsigned char *>(base) + psi_off;
+  f.sigp = nullptr;  // no packed sigma: the form kernels read sigma itself
   f.events = nullptr;
   return run_transform(f, sigma, u, stream);
 }

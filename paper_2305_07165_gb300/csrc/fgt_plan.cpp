@@ -564,9 +564,11 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
       if (tensor_form(K)) return fgt::form4_bytes(g, K, n1);
       return d == 3 ? fgt::form3_bytes(g, K, n1, rsz, csz) : fgt::form2_bytes(d, g, K, n1, nh, rsz, csz);
     };
+    // split precision, 3D blocks of K > 16: one block per CTA, sigma streamed from global memory
+    auto big_form = [&](int K) { return K > 16 && tensor_form(K) && fgt::form4b_bytes(K, n1) <= (size_t)smax; };
     auto gmax = [&](int K) {
       int G = 0;
-      if (K > 16) return 0;  // large blocks: staging sigma would leave one CTA per SM
+      if (K > 16) return big_form(K) ? 1 : 0;  // staging sigma would leave one CTA per SM
       for (int g = 1; g <= 8; ++g)
         if (gbytes(g, K) <= three_per_sm) G = g;
       if (G == 0 && gbytes(1, K) <= (size_t)smax) G = 1;
@@ -602,7 +604,8 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
       lr.first = first_group;
       lr.count = (int)f2ptr.size() - 1 - first_group;
       lr.K = K;
-      lr.smem = gbytes(G, K);
+      lr.big = K > 16 ? 1 : 0;
+      lr.smem = lr.big ? fgt::form4b_bytes(K, n1) : gbytes(G, K);
       lr.tensor = tensor_form(K) ? 1 : 0;
       ex.f2_ranges.push_back(lr);
     }
@@ -842,9 +845,22 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
     ex.zero_u = (ex.n_near_pairs > 0 || acc_blocks) ? 1 : 0;
   }
   ex.n_points = P.n_leaves * (int64_t)P.np();
+  // packed FP32 sigma for the tensor-core form (every block_leaves entry, tagged with its block)
+  std::vector<int32_t> pblock;
+  bool use_sigp = false;
+  for (const fgt::LaunchRange &lr : ex.f2_ranges) use_sigp = use_sigp || lr.tensor;
+  if (use_sigp) {
+    pblock.resize(bleaves.size());
+    for (size_t b = 0; b < blocks.size(); ++b) {
+      const int64_t nb = (int64_t)1 << (d * blocks[b].dl);
+      for (int64_t j = 0; j < nb; ++j) pblock[(size_t)(blocks[b].leaf0 + j)] = (int32_t)b;
+    }
+  }
+  ex.n_pack = (int64_t)pblock.size();
 
   // ---- upload
   const size_t o_blocks = pack.add("blocks", blocks), o_bleaves = pack.add("block_leaves", bleaves);
+  const size_t o_pblock = pack.add("pack_block", pblock);
   const size_t o_f1 = pack.add("form1_blocks", f1), o_f2 = pack.add("form2_blocks", f2),
                o_f2p = pack.add("form2_groups", f2ptr), o_e1 = pack.add("eval1_blocks", e1),
                o_e2 = pack.add("eval2_blocks", e2);
@@ -872,13 +888,15 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
 
   const size_t slot_bytes = sizeof(C) * (size_t)ex.slot_size;
   const size_t phi_bytes = slot_bytes * (size_t)ex.n_phi_slots, psi_bytes = slot_bytes * (size_t)ex.n_psi_slots;
+  const size_t psi_off = (phi_bytes + 255) & ~(size_t)255, sigp_off = (psi_off + psi_bytes + 255) & ~(size_t)255;
+  const size_t sigp_bytes = sizeof(float) * (size_t)ex.n_pack * P.np();
   fill_flops(P, ex, blocks, merge_h.size() + push_h.size() ? [&] {
     int64_t sf = 0;
     for (auto &s : merge_h) sf += 8 * (int64_t)s.items.size() * nc * ex.slot_size;
     for (auto &s : push_h) sf += 8 * (int64_t)s.items.size() * nc * ex.slot_size;
     return sf;
   }() : 0, anchors.size());
-  P.info.device_bytes = (int64_t)(pack.size + phi_bytes + psi_bytes);
+  P.info.device_bytes = (int64_t)(pack.size + sigp_off + sigp_bytes);
   if (!upload) {
     P.ex = ex;
     P.host_pack = std::move(pack);
@@ -895,19 +913,21 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
       e = cudaMemcpy((char *)P.dev + pt.first, pt.second.data(), pt.second.size(), cudaMemcpyHostToDevice);
       if (e != cudaSuccess) return cuda_fail(e, "upload");
     }
-  P.work_bytes = phi_bytes + psi_bytes;
+  P.work_bytes = sigp_off + sigp_bytes;
   if (P.work_bytes) {
     e = cudaMalloc(&P.work, P.work_bytes);
     if (e != cudaSuccess) {
       P.work = nullptr;
       P.work_bytes = 0;
       cudaGetLastError();
-      return fail(FGT_ERR_OOM, "expansion workspace of " + std::to_string(phi_bytes + psi_bytes) + " bytes");
+      return fail(FGT_ERR_OOM, "expansion workspace of " + std::to_string(sigp_off + sigp_bytes) + " bytes");
     }
   }
   auto at = [&](size_t off) { return (const void *)((const char *)P.dev + off); };
   ex.phi = P.work;
-  ex.psi = (char *)P.work + phi_bytes;
+  ex.psi = (char *)P.work + psi_off;
+  ex.sigp = sigp_bytes ? (float *)((char *)P.work + sigp_off) : nullptr;
+  ex.pack_block = (const int32_t *)at(o_pblock);
   ex.blocks = (const fgt::Block *)at(o_blocks);
   ex.f1_blocks = (const fgt::Block *)at(o_f1);
   ex.f2_blocks = (const fgt::Block *)at(o_f2);

@@ -90,6 +90,14 @@ def test_split_precision(d, delta):
     check(d, p, delta, 1e-6, tr, sig, prec=1)
 
 
+def test_split_precision_large_blocks():
+    """Split precision, uniform subtrees of K = 32 nodes per axis under each cutoff-level box:
+    one block per CTA, sigma streamed from global memory in the first contraction."""
+    tr = W.uniform_tree(3, 3)
+    sig = W.random_sigma(tr, 8, 21)
+    check(3, 8, 1e-2, 1e-6, tr, sig, prec=1)
+
+
 def test_3d_uniform_p8_sampled():
     """3D free space, uniform level-4 tree, p = 8 (2M points): sampled targets."""
     tr = W.uniform_tree(3, 4)

@@ -21,11 +21,17 @@ F = pytest.importorskip("paper_2305_07165_gb300")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("case", ["2d", "3d", "3d_split"])
+@pytest.mark.parametrize("case", ["2d", "3d", "3d_split", "3d_split_large_blocks"])
 def test_noalloc_matches_execute_twice(case):
     if case == "2d":
         w = W.config_2d_free_uniform(seed=0)
         d, p, delta, tol, tree, sig, prec = 2, w.p, w.delta, 1e-9, w.tree, w.sigma, F.PREC_FP64
+    elif case == "3d_split_large_blocks":
+        # K = 32 blocks: the allocation-free call reads sigma directly, the plan's own call
+        # through its packed FP32 copy, so the two paths check each other
+        tree = W.uniform_tree(3, 3)
+        d, p, delta, tol, prec = 3, 8, 1e-2, 1e-6, F.PREC_SPLIT
+        sig = W.random_sigma(tree, p, 17)
     else:
         tree = W.random_balanced_tree(3, 21, max_level=4, min_level=2, split_prob=0.2)
         d, p = 3, 4
