@@ -15,6 +15,7 @@ struct LaunchRange {
   size_t smem = 0;
   int tensor = 0;  // 1: the tensor-core (3xTF32) variant of the kernel
   int big = 0;     // 1: single blocks of K > 16, sigma streamed from global memory in stage 1
+  int rows = 0;    // evaluation: rows of a block per CTA
 };
 
 // One level of the hierarchical merge (child -> parent) or push (parent -> child).
@@ -133,9 +134,11 @@ inline size_t form4b_bytes(int K, int n1) {
 inline size_t eval3_bytes(int K, int n1, int nh) {
   return 8 * (8 * (size_t)n1 * n1 + 8 * (size_t)K * n1 + 2 * (size_t)K * n1 + 8 * (size_t)nh);
 }
-inline size_t eval2_bytes(int d, int K, int n1, int nh, size_t c) {
-  if (d == 3) return c * ((size_t)K * n1 * n1 + (size_t)K * K * n1 + 2 * (size_t)K * n1 + (size_t)K * nh);
-  return c * ((size_t)K * n1 + (size_t)K * n1 + (size_t)K * nh);
+// Whole-block evaluation, `rows` rows (along the last axis) of a block per CTA (4, 8 or 16).
+inline size_t eval2_bytes(int d, int K, int n1, int nh, size_t c, int rows) {
+  const size_t R = (size_t)(K < rows ? K : rows);  // rows held at once
+  if (d == 3) return c * (R * n1 * n1 + R * K * n1 + 2 * (size_t)K * n1 + R * nh);
+  return c * (R * n1 + (size_t)K * n1 + R * nh);
 }
 
 // Shared-memory bytes the form / evaluation kernels need for a block size K.

@@ -827,11 +827,11 @@ __global__ void __launch_bounds__(256) form4_kernel(const Block *__restrict__ bl
 
 // ----------------------------------------------------------------------------- whole-block evaluation
 
-// A CTA evaluates one whole block (K <= KM nodes per axis): the anchor's incoming expansion is
-// read once (each thread keeps K accumulators for its mode column), then the two remaining
-// contractions run from shared memory.
+// A CTA evaluates KM rows (along the last axis) of one block, all of it when K <= KM: the
+// anchor's incoming expansion is read once per CTA (each thread keeps KM accumulators for its
+// mode column), then the two remaining contractions run from shared memory.
 template <int D, typename R, int KM>
-__global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256) eval2_kernel(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
+__global__ void __launch_bounds__(256) eval2_kernel(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
                                                     const typename C2T<R>::T *__restrict__ Ef,
                                                     const typename C2T<R>::T *__restrict__ Eh,
                                                     const typename C2T<R>::T *__restrict__ psi, double *__restrict__ u,
@@ -840,22 +840,25 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256) eval2_kernel(const
   extern __shared__ unsigned char smem_raw[];
   const Block blk = blocks[blockIdx.x];
   const int K = blk.K, nl = 1 << blk.dl;
+  const int r0 = blockIdx.y * KM, nr = min(KM, K - r0);  // rows r0 .. r0 + nr - 1
+  if (nr <= 0) return;
+  const int RM = min(KM, K);                           // rows the shared arrays are sized for
   const int64_t *lv = bleaves + blk.leaf0;
   const C *ps = psi + (int64_t)blk.slot * slot_size;
   const bool acc_u = (blk.flags & 1) != 0;
   const int nn = (D == 3) ? n1 * n1 : n1;
-  C *Y1 = reinterpret_cast<C *>(smem_raw);            // [K][nn]
-  C *Y2 = Y1 + (size_t)K * nn;                         // [K][K][n1] (3D)
-  C *E1 = Y2 + (D == 3 ? (size_t)K * K * n1 : 0);      // [K][n1]
+  C *Y1 = reinterpret_cast<C *>(smem_raw);            // [RM][nn]
+  C *Y2 = Y1 + (size_t)RM * nn;                        // [RM][K][n1] (3D)
+  C *E1 = Y2 + (D == 3 ? (size_t)RM * K * n1 : 0);     // [K][n1]
   C *E2 = E1 + (size_t)K * n1;                         // [K][n1] (3D)
-  C *Ed = E2 + (D == 3 ? (size_t)K * n1 : 0);          // [K][nh]
+  C *Ed = E2 + (D == 3 ? (size_t)K * n1 : 0);          // [RM][nh]
   for (int e = threadIdx.x; e < K * n1; e += blockDim.x) {
     const int I = e / n1, m = e - I * n1;
     E1[e] = Ef[((int64_t)(blk.mat[0] + I / k) * k + I % k) * n1 + m];
     if (D == 3) E2[e] = Ef[((int64_t)(blk.mat[1] + I / k) * k + I % k) * n1 + m];
   }
-  for (int e = threadIdx.x; e < K * nh; e += blockDim.x) {
-    const int I = e / nh, m = e - I * nh;
+  for (int e = threadIdx.x; e < nr * nh; e += blockDim.x) {
+    const int I = r0 + e / nh, m = e % nh;
     Ed[e] = Eh[((int64_t)(blk.mat[D - 1] + I / k) * k + I % k) * nh + m];
   }
   __syncthreads();
@@ -874,44 +877,132 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256) eval2_kernel(const
         if (md0 + q < nh) {
 #pragma unroll
           for (int r = 0; r < KM; ++r)
-            if (r < K) cfma(ar[r], ai[r], Ed[r * nh + md0 + q], v[q]);
+            if (r < nr) cfma(ar[r], ai[r], Ed[r * nh + md0 + q], v[q]);
         }
       }
     }
 #pragma unroll
     for (int r = 0; r < KM; ++r)
-      if (r < K) Y1[(size_t)r * nn + idx] = C{ar[r], ai[r]};
+      if (r < nr) Y1[(size_t)r * nn + idx] = C{ar[r], ai[r]};
   }
   __syncthreads();
   const int kp = (D == 3) ? k * k * k : k * k;
   if (D == 3) {
-    // Y2[r][I2][m1] = sum_m2 E2[I2][m2] Y1[r][m2][m1]
-    for (int e = threadIdx.x; e < K * K * n1; e += blockDim.x) {
-      const int m1 = e % n1, rest = e / n1, I2 = rest % K, r = rest / K;
-      const C *ep = E2 + (size_t)I2 * n1;
-      const C *yp = Y1 + (size_t)r * nn + m1;
-      R ar = 0, ai = 0;
-      for (int m2 = 0; m2 < n1; ++m2) cfma(ar, ai, ep[m2], yp[m2 * n1]);
-      Y2[e] = C{ar, ai};
+    // Y2[r][I2][m1] = sum_m2 E2[I2][m2] Y1[r][m2][m1]; 4 x 4 register tiles over (I2, m1) when
+    // there are enough tiles to occupy the CTA, else one output per thread
+    const int tI = (K + 3) / 4, tm = (n1 + 3) / 4;
+    if (nr * tI * tm < (int)blockDim.x / 2) {
+      for (int e = threadIdx.x; e < nr * K * n1; e += blockDim.x) {
+        const int m1 = e % n1, rest = e / n1, I2 = rest % K, r = rest / K;
+        const C *ep = E2 + (size_t)I2 * n1;
+        const C *yp = Y1 + (size_t)r * nn + m1;
+        R ar = 0, ai = 0;
+        for (int m2 = 0; m2 < n1; ++m2) cfma(ar, ai, ep[m2], yp[m2 * n1]);
+        Y2[e] = C{ar, ai};
+      }
+    } else {
+      const int ntile = nr * tI * tm;
+      for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
+        const int bm = t % tm, rest = t / tm, bI = rest % tI, r = rest / tI;
+        R ar[4][4], ai[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) ar[i][j] = ai[i][j] = 0;
+        const C *yr = Y1 + (size_t)r * nn;
+        for (int m2 = 0; m2 < n1; ++m2) {
+          C a[4], b[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int I2 = bI * 4 + i;
+            a[i] = (I2 < K) ? E2[(size_t)I2 * n1 + m2] : C{0, 0};
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int m1 = bm * 4 + j;
+            b[j] = (m1 < n1) ? yr[(size_t)m2 * n1 + m1] : C{0, 0};
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) cfma(ar[i][j], ai[i][j], a[i], b[j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int I2 = bI * 4 + i, m1 = bm * 4 + j;
+            if (I2 < K && m1 < n1) Y2[((size_t)r * K + I2) * n1 + m1] = C{ar[i][j], ai[i][j]};
+          }
+      }
     }
     __syncthreads();
-    // u(r, I2, I1) = Re sum_m1 E1[I1][m1] Y2[r][I2][m1]
-    for (int e = threadIdx.x; e < K * K * K; e += blockDim.x) {
-      const int I1 = e % K, rest = e / K, I2 = rest % K, r = rest / K;
-      const C *ep = E1 + (size_t)I1 * n1;
-      const C *yp = Y2 + ((size_t)r * K + I2) * n1;
-      R acc = 0;
-      for (int m1 = 0; m1 < n1; ++m1) {
-        const C a = ep[m1], y = yp[m1];
-        acc = fma(a.x, y.x, acc);
-        acc = fma(-a.y, y.y, acc);
+    // u(r0 + r, I2, I1) = Re sum_m1 E1[I1][m1] Y2[r][I2][m1]; 4 x 4 register tiles over (I2, I1)
+    // when there are enough tiles, else one output per thread
+    if (nr * tI * tI < (int)blockDim.x / 2) {
+      for (int e = threadIdx.x; e < nr * K * K; e += blockDim.x) {
+        const int I1 = e % K, rest = e / K, I2 = rest % K, r = rest / K;
+        const C *ep = E1 + (size_t)I1 * n1;
+        const C *yp = Y2 + ((size_t)r * K + I2) * n1;
+        R acc = 0;
+        for (int m1 = 0; m1 < n1; ++m1) {
+          const C a = ep[m1], y = yp[m1];
+          acc = fma(a.x, y.x, acc);
+          acc = fma(-a.y, y.y, acc);
+        }
+        const int I3 = r0 + r, o1 = I1 / k, o2 = I2 / k, o3 = I3 / k;
+        double *up = u + lv[(o3 * nl + o2) * nl + o1] * kp + ((I3 - o3 * k) * k + (I2 - o2 * k)) * k + (I1 - o1 * k);
+        if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc;
       }
-      const int o1 = I1 / k, o2 = I2 / k, o3 = r / k;
-      double *up = u + lv[(o3 * nl + o2) * nl + o1] * kp + ((r - o3 * k) * k + (I2 - o2 * k)) * k + (I1 - o1 * k);
-      if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc;
+    } else {
+      const int ntile = nr * tI * tI;
+      for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
+        const int b1 = t % tI, rest = t / tI, b2 = rest % tI, r = rest / tI;
+        R acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+        const C *yr = Y2 + (size_t)r * K * n1;
+        for (int m1 = 0; m1 < n1; ++m1) {
+          C y[4], a[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int I2 = b2 * 4 + i;
+            y[i] = (I2 < K) ? yr[(size_t)I2 * n1 + m1] : C{0, 0};
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int I1 = b1 * 4 + j;
+            a[j] = (I1 < K) ? E1[(size_t)I1 * n1 + m1] : C{0, 0};
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              acc[i][j] = fma(a[j].x, y[i].x, acc[i][j]);
+              acc[i][j] = fma(-a[j].y, y[i].y, acc[i][j]);
+            }
+        }
+        const int I3 = r0 + r, o3 = I3 / k, t3 = I3 - o3 * k;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int I2 = b2 * 4 + i;
+          if (I2 >= K) continue;
+          const int o2 = I2 / k, t2 = I2 - o2 * k;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int I1 = b1 * 4 + j;
+            if (I1 >= K) continue;
+            const int o1 = I1 / k;
+            double *up = u + lv[(o3 * nl + o2) * nl + o1] * kp + (t3 * k + t2) * k + (I1 - o1 * k);
+            if (acc_u) atomicAdd(up, (double)acc[i][j]); else *up = (double)acc[i][j];
+          }
+        }
+      }
     }
   } else {
-    for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    for (int e = threadIdx.x; e < nr * K; e += blockDim.x) {
       const int I1 = e % K, r = e / K;
       const C *ep = E1 + (size_t)I1 * n1;
       const C *yp = Y1 + (size_t)r * nn;
@@ -921,8 +1012,8 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256) eval2_kernel(const
         acc = fma(a.x, y.x, acc);
         acc = fma(-a.y, y.y, acc);
       }
-      const int o1 = I1 / k, o2 = r / k;
-      double *up = u + lv[o2 * nl + o1] * kp + (r - o2 * k) * k + (I1 - o1 * k);
+      const int I2 = r0 + r, o1 = I1 / k, o2 = I2 / k;
+      double *up = u + lv[o2 * nl + o1] * kp + (I2 - o2 * k) * k + (I1 - o1 * k);
       if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc;
     }
   }
@@ -1501,11 +1592,14 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
       continue;
     }
-    auto kern = lr.K <= 8 ? eval2_kernel<D, R, 8> : eval2_kernel<D, R, 16>;
+    // lr.rows rows of a block per CTA
+    auto kern = lr.rows <= 4 ? eval2_kernel<D, R, 4> : lr.rows <= 8 ? eval2_kernel<D, R, 8> : eval2_kernel<D, R, 16>;
+    const int rows = lr.rows <= 4 ? 4 : lr.rows <= 8 ? 8 : 16;
+    const unsigned chunks = (unsigned)((lr.K + rows - 1) / rows);
     if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) !=
         cudaSuccess)
       return err;
-    kern<<<(unsigned)lr.count, sizeof(R) == 4 ? 512 : 256, lr.smem, st>>>(
+    kern<<<dim3((unsigned)lr.count, chunks), 256, lr.smem, st>>>(
         e.e2_blocks + lr.first, e.block_leaves, reinterpret_cast<const C *>(e.Ef), reinterpret_cast<const C *>(e.Eh),
         eval_src, u, e.k, n1, nh, ss);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;

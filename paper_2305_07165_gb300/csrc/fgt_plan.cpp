@@ -609,17 +609,25 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
       lr.tensor = tensor_form(K) ? 1 : 0;
       ex.f2_ranges.push_back(lr);
     }
-    // evaluation: whole-block kernel for K <= 16 when it fits, one launch per K
+    // evaluation: whole-block kernel for K <= 16 when it fits, one launch per K; in split
+    // precision (3D) larger blocks too, a few rows per CTA
+    // rows per CTA (split precision, 3D): 8 for K = 16 and 4 for larger blocks measured fastest
+    // on GB300 (more resident CTAs outweigh reading the anchor's expansion two or more times)
+    const int rows16 = 8, rows32 = 4;
     for (const fgt::Block &b : sorted) {
-      const size_t eb = tensor_eval ? fgt::eval3_bytes(b.K, n1, nh) : fgt::eval2_bytes(d, b.K, n1, nh, csz);
-      if (b.K <= 16 && eb <= (size_t)smax) {
+      const bool chunked = b.K > 16 && d == 3 && P.prec == FGT_PREC_SPLIT;
+      const int rows = b.K <= 8 ? 8 : b.K <= 16 ? (P.prec == FGT_PREC_SPLIT && d == 3 ? rows16 : 16) : rows32;
+      const size_t eb = (tensor_eval && !chunked) ? fgt::eval3_bytes(b.K, n1, nh)
+                                                  : fgt::eval2_bytes(d, b.K, n1, nh, csz, rows);
+      if ((b.K <= 16 || chunked) && eb <= (size_t)smax) {
         if (ex.e2_ranges.empty() || ex.e2_ranges.back().K != b.K) {
           fgt::LaunchRange lr;
           lr.first = (int)e2.size();
           lr.count = 0;
           lr.K = b.K;
+          lr.rows = rows;
           lr.smem = eb;
-          lr.tensor = tensor_eval ? 1 : 0;
+          lr.tensor = (tensor_eval && !chunked) ? 1 : 0;
           ex.e2_ranges.push_back(lr);
         }
         e2.push_back(b);
