@@ -65,6 +65,8 @@ struct ExecDesc {
   const int64_t *gather_ptr = nullptr;
   const GatherSrc *gather_src = nullptr;
   const void *Pf = nullptr, *Ph = nullptr;   // [3][n1], [3][nh]
+  const GatherSeg *gather_segs = nullptr;    // separable form of the same gather
+  int64_t n_gather_segs = 0;
 
   // hierarchical mode (empty in fused mode); merge in execution order (fine -> coarse)
   std::vector<ShiftStep> merge, push;

@@ -28,6 +28,16 @@ struct GatherSrc {
   int32_t code;      // (o1+1) + 3 (o2+1) + 9 (o3+1), o = S - T in box units
 };
 
+// Separable out->in gather: one run of up to kSegW consecutive boxes along x_1 at the cutoff
+// level (fixed x_2, x_3).  Line l = (o_2 + 1) + 3 (o_3 + 1) holds the outgoing slots of the
+// kSegW + 2 boxes x0 - 1 .. x0 + kSegW at x_2 + o_2, x_3 + o_3 (2D: lines 0..2 only); -1 where
+// there is no box with an outgoing expansion.
+constexpr int kSegW = 8;
+struct GatherSeg {
+  int32_t tgt[kSegW];            // incoming slot of box x0 + t, -1: not a target
+  int32_t src[9][kSegW + 2];
+};
+
 // One near-field (D-list) source for a target leaf.
 struct NearSrc {
   int64_t leaf;      // source leaf index

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -682,6 +683,46 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   }
   ex.n_gather = (int64_t)gdst.size();
   P.n_gather_pairs = (int64_t)gsrc.size();
+  // split precision: the same gather in separable form, runs of kSegW target boxes along x_1,
+  // each with the 3^(d-1) neighbouring source lines (one launch item per run)
+  std::vector<fgt::GatherSeg> gsegs;
+  if (P.prec == FGT_PREC_SPLIT && !P.fourier && !anchors.empty()) {
+    const int nb = 1 << P.lc, sw = std::min(fgt::kSegW, nb);
+    std::map<std::array<int32_t, 3>, size_t> seg_of;
+    auto slot_at = [&](int32_t x, int32_t y, int32_t z) -> int32_t {
+      int32_t q[3] = {x, y, z};
+      for (int a = 0; a < d; ++a) {
+        if (q[a] < 0 || q[a] >= nb) {
+          if (!per) return -1;
+          q[a] = (q[a] % nb + nb) % nb;
+        }
+      }
+      const int32_t S = P.find(P.lc, q);
+      return (S >= 0 && P.boxes[S].f) ? P.boxes[S].slot : -1;
+    };
+    for (int32_t T : anchors) {
+      const Box &Tb = P.boxes[T];
+      const int32_t x0 = Tb.c[0] / sw * sw, y = Tb.c[1], z = d == 3 ? Tb.c[2] : 0;
+      const std::array<int32_t, 3> key{x0, y, z};
+      auto it = seg_of.find(key);
+      if (it == seg_of.end()) {
+        fgt::GatherSeg g;
+        for (int t = 0; t < fgt::kSegW; ++t) g.tgt[t] = -1;
+        for (int l = 0; l < 9; ++l) {
+          // 2D uses lines 0..2 (o_2 = l - 1) only
+          const int o2 = l % 3 - 1, o3 = d == 3 ? l / 3 - 1 : 0;
+          for (int i = 0; i < fgt::kSegW + 2; ++i) {
+            // only the sw + 2 boxes around a run of sw targets are ever read
+            g.src[l][i] = (i < sw + 2 && (d == 3 || l < 3)) ? slot_at(x0 - 1 + i, y + o2, z + o3) : -1;
+          }
+        }
+        it = seg_of.emplace(key, gsegs.size()).first;
+        gsegs.push_back(g);
+      }
+      gsegs[it->second].tgt[Tb.c[0] - x0] = Tb.slot;
+    }
+  }
+  ex.n_gather_segs = (int64_t)gsegs.size();
   // phase vectors of T_out->in: S = T + o (box units) gives c_T - c_S = -o L_c
   std::vector<C> Pf, Ph;
   {
@@ -877,6 +918,7 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   const size_t o_gdst = pack.add("gather_dst", gdst), o_gptr = pack.add("gather_ptr", gptr),
                o_gsrc = pack.add("gather_src", gsrc);
   const size_t o_Pf = pack.add("Pf", Pf), o_Ph = pack.add("Ph", Ph);
+  const size_t o_gseg = pack.add("gather_segs", gsegs);
   const size_t o_ntgt = pack.add("near_tgt", ntgt), o_nflags = pack.add("near_flags", nflags),
                o_nptr = pack.add("near_ptr", nptr), o_nsrc = pack.add("near_src", nsrc),
                o_ntab = pack.add("near_tab", ntab), o_npairs = pack.add("near_pairs", npairs);
@@ -945,6 +987,7 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   ex.block_leaves = (const int64_t *)at(o_bleaves);
   ex.Ff = at(o_Ff); ex.Fh = at(o_Fh); ex.Ef = at(o_Ef); ex.Eh = at(o_Eh);
   ex.gather_dst = (const int32_t *)at(o_gdst);
+  ex.gather_segs = (const fgt::GatherSeg *)at(o_gseg);
   ex.gather_ptr = (const int64_t *)at(o_gptr);
   ex.gather_src = (const fgt::GatherSrc *)at(o_gsrc);
   ex.Pf = at(o_Pf); ex.Ph = at(o_Ph);

@@ -90,6 +90,21 @@ def test_split_precision(d, delta):
     check(d, p, delta, 1e-6, tr, sig, prec=1)
 
 
+@pytest.mark.parametrize("d,delta", [(2, 3e-3), (2, 2e-4), (3, 1e-3), (3, 2e-3)])
+def test_split_precision_periodic(d, delta):
+    """Split precision with periodic wrap-around of the cutoff-level gather (runs of boxes along
+    x_1 whose neighbours wrap, cutoff grids of 4 to 32 boxes per axis)."""
+    if d == 2:
+        tr = W.random_balanced_tree(2, 7, max_level=6, min_level=2, periodic=True, split_prob=0.35)
+        p = 8
+    else:
+        tr = W.random_balanced_tree(3, 9, max_level=4, min_level=2, split_prob=0.25, periodic=True)
+        p = 4
+    sig = W.random_sigma(tr, p, 19)
+    _, info = check(d, p, delta, 1e-6, tr, sig, bc=1, prec=1)
+    assert info["cutoff_level"] >= 2
+
+
 def test_split_precision_large_blocks():
     """Split precision, uniform subtrees of K = 32 nodes per axis under each cutoff-level box:
     one block per CTA, sigma streamed from global memory in the first contraction."""
