@@ -122,16 +122,18 @@ inline size_t form3_bytes(int G, int K, int n1, size_t r, size_t c) {
   return sig + c * (GK * n1 + (size_t)G * n1 * K + (size_t)G * Sc * K + Sc * G * (size_t)K * K +
                     Sc * (size_t)n1 * (GK + 1));
 }
-// Tensor-core 3D form (FP32 only): form3's layout plus the split B operands (2 x 2 n1p x (2GK+4)).
-inline size_t form4_bytes(int G, int K, int n1) {
-  const size_t GK = (size_t)G * K, n1p = ((size_t)n1 + 7) / 8 * 8;
-  // form3's Z2 rows are GK + 1 complex wide, form4's GK + 2
-  return form3_bytes(G, K, n1, 4, 8) + 4 * (size_t)n1 * 8 + 2 * (2 * n1p) * (2 * GK + 4) * 4;
+// Tensor-core 3D form (FP32 only): F1t and Z2 (rows GK + 2 complex wide) kept, then sigma, F2,
+// Fd and Z1, over which the split B operands (2 x 2 n1p x (2GK+4)) are built after stage 2.
+// big: one block of K > 16 whose sigma is read from global memory in stage 1 (no sigma tile).
+inline size_t form4_bytes(int G, int K, int n1, bool big = false) {
+  const size_t GK = (size_t)G * K, n1p = ((size_t)n1 + 7) / 8 * 8, c = 8, Sc = 4;
+  const size_t keep = c * (GK * n1 + Sc * (size_t)n1 * (GK + 2));
+  const size_t sig = big ? 0 : (((size_t)G * K * K * K * 4) + 15) & ~(size_t)15;
+  const size_t s12 = sig + c * ((size_t)G * n1 * K + (size_t)G * Sc * K + Sc * G * (size_t)K * K);
+  const size_t bops = 2 * (2 * n1p) * (2 * GK + 4) * 4;
+  return keep + (s12 > bops ? s12 : bops);
 }
-// form4 over one block of K > 16 whose sigma is read from global memory in stage 1: no sigma tile.
-inline size_t form4b_bytes(int K, int n1) {
-  return form4_bytes(1, K, n1) - ((((size_t)K * K * K * 4) + 15) & ~(size_t)15);
-}
+inline size_t form4b_bytes(int K, int n1) { return form4_bytes(1, K, n1, true); }
 // Tensor-core 3D evaluation (FP32 only): 8 output rows per CTA.
 inline size_t eval3_bytes(int K, int n1, int nh) {
   return 8 * (8 * (size_t)n1 * n1 + 8 * (size_t)K * n1 + 2 * (size_t)K * n1 + 8 * (size_t)nh);

@@ -594,7 +594,7 @@ __host__ __device__ inline int ldz4(int GK) { return GK + 2; }       // complex 
 __host__ __device__ inline int ldb4(int GK) { return 2 * GK + 4; }   // uint32 row stride of Bh / Bl
 
 template <int NBT, bool BIG>  // NBT: n-tiles of 8 output columns held in registers (>= 2 n1p / 8)
-__global__ void __launch_bounds__(256) form4_kernel(const Block *__restrict__ blocks, const int32_t *__restrict__ gptr,
+__global__ void __launch_bounds__(256, BIG ? 2 : (NBT > 8 ? 2 : 3)) form4_kernel(const Block *__restrict__ blocks, const int32_t *__restrict__ gptr,
                                                     const int64_t *__restrict__ bleaves,
                                                     const double *__restrict__ sigma, const float *__restrict__ sigp,
                                                     const float2 *__restrict__ Ff, const float2 *__restrict__ Fh,
@@ -603,21 +603,28 @@ __global__ void __launch_bounds__(256) form4_kernel(const Block *__restrict__ bl
   using R = float;
   using C = float2;
   extern __shared__ __align__(16) unsigned char smem4[];
-  const int b0 = gptr[blockIdx.x], G = gptr[blockIdx.x + 1] - b0;
+  // linear grid, plane chunk fastest: the CTAs of one group run close together and share its
+  // sigma and matrices in L2
+  const int nchunk = (nh + kSc - 1) / kSc;
+  const int grp = (int)(blockIdx.x / nchunk), chunk = (int)(blockIdx.x - (unsigned)grp * nchunk);
+  const int b0 = gptr[grp], G = gptr[grp + 1] - b0;
   const Block B0 = blocks[b0];
   const int K = B0.K, nl = 1 << B0.dl;
   const int KK = K * K, npb = KK * K, kp = k * k * k, GK = G * K, ldz = ldz4(GK), ldb = ldb4(GK);
   const int n1p = n1_pad8(n1), NB = 2 * n1p;
-  const int s0 = blockIdx.y * kSc, ns = min(kSc, nh - s0);
-  // BIG (one block of K > 16): no sigma tile, stage 1 streams it from global memory
-  R *sig = reinterpret_cast<R *>(smem4);                                      // [G][K^3]
+  const int s0 = chunk * kSc, ns = min(kSc, nh - s0);
+  // F1t and Z2 live through stage 3; sigma, F2, Fd and Z1 are dead after stage 2, and the split
+  // B operands of stage 3 are built over them.  BIG (one block of K > 16): no sigma tile,
+  // stage 1 streams it from global memory.
+  C *F1t = reinterpret_cast<C *>(smem4);                                      // [G K][n1]
+  C *Z2 = F1t + (size_t)GK * n1;                                              // [kSc][n1][ldz]
+  unsigned char *s12 = reinterpret_cast<unsigned char *>(Z2 + (size_t)kSc * n1 * ldz);
+  R *sig = reinterpret_cast<R *>(s12);                                        // [G][K^3]
   const size_t sig_bytes = BIG ? 0 : ((size_t)G * npb * sizeof(R) + 15) & ~(size_t)15;
-  C *F1t = reinterpret_cast<C *>(smem4 + sig_bytes);                          // [G K][n1]
-  C *F2 = F1t + (size_t)GK * n1;                                              // [G][n1][K]
+  C *F2 = reinterpret_cast<C *>(s12 + sig_bytes);                             // [G][n1][K]
   C *Fd = F2 + (size_t)G * n1 * K;                                            // [G][kSc][K]
   C *Z1 = Fd + (size_t)G * kSc * K;                                           // [kSc][G][K][K]
-  C *Z2 = Z1 + (size_t)kSc * G * KK;                                          // [kSc][n1][ldz]
-  uint32_t *Bh = reinterpret_cast<uint32_t *>(Z2 + (size_t)kSc * n1 * ldz);   // [NB][ldb]
+  uint32_t *Bh = reinterpret_cast<uint32_t *>(s12);                           // [NB][ldb], after stage 2
   uint32_t *Bl = Bh + (size_t)NB * ldb;
   for (int g = 0; g < G; ++g) {
     const Block b = blocks[b0 + g];
@@ -658,44 +665,55 @@ __global__ void __launch_bounds__(256) form4_kernel(const Block *__restrict__ bl
     }
   }
   __syncthreads();
-  // split B operands from F1t: column n < n1p -> real part of output m1 = n, else imaginary part
-  for (int e = threadIdx.x; e < NB * 2 * GK; e += blockDim.x) {
-    // columns in 16-wide pairs: 8 real-part columns of modes 8 jt .. 8 jt + 7, then their 8
-    // imaginary-part columns (so a tile and its partner sit at compile-time indices 2j, 2j+1)
-    const int n = e / (2 * GK), kr = e - n * 2 * GK, J = kr >> 1, odd = kr & 1;
-    const bool im = ((n >> 3) & 1) != 0;
-    const int m1 = (n >> 4) * 8 + (n & 7);
-    float v = 0.f;
-    if (m1 < n1) {
-      const C f = F1t[(size_t)J * n1 + m1];
-      v = im ? (odd ? f.x : f.y) : (odd ? -f.y : f.x);
-    }
-    uint32_t h, l;
-    split_tf32(v, h, l);
-    Bh[(size_t)n * ldb + kr] = h;
-    Bl[(size_t)n * ldb + kr] = l;
-  }
   // stage 1: Z1[q][g][J2][J1] = sum_J3 Fd[g][q][J3] sig[g][J3][J2][J1]
   if (BIG) {
     // one block, sigma from global memory: packed (coalesced along J1), else leaf by leaf
     const int64_t *lv = bleaves + B0.leaf0;
-    for (int rem = threadIdx.x; rem < KK; rem += blockDim.x) {
+    if (sigp != nullptr) {
+      // four columns per thread, two J3 steps per iteration: eight loads in flight
+      constexpr int NC = 4;
+      const int nth = blockDim.x;
+      for (int rem0 = threadIdx.x; rem0 < KK; rem0 += NC * nth) {
+        R ar[NC][kSc], ai[NC][kSc];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+          for (int q = 0; q < kSc; ++q) ar[c][q] = ai[c][q] = 0;
+        const float *sp = sigp + B0.leaf0 * kp + rem0;
+        for (int J3 = 0; J3 < K; J3 += 2) {
+          R v[2][NC];
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+              v[h][c] = (J3 + h < K && rem0 + c * nth < KK) ? __ldg(sp + (size_t)(J3 + h) * KK + c * nth) : 0.f;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (J3 + h >= K) break;
+#pragma unroll
+            for (int q = 0; q < kSc; ++q) {
+              const C f = Fd[q * K + J3 + h];
+#pragma unroll
+              for (int c = 0; c < NC; ++c) {
+                ar[c][q] = fmaf(f.x, v[h][c], ar[c][q]);
+                ai[c][q] = fmaf(f.y, v[h][c], ai[c][q]);
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          if (rem0 + c * nth < KK) {
+#pragma unroll
+            for (int q = 0; q < kSc; ++q) Z1[(size_t)q * KK + rem0 + c * nth] = C{ar[c][q], ai[c][q]};
+          }
+      }
+    }
+    for (int rem = threadIdx.x; rem < KK && sigp == nullptr; rem += blockDim.x) {
       R ar[kSc], ai[kSc];
 #pragma unroll
       for (int q = 0; q < kSc; ++q) ar[q] = ai[q] = 0;
-      if (sigp != nullptr) {
-        const float *sp = sigp + B0.leaf0 * kp + rem;
-#pragma unroll 4
-        for (int J3 = 0; J3 < K; ++J3) {
-          const R v = __ldg(sp + (size_t)J3 * KK);
-#pragma unroll
-          for (int q = 0; q < kSc; ++q) {
-            const C f = Fd[q * K + J3];
-            ar[q] = fmaf(f.x, v, ar[q]);
-            ai[q] = fmaf(f.y, v, ai[q]);
-          }
-        }
-      } else {
+      {
         const int J2 = rem / K, J1 = rem - J2 * K;
         const int o2 = J2 / k, j2 = J2 - o2 * k, o1 = J1 / k, j1 = J1 - o1 * k;
         for (int o3 = 0; o3 < nl; ++o3) {
@@ -776,6 +794,24 @@ __global__ void __launch_bounds__(256) form4_kernel(const Block *__restrict__ bl
           if (m < n1 && J1 < K) Z2[((size_t)q * n1 + m) * ldz + g * K + J1] = C{ar[i][j], ai[i][j]};
         }
     }
+  }
+  __syncthreads();
+  // split B operands from F1t: column n < n1p -> real part of output m1 = n, else imaginary part
+  for (int e = threadIdx.x; e < NB * 2 * GK; e += blockDim.x) {
+    // columns in 16-wide pairs: 8 real-part columns of modes 8 jt .. 8 jt + 7, then their 8
+    // imaginary-part columns (so a tile and its partner sit at compile-time indices 2j, 2j+1)
+    const int n = e / (2 * GK), kr = e - n * 2 * GK, J = kr >> 1, odd = kr & 1;
+    const bool im = ((n >> 3) & 1) != 0;
+    const int m1 = (n >> 4) * 8 + (n & 7);
+    float v = 0.f;
+    if (m1 < n1) {
+      const C f = F1t[(size_t)J * n1 + m1];
+      v = im ? (odd ? f.x : f.y) : (odd ? -f.y : f.x);
+    }
+    uint32_t h, l;
+    split_tf32(v, h, l);
+    Bh[(size_t)n * ldb + kr] = h;
+    Bl[(size_t)n * ldb + kr] = l;
   }
   __syncthreads();
   // stage 3 (tensor cores): per plane q and 16-row tile of m2, all 2*n1p output columns
@@ -1581,7 +1617,7 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
         if ((err = cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) !=
             cudaSuccess)
           return err;
-        fk<<<dim3((unsigned)lr.count, (unsigned)((nh + kSc - 1) / kSc)), 256, lr.smem, st>>>(
+        fk<<<(unsigned)(lr.count * ((nh + kSc - 1) / kSc)), 256, lr.smem, st>>>(
             e.f2_blocks, e.f2_gptr + lr.first, e.block_leaves, sigma, e.sigp, reinterpret_cast<const float2 *>(e.Ff),
             reinterpret_cast<const float2 *>(e.Fh), reinterpret_cast<float2 *>(phi), e.k, n1, nh, ss);
       } else if (D == 3) {
