@@ -43,7 +43,8 @@ WORKLOADS = {
     "uniform2d": lambda W: W.config_2d_free_uniform(seed=0),
 }
 FORMS = {"split": ("split_tol1e-6", 1e-6, 1), "fp64": ("fp64_tol1e-6", 1e-6, 0),
-         "fp64_1e-10": ("fp64_tol1e-10", 1e-10, 0)}
+         "fp64_1e-10": ("fp64_tol1e-10", 1e-10, 0), "fp64tc": ("fp64tc_tol1e-6", 1e-6, 2),
+         "fp64tc_1e-10": ("fp64tc_tol1e-10", 1e-10, 2)}
 
 
 def workload(name="adaptive3d"):
@@ -132,13 +133,15 @@ def whole_job_rate(points_per_replica, steps, world, seconds):
 
 
 def time_steps(plan, sigma, out, steps, warmup, flush):
-    """Per-step device times (ms) with an L2 flush before every step (not timed)."""
+    """Per-step device times (ms) with an L2 flush before every step (not timed).  The plan's
+    per-phase profile, when on, is reset after the warm-up so that it covers the timed steps."""
     import torch
     st = torch.cuda.current_stream()
     for _ in range(warmup):
         flush.zero_()
         plan(sigma, out=out)
     torch.cuda.synchronize()
+    plan.read_profile()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for e0, e1 in ev:
         flush.zero_()
@@ -162,19 +165,18 @@ def cpu_oracle_rate(w, budget_s=15.0, threads=0):
     m = int(np.clip(len(probe) * budget_s / t_probe, 8, n))
     sample = np.sort(rng.choice(n, size=m, replace=False))
     t0 = time.perf_counter()
-    oracle.box_fgt(w.d, w.p, w.delta, w.periodic, w.tree.level, w.tree.coord, w.sigma, targets=sample,
-                   threads=threads)
+    u = oracle.box_fgt(w.d, w.p, w.delta, w.periodic, w.tree.level, w.tree.coord, w.sigma, targets=sample,
+                       threads=threads)
     dt = time.perf_counter() - t0
     cores = threads if threads > 0 else oracle.default_threads()
-    return m * w.p ** w.d / dt, cores, m, dt
+    return m * w.p ** w.d / dt, cores, m, dt, sample, u
 
 
 def run_batched_and_serving(args, F, torch):
     """256 independent free-space transforms (d 2/3, depth 2-7, p 8/12/16, delta 1e-5..1e-1):
     one after another on one stream vs one batched graph launch, split form at tol 1e-6 (FP64
-    at 1e-6 too); then a Poisson-arrival serving run over the same requests."""
+    at 1e-6 too); then the serving runs."""
     import workloads as W
-    from paper_2305_07165_gb300 import serving as S
     ws = W.batched_configs(seed=0, n=256)
     npts = sum(w.n_points for w in ws)
     sig = [torch.from_numpy(w.sigma).cuda() for w in ws]
@@ -184,6 +186,10 @@ def run_batched_and_serving(args, F, torch):
     st = torch.cuda.current_stream()
     for name, prec in (("split_tol1e-6", F.PREC_SPLIT), ("fp64_tol1e-6", F.PREC_FP64)):
         plans = [F.Plan(w.d, w.p, w.delta, 1e-6, w.tree.level, w.tree.coord, prec=prec) for w in ws]
+        # launch shapes picked per transform by the library's autotuner before the graph is built
+        t0 = time.perf_counter()
+        knobs = [p.autotune(s, o, reps=2) for p, s, o in zip(plans, sig, out)]
+        tune_s = time.perf_counter() - t0
         batch = F.Batch(plans)
         reps = max(2, args.steps // 4)
         for _ in range(2):
@@ -203,28 +209,100 @@ def run_batched_and_serving(args, F, torch):
         torch.cuda.synchronize()
         t_serial = e0.elapsed_time(e1) / reps
         t_graph = e1.elapsed_time(e2) / reps
+        from collections import Counter
         res[name] = {"serial_ms": t_serial, "serial_points_per_s": npts / t_serial * 1e3,
-                     "batched_ms": t_graph, "batched_points_per_s": npts / t_graph * 1e3}
+                     "batched_ms": t_graph, "batched_points_per_s": npts / t_graph * 1e3,
+                     "autotune_s": tune_s,
+                     "autotuned": {k: dict(Counter(int(t[k]) for t in knobs))
+                                   for k in ("form_group", "eval_rows16", "eval_rows_large", "near_phase")}}
         batch.close()
         for p in plans:
             p.close()
-    # serving: Poisson arrivals (200 requests/s) of the same transforms, admitted by footprint
-    rate = 200.0
+    return res, run_serving(F, torch)
+
+
+def run_serving(F, torch):
+    """Serving: requests on 24 request geometries (d 2/3, free/periodic, tol 1e-6/1e-10, 2K to
+    1.1M points) with fresh densities, admitted by footprint, plans kept resident between
+    requests.  One pass over the geometries warms the plan cache; a burst of 96 requests gives
+    the saturation rate; then Poisson arrivals at 0.25, 0.5, 1 and 2 times that rate."""
+    import workloads as W
+    from paper_2305_07165_gb300 import serving as S
+    ws = W.serving_mix(seed=0, n=24)
     rng = np.random.default_rng(5)
-    srv = S.Server(hbm_budget_bytes=16 << 30, max_inflight=32).start()
-    t0 = time.perf_counter()
-    futs = []
-    for w in ws[:128]:
-        futs.append(srv.submit(S.Request(d=w.d, k=w.p, delta=w.delta, tol=1e-6, level=w.tree.level,
-                                         coord=w.tree.coord, sigma=w.sigma)))
-        time.sleep(rng.exponential(1.0 / rate))
-    for f in futs:
-        f.result(timeout=300)
+    srv = S.Server(hbm_budget_bytes=16 << 30, max_inflight=32, plan_cache_bytes=8 << 30).start()
+
+    def req(w):
+        return S.Request(d=w.d, k=w.p, delta=w.delta, tol=w.meta["tol"], level=w.tree.level, coord=w.tree.coord,
+                         sigma=w.sigma * float(rng.uniform(0.5, 1.5)), bc=int(w.periodic))
+
+    def run(n, rate):
+        srv.completed = []
+        hits0 = srv.cache_hits
+        picks = rng.integers(len(ws), size=n)
+        t0 = time.perf_counter()
+        futs = []
+        for i in picks:
+            futs.append(srv.submit(req(ws[i])))
+            if rate:
+                time.sleep(rng.exponential(1.0 / rate))
+        for f in futs:
+            f.result(timeout=600)
+        st = srv.stats(t0=t0)
+        st["plan_cache_hits"] = srv.cache_hits - hits0
+        return st
+
+    for f in [srv.submit(req(w)) for w in ws]:   # warm: every geometry planned once
+        f.result(timeout=600)
+    burst = run(96, None)
+    sat = burst["requests"] / (burst["points"] / burst["points_per_s"])
+    out = {"geometries": len(ws), "mix": "d 2/3, 3 in 10 periodic, 1 in 4 at tol 1e-10, delta log-U[1e-4,1e-2], "
+                                         f"{min(w.n_points for w in ws)}-{max(w.n_points for w in ws)} points",
+           "admission_budget_bytes": 16 << 30, "plan_cache_bytes": 8 << 30,
+           "saturation": dict(burst, requests_per_s=sat), "rate_sweep": {}}
+    for frac in (0.25, 0.5, 1.0, 2.0):
+        st = run(64, frac * sat)
+        st["arrival_rate_per_s"] = frac * sat
+        out["rate_sweep"][f"{frac:g}x"] = st
     srv.shutdown()
-    serving = srv.stats(t0=t0)
-    serving["arrival_rate_per_s"] = rate
-    serving["admission_budget_bytes"] = 16 << 30
-    return res, serving
+    return out
+
+
+def run_sweeps(args, F, torch, w_head, flush):
+    """The delta sweep of the 3D adaptive workload (delta 1e-4 and 1e-2 next to the headline's
+    1e-3) in every form, and the 3D periodic uniform workload (16.8M points) in split precision
+    at tol 1e-6 and FP64 at tol 1e-10.  Fewer steps than the headline (each row says how many)."""
+    out = {"delta_sweep": {}, "periodic3d": {}}
+    steps, warm = max(3, args.steps // 4), 2
+
+    def one(w, sig, outt, tol, prec):
+        plan = F.Plan(w.d, w.p, w.delta, tol, w.tree.level, w.tree.coord, bc=int(w.periodic), prec=prec)
+        info = plan.info()
+        t = time_steps(plan, sig, outt, steps, warm, flush)
+        plan.close()
+        ms = float(t.mean())
+        return {"ms_per_step": ms, "points_per_s": w.n_points / ms * 1e3, "steps": steps,
+                "cutoff_level": info["cutoff_level"], "n_f": info["n_f"]}
+
+    sig = torch.from_numpy(w_head.sigma).cuda()
+    o = torch.empty_like(sig)
+    import dataclasses
+    for delta in (1e-4, 1e-2):
+        wd = dataclasses.replace(w_head, delta=delta)
+        row = {}
+        for key in args.forms.split(","):
+            name, tol, prec = FORMS[key]
+            row[name] = one(wd, sig, o, tol, prec)
+        out["delta_sweep"][f"{delta:g}"] = row
+    del sig, o
+    wp = workload("periodic3d")
+    sig = torch.from_numpy(wp.sigma).cuda()
+    o = torch.empty_like(sig)
+    out["periodic3d"]["workload"] = workload_text(wp)
+    for key in ("split", "fp64_1e-10"):
+        name, tol, prec = FORMS[key]
+        out["periodic3d"][name] = one(wp, sig, o, tol, prec)
+    return out
 
 
 def metric_name(w):
@@ -284,8 +362,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="adaptive3d", choices=sorted(WORKLOADS))
     ap.add_argument("--no-batch", action="store_true", help="skip the batched and serving sections")
-    ap.add_argument("--forms", default="split,fp64,fp64_1e-10",
-                    help="comma list of split, fp64, fp64_1e-10; the first one is the headline")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the delta sweep and the periodic workload")
+    ap.add_argument("--forms", default="split,fp64,fp64_1e-10,fp64tc,fp64tc_1e-10",
+                    help="comma list of " + ", ".join(FORMS) + "; the first one is the headline")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -340,6 +419,9 @@ def main():
     batched = serving = None
     if not args.no_batch and rank == 0:
         batched, serving = run_batched_and_serving(args, F, torch)
+    sweeps = None
+    if not args.no_sweep and rank == 0:
+        sweeps = run_sweeps(args, F, torch, w, flush)
 
     # end to end through the host-buffer entry point (pinned host memory, copies timed)
     plan = head["plan"]
@@ -359,10 +441,16 @@ def main():
     line = None
     if rank == 0:
         cpu = None
+        err = None
         if not args.no_cpu_baseline and world == 1:
-            rate, cores, m, dt = cpu_oracle_rate(w)
+            rate, cores, m, dt, sample, u_or = cpu_oracle_rate(w)
             cpu = {"value": rate, "unit": "points/s", "cores": cores, "kind": "oracle",
                    "sample": f"{m} seeded target leaves of {w.tree.n_leaves} ({m * w.p ** w.d} points), {dt:.1f} s"}
+            # the headline form's result on the same sample, against the oracle (acceptance: 10 tol)
+            head["plan"](sigma, out=out)
+            u_gpu = out.cpu().numpy()[sample]
+            err = {"max_abs_over_max_u": float(np.abs(u_gpu - u_or).max() / np.abs(u_or).max()),
+                   "bound": 10 * head["tol"], "sample": cpu["sample"]}
         hr = results[head["name"]]
         line = {
             "metric": metric_name(w),
@@ -376,12 +464,14 @@ def main():
             "forms": results,
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "error_vs_oracle": err,
             "e2e": {"value": world * w.n_points * args.steps / e2e_s, "unit": "points/s",
                     "h2d_bytes_per_step": int(w.n_points * 8), "d2h_bytes_per_step": int(w.n_points * 8)},
             "gpu_launches": int(info["launches"] * args.steps),
             "clocks": clocks,
             "batched": batched,
             "serving": serving,
+            "sweeps": sweeps,
         }
         print(json.dumps(line))
     plan.close()

@@ -57,8 +57,12 @@ typedef enum { FGT_BC_FREE = 0, FGT_BC_PERIODIC = 1 } fgt_bc;
  * FGT_PREC_FP64: everything in FP64.
  * FGT_PREC_SPLIT: contractions and stored expansions in FP32 (accepted only
  *   when tol >= 1e-7); the near-field 1D tables, the tables' construction and
- *   the final per-leaf accumulation stay FP64. */
-typedef enum { FGT_PREC_FP64 = 0, FGT_PREC_SPLIT = 1 } fgt_prec;
+ *   the final per-leaf accumulation stay FP64.
+ * FGT_PREC_FP64_TC: as FGT_PREC_FP64, with the 3D form's last contraction and
+ *   the 3D evaluation's first two contractions on the FP64 tensor cores (DMMA);
+ *   FP64 products throughout, only the order of the sums differs.  2D plans and
+ *   the kernels without a DMMA form run as FGT_PREC_FP64. */
+typedef enum { FGT_PREC_FP64 = 0, FGT_PREC_SPLIT = 1, FGT_PREC_FP64_TC = 2 } fgt_prec;
 
 /* How the plane-wave hierarchy of Algorithm 4 is executed.
  * FGT_MODE_FUSED (default): the child-to-parent (T_c->p) and parent-to-child
@@ -198,6 +202,28 @@ fgt_status fgt_execute_batch(fgt_plan *const *plans, const double *const *sigma_
  * ms[0..5] and the number of executions covered, and starts a new accumulation. */
 fgt_status fgt_plan_set_profiling(fgt_plan *plan, int on);
 fgt_status fgt_plan_read_profile(fgt_plan *plan, double *ms, int *n_transforms);
+
+/* Launch-shape knobs of a plan and the autotuner that picks them.
+ *   form_group:      at most this many same-size blocks of one anchor per form CTA (1..8)
+ *   eval_rows16:     split precision, 3D: rows of a K = 16 block per evaluation CTA (4, 8, 16)
+ *   eval_rows_large: split precision, 3D: rows of a K > 16 block per evaluation CTA (4, 8)
+ *   near_phase:      the near field runs on a second stream, forked before the form (0), the
+ *                    gather (2) or the evaluation (4)
+ *   ms:              the step time the autotuner measured for the chosen knobs (0 if never tuned)
+ * None of them changes what is computed, only the launch shapes (results differ at most by
+ * the order of floating-point sums).  fgt_plan_autotune times the plan on the caller's
+ * sigma_dev / u_dev on `stream` (one warm-up and `reps` timed executions per candidate,
+ * coordinate descent over the knobs that apply to the plan), keeps the fastest setting, and
+ * writes it to *out (may be NULL).  It synchronises `stream`; u_dev holds a valid result
+ * afterwards.  fgt_plan_set_tuning applies known settings (e.g. from an earlier run). */
+typedef struct {
+  int32_t form_group, eval_rows16, eval_rows_large, near_phase;
+  double ms;
+} fgt_tuning;
+fgt_status fgt_plan_autotune(fgt_plan *plan, const double *sigma_dev, double *u_dev, void *stream, int reps,
+                             fgt_tuning *out);
+fgt_status fgt_plan_get_tuning(const fgt_plan *plan, fgt_tuning *out);
+fgt_status fgt_plan_set_tuning(fgt_plan *plan, const fgt_tuning *t);
 
 void fgt_destroy(fgt_plan *plan);
 

@@ -16,12 +16,12 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Plan", "FGTError", "lib", "BC_FREE", "BC_PERIODIC", "PREC_FP64", "PREC_SPLIT", "MODE_FUSED",
+__all__ = ["Plan", "FGTError", "Tuning", "lib", "BC_FREE", "BC_PERIODIC", "PREC_FP64", "PREC_SPLIT", "PREC_FP64_TC", "MODE_FUSED",
            "MODE_HIERARCHICAL", "gauss_legendre", "params", "nf_for_range", "legendre_gauss_integrals",
            "spherical_bessel", "legendre_fourier_integrals", "analyze", "HostPlan", "Batch"]
 
 BC_FREE, BC_PERIODIC = 0, 1
-PREC_FP64, PREC_SPLIT = 0, 1
+PREC_FP64, PREC_SPLIT, PREC_FP64_TC = 0, 1, 2
 MODE_FUSED, MODE_HIERARCHICAL = 0, 1
 _STATUS = {0: "FGT_OK", 1: "FGT_ERR_ARG", 2: "FGT_ERR_TREE", 3: "FGT_ERR_OOM", 4: "FGT_ERR_CUDA",
            5: "FGT_ERR_TIMEOUT", 6: "FGT_ERR_STATE"}
@@ -46,6 +46,15 @@ class PlanInfo(ctypes.Structure):
                                               "n_form_blocks", "n_direct_pairs", "n_gather_pairs", "form_flops",
                                               "eval_flops", "gather_flops", "direct_flops", "device_bytes")] + \
                [("prec", ctypes.c_int32), ("mode", ctypes.c_int32), ("launches", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class Tuning(ctypes.Structure):
+    """Launch-shape knobs of a plan (fgt_tuning)."""
+    _fields_ = [(n, ctypes.c_int32) for n in ("form_group", "eval_rows16", "eval_rows_large", "near_phase")] + \
+               [("ms", ctypes.c_double)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -87,6 +96,9 @@ def lib():
                 getattr(L, name).restype = ctypes.c_int
             L.fgt_plan_set_profiling.argtypes = [vp, i32]
             L.fgt_plan_read_profile.argtypes = [vp, vp, vp]
+            L.fgt_plan_autotune.argtypes = [vp, vp, vp, vp, i32, ctypes.POINTER(Tuning)]
+            L.fgt_plan_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+            L.fgt_plan_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
             L.fgt_destroy.argtypes = [vp]
             L.fgt_destroy.restype = None
             L.fgt_last_error.restype = ctypes.c_char_p
@@ -101,7 +113,8 @@ def lib():
                          "fgt_plan_set_mode", "fgt_execute", "fgt_execute_async", "fgt_execute_host",
                          "fgt_gauss_legendre", "fgt_params", "fgt_legendre_gauss_integrals",
                          "fgt_spherical_bessel", "fgt_legendre_fourier_integrals", "fgt_plan_set_profiling",
-                         "fgt_plan_read_profile"):
+                         "fgt_plan_read_profile", "fgt_plan_autotune", "fgt_plan_get_tuning",
+                         "fgt_plan_set_tuning"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -232,6 +245,32 @@ class Plan:
         return out
 
     __call__ = execute
+
+    def autotune(self, sigma, out=None, reps=3, stream=None) -> dict:
+        """Time the plan's launch-shape knobs on this input (fgt_plan_autotune) and keep the
+        fastest; returns the chosen knobs and the step time measured with them."""
+        import torch
+        self._check_tensor(sigma, "sigma")
+        if out is None:
+            out = torch.empty_like(sigma)
+        self._check_tensor(out, "out")
+        s = stream if stream is not None else torch.cuda.current_stream(sigma.device)
+        t = Tuning()
+        _check(lib().fgt_plan_autotune(self._h, ctypes.c_void_p(sigma.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                       ctypes.c_void_p(s.cuda_stream), int(reps), ctypes.byref(t)))
+        return t.as_dict()
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        _check(lib().fgt_plan_get_tuning(self._h, ctypes.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, **knobs):
+        t = Tuning()
+        _check(lib().fgt_plan_get_tuning(self._h, ctypes.byref(t)))
+        for k, v in knobs.items():
+            setattr(t, k, v)
+        _check(lib().fgt_plan_set_tuning(self._h, ctypes.byref(t)))
 
     def execute_noalloc(self, sigma, out, stream=None):
         """Same transform through fgt_execute_noalloc: the expansions live in the library's fixed

@@ -29,6 +29,7 @@ struct ShiftStep {
 struct ExecDesc {
   int d = 0, k = 0, n1 = 0, nh = 0;
   int prec = 0;                      // 0: FP64 expansions, 1: FP32 expansions
+  int tc64 = 0;                      // FP64 contractions on the tensor cores (DMMA) where a kernel has them
   int fourier = 0;                   // 1: no out->in gather, evaluation reads the outgoing slot
   int64_t slot_size = 0;             // complex elements per expansion slot
   int64_t n_phi_slots = 0, n_psi_slots = 0;

@@ -363,7 +363,47 @@ constexpr int kSc = 4;
 
 __host__ __device__ inline int pad_gk(int GK) { return GK + 1; }  // row stride of Z2 (bank spread)
 
-template <typename R>
+// ----------------------------------------------------------------------------- FP64 tensor-core tiles
+//
+// FP64 on the tensor cores: mma.m8n8k4 with f64 operands and accumulators (exact FP64 products,
+// only the summation order differs from the CUDA-core kernels).  A complex product C = A B is
+// embedded in real ones over an interleaved (re, im) contraction index (see the 3xTF32 helpers
+// below for the same embedding).  Fragments, g = lane / 4, t = lane % 4: a = A[g][t],
+// b = B[t][g], c = {C[g][2t], C[g][2t+1]}.
+__device__ __forceinline__ void dmma(double (&c)[2], double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+               : "+d"(c[0]), "+d"(c[1])
+               : "d"(a), "d"(b));
+}
+
+// One warp: rows i0 .. i0+7 of C (+)= A B for NBLK blocks of 8 columns from j0, A [arows][kc]
+// (row stride lda), B [kc][ncols] (row stride ldb), complex FP64.  acc[2 b] holds the real parts
+// of column block b, acc[2 b + 1] the imaginary parts.
+template <int NBLK>
+__device__ __forceinline__ void zgemm8_dmma(double (&acc)[2 * NBLK][2], const double2 *A, int lda, int arows, int i0,
+                                            const double2 *B, int ldb, int ncols, int j0, int kc) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int row = i0 + g;
+  for (int k0 = 0; k0 < 2 * kc; k0 += 4) {
+    const int kr = k0 + t, J = kr >> 1, part = kr & 1;
+    const bool kin = J < kc;
+    double a = 0.0;
+    if (kin && row < arows) {
+      const double2 v = A[(size_t)row * lda + J];
+      a = part ? v.y : v.x;
+    }
+#pragma unroll
+    for (int b = 0; b < NBLK; ++b) {
+      const int col = j0 + b * 8 + g;
+      double2 f = make_double2(0.0, 0.0);
+      if (kin && col < ncols) f = B[(size_t)J * ldb + col];
+      dmma(acc[2 * b], a, part ? -f.y : f.x);
+      dmma(acc[2 * b + 1], a, part ? f.x : f.y);
+    }
+  }
+}
+
+template <typename R, bool TC>  // TC (FP64 only): stage 3 on the tensor cores (DMMA)
 __global__ void __launch_bounds__(256) form3_kernel(const Block *__restrict__ blocks, const int32_t *__restrict__ gptr,
                                                     const int64_t *__restrict__ bleaves,
                                                     const double *__restrict__ sigma,
@@ -476,7 +516,31 @@ __global__ void __launch_bounds__(256) form3_kernel(const Block *__restrict__ bl
   __syncthreads();
   // stage 3: out[s0+q][m2][m1] += sum_{gJ} Z2[q][m2][gJ] F1t[gJ][m1]; 4 x 4 tiles over (m2, m1)
   C *out = phi + (int64_t)B0.slot * slot_size;
-  {
+  if constexpr (TC && sizeof(R) == 8) {
+    // one warp per (plane, 8 rows of m2, 32 columns of m1)
+    const int mt = (n1 + 7) / 8, cb = (n1 + 31) / 32;
+    for (int job = threadIdx.x >> 5; job < ns * mt * cb; job += blockDim.x >> 5) {
+      const int c0 = job % cb, rest = job / cb, bm = rest % mt, q = rest / mt;
+      double acc[8][2];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = 0.0;
+      zgemm8_dmma<4>(acc, Z2 + (size_t)q * n1 * ldz, ldz, n1, bm * 8, F1t, n1, n1, c0 * 32, GK);
+      const int lane = threadIdx.x & 31, m2 = bm * 8 + (lane >> 2);
+      C *o = out + (int64_t)(s0 + q) * n1 * n1;
+      if (m2 < n1) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const int m1 = c0 * 32 + b * 8 + 2 * (lane & 3) + c;
+            if (m1 < n1) {
+              atomicAdd(&o[m2 * n1 + m1].x, acc[2 * b][c]);
+              atomicAdd(&o[m2 * n1 + m1].y, acc[2 * b + 1][c]);
+            }
+          }
+      }
+    }
+  } else {
     const int tm = (n1 + 3) / 4, ntile = ns * tm * tm;
     for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
       const int b1 = t % tm, rest = t / tm, b2 = rest % tm, q = rest / tm;
@@ -866,7 +930,7 @@ __global__ void __launch_bounds__(256, BIG ? 2 : (NBT > 8 ? 2 : 3)) form4_kernel
 // A CTA evaluates KM rows (along the last axis) of one block, all of it when K <= KM: the
 // anchor's incoming expansion is read once per CTA (each thread keeps KM accumulators for its
 // mode column), then the two remaining contractions run from shared memory.
-template <int D, typename R, int KM>
+template <int D, typename R, int KM, bool TC = false>  // TC (FP64, 3D): stages 1-2 on the tensor cores
 __global__ void __launch_bounds__(256) eval2_kernel(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
                                                     const typename C2T<R>::T *__restrict__ Ef,
                                                     const typename C2T<R>::T *__restrict__ Eh,
@@ -900,6 +964,27 @@ __global__ void __launch_bounds__(256) eval2_kernel(const Block *__restrict__ bl
   __syncthreads();
   // Y1[r][mode] = sum_{m_d} Ed[r][m_d] psi[m_d][mode]; psi fetched 8 planes at a time so that
   // eight loads are in flight per thread
+  if constexpr (TC && sizeof(R) == 8 && D == 3) {
+    // one warp per (8 rows, 32 modes): A = Ed, B = psi straight from the slot
+    const int mt = (nr + 7) / 8, cb = (nn + 31) / 32;
+    for (int job = threadIdx.x >> 5; job < mt * cb; job += blockDim.x >> 5) {
+      const int c0 = job % cb, bm = job / cb;
+      double acc[8][2];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = 0.0;
+      zgemm8_dmma<4>(acc, Ed, nh, nr, bm * 8, ps, nn, nn, c0 * 32, nh);
+      const int lane = threadIdx.x & 31, r = bm * 8 + (lane >> 2);
+      if (r < nr) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const int mode = c0 * 32 + b * 8 + 2 * (lane & 3) + c;
+            if (mode < nn) Y1[(size_t)r * nn + mode] = C{acc[2 * b][c], acc[2 * b + 1][c]};
+          }
+      }
+    }
+  } else
   for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
     R ar[KM], ai[KM];
 #pragma unroll
@@ -927,7 +1012,27 @@ __global__ void __launch_bounds__(256) eval2_kernel(const Block *__restrict__ bl
     // Y2[r][I2][m1] = sum_m2 E2[I2][m2] Y1[r][m2][m1]; 4 x 4 register tiles over (I2, m1) when
     // there are enough tiles to occupy the CTA, else one output per thread
     const int tI = (K + 3) / 4, tm = (n1 + 3) / 4;
-    if (nr * tI * tm < (int)blockDim.x / 2) {
+    if constexpr (TC && sizeof(R) == 8) {
+      // one warp per (row r, 8 rows of I2, 32 columns of m1): A = E2, B = Y1[r]
+      const int mt = (K + 7) / 8, cb = (n1 + 31) / 32;
+      for (int job = threadIdx.x >> 5; job < nr * mt * cb; job += blockDim.x >> 5) {
+        const int c0 = job % cb, rest = job / cb, bm = rest % mt, r = rest / mt;
+        double acc[8][2];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = 0.0;
+        zgemm8_dmma<4>(acc, E2, n1, K, bm * 8, Y1 + (size_t)r * nn, n1, n1, c0 * 32, n1);
+        const int lane = threadIdx.x & 31, I2 = bm * 8 + (lane >> 2);
+        if (I2 < K) {
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              const int m1 = c0 * 32 + b * 8 + 2 * (lane & 3) + c;
+              if (m1 < n1) Y2[((size_t)r * K + I2) * n1 + m1] = C{acc[2 * b][c], acc[2 * b + 1][c]};
+            }
+        }
+      }
+    } else if (nr * tI * tm < (int)blockDim.x / 2) {
       for (int e = threadIdx.x; e < nr * K * n1; e += blockDim.x) {
         const int m1 = e % n1, rest = e / n1, I2 = rest % K, r = rest / K;
         const C *ep = E2 + (size_t)I2 * n1;
@@ -1621,10 +1726,11 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
             e.f2_blocks, e.f2_gptr + lr.first, e.block_leaves, sigma, e.sigp, reinterpret_cast<const float2 *>(e.Ff),
             reinterpret_cast<const float2 *>(e.Fh), reinterpret_cast<float2 *>(phi), e.k, n1, nh, ss);
       } else if (D == 3) {
-        if ((err = cudaFuncSetAttribute(form3_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)lr.smem)) != cudaSuccess)
+        auto f3 = lr.tensor ? form3_kernel<R, true> : form3_kernel<R, false>;
+        if ((err = cudaFuncSetAttribute(f3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) !=
+            cudaSuccess)
           return err;
-        form3_kernel<R><<<dim3((unsigned)lr.count, (unsigned)((nh + kSc - 1) / kSc)), 256, lr.smem, st>>>(
+        f3<<<dim3((unsigned)lr.count, (unsigned)((nh + kSc - 1) / kSc)), 256, lr.smem, st>>>(
             e.f2_blocks, e.f2_gptr + lr.first, e.block_leaves, sigma, reinterpret_cast<const C *>(e.Ff),
             reinterpret_cast<const C *>(e.Fh), phi, e.k, n1, nh, ss);
       } else {
@@ -1698,7 +1804,12 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
       continue;
     }
     // lr.rows rows of a block per CTA
-    auto kern = lr.rows <= 4 ? eval2_kernel<D, R, 4> : lr.rows <= 8 ? eval2_kernel<D, R, 8> : eval2_kernel<D, R, 16>;
+    auto kern = lr.tensor ? (lr.rows <= 4   ? eval2_kernel<D, R, 4, true>
+                             : lr.rows <= 8 ? eval2_kernel<D, R, 8, true>
+                                            : eval2_kernel<D, R, 16, true>)
+                          : (lr.rows <= 4   ? eval2_kernel<D, R, 4>
+                             : lr.rows <= 8 ? eval2_kernel<D, R, 8>
+                                            : eval2_kernel<D, R, 16>);
     const int rows = lr.rows <= 4 ? 4 : lr.rows <= 8 ? 8 : 16;
     const unsigned chunks = (unsigned)((lr.K + rows - 1) / rows);
     if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) !=

@@ -88,6 +88,10 @@ struct DevPack {
 
 struct fgt_plan {
   int d = 0, k = 0, bc = 0, prec = FGT_PREC_FP64, mode = FGT_MODE_FUSED;
+  bool f32() const { return prec == FGT_PREC_SPLIT; }  // FP32 expansions and contractions
+  // launch-shape knobs (fgt_plan_autotune picks them by timing; these defaults measured best
+  // on the 3D adaptive benchmark workload)
+  fgt_tuning tune{8, 8, 4, 2, 0.0};  // form_group, eval_rows16, eval_rows_large, near_phase, ms
   double delta = 0, tol = 0, eps_pw = 0;
   // parameters
   int lc = 0, fourier = 0, n_f = 0, n_p = 0, M = 0, n1 = 0, nh = 0, lmax = 0;
@@ -411,7 +415,8 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   const bool hier = P.mode == FGT_MODE_HIERARCHICAL && !P.fourier;
   DevPack pack;
   fgt::ExecDesc ex;
-  ex.d = d; ex.k = k; ex.n1 = n1; ex.nh = nh; ex.prec = P.prec; ex.fourier = P.fourier;
+  ex.d = d; ex.k = k; ex.n1 = n1; ex.nh = nh; ex.prec = P.f32() ? 1 : 0; ex.fourier = P.fourier;
+  ex.tc64 = P.prec == FGT_PREC_FP64_TC ? 1 : 0;
   ex.slot_size = (int64_t)nh * (d == 3 ? (int64_t)n1 * n1 : (int64_t)n1);
 
   // ---- slots and anchors
@@ -445,8 +450,8 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   while (((2 << dlcap) * k) <= 64) ++dlcap;
   auto fits = [&](int dl) {
     const int K = (1 << dl) * k;
-    return fgt::form_smem_bytes(d, K, n1, P.prec) <= (size_t)smax &&
-           fgt::eval_smem_bytes(d, K, n1, P.prec) <= (size_t)smax;
+    return fgt::form_smem_bytes(d, K, n1, P.f32()) <= (size_t)smax &&
+           fgt::eval_smem_bytes(d, K, n1, P.f32()) <= (size_t)smax;
   };
   while (dlcap > 0 && !fits(dlcap)) --dlcap;
   if (!fits(0)) return fail(FGT_ERR_ARG, "expansion too large for shared memory (n_f too big for this k)");
@@ -550,7 +555,7 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   std::vector<int32_t> f2ptr(1, 0);
   int Kf1 = 0, Ke1 = 0;
   {
-    const size_t rsz = P.prec ? sizeof(float) : sizeof(double), csz = sizeof(C);
+    const size_t rsz = P.f32() ? sizeof(float) : sizeof(double), csz = sizeof(C);
     const size_t three_per_sm = 72 * 1024;
     // 3D uses the register-tiled kernel (planes in chunks of 4), 2D the plain grouped one
     // split precision in 3D: the last contraction of the form and the first of the evaluation
@@ -570,7 +575,7 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
     auto gmax = [&](int K) {
       int G = 0;
       if (K > 16) return big_form(K) ? 1 : 0;  // staging sigma would leave one CTA per SM
-      for (int g = 1; g <= 8; ++g)
+      for (int g = 1; g <= P.tune.form_group; ++g)
         if (gbytes(g, K) <= three_per_sm) G = g;
       if (G == 0 && gbytes(1, K) <= (size_t)smax) G = 1;
       return G;
@@ -607,16 +612,18 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
       lr.K = K;
       lr.big = K > 16 ? 1 : 0;
       lr.smem = lr.big ? fgt::form4b_bytes(K, n1) : gbytes(G, K);
-      lr.tensor = tensor_form(K) ? 1 : 0;
+      lr.tensor = (tensor_form(K) || (ex.tc64 && d == 3)) ? 1 : 0;
       ex.f2_ranges.push_back(lr);
     }
     // evaluation: whole-block kernel for K <= 16 when it fits, one launch per K; in split
     // precision (3D) larger blocks too, a few rows per CTA
-    // rows per CTA (split precision, 3D): 8 for K = 16 and 4 for larger blocks measured fastest
-    // on GB300 (more resident CTAs outweigh reading the anchor's expansion two or more times)
-    const int rows16 = 8, rows32 = 4;
+    // rows per CTA (split precision, 3D): by default 8 for K = 16 and 4 for larger blocks, which
+    // measured fastest on GB300 (more resident CTAs outweigh reading the anchor's expansion two or
+    // more times)
+    auto norm_rows = [](int r) { return r <= 4 ? 4 : r <= 8 ? 8 : 16; };  // the kernel's instantiations
+    const int rows16 = norm_rows(P.tune.eval_rows16), rows32 = norm_rows(P.tune.eval_rows_large);
     for (const fgt::Block &b : sorted) {
-      const bool chunked = b.K > 16 && d == 3 && P.prec == FGT_PREC_SPLIT;
+      const bool chunked = b.K > 16 && d == 3 && (P.prec == FGT_PREC_SPLIT || ex.tc64);
       const int rows = b.K <= 8 ? 8 : b.K <= 16 ? (P.prec == FGT_PREC_SPLIT && d == 3 ? rows16 : 16) : rows32;
       const size_t eb = (tensor_eval && !chunked) ? fgt::eval3_bytes(b.K, n1, nh)
                                                   : fgt::eval2_bytes(d, b.K, n1, nh, csz, rows);
@@ -628,7 +635,7 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
           lr.K = b.K;
           lr.rows = rows;
           lr.smem = eb;
-          lr.tensor = (tensor_eval && !chunked) ? 1 : 0;
+          lr.tensor = ((tensor_eval && !chunked) || (ex.tc64 && d == 3)) ? 1 : 0;
           ex.e2_ranges.push_back(lr);
         }
         e2.push_back(b);
@@ -1022,9 +1029,9 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
       if (e != cudaSuccess) return cuda_fail(e, "near-field stream");
     }
     ex.aux = P.aux;
-    // forked before the gather: the near field's FP64 work then overlaps the L2-bound gather and
-    // the evaluation rather than the form, which measured fastest of the three fork points
-    ex.near_phase = 2;
+    // default: forked before the gather, so that the near field's FP64 work overlaps the L2-bound
+    // gather and the evaluation rather than the form (fastest of the three fork points measured)
+    ex.near_phase = (P.tune.near_phase == 0 || P.tune.near_phase == 4) ? P.tune.near_phase : 2;
     ex.fork = P.fork;
     ex.join = P.join;
   }
@@ -1050,7 +1057,8 @@ fgt_status create_impl(int d, double delta, double tol, double eps_pw, int bc, i
   if (!(delta > 0) || !std::isfinite(delta)) return fail(FGT_ERR_ARG, "delta must be positive");
   if (!(tol >= 1e-14 && tol <= 1e-1)) return fail(FGT_ERR_ARG, "tol must be in [1e-14, 1e-1]");
   if (bc != FGT_BC_FREE && bc != FGT_BC_PERIODIC) return fail(FGT_ERR_ARG, "bad bc");
-  if (prec != FGT_PREC_FP64 && prec != FGT_PREC_SPLIT) return fail(FGT_ERR_ARG, "bad precision");
+  if (prec != FGT_PREC_FP64 && prec != FGT_PREC_SPLIT && prec != FGT_PREC_FP64_TC)
+    return fail(FGT_ERR_ARG, "bad precision");
   if (prec == FGT_PREC_SPLIT && tol < 1e-7) return fail(FGT_ERR_ARG, "split precision needs tol >= 1e-7");
   if (mode != FGT_MODE_FUSED && mode != FGT_MODE_HIERARCHICAL) return fail(FGT_ERR_ARG, "bad mode");
   fgt_plan *P = new (std::nothrow) fgt_plan();
@@ -1200,7 +1208,8 @@ fgt_status fgt_plan_create(int d, double delta, double tol, int bc, const fgt_tr
 
 fgt_status fgt_plan_set_precision(fgt_plan *plan, int prec) {
   if (!plan) return fail(FGT_ERR_ARG, "plan is NULL");
-  if (prec != FGT_PREC_FP64 && prec != FGT_PREC_SPLIT) return fail(FGT_ERR_ARG, "bad precision");
+  if (prec != FGT_PREC_FP64 && prec != FGT_PREC_SPLIT && prec != FGT_PREC_FP64_TC)
+    return fail(FGT_ERR_ARG, "bad precision");
   if (prec == FGT_PREC_SPLIT && plan->tol < 1e-7) return fail(FGT_ERR_ARG, "split precision needs tol >= 1e-7");
   if (plan->prec != prec) { plan->prec = prec; plan->dirty = true; }
   return FGT_OK;
@@ -1263,6 +1272,96 @@ fgt_status fgt_execute_async(fgt_plan *plan, const double *sigma_dev, double *u_
   return FGT_OK;
 }
 
+fgt_status fgt_plan_get_tuning(const fgt_plan *plan, fgt_tuning *out) {
+  if (!plan || !out) return fail(FGT_ERR_ARG, "NULL argument");
+  *out = plan->tune;
+  return FGT_OK;
+}
+
+fgt_status fgt_plan_set_tuning(fgt_plan *plan, const fgt_tuning *t) {
+  if (!plan || !t) return fail(FGT_ERR_ARG, "NULL argument");
+  if (t->eval_rows16 < 1 || t->eval_rows_large < 1 || t->form_group < 1 || t->form_group > 8 ||
+      (t->near_phase != 0 && t->near_phase != 2 && t->near_phase != 4))
+    return fail(FGT_ERR_ARG, "tuning value out of range");
+  const double ms = plan->tune.ms;
+  plan->tune = *t;
+  plan->tune.ms = ms;
+  plan->dirty = true;
+  return FGT_OK;
+}
+
+fgt_status fgt_plan_autotune(fgt_plan *plan, const double *sigma_dev, double *u_dev, void *stream, int reps,
+                             fgt_tuning *out) {
+  if (!plan || !sigma_dev || !u_dev) return fail(FGT_ERR_ARG, "NULL argument");
+  if (plan->host_only) return fail(FGT_ERR_STATE, "host-only plan cannot execute");
+  if (reps < 1) reps = 3;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_fail(ce, "autotune events");
+  }
+  const bool prof = plan->profiling;
+  plan->profiling = false;
+  // one timing: re-plan with the candidate knobs, one warm-up, then reps executions
+  auto time_it = [&](double *ms) -> fgt_status {
+    plan->dirty = true;
+    fgt_status s = fgt_execute_async(plan, sigma_dev, u_dev, stream);
+    if (s != FGT_OK) return s;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && s == FGT_OK; ++r) s = fgt_execute_async(plan, sigma_dev, u_dev, stream);
+    cudaEventRecord(e1, st);
+    if (s != FGT_OK) return s;
+    cudaError_t c = cudaEventSynchronize(e1);
+    float v = 0.f;
+    if (c == cudaSuccess) c = cudaEventElapsedTime(&v, e0, e1);
+    if (c != cudaSuccess) return cuda_fail(c, "autotune timing");
+    *ms = v / reps;
+    return FGT_OK;
+  };
+  // coordinate descent, one pass, over the knobs that can matter for this plan
+  fgt_tuning best = plan->tune;
+  double best_ms = 0.0;
+  fgt_status s = time_it(&best_ms);
+  const bool split3 = plan->d == 3 && plan->prec == FGT_PREC_SPLIT;
+  struct Knob { int fgt_tuning::*field; std::vector<int> values; bool on; };
+  const Knob knobs[] = {
+      {&fgt_tuning::form_group, {2, 4, 8}, plan->mode == FGT_MODE_FUSED},
+      {&fgt_tuning::eval_rows16, {4, 8, 16}, split3},
+      {&fgt_tuning::eval_rows_large, {4, 8}, split3},
+      {&fgt_tuning::near_phase, {0, 2, 4}, plan->n_near_pairs > 0},
+  };
+  for (const Knob &kb : knobs) {
+    if (s != FGT_OK || !kb.on) continue;
+    for (int v : kb.values) {
+      if (v == best.*kb.field) continue;
+      plan->tune = best;
+      plan->tune.*kb.field = v;
+      double ms = 0.0;
+      s = time_it(&ms);
+      if (s != FGT_OK) break;
+      if (ms < best_ms) { best_ms = ms; best = plan->tune; }
+    }
+  }
+  plan->tune = best;
+  plan->tune.ms = best_ms;
+  plan->dirty = true;
+  plan->profiling = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != FGT_OK) return s;
+  try {
+    s = prepare(*plan);  // ready to execute with the chosen knobs
+  } catch (...) {
+    return fail(FGT_ERR_OOM, "host allocation");
+  }
+  if (s != FGT_OK) return s;
+  if (out) *out = plan->tune;
+  return FGT_OK;
+}
+
 fgt_status fgt_plan_set_profiling(fgt_plan *plan, int on) {
   if (!plan) return fail(FGT_ERR_ARG, "plan is NULL");
   plan->profiling = on != 0;
@@ -1294,7 +1393,7 @@ fgt_status fgt_execute_noalloc(fgt_plan *plan, const double *sigma_dev, double *
   if (plan->host_only) return fail(FGT_ERR_STATE, "host-only plan cannot execute");
   // re-planning would allocate: the plan must already be prepared for its mode and precision
   if (plan->dirty) return fail(FGT_ERR_STATE, "plan changed since it was prepared; run fgt_plan_get_info first");
-  const size_t c = plan->prec ? 8 : 16;
+  const size_t c = plan->f32() ? 8 : 16;
   const size_t phi = c * (size_t)plan->ex.slot_size * (size_t)plan->ex.n_phi_slots;
   const size_t psi = c * (size_t)plan->ex.slot_size * (size_t)plan->ex.n_psi_slots;
   if (((phi + 255) & ~(size_t)255) + psi > fgt::kNoallocScratchBytes)

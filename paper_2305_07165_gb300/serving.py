@@ -10,14 +10,23 @@ launches to finish.  Completed requests free their memory, which admits the
 next ones.  Trees, tables and expansions stay resident on the device for the
 life of a request; results come back to pinned host memory.
 
+Plans outlive their requests in a cache keyed by the request's geometry and
+parameters (tree, k, delta, tol, boundary condition, precision): a request on a
+geometry seen before reuses an idle resident plan -- its tables, lists and
+expansion workspace stay on the device -- and skips host planning.  The cache
+has its own device-memory budget; idle plans beyond it are released, least
+recently used first.
+
 Reports per-request latency (arrival -> result on the host) and the points/s
 achieved over the run.
 """
 from __future__ import annotations
 
+import hashlib
 import queue
 import threading
 import time
+from collections import OrderedDict
 from concurrent.futures import Future, ThreadPoolExecutor
 from dataclasses import dataclass, field
 
@@ -41,11 +50,19 @@ class Request:
     t_arrival: float = 0.0
     t_done: float = 0.0
     footprint: int = 0
+    cached: object = None           # an idle resident plan for this geometry, when one was free
     future: Future = field(default_factory=Future)
 
     @property
     def n_points(self):
         return int(self.sigma.size)
+
+    def key(self):
+        """Geometry and parameters that determine the plan (not the density)."""
+        h = hashlib.blake2b(digest_size=16)
+        h.update(np.ascontiguousarray(self.level, dtype=np.int32).tobytes())
+        h.update(np.ascontiguousarray(self.coord, dtype=np.int32).tobytes())
+        return (self.d, self.k, float(self.delta), float(self.tol), int(self.bc), int(self.prec), h.hexdigest())
 
 
 class Server:
@@ -53,12 +70,16 @@ class Server:
     one stream per in-flight request, completion by CUDA events."""
 
     def __init__(self, hbm_budget_bytes: int, max_inflight: int = 32, planner_threads: int = 4,
-                 device: int = 0):
+                 device: int = 0, plan_cache_bytes: int = 4 << 30):
         import torch
         self.torch = torch
         self.device = device
         self.budget = int(hbm_budget_bytes)
         self.used = 0
+        self.cache_budget = int(plan_cache_bytes)
+        self.cache: "OrderedDict[tuple, list]" = OrderedDict()   # key -> idle plans (LRU order)
+        self.cache_bytes = 0
+        self.cache_hits = 0
         self.max_inflight = max_inflight
         self.pending: "queue.Queue[Request]" = queue.Queue()
         self.pool = ThreadPoolExecutor(max_workers=planner_threads)
@@ -78,9 +99,19 @@ class Server:
             self.next_id += 1
         if req.prec is None:
             req.prec = PREC_SPLIT if req.tol >= 1e-7 else PREC_FP64
-        info = analyze(req.d, req.k, req.delta, req.tol, req.level, req.coord, bc=req.bc, prec=req.prec)
-        req.footprint = int(info["device_bytes"]) + 2 * 8 * req.n_points
+        with self.lock:
+            req.cached = self._cache_take(req.key())
+        if req.cached is not None:
+            # the plan is already resident (and counted in the cache): only sigma and u to place
+            req.footprint = 2 * 8 * req.n_points
+        else:
+            info = analyze(req.d, req.k, req.delta, req.tol, req.level, req.coord, bc=req.bc, prec=req.prec)
+            req.footprint = int(info["device_bytes"]) + 2 * 8 * req.n_points
         if req.footprint > self.budget:
+            if req.cached is not None:
+                with self.lock:
+                    self._cache_put(req.key(), req.cached)
+                req.cached = None
             req.future.set_exception(MemoryError(f"request needs {req.footprint} bytes, budget {self.budget}"))
             return req.future
         self.pending.put(req)
@@ -94,12 +125,48 @@ class Server:
         self.stop = True
         self.thread.join()
         self.pool.shutdown()
+        with self.lock:
+            for plans in self.cache.values():
+                for p in plans:
+                    p.close()
+            self.cache.clear()
+            self.cache_bytes = 0
+
+    # ---------------------------------------------------------------- plan cache
+    def _cache_take(self, key):
+        plans = self.cache.get(key)
+        if not plans:
+            return None
+        plan = plans.pop()
+        if not plans:
+            del self.cache[key]
+        self.cache_bytes -= plan.device_bytes()
+        self.cache_hits += 1
+        return plan
+
+    def _cache_put(self, key, plan):
+        nb = plan.device_bytes()
+        if nb > self.cache_budget:
+            plan.close()
+            return
+        while self.cache_bytes + nb > self.cache_budget and self.cache:
+            old_key, plans = next(iter(self.cache.items()))     # least recently used
+            victim = plans.pop(0)
+            if not plans:
+                del self.cache[old_key]
+            self.cache_bytes -= victim.device_bytes()
+            victim.close()
+        self.cache.setdefault(key, []).append(plan)
+        self.cache.move_to_end(key)
+        self.cache_bytes += nb
 
     # ---------------------------------------------------------------- loop
     def _plan(self, req: Request):
         torch = self.torch
         torch.cuda.set_device(self.device)
-        plan = Plan(req.d, req.k, req.delta, req.tol, req.level, req.coord, bc=req.bc, prec=req.prec)
+        plan = req.cached
+        if plan is None:
+            plan = Plan(req.d, req.k, req.delta, req.tol, req.level, req.coord, bc=req.bc, prec=req.prec)
         sig_h = torch.from_numpy(np.ascontiguousarray(req.sigma)).pin_memory()
         out_h = torch.empty_like(sig_h).pin_memory()
         return plan, sig_h, out_h
@@ -154,9 +221,11 @@ class Server:
                 if ev.query():
                     r.t_done = time.perf_counter()
                     r.future.set_result(out_h.numpy().reshape(r.sigma.shape))
-                    plan.close()
+                    with self.lock:
+                        self._cache_put(r.key(), plan)   # stays resident for the next request on it
                     self.free_streams.append(si)
-                    self.used -= r.footprint
+                    self.used -= r.footprint   # the plan's own bytes now count against the cache
+                    r.cached = None
                     self.completed.append(r)
                 else:
                     rest.append(item)
@@ -177,4 +246,4 @@ class Server:
         pts = sum(r.n_points for r in done)
         return {"requests": len(done), "points": pts, "points_per_s": pts / max(t1 - t0, 1e-9),
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "mean_ms": float(lat.mean())}
+                "mean_ms": float(lat.mean()), "plan_cache_hits": self.cache_hits}

@@ -20,7 +20,7 @@ class HostState:
         self.d, self.k = info["d"], info["k"]
         self.n1, self.nh = info["modes_1d"], info["modes_half"]
         self.fourier = info["fourier"]
-        cdt = np.complex128 if info["prec"] == 0 else np.complex64
+        cdt = np.complex64 if info["prec"] == 1 else np.complex128  # FP32 expansions only in split precision
         k, n1, nh = self.k, self.n1, self.nh
         self.blocks = hp.array("blocks", BLOCK)
         self.bleaves = hp.array("block_leaves", np.int64)

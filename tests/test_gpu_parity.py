@@ -105,6 +105,26 @@ def test_split_precision_periodic(d, delta):
     assert info["cutoff_level"] >= 2
 
 
+@pytest.mark.parametrize("delta,tol", [(1e-3, 1e-6), (1e-3, 1e-10), (1e-2, 1e-10), (3e-4, 1e-8)])
+def test_fp64_tensor_core(delta, tol):
+    """FP64 contractions on the tensor cores (DMMA): against the oracle, and against the
+    CUDA-core FP64 path, which does the same FP64 products in another order."""
+    tr = W.random_balanced_tree(3, 21, max_level=4, min_level=2, split_prob=0.2)
+    sig = W.random_sigma(tr, 6, 23)
+    check(3, 6, delta, tol, tr, sig, prec=F.PREC_FP64_TC)
+    u_tc, info = gpu_u(3, 6, delta, tol, tr, sig, prec=F.PREC_FP64_TC)
+    assert info["prec"] == F.PREC_FP64_TC
+    u_64, _ = gpu_u(3, 6, delta, tol, tr, sig, prec=F.PREC_FP64)
+    assert np.abs(u_tc - u_64).max() <= 1e-12 * np.abs(u_64).max()
+
+
+def test_fp64_tensor_core_periodic_and_large_blocks():
+    tr = W.random_balanced_tree(3, 9, max_level=3, min_level=2, split_prob=0.3, periodic=True)
+    check(3, 4, 1e-3, 1e-10, tr, W.random_sigma(tr, 4, 24), bc=1, prec=F.PREC_FP64_TC)
+    tr3 = W.uniform_tree(3, 3)  # K = 32 blocks under the level-1 cutoff boxes
+    check(3, 8, 1e-2, 1e-8, tr3, W.random_sigma(tr3, 8, 25), prec=F.PREC_FP64_TC)
+
+
 def test_split_precision_large_blocks():
     """Split precision, uniform subtrees of K = 32 nodes per axis under each cutoff-level box:
     one block per CTA, sigma streamed from global memory in the first contraction."""
@@ -174,3 +194,23 @@ def test_split_precision_tensor_core_evaluation(monkeypatch):
     sig = W.random_sigma(tr, 8, 16)
     check(3, 8, 1e-3, 1e-6, tr, sig, prec=1)
     check(3, 8, 1e-2, 1e-6, tr, sig, prec=1)
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_autotune_keeps_the_result(prec):
+    """The autotuner only changes launch shapes: the tuned plan gives the same transform."""
+    tr = W.random_balanced_tree(3, 21, max_level=4, min_level=2, split_prob=0.2)
+    p, tol = 8, 1e-6
+    sig = torch.from_numpy(W.random_sigma(tr, p, 26)).cuda()
+    plan = F.Plan(3, p, 1e-3, tol, tr.level, tr.coord, prec=prec)
+    u0 = plan(sig).clone()
+    knobs = plan.autotune(sig, reps=2)
+    assert knobs["ms"] > 0 and plan.tuning() == knobs
+    u1 = plan(sig)
+    torch.cuda.synchronize()
+    assert (u1 - u0).abs().max().item() <= 10 * tol * u0.abs().max().item()
+    plan.set_tuning(form_group=2, eval_rows16=16, eval_rows_large=8, near_phase=0)
+    u2 = plan(sig)
+    torch.cuda.synchronize()
+    assert (u2 - u0).abs().max().item() <= 10 * tol * u0.abs().max().item()
+    plan.close()

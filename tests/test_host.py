@@ -198,6 +198,20 @@ def test_planner_3d_free(delta, tol):
     _planner_vs_oracle(3, tr, 3, delta, tol)
 
 
+def test_planner_fp64_tensor_core_precision():
+    """FGT_PREC_FP64_TC plans the same FP64 tables as FGT_PREC_FP64 (only its kernel lists differ)
+    and reports itself."""
+    tr = W.random_balanced_tree(3, 21, max_level=3, min_level=1, split_prob=0.25)
+    info = _planner_vs_oracle(3, tr, 3, 1e-3, 1e-10, prec=F.PREC_FP64_TC)
+    assert info["prec"] == F.PREC_FP64_TC
+    a = F.analyze(3, 3, 1e-3, 1e-10, tr.level, tr.coord, prec=F.PREC_FP64_TC)
+    b = F.analyze(3, 3, 1e-3, 1e-10, tr.level, tr.coord, prec=F.PREC_FP64)
+    assert (a["n_f"], a["cutoff_level"]) == (b["n_f"], b["cutoff_level"])
+    assert abs(a["device_bytes"] - b["device_bytes"]) <= 0.01 * b["device_bytes"]
+    with pytest.raises(F.FGTError):
+        F.analyze(3, 3, 1e-3, 1e-10, tr.level, tr.coord, prec=3)
+
+
 @pytest.mark.parametrize("delta", [5e-2, 5e-3, 1e-3])
 def test_planner_3d_periodic(delta):
     tr = W.random_balanced_tree(3, 9, max_level=3, min_level=1, split_prob=0.3, periodic=True)
@@ -228,3 +242,20 @@ def test_analyze_reports_footprint():
     assert a["n_pw_leaves"] == 64 and a["n_direct_pairs"] == 0 and a["device_bytes"] > 0
     h = F.analyze(2, 8, 1e-2, 1e-9, w.tree.level, w.tree.coord, mode=F.MODE_HIERARCHICAL)
     assert h["device_bytes"] > a["device_bytes"]
+
+
+def test_tuning_knobs_validated_on_a_host_plan():
+    import ctypes
+    tr = W.random_balanced_tree(3, 21, max_level=3, min_level=1, split_prob=0.25)
+    hp = F.HostPlan(3, 4, 1e-3, 1e-6, tr.level, tr.coord, prec=F.PREC_SPLIT)
+    t = F.Tuning()
+    assert F.lib().fgt_plan_get_tuning(hp._h, ctypes.byref(t)) == 0
+    assert (t.form_group, t.eval_rows16, t.eval_rows_large, t.near_phase) == (8, 8, 4, 2) and t.ms == 0.0
+    for field, bad in (("form_group", 0), ("form_group", 9), ("near_phase", 1), ("eval_rows16", 0)):
+        u = F.Tuning(**{k: getattr(t, k) for k in ("form_group", "eval_rows16", "eval_rows_large", "near_phase")})
+        setattr(u, field, bad)
+        assert F.lib().fgt_plan_set_tuning(hp._h, ctypes.byref(u)) == 1
+    u = F.Tuning(form_group=4, eval_rows16=16, eval_rows_large=8, near_phase=4)
+    assert F.lib().fgt_plan_set_tuning(hp._h, ctypes.byref(u)) == 0
+    assert F.lib().fgt_plan_get_tuning(hp._h, ctypes.byref(t)) == 0
+    assert (t.form_group, t.eval_rows16, t.eval_rows_large, t.near_phase) == (4, 16, 8, 4)

@@ -68,3 +68,23 @@ def test_admission_refuses_requests_larger_than_the_budget():
     with pytest.raises(MemoryError):
         f.result(timeout=10)
     srv.shutdown()
+
+
+def test_plan_cache_reuses_resident_plans():
+    """Requests on geometries seen before run on the idle resident plan (no host planning) and
+    still equal the request transformed alone."""
+    base = _requests(3, seed=7)
+    rng = np.random.default_rng(1)
+    srv = S.Server(hbm_budget_bytes=2 << 30, max_inflight=4).start()
+    outs, reqs = [], []
+    for rnd in range(3):
+        batch = [S.Request(d=b.d, k=b.k, delta=b.delta, tol=b.tol, level=b.level, coord=b.coord,
+                           sigma=rng.uniform(-1, 1, size=b.sigma.shape), bc=b.bc) for b in base]
+        futs = [srv.submit(r) for r in batch]
+        outs += [f.result(timeout=120) for f in futs]   # the round's plans go back to the cache
+        reqs += batch
+    srv.shutdown()
+    assert srv.stats()["plan_cache_hits"] >= 2 * len(base)
+    for r, u in zip(reqs, outs):
+        ua = _alone(r)
+        assert np.abs(u - ua).max() <= 10 * r.tol * np.abs(ua).max()

@@ -285,6 +285,45 @@ def batched_configs(seed=0, n=256, max_points=1 << 18):
     return out
 
 
+def serving_mix(seed=0, n=24, max_points=1 << 22):
+    """n distinct request geometries for the serving loop: d in {2, 3}, free space or periodic
+    (3 in 10), tol 1e-6 or 1e-10 (1 in 4, stored in meta["tol"]), delta log-U[1e-4, 1e-2],
+    sizes log-spread from about 4K points up to max_points.  Free-space trees are refined around
+    1..8 Gaussians (as in batched_configs), periodic ones are uniform (level drawn to the size)
+    with a periodic Gaussian sum."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        d = int(rng.choice([2, 3]))
+        per = bool(rng.uniform() < 0.3)
+        tol = 1e-10 if rng.uniform() < 0.25 else 1e-6
+        delta = float(np.exp(rng.uniform(np.log(1e-4), np.log(1e-2))))
+        p = int(rng.choice([8, 12]))
+        target = float(np.exp(rng.uniform(np.log(4096), np.log(max_points))))
+        ng = int(rng.integers(1, 9))
+        centers = rng.uniform(-0.4, 0.4, size=(ng, d))
+        widths = np.exp(rng.uniform(np.log(1e-2), np.log(2e-1), size=ng))
+        if per:
+            level = max(1, int(round(np.log(max(target / p ** d, 1.0)) / np.log(2 ** d))))
+            while (1 << (d * level)) * p ** d > max_points and level > 1:
+                level -= 1
+            tree = uniform_tree(d, level, periodic=True)
+            sigma = gaussian_sum(node_positions(tree, p), centers, widths ** 2, periodic=True)
+        else:
+            depth = 9 if d == 2 else 7
+            while True:
+                tree = gaussian_refined_tree(d, centers, widths, rho=1.0, beta=3.0, max_level=depth, min_level=1,
+                                             balance=False)
+                if tree.n_leaves * p ** d * 1.5 <= min(target, max_points) or depth <= 2:
+                    break
+                depth -= 1
+            tree = gaussian_refined_tree(d, centers, widths, rho=1.0, beta=3.0, max_level=depth, min_level=1)
+            sigma = gaussian_sum(node_positions(tree, p), centers, widths ** 2)
+        out.append(Workload(f"serve{i}-{d}d-{'per' if per else 'free'}-p{p}", d, p, delta, per, tree, sigma,
+                            dict(seed=seed, index=i, tol=tol)))
+    return out
+
+
 def random_balanced_tree(d, seed, max_level=4, split_prob=0.45, periodic=False, min_level=0):
     """Random refinement (each box split with probability split_prob, seeded) then 2:1 balance."""
     rng = np.random.default_rng(seed)
