@@ -26,6 +26,8 @@ struct ShiftStep {
   const void *qh = nullptr;          // [2][nh] same for the last (half-range) axis
 };
 
+constexpr int kSides = 3;
+
 struct ExecDesc {
   int d = 0, k = 0, n1 = 0, nh = 0;
   int prec = 0;                      // 0: FP64 expansions, 1: FP32 expansions
@@ -87,9 +89,13 @@ struct ExecDesc {
   int64_t n_near_pairs = 0;
   int64_t n_points = 0;                  // n_leaves * k^d
   int zero_u = 0;                        // clear u first (near field or accumulating evaluation)
-  cudaStream_t aux = nullptr;            // second stream for the near field (nullptr: same stream)
-  int near_phase = 0;                    // phase the near field is forked before (0 form, 2 gather, 4 evaluate)
-  cudaEvent_t fork = nullptr, join = nullptr;
+  // side streams owned by the plan (nullptr: everything on the caller's stream).  Side 0 runs the
+  // near field, forked before phase near_phase (0 form, 2 gather, 4 evaluate) and joined at the
+  // end; sides 1 and 2 run the second and later per-size launches of the form and of the
+  // evaluation concurrently with the first, joined at the end of their phase.
+  cudaStream_t side[kSides] = {};
+  cudaEvent_t fork_ev[kSides] = {}, join_ev[kSides] = {};
+  int near_phase = 0;
 };
 
 constexpr int kPhases = 6;

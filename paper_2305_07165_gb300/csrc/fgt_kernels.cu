@@ -1363,12 +1363,13 @@ __global__ void __launch_bounds__(256) gather_kernel(const int32_t *__restrict__
   }
 }
 
-// Separable form of the same gather.  A CTA takes one run of up to kSegW target boxes along
-// x_1 (fixed x_2, x_3) and 256 consecutive modes.  For each of the 3^(d-1) neighbouring lines
-// (o_2, o_3) it loads the kSegW + 2 source boxes once, applies the x_1 factor as a 3-point
-// stencil along the run, and adds the result times the (o_2, o_3) factor into every target:
-// 9 (W + 2) loads per W targets in 3D instead of 27 W.  Used in split precision (FP32); the
-// FP64 expansions keep gather_kernel, which measured faster there (fewer registers per mode).
+// Separable form of the same gather.  A CTA takes one run of up to W target boxes along x_1
+// (fixed x_2, x_3) and 256 consecutive modes.  The phase factors are per axis, so the sum over the
+// 3^(d-1) neighbouring lines (o_2, o_3) is taken first, position by position along the run
+// (w_i = sum_lines P_2(o_2) P_3(o_3) phi[line][i], each of the W + 2 sources loaded once), and the
+// x_1 factor last, as a 3-point stencil over w: 9 (W + 2) + 3 W complex products per run in 3D,
+// against 27 + 9 + 3 per target for gather_kernel.  Used in split precision (FP32); the FP64
+// expansions keep gather_kernel, which measured faster there (fewer registers per mode).
 template <int D, typename R, int W>
 __global__ void __launch_bounds__(256) gather2_kernel(const GatherSeg *__restrict__ segs,
                                                       const typename C2T<R>::T *__restrict__ Pf,
@@ -1390,16 +1391,15 @@ __global__ void __launch_bounds__(256) gather2_kernel(const GatherSeg *__restric
   if (idx >= slot_size) return;
   int m1, m2, m3;
   mode_index<D>(idx, n1, m1, m2, m3);
-  C px[3], py[3], pz[3];
+  C py[3], pz[3];
 #pragma unroll
   for (int o = 0; o < 3; ++o) {
-    px[o] = Pf[o * n1 + m1];
     py[o] = (D == 3) ? Pf[o * n1 + m2] : Ph[o * nh + m2];
     pz[o] = (D == 3) ? Ph[o * nh + m3] : C{1, 0};
   }
-  R ar[W], ai[W];
+  R wr[W + 2], wi[W + 2];
 #pragma unroll
-  for (int t = 0; t < W; ++t) ar[t] = ai[t] = 0;
+  for (int i = 0; i < W + 2; ++i) wr[i] = wi[i] = 0;
 #pragma unroll
   for (int l = 0; l < NL; ++l) {
     const int32_t *sl = sg.src[l];
@@ -1412,19 +1412,21 @@ __global__ void __launch_bounds__(256) gather2_kernel(const GatherSeg *__restric
     for (int i = 0; i < W + 2; ++i) v[i] = (sl[i] >= 0) ? phi[(int64_t)sl[i] * slot_size + idx] : C{0, 0};
     const C f = cmul(py[l % 3], pz[l / 3]);
 #pragma unroll
-    for (int t = 0; t < W; ++t) {
-      if (sg.tgt[t] < 0) continue;
-      // source x0 - 1 + i seen from target x0 + t has o_1 = i - 1 - t
-      R tr = 0, ti = 0;
-      cfma(tr, ti, px[0], v[t]);
-      cfma(tr, ti, px[1], v[t + 1]);
-      cfma(tr, ti, px[2], v[t + 2]);
-      cfma(ar[t], ai[t], f, C{tr, ti});
-    }
+    for (int i = 0; i < W + 2; ++i) cfma(wr[i], wi[i], f, v[i]);
   }
+  C px[3];
 #pragma unroll
-  for (int t = 0; t < W; ++t)
-    if (sg.tgt[t] >= 0) psi[(int64_t)sg.tgt[t] * slot_size + idx] = C{ar[t], ai[t]};
+  for (int o = 0; o < 3; ++o) px[o] = Pf[o * n1 + m1];
+#pragma unroll
+  for (int t = 0; t < W; ++t) {
+    if (sg.tgt[t] < 0) continue;
+    // source x0 - 1 + i seen from target x0 + t has o_1 = i - 1 - t
+    R ar = 0, ai = 0;
+    cfma(ar, ai, px[0], C{wr[t], wi[t]});
+    cfma(ar, ai, px[1], C{wr[t + 1], wi[t + 1]});
+    cfma(ar, ai, px[2], C{wr[t + 2], wi[t + 2]});
+    psi[(int64_t)sg.tgt[t] * slot_size + idx] = C{ar, ai};
+  }
 }
 
 // phi[parent] = sum_children T_c->p(child) phi[child]
@@ -1651,6 +1653,44 @@ int max_dynamic_smem() {
   return v;
 }
 
+// The second and later launches of a phase go to side streams 1.. (round robin), forked from the
+// caller's stream before the first of them and joined back into it at the end of the phase, so
+// per-size launches with few CTAs (large blocks) run beside the others instead of after them.
+struct Spread {
+  const ExecDesc &e;
+  cudaStream_t st;
+  int n = 0;
+  bool used[kSides] = {};
+  cudaError_t err = cudaSuccess;
+  // the fork point is the construction: side launches wait for what st holds now, not for the
+  // phase's own first launch
+  Spread(const ExecDesc &ex, cudaStream_t s) : e(ex), st(s) {
+    if (e.side[1] != nullptr) err = cudaEventRecord(e.fork_ev[1], st);
+  }
+  cudaStream_t next() {
+    const int j = n++;
+    if (j == 0 || e.side[1] == nullptr) return st;
+    const int sd = 1 + (j - 1) % (kSides - 1);
+    if (!used[sd]) {
+      cudaError_t r = cudaStreamWaitEvent(e.side[sd], e.fork_ev[1], 0);
+      if (r != cudaSuccess && err == cudaSuccess) err = r;
+      used[sd] = true;
+    }
+    return e.side[sd];
+  }
+  cudaError_t join() {
+    for (int sd = 1; sd < kSides; ++sd) {
+      if (!used[sd]) continue;
+      cudaError_t r = cudaEventRecord(e.join_ev[sd], e.side[sd]);
+      if (r == cudaSuccess) r = cudaStreamWaitEvent(st, e.join_ev[sd], 0);
+      if (r != cudaSuccess && err == cudaSuccess) err = r;
+      used[sd] = false;
+    }
+    n = 0;
+    return err;
+  }
+};
+
 template <int D, typename R>
 static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, cudaStream_t st) {
   using C = typename C2T<R>::T;
@@ -1682,7 +1722,7 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
     if (e.events) cudaEventRecord(e.events[11], ns);
     return r;
   };
-  const bool near_aside = e.n_near_pairs > 0 && e.aux != nullptr;
+  const bool near_aside = e.n_near_pairs > 0 && e.side[0] != nullptr;
   if (!(e.n_near_pairs > 0) && e.events) {
     cudaEventRecord(e.events[10], st);
     cudaEventRecord(e.events[11], st);
@@ -1690,10 +1730,10 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
   auto fork_near = [&](int phase) -> cudaError_t {
     if (!near_aside || e.near_phase != phase) return cudaSuccess;
     cudaError_t r;
-    if ((r = cudaEventRecord(e.fork, st)) != cudaSuccess) return r;
-    if ((r = cudaStreamWaitEvent(e.aux, e.fork, 0)) != cudaSuccess) return r;
-    if ((r = launch_near(e.aux)) != cudaSuccess) return r;
-    return cudaEventRecord(e.join, e.aux);
+    if ((r = cudaEventRecord(e.fork_ev[0], st)) != cudaSuccess) return r;
+    if ((r = cudaStreamWaitEvent(e.side[0], e.fork_ev[0], 0)) != cudaSuccess) return r;
+    if ((r = launch_near(e.side[0])) != cudaSuccess) return r;
+    return cudaEventRecord(e.join_ev[0], e.side[0]);
   };
   if ((err = fork_near(0)) != cudaSuccess) return err;
   if (e.n_blocks > 0) {
@@ -1704,12 +1744,13 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
                                                             e.k);
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
+    Spread fs(e, st);
     if (e.n_f1 > 0) {
       const size_t fsm = form_smem_bytes(D, e.Kmax_f1, n1, sizeof(R) == 4);
       if ((err = cudaFuncSetAttribute(form_kernel<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm)) !=
           cudaSuccess)
         return err;
-      form_kernel<D, R><<<dim3((unsigned)e.n_f1, (unsigned)nh), 256, fsm, st>>>(
+      form_kernel<D, R><<<dim3((unsigned)e.n_f1, (unsigned)nh), 256, fsm, fs.next()>>>(
           e.f1_blocks, e.block_leaves, sigma, reinterpret_cast<const C *>(e.Ff), reinterpret_cast<const C *>(e.Fh),
           phi, e.k, n1, nh, ss, e.Kmax_f1);
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
@@ -1722,7 +1763,7 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
         if ((err = cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) !=
             cudaSuccess)
           return err;
-        fk<<<(unsigned)(lr.count * ((nh + kSc - 1) / kSc)), 256, lr.smem, st>>>(
+        fk<<<(unsigned)(lr.count * ((nh + kSc - 1) / kSc)), 256, lr.smem, fs.next()>>>(
             e.f2_blocks, e.f2_gptr + lr.first, e.block_leaves, sigma, e.sigp, reinterpret_cast<const float2 *>(e.Ff),
             reinterpret_cast<const float2 *>(e.Fh), reinterpret_cast<float2 *>(phi), e.k, n1, nh, ss);
       } else if (D == 3) {
@@ -1730,19 +1771,20 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
         if ((err = cudaFuncSetAttribute(f3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) !=
             cudaSuccess)
           return err;
-        f3<<<dim3((unsigned)lr.count, (unsigned)((nh + kSc - 1) / kSc)), 256, lr.smem, st>>>(
+        f3<<<dim3((unsigned)lr.count, (unsigned)((nh + kSc - 1) / kSc)), 256, lr.smem, fs.next()>>>(
             e.f2_blocks, e.f2_gptr + lr.first, e.block_leaves, sigma, reinterpret_cast<const C *>(e.Ff),
             reinterpret_cast<const C *>(e.Fh), phi, e.k, n1, nh, ss);
       } else {
         if ((err = cudaFuncSetAttribute(form2_kernel<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)lr.smem)) != cudaSuccess)
           return err;
-        form2_kernel<D, R><<<dim3((unsigned)lr.count, (unsigned)nh), 256, lr.smem, st>>>(
+        form2_kernel<D, R><<<dim3((unsigned)lr.count, (unsigned)nh), 256, lr.smem, fs.next()>>>(
             e.f2_blocks, e.f2_gptr + lr.first, e.block_leaves, sigma, reinterpret_cast<const C *>(e.Ff),
             reinterpret_cast<const C *>(e.Fh), phi, e.k, n1, nh, ss);
       }
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
+    if ((err = fs.join()) != cudaSuccess) return err;
   }
   mark(0, 1);
   mark(1, 0);
@@ -1780,12 +1822,13 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
   mark(3, 1);
   if ((err = fork_near(4)) != cudaSuccess) return err;
   mark(4, 0);
+  Spread es(e, st);
   if (e.n_e1 > 0) {
     const size_t esm = eval_smem_bytes(D, e.Kmax_e1, n1, sizeof(R) == 4);
     if ((err = cudaFuncSetAttribute(eval_kernel<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm)) !=
         cudaSuccess)
       return err;
-    eval_kernel<D, R><<<dim3((unsigned)e.n_e1, (unsigned)e.Kmax_e1), 256, esm, st>>>(
+    eval_kernel<D, R><<<dim3((unsigned)e.n_e1, (unsigned)e.Kmax_e1), 256, esm, es.next()>>>(
         e.e1_blocks, e.block_leaves, reinterpret_cast<const C *>(e.Ef), reinterpret_cast<const C *>(e.Eh), eval_src,
         u, e.k, n1, nh, ss);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
@@ -1795,7 +1838,7 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
       auto tk = (2 * nh <= 32) ? eval3_kernel<4> : eval3_kernel<8>;
       if ((err = cudaFuncSetAttribute(tk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) != cudaSuccess)
         return err;
-      tk<<<dim3((unsigned)lr.count, (unsigned)((lr.K + kEvalRows - 1) / kEvalRows)), 256, lr.smem, st>>>(
+      tk<<<dim3((unsigned)lr.count, (unsigned)((lr.K + kEvalRows - 1) / kEvalRows)), 256, lr.smem, es.next()>>>(
           e.e2_blocks + lr.first, e.block_leaves,
                                                    reinterpret_cast<const float2 *>(e.Ef),
                                                    reinterpret_cast<const float2 *>(e.Eh),
@@ -1815,16 +1858,17 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
     if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) !=
         cudaSuccess)
       return err;
-    kern<<<dim3((unsigned)lr.count, chunks), 256, lr.smem, st>>>(
+    kern<<<dim3((unsigned)lr.count, chunks), 256, lr.smem, es.next()>>>(
         e.e2_blocks + lr.first, e.block_leaves, reinterpret_cast<const C *>(e.Ef), reinterpret_cast<const C *>(e.Eh),
         eval_src, u, e.k, n1, nh, ss);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
+  if ((err = es.join()) != cudaSuccess) return err;
   mark(4, 1);
   if (e.n_near_pairs > 0 && !near_aside) {
     if ((err = launch_near(st)) != cudaSuccess) return err;
   }
-  if (near_aside && (err = cudaStreamWaitEvent(st, e.join, 0)) != cudaSuccess) return err;
+  if (near_aside && (err = cudaStreamWaitEvent(st, e.join_ev[0], 0)) != cudaSuccess) return err;
   return cudaSuccess;
 }
 

@@ -116,8 +116,8 @@ struct fgt_plan {
   double *stage = nullptr;  // host-path staging [2][n_leaves k^d]
   bool host_only = false;   // planned without a device (inspection only)
   bool tc_eval = false;     // split precision: evaluate with the tensor-core kernel (FGT_TC_EVAL=1)
-  cudaStream_t aux = nullptr;              // near-field stream
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaStream_t side[fgt::kSides] = {};     // near field and concurrent per-size launches
+  cudaEvent_t fork_ev[fgt::kSides] = {}, join_ev[fgt::kSides] = {};
   DevPack host_pack;        // host copy of the uploaded lists and tables (kept for host-only plans)
   fgt::ExecDesc ex;
   fgt_plan_info info{};
@@ -135,9 +135,11 @@ struct fgt_plan {
   int np() const { return d == 3 ? k * k * k : k * k; }
   ~fgt_plan() {
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
-    if (fork) cudaEventDestroy(fork);
-    if (join) cudaEventDestroy(join);
-    if (aux) cudaStreamDestroy(aux);
+    for (int i = 0; i < fgt::kSides; ++i) {
+      if (fork_ev[i]) cudaEventDestroy(fork_ev[i]);
+      if (join_ev[i]) cudaEventDestroy(join_ev[i]);
+      if (side[i]) cudaStreamDestroy(side[i]);
+    }
     if (dev) cudaFree(dev);
     if (work) cudaFree(work);
     if (stage) cudaFree(stage);
@@ -1021,19 +1023,23 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
     st.n = std::get<3>(step_off[si]);
     ex.push.push_back(st);
   }
-  if (ex.n_near_pairs > 0) {  // second stream for the near field, made once per plan
-    if (!P.aux) {
-      e = cudaStreamCreateWithFlags(&P.aux, cudaStreamNonBlocking);
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming);
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P.join, cudaEventDisableTiming);
-      if (e != cudaSuccess) return cuda_fail(e, "near-field stream");
+  const bool multi_form = (ex.n_f1 > 0) + ex.f2_ranges.size() > 1;
+  const bool multi_eval = (ex.n_e1 > 0) + ex.e2_ranges.size() > 1;
+  if (ex.n_near_pairs > 0 || multi_form || multi_eval) {  // side streams, made once per plan
+    for (int i = 0; i < fgt::kSides && !P.side[i]; ++i) {
+      e = cudaStreamCreateWithFlags(&P.side[i], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P.fork_ev[i], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P.join_ev[i], cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_fail(e, "side streams");
     }
-    ex.aux = P.aux;
+    for (int i = 0; i < fgt::kSides; ++i) {
+      ex.side[i] = P.side[i];
+      ex.fork_ev[i] = P.fork_ev[i];
+      ex.join_ev[i] = P.join_ev[i];
+    }
     // default: forked before the gather, so that the near field's FP64 work overlaps the L2-bound
     // gather and the evaluation rather than the form (fastest of the three fork points measured)
     ex.near_phase = (P.tune.near_phase == 0 || P.tune.near_phase == 4) ? P.tune.near_phase : 2;
-    ex.fork = P.fork;
-    ex.join = P.join;
   }
   P.ex = ex;
 
