@@ -1160,6 +1160,189 @@ __global__ void __launch_bounds__(256) eval2_kernel(const Block *__restrict__ bl
   }
 }
 
+// ----------------------------------------------------------------------------- tensor-core evaluation, stages 2-3 (3D, FP32)
+//
+// eval2_kernel's work split (KM rows of a block per CTA, psi read once in stage 1 on the CUDA
+// cores), with the two contractions that follow on the tensor cores in 3xTF32:
+//   stage 2, per row r: Y2[r] (K x n1) = E2 (K x n1) Y1[r] (n1 x n1), complex, embedded as a real
+//     product over the interleaved (re, im) index of m2 (A = E2, B = Y1[r]);
+//   stage 3, per row r: u[r] (K x K) = Re Y2[r] (K x n1) E1^T (n1 x K): only the real part, so B
+//     carries (Re E1, -Im E1) on the interleaved index of m1.
+// One warp per (row, 16-row tile); operands are split into TF32 hi / lo as they are loaded.
+template <int NBT, int KM>  // NBT: n-tiles of 8 stage-2 columns in registers (>= 2 ceil(n1/8)); KM rows per CTA
+__global__ void __launch_bounds__(256) eval4_kernel(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
+                                                    const float2 *__restrict__ Ef, const float2 *__restrict__ Eh,
+                                                    const float2 *__restrict__ psi, double *__restrict__ u, int k,
+                                                    int n1, int nh, int64_t slot_size) {
+  using C = float2;
+  extern __shared__ __align__(16) unsigned char smem_e4[];
+  const Block blk = blocks[blockIdx.x];
+  const int K = blk.K, nl = 1 << blk.dl;
+  const int r0 = blockIdx.y * KM, nr = min(KM, K - r0);
+  if (nr <= 0) return;
+  const int RM = min(KM, K);
+  const int64_t *lv = bleaves + blk.leaf0;
+  const C *ps = psi + (int64_t)blk.slot * slot_size;
+  const bool acc_u = (blk.flags & 1) != 0;
+  const int nn = n1 * n1;
+  C *Y1 = reinterpret_cast<C *>(smem_e4);              // [RM][nn]
+  C *Y2 = Y1 + (size_t)RM * nn;                         // [RM][K][n1]
+  C *E1 = Y2 + (size_t)RM * K * n1;                     // [K][n1]
+  C *E2 = E1 + (size_t)K * n1;                          // [K][n1]
+  C *Ed = E2 + (size_t)K * n1;                          // [RM][nh]
+  for (int e = threadIdx.x; e < K * n1; e += blockDim.x) {
+    const int I = e / n1, m = e - I * n1;
+    E1[e] = Ef[((int64_t)(blk.mat[0] + I / k) * k + I % k) * n1 + m];
+    E2[e] = Ef[((int64_t)(blk.mat[1] + I / k) * k + I % k) * n1 + m];
+  }
+  for (int e = threadIdx.x; e < nr * nh; e += blockDim.x) {
+    const int I = r0 + e / nh, m = e % nh;
+    Ed[e] = Eh[((int64_t)(blk.mat[2] + I / k) * k + I % k) * nh + m];
+  }
+  __syncthreads();
+  // stage 1 (CUDA cores): Y1[r][mode] = sum_m3 Ed[r][m3] psi[m3][mode], 8 planes in flight
+  for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+    float ar[KM], ai[KM];
+#pragma unroll
+    for (int r = 0; r < KM; ++r) ar[r] = ai[r] = 0.f;
+    for (int md0 = 0; md0 < nh; md0 += 8) {
+      C v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = (md0 + q < nh) ? ps[(int64_t)(md0 + q) * nn + idx] : C{0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (md0 + q < nh) {
+#pragma unroll
+          for (int r = 0; r < KM; ++r)
+            if (r < nr) cfma(ar[r], ai[r], Ed[r * nh + md0 + q], v[q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < KM; ++r)
+      if (r < nr) Y1[(size_t)r * nn + idx] = C{ar[r], ai[r]};
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int mt = (K + 15) / 16, kst = (2 * n1 + 7) / 8, nbt = 2 * ((n1 + 7) / 8);
+  // stage 2: per (r, 16-row tile of I2), all 2 * ceil(n1/8) column tiles (re / im pairs)
+  for (int job = warp; job < nr * mt; job += nwarp) {
+    const int r = job / mt, i0 = (job - r * mt) * 16;
+    const C *y1 = Y1 + (size_t)r * nn;
+    float acc[NBT][4];
+#pragma unroll
+    for (int j = 0; j < NBT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    const int ra = i0 + g, rb = ra + 8;
+    for (int ks = 0; ks < kst; ++ks) {
+      // real index k0 + t and k0 + t + 4 -> complex m2 = k0/2 + (t>>1) (+2), part t & 1
+      const int mA = ks * 4 + (t >> 1), mB = mA + 2, part = t & 1;
+      float av[4];
+      {
+        const C e0 = (ra < K && mA < n1) ? E2[(size_t)ra * n1 + mA] : C{0.f, 0.f};
+        const C e1 = (rb < K && mA < n1) ? E2[(size_t)rb * n1 + mA] : C{0.f, 0.f};
+        const C e2 = (ra < K && mB < n1) ? E2[(size_t)ra * n1 + mB] : C{0.f, 0.f};
+        const C e3 = (rb < K && mB < n1) ? E2[(size_t)rb * n1 + mB] : C{0.f, 0.f};
+        av[0] = part ? e0.y : e0.x;
+        av[1] = part ? e1.y : e1.x;
+        av[2] = part ? e2.y : e2.x;
+        av[3] = part ? e3.y : e3.x;
+      }
+      uint32_t ah[4], al[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) split_tf32(av[x], ah[x], al[x]);
+#pragma unroll
+      for (int jj = 0; jj < NBT / 2; ++jj) {
+        if (2 * jj >= nbt) break;
+        const int m1 = jj * 8 + g;
+        const C y0 = (mA < n1 && m1 < n1) ? y1[(size_t)mA * n1 + m1] : C{0.f, 0.f};
+        const C y4 = (mB < n1 && m1 < n1) ? y1[(size_t)mB * n1 + m1] : C{0.f, 0.f};
+        uint32_t bh0, bl0, bh1, bl1;
+        // real-part tile: (Re, -Im) on the interleaved index
+        split_tf32(part ? -y0.y : y0.x, bh0, bl0);
+        split_tf32(part ? -y4.y : y4.x, bh1, bl1);
+        mma3(acc[2 * jj], ah, al, bh0, bh1, bl0, bl1);
+        // imaginary-part tile: (Im, Re)
+        split_tf32(part ? y0.x : y0.y, bh0, bl0);
+        split_tf32(part ? y4.x : y4.y, bh1, bl1);
+        mma3(acc[2 * jj + 1], ah, al, bh0, bh1, bl0, bl1);
+      }
+    }
+    C *y2 = Y2 + (size_t)r * K * n1;
+#pragma unroll
+    for (int jj = 0; jj < NBT / 2; ++jj) {
+      if (2 * jj >= nbt) break;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int row = h ? rb : ra;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int m1 = jj * 8 + 2 * t + c;
+          if (row < K && m1 < n1) y2[(size_t)row * n1 + m1] = C{acc[2 * jj][2 * h + c], acc[2 * jj + 1][2 * h + c]};
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // stage 3: u(r0 + r, I2, I1) = Re sum_m1 Y2[r][I2][m1] E1[I1][m1]; per (r, 16-row tile of I2)
+  const int kp = k * k * k, ntk = (K + 7) / 8;
+  for (int job = warp; job < nr * mt; job += nwarp) {
+    const int r = job / mt, i0 = (job - r * mt) * 16;
+    const C *y2 = Y2 + (size_t)r * K * n1;
+    float acc[4][4];  // K <= 32: at most 4 column tiles
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    const int ra = i0 + g, rb = ra + 8;
+    for (int ks = 0; ks < kst; ++ks) {
+      const int mA = ks * 4 + (t >> 1), mB = mA + 2, part = t & 1;
+      float av[4];
+      {
+        const C e0 = (ra < K && mA < n1) ? y2[(size_t)ra * n1 + mA] : C{0.f, 0.f};
+        const C e1 = (rb < K && mA < n1) ? y2[(size_t)rb * n1 + mA] : C{0.f, 0.f};
+        const C e2 = (ra < K && mB < n1) ? y2[(size_t)ra * n1 + mB] : C{0.f, 0.f};
+        const C e3 = (rb < K && mB < n1) ? y2[(size_t)rb * n1 + mB] : C{0.f, 0.f};
+        av[0] = part ? e0.y : e0.x;
+        av[1] = part ? e1.y : e1.x;
+        av[2] = part ? e2.y : e2.x;
+        av[3] = part ? e3.y : e3.x;
+      }
+      uint32_t ah[4], al[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) split_tf32(av[x], ah[x], al[x]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (j >= ntk) break;
+        const int I1 = j * 8 + g;
+        const C f0 = (mA < n1 && I1 < K) ? E1[(size_t)I1 * n1 + mA] : C{0.f, 0.f};
+        const C f4 = (mB < n1 && I1 < K) ? E1[(size_t)I1 * n1 + mB] : C{0.f, 0.f};
+        uint32_t bh0, bl0, bh1, bl1;
+        split_tf32(part ? -f0.y : f0.x, bh0, bl0);
+        split_tf32(part ? -f4.y : f4.x, bh1, bl1);
+        mma3(acc[j], ah, al, bh0, bh1, bl0, bl1);
+      }
+    }
+    const int I3 = r0 + r, o3 = I3 / k, t3 = I3 - o3 * k;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (j >= ntk) break;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int I2 = h ? rb : ra;
+        if (I2 >= K) continue;
+        const int o2 = I2 / k, t2 = I2 - o2 * k;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int I1 = j * 8 + 2 * t + c;
+          if (I1 >= K) continue;
+          const int o1 = I1 / k;
+          double *up = u + lv[(o3 * nl + o2) * nl + o1] * kp + (t3 * k + t2) * k + (I1 - o1 * k);
+          const double v = (double)acc[j][2 * h + c];
+          if (acc_u) atomicAdd(up, v); else *up = v;
+        }
+      }
+    }
+  }
+}
+
 // ----------------------------------------------------------------------------- tensor-core evaluation (3D, FP32)
 //
 // eval2_kernel with its first contraction, Y1 (K x n1^2) = Ed (K x nh) psi (nh x n1^2), on the
@@ -1834,7 +2017,7 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   for (const LaunchRange &lr : e.e2_ranges) {  // one launch per block size K
-    if (D == 3 && lr.tensor && sizeof(R) == 4) {
+    if (D == 3 && lr.tensor == 1 && sizeof(R) == 4) {
       auto tk = (2 * nh <= 32) ? eval3_kernel<4> : eval3_kernel<8>;
       if ((err = cudaFuncSetAttribute(tk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) != cudaSuccess)
         return err;
@@ -1843,6 +2026,20 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
                                                    reinterpret_cast<const float2 *>(e.Ef),
                                                    reinterpret_cast<const float2 *>(e.Eh),
                                                    reinterpret_cast<const float2 *>(eval_src), u, e.k, n1, nh, ss);
+      if ((err = cudaGetLastError()) != cudaSuccess) return err;
+      continue;
+    }
+    if (D == 3 && lr.tensor == 2 && sizeof(R) == 4) {  // stages 2-3 on the tensor cores
+      const bool small_n = 2 * ((n1 + 7) / 8) <= 8;
+      auto tk = lr.rows <= 4 ? (small_n ? eval4_kernel<8, 4> : eval4_kernel<kNbtMax, 4>)
+                : lr.rows <= 8 ? (small_n ? eval4_kernel<8, 8> : eval4_kernel<kNbtMax, 8>)
+                               : (small_n ? eval4_kernel<8, 16> : eval4_kernel<kNbtMax, 16>);
+      const int rows4 = lr.rows <= 4 ? 4 : lr.rows <= 8 ? 8 : 16;
+      if ((err = cudaFuncSetAttribute(tk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) != cudaSuccess)
+        return err;
+      tk<<<dim3((unsigned)lr.count, (unsigned)((lr.K + rows4 - 1) / rows4)), 256, lr.smem, es.next()>>>(
+          e.e2_blocks + lr.first, e.block_leaves, reinterpret_cast<const float2 *>(e.Ef),
+          reinterpret_cast<const float2 *>(e.Eh), reinterpret_cast<const float2 *>(eval_src), u, e.k, n1, nh, ss);
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
       continue;
     }

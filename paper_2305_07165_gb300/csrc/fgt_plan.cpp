@@ -116,6 +116,7 @@ struct fgt_plan {
   double *stage = nullptr;  // host-path staging [2][n_leaves k^d]
   bool host_only = false;   // planned without a device (inspection only)
   bool tc_eval = false;     // split precision: evaluate with the tensor-core kernel (FGT_TC_EVAL=1)
+  bool tc_eval4 = false;    // split precision: stages 2-3 of the evaluation on the tensor cores
   cudaStream_t side[fgt::kSides] = {};     // near field and concurrent per-size launches
   cudaEvent_t fork_ev[fgt::kSides] = {}, join_ev[fgt::kSides] = {};
   DevPack host_pack;        // host copy of the uploaded lists and tables (kept for host-only plans)
@@ -568,6 +569,13 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
     // the tensor-core evaluation kernel measured slower than the whole-block CUDA-core one on
     // GB300 (its stages 2-3 dominate once stage 1 is on the tensor cores), so it is off by default
     const bool tensor_eval = d == 3 && P.prec == FGT_PREC_SPLIT && nh <= 32 && P.tc_eval;
+    // split precision, 3D: evaluation stages 2-3 in 3xTF32 (register tiles need K <= 32, n1 <= 56);
+    // by default for blocks of K > 16 only (measured faster there, slower for K <= 16), for every
+    // block with FGT_TC_EVAL4=1
+    auto eval4_ok = [&](int K) {
+      return d == 3 && P.prec == FGT_PREC_SPLIT && !P.tc_eval && (K > 16 || P.tc_eval4) && K <= 32 &&
+             2 * ((n1 + 7) / 8) <= 14;
+    };
     auto gbytes = [&](int g, int K) {
       if (tensor_form(K)) return fgt::form4_bytes(g, K, n1);
       return d == 3 ? fgt::form3_bytes(g, K, n1, rsz, csz) : fgt::form2_bytes(d, g, K, n1, nh, rsz, csz);
@@ -638,6 +646,7 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
           lr.rows = rows;
           lr.smem = eb;
           lr.tensor = ((tensor_eval && !chunked) || (ex.tc64 && d == 3)) ? 1 : 0;
+          if (eval4_ok(b.K)) lr.tensor = 2;  // stages 2-3 of the evaluation on the tensor cores
           ex.e2_ranges.push_back(lr);
         }
         e2.push_back(b);
@@ -1074,6 +1083,8 @@ fgt_status create_impl(int d, double delta, double tol, double eps_pw, int bc, i
   {
     const char *tc = std::getenv("FGT_TC_EVAL");
     P->tc_eval = tc && tc[0] == '1';
+    const char *tc4 = std::getenv("FGT_TC_EVAL4");
+    P->tc_eval4 = tc4 && tc4[0] == '1';
   }
   P->n_leaves = tree->n_leaves;
   P->leaf_level.assign(tree->leaf_level, tree->leaf_level + tree->n_leaves);

@@ -214,3 +214,15 @@ def test_autotune_keeps_the_result(prec):
     torch.cuda.synchronize()
     assert (u2 - u0).abs().max().item() <= 10 * tol * u0.abs().max().item()
     plan.close()
+
+
+def test_split_precision_tensor_core_evaluation_stages_2_3(monkeypatch):
+    """Evaluation with its second and third contractions in 3xTF32 on the tensor cores
+    (selected with FGT_TC_EVAL4=1): K = 8, 16 and 32 blocks, n1 up to 35."""
+    monkeypatch.setenv("FGT_TC_EVAL4", "1")
+    tr = W.random_balanced_tree(3, 21, max_level=4, min_level=2, split_prob=0.2)
+    sig = W.random_sigma(tr, 8, 27)
+    check(3, 8, 1e-3, 1e-6, tr, sig, prec=1)
+    check(3, 8, 1e-2, 1e-6, tr, sig, prec=1)
+    tr3 = W.uniform_tree(3, 3)
+    check(3, 8, 1e-2, 1e-6, tr3, W.random_sigma(tr3, 8, 28), prec=1)
