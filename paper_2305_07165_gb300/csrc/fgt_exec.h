@@ -145,6 +145,11 @@ inline size_t form4b_bytes(int K, int n1) { return form4_bytes(1, K, n1, true); 
 inline size_t eval3_bytes(int K, int n1, int nh) {
   return 8 * (8 * (size_t)n1 * n1 + 8 * (size_t)K * n1 + 2 * (size_t)K * n1 + 8 * (size_t)nh);
 }
+// Evaluation with the half-range axis contracted last: `rows` rows I1 of a block per CTA.
+inline size_t eval5_bytes(int K, int n1, int nh, size_t c, int rows) {
+  const size_t R = (size_t)(K < rows ? K : rows);
+  return c * (R * nh * n1 + R * K * nh + R * n1 + (size_t)K * n1 + (size_t)K * nh);
+}
 // Whole-block evaluation, `rows` rows (along the last axis) of a block per CTA (4, 8 or 16).
 inline size_t eval2_bytes(int d, int K, int n1, int nh, size_t c, int rows) {
   const size_t R = (size_t)(K < rows ? K : rows);  // rows held at once

@@ -1160,6 +1160,160 @@ __global__ void __launch_bounds__(256) eval2_kernel(const Block *__restrict__ bl
   }
 }
 
+// ----------------------------------------------------------------------------- evaluation, half-range axis last (3D)
+//
+// u(I3, I2, I1) = Re sum_{m3 >= 0} Eh(I3, m3) sum_m2 E2(I2, m2) sum_m1 E1(I1, m1) psi[m3][m2][m1]
+// contracted m1 first and the half-range axis m3 last: K nh n1^2 + K^2 nh n1 + K^3 nh complex
+// products (the last one real-valued) instead of K nh n1^2 + K^2 n1^2 + K^3 n1 with m3 first --
+// 18 % (K = 8) to 39 % (K = 32) fewer at n1 = 2 nh - 1.  A CTA takes RC rows I1 of a block:
+//   stage 1: T1[r][m3][m2] = sum_m1 E1(I1_r, m1) psi[m3][m2][m1]   (one thread per (m3, m2) row)
+//   stage 2: T2[r][I2][m3] = sum_m2 E2(I2, m2) T1[r][m3][m2]       (4 x 4 register tiles)
+//   stage 3: u = Re sum_m3 Eh(I3, m3) T2[r][I2][m3]                (4 x 4 register tiles)
+template <typename R, int RC>
+__global__ void __launch_bounds__(256) eval5_kernel(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
+                                                    const typename C2T<R>::T *__restrict__ Ef,
+                                                    const typename C2T<R>::T *__restrict__ Eh,
+                                                    const typename C2T<R>::T *__restrict__ psi, double *__restrict__ u,
+                                                    int k, int n1, int nh, int64_t slot_size) {
+  using C = typename C2T<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_e5[];
+  const Block blk = blocks[blockIdx.x];
+  const int K = blk.K, nl = 1 << blk.dl;
+  const int i0 = blockIdx.y * RC, nr = min(RC, K - i0);  // rows I1 = i0 .. i0 + nr - 1
+  if (nr <= 0) return;
+  const int64_t *lv = bleaves + blk.leaf0;
+  const C *ps = psi + (int64_t)blk.slot * slot_size;
+  const bool acc_u = (blk.flags & 1) != 0;
+  const int nrow = nh * n1;                             // (m3, m2) rows of the slot
+  C *T1 = reinterpret_cast<C *>(smem_e5);               // [RC][nh][n1]
+  C *T2 = T1 + (size_t)RC * nrow;                       // [RC][K][nh]
+  C *E1 = T2 + (size_t)RC * K * nh;                     // [RC][n1]  (rows I1 of the chunk)
+  C *E2 = E1 + (size_t)RC * n1;                         // [K][n1]
+  C *Ez = E2 + (size_t)K * n1;                          // [K][nh]   (last axis, m3 >= 0)
+  for (int e = threadIdx.x; e < nr * n1; e += blockDim.x) {
+    const int I = i0 + e / n1, m = e % n1;
+    E1[e] = Ef[((int64_t)(blk.mat[0] + I / k) * k + I % k) * n1 + m];
+  }
+  for (int e = threadIdx.x; e < K * n1; e += blockDim.x) {
+    const int I = e / n1, m = e - I * n1;
+    E2[e] = Ef[((int64_t)(blk.mat[1] + I / k) * k + I % k) * n1 + m];
+  }
+  for (int e = threadIdx.x; e < K * nh; e += blockDim.x) {
+    const int I = e / nh, m = e - I * nh;
+    Ez[e] = Eh[((int64_t)(blk.mat[2] + I / k) * k + I % k) * nh + m];
+  }
+  __syncthreads();
+  // stage 1: each thread one (m3, m2) row of the slot, RC accumulators
+  for (int row = threadIdx.x; row < nrow; row += blockDim.x) {
+    const C *pr = ps + (int64_t)row * n1;
+    R ar[RC], ai[RC];
+#pragma unroll
+    for (int r = 0; r < RC; ++r) ar[r] = ai[r] = 0;
+    for (int m0 = 0; m0 < n1; m0 += 4) {
+      C v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = (m0 + q < n1) ? pr[m0 + q] : C{0, 0};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (m0 + q >= n1) break;
+#pragma unroll
+        for (int r = 0; r < RC; ++r)
+          if (r < nr) cfma(ar[r], ai[r], E1[r * n1 + m0 + q], v[q]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RC; ++r)
+      if (r < nr) T1[(size_t)r * nrow + row] = C{ar[r], ai[r]};
+  }
+  __syncthreads();
+  // stage 2: T2[r][I2][m3] = sum_m2 E2[I2][m2] T1[r][m3][m2]; 4 x 4 tiles over (I2, m3)
+  {
+    const int tI = (K + 3) / 4, tm = (nh + 3) / 4, ntile = nr * tI * tm;
+    for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
+      const int bm = t % tm, rest = t / tm, bI = rest % tI, r = rest / tI;
+      R ar[4][4], ai[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ar[i][j] = ai[i][j] = 0;
+      const C *t1 = T1 + (size_t)r * nrow;
+      for (int m2 = 0; m2 < n1; ++m2) {
+        C a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int I2 = bI * 4 + i;
+          a[i] = (I2 < K) ? E2[(size_t)I2 * n1 + m2] : C{0, 0};
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int m3 = bm * 4 + j;
+          b[j] = (m3 < nh) ? t1[(size_t)m3 * n1 + m2] : C{0, 0};
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) cfma(ar[i][j], ai[i][j], a[i], b[j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int I2 = bI * 4 + i, m3 = bm * 4 + j;
+          if (I2 < K && m3 < nh) T2[((size_t)r * K + I2) * nh + m3] = C{ar[i][j], ai[i][j]};
+        }
+    }
+  }
+  __syncthreads();
+  // stage 3: u(I3, I2, I1) = Re sum_m3 Ez[I3][m3] T2[r][I2][m3]; 4 x 4 tiles over (I3, I2)
+  {
+    const int kp = k * k * k, tI = (K + 3) / 4, ntile = nr * tI * tI;
+    for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
+      const int b2 = t % tI, rest = t / tI, b3 = rest % tI, r = rest / tI;
+      R acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+      const C *t2 = T2 + (size_t)r * K * nh;
+      for (int m3 = 0; m3 < nh; ++m3) {
+        C a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int I3 = b3 * 4 + i;
+          a[i] = (I3 < K) ? Ez[(size_t)I3 * nh + m3] : C{0, 0};
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int I2 = b2 * 4 + j;
+          b[j] = (I2 < K) ? t2[(size_t)I2 * nh + m3] : C{0, 0};
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc[i][j] = fma(a[i].x, b[j].x, acc[i][j]);
+            acc[i][j] = fma(-a[i].y, b[j].y, acc[i][j]);
+          }
+      }
+      const int I1 = i0 + r, o1 = I1 / k, t1 = I1 - o1 * k;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int I3 = b3 * 4 + i;
+        if (I3 >= K) continue;
+        const int o3 = I3 / k, t3 = I3 - o3 * k;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int I2 = b2 * 4 + j;
+          if (I2 >= K) continue;
+          const int o2 = I2 / k, t2i = I2 - o2 * k;
+          double *up = u + lv[(o3 * nl + o2) * nl + o1] * kp + (t3 * k + t2i) * k + t1;
+          if (acc_u) atomicAdd(up, (double)acc[i][j]); else *up = (double)acc[i][j];
+        }
+      }
+    }
+  }
+}
+
 // ----------------------------------------------------------------------------- tensor-core evaluation, stages 2-3 (3D, FP32)
 //
 // eval2_kernel's work split (KM rows of a block per CTA, psi read once in stage 1 on the CUDA
@@ -2026,6 +2180,21 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
                                                    reinterpret_cast<const float2 *>(e.Ef),
                                                    reinterpret_cast<const float2 *>(e.Eh),
                                                    reinterpret_cast<const float2 *>(eval_src), u, e.k, n1, nh, ss);
+      if ((err = cudaGetLastError()) != cudaSuccess) return err;
+      continue;
+    }
+    if (D == 3 && lr.tensor == 3) {  // half-range axis contracted last
+      auto k5 = lr.rows <= 1   ? eval5_kernel<R, 1>
+                : lr.rows <= 2 ? eval5_kernel<R, 2>
+                : lr.rows <= 4 ? eval5_kernel<R, 4>
+                : lr.rows <= 8 ? eval5_kernel<R, 8>
+                               : eval5_kernel<R, 16>;
+      const int rc = lr.rows <= 1 ? 1 : lr.rows <= 2 ? 2 : lr.rows <= 4 ? 4 : lr.rows <= 8 ? 8 : 16;
+      if ((err = cudaFuncSetAttribute(k5, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) != cudaSuccess)
+        return err;
+      k5<<<dim3((unsigned)lr.count, (unsigned)((lr.K + rc - 1) / rc)), 256, lr.smem, es.next()>>>(
+          e.e2_blocks + lr.first, e.block_leaves, reinterpret_cast<const C *>(e.Ef), reinterpret_cast<const C *>(e.Eh),
+          eval_src, u, e.k, n1, nh, ss);
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
       continue;
     }

@@ -117,6 +117,7 @@ struct fgt_plan {
   bool host_only = false;   // planned without a device (inspection only)
   bool tc_eval = false;     // split precision: evaluate with the tensor-core kernel (FGT_TC_EVAL=1)
   bool tc_eval4 = false;    // split precision: stages 2-3 of the evaluation on the tensor cores
+  bool eval5 = false;       // 3D: evaluation with the half-range axis contracted last
   cudaStream_t side[fgt::kSides] = {};     // near field and concurrent per-size launches
   cudaEvent_t fork_ev[fgt::kSides] = {}, join_ev[fgt::kSides] = {};
   DevPack host_pack;        // host copy of the uploaded lists and tables (kept for host-only plans)
@@ -632,7 +633,32 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
     // more times)
     auto norm_rows = [](int r) { return r <= 4 ? 4 : r <= 8 ? 8 : 16; };  // the kernel's instantiations
     const int rows16 = norm_rows(P.tune.eval_rows16), rows32 = norm_rows(P.tune.eval_rows_large);
+    // 3D: the evaluation with the half-range axis last (fewer products), rows I1 per CTA as many
+    // as keep its shared memory within e5_budget
+    const size_t e5_budget = P.f32() ? 80 * 1024 : 112 * 1024;
+    auto e5_rows = [&](int K) {
+      for (int rc : {16, 8, 4, 2, 1})
+        if (rc <= K && fgt::eval5_bytes(K, n1, nh, csz, rc) <= e5_budget) return rc;
+      return fgt::eval5_bytes(K, n1, nh, csz, 1) <= (size_t)smax ? 1 : 0;
+    };
+    const bool use_e5 = d == 3 && P.eval5 && !P.tc_eval && !ex.tc64;
     for (const fgt::Block &b : sorted) {
+      if (use_e5 && e5_rows(b.K) > 0) {
+        const int rc = e5_rows(b.K);
+        if (ex.e2_ranges.empty() || ex.e2_ranges.back().K != b.K) {
+          fgt::LaunchRange lr;
+          lr.first = (int)e2.size();
+          lr.count = 0;
+          lr.K = b.K;
+          lr.rows = rc;
+          lr.smem = fgt::eval5_bytes(b.K, n1, nh, csz, rc);
+          lr.tensor = 3;
+          ex.e2_ranges.push_back(lr);
+        }
+        e2.push_back(b);
+        ex.e2_ranges.back().count++;
+        continue;
+      }
       const bool chunked = b.K > 16 && d == 3 && (P.prec == FGT_PREC_SPLIT || ex.tc64);
       const int rows = b.K <= 8 ? 8 : b.K <= 16 ? (P.prec == FGT_PREC_SPLIT && d == 3 ? rows16 : 16) : rows32;
       const size_t eb = (tensor_eval && !chunked) ? fgt::eval3_bytes(b.K, n1, nh)
@@ -1085,6 +1111,10 @@ fgt_status create_impl(int d, double delta, double tol, double eps_pw, int bc, i
     P->tc_eval = tc && tc[0] == '1';
     const char *tc4 = std::getenv("FGT_TC_EVAL4");
     P->tc_eval4 = tc4 && tc4[0] == '1';
+    // the evaluation with the half-range axis last: default in FP64 (fewer FP64 products, 10-35 %
+    // faster there), in split precision only with FGT_EVAL5=1 (measured no faster: issue-bound)
+    const char *e5 = std::getenv("FGT_EVAL5");
+    P->eval5 = e5 ? e5[0] == '1' : prec == FGT_PREC_FP64;
   }
   P->n_leaves = tree->n_leaves;
   P->leaf_level.assign(tree->leaf_level, tree->leaf_level + tree->n_leaves);

@@ -226,3 +226,17 @@ def test_split_precision_tensor_core_evaluation_stages_2_3(monkeypatch):
     check(3, 8, 1e-2, 1e-6, tr, sig, prec=1)
     tr3 = W.uniform_tree(3, 3)
     check(3, 8, 1e-2, 1e-6, tr3, W.random_sigma(tr3, 8, 28), prec=1)
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-6), (0, 1e-6), (0, 1e-10)])
+def test_evaluation_half_range_axis_last(monkeypatch, prec, tol):
+    """The evaluation contracted m1, m2, then the half-range m3 (FGT_EVAL5=1): adaptive blocks of
+    K = 6 to 24 (p = 6), K = 32 blocks, and a periodic tree."""
+    monkeypatch.setenv("FGT_EVAL5", "1")
+    tr = W.random_balanced_tree(3, 21, max_level=4, min_level=2, split_prob=0.2)
+    check(3, 6, 1e-3, tol, tr, W.random_sigma(tr, 6, 29), prec=prec)
+    check(3, 6, 1e-2, tol, tr, W.random_sigma(tr, 6, 30), prec=prec)
+    tr3 = W.uniform_tree(3, 3)
+    check(3, 8, 1e-2, tol, tr3, W.random_sigma(tr3, 8, 31), prec=prec)
+    trp = W.random_balanced_tree(3, 9, max_level=4, min_level=2, split_prob=0.25, periodic=True)
+    check(3, 4, 1e-3, tol, trp, W.random_sigma(trp, 4, 32), bc=1, prec=prec)
