@@ -240,3 +240,31 @@ def test_evaluation_half_range_axis_last(monkeypatch, prec, tol):
     check(3, 8, 1e-2, tol, tr3, W.random_sigma(tr3, 8, 31), prec=prec)
     trp = W.random_balanced_tree(3, 9, max_level=4, min_level=2, split_prob=0.25, periodic=True)
     check(3, 4, 1e-3, tol, trp, W.random_sigma(trp, 4, 32), bc=1, prec=prec)
+
+
+def _sample_targets(w, n, seed):
+    """Seeded target leaves, plus the leaf nearest to each Gaussian centre and leaves on the faces."""
+    rng = np.random.default_rng(seed)
+    tg = set(rng.choice(w.tree.n_leaves, n, replace=False).tolist())
+    lev = w.tree.level.astype(np.float64)
+    centre = (w.tree.coord + 0.5) / (2.0 ** lev)[:, None] - 0.5
+    for c in w.meta.get("centers", [])[:8]:
+        tg.add(int(np.argmin(((centre - c) ** 2).sum(axis=1))))
+    on_face = np.where(np.any((w.tree.coord == 0) | (w.tree.coord == (2 ** w.tree.level)[:, None] - 1), axis=1))[0]
+    tg.update(rng.choice(on_face, min(4, len(on_face)), replace=False).tolist())
+    return np.array(sorted(tg))
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-6), (0, 1e-10), (2, 1e-6)])
+def test_full_size_adaptive_workload_sampled(prec, tol):
+    """The benchmark's 3D free-space adaptive workload (2.09M points, delta 1e-3) as the
+    benchmark runs it, checked on sampled target leaves."""
+    w = W.config_3d_free_adaptive(seed=0, p=8, delta=1e-3)
+    check(3, w.p, w.delta, tol, w.tree, w.sigma, prec=prec, targets=_sample_targets(w, 24, 5))
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-6), (0, 1e-10)])
+def test_full_size_periodic_workload_sampled(prec, tol):
+    """3D periodic, uniform level 5 (16.8M points), sampled target leaves."""
+    w = W.config_3d_periodic_uniform(seed=0)
+    check(3, w.p, w.delta, tol, w.tree, w.sigma, bc=1, prec=prec, targets=_sample_targets(w, 16, 6))
