@@ -98,7 +98,14 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def roofline_of(info, prof, nprof, prec):
+# DRAM bytes (read + write) of one step's launches of a phase, from one ncu capture of the
+# benchmark command on this workload (profiles/split_kernels_adaptive3d.md: the evaluation's
+# three per-size launches, 26.2 + 13.5 + 1.0 MB read, nothing written back within the capture).
+# Keyed by (workload, form, phase); phases without a capture report null.
+NCU_TRAFFIC = {("adaptive3d", "split_tol1e-6", "evaluate"): 40.7e6}
+
+
+def roofline_of(info, prof, nprof, prec, traffic_key=None):
     """Dominant phase of one form (per-phase CUDA events over the timed region) against the
     ALU peak it is bound by: algorithmic flops of the phase / its average time per step."""
     phase_flops = {"form": info["form_flops"], "evaluate": info["eval_flops"], "gather": info["gather_flops"],
@@ -109,8 +116,9 @@ def roofline_of(info, prof, nprof, prec):
     achieved = phase_flops[dom] / (ms / 1e3) / 1e12
     fp32 = prec == 1 and dom in ("form", "evaluate", "gather")
     peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
+    traffic = NCU_TRAFFIC.get(traffic_key + (dom,)) if traffic_key else None
     return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": traffic,
             "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if fp32 else
                             "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"),
             "phase_ms_per_step": {k: v / n for k, v in prof.items()}}
@@ -404,7 +412,7 @@ def main():
             times = time_steps(plan, sigma, out, args.steps, args.warmup, flush)
         prof, nprof = plan.read_profile()
         plan.set_profiling(False)
-        form_roofline = roofline_of(info, prof, nprof, prec)
+        form_roofline = roofline_of(info, prof, nprof, prec, (args.workload, name))
         if is_head:
             head = dict(name=name, plan=plan, info=info, prof=prof, nprof=nprof, times=times, tol=tol, prec=prec,
                         roofline=form_roofline)
