@@ -278,8 +278,9 @@ def run_serving(F, torch):
 
 def run_sweeps(args, F, torch, w_head, flush):
     """The delta sweep of the 3D adaptive workload (delta 1e-4 and 1e-2 next to the headline's
-    1e-3) in every form, and the 3D periodic uniform workload (16.8M points) in split precision
-    at tol 1e-6 and FP64 at tol 1e-10.  Fewer steps than the headline (each row says how many)."""
+    1e-3) in every form, the paper-shaped k = 16 workloads over delta 1e-10 .. 1, and the 3D
+    periodic uniform workload (16.8M points), split precision at tol 1e-6 and FP64 at tol 1e-10.
+    Fewer steps than the headline (each row says how many)."""
     out = {"delta_sweep": {}, "periodic3d": {}}
     steps, warm = max(3, args.steps // 4), 2
 
@@ -292,9 +293,10 @@ def run_sweeps(args, F, torch, w_head, flush):
         return {"ms_per_step": ms, "points_per_s": w.n_points / ms * 1e3, "steps": steps,
                 "cutoff_level": info["cutoff_level"], "n_f": info["n_f"]}
 
+    import dataclasses
+    import workloads as W_
     sig = torch.from_numpy(w_head.sigma).cuda()
     o = torch.empty_like(sig)
-    import dataclasses
     for delta in (1e-4, 1e-2):
         wd = dataclasses.replace(w_head, delta=delta)
         row = {}
@@ -303,6 +305,20 @@ def run_sweeps(args, F, torch, w_head, flush):
             row[name] = one(wd, sig, o, tol, prec)
         out["delta_sweep"][f"{delta:g}"] = row
     del sig, o
+    # the paper's experiment shapes (Section 6): sigma_f (five centres, alpha_i = 4e-3 / i) and the
+    # periodic sigma_p (n_p = 4), k = 16, delta from 1e-10 to 1
+    out["paper_shaped"] = {}
+    wf = W_.paper_sigma_f(d=3, p=16, target_points=2_000_000)
+    wpp = W_.paper_sigma_p(d=3, p=16, n_p=4, level=3)
+    for wk, deltas in ((wf, (1e-10, 1e-8, 1e-6, 1e-4, 1e-3, 1e-2, 1e-1, 1.0)), (wpp, (1e-6, 1e-4, 1e-3, 1e-2, 1.0))):
+        sig = torch.from_numpy(wk.sigma).cuda()
+        o = torch.empty_like(sig)
+        rows = {"workload": workload_text(wk)}
+        for delta in deltas:
+            wd = dataclasses.replace(wk, delta=delta)
+            rows[f"{delta:g}"] = {FORMS[f][0]: one(wd, sig, o, FORMS[f][1], FORMS[f][2]) for f in ("split", "fp64_1e-10")}
+        out["paper_shaped"][wk.name] = rows
+        del sig, o
     wp = workload("periodic3d")
     sig = torch.from_numpy(wp.sigma).cuda()
     o = torch.empty_like(sig)

@@ -86,6 +86,7 @@ struct ExecDesc {
   const NearSrc *near_src = nullptr;
   const double *near_tab = nullptr;
   const NearPair *near_pairs = nullptr;  // flattened D-list, one CTA per pair
+  const int16_t *near_band = nullptr;    // per table and row: first and last kept column
   int64_t n_near_pairs = 0;
   int64_t n_points = 0;                  // n_leaves * k^d
   int zero_u = 0;                        // clear u first (near field or accumulating evaluation)

@@ -1821,21 +1821,28 @@ __global__ void push_kernel(const TreeShift *__restrict__ items, const typename 
 
 // One D-list pair per CTA: u_T += (K_d x ... x K_1) sigma_S with the three k x k tables of the
 // pair, added to u with FP64 atomics (u is cleared before the evaluation step stores into it).
-// Pair-parallel so that many pairs are in flight at once; the tables and sigma_S are staged in
-// shared memory.
+// Pair-parallel so that many pairs are in flight at once; the tables, their row bands and sigma_S
+// are staged in shared memory.  Each row of a table is applied over its band only (the columns
+// whose entries matter): the full row for wide Gaussians, a few columns as delta -> 0.
 template <int D>
 __global__ void __launch_bounds__(128) near2_kernel(const NearPair *__restrict__ pairs, const double *__restrict__ tab,
+                                                    const int16_t *__restrict__ band,
                                                     const double *__restrict__ sigma, double *__restrict__ u, int k) {
   extern __shared__ double sm[];
   const int kk = k * k;
   const int np = (D == 3) ? kk * k : kk;
   double *s0 = sm, *A = sm + np, *B = A + np, *T = B + np;
+  int16_t *bd = reinterpret_cast<int16_t *>(T + D * kk);  // [D][k][2]
   const NearPair pr = pairs[blockIdx.x];
   const double *sg = sigma + pr.src * np;
   for (int e = threadIdx.x; e < np; e += blockDim.x) s0[e] = __ldg(sg + e);
   for (int e = threadIdx.x; e < D * kk; e += blockDim.x) {
     const int a = e / kk;
     T[e] = __ldg(tab + (int64_t)pr.tab[a] * kk + (e - a * kk));
+  }
+  for (int e = threadIdx.x; e < D * 2 * k; e += blockDim.x) {
+    const int a = e / (2 * k);
+    bd[e] = __ldg(band + (int64_t)pr.tab[a] * 2 * k + (e - a * 2 * k));
   }
   __syncthreads();
   double *ut = u + pr.tgt * np;
@@ -1844,23 +1851,26 @@ __global__ void __launch_bounds__(128) near2_kernel(const NearPair *__restrict__
       const int row = e / k, t1 = e - row * k;
       const double *sp = s0 + row * k, *tp = T + t1 * k;
       double a = 0;
-      for (int j = 0; j < k; ++j) a = fma(tp[j], sp[j], a);
+      for (int j = bd[2 * t1]; j <= bd[2 * t1 + 1]; ++j) a = fma(tp[j], sp[j], a);
       A[e] = a;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < np; e += blockDim.x) {  // B[j3][t2][t1] = sum_j2 T2[t2][j2] A[j3][j2][t1]
       const int j3 = e / kk, rem = e - j3 * kk, t2 = rem / k, t1 = rem - t2 * k;
       const double *tp = T + kk + t2 * k, *ap = A + j3 * kk + t1;
+      const int16_t *b2 = bd + 2 * k + 2 * t2;
       double a = 0;
-      for (int j = 0; j < k; ++j) a = fma(tp[j], ap[j * k], a);
+      for (int j = b2[0]; j <= b2[1]; ++j) a = fma(tp[j], ap[j * k], a);
       B[e] = a;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < np; e += blockDim.x) {  // u[t3][t2][t1] += sum_j3 T3[t3][j3] B[j3][t2][t1]
       const int t3 = e / kk, rem = e - t3 * kk;
       const double *tp = T + 2 * kk + t3 * k, *bp = B + rem;
+      const int16_t *b3 = bd + 4 * k + 2 * t3;
+      if (b3[1] < b3[0]) continue;
       double a = 0;
-      for (int j = 0; j < k; ++j) a = fma(tp[j], bp[j * kk], a);
+      for (int j = b3[0]; j <= b3[1]; ++j) a = fma(tp[j], bp[j * kk], a);
       atomicAdd(ut + e, a);
     }
   } else {
@@ -1868,15 +1878,17 @@ __global__ void __launch_bounds__(128) near2_kernel(const NearPair *__restrict__
       const int j2 = e / k, t1 = e - j2 * k;
       const double *sp = s0 + j2 * k, *tp = T + t1 * k;
       double a = 0;
-      for (int j = 0; j < k; ++j) a = fma(tp[j], sp[j], a);
+      for (int j = bd[2 * t1]; j <= bd[2 * t1 + 1]; ++j) a = fma(tp[j], sp[j], a);
       A[e] = a;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < np; e += blockDim.x) {  // u[t2][t1] += sum_j2 T2[t2][j2] A[j2][t1]
       const int t2 = e / k, t1 = e - t2 * k;
       const double *tp = T + kk + t2 * k, *ap = A + t1;
+      const int16_t *b2 = bd + 2 * k + 2 * t2;
+      if (b2[1] < b2[0]) continue;
       double a = 0;
-      for (int j = 0; j < k; ++j) a = fma(tp[j], ap[j * k], a);
+      for (int j = b2[0]; j <= b2[1]; ++j) a = fma(tp[j], ap[j * k], a);
       atomicAdd(ut + e, a);
     }
   }
@@ -2050,11 +2062,11 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
   // plan's second stream (forked after the clear of u, joined before returning) when one exists
   auto launch_near = [&](cudaStream_t ns) -> cudaError_t {
     const int np = D == 3 ? e.k * e.k * e.k : e.k * e.k;
-    const size_t nsm = sizeof(double) * (3 * (size_t)np + (size_t)D * e.k * e.k);
+    const size_t nsm = sizeof(double) * (3 * (size_t)np + (size_t)D * e.k * e.k) + sizeof(int16_t) * 2 * D * e.k;
     cudaError_t r = cudaFuncSetAttribute(near2_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nsm);
     if (r != cudaSuccess) return r;
     if (e.events) cudaEventRecord(e.events[10], ns);
-    near2_kernel<D><<<(unsigned)e.n_near_pairs, 128, nsm, ns>>>(e.near_pairs, e.near_tab, sigma, u, e.k);
+    near2_kernel<D><<<(unsigned)e.n_near_pairs, 128, nsm, ns>>>(e.near_pairs, e.near_tab, e.near_band, sigma, u, e.k);
     r = cudaGetLastError();
     if (e.events) cudaEventRecord(e.events[11], ns);
     return r;

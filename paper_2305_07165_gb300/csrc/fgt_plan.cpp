@@ -920,7 +920,34 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
     }
   }
   ex.n_near = (int64_t)ntgt.size();
-  P.n_near_pairs = (int64_t)nsrc.size();
+  // Bands of the near-field tables: as delta -> 0 the 1D tables concentrate on their diagonal
+  // (a node only sees the part of the source polynomial within a few sqrt(delta)), so each row
+  // keeps only its entries above eta * (largest entry of the level's tables), eta = 1e-7 eps_pw
+  // (a row's dropped part is then below k^3 eta of the pair's magnitude in 3D, k <= 32).  A pair
+  // with an all-zero table along some axis contributes nothing and is dropped.
+  std::vector<int16_t> nband((ntab.size() / std::max<size_t>((size_t)k * k, 1)) * k * 2, 0);
+  std::vector<char> tab_empty(nband.size() / std::max(2 * k, 1), 0);
+  {
+    const size_t kk = (size_t)k * k, ntables = ntab.size() / std::max<size_t>(kk, 1);
+    for (size_t l0 = 0; l0 < ntables; l0 += fgt::kNearTypes) {
+      double mx = 0.0;
+      for (size_t t = l0; t < std::min(ntables, l0 + fgt::kNearTypes); ++t)
+        for (size_t e = 0; e < kk; ++e) mx = std::max(mx, std::fabs(ntab[t * kk + e]));
+      const double thr = 1e-7 * P.eps_pw * mx;
+      for (size_t t = l0; t < std::min(ntables, l0 + fgt::kNearTypes); ++t) {
+        bool any = false;
+        for (int r = 0; r < k; ++r) {
+          int lo = k, hi = -1;
+          for (int j = 0; j < k; ++j)
+            if (std::fabs(ntab[t * kk + (size_t)r * k + j]) > thr) { lo = std::min(lo, j); hi = j; }
+          nband[(t * k + r) * 2] = (int16_t)lo;
+          nband[(t * k + r) * 2 + 1] = (int16_t)hi;
+          any = any || hi >= lo;
+        }
+        tab_empty[t] = any ? 0 : 1;
+      }
+    }
+  }
   std::vector<fgt::NearPair> npairs;
   npairs.reserve(nsrc.size());
   for (size_t i = 0; i < ntgt.size(); ++i)
@@ -928,10 +955,15 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
       fgt::NearPair pr{};
       pr.tgt = ntgt[i];
       pr.src = nsrc[q].leaf;
-      for (int a = 0; a < 3; ++a) pr.tab[a] = nsrc[q].tab[a];
-      npairs.push_back(pr);
+      bool empty = false;
+      for (int a = 0; a < 3; ++a) {
+        pr.tab[a] = nsrc[q].tab[a];
+        if (a < d && tab_empty[(size_t)pr.tab[a]]) empty = true;
+      }
+      if (!empty) npairs.push_back(pr);
     }
   ex.n_near_pairs = (int64_t)npairs.size();
+  P.n_near_pairs = ex.n_near_pairs;
   {
     bool acc_blocks = false;
     for (const fgt::Block &b : blocks) acc_blocks = acc_blocks || (b.flags & 1);
@@ -966,6 +998,7 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   const size_t o_ntgt = pack.add("near_tgt", ntgt), o_nflags = pack.add("near_flags", nflags),
                o_nptr = pack.add("near_ptr", nptr), o_nsrc = pack.add("near_src", nsrc),
                o_ntab = pack.add("near_tab", ntab), o_npairs = pack.add("near_pairs", npairs);
+  const size_t o_nband = pack.add("near_band", nband);
   std::vector<std::tuple<size_t, size_t, size_t, int64_t>> step_off;  // items, qf, qh, n
   for (size_t i = 0; i < merge_h.size(); ++i) {
     auto &s = merge_h[i];
@@ -1041,6 +1074,7 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   ex.near_src = (const fgt::NearSrc *)at(o_nsrc);
   ex.near_tab = (const double *)at(o_ntab);
   ex.near_pairs = (const fgt::NearPair *)at(o_npairs);
+  ex.near_band = (const int16_t *)at(o_nband);
   size_t si = 0;
   for (size_t s = 0; s < merge_h.size(); ++s, ++si) {
     fgt::ShiftStep st;

@@ -268,3 +268,23 @@ def test_full_size_periodic_workload_sampled(prec, tol):
     """3D periodic, uniform level 5 (16.8M points), sampled target leaves."""
     w = W.config_3d_periodic_uniform(seed=0)
     check(3, w.p, w.delta, tol, w.tree, w.sigma, bc=1, prec=prec, targets=_sample_targets(w, 16, 6))
+
+
+@pytest.mark.parametrize("delta", [1e-10, 1e-6, 1e-3, 1e-1, 1.0])
+@pytest.mark.parametrize("prec,tol", [(1, 1e-6), (0, 1e-10)])
+def test_paper_free_space_density_k16(delta, prec, tol):
+    """The paper's free-space experiment shape (Section 6): sigma_f with its five centres,
+    alpha_i = 4e-3 / i, k = 16 nodes per axis, delta from 1e-10 (all direct) to 1 (root expansion)."""
+    w = W.paper_sigma_f(d=3, p=16, target_points=200_000)
+    check(3, 16, delta, tol, w.tree, w.sigma, prec=prec)
+
+
+@pytest.mark.parametrize("delta", [1e-4, 1e-3, 1e-2])
+def test_paper_periodic_density_k16(delta):
+    """The paper's periodic density (eq. sigmap, n_p = 4) at k = 16: an eigenfunction of the
+    periodic kernel, so u = (sqrt(pi delta) exp(-pi^2 delta n_p^2))^3 sigma up to interpolation."""
+    w = W.paper_sigma_p(d=3, p=16, n_p=4, level=2)
+    check(3, 16, delta, 1e-10, w.tree, w.sigma, bc=1)
+    lam = (np.sqrt(np.pi * delta) * np.exp(-np.pi ** 2 * delta * 16)) ** 3
+    ug, _ = gpu_u(3, 16, delta, 1e-10, w.tree, w.sigma, bc=1)
+    assert np.abs(ug - lam * w.sigma).max() <= 1e-8 * np.abs(lam * w.sigma).max()

@@ -258,6 +258,39 @@ def config_3d_periodic_uniform(seed=0, p=8, level=5, delta=1e-3, n_gauss=16, noi
                     dict(seed=seed, centers=centers, alphas=widths ** 2, noise=noise))
 
 
+# centres of the paper's free-space density (Section 6, eqs. sigmaf / xi3d); in 2D their projections
+# on the x_1 x_2 plane
+PAPER_SIGMA_F_CENTRES_3D = np.array([(-0.3, -0.4, -0.06), (-0.2, 0.0, -0.25), (0.18, -0.1, -0.03),
+                                     (-0.09, 0.3, 0.17), (-0.38, -0.05, -0.17)])
+
+
+def paper_sigma_f(d=3, p=16, delta=1e-3, n_g=5, alpha1=None, target_points=None, beta=4.0, max_level=10):
+    """The paper's free-space experiment (Section 6): sigma_f = sum_i exp(-|x - x_i|^2 / alpha_i)
+    with its five centres, alpha_i = alpha_1 / i (alpha_1 = 4e-3 in 3D, 1e-5 in 2D), k = 16
+    nodes per axis.  The tree is refined geometrically around the centres (widths sqrt(alpha_i))
+    and 2:1 balanced; with target_points set, the refinement ratio is tuned to about that size."""
+    if alpha1 is None:
+        alpha1 = 4e-3 if d == 3 else 1e-5
+    centers = PAPER_SIGMA_F_CENTRES_3D[:n_g, :d]
+    alphas = alpha1 / np.arange(1, n_g + 1)
+    widths = np.sqrt(alphas)
+    if target_points is None:
+        rho, tree = 1.0, gaussian_refined_tree(d, centers, widths, 1.0, beta, max_level)
+    else:
+        rho, tree = _tune_rho(d, centers, widths, target_points / p ** d, beta, max_level, False)
+    sigma = gaussian_sum(node_positions(tree, p), centers, alphas)
+    return Workload(f"paper-sigma-f-{d}d-p{p}", d, p, delta, False, tree, sigma,
+                    dict(centers=centers, alphas=alphas, rho=rho, beta=beta))
+
+
+def paper_sigma_p(d=3, p=16, delta=1e-3, n_p=4, level=3):
+    """The paper's periodic experiment (Section 6, eq. sigmap): trig density with n_p = 4 in 3D
+    (32 in 2D) on a uniform tree, k = 16."""
+    tree = uniform_tree(d, level, periodic=True)
+    sigma = trig_density(node_positions(tree, p), n_p)
+    return Workload(f"paper-sigma-p-{d}d-p{p}-l{level}", d, p, delta, True, tree, sigma, dict(n_p=n_p))
+
+
 def batched_configs(seed=0, n=256, max_points=1 << 18):
     """n independent free-space transforms: d in {2,3}, tree depth U{2..7}, p in {8,12,16},
     delta log-U[1e-5, 1e-1], sigma a sum of 1..8 Gaussians (widths log-U[1e-2, 2e-1]).  Each
