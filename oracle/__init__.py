@@ -44,6 +44,11 @@ def _load():
                 ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_long,
                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                 ctypes.c_long, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+            lib.oracle_box_fgt_boxes.restype = ctypes.c_int
+            lib.oracle_box_fgt_boxes.argtypes = [
+                ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_long,
+                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                ctypes.c_long, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
             lib.oracle_gauss_legendre.restype = ctypes.c_int
             lib.oracle_gauss_legendre.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
             lib.oracle_default_threads.restype = ctypes.c_int
@@ -82,4 +87,21 @@ def box_fgt(d, p, delta, periodic, leaf_level, leaf_coord, sigma, targets=None, 
                                 len(tg), tg.ctypes.data, u.ctypes.data, int(threads))
     if rc != 0:
         raise RuntimeError(f"oracle_box_fgt failed ({rc})")
+    return u
+
+
+def box_fgt_boxes(d, p, delta, periodic, leaf_level, leaf_coord, sigma, tgt_level, tgt_coord, threads=0):
+    """u[n_boxes, p**d] at the nodes of target boxes given by their own level and coordinates
+    (for example the leaves of an output tree that refines or coarsens the source tree)."""
+    lev = np.ascontiguousarray(leaf_level, dtype=np.int32)
+    crd = np.ascontiguousarray(leaf_coord, dtype=np.int32).reshape(-1)
+    sig = np.ascontiguousarray(sigma, dtype=np.float64).reshape(len(lev), p ** d)
+    tl = np.ascontiguousarray(tgt_level, dtype=np.int32)
+    tc = np.ascontiguousarray(tgt_coord, dtype=np.int32).reshape(-1)
+    u = np.zeros((len(tl), p ** d))
+    rc = _load().oracle_box_fgt_boxes(int(d), int(p), float(delta), int(bool(periodic)), len(lev),
+                                      lev.ctypes.data, crd.ctypes.data, sig.ctypes.data,
+                                      len(tl), tl.ctypes.data, tc.ctypes.data, u.ctypes.data, int(threads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_box_fgt_boxes failed ({rc})")
     return u

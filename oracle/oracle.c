@@ -100,7 +100,8 @@ typedef struct {
   const int *level, *coord;
   const double *sigma;
   long n_targets;
-  const long *targets;
+  const long *targets;           /* target leaves of the source tree, or */
+  const int *tlevel, *tcoord;    /* target boxes of their own (tlevel != NULL) */
   double *u;
   long next;                     /* work counter (guarded by mtx) */
   pthread_mutex_t mtx;
@@ -185,12 +186,13 @@ static void kcache_clear(kcache *kc) {
   kc->n = 0;
 }
 
-/* squared distance between two boxes (minimum image when periodic) */
-static double box_dist2(const orc_ctx *C, long T, long S) {
+/* squared distance between a target box (level lt, coordinates tc) and source leaf S (minimum
+ * image when periodic) */
+static double box_dist2(const orc_ctx *C, int lt, const int *tc, long S) {
   double d2 = 0.0;
   for (int i = 0; i < C->d; i++) {
-    int lt = C->level[T], ls = C->level[S];
-    double ct = box_center(lt, C->coord[T * C->d + i]);
+    int ls = C->level[S];
+    double ct = box_center(lt, tc[i]);
     double cs = box_center(ls, C->coord[S * C->d + i]);
     double half = 0.5 * (ldexp(1.0, -lt) + ldexp(1.0, -ls));
     double dc = fabs(ct - cs);
@@ -203,20 +205,27 @@ static double box_dist2(const orc_ctx *C, long T, long S) {
 
 static void one_target(orc_ctx *C, long ti, kcache kc[3], double *work) {
   int d = C->d, p = C->p;
-  long T = C->targets[ti];
+  int lt;
+  const int *tc;
+  if (C->tlevel) {
+    lt = C->tlevel[ti];
+    tc = C->tcoord + ti * C->d;
+  } else {
+    lt = C->level[C->targets[ti]];
+    tc = C->coord + C->targets[ti] * C->d;
+  }
   int np = 1;
   for (int i = 0; i < d; i++) np *= p;
   double *sum = work, *comp = work + np, *A = work + 2 * np, *Bm = work + 3 * np, *Cm = work + 4 * np;
   for (int q = 0; q < np; q++) { sum[q] = 0.0; comp[q] = 0.0; }
-  int lt = C->level[T];
   double Lt = ldexp(1.0, -lt);
   double r2 = C->delta * log(1.0 / ORC_CUT);
   for (int i = 0; i < d; i++) kcache_clear(&kc[i]);
   for (long S = 0; S < C->n_leaves; S++) {
-    if (box_dist2(C, T, S) > r2) continue;
+    if (box_dist2(C, lt, tc, S) > r2) continue;
     const double *K[3] = {NULL, NULL, NULL};
     for (int i = 0; i < d; i++) {
-      K[i] = kcache_get(C, &kc[i], box_center(lt, C->coord[T * d + i]), Lt, C->level[S], C->coord[S * d + i]);
+      K[i] = kcache_get(C, &kc[i], box_center(lt, tc[i]), Lt, C->level[S], C->coord[S * d + i]);
       if (!K[i]) { C->err = 1; return; }
     }
     const double *sg = C->sigma + S * np;
@@ -318,6 +327,43 @@ int oracle_box_fgt(int d, int p, double delta, int periodic, long n_leaves,
   C.n_targets = n_targets; C.targets = targets; C.u = u_out;
   for (long t = 0; t < n_targets; t++)
     if (targets[t] < 0 || targets[t] >= n_leaves) return 1;
+  pthread_mutex_init(&C.mtx, NULL);
+  int nt = n_threads > 0 ? n_threads : oracle_default_threads();
+  if (nt > 256) nt = 256;
+  pthread_t th[256];
+  int started = 0;
+  for (int i = 0; i < nt; i++)
+    if (pthread_create(&th[i], NULL, worker, &C) == 0) started++; else break;
+  if (started == 0) worker(&C);
+  for (int i = 0; i < started; i++) pthread_join(th[i], NULL);
+  pthread_mutex_destroy(&C.mtx);
+  return C.err;
+}
+
+/*
+ * u at the nodes of target boxes of their own: box t has level tgt_level[t] and integer
+ * coordinates tgt_coord[t*d .. t*d+d) (any level, 0 <= coordinate < 2^level), its nodes laid out
+ * like a leaf's.  Used for output trees that refine or coarsen the source tree (Algorithms 5, 6).
+ */
+int oracle_box_fgt_boxes(int d, int p, double delta, int periodic, long n_leaves,
+                         const int *leaf_level, const int *leaf_coord, const double *sigma,
+                         long n_tboxes, const int *tgt_level, const int *tgt_coord, double *u_out, int n_threads) {
+  if ((d != 2 && d != 3) || p < 1 || p > ORC_MAXP || !(delta > 0) || n_leaves < 0 || n_tboxes < 0)
+    return 1;
+  for (long t = 0; t < n_tboxes; t++) {
+    if (tgt_level[t] < 0 || tgt_level[t] > 30) return 1;
+    for (int i = 0; i < d; i++)
+      if (tgt_coord[t * d + i] < 0 || tgt_coord[t * d + i] >= (1 << tgt_level[t])) return 1;
+  }
+  orc_ctx C;
+  memset(&C, 0, sizeof(C));
+  C.d = d; C.p = p; C.periodic = periodic ? 1 : 0; C.delta = delta;
+  C.rcut = sqrt(delta * log(1.0 / ORC_CUT));
+  C.nq = p + 16 > 24 ? p + 16 : 24;
+  gauss_legendre(p, C.eta, C.weta);
+  gauss_legendre(C.nq, C.xq, C.wq);
+  C.n_leaves = n_leaves; C.level = leaf_level; C.coord = leaf_coord; C.sigma = sigma;
+  C.n_targets = n_tboxes; C.tlevel = tgt_level; C.tcoord = tgt_coord; C.u = u_out;
   pthread_mutex_init(&C.mtx, NULL);
   int nt = n_threads > 0 ? n_threads : oracle_default_threads();
   if (nt > 256) nt = 256;

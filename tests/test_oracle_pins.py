@@ -227,3 +227,49 @@ def test_golden_values():
                            np.array(c["coord"]), np.array(c["sigma"]))
         ref = np.array(c["u"])
         assert np.abs(u - ref).max() <= 1e-13 * np.abs(ref).max(), key
+
+
+def _children(tree, depth=1):
+    """Boxes `depth` levels below every leaf (an output tree refining the source tree)."""
+    d = tree.d
+    lev, crd = tree.level.copy(), tree.coord.copy()
+    for _ in range(depth):
+        off = np.array([[(c >> a) & 1 for a in range(d)] for c in range(1 << d)], dtype=np.int32)
+        crd = (2 * crd[:, None, :] + off[None, :, :]).reshape(-1, d)
+        lev = np.repeat(lev + 1, 1 << d)
+    return W.Tree(d, lev.astype(np.int32), crd.astype(np.int32), tree.periodic)
+
+
+@pytest.mark.parametrize("d,p,delta,depth", [(2, 8, 1e-2, 1), (2, 6, 1e-4, 2), (3, 5, 1e-2, 1)])
+def test_target_boxes_constant_density_free_space(d, p, delta, depth):
+    """u at the nodes of boxes refining the tree (Algorithm 5's output tree): sigma = 1 gives
+    the product of erf differences at any point."""
+    tr = W.random_balanced_tree(d, 11, max_level=3 if d == 2 else 2, min_level=1)
+    out = _children(tr, depth)
+    u = oracle.box_fgt_boxes(d, p, delta, False, tr.level, tr.coord, np.ones((tr.n_leaves, p ** d)),
+                             out.level, out.coord)
+    ex = _u_const_free(W.node_positions(out, p), delta)
+    assert np.abs(u - ex).max() <= 1e-13 * np.abs(ex).max()
+
+
+@pytest.mark.parametrize("d,p,delta", [(2, 16, 1e-2), (3, 12, 1e-2)])
+def test_target_boxes_periodic_eigenfunction_and_coarser_boxes(d, p, delta):
+    """Periodic trig density: u = lambda sigma_p at the nodes of finer and of coarser boxes."""
+    tr = W.uniform_tree(d, 2, periodic=True)
+    s = W.trig_density(W.node_positions(tr, p), 1)
+    lam = (np.sqrt(np.pi * delta) * np.exp(-np.pi ** 2 * delta)) ** d
+    for out in (_children(tr, 1), W.uniform_tree(d, 1, periodic=True)):
+        u = oracle.box_fgt_boxes(d, p, delta, True, tr.level, tr.coord, s, out.level, out.coord)
+        ex = lam * W.trig_density(W.node_positions(out, p), 1)
+        assert np.abs(u - ex).max() <= 1e-10 * np.abs(ex).max()
+
+
+def test_target_boxes_gaussian_density_closed_form():
+    d, p, delta = 2, 16, 1e-3
+    centers, alphas = np.array([[0.1, -0.2], [-0.25, 0.15]]), np.array([0.02, 0.01])
+    tr = W.gaussian_refined_tree(d, centers, np.sqrt(alphas), rho=1.5, beta=3.0, max_level=5, min_level=2)
+    s = W.gaussian_sum(W.node_positions(tr, p), centers, alphas)
+    out = _children(tr, 1)
+    u = oracle.box_fgt_boxes(d, p, delta, False, tr.level, tr.coord, s, out.level, out.coord)
+    ex = _gauss_closed_form(W.node_positions(out, p), centers, alphas, delta)
+    assert np.abs(u - ex).max() <= 1e-8 * np.abs(ex).max()
