@@ -203,6 +203,17 @@ fgt_status fgt_execute_batch(fgt_plan *const *plans, const double *const *sigma_
 fgt_status fgt_plan_set_profiling(fgt_plan *plan, int on);
 fgt_status fgt_plan_read_profile(fgt_plan *plan, double *ms, int *n_transforms);
 
+/* Output tree (Algorithm 5, tree refinement): evaluate u at the nodes of the leaves of `out`
+ * instead of the source tree's own leaves.  Every output leaf must lie inside one source leaf (at
+ * its level or finer, levels <= 20) and the output leaves must tile every source leaf without
+ * overlap; FGT_ERR_TREE otherwise.  The transform keeps the source tree's interaction lists: an
+ * output leaf takes the plane-wave expansion and the near-field sources of the source leaf that
+ * contains it, through evaluation matrices and near-field tables for its own nodes.  After this
+ * call fgt_execute* write u as [out->n_leaves][k^d] (leaf order of `out`); sigma is unchanged.
+ * out == NULL (or out->n_leaves == 0) restores the source tree.  Fused mode only.  The plan is
+ * re-planned at its next execution. */
+fgt_status fgt_plan_set_output_tree(fgt_plan *plan, const fgt_tree *out);
+
 /* Launch-shape knobs of a plan and the autotuner that picks them.
  *   form_group:      at most this many same-size blocks of one anchor per form CTA (1..8)
  *   eval_rows16:     split precision, 3D: rows of a K = 16 block per evaluation CTA (4, 8, 16)

@@ -97,6 +97,7 @@ def lib():
             L.fgt_plan_set_profiling.argtypes = [vp, i32]
             L.fgt_plan_read_profile.argtypes = [vp, vp, vp]
             L.fgt_plan_autotune.argtypes = [vp, vp, vp, vp, i32, ctypes.POINTER(Tuning)]
+            L.fgt_plan_set_output_tree.argtypes = [vp, ctypes.POINTER(_Tree)]
             L.fgt_plan_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
             L.fgt_plan_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
             L.fgt_destroy.argtypes = [vp]
@@ -114,7 +115,7 @@ def lib():
                          "fgt_gauss_legendre", "fgt_params", "fgt_legendre_gauss_integrals",
                          "fgt_spherical_bessel", "fgt_legendre_fourier_integrals", "fgt_plan_set_profiling",
                          "fgt_plan_read_profile", "fgt_plan_autotune", "fgt_plan_get_tuning",
-                         "fgt_plan_set_tuning"):
+                         "fgt_plan_set_tuning", "fgt_plan_set_output_tree"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -230,15 +231,36 @@ class Plan:
         import torch
         if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
             raise TypeError(f"{name} must be a contiguous CUDA float64 tensor")
-        if x.numel() != self.n_points:
-            raise ValueError(f"{name} must hold n_leaves * k**d = {self.n_points} values")
+        n = self.n_out_points if name == "out" else self.n_points
+        if x.numel() != n:
+            raise ValueError(f"{name} must hold {n} values ({'output' if name == 'out' else 'source'} leaves x k**d)")
+
+    # ---- output tree (Algorithms 5 and 6): u at the nodes of a tree refining the source tree
+    n_out_leaves = None
+
+    @property
+    def n_out_points(self):
+        return (self.n_out_leaves if self.n_out_leaves is not None else self.n_leaves) * self.k ** self.d
+
+    def set_output_tree(self, level=None, coord=None):
+        """Evaluate u at the leaves of an output tree whose every leaf lies inside (or equals) one
+        source leaf and which tiles them (fgt_plan_set_output_tree); None restores the source tree.
+        execute() then returns u as [n_out_leaves, k**d]."""
+        if level is None:
+            _check(lib().fgt_plan_set_output_tree(self._h, None))
+            self.n_out_leaves = None
+            return
+        t, keep = _tree_struct(self.d, self.k, level, coord)
+        _check(lib().fgt_plan_set_output_tree(self._h, ctypes.byref(t)))
+        self.n_out_leaves = int(keep[0].size)
 
     def execute(self, sigma, out=None, stream=None):
         """Enqueue u = transform(sigma) on `stream` (default: torch's current stream)."""
         import torch
         self._check_tensor(sigma, "sigma")
         if out is None:
-            out = torch.empty_like(sigma)
+            out = torch.empty((self.n_out_points // self.k ** self.d, self.k ** self.d), dtype=sigma.dtype,
+                              device=sigma.device)
         self._check_tensor(out, "out")
         s = stream if stream is not None else torch.cuda.current_stream(sigma.device)
         _check(lib().fgt_execute_async(self._h, sigma.data_ptr(), out.data_ptr(), ctypes.c_void_p(s.cuda_stream)))
@@ -287,8 +309,9 @@ class Plan:
         import torch
         for x, n in ((sigma, "sigma"), (out, "out")):
             if isinstance(x, torch.Tensor):
-                if x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous() or x.numel() != self.n_points:
-                    raise TypeError(f"{n} must be a contiguous host float64 tensor of n_points values")
+                want = self.n_out_points if n == "out" else self.n_points
+                if x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous() or x.numel() != want:
+                    raise TypeError(f"{n} must be a contiguous host float64 tensor of {want} values")
             else:
                 raise TypeError(f"{n} must be a host torch tensor")
         s = stream if stream is not None else torch.cuda.current_stream()

@@ -54,7 +54,8 @@ struct ExecDesc {
   const Block *e2_blocks = nullptr;  // whole-block evaluation kernel
   int64_t n_e2 = 0;
   std::vector<LaunchRange> e2_ranges;  // blocks by K
-  const int64_t *block_leaves = nullptr;
+  const int64_t *block_leaves = nullptr;  // form blocks' source leaves
+  const int64_t *eval_leaves = nullptr;   // evaluation blocks' target leaves (u rows)
   // split precision, 3D: sigma converted to FP32 once per transform, block by block (block b's
   // K^3 values at sigp + b.leaf0 k^3, in (J3, J2, J1) order); nullptr: kernels read sigma itself
   float *sigp = nullptr;

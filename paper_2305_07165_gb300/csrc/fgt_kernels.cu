@@ -2178,7 +2178,7 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
         cudaSuccess)
       return err;
     eval_kernel<D, R><<<dim3((unsigned)e.n_e1, (unsigned)e.Kmax_e1), 256, esm, es.next()>>>(
-        e.e1_blocks, e.block_leaves, reinterpret_cast<const C *>(e.Ef), reinterpret_cast<const C *>(e.Eh), eval_src,
+        e.e1_blocks, e.eval_leaves, reinterpret_cast<const C *>(e.Ef), reinterpret_cast<const C *>(e.Eh), eval_src,
         u, e.k, n1, nh, ss);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
@@ -2188,7 +2188,7 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
       if ((err = cudaFuncSetAttribute(tk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) != cudaSuccess)
         return err;
       tk<<<dim3((unsigned)lr.count, (unsigned)((lr.K + kEvalRows - 1) / kEvalRows)), 256, lr.smem, es.next()>>>(
-          e.e2_blocks + lr.first, e.block_leaves,
+          e.e2_blocks + lr.first, e.eval_leaves,
                                                    reinterpret_cast<const float2 *>(e.Ef),
                                                    reinterpret_cast<const float2 *>(e.Eh),
                                                    reinterpret_cast<const float2 *>(eval_src), u, e.k, n1, nh, ss);
@@ -2205,7 +2205,7 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
       if ((err = cudaFuncSetAttribute(k5, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) != cudaSuccess)
         return err;
       k5<<<dim3((unsigned)lr.count, (unsigned)((lr.K + rc - 1) / rc)), 256, lr.smem, es.next()>>>(
-          e.e2_blocks + lr.first, e.block_leaves, reinterpret_cast<const C *>(e.Ef), reinterpret_cast<const C *>(e.Eh),
+          e.e2_blocks + lr.first, e.eval_leaves, reinterpret_cast<const C *>(e.Ef), reinterpret_cast<const C *>(e.Eh),
           eval_src, u, e.k, n1, nh, ss);
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
       continue;
@@ -2219,7 +2219,7 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
       if ((err = cudaFuncSetAttribute(tk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) != cudaSuccess)
         return err;
       tk<<<dim3((unsigned)lr.count, (unsigned)((lr.K + rows4 - 1) / rows4)), 256, lr.smem, es.next()>>>(
-          e.e2_blocks + lr.first, e.block_leaves, reinterpret_cast<const float2 *>(e.Ef),
+          e.e2_blocks + lr.first, e.eval_leaves, reinterpret_cast<const float2 *>(e.Ef),
           reinterpret_cast<const float2 *>(e.Eh), reinterpret_cast<const float2 *>(eval_src), u, e.k, n1, nh, ss);
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
       continue;
@@ -2237,7 +2237,7 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
         cudaSuccess)
       return err;
     kern<<<dim3((unsigned)lr.count, chunks), 256, lr.smem, es.next()>>>(
-        e.e2_blocks + lr.first, e.block_leaves, reinterpret_cast<const C *>(e.Ef), reinterpret_cast<const C *>(e.Eh),
+        e.e2_blocks + lr.first, e.eval_leaves, reinterpret_cast<const C *>(e.Ef), reinterpret_cast<const C *>(e.Eh),
         eval_src, u, e.k, n1, nh, ss);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }

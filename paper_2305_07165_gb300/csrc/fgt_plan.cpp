@@ -100,6 +100,11 @@ struct fgt_plan {
   // tree
   int64_t n_leaves = 0;
   std::vector<int32_t> leaf_level, leaf_coord;
+  // optional output tree (refines the source tree): u is evaluated at its leaves' nodes
+  int64_t n_out = 0;                           // 0: the source tree's own leaves
+  std::vector<int32_t> out_level, out_coord;
+  std::vector<int64_t> out_src;                // source leaf containing each output leaf
+  int64_t n_targets() const { return n_out > 0 ? n_out : n_leaves; }
   std::vector<Box> boxes;
   std::vector<int32_t> children;
   std::unordered_map<uint64_t, int32_t> index;
@@ -113,7 +118,8 @@ struct fgt_plan {
   size_t dev_bytes = 0;
   void *work = nullptr;
   size_t work_bytes = 0;
-  double *stage = nullptr;  // host-path staging [2][n_leaves k^d]
+  double *stage = nullptr;  // host-path staging: sigma [n_leaves k^d], then u [n_targets k^d]
+  size_t stage_elems = 0;
   bool host_only = false;   // planned without a device (inspection only)
   bool tc_eval = false;     // split precision: evaluate with the tensor-core kernel (FGT_TC_EVAL=1)
   bool tc_eval4 = false;    // split precision: stages 2-3 of the evaluation on the tensor cores
@@ -338,15 +344,16 @@ void eval_matrix(const fgt_plan &P, int l, double shift, cd *E) {
 }
 
 // Near-field table (Lemma directbox): K[t][j] = int_S exp(-(x_t - y)^2/delta) l_j(y) dy for a
-// source of level ls and a target whose centre is offset by o4/4 source sides and whose side is
-// ratio times the source side; = (L/2) sum_n J_lambda[P_n](tau_t) Tvp[n][j], lambda = 2 sqrt(delta)/L.
-void near_table(const fgt_plan &P, int ls, int o4, double ratio, double *K) {
+// source of level ls and a target whose centre is offset by tau0 source half-sides and whose side
+// is ratio times the source side; = (L/2) sum_n J_lambda[P_n](tau_t) Tvp[n][j], lambda =
+// 2 sqrt(delta)/L, tau_t = tau0 + ratio eta_t.
+void near_table(const fgt_plan &P, int ls, double tau0, double ratio, double *K) {
   const int k = P.k;
   const double L = std::ldexp(1.0, -ls);
   const double lam = 2.0 * std::sqrt(P.delta) / L;
   double J[72];
   for (int t = 0; t < k; ++t) {
-    const double tau = 0.5 * o4 + ratio * P.eta[t];
+    const double tau = tau0 + ratio * P.eta[t];
     fgt::gauss_legendre_integrals(lam, tau, k - 1, J);
     for (int j = 0; j < k; ++j) {
       double s = 0;
@@ -499,6 +506,7 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   };
   std::vector<int32_t> stack;
   int Kmax = 0;
+  std::vector<int32_t> leaf_anchor(P.n_leaves, -1);  // anchor box of every plane-wave leaf
   auto add_block = [&](int32_t bb, int32_t anchor, int dl) {
     const Box &B = P.boxes[bb];
     const Box &A = P.boxes[anchor];
@@ -522,6 +530,7 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
       for (int a = 0; a < d; ++a) { q[a] = (B.c[a] << dl) + (r % nl); r /= nl; }
       const int32_t lb = P.find(l, q);
       bleaves.push_back(P.boxes[lb].leaf);
+      leaf_anchor[(size_t)P.boxes[lb].leaf] = anchor;
     }
     Kmax = std::max(Kmax, blk.K);
     blocks.push_back(blk);
@@ -549,6 +558,58 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   ex.n_blocks = (int64_t)blocks.size();
   ex.Kmax = Kmax;
   P.n_blocks = ex.n_blocks;
+
+  // ---- evaluation blocks.  Without an output tree they are the form's blocks.  With one (an
+  // output tree refining the source tree, Algorithm 5), an output leaf inside a source leaf B
+  // evaluated by plane waves takes B's anchor: the 2^(d r) leaves of a uniform refinement of B by
+  // r levels form one block of K = 2^r k (when K <= 32), any other output leaf a block of its own.
+  std::vector<fgt::Block> eblocks;
+  std::vector<int64_t> ebleaves;
+  if (P.n_out > 0) {
+    if (hier) return fail(FGT_ERR_ARG, "output trees need the fused mode");
+    std::vector<std::vector<int64_t>> kids((size_t)P.n_leaves);
+    for (int64_t i = 0; i < P.n_out; ++i) kids[(size_t)P.out_src[i]].push_back(i);
+    for (int64_t j = 0; j < P.n_leaves; ++j) {
+      const int32_t an = leaf_anchor[(size_t)j];
+      if (an < 0 || kids[(size_t)j].empty()) continue;  // not evaluated by plane waves
+      const Box &A = P.boxes[an];
+      const Box &B = P.boxes[P.leaf_box[j]];
+      const int lb = B.level;
+      const std::vector<int64_t> &ks = kids[(size_t)j];
+      const int r = P.out_level[(size_t)ks[0]] - lb;
+      bool uniform = ((1 << r) * k <= 32) && (int64_t)ks.size() == ((int64_t)1 << (d * r));
+      for (int64_t i : ks) uniform = uniform && P.out_level[(size_t)i] - lb == r;
+      auto make = [&](int lt, const int32_t *cbase, int dl, const std::vector<int64_t> &leaves) {
+        fgt::Block blk{};
+        blk.slot = A.slot;
+        blk.dl = dl;
+        blk.K = (1 << dl) * k;
+        blk.flags = (lb == P.lc && !P.fourier) ? 1 : 0;  // the near field also adds into these
+        for (int a = 0; a < d; ++a)
+          blk.mat[a] = get_mat(lt, A.level, cbase[a] - (A.c[a] << (lt - A.level)), dl, 0.0);
+        blk.leaf0 = (int64_t)ebleaves.size();
+        ebleaves.insert(ebleaves.end(), leaves.begin(), leaves.end());
+        eblocks.push_back(blk);
+      };
+      if (uniform) {
+        const int nl = 1 << r;
+        std::vector<int64_t> order(ks.size());
+        for (int64_t i : ks) {
+          int idx = 0;
+          for (int a = d - 1; a >= 0; --a) idx = idx * nl + (P.out_coord[(size_t)i * d + a] - (B.c[a] << r));
+          order[(size_t)idx] = i;
+        }
+        int32_t cb[3] = {0, 0, 0};
+        for (int a = 0; a < d; ++a) cb[a] = B.c[a] << r;
+        make(lb + r, cb, r, order);
+      } else {
+        for (int64_t i : ks) make(P.out_level[(size_t)i], &P.out_coord[(size_t)i * d], 0, {i});
+      }
+    }
+  } else {
+    eblocks = blocks;
+    ebleaves = bleaves;
+  }
 
   // ---- kernel choice per block.  Form: blocks whose sigma and matrices fit in shared memory go
   // to the grouped kernel, up to 8 blocks of one anchor and one size per CTA (fewer when they
@@ -642,7 +703,11 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
       return fgt::eval5_bytes(K, n1, nh, csz, 1) <= (size_t)smax ? 1 : 0;
     };
     const bool use_e5 = d == 3 && P.eval5 && !P.tc_eval && !ex.tc64;
-    for (const fgt::Block &b : sorted) {
+    std::vector<fgt::Block> esorted = eblocks;
+    std::stable_sort(esorted.begin(), esorted.end(), [](const fgt::Block &a, const fgt::Block &b) {
+      return a.K != b.K ? a.K < b.K : a.slot < b.slot;
+    });
+    for (const fgt::Block &b : esorted) {
       if (use_e5 && e5_rows(b.K) > 0) {
         const int rc = e5_rows(b.K);
         if (ex.e2_ranges.empty() || ex.e2_ranges.back().K != b.K) {
@@ -915,61 +980,115 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
         int o4, ldiff;
         double ratio;
         kind_geometry(kind, o4, ldiff, ratio);
-        near_table(P, l, o4, ratio, ntab.data() + ((size_t)l * fgt::kNearTypes + kind) * k * k);
+        near_table(P, l, 0.5 * o4, ratio, ntab.data() + ((size_t)l * fgt::kNearTypes + kind) * k * k);
       }
     }
   }
   ex.n_near = (int64_t)ntgt.size();
-  // Bands of the near-field tables: as delta -> 0 the 1D tables concentrate on their diagonal
-  // (a node only sees the part of the source polynomial within a few sqrt(delta)), so each row
-  // keeps only its entries above eta * (largest entry of the level's tables), eta = 1e-7 eps_pw
-  // (a row's dropped part is then below k^3 eta of the pair's magnitude in 3D, k <= 32).  A pair
-  // with an all-zero table along some axis contributes nothing and is dropped.
-  std::vector<int16_t> nband((ntab.size() / std::max<size_t>((size_t)k * k, 1)) * k * 2, 0);
-  std::vector<char> tab_empty(nband.size() / std::max(2 * k, 1), 0);
-  {
-    const size_t kk = (size_t)k * k, ntables = ntab.size() / std::max<size_t>(kk, 1);
-    for (size_t l0 = 0; l0 < ntables; l0 += fgt::kNearTypes) {
-      double mx = 0.0;
-      for (size_t t = l0; t < std::min(ntables, l0 + fgt::kNearTypes); ++t)
-        for (size_t e = 0; e < kk; ++e) mx = std::max(mx, std::fabs(ntab[t * kk + e]));
-      const double thr = 1e-7 * P.eps_pw * mx;
-      for (size_t t = l0; t < std::min(ntables, l0 + fgt::kNearTypes); ++t) {
-        bool any = false;
-        for (int r = 0; r < k; ++r) {
-          int lo = k, hi = -1;
-          for (int j = 0; j < k; ++j)
-            if (std::fabs(ntab[t * kk + (size_t)r * k + j]) > thr) { lo = std::min(lo, j); hi = j; }
-          nband[(t * k + r) * 2] = (int16_t)lo;
-          nband[(t * k + r) * 2 + 1] = (int16_t)hi;
-          any = any || hi >= lo;
+  // The pairs to apply: every D-list pair of the source tree, or with an output tree, each
+  // output leaf paired with the D-list sources of the source leaf containing it, through tables for
+  // the output leaf's own nodes (same source box, target interval of the finer box; Algorithm 5).
+  const size_t kk2 = (size_t)k * k;
+  size_t n_std_tables = ntab.size() / std::max<size_t>(kk2, 1);
+  std::vector<int> tab_ls(n_std_tables);
+  for (size_t t = 0; t < n_std_tables; ++t) tab_ls[t] = (int)(t / fgt::kNearTypes);
+  std::vector<fgt::NearPair> raw;
+  if (P.n_out == 0) {
+    for (size_t i = 0; i < ntgt.size(); ++i)
+      for (int64_t q = nptr[i]; q < nptr[i + 1]; ++q) {
+        fgt::NearPair pr{};
+        pr.tgt = ntgt[i];
+        pr.src = nsrc[q].leaf;
+        for (int a = 0; a < 3; ++a) pr.tab[a] = nsrc[q].tab[a];
+        raw.push_back(pr);
+      }
+  } else {
+    std::vector<int64_t> row_of((size_t)P.n_leaves, -1);
+    for (size_t i = 0; i < ntgt.size(); ++i) row_of[(size_t)ntgt[i]] = (int64_t)i;
+    std::map<std::tuple<int, int, int64_t>, int32_t> extra;  // (source level, target level, offset) -> table
+    for (int64_t ti = 0; ti < P.n_out; ++ti) {
+      const int64_t j = P.out_src[(size_t)ti];
+      const int64_t i = row_of[(size_t)j];
+      if (i < 0) continue;
+      const int lt = P.out_level[(size_t)ti], lb = P.leaf_level[(size_t)j];
+      for (int64_t q = nptr[(size_t)i]; q < nptr[(size_t)i + 1]; ++q) {
+        fgt::NearPair pr{};
+        pr.tgt = ti;
+        pr.src = nsrc[q].leaf;
+        for (int a = 0; a < 3; ++a) pr.tab[a] = nsrc[q].tab[a];
+        if (lt != lb) {
+          for (int a = 0; a < d; ++a) {
+            const int ls = nsrc[q].tab[a] / fgt::kNearTypes, kind = nsrc[q].tab[a] % fgt::kNearTypes;
+            int o4, ldiff;
+            double ratio;
+            kind_geometry(kind, o4, ldiff, ratio);
+            const double Ls = std::ldexp(1.0, -ls), Lt = std::ldexp(1.0, -lt), Lb = std::ldexp(1.0, -lb);
+            const double cb = -0.5 + (P.leaf_coord[(size_t)j * d + a] + 0.5) * Lb;
+            const double ct = -0.5 + (P.out_coord[(size_t)ti * d + a] + 0.5) * Lt;
+            const double off = (ct - cb) + 0.25 * o4 * Ls;  // target centre minus source centre (image)
+            const int64_t key = std::llround(off / (0.25 * std::min(Lt, Ls)));
+            auto it = extra.find({ls, lt, key});
+            int32_t id;
+            if (it == extra.end()) {
+              id = (int32_t)(ntab.size() / kk2);
+              ntab.resize(ntab.size() + kk2);
+              near_table(P, ls, off / (0.5 * Ls), Lt / Ls, ntab.data() + (size_t)id * kk2);
+              tab_ls.push_back(ls);
+              extra.emplace(std::make_tuple(ls, lt, key), id);
+            } else {
+              id = it->second;
+            }
+            pr.tab[a] = id;
+          }
         }
-        tab_empty[t] = any ? 0 : 1;
+        raw.push_back(pr);
       }
     }
   }
-  std::vector<fgt::NearPair> npairs;
-  npairs.reserve(nsrc.size());
-  for (size_t i = 0; i < ntgt.size(); ++i)
-    for (int64_t q = nptr[i]; q < nptr[i + 1]; ++q) {
-      fgt::NearPair pr{};
-      pr.tgt = ntgt[i];
-      pr.src = nsrc[q].leaf;
-      bool empty = false;
-      for (int a = 0; a < 3; ++a) {
-        pr.tab[a] = nsrc[q].tab[a];
-        if (a < d && tab_empty[(size_t)pr.tab[a]]) empty = true;
-      }
-      if (!empty) npairs.push_back(pr);
+  // Bands of the near-field tables: as delta -> 0 the 1D tables concentrate on their diagonal
+  // (a node only sees the part of the source polynomial within a few sqrt(delta)), so each row
+  // keeps only its entries above eta * (largest entry of its source level's tables), eta =
+  // 1e-7 eps_pw (a row's dropped part is then below k^3 eta of the pair's magnitude in 3D,
+  // k <= 32).  A pair with an all-zero table along some axis contributes nothing and is dropped.
+  const size_t ntables = ntab.size() / std::max<size_t>(kk2, 1);
+  std::vector<int16_t> nband(ntables * k * 2, 0);
+  std::vector<char> tab_empty(ntables, 0);
+  {
+    std::vector<double> level_max;
+    for (size_t t = 0; t < n_std_tables; ++t) {
+      if ((size_t)tab_ls[t] >= level_max.size()) level_max.resize(tab_ls[t] + 1, 0.0);
+      for (size_t e = 0; e < kk2; ++e) level_max[tab_ls[t]] = std::max(level_max[tab_ls[t]], std::fabs(ntab[t * kk2 + e]));
     }
+    for (size_t t = 0; t < ntables; ++t) {
+      const double mx = (size_t)tab_ls[t] < level_max.size() ? level_max[tab_ls[t]] : 0.0;
+      const double thr = 1e-7 * P.eps_pw * mx;
+      bool any = false;
+      for (int r = 0; r < k; ++r) {
+        int lo = k, hi = -1;
+        for (int jj = 0; jj < k; ++jj)
+          if (std::fabs(ntab[t * kk2 + (size_t)r * k + jj]) > thr) { lo = std::min(lo, jj); hi = jj; }
+        nband[(t * k + r) * 2] = (int16_t)lo;
+        nband[(t * k + r) * 2 + 1] = (int16_t)hi;
+        any = any || hi >= lo;
+      }
+      tab_empty[t] = any ? 0 : 1;
+    }
+  }
+  std::vector<fgt::NearPair> npairs;
+  npairs.reserve(raw.size());
+  for (const fgt::NearPair &pr : raw) {
+    bool empty = false;
+    for (int a = 0; a < d; ++a) empty = empty || tab_empty[(size_t)pr.tab[a]];
+    if (!empty) npairs.push_back(pr);
+  }
   ex.n_near_pairs = (int64_t)npairs.size();
   P.n_near_pairs = ex.n_near_pairs;
   {
     bool acc_blocks = false;
-    for (const fgt::Block &b : blocks) acc_blocks = acc_blocks || (b.flags & 1);
+    for (const fgt::Block &b : eblocks) acc_blocks = acc_blocks || (b.flags & 1);
     ex.zero_u = (ex.n_near_pairs > 0 || acc_blocks) ? 1 : 0;
   }
-  ex.n_points = P.n_leaves * (int64_t)P.np();
+  ex.n_points = P.n_targets() * (int64_t)P.np();
   // packed FP32 sigma for the tensor-core form (every block_leaves entry, tagged with its block)
   std::vector<int32_t> pblock;
   bool use_sigp = false;
@@ -985,6 +1104,7 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
 
   // ---- upload
   const size_t o_blocks = pack.add("blocks", blocks), o_bleaves = pack.add("block_leaves", bleaves);
+  const size_t o_ebleaves = pack.add("eval_block_leaves", ebleaves);
   const size_t o_pblock = pack.add("pack_block", pblock);
   const size_t o_f1 = pack.add("form1_blocks", f1), o_f2 = pack.add("form2_blocks", f2),
                o_f2p = pack.add("form2_groups", f2ptr), o_e1 = pack.add("eval1_blocks", e1),
@@ -1062,6 +1182,7 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   ex.e1_blocks = (const fgt::Block *)at(o_e1);
   ex.e2_blocks = (const fgt::Block *)at(o_e2);
   ex.block_leaves = (const int64_t *)at(o_bleaves);
+  ex.eval_leaves = (const int64_t *)at(o_ebleaves);
   ex.Ff = at(o_Ff); ex.Fh = at(o_Fh); ex.Ef = at(o_Ef); ex.Eh = at(o_Eh);
   ex.gather_dst = (const int32_t *)at(o_gdst);
   ex.gather_segs = (const fgt::GatherSeg *)at(o_gseg);
@@ -1320,7 +1441,7 @@ fgt_status fgt_plan_get_info(const fgt_plan *plan, fgt_plan_info *info) {
 
 size_t fgt_plan_device_bytes(const fgt_plan *plan) {
   if (!plan) return 0;
-  return plan->dev_bytes + plan->work_bytes + (plan->stage ? sizeof(double) * 2 * plan->n_leaves * plan->np() : 0);
+  return plan->dev_bytes + plan->work_bytes + (plan->stage ? sizeof(double) * plan->stage_elems : 0);
 }
 
 fgt_status fgt_execute_async(fgt_plan *plan, const double *sigma_dev, double *u_dev, void *stream) {
@@ -1350,6 +1471,64 @@ fgt_status fgt_execute_async(fgt_plan *plan, const double *sigma_dev, double *u_
   cudaError_t e = fgt::run_transform(plan->ex, sigma_dev, u_dev, (cudaStream_t)stream);
   plan->ex.events = nullptr;
   if (e != cudaSuccess) return cuda_fail(e, "transform launch");
+  return FGT_OK;
+}
+
+fgt_status fgt_plan_set_output_tree(fgt_plan *plan, const fgt_tree *out) {
+  if (!plan) return fail(FGT_ERR_ARG, "plan is NULL");
+  if (!out || out->n_leaves == 0) {
+    if (plan->n_out) plan->dirty = true;
+    plan->n_out = 0;
+    plan->out_level.clear(); plan->out_coord.clear(); plan->out_src.clear();
+    return FGT_OK;
+  }
+  const int d = plan->d;
+  if (out->d != d || out->k != plan->k || out->n_leaves < 0 || !out->leaf_level || !out->leaf_coord)
+    return fail(FGT_ERR_ARG, "output tree: dimension, k or arrays do not match the plan");
+  if (plan->lmax > 20) return fail(FGT_ERR_ARG, "output trees need source leaves at levels <= 20");
+  if (plan->mode == FGT_MODE_HIERARCHICAL) return fail(FGT_ERR_ARG, "output trees need the fused mode");
+  const int64_t n = out->n_leaves;
+  std::vector<int64_t> src(n);
+  std::unordered_map<uint64_t, int64_t> seen;
+  std::vector<uint64_t> covered(plan->n_leaves, 0);  // volume covered, in units of 2^-(d * 20)
+  for (int64_t i = 0; i < n; ++i) {
+    const int lt = out->leaf_level[i];
+    if (lt < 0 || lt > 20) return fail(FGT_ERR_TREE, "output tree: level out of range [0, 20]");
+    int32_t c[3] = {0, 0, 0};
+    for (int a = 0; a < d; ++a) {
+      c[a] = out->leaf_coord[i * d + a];
+      if (c[a] < 0 || c[a] >= (1 << lt)) return fail(FGT_ERR_TREE, "output tree: coordinate out of range");
+    }
+    if (!seen.emplace(box_key(lt, c), i).second) return fail(FGT_ERR_TREE, "output tree: repeated leaf");
+    int64_t leaf = -1;
+    for (int l = lt; l >= 0 && leaf < 0; --l) {
+      int32_t q[3] = {0, 0, 0};
+      for (int a = 0; a < d; ++a) q[a] = c[a] >> (lt - l);
+      const int32_t b = plan->find(l, q);
+      if (b >= 0) {
+        if (plan->boxes[b].leaf < 0) break;  // lies above a source leaf: coarser than the source tree
+        leaf = plan->boxes[b].leaf;
+      }
+    }
+    if (leaf < 0) return fail(FGT_ERR_TREE, "output tree: a leaf is not inside one source leaf");
+    src[i] = leaf;
+    covered[leaf] += (uint64_t)1 << (d * (20 - lt));
+  }
+  for (int64_t i = 0; i < n; ++i) {  // no output leaf inside another
+    for (int l = out->leaf_level[i] - 1; l >= plan->leaf_level[src[i]]; --l) {
+      int32_t q[3] = {0, 0, 0};
+      for (int a = 0; a < d; ++a) q[a] = out->leaf_coord[i * d + a] >> (out->leaf_level[i] - l);
+      if (seen.count(box_key(l, q))) return fail(FGT_ERR_TREE, "output tree: overlapping leaves");
+    }
+  }
+  for (int64_t j = 0; j < plan->n_leaves; ++j)
+    if (covered[j] != (uint64_t)1 << (d * (20 - plan->leaf_level[j])))
+      return fail(FGT_ERR_TREE, "output tree: the leaves do not tile every source leaf");
+  plan->n_out = n;
+  plan->out_level.assign(out->leaf_level, out->leaf_level + n);
+  plan->out_coord.assign(out->leaf_coord, out->leaf_coord + n * d);
+  plan->out_src = std::move(src);
+  plan->dirty = true;
   return FGT_OK;
 }
 
@@ -1499,10 +1678,15 @@ fgt_status fgt_execute(fgt_plan *plan, const double *sigma_dev, double *u_dev) {
 fgt_status fgt_execute_host(fgt_plan *plan, const double *sigma_host, double *u_host, void *stream) {
   if (!plan || !sigma_host || !u_host) return fail(FGT_ERR_ARG, "NULL argument");
   if (plan->host_only) return fail(FGT_ERR_STATE, "host-only plan cannot execute");
-  const size_t n = (size_t)plan->n_leaves * plan->np();
+  const size_t n = (size_t)plan->n_leaves * plan->np(), nu = (size_t)plan->n_targets() * plan->np();
+  if (plan->stage && plan->stage_elems < n + nu) {
+    cudaFree(plan->stage);
+    plan->stage = nullptr;
+  }
   if (!plan->stage) {
-    cudaError_t e = cudaMalloc(&plan->stage, sizeof(double) * 2 * n);
+    cudaError_t e = cudaMalloc(&plan->stage, sizeof(double) * (n + nu));
     if (e != cudaSuccess) { plan->stage = nullptr; cudaGetLastError(); return fail(FGT_ERR_OOM, "staging buffers"); }
+    plan->stage_elems = n + nu;
   }
   cudaStream_t st = (cudaStream_t)stream;
   double *sd = plan->stage, *ud = plan->stage + n;
@@ -1510,7 +1694,7 @@ fgt_status fgt_execute_host(fgt_plan *plan, const double *sigma_host, double *u_
   if (e != cudaSuccess) return cuda_fail(e, "copy in");
   fgt_status s = fgt_execute_async(plan, sd, ud, stream);
   if (s != FGT_OK) return s;
-  e = cudaMemcpyAsync(u_host, ud, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+  e = cudaMemcpyAsync(u_host, ud, sizeof(double) * nu, cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return cuda_fail(e, "copy out");
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "transform");

@@ -259,3 +259,23 @@ def test_tuning_knobs_validated_on_a_host_plan():
     assert F.lib().fgt_plan_set_tuning(hp._h, ctypes.byref(u)) == 0
     assert F.lib().fgt_plan_get_tuning(hp._h, ctypes.byref(t)) == 0
     assert (t.form_group, t.eval_rows16, t.eval_rows_large, t.near_phase) == (4, 16, 8, 4)
+
+
+def test_output_tree_validation():
+    """fgt_plan_set_output_tree accepts refinements that tile the source leaves and refuses the rest."""
+    import ctypes
+    lev, crd = np.array([1, 1, 1, 1], dtype=np.int32), np.array([[0, 0], [1, 0], [0, 1], [1, 1]], dtype=np.int32)
+    hp = F.HostPlan(2, 4, 1e-2, 1e-6, lev, crd)
+
+    def try_tree(l, c):
+        t, keep = F._tree_struct(2, 4, np.array(l, dtype=np.int32), np.array(c, dtype=np.int32))
+        return F.lib().fgt_plan_set_output_tree(hp._h, ctypes.byref(t))
+
+    kids = [[2 * x + a, 2 * y + b] for (x, y) in crd.tolist() for b in (0, 1) for a in (0, 1)]
+    assert try_tree([2] * 16, kids) == 0                                  # every leaf refined once
+    assert try_tree([1, 1, 1] + [2] * 4, crd.tolist()[:3] + kids[12:]) == 0  # one leaf refined
+    assert try_tree([0], [[0, 0]]) == 2                                   # coarser than the source
+    assert try_tree([1, 1, 1], crd.tolist()[:3]) == 2                     # a source leaf not covered
+    assert try_tree([1, 1, 1, 1, 2], crd.tolist() + [[0, 0]]) == 2         # overlapping leaves
+    assert try_tree([1, 1, 1, 1, 1], crd.tolist() + [[0, 0]]) == 2         # repeated leaf
+    assert F.lib().fgt_plan_set_output_tree(hp._h, None) == 0
