@@ -329,6 +329,45 @@ def run_sweeps(args, F, torch, w_head, flush):
     return out
 
 
+def run_refinement(F, torch):
+    """Output-tree refinement and coarsening (Algorithms 5 and 6) in the setting of the paper's
+    example (Section 4.3): two Gaussians with alpha = 1e-4 (seeded centres), delta = 4e-3, k = 8,
+    eps = 1e-12, FP64, 2D, the source tree resolving sigma (about 4000 leaves)."""
+    import workloads as W
+    from paper_2305_07165_gb300 import refine as RF
+    d, k, delta, eps = 2, 8, 4e-3, 1e-12
+    rng = np.random.default_rng(11)
+    centers, alphas = rng.uniform(-0.3, 0.3, size=(2, d)), np.array([1e-4, 1e-4])
+    _, tree = W._tune_rho(d, centers, np.sqrt(alphas), 4000, 4.0, 12, False)
+    sigma = torch.from_numpy(W.gaussian_sum(W.node_positions(tree, k), centers, alphas)).cuda()
+    plan = F.Plan(d, k, delta, 1e-12, tree.level, tree.coord)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lev, crd, u, rounds = RF.refine(plan, sigma, eps)
+    torch.cuda.synchronize()
+    t_ref = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    cl, _, _ = RF.coarsen(lev, crd, u, d, k, eps)
+    torch.cuda.synchronize()
+    t_coa = time.perf_counter() - t0
+    out = torch.empty_like(u)
+    st = torch.cuda.current_stream()
+    for _ in range(2):
+        plan(sigma, out=out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(5):
+        plan(sigma, out=out)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 5
+    plan.close()
+    return {"setting": "2D, two Gaussians alpha = 1e-4, delta = 4e-3, k = 8, eps = 1e-12, FP64",
+            "source_leaves": tree.n_leaves, "refined_leaves": int(len(lev)), "rounds": rounds,
+            "coarsened_leaves": int(len(cl)), "refine_s": t_ref, "coarsen_s": t_coa,
+            "output_tree_transform_ms": ms, "output_points_per_s": len(lev) * k ** d / ms * 1e3}
+
+
 def metric_name(w):
     return (f"target points/s (box FGT, {w.d}D {'periodic' if w.periodic else 'free space'}, "
             f"delta={w.delta:g}, tol 1e-6 split form)")
@@ -443,9 +482,10 @@ def main():
     batched = serving = None
     if not args.no_batch and rank == 0:
         batched, serving = run_batched_and_serving(args, F, torch)
-    sweeps = None
+    sweeps = refinement = None
     if not args.no_sweep and rank == 0:
         sweeps = run_sweeps(args, F, torch, w, flush)
+        refinement = run_refinement(F, torch)
 
     # end to end through the host-buffer entry point (pinned host memory, copies timed)
     plan = head["plan"]
@@ -496,6 +536,7 @@ def main():
             "batched": batched,
             "serving": serving,
             "sweeps": sweeps,
+            "refinement": refinement,
         }
         print(json.dumps(line))
     plan.close()

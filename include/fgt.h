@@ -214,6 +214,20 @@ fgt_status fgt_plan_read_profile(fgt_plan *plan, double *ms, int *n_transforms);
  * re-planned at its next execution. */
 fgt_status fgt_plan_set_output_tree(fgt_plan *plan, const fgt_tree *out);
 
+/* Refinement and coarsening helpers (Algorithms 5 and 6), on device arrays:
+ * fgt_leaf_errors: for n boxes with values vals_dev[n][k^d] at their tensor Gauss-Legendre
+ *   nodes, err_dev[i] = the error monitor of eq. (funerr), sqrt(mean |c_alpha|^2 over the tensor
+ *   Legendre coefficients with ||alpha||_2 >= k), and, if sumsq_dev is not NULL, sumsq_dev[i] =
+ *   sum_t w_t v_t^2 with the product Gauss weights of [-1,1]^d (scale by (L/2)^d for a box of side L).
+ * fgt_merge_children: for n_parents parents, the values at the parent's nodes of the piecewise
+ *   interpolant of its 2^d children, rows child_rows_dev[p * 2^d + c] of vals_dev, child c holding
+ *   the half (c >> a) & 1 along axis a; written to parent_dev[n_parents][k^d].
+ * Both: 2 <= d <= 3, 1 <= k <= 16, enqueued on `stream`. */
+fgt_status fgt_leaf_errors(int d, int k, int64_t n, const double *vals_dev, double *err_dev, double *sumsq_dev,
+                           void *stream);
+fgt_status fgt_merge_children(int d, int k, int64_t n_parents, const int64_t *child_rows_dev, const double *vals_dev,
+                              double *parent_dev, void *stream);
+
 /* Launch-shape knobs of a plan and the autotuner that picks them.
  *   form_group:      at most this many same-size blocks of one anchor per form CTA (1..8)
  *   eval_rows16:     split precision, 3D: rows of a K = 16 block per evaluation CTA (4, 8, 16)

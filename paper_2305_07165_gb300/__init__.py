@@ -98,6 +98,8 @@ def lib():
             L.fgt_plan_read_profile.argtypes = [vp, vp, vp]
             L.fgt_plan_autotune.argtypes = [vp, vp, vp, vp, i32, ctypes.POINTER(Tuning)]
             L.fgt_plan_set_output_tree.argtypes = [vp, ctypes.POINTER(_Tree)]
+            L.fgt_leaf_errors.argtypes = [i32, i32, i64, vp, vp, vp, vp]
+            L.fgt_merge_children.argtypes = [i32, i32, i64, vp, vp, vp, vp]
             L.fgt_plan_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
             L.fgt_plan_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
             L.fgt_destroy.argtypes = [vp]
@@ -115,7 +117,8 @@ def lib():
                          "fgt_gauss_legendre", "fgt_params", "fgt_legendre_gauss_integrals",
                          "fgt_spherical_bessel", "fgt_legendre_fourier_integrals", "fgt_plan_set_profiling",
                          "fgt_plan_read_profile", "fgt_plan_autotune", "fgt_plan_get_tuning",
-                         "fgt_plan_set_tuning", "fgt_plan_set_output_tree"):
+                         "fgt_plan_set_tuning", "fgt_plan_set_output_tree", "fgt_leaf_errors",
+                         "fgt_merge_children"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -193,6 +196,7 @@ class Plan:
         self.d, self.k, self.delta, self.tol, self.bc = d, k, delta, tol, bc
         t, keep = _tree_struct(d, k, level, coord)
         self.n_leaves = int(keep[0].size)
+        self._src_level, self._src_coord = keep[0], keep[1]
         self._h = ctypes.c_void_p()
         _check(lib().fgt_plan_create_ex(d, delta, tol, eps_pw, bc, prec, mode, ctypes.byref(t),
                                         ctypes.byref(self._h)))

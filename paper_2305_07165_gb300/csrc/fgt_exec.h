@@ -116,6 +116,17 @@ constexpr size_t kNoallocScratchBytes = size_t(64) << 20;
 cudaError_t noalloc_scratch(void **ptr);
 cudaError_t run_transform_noalloc(const ExecDesc &e, const double *sigma, double *u, cudaStream_t stream);
 
+// Gauss-Legendre rule passed by value to the refinement / coarsening kernels (k <= kMaxLeafK).
+constexpr int kMaxLeafK = 16;
+struct GLRule {
+  double x[kMaxLeafK], w[kMaxLeafK];
+};
+// Error monitor (eq. funerr) and quadrature sum of squares of n boxes' node values; device arrays.
+cudaError_t leaf_errors(int d, int k, int64_t n, const double *vals, double *err, double *sumsq, cudaStream_t st);
+// Parent node values from the interpolants of 2^d children (Algorithm 6); device arrays.
+cudaError_t merge_children(int d, int k, int64_t n_parents, const int64_t *child_rows, const double *vals,
+                           double *parent, cudaStream_t st);
+
 // Shared-memory bytes of the grouped form kernel (G blocks of K nodes per axis; r, c: real and
 // complex element sizes) and of the whole-block evaluation kernel.
 inline size_t form2_bytes(int d, int G, int K, int n1, int nh, size_t r, size_t c) {

@@ -23,6 +23,7 @@
 #include <mutex>
 
 #include "fgt_exec.h"
+#include "fgt_tables.h"
 
 namespace fgt {
 
@@ -2315,6 +2316,154 @@ cudaError_t run_transform_noalloc(const ExecDesc &e, const double *sigma, double
   f.sigp = nullptr;  // no packed sigma: the form kernels read sigma itself
   f.events = nullptr;
   return run_transform(f, sigma, u, stream);
+}
+
+// ----------------------------------------------------------------------------- tree refinement / coarsening
+//
+// Error monitor of Algorithms 3, 5 and 6 (eq. funerr): the tensor Legendre coefficients c of a
+// box's interpolant (val -> pol, Definition val2poldef: T[n][j] = (2n+1)/2 w_j P_n(eta_j) per axis)
+// and e = sqrt(mean of |c_alpha|^2 over ||alpha||_2 >= k).  Also returns the box's quadrature
+// sum of v^2 (weights of the reference box [-1,1]^d) for the norm the criterion is relative to.
+
+// Legendre values P_0..P_{k-1} at x by the three-term recurrence.
+__device__ inline void legendre_all(int k, double x, double *P) {
+  P[0] = 1.0;
+  if (k > 1) P[1] = x;
+  for (int n = 2; n < k; ++n) P[n] = ((2 * n - 1) * x * P[n - 1] - (n - 1) * P[n - 2]) / n;
+}
+
+__global__ void __launch_bounds__(256) leaf_error_kernel(int d, int k, GLRule gl, const double *__restrict__ vals,
+                                                         double *__restrict__ err, double *__restrict__ sumsq) {
+  extern __shared__ double sme[];
+  const int kk = k * k, np = d == 3 ? kk * k : kk;
+  double *V = sme, *A = V + np, *B = A + np, *T = B + np;  // T: [k][k]
+  const double *v = vals + (int64_t)blockIdx.x * np;
+  for (int e = threadIdx.x; e < np; e += blockDim.x) V[e] = v[e];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    double P[kMaxLeafK];
+    legendre_all(k, gl.x[j], P);
+    for (int n = 0; n < k; ++n) T[n * k + j] = 0.5 * (2 * n + 1) * gl.w[j] * P[n];
+  }
+  __syncthreads();
+  // c = (T x T (x T)) v, axis 1 first (node index j_1 fastest)
+  double *src = V, *dst = A;
+  for (int a = 0; a < d; ++a) {
+    const int stride = a == 0 ? 1 : (a == 1 ? k : kk);
+    for (int e = threadIdx.x; e < np; e += blockDim.x) {
+      const int na = (e / stride) % k, base = e - na * stride;
+      double acc = 0.0;
+      for (int j = 0; j < k; ++j) acc = fma(T[na * k + j], src[base + j * stride], acc);
+      dst[e] = acc;
+    }
+    __syncthreads();
+    src = dst;
+    dst = (dst == A) ? B : A;
+  }
+  // tail and quadrature sums
+  __shared__ double red[2][256];
+  __shared__ int cnt[256];
+  double tail = 0.0, sq = 0.0;
+  int ntail = 0;
+  for (int e = threadIdx.x; e < np; e += blockDim.x) {
+    const int a1 = e % k, a2 = (e / k) % k, a3 = d == 3 ? e / kk : 0;
+    if (a1 * a1 + a2 * a2 + a3 * a3 >= k * k) {
+      tail += src[e] * src[e];
+      ++ntail;
+    }
+    double w = gl.w[a1] * gl.w[a2] * (d == 3 ? gl.w[a3] : 1.0);
+    sq += w * V[e] * V[e];
+  }
+  red[0][threadIdx.x] = tail;
+  red[1][threadIdx.x] = sq;
+  cnt[threadIdx.x] = ntail;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + off];
+      red[1][threadIdx.x] += red[1][threadIdx.x + off];
+      cnt[threadIdx.x] += cnt[threadIdx.x + off];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    err[blockIdx.x] = cnt[0] > 0 ? sqrt(red[0][0] / cnt[0]) : 0.0;
+    if (sumsq) sumsq[blockIdx.x] = red[1][0];
+  }
+}
+
+// Algorithm 6: the values of a parent box at its k^d nodes from the interpolants of its 2^d
+// children (child c holds the half (c >> a) & 1 along axis a): a parent node in child c's half
+// is the child's Lagrange interpolant at the node's child-local coordinate 2 eta -/+ 1, applied
+// axis by axis.  One CTA per parent.
+__global__ void __launch_bounds__(256) merge_children_kernel(int d, int k, GLRule gl,
+                                                             const int64_t *__restrict__ child_rows,
+                                                             const double *__restrict__ vals,
+                                                             double *__restrict__ parent) {
+  extern __shared__ double smm[];
+  const int kk = k * k, np = d == 3 ? kk * k : kk, nc = 1 << d;
+  double *M = smm;                 // [2][k][k]: M[h][t][j] = l_j(2 eta_t - 1 + 2 (1 - h) ... )
+  double *A = M + 2 * kk, *B = A + np, *Cv = B + np;
+  for (int e = threadIdx.x; e < 2 * kk; e += blockDim.x) {
+    const int h = e / kk, t = (e / k) % k, j = e % k;
+    const double s = h ? 2.0 * gl.x[t] - 1.0 : 2.0 * gl.x[t] + 1.0;  // child-local coordinate
+    double l = 1.0;
+    for (int m = 0; m < k; ++m)
+      if (m != j) l *= (s - gl.x[m]) / (gl.x[j] - gl.x[m]);
+    M[e] = l;
+  }
+  __syncthreads();
+  double *out = parent + (int64_t)blockIdx.x * np;
+  for (int c = 0; c < nc; ++c) {
+    const double *v = vals + child_rows[(int64_t)blockIdx.x * nc + c] * np;
+    for (int e = threadIdx.x; e < np; e += blockDim.x) Cv[e] = v[e];
+    __syncthreads();
+    double *src = Cv, *dst = A;
+    for (int a = 0; a < d; ++a) {
+      const int stride = a == 0 ? 1 : (a == 1 ? k : kk), h = (c >> a) & 1;
+      for (int e = threadIdx.x; e < np; e += blockDim.x) {
+        const int ta = (e / stride) % k, base = e - ta * stride;
+        double acc = 0.0;
+        for (int j = 0; j < k; ++j) acc = fma(M[(h * k + ta) * k + j], src[base + j * stride], acc);
+        dst[e] = acc;
+      }
+      __syncthreads();
+      src = dst;
+      dst = (dst == A) ? B : A;
+    }
+    // keep the parent nodes that lie in child c's half on every axis (the middle node of an odd
+    // k goes to the upper half)
+    for (int e = threadIdx.x; e < np; e += blockDim.x) {
+      bool mine = true;
+      for (int a = 0, r = e; a < d; ++a, r /= k) mine = mine && ((gl.x[r % k] >= 0.0) == (((c >> a) & 1) == 1));
+      if (mine) out[e] = src[e];
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t leaf_errors(int d, int k, int64_t n, const double *vals, double *err, double *sumsq, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  GLRule gl;
+  gl_rule(k, gl.x, gl.w);
+  const int np = d == 3 ? k * k * k : k * k;
+  const size_t sm = sizeof(double) * (3 * (size_t)np + (size_t)k * k);
+  cudaError_t e = cudaFuncSetAttribute(leaf_error_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  leaf_error_kernel<<<(unsigned)n, 256, sm, st>>>(d, k, gl, vals, err, sumsq);
+  return cudaGetLastError();
+}
+
+cudaError_t merge_children(int d, int k, int64_t n_parents, const int64_t *child_rows, const double *vals,
+                           double *parent, cudaStream_t st) {
+  if (n_parents <= 0) return cudaSuccess;
+  GLRule gl;
+  gl_rule(k, gl.x, gl.w);
+  const int np = d == 3 ? k * k * k : k * k;
+  const size_t sm = sizeof(double) * (2 * (size_t)k * k + 3 * (size_t)np);
+  cudaError_t e = cudaFuncSetAttribute(merge_children_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  merge_children_kernel<<<(unsigned)n_parents, 256, sm, st>>>(d, k, gl, child_rows, vals, parent);
+  return cudaGetLastError();
 }
 
 }  // namespace fgt

@@ -1532,6 +1532,23 @@ fgt_status fgt_plan_set_output_tree(fgt_plan *plan, const fgt_tree *out) {
   return FGT_OK;
 }
 
+fgt_status fgt_leaf_errors(int d, int k, int64_t n, const double *vals_dev, double *err_dev, double *sumsq_dev,
+                           void *stream) {
+  if ((d != 2 && d != 3) || k < 1 || k > fgt::kMaxLeafK || n < 0 || (n > 0 && (!vals_dev || !err_dev)))
+    return fail(FGT_ERR_ARG, "leaf errors: d must be 2 or 3, 1 <= k <= 16, device arrays given");
+  cudaError_t e = fgt::leaf_errors(d, k, n, vals_dev, err_dev, sumsq_dev, (cudaStream_t)stream);
+  return e == cudaSuccess ? FGT_OK : cuda_fail(e, "leaf errors");
+}
+
+fgt_status fgt_merge_children(int d, int k, int64_t n_parents, const int64_t *child_rows_dev, const double *vals_dev,
+                              double *parent_dev, void *stream) {
+  if ((d != 2 && d != 3) || k < 1 || k > fgt::kMaxLeafK || n_parents < 0 ||
+      (n_parents > 0 && (!child_rows_dev || !vals_dev || !parent_dev)))
+    return fail(FGT_ERR_ARG, "merge children: d must be 2 or 3, 1 <= k <= 16, device arrays given");
+  cudaError_t e = fgt::merge_children(d, k, n_parents, child_rows_dev, vals_dev, parent_dev, (cudaStream_t)stream);
+  return e == cudaSuccess ? FGT_OK : cuda_fail(e, "merge children");
+}
+
 fgt_status fgt_plan_get_tuning(const fgt_plan *plan, fgt_tuning *out) {
   if (!plan || !out) return fail(FGT_ERR_ARG, "NULL argument");
   *out = plan->tune;
