@@ -228,6 +228,27 @@ fgt_status fgt_leaf_errors(int d, int k, int64_t n, const double *vals_dev, doub
 fgt_status fgt_merge_children(int d, int k, int64_t n_parents, const int64_t *child_rows_dev, const double *vals_dev,
                               double *parent_dev, void *stream);
 
+/* Algorithm 3 on the GPU for a density given as a sum of Gaussians,
+ *   sigma(x) = sum_i amps[i] exp(-|x - centers[i]|^2 / alphas[i])   (amps NULL: all 1;
+ *   periodic != 0: the minimum-image distance to each centre),
+ * centers [n_gauss][d].  Level by level from the root, every box's k^d node values are computed,
+ * then their Legendre coefficients and the error monitor of eq. (funerr); a box is subdivided
+ * while its level is below min_level, or while e > eps ||sigma||_2 (the norm over the current
+ * partition of B) and its level is below max_level.  The leaves are then 2:1 balanced (corners
+ * included, across the wrap when periodic) and sigma is evaluated at their nodes.  The result
+ * (*out, owned by the caller, freed with fgt_built_tree_destroy) holds the leaves (host arrays,
+ * the layout of fgt_tree) and sigma on the device [n_leaves][k^d], ready for fgt_plan_create and
+ * fgt_execute.  2 <= d <= 3, 1 <= k <= 16, 0 <= min_level <= max_level <= 20; synchronises `stream`. */
+typedef struct fgt_built_tree fgt_built_tree;
+fgt_status fgt_build_gaussian_tree(int d, int k, int n_gauss, const double *centers, const double *alphas,
+                                   const double *amps, int periodic, double eps, int min_level, int max_level,
+                                   void *stream, fgt_built_tree **out);
+fgt_status fgt_built_tree_get(const fgt_built_tree *t, int64_t *n_leaves, const int32_t **level,
+                              const int32_t **coord, const double **sigma_dev);
+/* Copies the tree's sigma into dst_dev [n_leaves][k^d] (device) on `stream`. */
+fgt_status fgt_built_tree_copy_sigma(const fgt_built_tree *t, double *dst_dev, void *stream);
+void fgt_built_tree_destroy(fgt_built_tree *t);
+
 /* Launch-shape knobs of a plan and the autotuner that picks them.
  *   form_group:      at most this many same-size blocks of one anchor per form CTA (1..8)
  *   eval_rows16:     split precision, 3D: rows of a K = 16 block per evaluation CTA (4, 8, 16)

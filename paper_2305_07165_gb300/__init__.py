@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Plan", "FGTError", "Tuning", "lib", "BC_FREE", "BC_PERIODIC", "PREC_FP64", "PREC_SPLIT", "PREC_FP64_TC", "MODE_FUSED",
+__all__ = ["Plan", "FGTError", "Tuning", "lib", "build_gaussian_tree", "BC_FREE", "BC_PERIODIC", "PREC_FP64", "PREC_SPLIT", "PREC_FP64_TC", "MODE_FUSED",
            "MODE_HIERARCHICAL", "gauss_legendre", "params", "nf_for_range", "legendre_gauss_integrals",
            "spherical_bessel", "legendre_fourier_integrals", "analyze", "HostPlan", "Batch"]
 
@@ -99,6 +99,13 @@ def lib():
             L.fgt_plan_autotune.argtypes = [vp, vp, vp, vp, i32, ctypes.POINTER(Tuning)]
             L.fgt_plan_set_output_tree.argtypes = [vp, ctypes.POINTER(_Tree)]
             L.fgt_leaf_errors.argtypes = [i32, i32, i64, vp, vp, vp, vp]
+            L.fgt_build_gaussian_tree.argtypes = [i32, i32, i32, vp, vp, vp, i32, dbl, i32, i32, vp,
+                                                  ctypes.POINTER(vp)]
+            L.fgt_built_tree_get.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                             ctypes.POINTER(vp)]
+            L.fgt_built_tree_copy_sigma.argtypes = [vp, vp, vp]
+            L.fgt_built_tree_destroy.argtypes = [vp]
+            L.fgt_built_tree_destroy.restype = None
             L.fgt_merge_children.argtypes = [i32, i32, i64, vp, vp, vp, vp]
             L.fgt_plan_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
             L.fgt_plan_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
@@ -118,7 +125,8 @@ def lib():
                          "fgt_spherical_bessel", "fgt_legendre_fourier_integrals", "fgt_plan_set_profiling",
                          "fgt_plan_read_profile", "fgt_plan_autotune", "fgt_plan_get_tuning",
                          "fgt_plan_set_tuning", "fgt_plan_set_output_tree", "fgt_leaf_errors",
-                         "fgt_merge_children"):
+                         "fgt_merge_children", "fgt_build_gaussian_tree", "fgt_built_tree_get",
+                         "fgt_built_tree_copy_sigma"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -411,3 +419,37 @@ def legendre_fourier_integrals(t, nmax):
     re, im = np.zeros(nmax + 1), np.zeros(nmax + 1)
     _check(lib().fgt_legendre_fourier_integrals(t, nmax, re.ctypes.data, im.ctypes.data))
     return re + 1j * im
+
+
+def build_gaussian_tree(d, k, centers, alphas, amps=None, periodic=False, eps=1e-10, min_level=0, max_level=12,
+                        stream=None):
+    """Algorithm 3 on the GPU (fgt_build_gaussian_tree) for sigma = sum_i a_i exp(-|x - c_i|^2 / alpha_i):
+    returns (level int32 [n], coord int32 [n, d], sigma CUDA float64 [n, k**d]) of the 2:1-balanced
+    tree whose leaves resolve sigma to eps ||sigma||_2 by the error monitor of eq. (funerr)."""
+    import torch
+    c = np.ascontiguousarray(centers, dtype=np.float64).reshape(-1, d)
+    a = np.ascontiguousarray(alphas, dtype=np.float64).reshape(-1)
+    w = None if amps is None else np.ascontiguousarray(amps, dtype=np.float64).reshape(-1)
+    if len(a) != len(c) or (w is not None and len(w) != len(c)):
+        raise ValueError("one alpha (and amplitude) per centre")
+    torch.cuda.current_device()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    h = ctypes.c_void_p()
+    _check(lib().fgt_build_gaussian_tree(d, k, len(a), c.ctypes.data, a.ctypes.data,
+                                         None if w is None else w.ctypes.data, int(bool(periodic)), float(eps),
+                                         int(min_level), int(max_level), ctypes.c_void_p(st.cuda_stream),
+                                         ctypes.byref(h)))
+    try:
+        n = ctypes.c_int64()
+        pl, pc, ps = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().fgt_built_tree_get(h, ctypes.byref(n), ctypes.byref(pl), ctypes.byref(pc), ctypes.byref(ps)))
+        nl = n.value
+        level = np.ctypeslib.as_array((ctypes.c_int32 * nl).from_address(pl.value)).copy() if nl else np.zeros(0, np.int32)
+        coord = (np.ctypeslib.as_array((ctypes.c_int32 * (nl * d)).from_address(pc.value)).copy().reshape(nl, d)
+                 if nl else np.zeros((0, d), np.int32))
+        sigma = torch.empty((nl, k ** d), dtype=torch.float64, device="cuda")
+        _check(lib().fgt_built_tree_copy_sigma(h, ctypes.c_void_p(sigma.data_ptr()), ctypes.c_void_p(st.cuda_stream)))
+        st.synchronize()
+    finally:
+        lib().fgt_built_tree_destroy(h)
+    return level, coord, sigma

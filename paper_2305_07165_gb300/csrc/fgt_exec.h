@@ -123,6 +123,10 @@ struct GLRule {
 };
 // Error monitor (eq. funerr) and quadrature sum of squares of n boxes' node values; device arrays.
 cudaError_t leaf_errors(int d, int k, int64_t n, const double *vals, double *err, double *sumsq, cudaStream_t st);
+// A sum of Gaussians at the nodes of n boxes (Algorithm 3's density evaluation); device arrays,
+// gparams[ng][d + 2] = (centre, alpha, amplitude).
+cudaError_t gauss_nodes(int d, int k, int64_t n, const int32_t *level, const int32_t *coord, int ng,
+                        const double *gparams, int periodic, double *vals, cudaStream_t st);
 // Parent node values from the interpolants of 2^d children (Algorithm 6); device arrays.
 cudaError_t merge_children(int d, int k, int64_t n_parents, const int64_t *child_rows, const double *vals,
                            double *parent, cudaStream_t st);

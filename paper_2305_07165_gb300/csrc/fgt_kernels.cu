@@ -2441,6 +2441,45 @@ __global__ void __launch_bounds__(256) merge_children_kernel(int d, int k, GLRul
   }
 }
 
+// Algorithm 3's density evaluation for a sum of Gaussians sigma(x) = sum_i a_i exp(-|x - c_i|^2 /
+// alpha_i) (periodic: the minimum-image distance to each centre) at the k^d tensor Gauss-Legendre
+// nodes of n boxes (level, integer coordinates); one CTA per box, node index j_1 fastest.
+__global__ void __launch_bounds__(256) gauss_nodes_kernel(int d, int k, GLRule gl, const int32_t *__restrict__ level,
+                                                          const int32_t *__restrict__ coord, int ng,
+                                                          const double *__restrict__ gparams, int periodic,
+                                                          double *__restrict__ vals) {
+  const int np = d == 3 ? k * k * k : k * k;
+  const int64_t b = blockIdx.x;
+  const double L = ldexp(1.0, -level[b]);
+  double c[3] = {0.0, 0.0, 0.0};
+  for (int a = 0; a < d; ++a) c[a] = -0.5 + (coord[b * d + a] + 0.5) * L;
+  for (int e = threadIdx.x; e < np; e += blockDim.x) {
+    double x[3] = {0.0, 0.0, 0.0};
+    for (int a = 0, r = e; a < d; ++a, r /= k) x[a] = c[a] + 0.5 * L * gl.x[r % k];
+    double v = 0.0;
+    for (int i = 0; i < ng; ++i) {
+      const double *g = gparams + (size_t)i * (d + 2);  // centre[d], alpha, amplitude
+      double r2 = 0.0;
+      for (int a = 0; a < d; ++a) {
+        double dx = x[a] - g[a];
+        if (periodic) dx -= rint(dx);
+        r2 += dx * dx;
+      }
+      v += g[d + 1] * exp(-r2 / g[d]);
+    }
+    vals[b * np + e] = v;
+  }
+}
+
+cudaError_t gauss_nodes(int d, int k, int64_t n, const int32_t *level, const int32_t *coord, int ng,
+                        const double *gparams, int periodic, double *vals, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  GLRule gl;
+  gl_rule(k, gl.x, gl.w);
+  gauss_nodes_kernel<<<(unsigned)n, 256, 0, st>>>(d, k, gl, level, coord, ng, gparams, periodic, vals);
+  return cudaGetLastError();
+}
+
 cudaError_t leaf_errors(int d, int k, int64_t n, const double *vals, double *err, double *sumsq, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   GLRule gl;

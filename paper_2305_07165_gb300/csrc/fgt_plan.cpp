@@ -1532,6 +1532,204 @@ fgt_status fgt_plan_set_output_tree(fgt_plan *plan, const fgt_tree *out) {
   return FGT_OK;
 }
 
+// ---------------------------------------------------------------------------- Algorithm 3 on the GPU
+
+struct fgt_built_tree {
+  int d = 0, k = 0;
+  std::vector<int32_t> level, coord;
+  double *sigma = nullptr;  // device [n][k^d]
+  ~fgt_built_tree() {
+    if (sigma) cudaFree(sigma);
+  }
+};
+
+namespace {
+
+// 2:1 balance (boxes sharing a boundary point, corners included, across the wrap when periodic):
+// a leaf with a neighbour leaf two or more levels coarser splits that neighbour, until none does.
+void balance_tree(int d, bool periodic, std::vector<int32_t> &level, std::vector<int32_t> &coord) {
+  struct Key { int l; int32_t c[3]; };
+  std::unordered_map<uint64_t, Key> leaves;
+  std::vector<Key> queue;
+  for (size_t i = 0; i < level.size(); ++i) {
+    Key kk{level[i], {0, 0, 0}};
+    for (int a = 0; a < d; ++a) kk.c[a] = coord[i * d + a];
+    leaves.emplace(box_key(kk.l, kk.c), kk);
+    queue.push_back(kk);
+  }
+  int noff = 1;
+  for (int a = 0; a < d; ++a) noff *= 3;
+  while (!queue.empty()) {
+    const Key t = queue.back();
+    queue.pop_back();
+    if (!leaves.count(box_key(t.l, t.c))) continue;
+    const int n = 1 << t.l;
+    for (int oc = 0; oc < noff; ++oc) {
+      int32_t q[3] = {0, 0, 0};
+      bool ok = true, self = true;
+      for (int a = 0, r = oc; a < d; ++a, r /= 3) {
+        const int o = r % 3 - 1;
+        self = self && o == 0;
+        int v = t.c[a] + o;
+        if (v < 0 || v >= n) {
+          if (!periodic) { ok = false; break; }
+          v = (v % n + n) % n;
+        }
+        q[a] = v;
+      }
+      if (!ok || self) continue;
+      // the leaf covering the neighbour position at level t.l, if it is coarser
+      for (int up = 2; up <= t.l; ++up) {
+        int32_t pc[3] = {0, 0, 0};
+        for (int a = 0; a < d; ++a) pc[a] = q[a] >> up;
+        auto it = leaves.find(box_key(t.l - up, pc));
+        if (it == leaves.end()) continue;
+        const Key s = it->second;
+        leaves.erase(it);
+        for (int ch = 0; ch < (1 << d); ++ch) {
+          Key kid{s.l + 1, {0, 0, 0}};
+          for (int a = 0; a < d; ++a) kid.c[a] = 2 * s.c[a] + ((ch >> a) & 1);
+          leaves.emplace(box_key(kid.l, kid.c), kid);
+          queue.push_back(kid);
+        }
+        queue.push_back(t);
+        break;
+      }
+    }
+  }
+  std::vector<std::pair<uint64_t, Key>> all(leaves.begin(), leaves.end());
+  std::sort(all.begin(), all.end(), [](const auto &x, const auto &y) { return x.first < y.first; });
+  level.clear();
+  coord.clear();
+  for (const auto &e : all) {
+    level.push_back(e.second.l);
+    for (int a = 0; a < d; ++a) coord.push_back(e.second.c[a]);
+  }
+}
+
+}  // namespace
+
+fgt_status fgt_build_gaussian_tree(int d, int k, int n_gauss, const double *centers, const double *alphas,
+                                   const double *amps, int periodic, double eps, int min_level, int max_level,
+                                   void *stream, fgt_built_tree **out) {
+  if (!out) return fail(FGT_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if ((d != 2 && d != 3) || k < 1 || k > fgt::kMaxLeafK || n_gauss < 1 || !centers || !alphas || !(eps > 0) ||
+      min_level < 0 || max_level < min_level || max_level > 20)
+    return fail(FGT_ERR_ARG, "build tree: bad arguments (d 2/3, 1 <= k <= 16, 0 <= min <= max <= 20)");
+  for (int i = 0; i < n_gauss; ++i)
+    if (!(alphas[i] > 0)) return fail(FGT_ERR_ARG, "build tree: alphas must be positive");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int np = d == 3 ? k * k * k : k * k;
+  std::vector<double> gp((size_t)n_gauss * (d + 2));
+  for (int i = 0; i < n_gauss; ++i) {
+    for (int a = 0; a < d; ++a) gp[(size_t)i * (d + 2) + a] = centers[(size_t)i * d + a];
+    gp[(size_t)i * (d + 2) + d] = alphas[i];
+    gp[(size_t)i * (d + 2) + d + 1] = amps ? amps[i] : 1.0;
+  }
+  // device scratch, grown as needed
+  double *dg = nullptr, *dv = nullptr, *de = nullptr, *ds = nullptr;
+  int32_t *dl = nullptr, *dc = nullptr;
+  size_t cap = 0;
+  auto release = [&]() {
+    cudaFree(dg); cudaFree(dv); cudaFree(de); cudaFree(ds); cudaFree(dl); cudaFree(dc);
+  };
+  auto reserve = [&](size_t n) -> cudaError_t {
+    if (n <= cap) return cudaSuccess;
+    cudaFree(dv); cudaFree(de); cudaFree(ds); cudaFree(dl); cudaFree(dc);
+    dv = de = ds = nullptr; dl = dc = nullptr;
+    cap = std::max(n, 2 * cap);
+    cudaError_t e = cudaMalloc(&dv, sizeof(double) * cap * np);
+    if (e == cudaSuccess) e = cudaMalloc(&de, sizeof(double) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&ds, sizeof(double) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&dl, sizeof(int32_t) * cap);
+    if (e == cudaSuccess) e = cudaMalloc(&dc, sizeof(int32_t) * cap * d);
+    return e;
+  };
+  cudaError_t ce = cudaMalloc(&dg, sizeof(double) * gp.size());
+  if (ce == cudaSuccess) ce = cudaMemcpy(dg, gp.data(), sizeof(double) * gp.size(), cudaMemcpyHostToDevice);
+  std::vector<int32_t> al(1, 0), ac((size_t)d, 0), ll, lc;  // active boxes, finished leaves
+  double leaf_sq = 0.0;
+  std::vector<double> err, sq;
+  for (int l = 0; ce == cudaSuccess && !al.empty(); ++l) {
+    const size_t na = al.size();
+    if ((ce = reserve(na)) != cudaSuccess) break;
+    ce = cudaMemcpyAsync(dl, al.data(), sizeof(int32_t) * na, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(dc, ac.data(), sizeof(int32_t) * na * d, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = fgt::gauss_nodes(d, k, (int64_t)na, dl, dc, n_gauss, dg, periodic, dv, st);
+    if (ce == cudaSuccess) ce = fgt::leaf_errors(d, k, (int64_t)na, dv, de, ds, st);
+    err.resize(na);
+    sq.resize(na);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(err.data(), de, sizeof(double) * na, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(sq.data(), ds, sizeof(double) * na, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) break;
+    // ||sigma||_2 over the current partition of B: finished leaves and this level's boxes
+    const double vol = std::pow(0.5 * std::ldexp(1.0, -l), d);
+    double norm2 = leaf_sq;
+    for (size_t i = 0; i < na; ++i) norm2 += sq[i] * vol;
+    const double thr = eps * std::sqrt(norm2);
+    std::vector<int32_t> nl, nc;
+    for (size_t i = 0; i < na; ++i) {
+      const bool split = l < max_level && (l < min_level || err[i] > thr);
+      if (split) {
+        for (int ch = 0; ch < (1 << d); ++ch) {
+          nl.push_back(l + 1);
+          for (int a = 0; a < d; ++a) nc.push_back(2 * ac[i * d + a] + ((ch >> a) & 1));
+        }
+      } else {
+        ll.push_back(l);
+        for (int a = 0; a < d; ++a) lc.push_back(ac[i * d + a]);
+        leaf_sq += sq[i] * vol;
+      }
+    }
+    al.swap(nl);
+    ac.swap(nc);
+  }
+  if (ce != cudaSuccess) {
+    release();
+    return cuda_fail(ce, "build tree");
+  }
+  balance_tree(d, periodic != 0, ll, lc);
+  auto *T = new (std::nothrow) fgt_built_tree();
+  if (!T) { release(); return fail(FGT_ERR_OOM, "host allocation"); }
+  T->d = d; T->k = k; T->level = ll; T->coord = lc;
+  const size_t n = ll.size();
+  ce = reserve(n);
+  if (ce == cudaSuccess) ce = cudaMalloc(&T->sigma, sizeof(double) * n * np);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(dl, ll.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(dc, lc.data(), sizeof(int32_t) * n * d, cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = fgt::gauss_nodes(d, k, (int64_t)n, dl, dc, n_gauss, dg, periodic, T->sigma, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  release();
+  if (ce != cudaSuccess) {
+    delete T;
+    return cuda_fail(ce, "build tree");
+  }
+  *out = T;
+  return FGT_OK;
+}
+
+fgt_status fgt_built_tree_get(const fgt_built_tree *t, int64_t *n_leaves, const int32_t **level,
+                              const int32_t **coord, const double **sigma_dev) {
+  if (!t) return fail(FGT_ERR_ARG, "tree is NULL");
+  if (n_leaves) *n_leaves = (int64_t)t->level.size();
+  if (level) *level = t->level.data();
+  if (coord) *coord = t->coord.data();
+  if (sigma_dev) *sigma_dev = t->sigma;
+  return FGT_OK;
+}
+
+fgt_status fgt_built_tree_copy_sigma(const fgt_built_tree *t, double *dst_dev, void *stream) {
+  if (!t || !dst_dev) return fail(FGT_ERR_ARG, "NULL argument");
+  const size_t np = t->d == 3 ? (size_t)t->k * t->k * t->k : (size_t)t->k * t->k;
+  cudaError_t e = cudaMemcpyAsync(dst_dev, t->sigma, sizeof(double) * np * t->level.size(), cudaMemcpyDeviceToDevice,
+                                  (cudaStream_t)stream);
+  return e == cudaSuccess ? FGT_OK : cuda_fail(e, "copy sigma");
+}
+
+void fgt_built_tree_destroy(fgt_built_tree *t) { delete t; }
+
 fgt_status fgt_leaf_errors(int d, int k, int64_t n, const double *vals_dev, double *err_dev, double *sumsq_dev,
                            void *stream) {
   if ((d != 2 && d != 3) || k < 1 || k > fgt::kMaxLeafK || n < 0 || (n > 0 && (!vals_dev || !err_dev)))

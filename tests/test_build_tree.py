@@ -1,0 +1,71 @@
+"""Algorithm 3 on the GPU (fgt_build_gaussian_tree): the tree is level-restricted and tiles B
+(the planner accepts it), sigma at its nodes equals the density, every leaf passes the error
+monitor unless it sits at the level cap, and the transform on it matches the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+F = pytest.importorskip("paper_2305_07165_gb300")
+R = pytest.importorskip("paper_2305_07165_gb300.refine")
+
+pytestmark = pytest.mark.gpu
+
+
+def _interp_error(level, coord, sigma, k, d, centers, alphas, periodic, n=4000, seed=0):
+    """Max |interpolant - sigma| at random points, the interpolant built with numpy."""
+    rng = np.random.default_rng(seed)
+    x, _ = np.polynomial.legendre.leggauss(k)
+    leaf = rng.integers(0, len(level), n)
+    s = rng.uniform(-1, 1, size=(n, d))
+    L = np.ldexp(1.0, -level[leaf])
+    pts = -0.5 + (coord[leaf] + 0.5) * L[:, None] + 0.5 * L[:, None] * s
+    exact = W.gaussian_sum(pts, centers, alphas, periodic=periodic)
+    def lag(t):
+        out = np.ones((len(t), k))
+        for j in range(k):
+            for m in range(k):
+                if m != j:
+                    out[:, j] *= (t - x[m]) / (x[j] - x[m])
+        return out
+    approx = sigma[leaf].reshape((n,) + (k,) * d)        # [n, j_d, .., j_1]: contract j_1 first
+    for a in range(d):
+        approx = np.einsum("n...j,nj->n...", approx, lag(s[:, a]))
+    return np.abs(approx - exact).max() / np.abs(exact).max()
+
+
+@pytest.mark.parametrize("d,k,periodic", [(2, 8, False), (3, 8, False), (3, 6, True), (2, 16, True)])
+def test_gpu_tree_resolves_the_density(d, k, periodic):
+    rng = np.random.default_rng(d + k)
+    centers = rng.uniform(-0.35, 0.35, size=(3, d))
+    alphas = np.array([4e-3, 1e-3, 2e-4])
+    eps = 1e-8
+    level, coord, sigma = F.build_gaussian_tree(d, k, centers, alphas, periodic=periodic, eps=eps, min_level=1,
+                                                max_level=8 if d == 2 else 6)
+    assert len(level) > 1 and sigma.shape == (len(level), k ** d)
+    tree = W.Tree(d, level, coord, periodic)
+    ref = W.gaussian_sum(W.node_positions(tree, k), centers, alphas, periodic=periodic)
+    sg = sigma.cpu().numpy()
+    assert np.abs(sg - ref).max() <= 1e-13 * np.abs(ref).max()
+    F.analyze(d, k, 1e-3, 1e-6, level, coord, bc=int(periodic))   # level-restricted and tiling B
+    err, sq = R.leaf_errors(sigma, d, k)
+    norm = R._norm(sq, level, d)
+    cap = 8 if d == 2 else 6
+    ok = (err.cpu().numpy() <= eps * norm) | (level == cap)
+    assert ok.all()
+    # leaves stopped by the level cap resolve sigma only as far as the cap allows
+    bound = 1e-5 if not (level == cap).any() else 1e-3
+    assert _interp_error(level, coord, sg, k, d, centers, alphas, periodic) <= bound
+
+
+def test_transform_on_the_gpu_built_tree():
+    d, k = 3, 6
+    centers, alphas = np.array([[0.1, -0.1, 0.05], [-0.2, 0.2, -0.1]]), np.array([2e-3, 8e-3])
+    level, coord, sigma = F.build_gaussian_tree(d, k, centers, alphas, eps=1e-7, min_level=1, max_level=5)
+    plan = F.Plan(d, k, 1e-3, 1e-8, level, coord)
+    u = plan(sigma).cpu().numpy()
+    plan.close()
+    uo = oracle.box_fgt(d, k, 1e-3, False, level, coord, sigma.cpu().numpy())
+    assert np.abs(u - uo).max() <= 1e-7 * np.abs(uo).max()
