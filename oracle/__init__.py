@@ -49,6 +49,10 @@ def _load():
                 ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_long,
                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                 ctypes.c_long, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+            lib.oracle_point_fgt.restype = ctypes.c_int
+            lib.oracle_point_fgt.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_long, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_long, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_int]
             lib.oracle_gauss_legendre.restype = ctypes.c_int
             lib.oracle_gauss_legendre.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
             lib.oracle_default_threads.restype = ctypes.c_int
@@ -104,4 +108,17 @@ def box_fgt_boxes(d, p, delta, periodic, leaf_level, leaf_coord, sigma, tgt_leve
                                       len(tl), tl.ctypes.data, tc.ctypes.data, u.ctypes.data, int(threads))
     if rc != 0:
         raise RuntimeError(f"oracle_box_fgt_boxes failed ({rc})")
+    return u
+
+
+def point_fgt(d, delta, src, q, tgt, threads=0):
+    """u[i] = sum_j exp(-|x_i - y_j|^2/delta) q_j (the discrete Gauss transform, summed directly)."""
+    y = np.ascontiguousarray(src, dtype=np.float64).reshape(-1, d)
+    w = np.ascontiguousarray(q, dtype=np.float64).reshape(-1)
+    x = np.ascontiguousarray(tgt, dtype=np.float64).reshape(-1, d)
+    u = np.zeros(len(x))
+    rc = _load().oracle_point_fgt(int(d), float(delta), len(y), y.ctypes.data, w.ctypes.data, len(x),
+                                  x.ctypes.data, u.ctypes.data, int(threads))
+    if rc != 0:
+        raise RuntimeError("oracle_point_fgt failed")
     return u

@@ -377,6 +377,68 @@ int oracle_box_fgt_boxes(int d, int p, double delta, int periodic, long n_leaves
   return C.err;
 }
 
+/* ---- discrete Gauss transform (Section 3's point FGT): the definition summed directly ---- */
+
+typedef struct {
+  int d;
+  double delta;
+  long n_src, n_tgt;
+  const double *src, *q, *tgt;
+  double *u;
+  long next;
+  pthread_mutex_t mtx;
+} pt_ctx;
+
+static void *pt_worker(void *arg) {
+  pt_ctx *C = (pt_ctx *)arg;
+  for (;;) {
+    pthread_mutex_lock(&C->mtx);
+    long i0 = C->next;
+    C->next += 256;
+    pthread_mutex_unlock(&C->mtx);
+    if (i0 >= C->n_tgt) break;
+    long i1 = i0 + 256 < C->n_tgt ? i0 + 256 : C->n_tgt;
+    for (long i = i0; i < i1; i++) {
+      const double *x = C->tgt + i * C->d;
+      double sum = 0.0, comp = 0.0;
+      for (long j = 0; j < C->n_src; j++) {
+        const double *y = C->src + j * C->d;
+        double r2 = 0.0;
+        for (int a = 0; a < C->d; a++) r2 += (x[a] - y[a]) * (x[a] - y[a]);
+        double v = exp(-r2 / C->delta) * C->q[j];
+        double t = sum + v;   /* Neumaier compensated sum */
+        if (fabs(sum) >= fabs(v)) comp += (sum - t) + v; else comp += (v - t) + sum;
+        sum = t;
+      }
+      C->u[i] = sum + comp;
+    }
+  }
+  return NULL;
+}
+
+/*
+ * u[i] = sum_j exp(-|x_i - y_j|^2 / delta) q_j for n_tgt targets x (tgt[n_tgt][d]) and n_src
+ * sources y (src[n_src][d]) with weights q, free space.  O(n_tgt n_src), all pairs, no cutoff.
+ */
+int oracle_point_fgt(int d, double delta, long n_src, const double *src, const double *q, long n_tgt,
+                     const double *tgt, double *u_out, int n_threads) {
+  if ((d != 1 && d != 2 && d != 3) || !(delta > 0) || n_src < 0 || n_tgt < 0) return 1;
+  pt_ctx C;
+  memset(&C, 0, sizeof(C));
+  C.d = d; C.delta = delta; C.n_src = n_src; C.n_tgt = n_tgt; C.src = src; C.q = q; C.tgt = tgt; C.u = u_out;
+  pthread_mutex_init(&C.mtx, NULL);
+  int nt = n_threads > 0 ? n_threads : oracle_default_threads();
+  if (nt > 256) nt = 256;
+  pthread_t th[256];
+  int started = 0;
+  for (int i = 0; i < nt; i++)
+    if (pthread_create(&th[i], NULL, pt_worker, &C) == 0) started++; else break;
+  if (started == 0) pt_worker(&C);
+  for (int i = 0; i < started; i++) pthread_join(th[i], NULL);
+  pthread_mutex_destroy(&C.mtx);
+  return 0;
+}
+
 /* The oracle's own Gauss-Legendre rule (exported so the tests can pin it). */
 int oracle_gauss_legendre(int n, double *x, double *w) {
   if (n < 1 || n > 64) return 1;

@@ -273,3 +273,22 @@ def test_target_boxes_gaussian_density_closed_form():
     u = oracle.box_fgt_boxes(d, p, delta, False, tr.level, tr.coord, s, out.level, out.coord)
     ex = _gauss_closed_form(W.node_positions(out, p), centers, alphas, delta)
     assert np.abs(u - ex).max() <= 1e-8 * np.abs(ex).max()
+
+
+def test_point_fgt_single_source_and_superposition():
+    """The discrete transform: one unit source gives the Gaussian itself; two sources add; a common
+    shift of all points changes nothing; delta enters as exp(-r^2/delta)."""
+    rng = np.random.default_rng(3)
+    for d in (2, 3):
+        x = rng.uniform(-0.5, 0.5, size=(50, d))
+        y1, y2 = rng.uniform(-0.5, 0.5, size=(2, d))
+        for delta in (1e-3, 3e-2, 1.0):
+            g1 = np.exp(-((x - y1) ** 2).sum(axis=1) / delta)
+            g2 = np.exp(-((x - y2) ** 2).sum(axis=1) / delta)
+            u1 = oracle.point_fgt(d, delta, y1[None, :], [1.0], x)
+            assert np.abs(u1 - g1).max() <= 1e-15
+            u12 = oracle.point_fgt(d, delta, np.stack([y1, y2]), [2.0, -0.5], x)
+            assert np.abs(u12 - (2 * g1 - 0.5 * g2)).max() <= 1e-14
+            s = rng.uniform(-1, 1, size=d)
+            us = oracle.point_fgt(d, delta, np.stack([y1, y2]) + s, [2.0, -0.5], x + s)
+            assert np.abs(us - u12).max() <= 1e-13
