@@ -249,6 +249,29 @@ fgt_status fgt_built_tree_get(const fgt_built_tree *t, int64_t *n_leaves, const 
 fgt_status fgt_built_tree_copy_sigma(const fgt_built_tree *t, double *dst_dev, void *stream);
 void fgt_built_tree_destroy(fgt_built_tree *t);
 
+/* Discrete (point) Gauss transform, free space (Section 3, Algorithms 1 and 2):
+ *   u[i] = sum_j exp(-|x_i - y_j|^2 / delta) q_j,  sources src[n_src][d], targets tgt[n_tgt][d] (host,
+ *   copied at create), weights q_dev[n_src] and result u_dev[n_tgt] on the device (original orders).
+ * The tree is Algorithm 1's at its cutoff level: the bounding cube of all points in 2^l_c boxes of
+ * side D0 sqrt(delta) per axis.  Boxes with more than n_s sources are dense: their sources are
+ * replaced by a tensor-product proxy grid of k_p^d Gauss-Legendre nodes (in place of the NUFFT),
+ * whose plane-wave expansion is formed, translated to every colleague (Eq. diagonaltranslation),
+ * evaluated on the colleagues' proxy grids and interpolated to their targets; sources of sparse
+ * boxes act on their colleagues' targets directly.  k_p is the smallest grid that reproduces every
+ * plane wave of the expansion on a box to 0.1 tol relative to the mode's weight (FGT_ERR_ARG above
+ * 40 nodes; about 21 at tol 1e-6 and 33 at 1e-10).  FP64. */
+typedef struct fgt_point_plan fgt_point_plan;
+typedef struct {
+  int32_t cutoff_level, proxy_order, modes_1d;
+  int64_t n_boxes, n_dense_boxes, n_incoming_boxes, n_direct_pairs;
+  double cutoff_length;
+} fgt_point_info;
+fgt_status fgt_point_plan_create(int d, double delta, double tol, int64_t n_src, const double *src, int64_t n_tgt,
+                                 const double *tgt, int n_s, fgt_point_plan **out);
+fgt_status fgt_point_execute(fgt_point_plan *plan, const double *q_dev, double *u_dev, void *stream);
+fgt_status fgt_point_plan_get_info(const fgt_point_plan *plan, fgt_point_info *info);
+void fgt_point_destroy(fgt_point_plan *plan);
+
 /* Launch-shape knobs of a plan and the autotuner that picks them.
  *   form_group:      at most this many same-size blocks of one anchor per form CTA (1..8)
  *   eval_rows16:     split precision, 3D: rows of a K = 16 block per evaluation CTA (4, 8, 16)

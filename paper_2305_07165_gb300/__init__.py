@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Plan", "FGTError", "Tuning", "lib", "build_gaussian_tree", "BC_FREE", "BC_PERIODIC", "PREC_FP64", "PREC_SPLIT", "PREC_FP64_TC", "MODE_FUSED",
+__all__ = ["Plan", "PointPlan", "FGTError", "Tuning", "lib", "build_gaussian_tree", "BC_FREE", "BC_PERIODIC", "PREC_FP64", "PREC_SPLIT", "PREC_FP64_TC", "MODE_FUSED",
            "MODE_HIERARCHICAL", "gauss_legendre", "params", "nf_for_range", "legendre_gauss_integrals",
            "spherical_bessel", "legendre_fourier_integrals", "analyze", "HostPlan", "Batch"]
 
@@ -46,6 +46,16 @@ class PlanInfo(ctypes.Structure):
                                               "n_form_blocks", "n_direct_pairs", "n_gather_pairs", "form_flops",
                                               "eval_flops", "gather_flops", "direct_flops", "device_bytes")] + \
                [("prec", ctypes.c_int32), ("mode", ctypes.c_int32), ("launches", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class PointInfo(ctypes.Structure):
+    """fgt_point_info."""
+    _fields_ = [(n, ctypes.c_int32) for n in ("cutoff_level", "proxy_order", "modes_1d")] + \
+               [(n, ctypes.c_int64) for n in ("n_boxes", "n_dense_boxes", "n_incoming_boxes", "n_direct_pairs")] + \
+               [("cutoff_length", ctypes.c_double)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -104,6 +114,11 @@ def lib():
             L.fgt_built_tree_get.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                              ctypes.POINTER(vp)]
             L.fgt_built_tree_copy_sigma.argtypes = [vp, vp, vp]
+            L.fgt_point_plan_create.argtypes = [i32, dbl, dbl, i64, vp, i64, vp, i32, ctypes.POINTER(vp)]
+            L.fgt_point_execute.argtypes = [vp, vp, vp, vp]
+            L.fgt_point_plan_get_info.argtypes = [vp, ctypes.POINTER(PointInfo)]
+            L.fgt_point_destroy.argtypes = [vp]
+            L.fgt_point_destroy.restype = None
             L.fgt_built_tree_destroy.argtypes = [vp]
             L.fgt_built_tree_destroy.restype = None
             L.fgt_merge_children.argtypes = [i32, i32, i64, vp, vp, vp, vp]
@@ -126,7 +141,8 @@ def lib():
                          "fgt_plan_read_profile", "fgt_plan_autotune", "fgt_plan_get_tuning",
                          "fgt_plan_set_tuning", "fgt_plan_set_output_tree", "fgt_leaf_errors",
                          "fgt_merge_children", "fgt_build_gaussian_tree", "fgt_built_tree_get",
-                         "fgt_built_tree_copy_sigma"):
+                         "fgt_built_tree_copy_sigma", "fgt_point_plan_create", "fgt_point_execute",
+                         "fgt_point_plan_get_info"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -453,3 +469,53 @@ def build_gaussian_tree(d, k, centers, alphas, amps=None, periodic=False, eps=1e
     finally:
         lib().fgt_built_tree_destroy(h)
     return level, coord, sigma
+
+
+class PointPlan:
+    """The discrete Gauss transform u_i = sum_j exp(-|x_i - y_j|^2/delta) q_j in free space
+    (fgt_point_plan_create / fgt_point_execute): sources and targets fixed at creation (host
+    arrays [n, d]), weights and results as CUDA float64 tensors in the callers' point orders."""
+
+    def __init__(self, d, delta, tol, src, tgt, n_s=64):
+        import torch
+        if not torch.cuda.is_available():
+            raise FGTError(4, "no CUDA device: the point FGT runs only on the GPU")
+        torch.cuda.current_device()
+        y = np.ascontiguousarray(src, dtype=np.float64).reshape(-1, d)
+        x = np.ascontiguousarray(tgt, dtype=np.float64).reshape(-1, d)
+        self.d, self.n_src, self.n_tgt = d, len(y), len(x)
+        self._h = ctypes.c_void_p()
+        _check(lib().fgt_point_plan_create(d, float(delta), float(tol), len(y), y.ctypes.data, len(x), x.ctypes.data,
+                                           int(n_s), ctypes.byref(self._h)))
+
+    def info(self) -> dict:
+        i = PointInfo()
+        _check(lib().fgt_point_plan_get_info(self._h, ctypes.byref(i)))
+        return i.as_dict()
+
+    def execute(self, q, out=None, stream=None):
+        import torch
+        if not (isinstance(q, torch.Tensor) and q.is_cuda and q.dtype == torch.float64 and q.is_contiguous()
+                and q.numel() == self.n_src):
+            raise TypeError(f"q must be a contiguous CUDA float64 tensor of {self.n_src} values")
+        if out is None:
+            out = torch.empty(self.n_tgt, dtype=torch.float64, device=q.device)
+        if not (out.is_cuda and out.dtype == torch.float64 and out.is_contiguous() and out.numel() == self.n_tgt):
+            raise TypeError(f"out must be a contiguous CUDA float64 tensor of {self.n_tgt} values")
+        s = stream if stream is not None else torch.cuda.current_stream(q.device)
+        _check(lib().fgt_point_execute(self._h, ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                       ctypes.c_void_p(s.cuda_stream)))
+        return out
+
+    __call__ = execute
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().fgt_point_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -131,6 +131,38 @@ cudaError_t gauss_nodes(int d, int k, int64_t n, const int32_t *level, const int
 cudaError_t merge_children(int d, int k, int64_t n_parents, const int64_t *child_rows, const double *vals,
                            double *parent, cudaStream_t st);
 
+// ---- discrete (point) Gauss transform with proxy grids (Algorithm 2)
+constexpr int kMaxProxy = 40;
+struct ProxyRule {
+  double x[kMaxProxy];   // Gauss-Legendre nodes on [-1, 1]
+  double bw[kMaxProxy];  // barycentric weights of the Lagrange basis on them
+};
+// Q[b][t] = sum_{j in dense box b} q_j prod_a l_{t_a}(s_{j,a}) (sources sorted by box, dense box b
+// holding the range [box_rng[2b], box_rng[2b+1]), local coordinates s in [-1, 1]^d); one CTA per box.
+cudaError_t point_anterp(int d, int kp, const ProxyRule &pr, int64_t n_dense, const int64_t *box_rng,
+                         const double *s_local, const double *q_sorted, double *Q, cudaStream_t st);
+// u[id_i] = (incoming boxes) sum_t prod_a l_{t_a}(s_{i,a}) U[in(box)][t] + sum over the box's direct
+// source boxes of exp(-|x_i - y_j|^2 / delta) q_j; one CTA per target box.
+struct PointTargets {
+  int d = 0, kp = 0;
+  double delta = 0;
+  int64_t n_tbox = 0;
+  const int64_t *tbox_ptr = nullptr;   // CSR over target boxes into the sorted targets
+  const double *t_xyz = nullptr;       // sorted targets, coordinates [n][d]
+  const double *t_local = nullptr;     // sorted targets, local coordinates in their box [n][d]
+  const int64_t *t_id = nullptr;       // original index of each sorted target
+  const int32_t *tbox_in = nullptr;    // row of U for the box, -1 if no plane-wave part
+  const double *U = nullptr;           // [n_in][kp^d]
+  const int64_t *dptr = nullptr;       // CSR over target boxes into dbox
+  const int32_t *dbox = nullptr;       // direct source boxes (indices into sptr)
+  const int64_t *sptr = nullptr;       // CSR over boxes into the sorted sources
+  const double *s_xyz = nullptr;       // sorted sources [n][d]
+  const double *q_sorted = nullptr;    // weights of the sorted sources
+};
+cudaError_t point_targets(const PointTargets &pt, const ProxyRule &pr, double *u, cudaStream_t st);
+// q permuted into the sources' box order: q_sorted[j] = q[s_id[j]]
+cudaError_t point_gather_q(int64_t n, const int64_t *s_id, const double *q, double *q_sorted, cudaStream_t st);
+
 // Shared-memory bytes of the grouped form kernel (G blocks of K nodes per axis; r, c: real and
 // complex element sizes) and of the whole-block evaluation kernel.
 inline size_t form2_bytes(int d, int G, int K, int n1, int nh, size_t r, size_t c) {

@@ -2480,6 +2480,144 @@ cudaError_t gauss_nodes(int d, int k, int64_t n, const int32_t *level, const int
   return cudaGetLastError();
 }
 
+// ----------------------------------------------------------------------------- point FGT (Algorithm 2)
+//
+// The discrete transform with tensor-product "proxy" grids in the cutoff-level boxes (Section 8's
+// closing remark): the sources of a dense box are replaced by the values Q on a k_p^d Gauss-
+// Legendre grid that reproduce every plane wave of the expansion (Q = the transpose of Lagrange
+// interpolation at the sources), the box-FGT form / gather / evaluation kernels run on those grids,
+// and the incoming expansion is interpolated from the grid to the targets.
+
+// l_t(s) for all t by the barycentric formula (exact at the nodes).
+__device__ inline void lagrange_bary(const ProxyRule &pr, int kp, double s, double *l) {
+  double den = 0.0;
+  int hit = -1;
+  for (int t = 0; t < kp; ++t) {
+    const double dx = s - pr.x[t];
+    if (dx == 0.0) hit = t;
+    l[t] = (dx == 0.0) ? 0.0 : pr.bw[t] / dx;
+    den += l[t];
+  }
+  if (hit >= 0) {
+    for (int t = 0; t < kp; ++t) l[t] = (t == hit) ? 1.0 : 0.0;
+    return;
+  }
+  const double inv = 1.0 / den;
+  for (int t = 0; t < kp; ++t) l[t] *= inv;
+}
+
+constexpr int kAnterpChunk = 32;
+
+__global__ void __launch_bounds__(256) point_anterp_kernel(int d, int kp, ProxyRule pr, const int64_t *__restrict__ box_rng,
+                                                           const double *__restrict__ s_local,
+                                                           const double *__restrict__ q_sorted, double *__restrict__ Q) {
+  extern __shared__ double sma[];
+  double *L = sma;                                    // [kAnterpChunk][d][kp]
+  double *qs = L + (size_t)kAnterpChunk * d * kp;      // [kAnterpChunk]
+  const int np = d == 3 ? kp * kp * kp : kp * kp;
+  const int64_t j0 = box_rng[2 * blockIdx.x], j1 = box_rng[2 * blockIdx.x + 1];
+  double *out = Q + (int64_t)blockIdx.x * np;
+  for (int e = threadIdx.x; e < np; e += blockDim.x) out[e] = 0.0;
+  for (int64_t c0 = j0; c0 < j1; c0 += kAnterpChunk) {
+    const int nc = (int)min((int64_t)kAnterpChunk, j1 - c0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nc * d; e += blockDim.x) {
+      const int j = e / d, a = e - j * d;
+      lagrange_bary(pr, kp, s_local[(c0 + j) * d + a], L + ((size_t)j * d + a) * kp);
+    }
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) qs[j] = q_sorted[c0 + j];
+    __syncthreads();
+    for (int e = threadIdx.x; e < np; e += blockDim.x) {
+      const int t1 = e % kp, t2 = (e / kp) % kp, t3 = d == 3 ? e / (kp * kp) : 0;
+      double acc = 0.0;
+      for (int j = 0; j < nc; ++j) {
+        const double *lj = L + (size_t)j * d * kp;
+        double v = qs[j] * lj[t1] * lj[kp + t2];
+        if (d == 3) v *= lj[2 * kp + t3];
+        acc += v;
+      }
+      out[e] += acc;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128) point_target_kernel(PointTargets pt, ProxyRule pr, double *__restrict__ u) {
+  const int d = pt.d, kp = pt.kp;
+  const int64_t b = blockIdx.x;
+  const int64_t i0 = pt.tbox_ptr[b], i1 = pt.tbox_ptr[b + 1];
+  const int in = pt.tbox_in[b];
+  const int np = d == 3 ? kp * kp * kp : kp * kp;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    double acc = 0.0;
+    if (in >= 0) {
+      double l[3][kMaxProxy];
+      for (int a = 0; a < d; ++a) lagrange_bary(pr, kp, pt.t_local[i * d + a], l[a]);
+      const double *Ub = pt.U + (int64_t)in * np;
+      if (d == 3) {
+        for (int t3 = 0; t3 < kp; ++t3) {
+          double s2 = 0.0;
+          for (int t2 = 0; t2 < kp; ++t2) {
+            const double *row = Ub + ((int64_t)t3 * kp + t2) * kp;
+            double s1 = 0.0;
+            for (int t1 = 0; t1 < kp; ++t1) s1 = fma(l[0][t1], __ldg(row + t1), s1);
+            s2 = fma(l[1][t2], s1, s2);
+          }
+          acc = fma(l[2][t3], s2, acc);
+        }
+      } else {
+        for (int t2 = 0; t2 < kp; ++t2) {
+          const double *row = Ub + (int64_t)t2 * kp;
+          double s1 = 0.0;
+          for (int t1 = 0; t1 < kp; ++t1) s1 = fma(l[0][t1], __ldg(row + t1), s1);
+          acc = fma(l[1][t2], s1, acc);
+        }
+      }
+    }
+    double x[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < d; ++a) x[a] = pt.t_xyz[i * d + a];
+    for (int64_t q = pt.dptr[b]; q < pt.dptr[b + 1]; ++q) {
+      const int32_t sb = pt.dbox[q];
+      for (int64_t j = pt.sptr[sb]; j < pt.sptr[sb + 1]; ++j) {
+        double r2 = 0.0;
+        for (int a = 0; a < d; ++a) {
+          const double dx = x[a] - __ldg(pt.s_xyz + j * d + a);
+          r2 = fma(dx, dx, r2);
+        }
+        acc = fma(exp(-r2 / pt.delta), __ldg(pt.q_sorted + j), acc);
+      }
+    }
+    u[pt.t_id[i]] = acc;
+  }
+}
+
+__global__ void point_gather_q_kernel(int64_t n, const int64_t *__restrict__ id, const double *__restrict__ q,
+                                      double *__restrict__ qs) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) qs[j] = q[id[j]];
+}
+
+cudaError_t point_anterp(int d, int kp, const ProxyRule &pr, int64_t n_dense, const int64_t *box_rng,
+                         const double *s_local, const double *q_sorted, double *Q, cudaStream_t st) {
+  if (n_dense <= 0) return cudaSuccess;
+  const size_t sm = sizeof(double) * ((size_t)kAnterpChunk * d * kp + kAnterpChunk);
+  cudaError_t e = cudaFuncSetAttribute(point_anterp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  point_anterp_kernel<<<(unsigned)n_dense, 256, sm, st>>>(d, kp, pr, box_rng, s_local, q_sorted, Q);
+  return cudaGetLastError();
+}
+
+cudaError_t point_targets(const PointTargets &pt, const ProxyRule &pr, double *u, cudaStream_t st) {
+  if (pt.n_tbox <= 0) return cudaSuccess;
+  point_target_kernel<<<(unsigned)pt.n_tbox, 128, 0, st>>>(pt, pr, u);
+  return cudaGetLastError();
+}
+
+cudaError_t point_gather_q(int64_t n, const int64_t *s_id, const double *q, double *q_sorted, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  point_gather_q_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, s_id, q, q_sorted);
+  return cudaGetLastError();
+}
+
 cudaError_t leaf_errors(int d, int k, int64_t n, const double *vals, double *err, double *sumsq, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   GLRule gl;

@@ -21,6 +21,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <new>
 #include <string>
 #include <tuple>
@@ -2104,3 +2105,377 @@ fgt_status fgt_execute_batch(fgt_plan *const *plans, const double *const *sigma_
 }
 
 }  // extern "C"
+
+// ============================================================================ point FGT (Algorithm 2)
+//
+// The discrete transform u(x_i) = sum_j exp(-|x_i - y_j|^2/delta) q_j in free space.  Algorithm 1's
+// tree is taken at its cutoff level only: the root is the bounding cube of all points enlarged to
+// 2^l_c boxes of side D0 sqrt(delta) (the "cutoff length"), every nonempty box at that level is a
+// leaf.  A box holding more than n_s sources is dense: its sources are replaced by a k_p^d proxy
+// grid (the plane-wave form then runs in tensor-product form, as the paper's closing remark
+// proposes in place of the NUFFT), its outgoing expansion reaches every colleague through the
+// diagonal translation, and the incoming expansion is evaluated on the target box's proxy grid and
+// interpolated to the targets.  Sources of sparse boxes reach their colleagues' targets directly.
+// k_p is the smallest grid on which Lagrange interpolation reproduces the highest plane wave of the
+// expansion to 5e-2 eps on the box.
+
+struct fgt_point_plan {
+  int d = 0, n_s = 0, kp = 0, M = 0, n1 = 0, nh = 0, lc = 0;
+  double delta = 0, tol = 0, D0 = 0, Lc = 0, h = 0, kappa = 0;
+  int64_t n_src = 0, n_tgt = 0, n_box = 0, n_dense = 0, n_in = 0, n_direct = 0;
+  fgt::ProxyRule pr{};
+  fgt::ExecDesc ex;
+  fgt::PointTargets pt;
+  void *dev = nullptr;     // lists, tables, sorted points
+  void *work = nullptr;    // phi, psi, Q, U, q_sorted
+  const int64_t *dense_rng = nullptr, *s_id = nullptr;
+  const double *s_local = nullptr;
+  double *Q = nullptr, *U = nullptr, *q_sorted = nullptr;
+  ~fgt_point_plan() {
+    if (dev) cudaFree(dev);
+    if (work) cudaFree(work);
+  }
+};
+
+namespace {
+
+struct Packer {
+  std::vector<unsigned char> buf;
+  template <typename T>
+  size_t add(const std::vector<T> &v) {
+    const size_t off = (buf.size() + 255) & ~(size_t)255;
+    buf.resize(off + sizeof(T) * v.size());
+    if (!v.empty()) std::memcpy(buf.data() + off, v.data(), sizeof(T) * v.size());
+    return off;
+  }
+};
+
+// Smallest Gauss-Legendre grid on which Lagrange interpolation reproduces every plane wave of the
+// expansion well enough: mode m (phase kappa m (Lc/2) s over a box, s in [-1, 1]) enters the
+// expansion with the relative weight exp(-m^2 h^2 / 4), so its interpolation error times that
+// weight must stay within tol.
+int proxy_order(double kappa_half_L, double h, int M, double tol, fgt::ProxyRule &pr) {
+  for (int n = 4; n <= fgt::kMaxProxy; ++n) {
+    double x[fgt::kMaxProxy], wt[fgt::kMaxProxy];
+    fgt::gl_rule(n, x, wt);
+    double bw[fgt::kMaxProxy];
+    for (int t = 0; t < n; ++t) {
+      double p = 1.0;
+      for (int m = 0; m < n; ++m)
+        if (m != t) p *= (x[t] - x[m]);
+      bw[t] = 1.0 / p;
+    }
+    double worst = 0.0;
+    for (int m = 1; m < M && worst <= tol; ++m) {
+      const double w = kappa_half_L * m, rel = std::exp(-0.25 * m * m * h * h);
+      for (int q = 0; q <= 400; ++q) {
+        const double s = -1.0 + 2.0 * q / 400.0;
+        double num_r = 0.0, num_i = 0.0, den = 0.0;
+        bool hit = false;
+        for (int t = 0; t < n; ++t) {
+          const double dx = s - x[t];
+          if (dx == 0.0) { hit = true; break; }
+          const double c = bw[t] / dx;
+          num_r += c * std::cos(w * x[t]);
+          num_i += c * std::sin(w * x[t]);
+          den += c;
+        }
+        if (hit) continue;
+        worst = std::max(worst, rel * std::hypot(num_r / den - std::cos(w * s), num_i / den - std::sin(w * s)));
+      }
+    }
+    if (worst <= tol) {
+      for (int t = 0; t < n; ++t) { pr.x[t] = x[t]; pr.bw[t] = bw[t]; }
+      return n;
+    }
+  }
+  return -1;
+}
+
+}  // namespace
+
+fgt_status fgt_point_plan_create(int d, double delta, double tol, int64_t n_src, const double *src, int64_t n_tgt,
+                                 const double *tgt, int n_s, fgt_point_plan **out) {
+  if (!out) return fail(FGT_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if ((d != 2 && d != 3) || !(delta > 0) || !(tol > 0 && tol < 1) || n_src < 0 || n_tgt < 0 || n_s < 1 ||
+      (n_src > 0 && !src) || (n_tgt > 0 && !tgt))
+    return fail(FGT_ERR_ARG, "point plan: bad arguments");
+  auto *P = new (std::nothrow) fgt_point_plan();
+  if (!P) return fail(FGT_ERR_OOM, "host allocation");
+  std::unique_ptr<fgt_point_plan> guard(P);
+  P->d = d; P->delta = delta; P->tol = tol; P->n_s = n_s; P->n_src = n_src; P->n_tgt = n_tgt;
+  // Theorem 1 for colleagues at the cutoff length: |x_a - y_a| <= 2 D0 sqrt(delta), R = 2 D0
+  P->D0 = std::sqrt(std::log(3.0 / tol));
+  P->Lc = P->D0 * std::sqrt(delta);
+  const double R = 2.0 * P->D0;
+  P->h = 2.0 * kPi / (R + P->D0);
+  P->M = (int)std::ceil(P->D0 * (R + P->D0) / kPi);
+  P->n1 = 2 * P->M - 1;
+  P->nh = P->M;
+  P->kappa = P->h / std::sqrt(delta);
+  P->kp = proxy_order(P->kappa * 0.5 * P->Lc, P->h, P->M, 0.1 * tol, P->pr);
+  if (P->kp < 0) return fail(FGT_ERR_ARG, "point plan: tolerance needs a proxy grid above 40 nodes per axis");
+  // root: the bounding cube of all points, 2^l_c cutoff boxes wide
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int a = 0; a < d; ++a) { lo[a] = HUGE_VAL; hi[a] = -HUGE_VAL; }
+  for (const auto &pts : {std::make_pair(src, n_src), std::make_pair(tgt, n_tgt)})
+    for (int64_t i = 0; i < pts.second; ++i)
+      for (int a = 0; a < d; ++a) {
+        const double v = pts.first[i * d + a];
+        if (!std::isfinite(v)) return fail(FGT_ERR_ARG, "point plan: non-finite coordinate");
+        lo[a] = std::min(lo[a], v);
+        hi[a] = std::max(hi[a], v);
+      }
+  if (n_src + n_tgt == 0)
+    for (int a = 0; a < d; ++a) lo[a] = hi[a] = 0.0;
+  double ext = 0.0, c0[3] = {0, 0, 0};
+  for (int a = 0; a < d; ++a) { ext = std::max(ext, hi[a] - lo[a]); c0[a] = 0.5 * (lo[a] + hi[a]); }
+  int lc = 0;
+  while (std::ldexp(P->Lc, lc) < ext * (1.0 + 1e-12) + 1e-300 && lc < 20) ++lc;
+  if (std::ldexp(P->Lc, lc) < ext) return fail(FGT_ERR_ARG, "point plan: more than 2^20 cutoff boxes per axis");
+  P->lc = lc;
+  const int64_t nb = (int64_t)1 << lc;
+  const double L0 = std::ldexp(P->Lc, lc);
+  double corner[3] = {0, 0, 0};
+  for (int a = 0; a < d; ++a) corner[a] = c0[a] - 0.5 * L0;
+  // box of every point, and the nonempty boxes
+  std::unordered_map<uint64_t, int32_t> box_of;
+  std::vector<std::array<int32_t, 3>> bc;
+  auto box_index = [&](const double *x, std::array<int32_t, 3> &c) {
+    for (int a = 0; a < 3; ++a) c[a] = 0;
+    for (int a = 0; a < d; ++a) {
+      int64_t v = (int64_t)std::floor((x[a] - corner[a]) / P->Lc);
+      c[a] = (int32_t)std::min<int64_t>(std::max<int64_t>(v, 0), nb - 1);
+    }
+    const uint64_t key = box_key(lc, c.data());
+    auto it = box_of.find(key);
+    if (it != box_of.end()) return it->second;
+    const int32_t id = (int32_t)bc.size();
+    box_of.emplace(key, id);
+    bc.push_back(c);
+    return id;
+  };
+  std::vector<int32_t> sbox(n_src), tbox(n_tgt);
+  std::array<int32_t, 3> c{};
+  for (int64_t j = 0; j < n_src; ++j) sbox[j] = box_index(src + j * d, c);
+  for (int64_t i = 0; i < n_tgt; ++i) tbox[i] = box_index(tgt + i * d, c);
+  const int64_t nbox = (int64_t)bc.size();
+  P->n_box = nbox;
+  // sources and targets sorted by box (counting sort)
+  std::vector<int64_t> sptr(nbox + 1, 0), tptr(nbox + 1, 0);
+  for (int32_t b : sbox) sptr[b + 1]++;
+  for (int32_t b : tbox) tptr[b + 1]++;
+  for (int64_t b = 0; b < nbox; ++b) { sptr[b + 1] += sptr[b]; tptr[b + 1] += tptr[b]; }
+  std::vector<int64_t> s_id(n_src), t_id(n_tgt), fill_s(sptr.begin(), sptr.end() - 1), fill_t(tptr.begin(), tptr.end() - 1);
+  for (int64_t j = 0; j < n_src; ++j) s_id[fill_s[sbox[j]]++] = j;
+  for (int64_t i = 0; i < n_tgt; ++i) t_id[fill_t[tbox[i]]++] = i;
+  auto centre = [&](int64_t b, int a) { return corner[a] + (bc[b][a] + 0.5) * P->Lc; };
+  std::vector<double> s_xyz(n_src * d), s_loc(n_src * d), t_xyz(n_tgt * d), t_loc(n_tgt * d);
+  for (int64_t j = 0; j < n_src; ++j)
+    for (int a = 0; a < d; ++a) {
+      s_xyz[j * d + a] = src[s_id[j] * d + a];
+      s_loc[j * d + a] = (s_xyz[j * d + a] - centre(sbox[s_id[j]], a)) / (0.5 * P->Lc);
+    }
+  for (int64_t i = 0; i < n_tgt; ++i)
+    for (int a = 0; a < d; ++a) {
+      t_xyz[i * d + a] = tgt[t_id[i] * d + a];
+      t_loc[i * d + a] = (t_xyz[i * d + a] - centre(tbox[t_id[i]], a)) / (0.5 * P->Lc);
+    }
+  // dense boxes (outgoing slots): their sources are the runs [sptr[b], sptr[b+1]) of the box order
+  std::vector<int32_t> dense_slot(nbox, -1);
+  std::vector<int64_t> dense_rng;
+  for (int64_t b = 0; b < nbox; ++b)
+    if (sptr[b + 1] - sptr[b] > n_s) {
+      dense_slot[b] = (int32_t)P->n_dense++;
+      dense_rng.push_back(sptr[b]);
+      dense_rng.push_back(sptr[b + 1]);
+    }
+  // neighbour lists: incoming boxes (targets with a dense colleague), gather sources by code,
+  // direct source boxes (sparse colleagues with sources)
+  int noff = 1;
+  for (int a = 0; a < d; ++a) noff *= 3;
+  std::vector<int32_t> in_row(nbox, -1), gdst, dbox;
+  std::vector<int64_t> gptr(1, 0), dptr(1, 0);
+  std::vector<fgt::GatherSrc> gsrc;
+  for (int64_t b = 0; b < nbox; ++b) {
+    const bool has_t = tptr[b + 1] > tptr[b];
+    std::vector<fgt::GatherSrc> g;
+    for (int oc = 0; oc < noff; ++oc) {
+      std::array<int32_t, 3> q{};
+      bool ok = true;
+      int code = 0, mul = 1;
+      for (int a = 0, r = oc; a < d; ++a, r /= 3) {
+        const int o = r % 3 - 1;
+        const int64_t v = bc[b][a] + o;
+        if (v < 0 || v >= nb) { ok = false; break; }
+        q[a] = (int32_t)v;
+        code += (o + 1) * mul;
+        mul *= 3;
+      }
+      if (!ok) continue;
+      auto it = box_of.find(box_key(lc, q.data()));
+      if (it == box_of.end()) continue;
+      const int32_t s = it->second;
+      if (sptr[s + 1] == sptr[s]) continue;
+      if (dense_slot[s] >= 0) g.push_back(fgt::GatherSrc{dense_slot[s], code});
+      else if (has_t) dbox.push_back(s);
+    }
+    if (has_t) dptr.push_back((int64_t)dbox.size());
+    if (has_t && !g.empty()) {
+      in_row[b] = (int32_t)P->n_in++;
+      gdst.push_back(in_row[b]);
+      gsrc.insert(gsrc.end(), g.begin(), g.end());
+      gptr.push_back((int64_t)gsrc.size());
+    }
+  }
+  P->n_direct = (int64_t)dbox.size();
+  // target boxes (those with targets), in box order
+  std::vector<int64_t> tb_ptr(1, 0);
+  std::vector<int32_t> tb_in;
+  for (int64_t b = 0; b < nbox; ++b)
+    if (tptr[b + 1] > tptr[b]) {
+      tb_ptr.push_back(tptr[b + 1]);
+      tb_in.push_back(in_row[b]);
+    }
+  // plane-wave matrices of a box about its own centre: form F[a][t] = w_a exp(-i kappa m_a
+  // (Lc/2) eta_t) (last axis m >= 0, factor 2 for m > 0), evaluation E[t][a] = exp(+i ...)
+  const int kp = P->kp, n1 = P->n1, nh = P->nh, M = P->M;
+  std::vector<double2> Ff((size_t)n1 * kp), Fh((size_t)nh * kp), Ef((size_t)kp * n1), Eh((size_t)kp * nh);
+  for (int a = 0; a < n1; ++a) {
+    const int m = a - (M - 1);
+    const double w = P->h / (2.0 * std::sqrt(kPi)) * std::exp(-0.25 * m * m * P->h * P->h);
+    for (int t = 0; t < kp; ++t) {
+      const double ph = P->kappa * m * 0.5 * P->Lc * P->pr.x[t];
+      Ff[(size_t)a * kp + t] = make_double2(w * std::cos(ph), -w * std::sin(ph));
+      Ef[(size_t)t * n1 + a] = make_double2(std::cos(ph), std::sin(ph));
+      if (m >= 0) {
+        Fh[(size_t)m * kp + t] = make_double2((m == 0 ? 1.0 : 2.0) * w * std::cos(ph), -(m == 0 ? 1.0 : 2.0) * w * std::sin(ph));
+        Eh[(size_t)t * nh + m] = make_double2(std::cos(ph), std::sin(ph));
+      }
+    }
+  }
+  // diagonal translation phases for S = T + o: exp(+i k (c_T - c_S)) = exp(-i kappa m o Lc)
+  std::vector<double2> Pf((size_t)3 * n1), Ph((size_t)3 * nh);
+  for (int o = -1; o <= 1; ++o) {
+    for (int a = 0; a < n1; ++a) {
+      const double ph = -P->kappa * (a - (M - 1)) * o * P->Lc;
+      Pf[(size_t)(o + 1) * n1 + a] = make_double2(std::cos(ph), std::sin(ph));
+    }
+    for (int b = 0; b < nh; ++b) {
+      const double ph = -P->kappa * b * o * P->Lc;
+      Ph[(size_t)(o + 1) * nh + b] = make_double2(std::cos(ph), std::sin(ph));
+    }
+  }
+  // form blocks (dense boxes) and evaluation blocks (incoming boxes): one proxy grid each
+  std::vector<fgt::Block> fblk, eblk;
+  std::vector<int64_t> fleaf, eleaf;
+  for (int64_t i = 0; i < P->n_dense; ++i) {
+    fgt::Block b{};
+    b.slot = (int32_t)i; b.K = kp; b.dl = 0; b.flags = 0; b.leaf0 = (int64_t)fleaf.size();
+    fleaf.push_back(i);
+    fblk.push_back(b);
+  }
+  for (int64_t i = 0; i < P->n_in; ++i) {
+    fgt::Block b{};
+    b.slot = (int32_t)i; b.K = kp; b.dl = 0; b.flags = 0; b.leaf0 = (int64_t)eleaf.size();
+    eleaf.push_back(i);
+    eblk.push_back(b);
+  }
+  Packer pk;
+  const size_t o_fblk = pk.add(fblk), o_eblk = pk.add(eblk), o_fleaf = pk.add(fleaf), o_eleaf = pk.add(eleaf);
+  const size_t o_Ff = pk.add(Ff), o_Fh = pk.add(Fh), o_Ef = pk.add(Ef), o_Eh = pk.add(Eh), o_Pf = pk.add(Pf),
+               o_Ph = pk.add(Ph);
+  const size_t o_gdst = pk.add(gdst), o_gptr = pk.add(gptr), o_gsrc = pk.add(gsrc);
+  const size_t o_drng = pk.add(dense_rng), o_sloc = pk.add(s_loc);
+  const size_t o_tbp = pk.add(tb_ptr), o_txyz = pk.add(t_xyz), o_tloc = pk.add(t_loc), o_tid = pk.add(t_id),
+               o_tbin = pk.add(tb_in), o_dp = pk.add(dptr), o_db = pk.add(dbox), o_sp = pk.add(sptr),
+               o_sxyz = pk.add(s_xyz), o_sid = pk.add(s_id);
+  cudaError_t e = cudaMalloc(&P->dev, std::max<size_t>(pk.buf.size(), 256));
+  if (e != cudaSuccess) { P->dev = nullptr; cudaGetLastError(); return fail(FGT_ERR_OOM, "point plan: device tables"); }
+  e = cudaMemcpy(P->dev, pk.buf.data(), pk.buf.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "point plan upload");
+  auto at = [&](size_t off) { return (const void *)((const char *)P->dev + off); };
+  const int64_t np = d == 3 ? (int64_t)kp * kp * kp : (int64_t)kp * kp;
+  const int64_t ss = d == 3 ? (int64_t)nh * n1 * n1 : (int64_t)nh * n1;
+  const size_t phi_b = sizeof(double2) * ss * P->n_dense, psi_b = sizeof(double2) * ss * P->n_in;
+  const size_t q_b = sizeof(double) * np * P->n_dense, u_b = sizeof(double) * np * P->n_in;
+  const size_t qs_b = sizeof(double) * std::max<int64_t>(n_src, 1);
+  size_t off = 0;
+  auto place = [&](size_t bytes) { const size_t o = off; off = (off + bytes + 255) & ~(size_t)255; return o; };
+  const size_t w_phi = place(phi_b), w_psi = place(psi_b), w_q = place(q_b), w_u = place(u_b), w_qs = place(qs_b);
+  e = cudaMalloc(&P->work, std::max<size_t>(off, 256));
+  if (e != cudaSuccess) { P->work = nullptr; cudaGetLastError(); return fail(FGT_ERR_OOM, "point plan: workspace"); }
+  auto wk = [&](size_t o) { return (void *)((char *)P->work + o); };
+  P->Q = (double *)wk(w_q);
+  P->U = (double *)wk(w_u);
+  P->q_sorted = (double *)wk(w_qs);
+  P->dense_rng = (const int64_t *)at(o_drng);
+  P->s_local = (const double *)at(o_sloc);
+  P->s_id = (const int64_t *)at(o_sid);
+  fgt::ExecDesc &x = P->ex;
+  x.d = d; x.k = kp; x.n1 = n1; x.nh = nh; x.prec = 0; x.fourier = 0;
+  x.slot_size = ss;
+  x.n_phi_slots = P->n_dense; x.n_psi_slots = P->n_in;
+  x.phi = wk(w_phi); x.psi = wk(w_psi);
+  x.blocks = (const fgt::Block *)at(o_fblk);
+  x.n_blocks = P->n_dense;
+  x.Kmax = kp;
+  x.f1_blocks = (const fgt::Block *)at(o_fblk);
+  x.n_f1 = P->n_dense;
+  x.Kmax_f1 = kp;
+  x.e1_blocks = (const fgt::Block *)at(o_eblk);
+  x.n_e1 = P->n_in;
+  x.Kmax_e1 = kp;
+  x.block_leaves = (const int64_t *)at(o_fleaf);
+  x.eval_leaves = (const int64_t *)at(o_eleaf);
+  x.Ff = at(o_Ff); x.Fh = at(o_Fh); x.Ef = at(o_Ef); x.Eh = at(o_Eh);
+  x.n_gather = P->n_in;
+  x.gather_dst = (const int32_t *)at(o_gdst);
+  x.gather_ptr = (const int64_t *)at(o_gptr);
+  x.gather_src = (const fgt::GatherSrc *)at(o_gsrc);
+  x.Pf = at(o_Pf); x.Ph = at(o_Ph);
+  x.n_points = P->n_in * np;
+  fgt::PointTargets &t = P->pt;
+  t.d = d; t.kp = kp; t.delta = delta;
+  t.n_tbox = (int64_t)tb_in.size();
+  t.tbox_ptr = (const int64_t *)at(o_tbp);
+  t.t_xyz = (const double *)at(o_txyz);
+  t.t_local = (const double *)at(o_tloc);
+  t.t_id = (const int64_t *)at(o_tid);
+  t.tbox_in = (const int32_t *)at(o_tbin);
+  t.U = P->U;
+  t.dptr = (const int64_t *)at(o_dp);
+  t.dbox = (const int32_t *)at(o_db);
+  t.sptr = (const int64_t *)at(o_sp);
+  t.s_xyz = (const double *)at(o_sxyz);
+  t.q_sorted = P->q_sorted;
+  *out = guard.release();
+  return FGT_OK;
+}
+
+fgt_status fgt_point_execute(fgt_point_plan *P, const double *q_dev, double *u_dev, void *stream) {
+  if (!P || (P->n_src > 0 && !q_dev) || (P->n_tgt > 0 && !u_dev)) return fail(FGT_ERR_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = fgt::point_gather_q(P->n_src, P->s_id, q_dev, P->q_sorted, st);
+  if (e == cudaSuccess) e = fgt::point_anterp(P->d, P->kp, P->pr, P->n_dense, P->dense_rng, P->s_local, P->q_sorted,
+                                              P->Q, st);
+  if (e == cudaSuccess && P->n_dense > 0 && P->n_in > 0) e = fgt::run_transform(P->ex, P->Q, P->U, st);
+  if (e == cudaSuccess) e = fgt::point_targets(P->pt, P->pr, u_dev, st);
+  return e == cudaSuccess ? FGT_OK : cuda_fail(e, "point transform");
+}
+
+fgt_status fgt_point_plan_get_info(const fgt_point_plan *P, fgt_point_info *info) {
+  if (!P || !info) return fail(FGT_ERR_ARG, "NULL argument");
+  info->cutoff_level = P->lc;
+  info->proxy_order = P->kp;
+  info->modes_1d = P->n1;
+  info->n_boxes = P->n_box;
+  info->n_dense_boxes = P->n_dense;
+  info->n_incoming_boxes = P->n_in;
+  info->n_direct_pairs = P->n_direct;
+  info->cutoff_length = P->Lc;
+  return FGT_OK;
+}
+
+void fgt_point_destroy(fgt_point_plan *P) { delete P; }
