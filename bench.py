@@ -368,6 +368,41 @@ def run_refinement(F, torch):
             "output_tree_transform_ms": ms, "output_points_per_s": len(lev) * k ** d / ms * 1e3}
 
 
+def run_point_fgt(F, torch):
+    """The discrete Gauss transform (Algorithm 2 with proxy grids): 1M sources and 1M targets
+    (the same points) clustered around 8 centres in 3D and uniform in 2D, delta = 1e-3 (3D) /
+    1e-4 (2D), tol 1e-6 and 1e-10, n_s = 64; points/s = (sources + targets) / time."""
+    rng = np.random.default_rng(17)
+    out = {}
+    c = rng.uniform(-0.4, 0.4, size=(8, 3))
+    w = np.exp(rng.uniform(np.log(0.02), np.log(0.1), size=8))
+    lab = rng.integers(0, 8, 1 << 20)
+    sets = {"3d_clustered": (3, 1e-3, c[lab] + w[lab, None] * rng.standard_normal((1 << 20, 3))),
+            "2d_uniform": (2, 1e-4, rng.uniform(-0.5, 0.5, size=(1 << 20, 2)))}
+    for name, (d, delta, pts) in sets.items():
+        q = torch.from_numpy(rng.uniform(0.5, 1.5, len(pts))).cuda()
+        u = torch.empty_like(q)
+        row = {"points": len(pts), "delta": delta}
+        for tol in (1e-6, 1e-10):
+            t0 = time.perf_counter()
+            plan = F.PointPlan(d, delta, tol, pts, pts, n_s=64)
+            t_plan = time.perf_counter() - t0
+            st = torch.cuda.current_stream()
+            for _ in range(2):
+                plan(q, out=u)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(5):
+                plan(q, out=u)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 5
+            row[f"tol{tol:g}"] = dict(plan.info(), ms=ms, plan_s=t_plan, points_per_s=2 * len(pts) / ms * 1e3)
+            plan.close()
+        out[name] = row
+    return out
+
+
 def metric_name(w):
     return (f"target points/s (box FGT, {w.d}D {'periodic' if w.periodic else 'free space'}, "
             f"delta={w.delta:g}, tol 1e-6 split form)")
@@ -486,6 +521,7 @@ def main():
     if not args.no_sweep and rank == 0:
         sweeps = run_sweeps(args, F, torch, w, flush)
         refinement = run_refinement(F, torch)
+        refinement["point_fgt"] = run_point_fgt(F, torch)
 
     # end to end through the host-buffer entry point (pinned host memory, copies timed)
     plan = head["plan"]

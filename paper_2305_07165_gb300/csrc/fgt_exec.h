@@ -137,17 +137,19 @@ struct ProxyRule {
   double x[kMaxProxy];   // Gauss-Legendre nodes on [-1, 1]
   double bw[kMaxProxy];  // barycentric weights of the Lagrange basis on them
 };
-// Q[b][t] = sum_{j in dense box b} q_j prod_a l_{t_a}(s_{j,a}) (sources sorted by box, dense box b
-// holding the range [box_rng[2b], box_rng[2b+1]), local coordinates s in [-1, 1]^d); one CTA per box.
-cudaError_t point_anterp(int d, int kp, const ProxyRule &pr, int64_t n_dense, const int64_t *box_rng,
+// Points per CTA of the point-FGT kernels (segments of a box's sources or targets).
+constexpr int64_t kPointSeg = 1024;
+// Q[b][t] = sum_{j in dense box b} q_j prod_a l_{t_a}(s_{j,a}) (sources sorted by box, local
+// coordinates s in [-1, 1]^d); one CTA per segment seg[3s..3s+2] = (box, first, end).
+cudaError_t point_anterp(int d, int kp, const ProxyRule &pr, int64_t n_dense, int64_t n_seg, const int64_t *seg,
                          const double *s_local, const double *q_sorted, double *Q, cudaStream_t st);
 // u[id_i] = (incoming boxes) sum_t prod_a l_{t_a}(s_{i,a}) U[in(box)][t] + sum over the box's direct
 // source boxes of exp(-|x_i - y_j|^2 / delta) q_j; one CTA per target box.
 struct PointTargets {
   int d = 0, kp = 0;
   double delta = 0;
-  int64_t n_tbox = 0;
-  const int64_t *tbox_ptr = nullptr;   // CSR over target boxes into the sorted targets
+  int64_t n_tseg = 0;
+  const int64_t *tseg = nullptr;       // segments (target box, first, end) of at most kPointSeg targets
   const double *t_xyz = nullptr;       // sorted targets, coordinates [n][d]
   const double *t_local = nullptr;     // sorted targets, local coordinates in their box [n][d]
   const int64_t *t_id = nullptr;       // original index of each sorted target

@@ -19,6 +19,7 @@
 // m_2 * n1 + m_1 in 2D, m_1 fastest.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -2488,91 +2489,184 @@ cudaError_t gauss_nodes(int d, int k, int64_t n, const int32_t *level, const int
 // interpolation at the sources), the box-FGT form / gather / evaluation kernels run on those grids,
 // and the incoming expansion is interpolated from the grid to the targets.
 
-// l_t(s) for all t by the barycentric formula (exact at the nodes).
-__device__ inline void lagrange_bary(const ProxyRule &pr, int kp, double s, double *l) {
-  double den = 0.0;
+// l_t(s), t < kp, by the barycentric formula: the k_p reciprocals 1/(s - x_t) come from one
+// division and prefix / suffix products of the differences (batch inversion).  A point within
+// 1e-100 of a node takes that node's unit vector (the formula's limit to double precision).
+// Entries kp..KP-1 are zero.  l[t] is written at l[t * stride].
+template <int KP>
+__device__ inline void lagrange_row(const ProxyRule &pr, int kp, double s, double *l, int stride) {
+  double p = 1.0;
   int hit = -1;
   for (int t = 0; t < kp; ++t) {
     const double dx = s - pr.x[t];
-    if (dx == 0.0) hit = t;
-    l[t] = (dx == 0.0) ? 0.0 : pr.bw[t] / dx;
-    den += l[t];
+    if (fabs(dx) < 1e-100) hit = t;
+    l[t * stride] = p;  // prod_{m < t} (s - x_m)
+    p *= dx;
   }
+  for (int t = kp; t < KP; ++t) l[t * stride] = 0.0;
   if (hit >= 0) {
-    for (int t = 0; t < kp; ++t) l[t] = (t == hit) ? 1.0 : 0.0;
+    for (int t = 0; t < kp; ++t) l[t * stride] = (t == hit) ? 1.0 : 0.0;
     return;
   }
-  const double inv = 1.0 / den;
-  for (int t = 0; t < kp; ++t) l[t] *= inv;
+  double inv = 1.0 / p, den = 0.0;  // inv = 1 / prod_{m <= t} (s - x_m) going down
+  for (int t = kp - 1; t >= 0; --t) {
+    const double c = pr.bw[t] * (inv * l[t * stride]);
+    inv *= s - pr.x[t];
+    l[t * stride] = c;
+    den += c;
+  }
+  const double sc = 1.0 / den;
+  for (int t = 0; t < kp; ++t) l[t * stride] *= sc;
 }
 
-constexpr int kAnterpChunk = 32;
-
-__global__ void __launch_bounds__(256) point_anterp_kernel(int d, int kp, ProxyRule pr, const int64_t *__restrict__ box_rng,
-                                                           const double *__restrict__ s_local,
-                                                           const double *__restrict__ q_sorted, double *__restrict__ Q) {
-  extern __shared__ double sma[];
-  double *L = sma;                                    // [kAnterpChunk][d][kp]
-  double *qs = L + (size_t)kAnterpChunk * d * kp;      // [kAnterpChunk]
-  const int np = d == 3 ? kp * kp * kp : kp * kp;
-  const int64_t j0 = box_rng[2 * blockIdx.x], j1 = box_rng[2 * blockIdx.x + 1];
-  double *out = Q + (int64_t)blockIdx.x * np;
-  for (int e = threadIdx.x; e < np; e += blockDim.x) out[e] = 0.0;
-  for (int64_t c0 = j0; c0 < j1; c0 += kAnterpChunk) {
-    const int nc = (int)min((int64_t)kAnterpChunk, j1 - c0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < nc * d; e += blockDim.x) {
-      const int j = e / d, a = e - j * d;
-      lagrange_bary(pr, kp, s_local[(c0 + j) * d + a], L + ((size_t)j * d + a) * kp);
-    }
-    for (int j = threadIdx.x; j < nc; j += blockDim.x) qs[j] = q_sorted[c0 + j];
-    __syncthreads();
-    for (int e = threadIdx.x; e < np; e += blockDim.x) {
-      const int t1 = e % kp, t2 = (e / kp) % kp, t3 = d == 3 ? e / (kp * kp) : 0;
-      double acc = 0.0;
-      for (int j = 0; j < nc; ++j) {
-        const double *lj = L + (size_t)j * d * kp;
-        double v = qs[j] * lj[t1] * lj[kp + t2];
-        if (d == 3) v *= lj[2 * kp + t3];
-        acc += v;
-      }
-      out[e] += acc;
+// The same into registers (fully unrolled over the padded order KP).
+template <int KP>
+__device__ inline void lagrange_reg(const ProxyRule &pr, int kp, double s, double (&l)[KP]) {
+  double p = 1.0;
+  int hit = -1;
+#pragma unroll
+  for (int t = 0; t < KP; ++t) {
+    l[t] = 0.0;
+    if (t < kp) {
+      const double dx = s - pr.x[t];
+      if (fabs(dx) < 1e-100) hit = t;
+      l[t] = p;
+      p *= dx;
     }
   }
+  if (hit >= 0) {
+#pragma unroll
+    for (int t = 0; t < KP; ++t) l[t] = (t == hit) ? 1.0 : 0.0;
+    return;
+  }
+  double inv = 1.0 / p, den = 0.0;
+#pragma unroll
+  for (int t = KP - 1; t >= 0; --t)
+    if (t < kp) {
+      const double c = pr.bw[t] * (inv * l[t]);
+      inv *= s - pr.x[t];
+      l[t] = c;
+      den += c;
+    }
+  const double sc = 1.0 / den;
+#pragma unroll
+  for (int t = 0; t < KP; ++t) l[t] *= sc;
 }
 
-__global__ void __launch_bounds__(128) point_target_kernel(PointTargets pt, ProxyRule pr, double *__restrict__ u) {
-  const int d = pt.d, kp = pt.kp;
-  const int64_t b = blockIdx.x;
-  const int64_t i0 = pt.tbox_ptr[b], i1 = pt.tbox_ptr[b + 1];
+constexpr int kPointThreads = 128;
+constexpr int kLChunk = 32;  // points whose Lagrange rows are staged in shared memory at once
+
+// Anterpolation.  Grid: x = source segment (box seg[3s], sources [seg[3s+1], seg[3s+2])), y = block
+// of kPointThreads rows of the box's grid.  In 3D a thread owns the row (t_3, t_2) and keeps its k_p
+// values along t_1 in registers for the whole segment, so each source costs it one product
+// a = q_j l_{t_3} l_{t_2} and k_p FMAs against the shared l_{t_1} row; in 2D (k_p rows) the block's
+// threads form groups of k_p that take every G-th source.  The segment's sums are added into the
+// box's (cleared) grid atomically, so a crowded box spreads over many CTAs.
+template <int KP>
+__global__ void __launch_bounds__(kPointThreads) point_anterp_kernel(int d, int kp, ProxyRule pr,
+                                                                     const int64_t *__restrict__ seg,
+                                                                     const double *__restrict__ s_local,
+                                                                     const double *__restrict__ q_sorted,
+                                                                     double *__restrict__ Q) {
+  __shared__ double L[kLChunk][3][KP];
+  __shared__ double qs[kLChunk];
+  const int tid = threadIdx.x;
+  int r, g, G;
+  if (d == 3) {
+    r = blockIdx.y * kPointThreads + tid;
+    g = 0;
+    G = 1;
+  } else {
+    G = kPointThreads / kp;
+    g = tid / kp;
+    r = tid - g * kp;
+  }
+  const bool active = d == 3 ? r < kp * kp : g < G;
+  const int t2 = d == 3 ? r % kp : r, t3 = d == 3 ? r / kp : 0;
+  const int64_t box = seg[3 * blockIdx.x], j0 = seg[3 * blockIdx.x + 1], j1 = seg[3 * blockIdx.x + 2];
+  double acc[KP];
+#pragma unroll
+  for (int t = 0; t < KP; ++t) acc[t] = 0.0;
+  for (int64_t c0 = j0; c0 < j1; c0 += kLChunk) {
+    const int nc = (int)min((int64_t)kLChunk, j1 - c0);
+    __syncthreads();
+    for (int e = tid; e < nc * d; e += kPointThreads) {
+      const int j = e / d, a = e - j * d;
+      lagrange_row<KP>(pr, kp, s_local[(c0 + j) * d + a], &L[j][a][0], 1);
+    }
+    for (int j = tid; j < nc; j += kPointThreads) qs[j] = q_sorted[c0 + j];
+    __syncthreads();
+    if (!active) continue;
+    for (int j = g; j < nc; j += G) {
+      double a = qs[j] * L[j][1][t2];
+      if (d == 3) a *= L[j][2][t3];
+#pragma unroll
+      for (int t = 0; t < KP; ++t) acc[t] = fma(a, L[j][0][t], acc[t]);
+    }
+  }
+  if (!active) return;
+  const int rows = d == 3 ? kp * kp : kp;
+  double *o = Q + box * rows * kp + (int64_t)r * kp;
+#pragma unroll
+  for (int t = 0; t < KP; ++t)
+    if (t < kp) atomicAdd(o + t, acc[t]);
+}
+
+// Targets.  Grid: one CTA per target segment (box b, targets [i0, i1)), one target per thread.  The
+// box's incoming grid values are staged through shared memory in slabs of t_d (zero-padded to
+// KP x KP per slab; every thread reads the same entry at a time); l_{t_1} lives in registers, l_{t_2}
+// and l_{t_3} in shared memory.  The sparse colleagues' sources are then summed directly, and the
+// thread writes its target's value.
+constexpr size_t kTargetSlabBytes = 64 * 1024;
+
+template <int KP>
+__global__ void __launch_bounds__(kPointThreads) point_target_kernel(PointTargets pt, ProxyRule pr, int slab,
+                                                                     double *__restrict__ u) {
+  extern __shared__ double smt[];
+  double *Ls = smt;                                   // [2][KP][kPointThreads]: l_{t_2}, l_{t_3}
+  double *Us = smt + 2 * KP * kPointThreads;          // [slab][KP][KP]
+  const int d = pt.d, kp = pt.kp, tid = threadIdx.x;
+  const int64_t b = pt.tseg[3 * blockIdx.x], i0 = pt.tseg[3 * blockIdx.x + 1], i1 = pt.tseg[3 * blockIdx.x + 2];
   const int in = pt.tbox_in[b];
-  const int np = d == 3 ? kp * kp * kp : kp * kp;
-  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+  const int nq = d == 3 ? kp : 1;                     // slices along t_d
+  const int plane = d == 3 ? kp * kp : kp * kp;       // grid values per slice (t_2, t_1)
+  for (int64_t base = i0; base < i1; base += kPointThreads) {
+    const int64_t i = base + tid;
+    const bool live = i < i1;
     double acc = 0.0;
     if (in >= 0) {
-      double l[3][kMaxProxy];
-      for (int a = 0; a < d; ++a) lagrange_bary(pr, kp, pt.t_local[i * d + a], l[a]);
-      const double *Ub = pt.U + (int64_t)in * np;
-      if (d == 3) {
-        for (int t3 = 0; t3 < kp; ++t3) {
+      double l1[KP];
+#pragma unroll
+      for (int t = 0; t < KP; ++t) l1[t] = 0.0;
+      if (live) {
+        lagrange_reg<KP>(pr, kp, pt.t_local[i * d], l1);
+        lagrange_row<KP>(pr, kp, pt.t_local[i * d + 1], Ls + tid, kPointThreads);
+        if (d == 3) lagrange_row<KP>(pr, kp, pt.t_local[i * d + 2], Ls + KP * kPointThreads + tid, kPointThreads);
+      }
+      const double *Ub = pt.U + (int64_t)in * nq * plane;
+      for (int s0 = 0; s0 < nq; s0 += slab) {
+        const int ns = min(slab, nq - s0);
+        __syncthreads();
+        for (int e = tid; e < ns * KP * KP; e += kPointThreads) {
+          const int q = e / (KP * KP), rem = e - q * KP * KP, r2 = rem / KP, r1 = rem - r2 * KP;
+          Us[e] = (r2 < kp && r1 < kp) ? Ub[(int64_t)(s0 + q) * plane + r2 * kp + r1] : 0.0;
+        }
+        __syncthreads();
+        if (!live) continue;
+        for (int q = 0; q < ns; ++q) {
           double s2 = 0.0;
           for (int t2 = 0; t2 < kp; ++t2) {
-            const double *row = Ub + ((int64_t)t3 * kp + t2) * kp;
+            const double *row = Us + (q * KP + t2) * KP;
             double s1 = 0.0;
-            for (int t1 = 0; t1 < kp; ++t1) s1 = fma(l[0][t1], __ldg(row + t1), s1);
-            s2 = fma(l[1][t2], s1, s2);
+#pragma unroll
+            for (int t = 0; t < KP; ++t) s1 = fma(l1[t], row[t], s1);
+            s2 = fma(Ls[t2 * kPointThreads + tid], s1, s2);
           }
-          acc = fma(l[2][t3], s2, acc);
-        }
-      } else {
-        for (int t2 = 0; t2 < kp; ++t2) {
-          const double *row = Ub + (int64_t)t2 * kp;
-          double s1 = 0.0;
-          for (int t1 = 0; t1 < kp; ++t1) s1 = fma(l[0][t1], __ldg(row + t1), s1);
-          acc = fma(l[1][t2], s1, acc);
+          acc = d == 3 ? fma(Ls[(KP + s0 + q) * kPointThreads + tid], s2, acc) : acc + s2;
         }
       }
     }
+    if (!live) continue;
     double x[3] = {0.0, 0.0, 0.0};
     for (int a = 0; a < d; ++a) x[a] = pt.t_xyz[i * d + a];
     for (int64_t q = pt.dptr[b]; q < pt.dptr[b + 1]; ++q) {
@@ -2596,20 +2690,62 @@ __global__ void point_gather_q_kernel(int64_t n, const int64_t *__restrict__ id,
   if (j < n) qs[j] = q[id[j]];
 }
 
-cudaError_t point_anterp(int d, int kp, const ProxyRule &pr, int64_t n_dense, const int64_t *box_rng,
-                         const double *s_local, const double *q_sorted, double *Q, cudaStream_t st) {
-  if (n_dense <= 0) return cudaSuccess;
-  const size_t sm = sizeof(double) * ((size_t)kAnterpChunk * d * kp + kAnterpChunk);
-  cudaError_t e = cudaFuncSetAttribute(point_anterp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  point_anterp_kernel<<<(unsigned)n_dense, 256, sm, st>>>(d, kp, pr, box_rng, s_local, q_sorted, Q);
+namespace {
+
+template <int KP>
+cudaError_t point_anterp_launch(int d, int kp, const ProxyRule &pr, int64_t n_seg, const int64_t *seg,
+                                const double *s_local, const double *q_sorted, double *Q, cudaStream_t st) {
+  const unsigned ny = d == 3 ? (unsigned)((kp * kp + kPointThreads - 1) / kPointThreads) : 1u;
+  point_anterp_kernel<KP><<<dim3((unsigned)n_seg, ny), kPointThreads, 0, st>>>(d, kp, pr, seg, s_local, q_sorted, Q);
   return cudaGetLastError();
 }
 
-cudaError_t point_targets(const PointTargets &pt, const ProxyRule &pr, double *u, cudaStream_t st) {
-  if (pt.n_tbox <= 0) return cudaSuccess;
-  point_target_kernel<<<(unsigned)pt.n_tbox, 128, 0, st>>>(pt, pr, u);
+template <int KP>
+cudaError_t point_target_launch(const PointTargets &pt, const ProxyRule &pr, double *u, cudaStream_t st) {
+  const size_t slice = sizeof(double) * KP * KP;
+  const int nq = pt.d == 3 ? pt.kp : 1;
+  const int slab = (int)std::max<size_t>(1, std::min<size_t>((size_t)nq, kTargetSlabBytes / slice));
+  const size_t sm = sizeof(double) * 2 * KP * kPointThreads + slice * slab;
+  cudaError_t e = cudaFuncSetAttribute(point_target_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  point_target_kernel<KP><<<(unsigned)pt.n_tseg, kPointThreads, sm, st>>>(pt, pr, slab, u);
   return cudaGetLastError();
+}
+
+// k_p rounded up to an even padded order
+#define FGT_KP_SWITCH(kp, CALL)                                                           \
+  switch (((kp) + 1) & ~1) {                                                              \
+    case 4: return CALL(4); case 6: return CALL(6); case 8: return CALL(8);               \
+    case 10: return CALL(10); case 12: return CALL(12); case 14: return CALL(14);         \
+    case 16: return CALL(16); case 18: return CALL(18); case 20: return CALL(20);         \
+    case 22: return CALL(22); case 24: return CALL(24); case 26: return CALL(26);         \
+    case 28: return CALL(28); case 30: return CALL(30); case 32: return CALL(32);         \
+    case 34: return CALL(34); case 36: return CALL(36); case 38: return CALL(38);         \
+    case 40: return CALL(40);                                                             \
+    default: return cudaErrorInvalidValue;                                                \
+  }
+static_assert(kMaxProxy == 40, "padded proxy orders cover 4..40");
+
+}  // namespace
+
+cudaError_t point_anterp(int d, int kp, const ProxyRule &pr, int64_t n_dense, int64_t n_seg, const int64_t *seg,
+                         const double *s_local, const double *q_sorted, double *Q, cudaStream_t st) {
+  if (n_dense <= 0) return cudaSuccess;
+  if (kp < 1 || kp > kMaxProxy) return cudaErrorInvalidValue;
+  const size_t np = d == 3 ? (size_t)kp * kp * kp : (size_t)kp * kp;
+  cudaError_t e = cudaMemsetAsync(Q, 0, sizeof(double) * np * n_dense, st);
+  if (e != cudaSuccess || n_seg <= 0) return e;
+#define FGT_ANTERP(K) point_anterp_launch<K>(d, kp, pr, n_seg, seg, s_local, q_sorted, Q, st)
+  FGT_KP_SWITCH(kp, FGT_ANTERP)
+#undef FGT_ANTERP
+}
+
+cudaError_t point_targets(const PointTargets &pt, const ProxyRule &pr, double *u, cudaStream_t st) {
+  if (pt.n_tseg <= 0) return cudaSuccess;
+  if (pt.kp < 1 || pt.kp > kMaxProxy) return cudaErrorInvalidValue;
+#define FGT_TARGETS(K) point_target_launch<K>(pt, pr, u, st)
+  FGT_KP_SWITCH(pt.kp, FGT_TARGETS)
+#undef FGT_TARGETS
 }
 
 cudaError_t point_gather_q(int64_t n, const int64_t *s_id, const double *q, double *q_sorted, cudaStream_t st) {

@@ -2128,7 +2128,8 @@ struct fgt_point_plan {
   fgt::PointTargets pt;
   void *dev = nullptr;     // lists, tables, sorted points
   void *work = nullptr;    // phi, psi, Q, U, q_sorted
-  const int64_t *dense_rng = nullptr, *s_id = nullptr;
+  const int64_t *aseg = nullptr, *s_id = nullptr;
+  int64_t n_aseg = 0;
   const double *s_local = nullptr;
   double *Q = nullptr, *U = nullptr, *q_sorted = nullptr;
   ~fgt_point_plan() {
@@ -2284,13 +2285,17 @@ fgt_status fgt_point_plan_create(int d, double delta, double tol, int64_t n_src,
     }
   // dense boxes (outgoing slots): their sources are the runs [sptr[b], sptr[b+1]) of the box order
   std::vector<int32_t> dense_slot(nbox, -1);
-  std::vector<int64_t> dense_rng;
+  std::vector<int64_t> aseg;  // (dense slot, first, end) segments of at most kPointSeg sources
   for (int64_t b = 0; b < nbox; ++b)
     if (sptr[b + 1] - sptr[b] > n_s) {
       dense_slot[b] = (int32_t)P->n_dense++;
-      dense_rng.push_back(sptr[b]);
-      dense_rng.push_back(sptr[b + 1]);
+      for (int64_t j = sptr[b]; j < sptr[b + 1]; j += fgt::kPointSeg) {
+        aseg.push_back(dense_slot[b]);
+        aseg.push_back(j);
+        aseg.push_back(std::min(j + fgt::kPointSeg, sptr[b + 1]));
+      }
     }
+  P->n_aseg = (int64_t)aseg.size() / 3;
   // neighbour lists: incoming boxes (targets with a dense colleague), gather sources by code,
   // direct source boxes (sparse colleagues with sources)
   int noff = 1;
@@ -2330,13 +2335,18 @@ fgt_status fgt_point_plan_create(int d, double delta, double tol, int64_t n_src,
     }
   }
   P->n_direct = (int64_t)dbox.size();
-  // target boxes (those with targets), in box order
-  std::vector<int64_t> tb_ptr(1, 0);
+  // target boxes (those with targets), in box order, and their segments of <= kPointSeg targets
   std::vector<int32_t> tb_in;
+  std::vector<int64_t> tseg;
   for (int64_t b = 0; b < nbox; ++b)
     if (tptr[b + 1] > tptr[b]) {
-      tb_ptr.push_back(tptr[b + 1]);
+      const int64_t tb = (int64_t)tb_in.size();
       tb_in.push_back(in_row[b]);
+      for (int64_t i = tptr[b]; i < tptr[b + 1]; i += fgt::kPointSeg) {
+        tseg.push_back(tb);
+        tseg.push_back(i);
+        tseg.push_back(std::min(i + fgt::kPointSeg, tptr[b + 1]));
+      }
     }
   // plane-wave matrices of a box about its own centre: form F[a][t] = w_a exp(-i kappa m_a
   // (Lc/2) eta_t) (last axis m >= 0, factor 2 for m > 0), evaluation E[t][a] = exp(+i ...)
@@ -2387,8 +2397,8 @@ fgt_status fgt_point_plan_create(int d, double delta, double tol, int64_t n_src,
   const size_t o_Ff = pk.add(Ff), o_Fh = pk.add(Fh), o_Ef = pk.add(Ef), o_Eh = pk.add(Eh), o_Pf = pk.add(Pf),
                o_Ph = pk.add(Ph);
   const size_t o_gdst = pk.add(gdst), o_gptr = pk.add(gptr), o_gsrc = pk.add(gsrc);
-  const size_t o_drng = pk.add(dense_rng), o_sloc = pk.add(s_loc);
-  const size_t o_tbp = pk.add(tb_ptr), o_txyz = pk.add(t_xyz), o_tloc = pk.add(t_loc), o_tid = pk.add(t_id),
+  const size_t o_aseg = pk.add(aseg), o_sloc = pk.add(s_loc);
+  const size_t o_tseg = pk.add(tseg), o_txyz = pk.add(t_xyz), o_tloc = pk.add(t_loc), o_tid = pk.add(t_id),
                o_tbin = pk.add(tb_in), o_dp = pk.add(dptr), o_db = pk.add(dbox), o_sp = pk.add(sptr),
                o_sxyz = pk.add(s_xyz), o_sid = pk.add(s_id);
   cudaError_t e = cudaMalloc(&P->dev, std::max<size_t>(pk.buf.size(), 256));
@@ -2410,7 +2420,7 @@ fgt_status fgt_point_plan_create(int d, double delta, double tol, int64_t n_src,
   P->Q = (double *)wk(w_q);
   P->U = (double *)wk(w_u);
   P->q_sorted = (double *)wk(w_qs);
-  P->dense_rng = (const int64_t *)at(o_drng);
+  P->aseg = (const int64_t *)at(o_aseg);
   P->s_local = (const double *)at(o_sloc);
   P->s_id = (const int64_t *)at(o_sid);
   fgt::ExecDesc &x = P->ex;
@@ -2438,8 +2448,8 @@ fgt_status fgt_point_plan_create(int d, double delta, double tol, int64_t n_src,
   x.n_points = P->n_in * np;
   fgt::PointTargets &t = P->pt;
   t.d = d; t.kp = kp; t.delta = delta;
-  t.n_tbox = (int64_t)tb_in.size();
-  t.tbox_ptr = (const int64_t *)at(o_tbp);
+  t.n_tseg = (int64_t)tseg.size() / 3;
+  t.tseg = (const int64_t *)at(o_tseg);
   t.t_xyz = (const double *)at(o_txyz);
   t.t_local = (const double *)at(o_tloc);
   t.t_id = (const int64_t *)at(o_tid);
@@ -2458,8 +2468,8 @@ fgt_status fgt_point_execute(fgt_point_plan *P, const double *q_dev, double *u_d
   if (!P || (P->n_src > 0 && !q_dev) || (P->n_tgt > 0 && !u_dev)) return fail(FGT_ERR_ARG, "NULL argument");
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = fgt::point_gather_q(P->n_src, P->s_id, q_dev, P->q_sorted, st);
-  if (e == cudaSuccess) e = fgt::point_anterp(P->d, P->kp, P->pr, P->n_dense, P->dense_rng, P->s_local, P->q_sorted,
-                                              P->Q, st);
+  if (e == cudaSuccess) e = fgt::point_anterp(P->d, P->kp, P->pr, P->n_dense, P->n_aseg, P->aseg, P->s_local,
+                                              P->q_sorted, P->Q, st);
   if (e == cudaSuccess && P->n_dense > 0 && P->n_in > 0) e = fgt::run_transform(P->ex, P->Q, P->U, st);
   if (e == cudaSuccess) e = fgt::point_targets(P->pt, P->pr, u_dev, st);
   return e == cudaSuccess ? FGT_OK : cuda_fail(e, "point transform");
