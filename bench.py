@@ -371,7 +371,8 @@ def run_refinement(F, torch):
 def run_point_fgt(F, torch):
     """The discrete Gauss transform (Algorithm 2 with proxy grids): 1M sources and 1M targets
     (the same points) clustered around 8 centres in 3D and uniform in 2D, delta = 1e-3 (3D) /
-    1e-4 (2D), tol 1e-6 and 1e-10, n_s = 64; points/s = (sources + targets) / time."""
+    1e-4 (2D); FP64 at tol 1e-6 and 1e-10, split at tol 1e-6; n_s = 64; points/s = (sources +
+    targets) / time."""
     rng = np.random.default_rng(17)
     out = {}
     c = rng.uniform(-0.4, 0.4, size=(8, 3))
@@ -383,9 +384,10 @@ def run_point_fgt(F, torch):
         q = torch.from_numpy(rng.uniform(0.5, 1.5, len(pts))).cuda()
         u = torch.empty_like(q)
         row = {"points": len(pts), "delta": delta}
-        for tol in (1e-6, 1e-10):
+        for tol, prec, key in ((1e-6, F.PREC_FP64, "tol1e-06"), (1e-6, F.PREC_SPLIT, "split_tol1e-06"),
+                               (1e-10, F.PREC_FP64, "tol1e-10")):
             t0 = time.perf_counter()
-            plan = F.PointPlan(d, delta, tol, pts, pts, n_s=64)
+            plan = F.PointPlan(d, delta, tol, pts, pts, n_s=64, prec=prec)
             t_plan = time.perf_counter() - t0
             st = torch.cuda.current_stream()
             for _ in range(2):
@@ -397,7 +399,7 @@ def run_point_fgt(F, torch):
             e1.record(st)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / 5
-            row[f"tol{tol:g}"] = dict(plan.info(), ms=ms, plan_s=t_plan, points_per_s=2 * len(pts) / ms * 1e3)
+            row[key] = dict(plan.info(), ms=ms, plan_s=t_plan, points_per_s=2 * len(pts) / ms * 1e3)
             plan.close()
         out[name] = row
     return out
@@ -463,9 +465,17 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the delta sweep and the periodic workload")
     ap.add_argument("--forms", default="split,fp64,fp64_1e-10,fp64tc,fp64tc_1e-10",
                     help="comma list of " + ", ".join(FORMS) + "; the first one is the headline")
+    ap.add_argument("--point-fgt-only", action="store_true",
+                    help="run only the point-FGT section and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.point_fgt_only:
+        import torch
+
+        import paper_2305_07165_gb300 as F
+        print(json.dumps({"point_fgt": run_point_fgt(F, torch)}))
+        return 0
 
     import torch
     import torch.distributed as dist

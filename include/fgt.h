@@ -259,15 +259,20 @@ void fgt_built_tree_destroy(fgt_built_tree *t);
  * evaluated on the colleagues' proxy grids and interpolated to their targets; sources of sparse
  * boxes act on their colleagues' targets directly.  k_p is the smallest grid that reproduces every
  * plane wave of the expansion on a box to 0.1 tol relative to the mode's weight (FGT_ERR_ARG above
- * 40 nodes; about 21 at tol 1e-6 and 33 at 1e-10).  FP64. */
+ * 40 nodes; about 21 at tol 1e-6 and 33 at 1e-10).
+ * prec (fgt_prec): FGT_PREC_FP64 computes everything in FP64.  FGT_PREC_SPLIT (tol >= 1e-7 only)
+ * computes the Lagrange weights, the anterpolation and the interpolation in FP32 (sums of at most
+ * 32 terms in plain FP32, longer ones compensated) and the plane-wave expansions in FP32; the proxy
+ * values Q and U, the direct pairs and the result stay FP64.  Other values: FGT_ERR_ARG. */
 typedef struct fgt_point_plan fgt_point_plan;
 typedef struct {
   int32_t cutoff_level, proxy_order, modes_1d;
   int64_t n_boxes, n_dense_boxes, n_incoming_boxes, n_direct_pairs;
   double cutoff_length;
+  int32_t prec;
 } fgt_point_info;
 fgt_status fgt_point_plan_create(int d, double delta, double tol, int64_t n_src, const double *src, int64_t n_tgt,
-                                 const double *tgt, int n_s, fgt_point_plan **out);
+                                 const double *tgt, int n_s, int prec, fgt_point_plan **out);
 fgt_status fgt_point_execute(fgt_point_plan *plan, const double *q_dev, double *u_dev, void *stream);
 fgt_status fgt_point_plan_get_info(const fgt_point_plan *plan, fgt_point_info *info);
 void fgt_point_destroy(fgt_point_plan *plan);

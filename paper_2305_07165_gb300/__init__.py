@@ -55,7 +55,7 @@ class PointInfo(ctypes.Structure):
     """fgt_point_info."""
     _fields_ = [(n, ctypes.c_int32) for n in ("cutoff_level", "proxy_order", "modes_1d")] + \
                [(n, ctypes.c_int64) for n in ("n_boxes", "n_dense_boxes", "n_incoming_boxes", "n_direct_pairs")] + \
-               [("cutoff_length", ctypes.c_double)]
+               [("cutoff_length", ctypes.c_double), ("prec", ctypes.c_int32)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -114,7 +114,7 @@ def lib():
             L.fgt_built_tree_get.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                              ctypes.POINTER(vp)]
             L.fgt_built_tree_copy_sigma.argtypes = [vp, vp, vp]
-            L.fgt_point_plan_create.argtypes = [i32, dbl, dbl, i64, vp, i64, vp, i32, ctypes.POINTER(vp)]
+            L.fgt_point_plan_create.argtypes = [i32, dbl, dbl, i64, vp, i64, vp, i32, i32, ctypes.POINTER(vp)]
             L.fgt_point_execute.argtypes = [vp, vp, vp, vp]
             L.fgt_point_plan_get_info.argtypes = [vp, ctypes.POINTER(PointInfo)]
             L.fgt_point_destroy.argtypes = [vp]
@@ -474,9 +474,11 @@ def build_gaussian_tree(d, k, centers, alphas, amps=None, periodic=False, eps=1e
 class PointPlan:
     """The discrete Gauss transform u_i = sum_j exp(-|x_i - y_j|^2/delta) q_j in free space
     (fgt_point_plan_create / fgt_point_execute): sources and targets fixed at creation (host
-    arrays [n, d]), weights and results as CUDA float64 tensors in the callers' point orders."""
+    arrays [n, d]), weights and results as CUDA float64 tensors in the callers' point orders.
+    prec: PREC_FP64, or PREC_SPLIT (tol >= 1e-7) for FP32 Lagrange weights, anterpolation,
+    interpolation and expansions around FP64 proxy values, direct pairs and results."""
 
-    def __init__(self, d, delta, tol, src, tgt, n_s=64):
+    def __init__(self, d, delta, tol, src, tgt, n_s=64, prec=PREC_FP64):
         import torch
         if not torch.cuda.is_available():
             raise FGTError(4, "no CUDA device: the point FGT runs only on the GPU")
@@ -486,7 +488,7 @@ class PointPlan:
         self.d, self.n_src, self.n_tgt = d, len(y), len(x)
         self._h = ctypes.c_void_p()
         _check(lib().fgt_point_plan_create(d, float(delta), float(tol), len(y), y.ctypes.data, len(x), x.ctypes.data,
-                                           int(n_s), ctypes.byref(self._h)))
+                                           int(n_s), int(prec), ctypes.byref(self._h)))
 
     def info(self) -> dict:
         i = PointInfo()

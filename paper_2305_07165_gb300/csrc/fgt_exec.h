@@ -133,20 +133,24 @@ cudaError_t merge_children(int d, int k, int64_t n_parents, const int64_t *child
 
 // ---- discrete (point) Gauss transform with proxy grids (Algorithm 2)
 constexpr int kMaxProxy = 40;
+constexpr int kMaxProxy32 = 30;  // largest k_p of the FP32 (split) point kernels
 struct ProxyRule {
   double x[kMaxProxy];   // Gauss-Legendre nodes on [-1, 1]
   double bw[kMaxProxy];  // barycentric weights of the Lagrange basis on them
+  float xf[kMaxProxy];   // the nodes rounded to FP32
+  float bwf[kMaxProxy];  // the weights over their largest magnitude, rounded to FP32
 };
 // Points per CTA of the point-FGT kernels (segments of a box's sources or targets).
 constexpr int64_t kPointSeg = 1024;
 // Q[b][t] = sum_{j in dense box b} q_j prod_a l_{t_a}(s_{j,a}) (sources sorted by box, local
-// coordinates s in [-1, 1]^d); one CTA per segment seg[3s..3s+2] = (box, first, end).
-cudaError_t point_anterp(int d, int kp, const ProxyRule &pr, int64_t n_dense, int64_t n_seg, const int64_t *seg,
+// coordinates s in [-1, 1]^d); segments seg[3s..3s+2] = (box, first, end).  f32: the FP32 kernel.
+cudaError_t point_anterp(int d, int kp, bool f32, const ProxyRule &pr, int64_t n_dense, int64_t n_seg,
+                         const int64_t *seg,
                          const double *s_local, const double *q_sorted, double *Q, cudaStream_t st);
 // u[id_i] = (incoming boxes) sum_t prod_a l_{t_a}(s_{i,a}) U[in(box)][t] + sum over the box's direct
 // source boxes of exp(-|x_i - y_j|^2 / delta) q_j; one CTA per target box.
 struct PointTargets {
-  int d = 0, kp = 0;
+  int d = 0, kp = 0, f32 = 0;          // f32: interpolation in FP32 (direct pairs stay FP64)
   double delta = 0;
   int64_t n_tseg = 0;
   const int64_t *tseg = nullptr;       // segments (target box, first, end) of at most kPointSeg targets
@@ -160,10 +164,18 @@ struct PointTargets {
   const int64_t *sptr = nullptr;       // CSR over boxes into the sorted sources
   const double *s_xyz = nullptr;       // sorted sources [n][d]
   const double *q_sorted = nullptr;    // weights of the sorted sources
+  double inv_delta = 0;                // 1 / delta
+  // FP32 direct pairs (split precision): differences from local coordinates,
+  // x - y = (Lc/2) (t_local - s_local - 2 o) for a source box at offset o (in boxes) from the target's
+  const int32_t *dcode = nullptr;      // per dbox entry: sum_a (o_a + 1) 3^a
+  const float *s_local32 = nullptr;    // sorted sources' local coordinates [n][d], FP32
+  const float *q32 = nullptr;          // weights of the sorted sources, FP32
+  float dcoef = 0;                     // (Lc/2)^2 / delta
 };
 cudaError_t point_targets(const PointTargets &pt, const ProxyRule &pr, double *u, cudaStream_t st);
-// q permuted into the sources' box order: q_sorted[j] = q[s_id[j]]
-cudaError_t point_gather_q(int64_t n, const int64_t *s_id, const double *q, double *q_sorted, cudaStream_t st);
+// q permuted into the sources' box order: q_sorted[j] = q[s_id[j]] (and its FP32 copy when q32 != NULL)
+cudaError_t point_gather_q(int64_t n, const int64_t *s_id, const double *q, double *q_sorted, float *q32,
+                           cudaStream_t st);
 
 // Shared-memory bytes of the grouped form kernel (G blocks of K nodes per axis; r, c: real and
 // complex element sizes) and of the whole-block evaluation kernel.

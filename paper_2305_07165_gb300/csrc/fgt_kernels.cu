@@ -2677,17 +2677,261 @@ __global__ void __launch_bounds__(kPointThreads) point_target_kernel(PointTarget
           const double dx = x[a] - __ldg(pt.s_xyz + j * d + a);
           r2 = fma(dx, dx, r2);
         }
-        acc = fma(exp(-r2 / pt.delta), __ldg(pt.q_sorted + j), acc);
+        acc = fma(exp(-r2 * pt.inv_delta), __ldg(pt.q_sorted + j), acc);
       }
     }
     u[pt.t_id[i]] = acc;
   }
 }
 
+// ---- FP32 variants (split precision, tol >= 1e-7)
+
+// l_t(s) in FP32 from the normalised barycentric weights: c_t = w_t / (s - x_t) (IEEE reciprocal),
+// l_t = c_t / sum_m c_m.  A point within 1e-30 of a node takes that node's unit vector.
+template <int KP>
+__device__ inline void lagrange_row32(const ProxyRule &pr, int kp, float s, float *l, int stride) {
+  float den = 0.f;
+  int hit = -1;
+  for (int t = 0; t < kp; ++t) {
+    const float dx = s - pr.xf[t];
+    float c = 0.f;
+    if (fabsf(dx) < 1e-30f) hit = t;
+    else c = pr.bwf[t] * __frcp_rn(dx);
+    l[t * stride] = c;
+    den += c;
+  }
+  for (int t = kp; t < KP; ++t) l[t * stride] = 0.f;
+  if (hit >= 0) {
+    for (int t = 0; t < kp; ++t) l[t * stride] = (t == hit) ? 1.f : 0.f;
+    return;
+  }
+  const float sc = __frcp_rn(den);
+  for (int t = 0; t < kp; ++t) l[t * stride] *= sc;
+}
+
+template <int KP>
+__device__ inline void lagrange_reg32(const ProxyRule &pr, int kp, float s, float (&l)[KP]) {
+  float den = 0.f;
+  int hit = -1;
+#pragma unroll
+  for (int t = 0; t < KP; ++t) {
+    l[t] = 0.f;
+    if (t < kp) {
+      const float dx = s - pr.xf[t];
+      if (fabsf(dx) < 1e-30f) hit = t;
+      else l[t] = pr.bwf[t] * __frcp_rn(dx);
+      den += l[t];
+    }
+  }
+  if (hit >= 0) {
+#pragma unroll
+    for (int t = 0; t < KP; ++t) l[t] = (t == hit) ? 1.f : 0.f;
+    return;
+  }
+  const float sc = __frcp_rn(den);
+#pragma unroll
+  for (int t = 0; t < KP; ++t) l[t] *= sc;
+}
+
+constexpr int kLChunk32 = 64;  // sources per staged chunk of the FP32 anterpolation
+
+// s + x with the running compensation c (Kahan).
+__device__ inline void kahan_add(float &s, float &c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// FP32 anterpolation.  Threads form G groups of TG; a thread owns two rows of the block's RB grid rows
+// (ra = rt and ra + TG), so every l_{t_1} pair read from shared memory feeds four FMAs.  A group
+// takes every G-th source of a chunk (G = 1 in 3D).  Chunk sums (at most 64 terms) are plain FP32
+// and are added into the segment's sums with compensation; the segment's sums go into the box's
+// FP64 grid atomically.
+template <int KP>
+__global__ void __launch_bounds__(256) point_anterp32_kernel(int d, int kp, int RB, int TG, int G, ProxyRule pr,
+                                                             const int64_t *__restrict__ seg,
+                                                             const double *__restrict__ s_local,
+                                                             const double *__restrict__ q_sorted,
+                                                             double *__restrict__ Q) {
+  static_assert(KP % 2 == 0, "rows are read as float2");
+  __shared__ __align__(16) float L[kLChunk32][3][KP];
+  __shared__ float qs[kLChunk32];
+  const int tid = threadIdx.x, g = tid / TG, rt = tid - g * TG;
+  const int rows = d == 3 ? kp * kp : kp;
+  const int ra = blockIdx.y * RB + rt, rb = ra + TG;
+  const bool act = g < G && rt < RB && ra < rows;
+  const bool actb = act && rt + TG < RB && rb < rows;
+  const int rbb = actb ? rb : ra;
+  const int a2 = ra % kp, a3 = d == 3 ? ra / kp : 0, b2 = rbb % kp, b3 = d == 3 ? rbb / kp : 0;
+  const int64_t box = seg[3 * blockIdx.x], j0 = seg[3 * blockIdx.x + 1], j1 = seg[3 * blockIdx.x + 2];
+  float acc_a[KP], acc_b[KP], sa[KP], ca[KP], sb[KP], cb[KP];
+#pragma unroll
+  for (int t = 0; t < KP; ++t) acc_a[t] = acc_b[t] = sa[t] = ca[t] = sb[t] = cb[t] = 0.f;
+  for (int64_t c0 = j0; c0 < j1; c0 += kLChunk32) {
+    const int nc = (int)min((int64_t)kLChunk32, j1 - c0);
+    __syncthreads();
+    for (int e = tid; e < nc * d; e += blockDim.x) {
+      const int j = e / d, a = e - j * d;
+      lagrange_row32<KP>(pr, kp, (float)s_local[(c0 + j) * d + a], &L[j][a][0], 1);
+    }
+    for (int j = tid; j < nc; j += blockDim.x) qs[j] = (float)q_sorted[c0 + j];
+    __syncthreads();
+    if (!act) continue;
+    for (int j = g; j < nc; j += G) {
+      float pa = qs[j] * L[j][1][a2], pb = qs[j] * L[j][1][b2];
+      if (d == 3) {
+        pa *= L[j][2][a3];
+        pb *= L[j][2][b3];
+      }
+      const float2 *l1 = reinterpret_cast<const float2 *>(&L[j][0][0]);
+#pragma unroll
+      for (int t = 0; t < KP / 2; ++t) {
+        const float2 v = l1[t];
+        acc_a[2 * t] = fmaf(pa, v.x, acc_a[2 * t]);
+        acc_a[2 * t + 1] = fmaf(pa, v.y, acc_a[2 * t + 1]);
+        acc_b[2 * t] = fmaf(pb, v.x, acc_b[2 * t]);
+        acc_b[2 * t + 1] = fmaf(pb, v.y, acc_b[2 * t + 1]);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < KP; ++t) {
+      kahan_add(sa[t], ca[t], acc_a[t]);
+      kahan_add(sb[t], cb[t], acc_b[t]);
+      acc_a[t] = acc_b[t] = 0.f;
+    }
+  }
+  if (!act) return;
+  double *oa = Q + box * rows * kp + (int64_t)ra * kp;
+#pragma unroll
+  for (int t = 0; t < KP; ++t)
+    if (t < kp) atomicAdd(oa + t, (double)sa[t] - (double)ca[t]);
+  if (!actb) return;
+  double *ob = Q + box * rows * kp + (int64_t)rb * kp;
+#pragma unroll
+  for (int t = 0; t < KP; ++t)
+    if (t < kp) atomicAdd(ob + t, (double)sb[t] - (double)cb[t]);
+}
+
+// FP32 interpolation to the targets: two targets per thread (base + tid and base + 128 + tid), so
+// every grid pair read from shared memory feeds four FMAs.  The box's grid is converted to FP32 in
+// shared memory (all of it when it fits, else in slabs of t_d); l_{t_1} of both targets in
+// registers, l_{t_2} and l_{t_3} in shared memory.  Sums along t_1 and t_2 are plain FP32 (at most
+// 40 terms), the sum along t_3 is compensated.  The direct pairs are summed in FP32 from the local
+// coordinates of the target and the source in their boxes (compensated).
+template <int KP>
+__global__ void __launch_bounds__(kPointThreads) point_target32_kernel(PointTargets pt, ProxyRule pr, int slab,
+                                                                       double *__restrict__ u) {
+  static_assert(KP % 2 == 0, "rows are read as float2");
+  constexpr int NT = 2 * kPointThreads;             // targets per pass
+  extern __shared__ float4 smf4[];
+  float *Ls = reinterpret_cast<float *>(smf4);       // [2][KP][NT]: l_{t_2}, l_{t_3}
+  float *Us = Ls + 2 * KP * NT;                      // [slab][KP][KP]
+  const int d = pt.d, kp = pt.kp, tid = threadIdx.x;
+  const int64_t b = pt.tseg[3 * blockIdx.x], i0 = pt.tseg[3 * blockIdx.x + 1], i1 = pt.tseg[3 * blockIdx.x + 2];
+  const int in = pt.tbox_in[b];
+  const int nq = d == 3 ? kp : 1, plane = kp * kp;
+  const bool whole = slab >= nq;
+  const double *Ub = in >= 0 ? pt.U + (int64_t)in * nq * plane : nullptr;
+  auto stage = [&](int s0, int ns) {
+    for (int e = tid; e < ns * KP * KP; e += kPointThreads) {
+      const int q = e / (KP * KP), rem = e - q * KP * KP, r2 = rem / KP, r1 = rem - r2 * KP;
+      Us[e] = (r2 < kp && r1 < kp) ? (float)Ub[(int64_t)(s0 + q) * plane + r2 * kp + r1] : 0.f;
+    }
+  };
+  if (in >= 0 && whole) stage(0, nq);
+  for (int64_t base = i0; base < i1; base += NT) {
+    const int64_t ia = base + tid, ib = base + kPointThreads + tid;
+    const bool la = ia < i1, lb = ib < i1;
+    float sa = 0.f, ca = 0.f, sb = 0.f, cb = 0.f;
+    if (in >= 0) {
+      float l1a[KP], l1b[KP];
+#pragma unroll
+      for (int t = 0; t < KP; ++t) l1a[t] = l1b[t] = 0.f;
+      __syncthreads();  // the previous pass is done with Ls
+      if (la) {
+        lagrange_reg32<KP>(pr, kp, (float)pt.t_local[ia * d], l1a);
+        lagrange_row32<KP>(pr, kp, (float)pt.t_local[ia * d + 1], Ls + tid, NT);
+        if (d == 3) lagrange_row32<KP>(pr, kp, (float)pt.t_local[ia * d + 2], Ls + KP * NT + tid, NT);
+      }
+      if (lb) {
+        lagrange_reg32<KP>(pr, kp, (float)pt.t_local[ib * d], l1b);
+        lagrange_row32<KP>(pr, kp, (float)pt.t_local[ib * d + 1], Ls + kPointThreads + tid, NT);
+        if (d == 3) lagrange_row32<KP>(pr, kp, (float)pt.t_local[ib * d + 2], Ls + KP * NT + kPointThreads + tid, NT);
+      }
+      for (int s0 = 0; s0 < nq; s0 += slab) {
+        const int ns = min(slab, nq - s0);
+        if (!whole) {
+          __syncthreads();
+          stage(s0, ns);
+        }
+        __syncthreads();
+        if (!(la || lb)) continue;
+        for (int q = 0; q < ns; ++q) {
+          float s2a = 0.f, s2b = 0.f;
+          for (int t2 = 0; t2 < kp; ++t2) {
+            const float2 *row = reinterpret_cast<const float2 *>(Us + (q * KP + t2) * KP);
+            float s1a = 0.f, s1b = 0.f, s1c = 0.f, s1d = 0.f;  // even / odd t_1 of both targets
+#pragma unroll
+            for (int t = 0; t < KP / 2; ++t) {
+              const float2 v = row[t];
+              s1a = fmaf(l1a[2 * t], v.x, s1a);
+              s1b = fmaf(l1b[2 * t], v.x, s1b);
+              s1c = fmaf(l1a[2 * t + 1], v.y, s1c);
+              s1d = fmaf(l1b[2 * t + 1], v.y, s1d);
+            }
+            s2a = fmaf(Ls[t2 * NT + tid], s1a + s1c, s2a);
+            s2b = fmaf(Ls[t2 * NT + kPointThreads + tid], s1b + s1d, s2b);
+          }
+          if (d == 3) {
+            const int t3 = s0 + q;
+            s2a *= Ls[(KP + t3) * NT + tid];
+            s2b *= Ls[(KP + t3) * NT + kPointThreads + tid];
+          }
+          kahan_add(sa, ca, s2a);
+          kahan_add(sb, cb, s2b);
+        }
+      }
+    }
+    // direct pairs in FP32 from local coordinates (compensated sum), both targets together
+    float ta[3] = {0.f, 0.f, 0.f}, tb[3] = {0.f, 0.f, 0.f};
+    for (int a = 0; a < d; ++a) {
+      if (la) ta[a] = (float)pt.t_local[ia * d + a];
+      if (lb) tb[a] = (float)pt.t_local[ib * d + a];
+    }
+    float da = 0.f, dca = 0.f, db = 0.f, dcb = 0.f;
+    for (int64_t q = pt.dptr[b]; q < pt.dptr[b + 1]; ++q) {
+      const int32_t sbx = pt.dbox[q];
+      float ba[3] = {0.f, 0.f, 0.f}, bb[3] = {0.f, 0.f, 0.f};
+      for (int a = 0, c = pt.dcode[q]; a < d; ++a, c /= 3) {
+        const float o2 = 2.f * (float)(c % 3 - 1);
+        ba[a] = ta[a] - o2;
+        bb[a] = tb[a] - o2;
+      }
+      for (int64_t j = pt.sptr[sbx]; j < pt.sptr[sbx + 1]; ++j) {
+        float ra = 0.f, rb = 0.f;
+        for (int a = 0; a < d; ++a) {
+          const float y = __ldg(pt.s_local32 + j * d + a);
+          ra = fmaf(ba[a] - y, ba[a] - y, ra);
+          rb = fmaf(bb[a] - y, bb[a] - y, rb);
+        }
+        const float qj = __ldg(pt.q32 + j);
+        kahan_add(da, dca, qj * expf(-pt.dcoef * ra));
+        kahan_add(db, dcb, qj * expf(-pt.dcoef * rb));
+      }
+    }
+    if (la) u[pt.t_id[ia]] = ((double)sa - (double)ca) + ((double)da - (double)dca);
+    if (lb) u[pt.t_id[ib]] = ((double)sb - (double)cb) + ((double)db - (double)dcb);
+  }
+}
+
 __global__ void point_gather_q_kernel(int64_t n, const int64_t *__restrict__ id, const double *__restrict__ q,
-                                      double *__restrict__ qs) {
+                                      double *__restrict__ qs, float *__restrict__ q32) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < n) qs[j] = q[id[j]];
+  if (j >= n) return;
+  const double v = q[id[j]];
+  qs[j] = v;
+  if (q32) q32[j] = (float)v;
 }
 
 namespace {
@@ -2697,6 +2941,43 @@ cudaError_t point_anterp_launch(int d, int kp, const ProxyRule &pr, int64_t n_se
                                 const double *s_local, const double *q_sorted, double *Q, cudaStream_t st) {
   const unsigned ny = d == 3 ? (unsigned)((kp * kp + kPointThreads - 1) / kPointThreads) : 1u;
   point_anterp_kernel<KP><<<dim3((unsigned)n_seg, ny), kPointThreads, 0, st>>>(d, kp, pr, seg, s_local, q_sorted, Q);
+  return cudaGetLastError();
+}
+
+template <int KP>
+cudaError_t point_anterp32_launch(int d, int kp, const ProxyRule &pr, int64_t n_seg, const int64_t *seg,
+                                  const double *s_local, const double *q_sorted, double *Q, cudaStream_t st) {
+  // 3D: blocks of RB <= 512 grid rows, two rows per thread; 2D: groups of ceil(kp / 2) threads
+  const int rows = d == 3 ? kp * kp : kp;
+  int RB, TG, G, threads;
+  unsigned ny;
+  if (d == 3) {
+    ny = (unsigned)((rows + 511) / 512);
+    RB = (rows + (int)ny - 1) / (int)ny;
+    TG = (RB + 1) / 2;
+    G = 1;
+    threads = (TG + 31) / 32 * 32;
+  } else {
+    ny = 1;
+    RB = kp;
+    TG = (kp + 1) / 2;
+    threads = 256;
+    G = threads / TG;
+  }
+  point_anterp32_kernel<KP><<<dim3((unsigned)n_seg, ny), threads, 0, st>>>(d, kp, RB, TG, G, pr, seg, s_local,
+                                                                            q_sorted, Q);
+  return cudaGetLastError();
+}
+
+template <int KP>
+cudaError_t point_target32_launch(const PointTargets &pt, const ProxyRule &pr, double *u, cudaStream_t st) {
+  const size_t slice = sizeof(float) * KP * KP;
+  const int nq = pt.d == 3 ? pt.kp : 1;
+  const int slab = (int)std::max<size_t>(1, std::min<size_t>((size_t)nq, kTargetSlabBytes / slice));
+  const size_t sm = sizeof(float) * 2 * KP * 2 * kPointThreads + slice * slab;
+  cudaError_t e = cudaFuncSetAttribute(point_target32_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  point_target32_kernel<KP><<<(unsigned)pt.n_tseg, kPointThreads, sm, st>>>(pt, pr, slab, u);
   return cudaGetLastError();
 }
 
@@ -2725,18 +3006,35 @@ cudaError_t point_target_launch(const PointTargets &pt, const ProxyRule &pr, dou
     default: return cudaErrorInvalidValue;                                                \
   }
 static_assert(kMaxProxy == 40, "padded proxy orders cover 4..40");
+// FP32 kernels: k_p up to kMaxProxy32 (split precision needs tol >= 1e-7, about k_p <= 24)
+#define FGT_KP_SWITCH32(kp, CALL)                                                         \
+  switch (((kp) + 1) & ~1) {                                                              \
+    case 4: return CALL(4); case 6: return CALL(6); case 8: return CALL(8);               \
+    case 10: return CALL(10); case 12: return CALL(12); case 14: return CALL(14);         \
+    case 16: return CALL(16); case 18: return CALL(18); case 20: return CALL(20);         \
+    case 22: return CALL(22); case 24: return CALL(24); case 26: return CALL(26);         \
+    case 28: return CALL(28); case 30: return CALL(30);                                   \
+    default: return cudaErrorInvalidValue;                                                \
+  }
+static_assert(kMaxProxy32 == 30, "FP32 padded proxy orders cover 4..30");
 
 }  // namespace
 
-cudaError_t point_anterp(int d, int kp, const ProxyRule &pr, int64_t n_dense, int64_t n_seg, const int64_t *seg,
-                         const double *s_local, const double *q_sorted, double *Q, cudaStream_t st) {
+cudaError_t point_anterp(int d, int kp, bool f32, const ProxyRule &pr, int64_t n_dense, int64_t n_seg,
+                         const int64_t *seg, const double *s_local, const double *q_sorted, double *Q,
+                         cudaStream_t st) {
   if (n_dense <= 0) return cudaSuccess;
   if (kp < 1 || kp > kMaxProxy) return cudaErrorInvalidValue;
   const size_t np = d == 3 ? (size_t)kp * kp * kp : (size_t)kp * kp;
   cudaError_t e = cudaMemsetAsync(Q, 0, sizeof(double) * np * n_dense, st);
   if (e != cudaSuccess || n_seg <= 0) return e;
 #define FGT_ANTERP(K) point_anterp_launch<K>(d, kp, pr, n_seg, seg, s_local, q_sorted, Q, st)
+#define FGT_ANTERP32(K) point_anterp32_launch<K>(d, kp, pr, n_seg, seg, s_local, q_sorted, Q, st)
+  if (f32) {
+    FGT_KP_SWITCH32(kp, FGT_ANTERP32)
+  }
   FGT_KP_SWITCH(kp, FGT_ANTERP)
+#undef FGT_ANTERP32
 #undef FGT_ANTERP
 }
 
@@ -2744,13 +3042,19 @@ cudaError_t point_targets(const PointTargets &pt, const ProxyRule &pr, double *u
   if (pt.n_tseg <= 0) return cudaSuccess;
   if (pt.kp < 1 || pt.kp > kMaxProxy) return cudaErrorInvalidValue;
 #define FGT_TARGETS(K) point_target_launch<K>(pt, pr, u, st)
+#define FGT_TARGETS32(K) point_target32_launch<K>(pt, pr, u, st)
+  if (pt.f32) {
+    FGT_KP_SWITCH32(pt.kp, FGT_TARGETS32)
+  }
   FGT_KP_SWITCH(pt.kp, FGT_TARGETS)
+#undef FGT_TARGETS32
 #undef FGT_TARGETS
 }
 
-cudaError_t point_gather_q(int64_t n, const int64_t *s_id, const double *q, double *q_sorted, cudaStream_t st) {
+cudaError_t point_gather_q(int64_t n, const int64_t *s_id, const double *q, double *q_sorted, float *q32,
+                           cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  point_gather_q_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, s_id, q, q_sorted);
+  point_gather_q_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, s_id, q, q_sorted, q32);
   return cudaGetLastError();
 }
 

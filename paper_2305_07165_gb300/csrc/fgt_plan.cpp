@@ -2120,7 +2120,7 @@ fgt_status fgt_execute_batch(fgt_plan *const *plans, const double *const *sigma_
 // expansion to 5e-2 eps on the box.
 
 struct fgt_point_plan {
-  int d = 0, n_s = 0, kp = 0, M = 0, n1 = 0, nh = 0, lc = 0;
+  int d = 0, n_s = 0, kp = 0, M = 0, n1 = 0, nh = 0, lc = 0, prec = 0;
   double delta = 0, tol = 0, D0 = 0, Lc = 0, h = 0, kappa = 0;
   int64_t n_src = 0, n_tgt = 0, n_box = 0, n_dense = 0, n_in = 0, n_direct = 0;
   fgt::ProxyRule pr{};
@@ -2132,6 +2132,7 @@ struct fgt_point_plan {
   int64_t n_aseg = 0;
   const double *s_local = nullptr;
   double *Q = nullptr, *U = nullptr, *q_sorted = nullptr;
+  float *q32 = nullptr;
   ~fgt_point_plan() {
     if (dev) cudaFree(dev);
     if (work) cudaFree(work);
@@ -2186,7 +2187,16 @@ int proxy_order(double kappa_half_L, double h, int M, double tol, fgt::ProxyRule
       }
     }
     if (worst <= tol) {
-      for (int t = 0; t < n; ++t) { pr.x[t] = x[t]; pr.bw[t] = bw[t]; }
+      double bmax = 0.0;
+      for (int t = 0; t < n; ++t) {
+        pr.x[t] = x[t];
+        pr.bw[t] = bw[t];
+        bmax = std::max(bmax, std::fabs(bw[t]));
+      }
+      for (int t = 0; t < n; ++t) {
+        pr.xf[t] = (float)x[t];
+        pr.bwf[t] = (float)(bw[t] / bmax);
+      }
       return n;
     }
   }
@@ -2196,12 +2206,16 @@ int proxy_order(double kappa_half_L, double h, int M, double tol, fgt::ProxyRule
 }  // namespace
 
 fgt_status fgt_point_plan_create(int d, double delta, double tol, int64_t n_src, const double *src, int64_t n_tgt,
-                                 const double *tgt, int n_s, fgt_point_plan **out) {
+                                 const double *tgt, int n_s, int prec, fgt_point_plan **out) {
   if (!out) return fail(FGT_ERR_ARG, "out is NULL");
   *out = nullptr;
   if ((d != 2 && d != 3) || !(delta > 0) || !(tol > 0 && tol < 1) || n_src < 0 || n_tgt < 0 || n_s < 1 ||
       (n_src > 0 && !src) || (n_tgt > 0 && !tgt))
     return fail(FGT_ERR_ARG, "point plan: bad arguments");
+  if (prec != FGT_PREC_FP64 && prec != FGT_PREC_SPLIT)
+    return fail(FGT_ERR_ARG, "point plan: precision must be FGT_PREC_FP64 or FGT_PREC_SPLIT");
+  if (prec == FGT_PREC_SPLIT && tol < 1e-7) return fail(FGT_ERR_ARG, "split precision needs tol >= 1e-7");
+  const bool split = prec == FGT_PREC_SPLIT;
   auto *P = new (std::nothrow) fgt_point_plan();
   if (!P) return fail(FGT_ERR_OOM, "host allocation");
   std::unique_ptr<fgt_point_plan> guard(P);
@@ -2217,6 +2231,9 @@ fgt_status fgt_point_plan_create(int d, double delta, double tol, int64_t n_src,
   P->kappa = P->h / std::sqrt(delta);
   P->kp = proxy_order(P->kappa * 0.5 * P->Lc, P->h, P->M, 0.1 * tol, P->pr);
   if (P->kp < 0) return fail(FGT_ERR_ARG, "point plan: tolerance needs a proxy grid above 40 nodes per axis");
+  if (split && P->kp > fgt::kMaxProxy32)
+    return fail(FGT_ERR_ARG, "point plan: split precision needs a proxy grid of at most 30 nodes per axis");
+  P->prec = prec;
   // root: the bounding cube of all points, 2^l_c cutoff boxes wide
   double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
   for (int a = 0; a < d; ++a) { lo[a] = HUGE_VAL; hi[a] = -HUGE_VAL; }
@@ -2300,7 +2317,7 @@ fgt_status fgt_point_plan_create(int d, double delta, double tol, int64_t n_src,
   // direct source boxes (sparse colleagues with sources)
   int noff = 1;
   for (int a = 0; a < d; ++a) noff *= 3;
-  std::vector<int32_t> in_row(nbox, -1), gdst, dbox;
+  std::vector<int32_t> in_row(nbox, -1), gdst, dbox, dcode;
   std::vector<int64_t> gptr(1, 0), dptr(1, 0);
   std::vector<fgt::GatherSrc> gsrc;
   for (int64_t b = 0; b < nbox; ++b) {
@@ -2324,7 +2341,10 @@ fgt_status fgt_point_plan_create(int d, double delta, double tol, int64_t n_src,
       const int32_t s = it->second;
       if (sptr[s + 1] == sptr[s]) continue;
       if (dense_slot[s] >= 0) g.push_back(fgt::GatherSrc{dense_slot[s], code});
-      else if (has_t) dbox.push_back(s);
+      else if (has_t) {
+        dbox.push_back(s);
+        dcode.push_back(code);
+      }
     }
     if (has_t) dptr.push_back((int64_t)dbox.size());
     if (has_t && !g.empty()) {
@@ -2394,13 +2414,23 @@ fgt_status fgt_point_plan_create(int d, double delta, double tol, int64_t n_src,
   }
   Packer pk;
   const size_t o_fblk = pk.add(fblk), o_eblk = pk.add(eblk), o_fleaf = pk.add(fleaf), o_eleaf = pk.add(eleaf);
-  const size_t o_Ff = pk.add(Ff), o_Fh = pk.add(Fh), o_Ef = pk.add(Ef), o_Eh = pk.add(Eh), o_Pf = pk.add(Pf),
-               o_Ph = pk.add(Ph);
+  // complex tables in the expansions' precision
+  auto add_c = [&](const std::vector<double2> &v) {
+    if (!split) return pk.add(v);
+    std::vector<float2> f(v.size());
+    for (size_t i = 0; i < v.size(); ++i) f[i] = make_float2((float)v[i].x, (float)v[i].y);
+    return pk.add(f);
+  };
+  const size_t o_Ff = add_c(Ff), o_Fh = add_c(Fh), o_Ef = add_c(Ef), o_Eh = add_c(Eh), o_Pf = add_c(Pf),
+               o_Ph = add_c(Ph);
   const size_t o_gdst = pk.add(gdst), o_gptr = pk.add(gptr), o_gsrc = pk.add(gsrc);
   const size_t o_aseg = pk.add(aseg), o_sloc = pk.add(s_loc);
   const size_t o_tseg = pk.add(tseg), o_txyz = pk.add(t_xyz), o_tloc = pk.add(t_loc), o_tid = pk.add(t_id),
                o_tbin = pk.add(tb_in), o_dp = pk.add(dptr), o_db = pk.add(dbox), o_sp = pk.add(sptr),
-               o_sxyz = pk.add(s_xyz), o_sid = pk.add(s_id);
+               o_sxyz = pk.add(s_xyz), o_sid = pk.add(s_id), o_dcode = pk.add(dcode);
+  std::vector<float> s_loc32;
+  if (split) s_loc32.assign(s_loc.begin(), s_loc.end());
+  const size_t o_sloc32 = pk.add(s_loc32);
   cudaError_t e = cudaMalloc(&P->dev, std::max<size_t>(pk.buf.size(), 256));
   if (e != cudaSuccess) { P->dev = nullptr; cudaGetLastError(); return fail(FGT_ERR_OOM, "point plan: device tables"); }
   e = cudaMemcpy(P->dev, pk.buf.data(), pk.buf.size(), cudaMemcpyHostToDevice);
@@ -2408,23 +2438,27 @@ fgt_status fgt_point_plan_create(int d, double delta, double tol, int64_t n_src,
   auto at = [&](size_t off) { return (const void *)((const char *)P->dev + off); };
   const int64_t np = d == 3 ? (int64_t)kp * kp * kp : (int64_t)kp * kp;
   const int64_t ss = d == 3 ? (int64_t)nh * n1 * n1 : (int64_t)nh * n1;
-  const size_t phi_b = sizeof(double2) * ss * P->n_dense, psi_b = sizeof(double2) * ss * P->n_in;
+  const size_t csz = split ? sizeof(float2) : sizeof(double2);
+  const size_t phi_b = csz * ss * P->n_dense, psi_b = csz * ss * P->n_in;
   const size_t q_b = sizeof(double) * np * P->n_dense, u_b = sizeof(double) * np * P->n_in;
   const size_t qs_b = sizeof(double) * std::max<int64_t>(n_src, 1);
+  const size_t q32_b = split ? sizeof(float) * std::max<int64_t>(n_src, 1) : 0;
   size_t off = 0;
   auto place = [&](size_t bytes) { const size_t o = off; off = (off + bytes + 255) & ~(size_t)255; return o; };
-  const size_t w_phi = place(phi_b), w_psi = place(psi_b), w_q = place(q_b), w_u = place(u_b), w_qs = place(qs_b);
+  const size_t w_phi = place(phi_b), w_psi = place(psi_b), w_q = place(q_b), w_u = place(u_b), w_qs = place(qs_b),
+               w_q32 = place(q32_b);
   e = cudaMalloc(&P->work, std::max<size_t>(off, 256));
   if (e != cudaSuccess) { P->work = nullptr; cudaGetLastError(); return fail(FGT_ERR_OOM, "point plan: workspace"); }
   auto wk = [&](size_t o) { return (void *)((char *)P->work + o); };
   P->Q = (double *)wk(w_q);
   P->U = (double *)wk(w_u);
   P->q_sorted = (double *)wk(w_qs);
+  P->q32 = split ? (float *)wk(w_q32) : nullptr;
   P->aseg = (const int64_t *)at(o_aseg);
   P->s_local = (const double *)at(o_sloc);
   P->s_id = (const int64_t *)at(o_sid);
   fgt::ExecDesc &x = P->ex;
-  x.d = d; x.k = kp; x.n1 = n1; x.nh = nh; x.prec = 0; x.fourier = 0;
+  x.d = d; x.k = kp; x.n1 = n1; x.nh = nh; x.prec = split ? 1 : 0; x.fourier = 0;
   x.slot_size = ss;
   x.n_phi_slots = P->n_dense; x.n_psi_slots = P->n_in;
   x.phi = wk(w_phi); x.psi = wk(w_psi);
@@ -2447,7 +2481,7 @@ fgt_status fgt_point_plan_create(int d, double delta, double tol, int64_t n_src,
   x.Pf = at(o_Pf); x.Ph = at(o_Ph);
   x.n_points = P->n_in * np;
   fgt::PointTargets &t = P->pt;
-  t.d = d; t.kp = kp; t.delta = delta;
+  t.d = d; t.kp = kp; t.f32 = split ? 1 : 0; t.delta = delta;
   t.n_tseg = (int64_t)tseg.size() / 3;
   t.tseg = (const int64_t *)at(o_tseg);
   t.t_xyz = (const double *)at(o_txyz);
@@ -2460,6 +2494,11 @@ fgt_status fgt_point_plan_create(int d, double delta, double tol, int64_t n_src,
   t.sptr = (const int64_t *)at(o_sp);
   t.s_xyz = (const double *)at(o_sxyz);
   t.q_sorted = P->q_sorted;
+  t.inv_delta = 1.0 / delta;
+  t.dcode = (const int32_t *)at(o_dcode);
+  t.s_local32 = split ? (const float *)at(o_sloc32) : nullptr;
+  t.q32 = P->q32;
+  t.dcoef = (float)(0.25 * P->Lc * P->Lc / delta);
   *out = guard.release();
   return FGT_OK;
 }
@@ -2467,9 +2506,10 @@ fgt_status fgt_point_plan_create(int d, double delta, double tol, int64_t n_src,
 fgt_status fgt_point_execute(fgt_point_plan *P, const double *q_dev, double *u_dev, void *stream) {
   if (!P || (P->n_src > 0 && !q_dev) || (P->n_tgt > 0 && !u_dev)) return fail(FGT_ERR_ARG, "NULL argument");
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = fgt::point_gather_q(P->n_src, P->s_id, q_dev, P->q_sorted, st);
-  if (e == cudaSuccess) e = fgt::point_anterp(P->d, P->kp, P->pr, P->n_dense, P->n_aseg, P->aseg, P->s_local,
-                                              P->q_sorted, P->Q, st);
+  cudaError_t e = fgt::point_gather_q(P->n_src, P->s_id, q_dev, P->q_sorted, P->q32, st);
+  if (e == cudaSuccess)
+    e = fgt::point_anterp(P->d, P->kp, P->prec == FGT_PREC_SPLIT, P->pr, P->n_dense, P->n_aseg, P->aseg,
+                          P->s_local, P->q_sorted, P->Q, st);
   if (e == cudaSuccess && P->n_dense > 0 && P->n_in > 0) e = fgt::run_transform(P->ex, P->Q, P->U, st);
   if (e == cudaSuccess) e = fgt::point_targets(P->pt, P->pr, u_dev, st);
   return e == cudaSuccess ? FGT_OK : cuda_fail(e, "point transform");
@@ -2485,6 +2525,7 @@ fgt_status fgt_point_plan_get_info(const fgt_point_plan *P, fgt_point_info *info
   info->n_incoming_boxes = P->n_in;
   info->n_direct_pairs = P->n_direct;
   info->cutoff_length = P->Lc;
+  info->prec = P->prec;
   return FGT_OK;
 }
 

@@ -279,3 +279,20 @@ def test_output_tree_validation():
     assert try_tree([1, 1, 1, 1, 2], crd.tolist() + [[0, 0]]) == 2         # overlapping leaves
     assert try_tree([1, 1, 1, 1, 1], crd.tolist() + [[0, 0]]) == 2         # repeated leaf
     assert F.lib().fgt_plan_set_output_tree(hp._h, None) == 0
+
+
+def test_point_plan_argument_checks():
+    """fgt_point_plan_create rejects bad precisions and split below tol 1e-7 before touching the device."""
+    import ctypes
+    L = F.lib()
+    pts = np.zeros((4, 3))
+    h = ctypes.c_void_p()
+
+    def create(tol, prec, d=3):
+        return L.fgt_point_plan_create(d, 1e-3, tol, 4, pts.ctypes.data, 4, pts.ctypes.data, 8, prec,
+                                       ctypes.byref(h))
+    assert create(1e-6, 7) == 1
+    assert create(1e-8, F.PREC_SPLIT) == 1
+    assert create(1e-6, F.PREC_FP64_TC) == 1
+    assert create(1e-6, F.PREC_FP64, d=4) == 1
+    assert h.value is None

@@ -18,10 +18,10 @@ def _clustered(rng, n, d, k=6):
     return c[lab] + w[lab, None] * rng.standard_normal((n, d))
 
 
-def check(d, delta, tol, src, tgt, n_s, seed=0):
+def check(d, delta, tol, src, tgt, n_s, seed=0, prec=0):
     rng = np.random.default_rng(seed)
     q = rng.uniform(0.5, 1.5, len(src))
-    plan = F.PointPlan(d, delta, tol, src, tgt, n_s=n_s)
+    plan = F.PointPlan(d, delta, tol, src, tgt, n_s=n_s, prec=prec)
     u = plan(torch.from_numpy(q).cuda()).cpu().numpy()
     info = plan.info()
     plan.close()
@@ -67,3 +67,48 @@ def test_empty_and_tiny_sets():
     plan.close()
     check(2, 1e-2, 1e-6, pts[:1], pts, n_s=8)
     check(2, 1e-2, 1e-6, pts, pts[:1], n_s=8)
+
+
+@pytest.mark.parametrize("d,delta,tol", [(2, 1e-3, 1e-6), (3, 1e-3, 1e-6), (3, 3e-3, 1e-7)])
+def test_split_uniform_points(d, delta, tol):
+    """FP32 Lagrange weights, anterpolation, interpolation and expansions: the same bound."""
+    rng = np.random.default_rng(20 + d)
+    pts = rng.uniform(-0.5, 0.5, size=(20000, d))
+    info = check(d, delta, tol, pts, pts, n_s=32, prec=F.PREC_SPLIT)
+    assert info["prec"] == F.PREC_SPLIT and info["n_dense_boxes"] > 0
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_split_clustered(d):
+    """Crowded boxes: many source and target segments per box, with sparse colleagues."""
+    rng = np.random.default_rng(30 + d)
+    src = _clustered(rng, 60000, d)
+    tgt = np.concatenate([_clustered(rng, 10000, d), rng.uniform(-0.6, 0.6, size=(5000, d))])
+    info = check(d, 1e-3, 1e-6, src, tgt, n_s=40, prec=F.PREC_SPLIT)
+    assert info["n_dense_boxes"] > 0 and info["n_direct_pairs"] > 0
+
+
+def test_split_nodes_and_box_edges():
+    """Points on proxy nodes' coordinates and on box faces (Lagrange weights at a node, s = +-1)."""
+    rng = np.random.default_rng(41)
+    pts = rng.uniform(-0.5, 0.5, size=(4000, 3))
+    pts[:50] = 0.0                       # the centre of the root; a node coordinate for odd k_p
+    pts[50:100, 0] = pts[50:100, 0].round(1)
+    for prec in (F.PREC_FP64, F.PREC_SPLIT):
+        check(3, 1e-3, 1e-6, pts, pts, n_s=8, prec=prec)
+
+
+def test_split_rejects_tight_tolerance():
+    pts = np.zeros((4, 3))
+    with pytest.raises(F.FGTError):
+        F.PointPlan(3, 1e-3, 1e-8, pts, pts, prec=F.PREC_SPLIT)
+    with pytest.raises(F.FGTError):
+        F.PointPlan(3, 1e-3, 1e-6, pts, pts, prec=7)
+
+
+def test_split_all_direct():
+    """No dense box: every pair through the FP32 direct sum from local coordinates."""
+    rng = np.random.default_rng(43)
+    pts = rng.uniform(-0.5, 0.5, size=(6000, 3))
+    info = check(3, 1e-3, 1e-6, pts, pts, n_s=10 ** 9, prec=F.PREC_SPLIT)
+    assert info["n_dense_boxes"] == 0 and info["n_direct_pairs"] > 0
