@@ -577,7 +577,7 @@ def main():
             "error_vs_oracle": err,
             "e2e": {"value": world * w.n_points * args.steps / e2e_s, "unit": "points/s",
                     "h2d_bytes_per_step": int(w.n_points * 8), "d2h_bytes_per_step": int(w.n_points * 8)},
-            "gpu_launches": int(info["launches"] * args.steps),
+            "gpu_launches": int(head["info"]["launches"] * args.steps),
             "clocks": clocks,
             "batched": batched,
             "serving": serving,
