@@ -303,6 +303,14 @@ void fgt_destroy(fgt_plan *plan);
 
 const char *fgt_last_error(void);
 
+/* Status of the tensor-core (tcgen05) evaluation kernels on the current device.  Those kernels wait
+ * on the tensor cores through mbarriers with a time limit of about one second; a wait that runs out
+ * makes the kernel skip the rest of its block (u is then wrong there), free its tensor memory and
+ * set a device status word instead of hanging.  This call copies that word to *status (0: no wait
+ * ran out since the last call, 1: one did) and clears it.  It synchronises with the device.
+ * FGT_ERR_ARG if status is NULL, FGT_ERR_CUDA if the copy fails. */
+fgt_status fgt_device_status(int *status);
+
 /* ---- Host-side building blocks of the 1D tables (Section 2.4), exposed for tests ---- */
 
 /* k-point Gauss-Legendre rule on [-1,1], ascending nodes. 1 <= k <= 64. */

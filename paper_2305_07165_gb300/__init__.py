@@ -127,6 +127,7 @@ def lib():
             L.fgt_destroy.argtypes = [vp]
             L.fgt_destroy.restype = None
             L.fgt_last_error.restype = ctypes.c_char_p
+            L.fgt_device_status.argtypes = [vp]
             L.fgt_gauss_legendre.argtypes = [i32, vp, vp]
             L.fgt_params.argtypes = [dbl, dbl, i32, vp, vp, vp, vp, vp, vp]
             L.fgt_nf_for_range.argtypes = [dbl, dbl]
@@ -151,6 +152,14 @@ def lib():
 def _check(status):
     if status != 0:
         raise FGTError(status, lib().fgt_last_error().decode(errors="replace"))
+
+
+def device_status() -> int:
+    """fgt_device_status: 1 if a wait of a tensor-core kernel ran out since the last call, else 0
+    (and clears it)."""
+    v = ctypes.c_int(0)
+    _check(lib().fgt_device_status(ctypes.byref(v)))
+    return v.value
 
 
 def _tree_struct(d, k, level, coord):

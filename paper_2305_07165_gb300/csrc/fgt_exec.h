@@ -16,6 +16,7 @@ struct LaunchRange {
   int tensor = 0;  // 1: the tensor-core (3xTF32) variant of the kernel
   int big = 0;     // 1: single blocks of K > 16, sigma streamed from global memory in stage 1
   int rows = 0;    // evaluation: rows of a block per CTA
+  int tmem_cols = 0;  // tcgen05 evaluation: tensor-memory columns per CTA
 };
 
 // One level of the hierarchical merge (child -> parent) or push (parent -> child).
@@ -62,6 +63,10 @@ struct ExecDesc {
   const int32_t *pack_block = nullptr;  // index into blocks of every block_leaves entry
   int64_t n_pack = 0;                   // block_leaves entries
   const void *Ff = nullptr, *Fh = nullptr, *Ef = nullptr, *Eh = nullptr;
+  // tcgen05 evaluation: the expansions it reads in the tensor cores' operand layout (written once
+  // per transform after the gather); nullptr: the tcgen05 ranges fall back to the CUDA-core kernel
+  void *psi_tc = nullptr;
+  int64_t n_psi_tc_slots = 0;
 
   // out->in gather at the cutoff level
   int64_t n_gather = 0;
@@ -107,6 +112,10 @@ int launches_per_transform(const ExecDesc &e);
 
 // Enqueue the whole transform on `stream`.  sigma, u: device FP64 [n_leaves][k^d].
 cudaError_t run_transform(const ExecDesc &e, const double *sigma, double *u, cudaStream_t stream);
+
+// Reads and clears the status word of the tcgen05 kernels: 1 when a wait on the tensor cores ran
+// out since the last read (the affected blocks were skipped), else 0.  Synchronous.
+cudaError_t read_tc_status(int *status);
 
 // Allocation-free execution: the expansion workspace lives in a fixed device array of
 // kNoallocScratchBytes inside the library instead of the plan's own buffers.  The first call
@@ -218,6 +227,35 @@ inline size_t eval2_bytes(int d, int K, int n1, int nh, size_t c, int rows) {
   const size_t R = (size_t)(K < rows ? K : rows);  // rows held at once
   if (d == 3) return c * (R * n1 * n1 + R * K * n1 + 2 * (size_t)K * n1 + R * nh);
   return c * (R * n1 + (size_t)K * n1 + R * nh);
+}
+
+// Whole-block 3D evaluation with stage 1 on tcgen05 (split precision).  The expansion's operand
+// copy: per slot, tiles of 128 modes, each a TF32 hi half and a lo half of 128 x kp2 values
+// (kp2 = 2 nh padded to a multiple of 8), K-major core matrices.  Shared memory: a ring of
+// kEval6Ring half-tiles and the rows' B operand (hi and lo), overlaid after stage 1 by the FP32
+// stage-1 result; then the stage-2 result, the E1 / E2 matrices and the barrier words.
+inline int eval6_kpad(int nh) { return (2 * nh + 7) / 8 * 8; }
+constexpr int kEval6MaxKp2 = 64;  // largest padded 2 nh (nh <= 32)
+constexpr int kEval6Ring = 3;
+inline int eval6_n(int rows) { return rows <= 8 ? 16 : 2 * rows; }
+inline size_t eval6_half_bytes(int nh) { return 128 * (size_t)eval6_kpad(nh) * 4; }
+inline size_t eval6_slot_bytes(int n1, int nh) {
+  return (size_t)((n1 * n1 + 127) / 128) * 2 * eval6_half_bytes(nh);
+}
+inline size_t eval6_bytes(int K, int n1, int nh, int rows) {
+  const size_t R = (size_t)(K < rows ? K : rows), kp2 = (size_t)eval6_kpad(nh);
+  const size_t stage = kEval6Ring * eval6_half_bytes(nh) + 2 * (size_t)eval6_n(rows) * kp2 * 4;
+  const size_t y1 = 8 * R * n1 * n1;
+  const size_t r1 = ((stage > y1 ? stage : y1) + 127) & ~(size_t)127;
+  return r1 + 8 * (R * K * n1 + 2 * (size_t)K * n1) + 64;
+}
+// Tensor-memory columns of that kernel: one 128 x N accumulator per 128-mode tile, rounded up to a
+// power of two (at least 32); 0 when the tiles do not fit the 512 columns of an SM.
+inline int eval6_tmem_cols(int n1, int rows) {
+  const int tiles = (n1 * n1 + 127) / 128, cols = tiles * eval6_n(rows);
+  int c = 32;
+  while (c < cols) c *= 2;
+  return c <= 512 ? c : 0;
 }
 
 // Shared-memory bytes the form / evaluation kernels need for a block size K.

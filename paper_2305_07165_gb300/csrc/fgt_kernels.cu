@@ -929,6 +929,137 @@ __global__ void __launch_bounds__(256, BIG ? 2 : (NBT > 8 ? 2 : 3)) form4_kernel
 
 // ----------------------------------------------------------------------------- whole-block evaluation
 
+// Stage 2 of the 3D evaluation on the CUDA cores (shared by the whole-block kernels):
+// Y2[r][I2][m1] = sum_m2 E2[I2][m2] Y1[r][m2][m1]; 4 x 4 register tiles over (I2, m1) when there
+// are enough tiles to occupy the CTA, else one output per thread.
+template <typename R>
+__device__ __forceinline__ void eval_stage2_3d(const typename C2T<R>::T *__restrict__ Y1,
+                                               typename C2T<R>::T *__restrict__ Y2,
+                                               const typename C2T<R>::T *__restrict__ E2, int nr, int K, int n1) {
+  using C = typename C2T<R>::T;
+  const int nn = n1 * n1, tI = (K + 3) / 4, tm = (n1 + 3) / 4;
+  if (nr * tI * tm < (int)blockDim.x / 2) {
+    for (int e = threadIdx.x; e < nr * K * n1; e += blockDim.x) {
+      const int m1 = e % n1, rest = e / n1, I2 = rest % K, r = rest / K;
+      const C *ep = E2 + (size_t)I2 * n1;
+      const C *yp = Y1 + (size_t)r * nn + m1;
+      R ar = 0, ai = 0;
+      for (int m2 = 0; m2 < n1; ++m2) cfma(ar, ai, ep[m2], yp[m2 * n1]);
+      Y2[e] = C{ar, ai};
+    }
+  } else {
+    const int ntile = nr * tI * tm;
+    for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
+      const int bm = t % tm, rest = t / tm, bI = rest % tI, r = rest / tI;
+      R ar[4][4], ai[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ar[i][j] = ai[i][j] = 0;
+      const C *yr = Y1 + (size_t)r * nn;
+      for (int m2 = 0; m2 < n1; ++m2) {
+        C a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int I2 = bI * 4 + i;
+          a[i] = (I2 < K) ? E2[(size_t)I2 * n1 + m2] : C{0, 0};
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int m1 = bm * 4 + j;
+          b[j] = (m1 < n1) ? yr[(size_t)m2 * n1 + m1] : C{0, 0};
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) cfma(ar[i][j], ai[i][j], a[i], b[j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int I2 = bI * 4 + i, m1 = bm * 4 + j;
+          if (I2 < K && m1 < n1) Y2[((size_t)r * K + I2) * n1 + m1] = C{ar[i][j], ai[i][j]};
+        }
+    }
+  }
+}
+
+// Stage 3 of the 3D evaluation on the CUDA cores: u(r0 + r, I2, I1) = Re sum_m1 E1[I1][m1]
+// Y2[r][I2][m1], stored (or added, acc_u) into the block's leaves.
+template <typename R>
+__device__ __forceinline__ void eval_stage3_3d(const typename C2T<R>::T *__restrict__ Y2,
+                                               const typename C2T<R>::T *__restrict__ E1, int nr, int K, int n1,
+                                               int r0, int k, int nl, const int64_t *__restrict__ lv,
+                                               double *__restrict__ u, bool acc_u) {
+  using C = typename C2T<R>::T;
+  const int tI = (K + 3) / 4, kp = k * k * k;
+  // u(r0 + r, I2, I1) = Re sum_m1 E1[I1][m1] Y2[r][I2][m1]; 4 x 4 register tiles over (I2, I1)
+  // when there are enough tiles, else one output per thread
+  if (nr * tI * tI < (int)blockDim.x / 2) {
+    for (int e = threadIdx.x; e < nr * K * K; e += blockDim.x) {
+      const int I1 = e % K, rest = e / K, I2 = rest % K, r = rest / K;
+      const C *ep = E1 + (size_t)I1 * n1;
+      const C *yp = Y2 + ((size_t)r * K + I2) * n1;
+      R acc = 0;
+      for (int m1 = 0; m1 < n1; ++m1) {
+        const C a = ep[m1], y = yp[m1];
+        acc = fma(a.x, y.x, acc);
+        acc = fma(-a.y, y.y, acc);
+      }
+      const int I3 = r0 + r, o1 = I1 / k, o2 = I2 / k, o3 = I3 / k;
+      double *up = u + lv[(o3 * nl + o2) * nl + o1] * kp + ((I3 - o3 * k) * k + (I2 - o2 * k)) * k + (I1 - o1 * k);
+      if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc;
+    }
+  } else {
+    const int ntile = nr * tI * tI;
+    for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
+      const int b1 = t % tI, rest = t / tI, b2 = rest % tI, r = rest / tI;
+      R acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+      const C *yr = Y2 + (size_t)r * K * n1;
+      for (int m1 = 0; m1 < n1; ++m1) {
+        C y[4], a[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int I2 = b2 * 4 + i;
+          y[i] = (I2 < K) ? yr[(size_t)I2 * n1 + m1] : C{0, 0};
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int I1 = b1 * 4 + j;
+          a[j] = (I1 < K) ? E1[(size_t)I1 * n1 + m1] : C{0, 0};
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc[i][j] = fma(a[j].x, y[i].x, acc[i][j]);
+            acc[i][j] = fma(-a[j].y, y[i].y, acc[i][j]);
+          }
+      }
+      const int I3 = r0 + r, o3 = I3 / k, t3 = I3 - o3 * k;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int I2 = b2 * 4 + i;
+        if (I2 >= K) continue;
+        const int o2 = I2 / k, t2 = I2 - o2 * k;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int I1 = b1 * 4 + j;
+          if (I1 >= K) continue;
+          const int o1 = I1 / k;
+          double *up = u + lv[(o3 * nl + o2) * nl + o1] * kp + (t3 * k + t2) * k + (I1 - o1 * k);
+          if (acc_u) atomicAdd(up, (double)acc[i][j]); else *up = (double)acc[i][j];
+        }
+      }
+    }
+  }
+}
+
 // A CTA evaluates KM rows (along the last axis) of one block, all of it when K <= KM: the
 // anchor's incoming expansion is read once per CTA (each thread keeps KM accumulators for its
 // mode column), then the two remaining contractions run from shared memory.
@@ -1011,9 +1142,7 @@ __global__ void __launch_bounds__(256) eval2_kernel(const Block *__restrict__ bl
   __syncthreads();
   const int kp = (D == 3) ? k * k * k : k * k;
   if (D == 3) {
-    // Y2[r][I2][m1] = sum_m2 E2[I2][m2] Y1[r][m2][m1]; 4 x 4 register tiles over (I2, m1) when
-    // there are enough tiles to occupy the CTA, else one output per thread
-    const int tI = (K + 3) / 4, tm = (n1 + 3) / 4;
+    // Y2[r][I2][m1] = sum_m2 E2[I2][m2] Y1[r][m2][m1]
     if constexpr (TC && sizeof(R) == 8) {
       // one warp per (row r, 8 rows of I2, 32 columns of m1): A = E2, B = Y1[r]
       const int mt = (K + 7) / 8, cb = (n1 + 31) / 32;
@@ -1034,116 +1163,11 @@ __global__ void __launch_bounds__(256) eval2_kernel(const Block *__restrict__ bl
             }
         }
       }
-    } else if (nr * tI * tm < (int)blockDim.x / 2) {
-      for (int e = threadIdx.x; e < nr * K * n1; e += blockDim.x) {
-        const int m1 = e % n1, rest = e / n1, I2 = rest % K, r = rest / K;
-        const C *ep = E2 + (size_t)I2 * n1;
-        const C *yp = Y1 + (size_t)r * nn + m1;
-        R ar = 0, ai = 0;
-        for (int m2 = 0; m2 < n1; ++m2) cfma(ar, ai, ep[m2], yp[m2 * n1]);
-        Y2[e] = C{ar, ai};
-      }
     } else {
-      const int ntile = nr * tI * tm;
-      for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
-        const int bm = t % tm, rest = t / tm, bI = rest % tI, r = rest / tI;
-        R ar[4][4], ai[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) ar[i][j] = ai[i][j] = 0;
-        const C *yr = Y1 + (size_t)r * nn;
-        for (int m2 = 0; m2 < n1; ++m2) {
-          C a[4], b[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int I2 = bI * 4 + i;
-            a[i] = (I2 < K) ? E2[(size_t)I2 * n1 + m2] : C{0, 0};
-          }
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int m1 = bm * 4 + j;
-            b[j] = (m1 < n1) ? yr[(size_t)m2 * n1 + m1] : C{0, 0};
-          }
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) cfma(ar[i][j], ai[i][j], a[i], b[j]);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int I2 = bI * 4 + i, m1 = bm * 4 + j;
-            if (I2 < K && m1 < n1) Y2[((size_t)r * K + I2) * n1 + m1] = C{ar[i][j], ai[i][j]};
-          }
-      }
+      eval_stage2_3d<R>(Y1, Y2, E2, nr, K, n1);
     }
     __syncthreads();
-    // u(r0 + r, I2, I1) = Re sum_m1 E1[I1][m1] Y2[r][I2][m1]; 4 x 4 register tiles over (I2, I1)
-    // when there are enough tiles, else one output per thread
-    if (nr * tI * tI < (int)blockDim.x / 2) {
-      for (int e = threadIdx.x; e < nr * K * K; e += blockDim.x) {
-        const int I1 = e % K, rest = e / K, I2 = rest % K, r = rest / K;
-        const C *ep = E1 + (size_t)I1 * n1;
-        const C *yp = Y2 + ((size_t)r * K + I2) * n1;
-        R acc = 0;
-        for (int m1 = 0; m1 < n1; ++m1) {
-          const C a = ep[m1], y = yp[m1];
-          acc = fma(a.x, y.x, acc);
-          acc = fma(-a.y, y.y, acc);
-        }
-        const int I3 = r0 + r, o1 = I1 / k, o2 = I2 / k, o3 = I3 / k;
-        double *up = u + lv[(o3 * nl + o2) * nl + o1] * kp + ((I3 - o3 * k) * k + (I2 - o2 * k)) * k + (I1 - o1 * k);
-        if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc;
-      }
-    } else {
-      const int ntile = nr * tI * tI;
-      for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
-        const int b1 = t % tI, rest = t / tI, b2 = rest % tI, r = rest / tI;
-        R acc[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = 0;
-        const C *yr = Y2 + (size_t)r * K * n1;
-        for (int m1 = 0; m1 < n1; ++m1) {
-          C y[4], a[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int I2 = b2 * 4 + i;
-            y[i] = (I2 < K) ? yr[(size_t)I2 * n1 + m1] : C{0, 0};
-          }
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int I1 = b1 * 4 + j;
-            a[j] = (I1 < K) ? E1[(size_t)I1 * n1 + m1] : C{0, 0};
-          }
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              acc[i][j] = fma(a[j].x, y[i].x, acc[i][j]);
-              acc[i][j] = fma(-a[j].y, y[i].y, acc[i][j]);
-            }
-        }
-        const int I3 = r0 + r, o3 = I3 / k, t3 = I3 - o3 * k;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int I2 = b2 * 4 + i;
-          if (I2 >= K) continue;
-          const int o2 = I2 / k, t2 = I2 - o2 * k;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int I1 = b1 * 4 + j;
-            if (I1 >= K) continue;
-            const int o1 = I1 / k;
-            double *up = u + lv[(o3 * nl + o2) * nl + o1] * kp + (t3 * k + t2) * k + (I1 - o1 * k);
-            if (acc_u) atomicAdd(up, (double)acc[i][j]); else *up = (double)acc[i][j];
-          }
-        }
-      }
-    }
+    eval_stage3_3d<R>(Y2, E1, nr, K, n1, r0, k, nl, lv, u, acc_u);
   } else {
     for (int e = threadIdx.x; e < nr * K; e += blockDim.x) {
       const int I1 = e % K, r = e / K;
@@ -1160,6 +1184,287 @@ __global__ void __launch_bounds__(256) eval2_kernel(const Block *__restrict__ bl
       if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc;
     }
   }
+}
+
+// ----------------------------------------------------------------------------- tcgen05 helpers
+//
+// Fifth-generation tensor cores (sm_100 family): tcgen05.mma reads its operands from shared memory
+// through 64-bit matrix descriptors and accumulates in tensor memory (TMEM, 128 lanes x 512
+// 32-bit columns per SM), which the CTA allocates, reads back with tcgen05.ld and frees.
+// Operand layout used here: K-major without swizzle, 8-row x 16-byte core matrices, the core
+// matrices adjacent along K 128 bytes apart (leading byte offset) and the 8-row groups `sbo`
+// bytes apart (stride byte offset).
+
+__device__ int g_tc_status;  // set to 1 when a wait on the tensor cores ran out (read by fgt_device_status)
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)(128 >> 4) << 16;                  // leading byte offset: next core matrix along K
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;        // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                            // descriptor version of the sm_100 family
+  return d;                                          // base offset 0, no swizzle
+}
+
+// Instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both K-major, M x N.
+__host__ __device__ constexpr uint32_t umma_idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element (row, kk) in a K-major operand tile whose 8-row groups are sbo bytes apart.
+__device__ __forceinline__ uint32_t umma_off(int row, int kk, uint32_t sbo) {
+  return (uint32_t)(row >> 3) * sbo + (uint32_t)(kk >> 2) * 128u + (uint32_t)(row & 7) * 16u + (uint32_t)(kk & 3) * 4u;
+}
+
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+// Waits for the completion of the mbarrier phase of the given parity; gives up after about
+// 2^31 clocks (about one second) and returns false.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1LL << 31)) return false;
+  }
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Bulk asynchronous copy (the copy engine of the sm_90+ memory system): `bytes` (a multiple of 16,
+// both addresses 16-byte aligned) from global to shared memory, completing on an mbarrier that
+// the issuing thread armed for that many bytes.
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
+// ----------------------------------------------------------------------------- expansions in tcgen05 operand layout
+//
+// The incoming expansions, copied once per transform into the A-operand layout of the tcgen05
+// evaluation: slot s, tile t (modes q = 128 t .. 128 t + 127, q = m2 n1 + m1), half h (TF32 hi, lo)
+// at s * slot_bytes + (2 t + h) * half_bytes, element (row = q - 128 t, kk = 2 m3 + c) at the
+// K-major core-matrix offset umma_off(row, kk, 32 kp2); A[q][2 m3] = Re psi[m3][q],
+// A[q][2 m3 + 1] = Im psi[m3][q], zero for q >= n1^2 and kk >= 2 nh.  One thread per
+// (slot, tile, 4 consecutive kk, row): two complex coefficients, one 16-byte store per half.
+__global__ void __launch_bounds__(256) psi_tc_kernel(const float2 *__restrict__ psi, unsigned char *__restrict__ out,
+                                                     int n1, int nh, int64_t slot_size, int64_t n_slots) {
+  const int nn = n1 * n1, mt = (nn + 127) / 128, kp2 = (2 * nh + 7) / 8 * 8, nq = kp2 / 4;
+  const uint32_t sbo = (uint32_t)kp2 * 32, half = 16u * sbo;
+  const int64_t per_slot = (int64_t)mt * nq * 128;
+  const int64_t total = per_slot * n_slots;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = g / per_slot;
+    const int rem = (int)(g - s * per_slot), row = rem & 127, j = (rem >> 7) % nq, t = (rem >> 7) / nq;
+    const int q = t * 128 + row;
+    const float2 *ps = psi + s * slot_size;
+    float2 v0 = make_float2(0.f, 0.f), v1 = v0;
+    if (q < nn) {
+      if (2 * j < nh) v0 = ps[(int64_t)(2 * j) * nn + q];
+      if (2 * j + 1 < nh) v1 = ps[(int64_t)(2 * j + 1) * nn + q];
+    }
+    uint4 h, l;
+    split_tf32(v0.x, h.x, l.x);
+    split_tf32(v0.y, h.y, l.y);
+    split_tf32(v1.x, h.z, l.z);
+    split_tf32(v1.y, h.w, l.w);
+    unsigned char *base = out + (size_t)s * ((size_t)mt * 2 * half) + (size_t)(2 * t) * half + umma_off(row, 4 * j, sbo);
+    *reinterpret_cast<uint4 *>(base) = h;
+    *reinterpret_cast<uint4 *>(base + half) = l;
+  }
+}
+
+// ----------------------------------------------------------------------------- evaluation, stage 1 on tcgen05 (3D, FP32)
+//
+// Whole-block evaluation of KM rows I3 of a block (as eval2_kernel) whose first contraction
+//   Y1[r][q] = sum_m3 Ed(I3_r, m3) psi[m3][q],   q = m2 n1 + m1 (nn = n1^2 modes)
+// runs on the tensor cores in real form, per tile of 128 modes q:
+//   D[q][2r + c] = sum_kk A[q][kk] B[kk][2r + c],   kk = 2 m3 + c'  (c, c' = real, imaginary part),
+//   A[q][2 m3] = Re psi, A[q][2 m3 + 1] = Im psi,
+//   B[2 m3][2r] = Re Ed, B[2 m3 + 1][2r] = -Im Ed, B[2 m3][2r + 1] = Im Ed, B[2 m3 + 1][2r + 1] = Re Ed,
+// each operand split into TF32 hi and lo halves and the product taken as lo*hi + hi*lo + hi*hi
+// (3xTF32, FP32-accurate), accumulated in FP32 in TMEM (one 128 x N accumulator per tile,
+// N = max(16, 2 KM)).  A comes from the operand copy of the expansion (psi_tc_kernel): thread 0
+// streams its half-tiles through a ring of kEval6Ring shared buffers with bulk asynchronous copies
+// (a full and an empty mbarrier per buffer), issues the MMAs of each half as it lands and commits
+// them to the buffer's empty barrier, keeping two copies in flight ahead of the tensor cores.
+// The other threads build B and the E1 / E2 matrices meanwhile, then everyone reads the
+// accumulators back and stages 2-3 run from shared memory on the CUDA cores (eval_stage2_3d /
+// eval_stage3_3d).  A wait that runs out sets g_tc_status, skips the rest of the block and frees
+// the tensor memory.
+template <int KM>
+__global__ void __launch_bounds__(256) eval6_kernel(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
+                                                    const float2 *__restrict__ Ef, const float2 *__restrict__ Eh,
+                                                    const unsigned char *__restrict__ psi_tc, double *__restrict__ u,
+                                                    int k, int n1, int nh, int tmem_cols) {
+  constexpr int N = KM <= 8 ? 16 : 2 * KM, S = kEval6Ring;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const Block blk = blocks[blockIdx.x];
+  const int K = blk.K, nl = 1 << blk.dl;
+  const int r0 = blockIdx.y * KM, nr = min(KM, K - r0);
+  if (nr <= 0) return;
+  const int RM = min(KM, K);
+  const int64_t *lv = bleaves + blk.leaf0;
+  const bool acc_u = (blk.flags & 1) != 0;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nn = n1 * n1, mt = (nn + 127) / 128, nst = 2 * mt;  // stages: (tile, half)
+  const int kp2 = (2 * nh + 7) / 8 * 8, ksteps = kp2 / 8;
+  const uint32_t sbo = (uint32_t)kp2 * 32, half_b = 16u * sbo;
+  const unsigned char *src = psi_tc + (size_t)blk.slot * ((size_t)nst * half_b);
+  // shared memory: ring [S] half-tiles, B hi, B lo | overlaid by Y1 after stage 1; Y2, E1, E2, words
+  unsigned char *ring = smem_raw;
+  unsigned char *bh = ring + (size_t)S * half_b, *bl = bh + (size_t)N * kp2 * 4;
+  const size_t stage_b = (size_t)S * half_b + 2 * (size_t)N * kp2 * 4, y1_b = 8 * (size_t)RM * nn;
+  const size_t r1 = ((stage_b > y1_b ? stage_b : y1_b) + 127) & ~(size_t)127;
+  float2 *Y1 = reinterpret_cast<float2 *>(smem_raw);
+  float2 *Y2 = reinterpret_cast<float2 *>(smem_raw + r1);
+  float2 *E1 = Y2 + (size_t)RM * K * n1;
+  float2 *E2 = E1 + (size_t)K * n1;
+  uint64_t *full = reinterpret_cast<uint64_t *>(E2 + (size_t)K * n1);  // [S]
+  uint64_t *empty = full + S;                                          // [S]
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(empty + S);
+  if (tid == 0) {
+    for (int b = 0; b < S; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(full + b)), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(empty + b)), "r"(1));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // the first S - 1 copies start before anything else
+  if (tid == 0)
+    for (int i = 0; i < S - 1 && i < nst; ++i)
+      bulk_copy_g2s(smem_addr(ring + (size_t)i * half_b), src + (size_t)i * half_b, half_b, smem_addr(full + i));
+  for (int e = tid; e < K * n1; e += blockDim.x) {
+    const int I = e / n1, m = e - I * n1;
+    E1[e] = Ef[((int64_t)(blk.mat[0] + I / k) * k + I % k) * n1 + m];
+    E2[e] = Ef[((int64_t)(blk.mat[1] + I / k) * k + I % k) * n1 + m];
+  }
+  // B operand: rows n = 2r + c (N of them, rows of absent output rows zero), K-major over kk
+  for (int e = tid; e < N * kp2; e += blockDim.x) {
+    const int n = e / kp2, kk = e - n * kp2, r = n >> 1, m3 = kk >> 1;
+    float v = 0.f;
+    if (r < nr && m3 < nh) {
+      const int I = r0 + r;
+      const float2 ed = Eh[((int64_t)(blk.mat[2] + I / k) * k + I % k) * nh + m3];
+      v = (n & 1) ? ((kk & 1) ? ed.x : ed.y) : ((kk & 1) ? -ed.y : ed.x);
+    }
+    uint32_t hi, lo;
+    split_tf32(v, hi, lo);
+    const uint32_t o = umma_off(n, kk, sbo);
+    *reinterpret_cast<uint32_t *>(bh + o) = hi;
+    *reinterpret_cast<uint32_t *>(bl + o) = lo;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                 "r"(tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B, written by these threads, read by the MMAs
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  bool fail = false;
+  if (tid == 0) {
+    // producer of the copies and issuer of the MMAs: stage i = (tile i / 2, half i % 2) in buffer i % S
+    const uint32_t idesc = umma_idesc_tf32(128, N), sbh = smem_addr(bh), sbl = smem_addr(bl);
+    int issued = min(S - 1, nst), committed = -1;
+    for (int i = 0; i < nst; ++i) {
+      const int b = i % S;
+      if (!mbar_wait(smem_addr(full + b), (uint32_t)((i / S) & 1))) { fail = true; break; }
+      tc_fence_after();
+      const int t = i >> 1;
+      const uint32_t d = tmem + (uint32_t)(t * N), sa = smem_addr(ring + (size_t)b * half_b);
+      for (int s = 0; s < ksteps; ++s) {
+        const uint32_t ko = (uint32_t)s * 256u;  // two core matrices along K per MMA (K = 8)
+        if ((i & 1) == 0) {                      // hi half of A: hi * lo, hi * hi
+          umma_tf32(d, umma_desc(sa + ko, sbo), umma_desc(sbl + ko, sbo), idesc, s > 0);
+          umma_tf32(d, umma_desc(sa + ko, sbo), umma_desc(sbh + ko, sbo), idesc, 1);
+        } else {                                 // lo half of A: lo * hi
+          umma_tf32(d, umma_desc(sa + ko, sbo), umma_desc(sbh + ko, sbo), idesc, 1);
+        }
+      }
+      umma_commit(smem_addr(empty + b));
+      committed = i;
+      const int j = i + S - 1;  // next copy, into the buffer stage i - 1 read (its MMAs run behind these)
+      if (j < nst) {
+        const int bj = j % S;
+        if (j >= S && !mbar_wait(smem_addr(empty + bj), (uint32_t)((j / S - 1) & 1))) { fail = true; break; }
+        bulk_copy_g2s(smem_addr(ring + (size_t)bj * half_b), src + (size_t)j * half_b, half_b, smem_addr(full + bj));
+        issued = j + 1;
+      }
+    }
+    if (!fail) {
+      if (!mbar_wait(smem_addr(empty + (nst - 1) % S), (uint32_t)(((nst - 1) / S) & 1))) fail = true;
+    } else {
+      // give the copies and MMAs still in flight a bounded chance to land before the exit
+      for (int i = max(committed + 1, issued - S); i < issued; ++i)
+        if (i >= 0) mbar_wait(smem_addr(full + i % S), (uint32_t)((i / S) & 1));
+      if (committed >= 0) mbar_wait(smem_addr(empty + committed % S), (uint32_t)((committed / S) & 1));
+    }
+  }
+  if (__syncthreads_or(fail)) {
+    if (tid == 0) atomicExch(&g_tc_status, 1);
+    fail = true;
+  }
+  tc_fence_after();
+  if (!fail) {
+    // read the accumulators back: warp w holds TMEM lanes 32 (w % 4) .. + 31, columns
+    // (w / 4) N/2 .. + N/2 - 1, i.e. rows r = (w / 4) N/4 .. + N/4 - 1 of its modes
+    constexpr int HC = N / 2;
+    const int c0 = (warp >> 2) * HC;
+    for (int t = 0; t < mt; ++t) {
+      uint32_t v[HC];
+      const uint32_t addr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(t * N + c0);
+      if constexpr (HC == 8) {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                     : "r"(addr));
+      } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(addr));
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const int q = t * 128 + 32 * (warp & 3) + lane;
+      if (q < nn) {
+#pragma unroll
+        for (int j = 0; j < HC / 2; ++j) {
+          const int r = c0 / 2 + j;
+          if (r < nr) Y1[(size_t)r * nn + q] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+  if (fail) return;
+  eval_stage2_3d<float>(Y1, Y2, E2, nr, K, n1);
+  __syncthreads();
+  eval_stage3_3d<float>(Y2, E1, nr, K, n1, r0, k, nl, lv, u, acc_u);
 }
 
 // ----------------------------------------------------------------------------- evaluation, half-range axis last (3D)
@@ -2173,6 +2478,14 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
   mark(3, 1);
   if ((err = fork_near(4)) != cudaSuccess) return err;
   mark(4, 0);
+  if (D == 3 && sizeof(R) == 4 && e.psi_tc != nullptr && e.n_psi_tc_slots > 0) {
+    // the expansions the tcgen05 evaluation reads, in its operand layout (before the fork below)
+    const int64_t items = (int64_t)((n1 * n1 + 127) / 128) * (eval6_kpad(nh) / 4) * 128 * e.n_psi_tc_slots;
+    const unsigned g = (unsigned)std::min<int64_t>((items + 255) / 256, 152 * 16);
+    psi_tc_kernel<<<g, 256, 0, st>>>(reinterpret_cast<const float2 *>(eval_src),
+                                     static_cast<unsigned char *>(e.psi_tc), n1, nh, ss, e.n_psi_tc_slots);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
   Spread es(e, st);
   if (e.n_e1 > 0) {
     const size_t esm = eval_smem_bytes(D, e.Kmax_e1, n1, sizeof(R) == 4);
@@ -2194,6 +2507,18 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
                                                    reinterpret_cast<const float2 *>(e.Ef),
                                                    reinterpret_cast<const float2 *>(e.Eh),
                                                    reinterpret_cast<const float2 *>(eval_src), u, e.k, n1, nh, ss);
+      if ((err = cudaGetLastError()) != cudaSuccess) return err;
+      continue;
+    }
+    if (D == 3 && lr.tensor == 4 && sizeof(R) == 4 && e.psi_tc != nullptr) {  // stage 1 on tcgen05
+      auto k6 = lr.rows <= 4 ? eval6_kernel<4> : lr.rows <= 8 ? eval6_kernel<8> : eval6_kernel<16>;
+      const int rows6 = lr.rows <= 4 ? 4 : lr.rows <= 8 ? 8 : 16;
+      if ((err = cudaFuncSetAttribute(k6, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) != cudaSuccess)
+        return err;
+      k6<<<dim3((unsigned)lr.count, (unsigned)((lr.K + rows6 - 1) / rows6)), 256, lr.smem, es.next()>>>(
+          e.e2_blocks + lr.first, e.eval_leaves, reinterpret_cast<const float2 *>(e.Ef),
+          reinterpret_cast<const float2 *>(e.Eh), static_cast<const unsigned char *>(e.psi_tc), u, e.k, n1, nh,
+          lr.tmem_cols);
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
       continue;
     }
@@ -2226,8 +2551,10 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
       continue;
     }
-    // lr.rows rows of a block per CTA
-    auto kern = lr.tensor ? (lr.rows <= 4   ? eval2_kernel<D, R, 4, true>
+    // lr.rows rows of a block per CTA (tcgen05 ranges without the operand copy of the expansions, as
+    // in the allocation-free call, take the CUDA-core kernel)
+    const bool tc_fallback = lr.tensor == 4;
+    auto kern = (lr.tensor && !tc_fallback) ? (lr.rows <= 4   ? eval2_kernel<D, R, 4, true>
                              : lr.rows <= 8 ? eval2_kernel<D, R, 8, true>
                                             : eval2_kernel<D, R, 16, true>)
                           : (lr.rows <= 4   ? eval2_kernel<D, R, 4>
@@ -2235,10 +2562,10 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
                                             : eval2_kernel<D, R, 16>);
     const int rows = lr.rows <= 4 ? 4 : lr.rows <= 8 ? 8 : 16;
     const unsigned chunks = (unsigned)((lr.K + rows - 1) / rows);
-    if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) !=
-        cudaSuccess)
+    const size_t esm2 = tc_fallback ? eval2_bytes(D, lr.K, n1, nh, sizeof(C), rows) : lr.smem;
+    if ((err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm2)) != cudaSuccess)
       return err;
-    kern<<<dim3((unsigned)lr.count, chunks), 256, lr.smem, es.next()>>>(
+    kern<<<dim3((unsigned)lr.count, chunks), 256, esm2, es.next()>>>(
         e.e2_blocks + lr.first, e.eval_leaves, reinterpret_cast<const C *>(e.Ef), reinterpret_cast<const C *>(e.Eh),
         eval_src, u, e.k, n1, nh, ss);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
@@ -2255,6 +2582,7 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
 int launches_per_transform(const ExecDesc &e) {
   int n = 0;
   n += (e.d == 3 && e.prec == 1 && e.n_pack > 0);  // sigma packing
+  n += (e.d == 3 && e.prec == 1 && e.n_psi_tc_slots > 0);  // tcgen05 operand copy of the expansions
   n += (e.n_f1 > 0) + (int)e.f2_ranges.size() + (e.n_e1 > 0) + (int)e.e2_ranges.size();  // form + evaluate
   for (const ShiftStep &s : e.merge) n += s.n > 0;
   for (const ShiftStep &s : e.push) n += s.n > 0;
@@ -2266,6 +2594,18 @@ int launches_per_transform(const ExecDesc &e) {
 cudaError_t run_transform(const ExecDesc &e, const double *sigma, double *u, cudaStream_t stream) {
   if (e.d == 3) return e.prec ? run_typed<3, float>(e, sigma, u, stream) : run_typed<3, double>(e, sigma, u, stream);
   return e.prec ? run_typed<2, float>(e, sigma, u, stream) : run_typed<2, double>(e, sigma, u, stream);
+}
+
+cudaError_t read_tc_status(int *status) {
+  int v = 0;
+  cudaError_t err = cudaMemcpyFromSymbol(&v, g_tc_status, sizeof(int));
+  if (err != cudaSuccess) return err;
+  if (v != 0) {
+    const int zero = 0;
+    if ((err = cudaMemcpyToSymbol(g_tc_status, &zero, sizeof(int))) != cudaSuccess) return err;
+  }
+  *status = v;
+  return cudaSuccess;
 }
 
 // ----------------------------------------------------------------------------- allocation-free variant
@@ -2315,6 +2655,8 @@ cudaError_t run_transform_noalloc(const ExecDesc &e, const double *sigma, double
   f.phi = base;
   f.psi = static_cast<unsigned char *>(base) + psi_off;
   f.sigp = nullptr;  // no packed sigma: the form kernels read sigma itself
+  f.psi_tc = nullptr;  // no operand copy of the expansions: the CUDA-core evaluation throughout
+  f.n_psi_tc_slots = 0;
   f.events = nullptr;
   return run_transform(f, sigma, u, stream);
 }

@@ -125,6 +125,7 @@ struct fgt_plan {
   bool tc_eval = false;     // split precision: evaluate with the tensor-core kernel (FGT_TC_EVAL=1)
   bool tc_eval4 = false;    // split precision: stages 2-3 of the evaluation on the tensor cores
   bool eval5 = false;       // 3D: evaluation with the half-range axis contracted last
+  bool tc_eval6 = false;    // split precision, 3D, K <= 16: evaluation stage 1 on tcgen05 (FGT_TC_EVAL6=1)
   cudaStream_t side[fgt::kSides] = {};     // near field and concurrent per-size launches
   cudaEvent_t fork_ev[fgt::kSides] = {}, join_ev[fgt::kSides] = {};
   DevPack host_pack;        // host copy of the uploaded lists and tables (kept for host-only plans)
@@ -727,6 +728,32 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
       }
       const bool chunked = b.K > 16 && d == 3 && (P.prec == FGT_PREC_SPLIT || ex.tc64);
       const int rows = b.K <= 8 ? 8 : b.K <= 16 ? (P.prec == FGT_PREC_SPLIT && d == 3 ? rows16 : 16) : rows32;
+      // split precision, 3D, K <= 16: stage 1 on tcgen05 when its accumulators fit tensor memory;
+      // shared memory padded so that the CTAs an SM can hold never ask for more than its 512 columns
+      const int tc6_cols = fgt::eval6_tmem_cols(n1, rows);
+      if (d == 3 && P.prec == FGT_PREC_SPLIT && P.tc_eval6 && !P.tc_eval && !P.tc_eval4 && b.K <= 16 &&
+          tc6_cols > 0 && fgt::eval6_kpad(nh) <= fgt::kEval6MaxKp2) {
+        size_t sm6 = fgt::eval6_bytes(b.K, n1, nh, rows);
+        // CTAs an SM holds: 228 KB of shared memory, 1 KB reserved per CTA, at most 8 of 256 threads
+        auto ctas = [](size_t b) { return std::min<size_t>(8, 233472 / (b + 1024)); };
+        while (ctas(sm6) * (size_t)tc6_cols > 512) sm6 += 1024;
+        if (sm6 <= (size_t)smax) {
+          if (ex.e2_ranges.empty() || ex.e2_ranges.back().K != b.K) {
+            fgt::LaunchRange lr;
+            lr.first = (int)e2.size();
+            lr.count = 0;
+            lr.K = b.K;
+            lr.rows = rows;
+            lr.smem = sm6;
+            lr.tensor = 4;
+            lr.tmem_cols = tc6_cols;
+            ex.e2_ranges.push_back(lr);
+          }
+          e2.push_back(b);
+          ex.e2_ranges.back().count++;
+          continue;
+        }
+      }
       const size_t eb = (tensor_eval && !chunked) ? fgt::eval3_bytes(b.K, n1, nh)
                                                   : fgt::eval2_bytes(d, b.K, n1, nh, csz, rows);
       if ((b.K <= 16 || chunked) && eb <= (size_t)smax) {
@@ -1138,13 +1165,20 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   const size_t phi_bytes = slot_bytes * (size_t)ex.n_phi_slots, psi_bytes = slot_bytes * (size_t)ex.n_psi_slots;
   const size_t psi_off = (phi_bytes + 255) & ~(size_t)255, sigp_off = (psi_off + psi_bytes + 255) & ~(size_t)255;
   const size_t sigp_bytes = sizeof(float) * (size_t)ex.n_pack * P.np();
+  // tcgen05 evaluation: the expansions it reads, once more in the tensor cores' operand layout
+  bool use_tc6 = false;
+  for (const fgt::LaunchRange &lr : ex.e2_ranges) use_tc6 = use_tc6 || lr.tensor == 4;
+  const int64_t tc6_slots = P.fourier ? ex.n_phi_slots : ex.n_psi_slots;
+  const size_t ptc_off = (sigp_off + sigp_bytes + 255) & ~(size_t)255;
+  const size_t ptc_bytes = use_tc6 ? fgt::eval6_slot_bytes(n1, nh) * (size_t)tc6_slots : 0;
+  ex.n_psi_tc_slots = use_tc6 ? tc6_slots : 0;
   fill_flops(P, ex, blocks, merge_h.size() + push_h.size() ? [&] {
     int64_t sf = 0;
     for (auto &s : merge_h) sf += 8 * (int64_t)s.items.size() * nc * ex.slot_size;
     for (auto &s : push_h) sf += 8 * (int64_t)s.items.size() * nc * ex.slot_size;
     return sf;
   }() : 0, anchors.size());
-  P.info.device_bytes = (int64_t)(pack.size + sigp_off + sigp_bytes);
+  P.info.device_bytes = (int64_t)(pack.size + ptc_off + ptc_bytes);
   if (!upload) {
     P.ex = ex;
     P.host_pack = std::move(pack);
@@ -1161,20 +1195,21 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
       e = cudaMemcpy((char *)P.dev + pt.first, pt.second.data(), pt.second.size(), cudaMemcpyHostToDevice);
       if (e != cudaSuccess) return cuda_fail(e, "upload");
     }
-  P.work_bytes = sigp_off + sigp_bytes;
+  P.work_bytes = ptc_off + ptc_bytes;
   if (P.work_bytes) {
     e = cudaMalloc(&P.work, P.work_bytes);
     if (e != cudaSuccess) {
       P.work = nullptr;
       P.work_bytes = 0;
       cudaGetLastError();
-      return fail(FGT_ERR_OOM, "expansion workspace of " + std::to_string(sigp_off + sigp_bytes) + " bytes");
+      return fail(FGT_ERR_OOM, "expansion workspace of " + std::to_string(ptc_off + ptc_bytes) + " bytes");
     }
   }
   auto at = [&](size_t off) { return (const void *)((const char *)P.dev + off); };
   ex.phi = P.work;
   ex.psi = (char *)P.work + psi_off;
   ex.sigp = sigp_bytes ? (float *)((char *)P.work + sigp_off) : nullptr;
+  ex.psi_tc = ptc_bytes ? (void *)((char *)P.work + ptc_off) : nullptr;
   ex.pack_block = (const int32_t *)at(o_pblock);
   ex.blocks = (const fgt::Block *)at(o_blocks);
   ex.f1_blocks = (const fgt::Block *)at(o_f1);
@@ -1271,6 +1306,11 @@ fgt_status create_impl(int d, double delta, double tol, double eps_pw, int bc, i
     // faster there), in split precision only with FGT_EVAL5=1 (measured no faster: issue-bound)
     const char *e5 = std::getenv("FGT_EVAL5");
     P->eval5 = e5 ? e5[0] == '1' : prec == FGT_PREC_FP64;
+    // evaluation stage 1 on tcgen05 (split precision, K <= 16): opt-in with FGT_TC_EVAL6=1; measured
+    // slower than the CUDA-core kernel on GB300 (stages 2-3 dominate, and every CTA streams the
+    // split expansion, twice the bytes of the FP32 one, from L2)
+    const char *t6 = std::getenv("FGT_TC_EVAL6");
+    P->tc_eval6 = t6 && t6[0] == '1';
   }
   P->n_leaves = tree->n_leaves;
   P->leaf_level.assign(tree->leaf_level, tree->leaf_level + tree->n_leaves);
@@ -1920,6 +1960,12 @@ fgt_status fgt_execute_host(fgt_plan *plan, const double *sigma_host, double *u_
 void fgt_destroy(fgt_plan *plan) { delete plan; }
 
 const char *fgt_last_error(void) { return g_err.c_str(); }
+
+fgt_status fgt_device_status(int *status) {
+  if (!status) return fail(FGT_ERR_ARG, "status is NULL");
+  const cudaError_t e = fgt::read_tc_status(status);
+  return e == cudaSuccess ? FGT_OK : cuda_fail(e, "device status");
+}
 
 fgt_status fgt_gauss_legendre(int k, double *nodes, double *weights) {
   if (k < 1 || k > 64 || !nodes || !weights) return fail(FGT_ERR_ARG, "k must be in [1, 64]");

@@ -288,3 +288,60 @@ def test_paper_periodic_density_k16(delta):
     lam = (np.sqrt(np.pi * delta) * np.exp(-np.pi ** 2 * delta * 16)) ** 3
     ug, _ = gpu_u(3, 16, delta, 1e-10, w.tree, w.sigma, bc=1)
     assert np.abs(ug - lam * w.sigma).max() <= 1e-8 * np.abs(lam * w.sigma).max()
+
+
+def _split_u(monkeypatch, tc6, tree, p, delta, sig, bc=0, tuning=None):
+    monkeypatch.setenv("FGT_TC_EVAL6", "1" if tc6 else "0")
+    plan = F.Plan(3, p, delta, 1e-6, tree.level, tree.coord, bc=bc, prec=F.PREC_SPLIT)
+    if tuning:
+        plan.set_tuning(**tuning)
+    u = plan(torch.from_numpy(np.ascontiguousarray(sig)).cuda()).cpu().numpy()
+    plan.close()
+    return u
+
+
+@pytest.mark.parametrize("p,delta,bc,rows16", [(8, 1e-3, 0, 8), (8, 1e-3, 0, 4), (8, 1e-2, 0, 16), (6, 1e-3, 0, 8),
+                                               (4, 1e-3, 1, 8)])
+def test_split_evaluation_stage1_on_tcgen05(monkeypatch, p, delta, bc, rows16):
+    """Split precision, 3D, blocks of K <= 16: the evaluation whose first contraction runs on the
+    fifth-generation tensor cores (tcgen05.mma kind::tf32 in 3xTF32, accumulators in tensor memory)
+    selected with FGT_TC_EVAL6=1, against the CUDA-core kernel and against the oracle; K = 8 and 16 blocks, rows
+    per CTA 4, 8 and 16, ragged K (p = 6), a periodic tree; no wait of the kernel may run out."""
+    tr = W.random_balanced_tree(3, 21 + p, max_level=4, min_level=2, split_prob=0.2, periodic=bool(bc))
+    sig = W.random_sigma(tr, p, 40 + p)
+    tun = {"eval_rows16": rows16}
+    u6 = _split_u(monkeypatch, True, tr, p, delta, sig, bc, tun)
+    u2 = _split_u(monkeypatch, False, tr, p, delta, sig, bc, tun)
+    assert F.device_status() == 0
+    uo = oracle.box_fgt(3, p, delta, bool(bc), tr.level, tr.coord, sig)
+    scale = np.abs(uo).max()
+    assert np.all(np.isfinite(u6))
+    assert np.abs(u6 - uo).max() <= 10 * 1e-6 * scale
+    # both kernels compute the same FP32-accurate contractions: they agree far inside the bound
+    assert np.abs(u6 - u2).max() <= 1e-6 * scale
+
+
+def test_split_evaluation_tcgen05_full_size_workload(monkeypatch):
+    """The 2.09M-point adaptive benchmark workload (K = 8 and 16 blocks on tcgen05) against the
+    CUDA-core evaluation, every point, and the status word stays clear over repeated calls."""
+    w = W.config_3d_free_adaptive(seed=0, p=8, delta=1e-3)
+    u6 = _split_u(monkeypatch, True, w.tree, w.p, w.delta, w.sigma)
+    u2 = _split_u(monkeypatch, False, w.tree, w.p, w.delta, w.sigma)
+    assert F.device_status() == 0
+    assert np.abs(u6 - u2).max() <= 1e-6 * np.abs(u2).max()
+
+
+def test_split_evaluation_tcgen05_plan_without_operand_copy(monkeypatch):
+    """A plan with tcgen05 evaluation ranges run through the allocation-free call, which has no
+    operand copy of the expansions: those ranges fall back to the CUDA-core kernel, same result."""
+    monkeypatch.setenv("FGT_TC_EVAL6", "1")
+    tr = W.random_balanced_tree(3, 21, max_level=4, min_level=2, split_prob=0.2)
+    s = torch.from_numpy(W.random_sigma(tr, 4, 13)).cuda()
+    plan = F.Plan(3, 4, 1e-3, 1e-6, tr.level, tr.coord, prec=F.PREC_SPLIT)
+    ref = plan(s)
+    out = torch.empty_like(s)
+    plan.execute_noalloc(s, out)
+    torch.cuda.synchronize()
+    assert F.device_status() == 0
+    assert (out - ref).abs().max().item() <= 1e-6 * ref.abs().max().item()
+    plan.close()
