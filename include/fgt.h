@@ -310,6 +310,10 @@ const char *fgt_last_error(void);
  * ran out since the last call, 1: one did) and clears it.  It synchronises with the device.
  * FGT_ERR_ARG if status is NULL, FGT_ERR_CUDA if the copy fails. */
 fgt_status fgt_device_status(int *status);
+/* Self-test of that time-out path (no counterpart in the paper): launches one thread that waits
+ * about a millisecond on an mbarrier nothing completes, so that it gives up and sets the status word;
+ * the next fgt_device_status returns 1.  Faults nothing and hangs nothing.  Synchronous. */
+fgt_status fgt_selftest_tc_timeout(void);
 
 /* ---- Host-side building blocks of the 1D tables (Section 2.4), exposed for tests ---- */
 

@@ -128,6 +128,7 @@ def lib():
             L.fgt_destroy.restype = None
             L.fgt_last_error.restype = ctypes.c_char_p
             L.fgt_device_status.argtypes = [vp]
+            L.fgt_selftest_tc_timeout.argtypes = []
             L.fgt_gauss_legendre.argtypes = [i32, vp, vp]
             L.fgt_params.argtypes = [dbl, dbl, i32, vp, vp, vp, vp, vp, vp]
             L.fgt_nf_for_range.argtypes = [dbl, dbl]
@@ -160,6 +161,11 @@ def device_status() -> int:
     v = ctypes.c_int(0)
     _check(lib().fgt_device_status(ctypes.byref(v)))
     return v.value
+
+
+def selftest_tc_timeout() -> None:
+    """fgt_selftest_tc_timeout: a bounded wait that runs out on purpose and sets the status word."""
+    _check(lib().fgt_selftest_tc_timeout())
 
 
 def _tree_struct(d, k, level, coord):

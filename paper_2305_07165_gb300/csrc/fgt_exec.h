@@ -116,6 +116,9 @@ cudaError_t run_transform(const ExecDesc &e, const double *sigma, double *u, cud
 // Reads and clears the status word of the tcgen05 kernels: 1 when a wait on the tensor cores ran
 // out since the last read (the affected blocks were skipped), else 0.  Synchronous.
 cudaError_t read_tc_status(int *status);
+// Runs a kernel whose only wait (about a millisecond) is on an mbarrier that nothing completes, so
+// that it sets the status word; synchronous.
+cudaError_t selftest_tc_timeout();
 
 // Allocation-free execution: the expansion workspace lives in a fixed device array of
 // kNoallocScratchBytes inside the library instead of the plan's own buffers.  The first call

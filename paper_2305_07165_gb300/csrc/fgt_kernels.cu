@@ -1228,9 +1228,9 @@ __device__ __forceinline__ void umma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
 
-// Waits for the completion of the mbarrier phase of the given parity; gives up after about
-// 2^31 clocks (about one second) and returns false.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+// Waits for the completion of the mbarrier phase of the given parity; gives up after `limit`
+// clocks (by default 2^31, about one second) and returns false.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit = 1LL << 31) {
   const long long t0 = clock64();
   for (;;) {
     uint32_t ok;
@@ -1240,8 +1240,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
         : "r"(mbar), "r"(parity)
         : "memory");
     if (ok) return true;
-    if (clock64() - t0 > (1LL << 31)) return false;
+    if (clock64() - t0 > limit) return false;
   }
+}
+
+// Self-test of the time-out path: one thread waits, `clocks` at most, on an mbarrier that nothing
+// completes, and sets the status word as the tensor-core kernels do when their waits run out.
+__global__ void wait_timeout_selftest_kernel(long long clocks) {
+  __shared__ uint64_t bar;
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&bar)), "r"(1));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (!mbar_wait(smem_addr(&bar), 0, clocks)) atomicExch(&g_tc_status, 1);
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -2594,6 +2603,12 @@ int launches_per_transform(const ExecDesc &e) {
 cudaError_t run_transform(const ExecDesc &e, const double *sigma, double *u, cudaStream_t stream) {
   if (e.d == 3) return e.prec ? run_typed<3, float>(e, sigma, u, stream) : run_typed<3, double>(e, sigma, u, stream);
   return e.prec ? run_typed<2, float>(e, sigma, u, stream) : run_typed<2, double>(e, sigma, u, stream);
+}
+
+cudaError_t selftest_tc_timeout() {
+  wait_timeout_selftest_kernel<<<1, 1>>>(1LL << 21);  // about a millisecond
+  cudaError_t err = cudaGetLastError();
+  return err != cudaSuccess ? err : cudaDeviceSynchronize();
 }
 
 cudaError_t read_tc_status(int *status) {

@@ -1961,6 +1961,11 @@ void fgt_destroy(fgt_plan *plan) { delete plan; }
 
 const char *fgt_last_error(void) { return g_err.c_str(); }
 
+fgt_status fgt_selftest_tc_timeout(void) {
+  const cudaError_t e = fgt::selftest_tc_timeout();
+  return e == cudaSuccess ? FGT_OK : cuda_fail(e, "time-out self-test");
+}
+
 fgt_status fgt_device_status(int *status) {
   if (!status) return fail(FGT_ERR_ARG, "status is NULL");
   const cudaError_t e = fgt::read_tc_status(status);

@@ -345,3 +345,15 @@ def test_split_evaluation_tcgen05_plan_without_operand_copy(monkeypatch):
     assert F.device_status() == 0
     assert (out - ref).abs().max().item() <= 1e-6 * ref.abs().max().item()
     plan.close()
+
+
+def test_tensor_core_wait_time_out_is_reported():
+    """The time-out path of the tcgen05 kernels' waits: a wait that nothing completes gives up after
+    its limit and sets the device status word, which the host reads once and which then reads clear;
+    the context stays usable (a transform right after matches the oracle)."""
+    assert F.device_status() == 0
+    F.selftest_tc_timeout()
+    assert F.device_status() == 1
+    assert F.device_status() == 0
+    tr = W.random_balanced_tree(3, 21, max_level=4, min_level=2, split_prob=0.2)
+    check(3, 4, 1e-3, 1e-8, tr, W.random_sigma(tr, 4, 13))
