@@ -463,6 +463,7 @@ def main():
     ap.add_argument("--workload", default="adaptive3d", choices=sorted(WORKLOADS))
     ap.add_argument("--no-batch", action="store_true", help="skip the batched and serving sections")
     ap.add_argument("--no-sweep", action="store_true", help="skip the delta sweep and the periodic workload")
+    ap.add_argument("--no-autotune", action="store_true", help="time the default launch shapes")
     ap.add_argument("--forms", default="split,fp64,fp64_1e-10,fp64tc,fp64tc_1e-10",
                     help="comma list of " + ", ".join(FORMS) + "; the first one is the headline")
     ap.add_argument("--point-fgt-only", action="store_true",
@@ -498,6 +499,8 @@ def main():
     for name, tol, prec in forms:
         plan = F.Plan(w.d, w.p, w.delta, tol, w.tree.level, w.tree.coord, bc=int(w.periodic), prec=prec)
         info = plan.info()
+        # launch shapes from the library's autotuner, picked on this input before anything is timed
+        tuned = None if args.no_autotune else plan.autotune(sigma, out, reps=3)
         is_head = head is None
         plan.set_profiling(True)
         if is_head:
@@ -522,7 +525,7 @@ def main():
         results[name] = dict(points_per_s=whole_job_rate(w.n_points, args.steps, world, tot / 1e3),
                              ms_per_step=tot / args.steps, p50_ms=float(np.percentile(times, 50)),
                              p99_ms=float(np.percentile(times, 99)), cutoff_level=info["cutoff_level"],
-                             n_f=info["n_f"], launches=info["launches"], roofline=form_roofline)
+                             n_f=info["n_f"], launches=info["launches"], roofline=form_roofline, tuning=tuned)
 
     batched = serving = None
     if not args.no_batch and rank == 0:
