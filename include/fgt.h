@@ -178,6 +178,19 @@ fgt_status fgt_execute_noalloc(fgt_plan *plan, const double *sigma_dev, double *
  * copies in, transforms, copies out on `stream` and synchronises it. */
 fgt_status fgt_execute_host(fgt_plan *plan, const double *sigma_host, double *u_host, void *stream);
 
+/* End to end, pipelined: the host-buffer transform of fgt_execute_host without the wait, so that
+ * successive calls on one plan overlap.  Each call copies sigma_host in on the plan's copy-in
+ * stream (into one of two device staging buffers, once the call two before it has copied its
+ * result out of that buffer), transforms on `stream` once its input has arrived (calls on one plan
+ * run their transforms in call order), and copies u_host out on the plan's copy-out stream.  So a
+ * call's copy-in overlaps the previous call's transform, and its copy-out the next call's.
+ * sigma_host and u_host (pinned for full copy speed) must stay untouched until fgt_host_sync
+ * returns.  fgt_host_sync(plan) waits for every pipelined call on the plan to have written its
+ * u_host.  Errors: as fgt_execute_host; FGT_ERR_OOM if the staging buffers or streams cannot be
+ * created. */
+fgt_status fgt_execute_host_async(fgt_plan *plan, const double *sigma_host, double *u_host, void *stream);
+fgt_status fgt_host_sync(fgt_plan *plan);
+
 /* ---- Batched execution: many independent transforms in one launch ----
  * The paper transforms one density at a time; batching is how the GPU is kept busy with many
  * small transforms of uneven depth, k and delta.  fgt_batch_create takes n prepared device

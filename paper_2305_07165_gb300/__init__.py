@@ -95,6 +95,8 @@ def lib():
             L.fgt_execute.argtypes = [vp, vp, vp]
             L.fgt_execute_async.argtypes = [vp, vp, vp, vp]
             L.fgt_execute_host.argtypes = [vp, vp, vp, vp]
+            L.fgt_execute_host_async.argtypes = [vp, vp, vp, vp]
+            L.fgt_host_sync.argtypes = [vp]
             L.fgt_execute_noalloc.argtypes = [vp, vp, vp, vp]
             L.fgt_execute_noalloc.restype = ctypes.c_int
             L.fgt_batch_create.argtypes = [vp, i32, vp]
@@ -137,7 +139,7 @@ def lib():
             L.fgt_spherical_bessel.argtypes = [dbl, i32, vp]
             L.fgt_legendre_fourier_integrals.argtypes = [dbl, i32, vp, vp]
             for name in ("fgt_plan_create_ex", "fgt_plan_create_host", "fgt_plan_host_array", "fgt_plan_analyze", "fgt_plan_get_info", "fgt_plan_set_precision",
-                         "fgt_plan_set_mode", "fgt_execute", "fgt_execute_async", "fgt_execute_host",
+                         "fgt_plan_set_mode", "fgt_execute", "fgt_execute_async", "fgt_execute_host", "fgt_execute_host_async", "fgt_host_sync",
                          "fgt_gauss_legendre", "fgt_params", "fgt_legendre_gauss_integrals",
                          "fgt_spherical_bessel", "fgt_legendre_fourier_integrals", "fgt_plan_set_profiling",
                          "fgt_plan_read_profile", "fgt_plan_autotune", "fgt_plan_get_tuning",
@@ -360,6 +362,23 @@ class Plan:
         s = stream if stream is not None else torch.cuda.current_stream()
         _check(lib().fgt_execute_host(self._h, sigma.data_ptr(), out.data_ptr(), ctypes.c_void_p(s.cuda_stream)))
         return out
+
+    def execute_host_async(self, sigma, out, stream=None):
+        """Pipelined host-buffer transform (fgt_execute_host_async): returns at once; sigma and out
+        stay untouched until host_sync().  Successive calls overlap copies with transforms."""
+        import torch
+        for x, n in ((sigma, "sigma"), (out, "out")):
+            want = self.n_out_points if n == "out" else self.n_points
+            if (not isinstance(x, torch.Tensor) or x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous()
+                    or x.numel() != want):
+                raise TypeError(f"{n} must be a contiguous host float64 tensor of {want} values")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(lib().fgt_execute_host_async(self._h, sigma.data_ptr(), out.data_ptr(), ctypes.c_void_p(s.cuda_stream)))
+        return out
+
+    def host_sync(self):
+        """fgt_host_sync: wait until every pipelined host call on this plan has written its output."""
+        _check(lib().fgt_host_sync(self._h))
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -120,6 +120,14 @@ struct fgt_plan {
   void *work = nullptr;
   size_t work_bytes = 0;
   double *stage = nullptr;  // host-path staging: sigma [n_leaves k^d], then u [n_targets k^d]
+  // pipelined host path: copy-in and copy-out streams, two staging slots (sigma then u each), per
+  // slot the events "input arrived", "transform done" and "output copied out"
+  cudaStream_t hp_in = nullptr, hp_out = nullptr;
+  cudaEvent_t hp_in_ev[2] = {}, hp_done_ev[2] = {}, hp_free_ev[2] = {};
+  double *hp_stage = nullptr;
+  size_t hp_elems = 0;     // per slot
+  int hp_next = 0;         // slot of the next call
+  bool hp_used[2] = {false, false};
   size_t stage_elems = 0;
   bool host_only = false;   // planned without a device (inspection only)
   bool tc_eval = false;     // split precision: evaluate with the tensor-core kernel (FGT_TC_EVAL=1)
@@ -144,6 +152,7 @@ struct fgt_plan {
   }
   int np() const { return d == 3 ? k * k * k : k * k; }
   ~fgt_plan() {
+    if (hp_out) cudaStreamSynchronize(hp_out);  // pipelined host calls still copying out
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (int i = 0; i < fgt::kSides; ++i) {
       if (fork_ev[i]) cudaEventDestroy(fork_ev[i]);
@@ -153,6 +162,14 @@ struct fgt_plan {
     if (dev) cudaFree(dev);
     if (work) cudaFree(work);
     if (stage) cudaFree(stage);
+    for (int i = 0; i < 2; ++i) {
+      if (hp_in_ev[i]) cudaEventDestroy(hp_in_ev[i]);
+      if (hp_done_ev[i]) cudaEventDestroy(hp_done_ev[i]);
+      if (hp_free_ev[i]) cudaEventDestroy(hp_free_ev[i]);
+    }
+    if (hp_in) cudaStreamDestroy(hp_in);
+    if (hp_out) cudaStreamDestroy(hp_out);
+    if (hp_stage) cudaFree(hp_stage);
   }
 };
 
@@ -1955,6 +1972,68 @@ fgt_status fgt_execute_host(fgt_plan *plan, const double *sigma_host, double *u_
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "transform");
   return FGT_OK;
+}
+
+fgt_status fgt_execute_host_async(fgt_plan *plan, const double *sigma_host, double *u_host, void *stream) {
+  if (!plan || !sigma_host || !u_host) return fail(FGT_ERR_ARG, "NULL argument");
+  if (plan->host_only) return fail(FGT_ERR_STATE, "host-only plan cannot execute");
+  const size_t n = (size_t)plan->n_leaves * plan->np(), nu = (size_t)plan->n_targets() * plan->np();
+  cudaError_t e = cudaSuccess;
+  if (plan->hp_stage && plan->hp_elems < n + nu) {
+    if ((e = cudaStreamSynchronize(plan->hp_out)) != cudaSuccess) return cuda_fail(e, "host pipeline");
+    cudaFree(plan->hp_stage);
+    plan->hp_stage = nullptr;
+    plan->hp_used[0] = plan->hp_used[1] = false;
+  }
+  if (!plan->hp_in) {
+    if (cudaStreamCreateWithFlags(&plan->hp_in, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&plan->hp_out, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FGT_ERR_OOM, "host pipeline streams");
+    }
+    for (int i = 0; i < 2; ++i)
+      if (cudaEventCreateWithFlags(&plan->hp_in_ev[i], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&plan->hp_done_ev[i], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&plan->hp_free_ev[i], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FGT_ERR_OOM, "host pipeline events");
+      }
+  }
+  if (!plan->hp_stage) {
+    e = cudaMalloc(&plan->hp_stage, 2 * sizeof(double) * (n + nu));
+    if (e != cudaSuccess) { plan->hp_stage = nullptr; cudaGetLastError(); return fail(FGT_ERR_OOM, "staging buffers"); }
+    plan->hp_elems = n + nu;
+  }
+  const int slot = plan->hp_next;
+  plan->hp_next ^= 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  double *sd = plan->hp_stage + (size_t)slot * plan->hp_elems, *ud = sd + n;
+  // copy in, once the call that last used this slot has copied its result out
+  if (plan->hp_used[slot] && (e = cudaStreamWaitEvent(plan->hp_in, plan->hp_free_ev[slot], 0)) != cudaSuccess)
+    return cuda_fail(e, "host pipeline");
+  if ((e = cudaMemcpyAsync(sd, sigma_host, sizeof(double) * n, cudaMemcpyHostToDevice, plan->hp_in)) != cudaSuccess)
+    return cuda_fail(e, "copy in");
+  if ((e = cudaEventRecord(plan->hp_in_ev[slot], plan->hp_in)) != cudaSuccess) return cuda_fail(e, "host pipeline");
+  // transform on the caller's stream once the input is there
+  if ((e = cudaStreamWaitEvent(st, plan->hp_in_ev[slot], 0)) != cudaSuccess) return cuda_fail(e, "host pipeline");
+  fgt_status s = fgt_execute_async(plan, sd, ud, stream);
+  if (s != FGT_OK) return s;
+  if ((e = cudaEventRecord(plan->hp_done_ev[slot], st)) != cudaSuccess) return cuda_fail(e, "host pipeline");
+  // copy out on the copy-out stream, then free the slot
+  if ((e = cudaStreamWaitEvent(plan->hp_out, plan->hp_done_ev[slot], 0)) != cudaSuccess)
+    return cuda_fail(e, "host pipeline");
+  if ((e = cudaMemcpyAsync(u_host, ud, sizeof(double) * nu, cudaMemcpyDeviceToHost, plan->hp_out)) != cudaSuccess)
+    return cuda_fail(e, "copy out");
+  if ((e = cudaEventRecord(plan->hp_free_ev[slot], plan->hp_out)) != cudaSuccess) return cuda_fail(e, "host pipeline");
+  plan->hp_used[slot] = true;
+  return FGT_OK;
+}
+
+fgt_status fgt_host_sync(fgt_plan *plan) {
+  if (!plan) return fail(FGT_ERR_ARG, "NULL plan");
+  if (!plan->hp_out) return FGT_OK;
+  const cudaError_t e = cudaStreamSynchronize(plan->hp_out);
+  return e == cudaSuccess ? FGT_OK : cuda_fail(e, "host pipeline");
 }
 
 void fgt_destroy(fgt_plan *plan) { delete plan; }
