@@ -2102,8 +2102,9 @@ fgt_status fgt_legendre_fourier_integrals(double t, int nmax, double *re, double
 // ============================================================================ batched execution
 //
 // Many independent transforms in one launch: the kernel sequence of every plan is captured
-// once into a CUDA graph in which each transform is its own branch (branches rotate over a
-// small pool of capture streams), so the device runs the transforms' kernels concurrently and
+// once into a CUDA graph in which each transform is a branch (branches rotate over a small pool of
+// capture streams, which chains the branches sharing one), so the device runs up to that many
+// transforms concurrently and
 // the host issues a single graph launch.  The graph is rebuilt only when the input / output
 // pointers change.
 
@@ -2179,6 +2180,9 @@ fgt_status fgt_batch_create(fgt_plan *const *plans, int n, fgt_batch **out) {
     }
     b->plans.push_back(p);
   }
+  // 16 capture streams: transforms sharing a stream are chained in the graph, so at most 16 run
+  // at once; one stream per transform (every branch free) measured 1.9x slower on 256 transforms
+  // (their working sets compete in L2)
   const int nstreams = std::min(n, 16);
   cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   for (int i = 0; i < nstreams && e == cudaSuccess; ++i) {
