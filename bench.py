@@ -117,8 +117,16 @@ def roofline_of(info, prof, nprof, prec, traffic_key=None):
     fp32 = prec == 1 and dom in ("form", "evaluate", "gather")
     peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
     traffic = NCU_TRAFFIC.get(traffic_key + (dom,)) if traffic_key else None
+    # every phase against its own ALU peak (FP32 for the split form's plane-wave phases, FP64 else)
+    phases = {}
+    for ph, fl in phase_flops.items():
+        t = prof.get(ph, 0.0) / n
+        if fl > 0 and t > 0:
+            pk = FP32_PEAK_TFLOPS if (prec == 1 and ph in ("form", "evaluate", "gather")) else FP64_PEAK_TFLOPS
+            a = fl / (t / 1e3) / 1e12
+            phases[ph] = {"ms": t, "achieved_tflops": a, "peak_tflops": pk, "frac": a / pk}
     return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic,
+            "frac": achieved / peak, "traffic": traffic, "phases": phases,
             "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if fp32 else
                             "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"),
             "phase_ms_per_step": {k: v / n for k, v in prof.items()}}
