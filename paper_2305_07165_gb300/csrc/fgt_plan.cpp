@@ -420,11 +420,19 @@ void fill_flops(fgt_plan &P, const fgt::ExecDesc &ex, const std::vector<fgt::Blo
   I.n_direct_pairs = P.n_near_pairs;
   I.n_gather_pairs = P.n_gather_pairs;
   int64_t ff = 0, ef = 0;
+  // evaluation flops in the contraction order of the kernel that takes the block: the half-range
+  // axis last (eval5 ranges) or first (all others)
+  auto half_range_last = [&](int64_t K) {
+    for (const fgt::LaunchRange &lr : ex.e2_ranges)
+      if (lr.K == K) return lr.tensor == 3;
+    return false;
+  };
   for (const fgt::Block &b : blocks) {
     const int64_t K = b.K;
     if (d == 3) {
       ff += 4 * nh * K * K * K + 8 * nh * n1 * K * K + 8 * nh * n1 * n1 * K;
-      ef += K * (8 * nh * n1 * n1 + 8 * K * n1 * n1 + 4 * K * K * n1);
+      ef += half_range_last(K) ? 8 * K * nh * n1 * n1 + 8 * K * K * nh * n1 + 4 * K * K * K * nh
+                               : K * (8 * nh * n1 * n1 + 8 * K * n1 * n1 + 4 * K * K * n1);
     } else {
       ff += 4 * nh * K * K + 8 * nh * n1 * K;
       ef += K * (8 * nh * n1 + 4 * K * n1);
