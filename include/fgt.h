@@ -328,6 +328,17 @@ fgt_status fgt_device_status(int *status);
  * the next fgt_device_status returns 1.  Faults nothing and hangs nothing.  Synchronous. */
 fgt_status fgt_selftest_tc_timeout(void);
 
+/* Bounds-checked build (libfgt_checked.so, compiled with -DFGT_CHECKED; the paper has no
+ * counterpart).  There, every instrumented global access of the kernels (all stores of u, the
+ * expansions and the packed density, the streamed loads of sigma and of the expansions) first
+ * checks that its bytes lie in the buffers registered for the call (sigma, u, the plan's tables and
+ * workspace, or the allocation-free scratch); a failing access is skipped and counted, so an index
+ * error is reported instead of faulting.  Batched graphs run unchecked.  Checks assume one transform
+ * in flight at a time.  This call reads and clears the first failing access's source line (*site)
+ * and the number of failures (*count) since the last call, and sets *checked to 1 in the checked
+ * build (in the normal build: *checked = 0, *site = *count = 0).  Synchronous. */
+fgt_status fgt_check_status(unsigned *site, unsigned *count, int *checked);
+
 /* ---- Host-side building blocks of the 1D tables (Section 2.4), exposed for tests ---- */
 
 /* k-point Gauss-Legendre rule on [-1,1], ascending nodes. 1 <= k <= 64. */

@@ -75,11 +75,14 @@ _lock = threading.Lock()
 
 
 def lib():
-    """Load (building first if the sources are newer) the in-tree libfgt.so."""
+    """Load (building first if the sources are newer) the in-tree libfgt.so, or its bounds-checked
+    build libfgt_checked.so when the environment has FGT_LIB=checked."""
     global _lib
     with _lock:
         if _lib is None:
             path = _build.build()
+            if os.environ.get("FGT_LIB") == "checked":
+                path = _build.CHECKED_LIB
             L = ctypes.CDLL(path)
             vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
             L.fgt_plan_create_ex.argtypes = [i32, dbl, dbl, dbl, i32, i32, i32, ctypes.POINTER(_Tree), vp]
@@ -130,6 +133,7 @@ def lib():
             L.fgt_destroy.restype = None
             L.fgt_last_error.restype = ctypes.c_char_p
             L.fgt_device_status.argtypes = [vp]
+            L.fgt_check_status.argtypes = [vp, vp, vp]
             L.fgt_selftest_tc_timeout.argtypes = []
             L.fgt_gauss_legendre.argtypes = [i32, vp, vp]
             L.fgt_params.argtypes = [dbl, dbl, i32, vp, vp, vp, vp, vp, vp]
@@ -155,6 +159,14 @@ def lib():
 def _check(status):
     if status != 0:
         raise FGTError(status, lib().fgt_last_error().decode(errors="replace"))
+
+
+def check_status() -> dict:
+    """fgt_check_status: in the bounds-checked build, the first failing access's source line and the
+    failure count since the last call (cleared); {"checked": 0, ...} in the normal build."""
+    site, count, checked = ctypes.c_uint(0), ctypes.c_uint(0), ctypes.c_int(0)
+    _check(lib().fgt_check_status(ctypes.byref(site), ctypes.byref(count), ctypes.byref(checked)))
+    return {"checked": checked.value, "site": site.value, "count": count.value}
 
 
 def device_status() -> int:

@@ -1,6 +1,7 @@
-"""Builds libfgt.so in-tree with nvcc for sm_103a (GB300).
+"""Builds libfgt.so in-tree with nvcc for sm_103a (GB300), and libfgt_checked.so (the same
+library with bounds-checked kernels).
 
-Three translation units compiled in parallel, then linked with the CUDA
+Four translation units (the kernels twice) are compiled in parallel, then linked with the CUDA
 runtime.  Used by ``__graft_entry__.build()`` and on first import of the
 package when the library is missing or older than its sources.
 """
@@ -15,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libfgt.so")
+CHECKED_LIB = os.path.join(HERE, "libfgt_checked.so")  # kernels built with -DFGT_CHECKED
 OBJDIR = os.path.join(HERE, "_build")
 SOURCES = ["fgt_kernels.cu", "fgt_plan.cpp", "fgt_tables.cpp"]
 HEADERS = ["fgt_internal.h", "fgt_exec.h", "fgt_tables.h"]
@@ -29,9 +31,9 @@ def _nvcc() -> str:
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(CHECKED_LIB):
         return True
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(CHECKED_LIB))
     deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [os.path.join(INCLUDE, "fgt.h")]
     return any(os.path.getmtime(p) > t for p in deps)
 
@@ -43,9 +45,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OBJDIR, exist_ok=True)
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", f"-I{INCLUDE}"]
 
-    def compile_one(src):
-        obj = os.path.join(OBJDIR, src + ".o")
-        cmd = [nvcc] + common + ARCH + ["-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(job):
+        src, defs = job
+        obj = os.path.join(OBJDIR, src + ("_checked" if defs else "") + ".o")
+        cmd = [nvcc] + common + defs + ARCH + ["-c", os.path.join(CSRC, src), "-o", obj]
         if src.endswith(".cpp"):
             cmd = [nvcc] + common + ["-x", "c++", "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -55,13 +58,17 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stdout, r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([nvcc, "-shared"] + ARCH + objs + ["-o", tmp, "-lcudart"], capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    # the kernels once more with the bounds checks for libfgt_checked.so (same host objects)
+    jobs = [(src, []) for src in SOURCES] + [("fgt_kernels.cu", ["-DFGT_CHECKED"])]
+    with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        objs = list(ex.map(compile_one, jobs))
+    plain, checked = objs[: len(SOURCES)], [objs[-1]] + objs[1: len(SOURCES)]
+    for out, parts in ((LIB, plain), (CHECKED_LIB, checked)):
+        tmp = out + f".tmp{os.getpid()}"
+        r = subprocess.run([nvcc, "-shared"] + ARCH + parts + ["-o", tmp, "-lcudart"], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, out)
     return LIB
 
 

@@ -113,6 +113,14 @@ int launches_per_transform(const ExecDesc &e);
 // Enqueue the whole transform on `stream`.  sigma, u: device FP64 [n_leaves][k^d].
 cudaError_t run_transform(const ExecDesc &e, const double *sigma, double *u, cudaStream_t stream);
 
+// Checked build (-DFGT_CHECKED): the buffers the next kernels on `st` may touch (at most
+// kCheckRanges; n = 0 turns the checks off), and the first failing access's source line and the
+// failure count since the last read (read and cleared; synchronous).  No-ops in the normal build
+// (*checked = 0).  One transform at a time: the ranges are global to the device.
+constexpr int kCheckRanges = 8;
+cudaError_t set_check_ranges(const void *const *base, const size_t *bytes, int n, cudaStream_t st);
+cudaError_t read_check(unsigned *site, unsigned *count, int *checked);
+
 // Reads and clears the status word of the tcgen05 kernels: 1 when a wait on the tensor cores ran
 // out since the last read (the affected blocks were skipped), else 0.  Synchronous.
 cudaError_t read_tc_status(int *status);

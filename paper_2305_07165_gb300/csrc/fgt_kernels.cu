@@ -48,6 +48,39 @@ __device__ __forceinline__ C cmul(C a, C b) {
   return r;
 }
 
+// ----------------------------------------------------------------------------- checked build
+//
+// Built with -DFGT_CHECKED (libfgt_checked.so), every instrumented global access first checks that
+// its bytes lie inside one of the buffers the host registered for the transform (sigma, u, the
+// plan's tables and workspace).  A failing access is skipped, and the first failing site's source
+// line is kept in g_check_word with a count in g_check_count, for the host to read: an
+// out-of-range index becomes a reported error instead of a fault.  With no buffers registered
+// (batched graphs), nothing is checked.  In the normal build FGT_OK_PTR is the constant true.
+#ifdef FGT_CHECKED
+struct CheckRanges {
+  const char *lo[kCheckRanges];
+  const char *hi[kCheckRanges];
+  int n;
+};
+__device__ CheckRanges g_check_ranges;
+__device__ unsigned int g_check_word, g_check_count;
+__device__ __noinline__ bool chk_bytes(const void *p, size_t n, int site) {
+  const CheckRanges &r = g_check_ranges;
+  if (r.n == 0) return true;
+  const char *c = static_cast<const char *>(p);
+  for (int i = 0; i < r.n && i < kCheckRanges; ++i)
+    if (c >= r.lo[i] && c + n <= r.hi[i]) return true;
+  atomicCAS(&g_check_word, 0u, (unsigned)site);
+  atomicAdd(&g_check_count, 1u);
+  return false;
+}
+#define FGT_OK_PTR(p) ::fgt::chk_bytes((const void *)(p), sizeof(*(p)), __LINE__)
+#define FGT_OK_BYTES(p, n) ::fgt::chk_bytes((const void *)(p), (size_t)(n), __LINE__)
+#else
+#define FGT_OK_PTR(p) true
+#define FGT_OK_BYTES(p, n) true
+#endif
+
 // ----------------------------------------------------------------------------- form
 
 template <int D, typename R>
@@ -109,8 +142,10 @@ __global__ void __launch_bounds__(256) form_kernel(const Block *__restrict__ blo
         const C *zp = Z2 + m2 * K + o1 * k;
         for (int j1 = 0; j1 < k; ++j1) cfma(ar, ai, fp[j1], zp[j1]);
       }
-      atomicAdd(&o[idx].x, ar);
-      atomicAdd(&o[idx].y, ai);
+      if (FGT_OK_PTR(&o[idx])) {
+        atomicAdd(&o[idx].x, ar);
+        atomicAdd(&o[idx].y, ai);
+      }
     }
   } else {
     const int kk = k * k;
@@ -139,8 +174,10 @@ __global__ void __launch_bounds__(256) form_kernel(const Block *__restrict__ blo
         const C *zp = Z1 + o1 * k;
         for (int j1 = 0; j1 < k; ++j1) cfma(ar, ai, fp[j1], zp[j1]);
       }
-      atomicAdd(&o[m1].x, ar);
-      atomicAdd(&o[m1].y, ai);
+      if (FGT_OK_PTR(&o[m1])) {
+        atomicAdd(&o[m1].x, ar);
+        atomicAdd(&o[m1].y, ai);
+      }
     }
   }
 }
@@ -199,7 +236,7 @@ __global__ void __launch_bounds__(256) eval_kernel(const Block *__restrict__ blo
         acc = fma(-e.y, y.y, acc);
       }
       double *up = u + lv[(od * nl + o2) * nl + o1] * k3 + (td * k + t2) * k + t1;
-      if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc;
+      if (FGT_OK_PTR(up)) { if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc; }
     }
   } else {
     const int kk = k * k;
@@ -220,7 +257,7 @@ __global__ void __launch_bounds__(256) eval_kernel(const Block *__restrict__ blo
         acc = fma(-e.y, y.y, acc);
       }
       double *up = u + lv[od * nl + o1] * kk + td * k + t1;
-      if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc;
+      if (FGT_OK_PTR(up)) { if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc; }
     }
   }
 }
@@ -318,8 +355,10 @@ __global__ void __launch_bounds__(256) form2_kernel(const Block *__restrict__ bl
           const C *zp = Z2 + ((size_t)g * n1 + m2) * K;
           for (int J1 = 0; J1 < K; ++J1) cfma(ar, ai, fp[J1 * n1], zp[J1]);
         }
-        atomicAdd(&o[idx].x, ar);
-        atomicAdd(&o[idx].y, ai);
+        if (FGT_OK_PTR(&o[idx])) {
+          atomicAdd(&o[idx].x, ar);
+          atomicAdd(&o[idx].y, ai);
+        }
       }
       __syncthreads();
     } else {
@@ -346,8 +385,10 @@ __global__ void __launch_bounds__(256) form2_kernel(const Block *__restrict__ bl
           const C *zp = Z1 + (size_t)g * K;
           for (int J1 = 0; J1 < K; ++J1) cfma(ar, ai, fp[J1 * n1], zp[J1]);
         }
-        atomicAdd(&o[m1].x, ar);
-        atomicAdd(&o[m1].y, ai);
+        if (FGT_OK_PTR(&o[m1])) {
+          atomicAdd(&o[m1].x, ar);
+          atomicAdd(&o[m1].y, ai);
+        }
       }
       __syncthreads();
     }
@@ -536,8 +577,10 @@ __global__ void __launch_bounds__(256) form3_kernel(const Block *__restrict__ bl
           for (int c = 0; c < 2; ++c) {
             const int m1 = c0 * 32 + b * 8 + 2 * (lane & 3) + c;
             if (m1 < n1) {
-              atomicAdd(&o[m2 * n1 + m1].x, acc[2 * b][c]);
-              atomicAdd(&o[m2 * n1 + m1].y, acc[2 * b + 1][c]);
+              if (FGT_OK_PTR(&o[m2 * n1 + m1])) {
+                atomicAdd(&o[m2 * n1 + m1].x, acc[2 * b][c]);
+                atomicAdd(&o[m2 * n1 + m1].y, acc[2 * b + 1][c]);
+              }
             }
           }
       }
@@ -576,8 +619,10 @@ __global__ void __launch_bounds__(256) form3_kernel(const Block *__restrict__ bl
         for (int j = 0; j < 4; ++j) {
           const int m2 = b2 * 4 + i, m1 = b1 * 4 + j;
           if (m2 < n1 && m1 < n1) {
-            atomicAdd(&o[m2 * n1 + m1].x, ar[i][j]);
-            atomicAdd(&o[m2 * n1 + m1].y, ai[i][j]);
+            if (FGT_OK_PTR(&o[m2 * n1 + m1])) {
+              atomicAdd(&o[m2 * n1 + m1].x, ar[i][j]);
+              atomicAdd(&o[m2 * n1 + m1].y, ai[i][j]);
+            }
           }
         }
     }
@@ -643,7 +688,8 @@ __global__ void __launch_bounds__(256) sigma_pack_kernel(const Block *__restrict
   float *dst = sigp + b.leaf0 * kp;
   for (int node = threadIdx.x; node < kp; node += blockDim.x) {
     const int j1 = node % k, j2 = (node / k) % k, j3 = node / (k * k);
-    dst[((o3 * k + j3) * K + (o2 * k + j2)) * K + (o1 * k + j1)] = (float)__ldg(src + node);
+    float *dp = dst + ((o3 * k + j3) * K + (o2 * k + j2)) * K + (o1 * k + j1);
+    if (FGT_OK_PTR(dp) && FGT_OK_PTR(src + node)) *dp = (float)__ldg(src + node);
   }
 }
 
@@ -919,7 +965,7 @@ __global__ void __launch_bounds__(256, BIG ? 2 : (NBT > 8 ? 2 : 3)) form4_kernel
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             const int m1 = j * 8 + 2 * tq + c;
-            if (m2 < n1 && m1 < n1) atomicAdd(&o[m2 * n1 + m1], make_float2(acc[2 * j][2 * h + c], acc[2 * j + 1][2 * h + c]));
+            if (m2 < n1 && m1 < n1 && FGT_OK_PTR(&o[m2 * n1 + m1])) atomicAdd(&o[m2 * n1 + m1], make_float2(acc[2 * j][2 * h + c], acc[2 * j + 1][2 * h + c]));
           }
         }
       }
@@ -1009,7 +1055,7 @@ __device__ __forceinline__ void eval_stage3_3d(const typename C2T<R>::T *__restr
       }
       const int I3 = r0 + r, o1 = I1 / k, o2 = I2 / k, o3 = I3 / k;
       double *up = u + lv[(o3 * nl + o2) * nl + o1] * kp + ((I3 - o3 * k) * k + (I2 - o2 * k)) * k + (I1 - o1 * k);
-      if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc;
+      if (FGT_OK_PTR(up)) { if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc; }
     }
   } else {
     const int ntile = nr * tI * tI;
@@ -1053,7 +1099,7 @@ __device__ __forceinline__ void eval_stage3_3d(const typename C2T<R>::T *__restr
           if (I1 >= K) continue;
           const int o1 = I1 / k;
           double *up = u + lv[(o3 * nl + o2) * nl + o1] * kp + (t3 * k + t2) * k + (I1 - o1 * k);
-          if (acc_u) atomicAdd(up, (double)acc[i][j]); else *up = (double)acc[i][j];
+          if (FGT_OK_PTR(up)) { if (acc_u) atomicAdd(up, (double)acc[i][j]); else *up = (double)acc[i][j]; }
         }
       }
     }
@@ -1125,7 +1171,8 @@ __global__ void __launch_bounds__(256) eval2_kernel(const Block *__restrict__ bl
     for (int md0 = 0; md0 < nh; md0 += 8) {
       C v[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = (md0 + q < nh) ? ps[(int64_t)(md0 + q) * nn + idx] : C{0, 0};
+      for (int q = 0; q < 8; ++q)
+        v[q] = (md0 + q < nh && FGT_OK_PTR(&ps[(int64_t)(md0 + q) * nn + idx])) ? ps[(int64_t)(md0 + q) * nn + idx] : C{0, 0};
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         if (md0 + q < nh) {
@@ -1181,7 +1228,7 @@ __global__ void __launch_bounds__(256) eval2_kernel(const Block *__restrict__ bl
       }
       const int I2 = r0 + r, o1 = I1 / k, o2 = I2 / k;
       double *up = u + lv[o2 * nl + o1] * kp + (I2 - o2 * k) * k + (I1 - o1 * k);
-      if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc;
+      if (FGT_OK_PTR(up)) { if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc; }
     }
   }
 }
@@ -1296,8 +1343,10 @@ __global__ void __launch_bounds__(256) psi_tc_kernel(const float2 *__restrict__ 
     split_tf32(v1.x, h.z, l.z);
     split_tf32(v1.y, h.w, l.w);
     unsigned char *base = out + (size_t)s * ((size_t)mt * 2 * half) + (size_t)(2 * t) * half + umma_off(row, 4 * j, sbo);
-    *reinterpret_cast<uint4 *>(base) = h;
-    *reinterpret_cast<uint4 *>(base + half) = l;
+    if (FGT_OK_BYTES(base, 16) && FGT_OK_BYTES(base + half, 16)) {
+      *reinterpret_cast<uint4 *>(base) = h;
+      *reinterpret_cast<uint4 *>(base + half) = l;
+    }
   }
 }
 
@@ -1623,7 +1672,7 @@ __global__ void __launch_bounds__(256) eval5_kernel(const Block *__restrict__ bl
           if (I2 >= K) continue;
           const int o2 = I2 / k, t2i = I2 - o2 * k;
           double *up = u + lv[(o3 * nl + o2) * nl + o1] * kp + (t3 * k + t2i) * k + t1;
-          if (acc_u) atomicAdd(up, (double)acc[i][j]); else *up = (double)acc[i][j];
+          if (FGT_OK_PTR(up)) { if (acc_u) atomicAdd(up, (double)acc[i][j]); else *up = (double)acc[i][j]; }
         }
       }
     }
@@ -1806,7 +1855,7 @@ __global__ void __launch_bounds__(256) eval4_kernel(const Block *__restrict__ bl
           const int o1 = I1 / k;
           double *up = u + lv[(o3 * nl + o2) * nl + o1] * kp + (t3 * k + t2) * k + (I1 - o1 * k);
           const double v = (double)acc[j][2 * h + c];
-          if (acc_u) atomicAdd(up, v); else *up = v;
+          if (FGT_OK_PTR(up)) { if (acc_u) atomicAdd(up, v); else *up = v; }
         }
       }
     }
@@ -1922,7 +1971,7 @@ __global__ void __launch_bounds__(256) eval3_kernel(const Block *__restrict__ bl
     }
     const int o1 = I1 / k, o2 = I2 / k, o3 = rg / k;
     double *up = u + lv[(o3 * nl + o2) * nl + o1] * kp + ((rg - o3 * k) * k + (I2 - o2 * k)) * k + (I1 - o1 * k);
-    if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc;
+    if (FGT_OK_PTR(up)) { if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc; }
   }
 }
 
@@ -2009,9 +2058,9 @@ __global__ void __launch_bounds__(256) gather_kernel(const int32_t *__restrict__
     if (g1 >= 0) cfma(a2r[j], a2i[j], P2[(g1 % 3) * s2 + m2[j]], C{a1r[j], a1i[j]});
     if (D == 3) {
       if (g2 >= 0) cfma(a3r[j], a3i[j], Ph[g2 * nh + m3[j]], C{a2r[j], a2i[j]});
-      if (ok[j]) out[(int64_t)j * blockDim.x] = C{a3r[j], a3i[j]};
+      if (ok[j] && FGT_OK_PTR(&out[(int64_t)j * blockDim.x])) out[(int64_t)j * blockDim.x] = C{a3r[j], a3i[j]};
     } else {
-      if (ok[j]) out[(int64_t)j * blockDim.x] = C{a2r[j], a2i[j]};
+      if (ok[j] && FGT_OK_PTR(&out[(int64_t)j * blockDim.x])) out[(int64_t)j * blockDim.x] = C{a2r[j], a2i[j]};
     }
   }
 }
@@ -2078,7 +2127,7 @@ __global__ void __launch_bounds__(256) gather2_kernel(const GatherSeg *__restric
     cfma(ar, ai, px[0], C{wr[t], wi[t]});
     cfma(ar, ai, px[1], C{wr[t + 1], wi[t + 1]});
     cfma(ar, ai, px[2], C{wr[t + 2], wi[t + 2]});
-    psi[(int64_t)sg.tgt[t] * slot_size + idx] = C{ar, ai};
+    if (FGT_OK_PTR(&psi[(int64_t)sg.tgt[t] * slot_size + idx])) psi[(int64_t)sg.tgt[t] * slot_size + idx] = C{ar, ai};
   }
 }
 
@@ -2105,7 +2154,7 @@ __global__ void merge_kernel(const TreeShift *__restrict__ items, const typename
     }
     cfma(ar, ai, ph, phi[(int64_t)it.child[c] * slot_size + idx]);
   }
-  phi[(int64_t)it.parent * slot_size + idx] = C{ar, ai};
+  if (FGT_OK_PTR(&phi[(int64_t)it.parent * slot_size + idx])) phi[(int64_t)it.parent * slot_size + idx] = C{ar, ai};
 }
 
 // psi[child] = T_p->c(child) psi[parent]
@@ -2129,7 +2178,7 @@ __global__ void push_kernel(const TreeShift *__restrict__ items, const typename 
     } else {
       ph = cmul(ph, qh[b2 * nh + m2]);
     }
-    psi[(int64_t)it.child[c] * slot_size + idx] = cmul(ph, v);
+    if (FGT_OK_PTR(&psi[(int64_t)it.child[c] * slot_size + idx])) psi[(int64_t)it.child[c] * slot_size + idx] = cmul(ph, v);
   }
 }
 
@@ -2151,7 +2200,7 @@ __global__ void __launch_bounds__(128) near2_kernel(const NearPair *__restrict__
   int16_t *bd = reinterpret_cast<int16_t *>(T + D * kk);  // [D][k][2]
   const NearPair pr = pairs[blockIdx.x];
   const double *sg = sigma + pr.src * np;
-  for (int e = threadIdx.x; e < np; e += blockDim.x) s0[e] = __ldg(sg + e);
+  for (int e = threadIdx.x; e < np; e += blockDim.x) s0[e] = FGT_OK_PTR(sg + e) ? __ldg(sg + e) : 0.0;
   for (int e = threadIdx.x; e < D * kk; e += blockDim.x) {
     const int a = e / kk;
     T[e] = __ldg(tab + (int64_t)pr.tab[a] * kk + (e - a * kk));
@@ -2187,7 +2236,7 @@ __global__ void __launch_bounds__(128) near2_kernel(const NearPair *__restrict__
       if (b3[1] < b3[0]) continue;
       double a = 0;
       for (int j = b3[0]; j <= b3[1]; ++j) a = fma(tp[j], bp[j * kk], a);
-      atomicAdd(ut + e, a);
+      if (FGT_OK_PTR(ut + e)) atomicAdd(ut + e, a);
     }
   } else {
     for (int e = threadIdx.x; e < np; e += blockDim.x) {  // A[j2][t1] = sum_j1 T1[t1][j1] s0[j2][j1]
@@ -2205,7 +2254,7 @@ __global__ void __launch_bounds__(128) near2_kernel(const NearPair *__restrict__
       if (b2[1] < b2[0]) continue;
       double a = 0;
       for (int j = b2[0]; j <= b2[1]; ++j) a = fma(tp[j], ap[j * k], a);
-      atomicAdd(ut + e, a);
+      if (FGT_OK_PTR(ut + e)) atomicAdd(ut + e, a);
     }
   }
 }
@@ -2227,7 +2276,7 @@ __global__ void __launch_bounds__(256) near_kernel(const int64_t *__restrict__ t
   for (int64_t p = ptr[i]; p < ptr[i + 1]; ++p) {
     const NearSrc ns = src[p];
     const double *sg = sigma + ns.leaf * np;
-    for (int e = threadIdx.x; e < np; e += blockDim.x) s0[e] = __ldg(sg + e);
+    for (int e = threadIdx.x; e < np; e += blockDim.x) s0[e] = FGT_OK_PTR(sg + e) ? __ldg(sg + e) : 0.0;
     for (int e = threadIdx.x; e < D * kk; e += blockDim.x) {
       const int a = e / kk;
       T[e] = __ldg(tab + (int64_t)ns.tab[a] * kk + (e - a * kk));
@@ -2605,6 +2654,37 @@ cudaError_t run_transform(const ExecDesc &e, const double *sigma, double *u, cud
   return e.prec ? run_typed<2, float>(e, sigma, u, stream) : run_typed<2, double>(e, sigma, u, stream);
 }
 
+cudaError_t set_check_ranges(const void *const *base, const size_t *bytes, int n, cudaStream_t st) {
+#ifdef FGT_CHECKED
+  CheckRanges r{};
+  r.n = n < kCheckRanges ? n : kCheckRanges;
+  for (int i = 0; i < r.n; ++i) {
+    r.lo[i] = static_cast<const char *>(base[i]);
+    r.hi[i] = r.lo[i] + bytes[i];
+  }
+  return cudaMemcpyToSymbolAsync(g_check_ranges, &r, sizeof(r), 0, cudaMemcpyHostToDevice, st);
+#else
+  (void)base, (void)bytes, (void)n, (void)st;
+  return cudaSuccess;
+#endif
+}
+
+cudaError_t read_check(unsigned *site, unsigned *count, int *checked) {
+#ifdef FGT_CHECKED
+  *checked = 1;
+  cudaError_t err = cudaMemcpyFromSymbol(site, g_check_word, sizeof(unsigned));
+  if (err == cudaSuccess) err = cudaMemcpyFromSymbol(count, g_check_count, sizeof(unsigned));
+  const unsigned zero = 0;
+  if (err == cudaSuccess) err = cudaMemcpyToSymbol(g_check_word, &zero, sizeof(unsigned));
+  if (err == cudaSuccess) err = cudaMemcpyToSymbol(g_check_count, &zero, sizeof(unsigned));
+  return err;
+#else
+  *checked = 0;
+  *site = *count = 0;
+  return cudaSuccess;
+#endif
+}
+
 cudaError_t selftest_tc_timeout() {
   wait_timeout_selftest_kernel<<<1, 1>>>(1LL << 21);  // about a millisecond
   cudaError_t err = cudaGetLastError();
@@ -2966,7 +3046,7 @@ __global__ void __launch_bounds__(kPointThreads) point_anterp_kernel(int d, int 
   double *o = Q + box * rows * kp + (int64_t)r * kp;
 #pragma unroll
   for (int t = 0; t < KP; ++t)
-    if (t < kp) atomicAdd(o + t, acc[t]);
+    if (t < kp && FGT_OK_PTR(o + t)) atomicAdd(o + t, acc[t]);
 }
 
 // Targets.  Grid: one CTA per target segment (box b, targets [i0, i1)), one target per thread.  The
@@ -3037,7 +3117,7 @@ __global__ void __launch_bounds__(kPointThreads) point_target_kernel(PointTarget
         acc = fma(exp(-r2 * pt.inv_delta), __ldg(pt.q_sorted + j), acc);
       }
     }
-    u[pt.t_id[i]] = acc;
+    if (FGT_OK_PTR(u + pt.t_id[i])) u[pt.t_id[i]] = acc;
   }
 }
 
@@ -3162,12 +3242,12 @@ __global__ void __launch_bounds__(256) point_anterp32_kernel(int d, int kp, int 
   double *oa = Q + box * rows * kp + (int64_t)ra * kp;
 #pragma unroll
   for (int t = 0; t < KP; ++t)
-    if (t < kp) atomicAdd(oa + t, (double)sa[t] - (double)ca[t]);
+    if (t < kp && FGT_OK_PTR(oa + t)) atomicAdd(oa + t, (double)sa[t] - (double)ca[t]);
   if (!actb) return;
   double *ob = Q + box * rows * kp + (int64_t)rb * kp;
 #pragma unroll
   for (int t = 0; t < KP; ++t)
-    if (t < kp) atomicAdd(ob + t, (double)sb[t] - (double)cb[t]);
+    if (t < kp && FGT_OK_PTR(ob + t)) atomicAdd(ob + t, (double)sb[t] - (double)cb[t]);
 }
 
 // FP32 interpolation to the targets: two targets per thread (base + tid and base + 128 + tid), so

@@ -1534,6 +1534,14 @@ fgt_status fgt_execute_async(fgt_plan *plan, const double *sigma_dev, double *u_
     plan->ex.events = plan->ev_pool.data() + plan->ev_used;
     plan->ev_used = need;
   }
+  {  // checked build: the buffers this transform may touch (a no-op otherwise)
+    const size_t np = (size_t)plan->np();
+    const void *b[4] = {sigma_dev, u_dev, plan->dev, plan->work};
+    const size_t n[4] = {8 * np * (size_t)plan->n_leaves, 8 * np * (size_t)plan->n_targets(), plan->dev_bytes,
+                         plan->work_bytes};
+    cudaError_t ce = fgt::set_check_ranges(b, n, 4, (cudaStream_t)stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "check ranges");
+  }
   cudaError_t e = fgt::run_transform(plan->ex, sigma_dev, u_dev, (cudaStream_t)stream);
   plan->ex.events = nullptr;
   if (e != cudaSuccess) return cuda_fail(e, "transform launch");
@@ -1943,6 +1951,16 @@ fgt_status fgt_execute_noalloc(fgt_plan *plan, const double *sigma_dev, double *
                                  std::to_string(fgt::kNoallocScratchBytes) + " bytes");
   fgt::ExecDesc ex = plan->ex;
   ex.events = nullptr;
+  {  // checked build: sigma, u, the plan's tables and the fixed scratch array
+    void *scratch = nullptr;
+    cudaError_t ce = fgt::noalloc_scratch(&scratch);
+    if (ce != cudaSuccess) return cuda_fail(ce, "allocation-free scratch");
+    const size_t np = (size_t)plan->np();
+    const void *b[4] = {sigma_dev, u_dev, plan->dev, scratch};
+    const size_t n[4] = {8 * np * (size_t)plan->n_leaves, 8 * np * (size_t)plan->n_targets(), plan->dev_bytes,
+                         fgt::kNoallocScratchBytes};
+    if ((ce = fgt::set_check_ranges(b, n, 4, (cudaStream_t)stream)) != cudaSuccess) return cuda_fail(ce, "check ranges");
+  }
   cudaError_t e = fgt::run_transform_noalloc(ex, sigma_dev, u_dev, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "allocation-free transform");
   return FGT_OK;
@@ -2051,6 +2069,12 @@ const char *fgt_last_error(void) { return g_err.c_str(); }
 fgt_status fgt_selftest_tc_timeout(void) {
   const cudaError_t e = fgt::selftest_tc_timeout();
   return e == cudaSuccess ? FGT_OK : cuda_fail(e, "time-out self-test");
+}
+
+fgt_status fgt_check_status(unsigned *site, unsigned *count, int *checked) {
+  if (!site || !count || !checked) return fail(FGT_ERR_ARG, "NULL argument");
+  const cudaError_t e = fgt::read_check(site, count, checked);
+  return e == cudaSuccess ? FGT_OK : cuda_fail(e, "check status");
 }
 
 fgt_status fgt_device_status(int *status) {
@@ -2226,7 +2250,9 @@ fgt_status fgt_batch_execute(fgt_batch *b, const double *const *sigma_dev, doubl
     fgt_status s = batch_capture(b);
     if (s != FGT_OK) return s;
   }
-  cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+  cudaError_t e = fgt::set_check_ranges(nullptr, nullptr, 0, (cudaStream_t)stream);  // checked build: no checks
+  if (e != cudaSuccess) return cuda_fail(e, "check ranges");
+  e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "batch launch");
   return FGT_OK;
 }
@@ -2270,6 +2296,7 @@ struct fgt_point_plan {
   fgt::PointTargets pt;
   void *dev = nullptr;     // lists, tables, sorted points
   void *work = nullptr;    // phi, psi, Q, U, q_sorted
+  size_t dev_bytes = 0, work_bytes = 0;
   const int64_t *aseg = nullptr, *s_id = nullptr;
   int64_t n_aseg = 0;
   const double *s_local = nullptr;
@@ -2574,6 +2601,7 @@ fgt_status fgt_point_plan_create(int d, double delta, double tol, int64_t n_src,
   if (split) s_loc32.assign(s_loc.begin(), s_loc.end());
   const size_t o_sloc32 = pk.add(s_loc32);
   cudaError_t e = cudaMalloc(&P->dev, std::max<size_t>(pk.buf.size(), 256));
+  P->dev_bytes = std::max<size_t>(pk.buf.size(), 256);
   if (e != cudaSuccess) { P->dev = nullptr; cudaGetLastError(); return fail(FGT_ERR_OOM, "point plan: device tables"); }
   e = cudaMemcpy(P->dev, pk.buf.data(), pk.buf.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "point plan upload");
@@ -2590,6 +2618,7 @@ fgt_status fgt_point_plan_create(int d, double delta, double tol, int64_t n_src,
   const size_t w_phi = place(phi_b), w_psi = place(psi_b), w_q = place(q_b), w_u = place(u_b), w_qs = place(qs_b),
                w_q32 = place(q32_b);
   e = cudaMalloc(&P->work, std::max<size_t>(off, 256));
+  P->work_bytes = std::max<size_t>(off, 256);
   if (e != cudaSuccess) { P->work = nullptr; cudaGetLastError(); return fail(FGT_ERR_OOM, "point plan: workspace"); }
   auto wk = [&](size_t o) { return (void *)((char *)P->work + o); };
   P->Q = (double *)wk(w_q);
@@ -2648,6 +2677,12 @@ fgt_status fgt_point_plan_create(int d, double delta, double tol, int64_t n_src,
 fgt_status fgt_point_execute(fgt_point_plan *P, const double *q_dev, double *u_dev, void *stream) {
   if (!P || (P->n_src > 0 && !q_dev) || (P->n_tgt > 0 && !u_dev)) return fail(FGT_ERR_ARG, "NULL argument");
   cudaStream_t st = (cudaStream_t)stream;
+  {  // checked build: q, u, the plan's tables and workspace
+    const void *b[4] = {q_dev, u_dev, P->dev, P->work};
+    const size_t n[4] = {8 * (size_t)P->n_src, 8 * (size_t)P->n_tgt, P->dev_bytes, P->work_bytes};
+    cudaError_t ce = fgt::set_check_ranges(b, n, 4, st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "check ranges");
+  }
   cudaError_t e = fgt::point_gather_q(P->n_src, P->s_id, q_dev, P->q_sorted, P->q32, st);
   if (e == cudaSuccess)
     e = fgt::point_anterp(P->d, P->kp, P->prec == FGT_PREC_SPLIT, P->pr, P->n_dense, P->n_aseg, P->aseg,

@@ -26,6 +26,12 @@ def test_library_exports_every_declared_symbol():
     L = F.lib()
     for n in sorted(names):
         assert hasattr(L, n), n
+    # the bounds-checked build exports the same interface
+    import ctypes
+    from paper_2305_07165_gb300 import build as B
+    Lc = ctypes.CDLL(B.CHECKED_LIB)
+    for n in sorted(names):
+        assert hasattr(Lc, n), n
 
 
 def _read_table(name):
