@@ -337,6 +337,43 @@ def run_sweeps(args, F, torch, w_head, flush):
     return out
 
 
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of the GB300s (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def run_hierarchical(F, torch, w, sigma, out, flush):
+    """The literal order of Algorithm 4 (hierarchical mode): leaves form at their own level, the
+    expansions are merged child -> parent level by level (T_c->p), gathered at the cutoff level
+    and pushed parent -> child (T_p->c) before the leaves evaluate.  Reports the merge and push
+    kernels against the HBM roofline: each merge item reads its 2^d children's slots and writes
+    the parent's, each push item reads the parent's slot and writes its 2^d children's."""
+    peak, src = hbm_peak_gbs()
+    res = {"hbm_peak_gbs": peak, "peak_source": src}
+    for name, tol, prec in (FORMS["split"], FORMS["fp64"]):
+        plan = F.Plan(w.d, w.p, w.delta, tol, w.tree.level, w.tree.coord, bc=int(w.periodic), prec=prec,
+                      mode=F.MODE_HIERARCHICAL)
+        info = plan.info()
+        plan.set_profiling(True)
+        t = time_steps(plan, sigma, out, 5, 3, flush)
+        prof, nprof = plan.read_profile()
+        plan.close()
+        slot_bytes = (8 if prec == F.PREC_SPLIT else 16) * info["modes_1d"] ** (w.d - 1) * info["modes_half"]
+        row = {"ms_per_step": float(t.mean()), "merge_items": info["n_merge_items"], "push_items": info["n_push_items"],
+               "slot_bytes": slot_bytes}
+        for ph, n_items in (("merge", info["n_merge_items"]), ("push", info["n_push_items"])):
+            ms = prof.get(ph, 0.0) / max(nprof, 1)
+            nbytes = n_items * (2 ** w.d + 1) * slot_bytes
+            gbs = nbytes / (ms / 1e3) / 1e9 if ms > 0 else None
+            row[ph] = {"ms": ms, "bytes": nbytes, "achieved_gbs": gbs, "frac": gbs / peak if gbs else None}
+        res[name] = row
+    return res
+
+
 def run_refinement(F, torch):
     """Output-tree refinement and coarsening (Algorithms 5 and 6) in the setting of the paper's
     example (Section 4.3): two Gaussians with alpha = 1e-4 (seeded centres), delta = 4e-3, k = 8,
@@ -546,6 +583,7 @@ def main():
         sweeps = run_sweeps(args, F, torch, w, flush)
         refinement = run_refinement(F, torch)
         refinement["point_fgt"] = run_point_fgt(F, torch)
+        refinement["hierarchical"] = run_hierarchical(F, torch, w, sigma, out, flush)
 
     # end to end through the host-buffer entry points (pinned host memory, every step's copy in and
     # copy out inside the timed region): pipelined calls (fgt_execute_host_async, two pairs of host

@@ -108,6 +108,8 @@ typedef struct {
   int64_t device_bytes;       /* tables + lists + expansion workspace (excludes host-path staging) */
   int32_t prec, mode;
   int32_t launches;           /* CUDA kernels one execution launches */
+  int64_t n_merge_items;      /* hierarchical mode: parents merged from their 2^d children (T_c->p) */
+  int64_t n_push_items;       /* hierarchical mode: parents pushed to their 2^d children (T_p->c) */
 } fgt_plan_info;
 
 /* Build a plan: validate the tree, choose l_c, n_f (or n_p), build the lists

@@ -1204,6 +1204,9 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
     return sf;
   }() : 0, anchors.size());
   P.info.device_bytes = (int64_t)(pack.size + ptc_off + ptc_bytes);
+  P.info.n_merge_items = P.info.n_push_items = 0;
+  for (auto &s : merge_h) P.info.n_merge_items += (int64_t)s.items.size();
+  for (auto &s : push_h) P.info.n_push_items += (int64_t)s.items.size();
   if (!upload) {
     P.ex = ex;
     P.host_pack = std::move(pack);
