@@ -1,0 +1,53 @@
+"""Host arithmetic of the benchmark line, on CPU: the roofline object (dominant phase and every
+phase against its ALU peak), the HBM peak lookup and the whole-job rate of replicas."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    return m
+
+
+def test_roofline_phases_and_dominant_phase(bench):
+    info = {"form_flops": 2.0e9, "eval_flops": 3.0e9, "gather_flops": 0.5e9, "direct_flops": 0.1e9}
+    # 4 profiled steps; per step: form 0.2 ms, evaluate 0.3 ms, gather 0.05 ms, near 0.1 ms
+    prof = {"form": 0.8, "evaluate": 1.2, "gather": 0.2, "near": 0.4, "merge": 0.0, "push": 0.0}
+    r = bench.roofline_of(info, prof, 4, 1)
+    assert r["kernel"] == "evaluate" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - 3.0e9 / 0.3e-3 / 1e12) < 1e-9
+    assert r["peak"] == bench.FP32_PEAK_TFLOPS and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    ph = r["phases"]
+    assert set(ph) == {"form", "evaluate", "gather", "near"}          # phases without work are left out
+    assert ph["near"]["peak_tflops"] == bench.FP64_PEAK_TFLOPS        # the near field stays FP64
+    assert abs(ph["form"]["achieved_tflops"] - 10.0) < 1e-9 and abs(ph["form"]["ms"] - 0.2) < 1e-12
+    # FP64 form: every phase against the FP64 peak
+    r64 = bench.roofline_of(info, prof, 4, 0)
+    assert all(v["peak_tflops"] == bench.FP64_PEAK_TFLOPS for v in r64["phases"].values())
+
+
+def test_derived_alu_peaks(bench):
+    # 152 SMs at 2.07 GHz: 2 FP64 FMA / clock / SM and 128 FP32 lanes, 2 flops per FMA
+    assert abs(bench.FP64_PEAK_TFLOPS - 1.25856) < 1e-9
+    assert abs(bench.FP32_PEAK_TFLOPS - 80.54784) < 1e-9
+
+
+def test_hbm_peak_lookup(bench, tmp_path, monkeypatch):
+    f = tmp_path / "peaks.json"
+    f.write_text('{"hbm_gbs": 6000.5}')
+    monkeypatch.setattr(bench, "PEAKS_FILE", str(f))
+    assert bench.hbm_peak_gbs() == (6000.5, "measured")
+    monkeypatch.setattr(bench, "PEAKS_FILE", str(tmp_path / "missing.json"))
+    assert bench.hbm_peak_gbs() == (6800.0, "fallback")
+
+
+def test_whole_job_rate_of_replicas(bench):
+    # weak scaling: every rank transforms its own copy each step
+    assert bench.whole_job_rate(1000, 10, 4, 2.0) == 4 * 1000 * 10 / 2.0
