@@ -180,7 +180,8 @@ fgt_status fgt_execute_noalloc(fgt_plan *plan, const double *sigma_dev, double *
  * copies in, transforms, copies out on `stream` and synchronises it. */
 fgt_status fgt_execute_host(fgt_plan *plan, const double *sigma_host, double *u_host, void *stream);
 
-/* End to end, pipelined: the host-buffer transform of fgt_execute_host without the wait, so that
+/* End to end, pipelined (the transform of Algorithm 4, Section 4.2; the pipelining has no counterpart
+ * in the paper): the host-buffer transform of fgt_execute_host without the wait, so that
  * successive calls on one plan overlap.  Each call copies sigma_host in on the plan's copy-in
  * stream (into one of two device staging buffers, once the call two before it has copied its
  * result out of that buffer), transforms on `stream` once its input has arrived (calls on one plan
@@ -318,7 +319,8 @@ void fgt_destroy(fgt_plan *plan);
 
 const char *fgt_last_error(void);
 
-/* Status of the tensor-core (tcgen05) evaluation kernels on the current device.  Those kernels wait
+/* Status of the tensor-core (tcgen05) evaluation kernels on the current device (no counterpart in the
+ * paper).  Those kernels wait
  * on the tensor cores through mbarriers with a time limit of about one second; a wait that runs out
  * makes the kernel skip the rest of its block (u is then wrong there), free its tensor memory and
  * set a device status word instead of hanging.  This call copies that word to *status (0: no wait
