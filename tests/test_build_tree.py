@@ -69,3 +69,38 @@ def test_transform_on_the_gpu_built_tree():
     plan.close()
     uo = oracle.box_fgt(d, k, 1e-3, False, level, coord, sigma.cpu().numpy())
     assert np.abs(u - uo).max() <= 1e-7 * np.abs(uo).max()
+
+
+def _sorted_leaves(level, coord):
+    keys = sorted(zip(np.asarray(level).tolist(), [tuple(c) for c in np.asarray(coord).tolist()]))
+    return keys
+
+
+@pytest.mark.parametrize("d,k,periodic,eps,seed", [(2, 8, False, 1e-8, 0), (2, 6, True, 1e-9, 1),
+                                                   (3, 8, False, 1e-7, 2), (3, 6, True, 1e-6, 3),
+                                                   (2, 16, False, 1e-10, 4)])
+def test_gpu_tree_equals_the_oracle_tree(d, k, periodic, eps, seed):
+    """Algorithm 3 on the GPU against the oracle's plain restatement (oracle/tree.py): the same
+    leaves, level and integer coordinates, bit for bit; and the parent of every leaf the
+    refinement loop produced fails the monitor of eq. (funerr) as the GPU computes it."""
+    from oracle import tree as OT
+    rng = np.random.default_rng(100 + seed)
+    centers = rng.uniform(-0.4, 0.4, size=(4, d))
+    alphas = np.exp(rng.uniform(np.log(2e-4), np.log(5e-3), size=4))
+    cap = 8 if d == 2 else 5
+    level, coord, sigma = F.build_gaussian_tree(d, k, centers, alphas, periodic=periodic, eps=eps, min_level=1,
+                                                max_level=cap)
+    lo, co, info = OT.build_tree(d, k, centers, alphas, periodic=periodic, eps=eps, min_level=1, max_level=cap,
+                                 return_unbalanced=True)
+    assert _sorted_leaves(level, coord) == _sorted_leaves(lo, co)
+    # parents of the loop's leaves (not below min_level) fail the GPU monitor at the oracle's threshold
+    par = sorted({(it["level"] - 1, tuple(v >> 1 for v in it["coord"]), it["parent"][1])
+                  for it in info if it["parent"] is not None and not it["parent"][2]})
+    if par:
+        pl = np.array([p[0] for p in par], dtype=np.int32)
+        pc = np.array([p[1] for p in par], dtype=np.int32).reshape(-1, d)
+        tr = W.Tree(d, pl, pc, periodic)
+        vals = torch.from_numpy(W.gaussian_sum(W.node_positions(tr, k), centers, alphas, periodic=periodic)).cuda()
+        err, _ = R.leaf_errors(vals, d, k)
+        thr = np.array([p[2] for p in par])
+        assert np.all(err.cpu().numpy() > thr)
