@@ -169,6 +169,9 @@ fgt_status fgt_execute_async(fgt_plan *plan, const double *sigma_dev, double *u_
  *   - All calls share the array and each call overwrites it (the outgoing
  *     expansions are cleared at the start of every call): calls that overlap on
  *     the GPU race and give wrong results.  Serialise them.
+ *   - sigma_dev and u_dev must be device memory on the plan's device; that
+ *     device is made current for the call (the array is per device) and the
+ *     caller's current device is restored afterwards.  FGT_ERR_ARG otherwise.
  *   - Returns FGT_ERR_ARG (with the sizes in the message) when the plan's
  *     expansion workspace is larger than the array, and FGT_ERR_STATE when the
  *     plan's mode or precision changed since it was last prepared (preparing
@@ -203,7 +206,8 @@ fgt_status fgt_host_sync(fgt_plan *plan);
  * branch, so their kernels run concurrently; sigma_dev[i], u_dev[i] are device FP64 arrays of
  * plan i's size.  The graph is captured on the first call and again only when a pointer
  * changes.  Executions of one batch must not overlap each other or other executions of its
- * plans.  fgt_execute_batch = create + execute + synchronise `stream` + destroy. */
+ * plans; a plan listed twice would race with itself and is rejected with FGT_ERR_ARG.
+ * fgt_execute_batch = create + execute + synchronise `stream` + destroy. */
 typedef struct fgt_batch fgt_batch;
 fgt_status fgt_batch_create(fgt_plan *const *plans, int n, fgt_batch **out);
 fgt_status fgt_batch_execute(fgt_batch *batch, const double *const *sigma_dev, double *const *u_dev, void *stream);
@@ -323,8 +327,14 @@ const char *fgt_last_error(void);
  * paper).  Those kernels wait
  * on the tensor cores through mbarriers with a time limit of about one second; a wait that runs out
  * makes the kernel skip the rest of its block (u is then wrong there), free its tensor memory and
- * set a device status word instead of hanging.  This call copies that word to *status (0: no wait
- * ran out since the last call, 1: one did) and clears it.  It synchronises with the device.
+ * set a device status word instead of hanging.  This call copies that word to *status and clears it:
+ *   0: no wait ran out since the last call;
+ *   1: a wait ran out, and the copies and MMAs the kernel had in flight completed before it
+ *      exited (u is wrong in the skipped blocks, the context is sound);
+ *   2: a wait ran out and so did the bounded wait for those copies or MMAs, so one may have
+ *      landed after the kernel freed its shared or tensor memory: treat the context as suspect
+ *      (results of later kernels on it cannot be trusted until the process restarts the device).
+ * The largest value seen since the last call is kept.  It synchronises with the device.
  * FGT_ERR_ARG if status is NULL, FGT_ERR_CUDA if the copy fails. */
 fgt_status fgt_device_status(int *status);
 /* Self-test of that time-out path (no counterpart in the paper): launches one thread that waits

@@ -1441,7 +1441,7 @@ __global__ void __launch_bounds__(256) eval6_kernel(const Block *__restrict__ bl
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
-  bool fail = false;
+  bool fail = false, drained = true;
   if (tid == 0) {
     // producer of the copies and issuer of the MMAs: stage i = (tile i / 2, half i % 2) in buffer i % S
     const uint32_t idesc = umma_idesc_tf32(128, N), sbh = smem_addr(bh), sbl = smem_addr(bl);
@@ -1474,14 +1474,17 @@ __global__ void __launch_bounds__(256) eval6_kernel(const Block *__restrict__ bl
     if (!fail) {
       if (!mbar_wait(smem_addr(empty + (nst - 1) % S), (uint32_t)(((nst - 1) / S) & 1))) fail = true;
     } else {
-      // give the copies and MMAs still in flight a bounded chance to land before the exit
+      // give the copies and MMAs still in flight a bounded chance to land before the exit; if one
+      // of these waits runs out as well, an asynchronous copy or MMA may still land after this CTA
+      // has freed its shared and tensor memory, which status 2 reports
       for (int i = max(committed + 1, issued - S); i < issued; ++i)
-        if (i >= 0) mbar_wait(smem_addr(full + i % S), (uint32_t)((i / S) & 1));
-      if (committed >= 0) mbar_wait(smem_addr(empty + committed % S), (uint32_t)((committed / S) & 1));
+        if (i >= 0 && !mbar_wait(smem_addr(full + i % S), (uint32_t)((i / S) & 1))) drained = false;
+      if (committed >= 0 && !mbar_wait(smem_addr(empty + committed % S), (uint32_t)((committed / S) & 1)))
+        drained = false;
     }
   }
   if (__syncthreads_or(fail)) {
-    if (tid == 0) atomicExch(&g_tc_status, 1);
+    if (tid == 0) atomicMax(&g_tc_status, drained ? 1 : 2);
     fail = true;
   }
   tc_fence_after();

@@ -26,6 +26,7 @@
 #include <string>
 #include <tuple>
 #include <unordered_map>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/fgt.h"
@@ -1940,6 +1941,9 @@ fgt_status fgt_plan_read_profile(fgt_plan *plan, double *ms, int *n_transforms) 
   return FGT_OK;
 }
 
+static_assert(fgt::kNoallocScratchBytes == FGT_NOALLOC_SCRATCH_BYTES,
+              "the header's scratch size must match the library's array");
+
 fgt_status fgt_execute_noalloc(fgt_plan *plan, const double *sigma_dev, double *u_dev, void *stream) {
   if (!plan || !sigma_dev || !u_dev) return fail(FGT_ERR_ARG, "NULL argument");
   if (plan->host_only) return fail(FGT_ERR_STATE, "host-only plan cannot execute");
@@ -1952,6 +1956,37 @@ fgt_status fgt_execute_noalloc(fgt_plan *plan, const double *sigma_dev, double *
     return fail(FGT_ERR_ARG, "expansion workspace of " + std::to_string(phi + psi) +
                                  " bytes exceeds the fixed allocation-free scratch of " +
                                  std::to_string(fgt::kNoallocScratchBytes) + " bytes");
+  // The scratch array is per device and is looked up for the current device: every buffer must
+  // live on the plan's device, which is made current for the call (and restored afterwards).
+  int plan_dev = -1;
+  {
+    cudaPointerAttributes pa{};
+    cudaError_t ce = cudaPointerGetAttributes(&pa, plan->dev);
+    if (ce != cudaSuccess || pa.type != cudaMemoryTypeDevice) return cuda_fail(ce, "plan device");
+    plan_dev = pa.device;
+    const void *bufs[2] = {sigma_dev, u_dev};
+    for (const void *b : bufs) {
+      cudaPointerAttributes ba{};
+      ce = cudaPointerGetAttributes(&ba, b);
+      if (ce != cudaSuccess) { cudaGetLastError(); return fail(FGT_ERR_ARG, "sigma or u is not device memory"); }
+      if (ba.type != cudaMemoryTypeDevice && ba.type != cudaMemoryTypeManaged)
+        return fail(FGT_ERR_ARG, "sigma or u is not device memory");
+      if (ba.device != plan_dev)
+        return fail(FGT_ERR_ARG, "sigma or u is on device " + std::to_string(ba.device) + ", the plan on device " +
+                                     std::to_string(plan_dev));
+    }
+  }
+  int cur_dev = -1;
+  if (cudaGetDevice(&cur_dev) != cudaSuccess) return fail(FGT_ERR_CUDA, "cudaGetDevice");
+  struct DeviceGuard {
+    int prev;
+    bool switched;
+    ~DeviceGuard() { if (switched) cudaSetDevice(prev); }
+  } guard{cur_dev, cur_dev != plan_dev};
+  if (guard.switched && cudaSetDevice(plan_dev) != cudaSuccess) {
+    guard.switched = false;
+    return fail(FGT_ERR_CUDA, "cudaSetDevice");
+  }
   fgt::ExecDesc ex = plan->ex;
   ex.events = nullptr;
   {  // checked build: sigma, u, the plan's tables and the fixed scratch array
@@ -2204,6 +2239,14 @@ extern "C" {
 fgt_status fgt_batch_create(fgt_plan *const *plans, int n, fgt_batch **out) {
   if (!out || !plans || n < 1) return fail(FGT_ERR_ARG, "bad batch arguments");
   *out = nullptr;
+  // every transform of the batch writes its plan's workspace and records its plan's side-stream
+  // events: a plan listed twice would have two branches racing on them
+  {
+    std::unordered_set<const fgt_plan *> seen;
+    for (int i = 0; i < n; ++i)
+      if (plans[i] && !seen.insert(plans[i]).second)
+        return fail(FGT_ERR_ARG, "batch plan " + std::to_string(i) + " is listed twice (duplicate plan pointer)");
+  }
   fgt_batch *b = new (std::nothrow) fgt_batch();
   if (!b) return fail(FGT_ERR_OOM, "host allocation");
   for (int i = 0; i < n; ++i) {

@@ -302,3 +302,15 @@ def test_point_plan_argument_checks():
     assert create(1e-6, F.PREC_FP64_TC) == 1
     assert create(1e-6, F.PREC_FP64, d=4) == 1
     assert h.value is None
+
+
+def test_batch_rejects_a_plan_listed_twice():
+    """A batch runs its transforms as concurrent branches, each writing its own plan's workspace:
+    the same plan twice would race with itself, so the batch is refused (before any device work)."""
+    tr = W.random_balanced_tree(2, 3, max_level=3, min_level=1)
+    hp = F.HostPlan(2, 4, 1e-2, 1e-6, tr.level, tr.coord)
+    with pytest.raises(F.FGTError, match="listed twice"):
+        F.Batch([hp, hp])
+    with pytest.raises(F.FGTError, match="not a device plan"):
+        F.Batch([hp])
+    hp.close()
