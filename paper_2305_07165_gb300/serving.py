@@ -13,9 +13,10 @@ life of a request; results come back to pinned host memory.
 Plans outlive their requests in a cache keyed by the request's geometry and
 parameters (tree, k, delta, tol, boundary condition, precision): a request on a
 geometry seen before reuses an idle resident plan -- its tables, lists and
-expansion workspace stay on the device -- and skips host planning.  The cache
-has its own device-memory budget; idle plans beyond it are released, least
-recently used first.
+expansion workspace stay on the device -- and skips host planning.  Idle plans
+count against the same device-memory budget as the requests in flight: a
+request that does not fit next to them evicts idle plans, least recently used
+first, before it waits; the cache also has a cap of its own.
 
 Reports per-request latency (arrival -> result on the host) and the points/s
 achieved over the run.
@@ -80,6 +81,8 @@ class Server:
         self.cache: "OrderedDict[tuple, list]" = OrderedDict()   # key -> idle plans (LRU order)
         self.cache_bytes = 0
         self.cache_hits = 0
+        self.peak_resident = 0      # largest in-flight + idle-cached footprint seen (bytes)
+        self.held = 0               # resident plans taken from the cache by requests not yet admitted
         self.max_inflight = max_inflight
         self.pending: "queue.Queue[Request]" = queue.Queue()
         self.pool = ThreadPoolExecutor(max_workers=planner_threads)
@@ -101,15 +104,19 @@ class Server:
             req.prec = PREC_SPLIT if req.tol >= 1e-7 else PREC_FP64
         with self.lock:
             req.cached = self._cache_take(req.key())
+            if req.cached is not None:
+                self.held += int(req.cached.device_bytes())
         if req.cached is not None:
-            # the plan is already resident (and counted in the cache): only sigma and u to place
-            req.footprint = 2 * 8 * req.n_points
+            # the plan is resident already: it now counts as in flight (taken out of the cache's
+            # bytes), with sigma and u to place beside it
+            req.footprint = int(req.cached.device_bytes()) + 2 * 8 * req.n_points
         else:
             info = analyze(req.d, req.k, req.delta, req.tol, req.level, req.coord, bc=req.bc, prec=req.prec)
             req.footprint = int(info["device_bytes"]) + 2 * 8 * req.n_points
         if req.footprint > self.budget:
             if req.cached is not None:
                 with self.lock:
+                    self.held -= int(req.cached.device_bytes())
                     self._cache_put(req.key(), req.cached)
                 req.cached = None
             req.future.set_exception(MemoryError(f"request needs {req.footprint} bytes, budget {self.budget}"))
@@ -144,18 +151,28 @@ class Server:
         self.cache_hits += 1
         return plan
 
+    def _resident(self):
+        """Device bytes held by requests in flight, idle cached plans and plans held for pending
+        requests."""
+        return self.used + self.cache_bytes + self.held
+
+    def _cache_evict_one(self):
+        old_key, plans = next(iter(self.cache.items()))     # least recently used
+        victim = plans.pop(0)
+        if not plans:
+            del self.cache[old_key]
+        self.cache_bytes -= victim.device_bytes()
+        victim.close()
+
     def _cache_put(self, key, plan):
+        """Keep an idle plan resident when it fits both the cache's cap and, next to the requests
+        in flight, the device-memory budget (evicting older idle plans first); else release it."""
         nb = plan.device_bytes()
-        if nb > self.cache_budget:
+        if nb > min(self.cache_budget, self.budget - self.used - self.held):
             plan.close()
             return
-        while self.cache_bytes + nb > self.cache_budget and self.cache:
-            old_key, plans = next(iter(self.cache.items()))     # least recently used
-            victim = plans.pop(0)
-            if not plans:
-                del self.cache[old_key]
-            self.cache_bytes -= victim.device_bytes()
-            victim.close()
+        while (self.cache_bytes + nb > self.cache_budget or self._resident() + nb > self.budget) and self.cache:
+            self._cache_evict_one()
         self.cache.setdefault(key, []).append(plan)
         self.cache.move_to_end(key)
         self.cache_bytes += nb
@@ -186,10 +203,22 @@ class Server:
                     except queue.Empty:
                         break
                 r = waiting[0]
-                if self.used + r.footprint > self.budget or len(planning) + len(inflight) >= self.max_inflight:
+                if len(planning) + len(inflight) >= self.max_inflight:
+                    break
+                with self.lock:
+                    # a plan this request took from the cache is already resident (counted as held)
+                    own = int(r.cached.device_bytes()) if r.cached is not None else 0
+                    # idle resident plans give way to requests, least recently used first
+                    while self._resident() - own + r.footprint > self.budget and self.cache:
+                        self._cache_evict_one()
+                    fits = self._resident() - own + r.footprint <= self.budget
+                    if fits:
+                        self.held -= own
+                        self.used += r.footprint
+                        self.peak_resident = max(self.peak_resident, self._resident())
+                if not fits:
                     break
                 waiting.pop(0)
-                self.used += r.footprint
                 planning.append((r, self.pool.submit(self._plan, r)))
             # launch everything that finished planning
             still = []
@@ -221,10 +250,11 @@ class Server:
                 if ev.query():
                     r.t_done = time.perf_counter()
                     r.future.set_result(out_h.numpy().reshape(r.sigma.shape))
-                    with self.lock:
-                        self._cache_put(r.key(), plan)   # stays resident for the next request on it
                     self.free_streams.append(si)
-                    self.used -= r.footprint   # the plan's own bytes now count against the cache
+                    with self.lock:
+                        self.used -= r.footprint   # sigma, u and the plan leave the in-flight count ...
+                        self._cache_put(r.key(), plan)   # ... and the plan stays resident if it fits
+                        self.peak_resident = max(self.peak_resident, self._resident())
                     r.cached = None
                     self.completed.append(r)
                 else:
@@ -246,4 +276,5 @@ class Server:
         pts = sum(r.n_points for r in done)
         return {"requests": len(done), "points": pts, "points_per_s": pts / max(t1 - t0, 1e-9),
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "mean_ms": float(lat.mean()), "plan_cache_hits": self.cache_hits}
+                "mean_ms": float(lat.mean()), "plan_cache_hits": self.cache_hits,
+                "peak_resident_bytes": int(self.peak_resident)}

@@ -21,16 +21,41 @@ def test_roofline_phases_and_dominant_phase(bench):
     # 4 profiled steps; per step: form 0.2 ms, evaluate 0.3 ms, gather 0.05 ms, near 0.1 ms
     prof = {"form": 0.8, "evaluate": 1.2, "gather": 0.2, "near": 0.4, "merge": 0.0, "push": 0.0}
     r = bench.roofline_of(info, prof, 4, 1)
-    assert r["kernel"] == "evaluate" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    # split form: the contractions against the 3xTF32 tensor-pipe roofline, FP32 CUDA cores beside it
+    tpk, _ = bench.split_tensor_peak_tflops()
+    assert r["kernel"] == "evaluate" and r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
     assert abs(r["achieved"] - 3.0e9 / 0.3e-3 / 1e12) < 1e-9
-    assert r["peak"] == bench.FP32_PEAK_TFLOPS and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert r["peak"] == tpk and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert abs(r["frac_of_fp32_cuda_core"] - r["achieved"] / bench.FP32_PEAK_TFLOPS) < 1e-12
     ph = r["phases"]
     assert set(ph) == {"form", "evaluate", "gather", "near"}          # phases without work are left out
     assert ph["near"]["peak_tflops"] == bench.FP64_PEAK_TFLOPS        # the near field stays FP64
     assert abs(ph["form"]["achieved_tflops"] - 10.0) < 1e-9 and abs(ph["form"]["ms"] - 0.2) < 1e-12
+    assert ph["form"]["peak_tflops"] == tpk and "frac_of_fp32_cuda_core" in ph["form"]
     # FP64 form: every phase against the FP64 peak
     r64 = bench.roofline_of(info, prof, 4, 0)
+    assert r64["bound"] == "alu" and r64["peak"] == bench.FP64_PEAK_TFLOPS
     assert all(v["peak_tflops"] == bench.FP64_PEAK_TFLOPS for v in r64["phases"].values())
+
+
+def test_split_tensor_peak(bench, tmp_path, monkeypatch):
+    # measured BF16 burst rate x 1/2 (TF32 runs at half the BF16 rate) / 3 products per 3xTF32 product
+    f = tmp_path / "peaks.json"
+    f.write_text('{"hbm_gbs": 6000.0, "bf16_tflops": 1800.0}')
+    monkeypatch.setattr(bench, "PEAKS_FILE", str(f))
+    assert bench.split_tensor_peak_tflops() == (300.0, "measured")
+    monkeypatch.setattr(bench, "PEAKS_FILE", str(tmp_path / "missing.json"))
+    assert bench.split_tensor_peak_tflops() == (1900.0 / 6, "fallback")
+
+
+def test_error_vs_oracle_row(bench):
+    import numpy as np
+    u_or = np.ones((3, 8))
+    u = np.ones((10, 8))
+    u[4, 2] = 1 + 3e-6
+    r = bench.error_vs_oracle(u.reshape(-1), np.array([1, 4, 7]), u_or, 1e-6)
+    assert abs(r["max_abs_over_max_u"] - 3e-6) < 1e-15 and abs(r["bound"] - 1e-5) < 1e-20 and r["within_bound"]
+    assert r["sample_leaves"] == 3
 
 
 def test_derived_alu_peaks(bench):

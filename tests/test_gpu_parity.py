@@ -255,7 +255,7 @@ def _sample_targets(w, n, seed):
     return np.array(sorted(tg))
 
 
-@pytest.mark.parametrize("prec,tol", [(1, 1e-6), (0, 1e-10), (2, 1e-6)])
+@pytest.mark.parametrize("prec,tol", [(1, 1e-6), (0, 1e-10), (2, 1e-6), (2, 1e-10)])
 def test_full_size_adaptive_workload_sampled(prec, tol):
     """The benchmark's 3D free-space adaptive workload (2.09M points, delta 1e-3) as the
     benchmark runs it, checked on sampled target leaves."""
@@ -263,11 +263,37 @@ def test_full_size_adaptive_workload_sampled(prec, tol):
     check(3, w.p, w.delta, tol, w.tree, w.sigma, prec=prec, targets=_sample_targets(w, 24, 5))
 
 
-@pytest.mark.parametrize("prec,tol", [(1, 1e-6), (0, 1e-10)])
-def test_full_size_periodic_workload_sampled(prec, tol):
-    """3D periodic, uniform level 5 (16.8M points), sampled target leaves."""
+@pytest.fixture(scope="module")
+def periodic_full():
+    """3D periodic, uniform level 5 (16.8M points): the workload and the oracle on sampled leaves."""
     w = W.config_3d_periodic_uniform(seed=0)
-    check(3, w.p, w.delta, tol, w.tree, w.sigma, bc=1, prec=prec, targets=_sample_targets(w, 16, 6))
+    tg = _sample_targets(w, 24, 6)
+    uo = oracle.box_fgt(3, w.p, w.delta, True, w.tree.level, w.tree.coord, w.sigma, targets=tg)
+    return w, tg, uo
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-6), (0, 1e-10), (0, 1e-6), (2, 1e-6), (2, 1e-10)])
+def test_full_size_periodic_workload_sampled(periodic_full, prec, tol):
+    """The benchmark's headline workload in every form it times, sampled target leaves."""
+    w, tg, uo = periodic_full
+    u, info = gpu_u(3, w.p, w.delta, tol, w.tree, w.sigma, bc=1, prec=prec)
+    assert np.all(np.isfinite(u))
+    err = np.abs(u[tg] - uo).max() / np.abs(uo).max()
+    assert err <= 10 * tol, (err, info)
+
+
+@pytest.mark.parametrize("delta", [1e-4, 1e-2])
+def test_full_size_adaptive_delta_sweep_sampled(delta):
+    """The benchmark's delta sweep on the 2.09M-point adaptive tree (same tree and density, delta
+    1e-4 and 1e-2), every form it times, against the oracle on sampled target leaves."""
+    w = W.config_3d_free_adaptive(seed=0, p=8, delta=1e-3)
+    tg = _sample_targets(w, 24, 7)
+    uo = oracle.box_fgt(3, w.p, delta, False, w.tree.level, w.tree.coord, w.sigma, targets=tg)
+    for prec, tol in [(1, 1e-6), (0, 1e-6), (0, 1e-10), (2, 1e-6), (2, 1e-10)]:
+        u, info = gpu_u(3, w.p, delta, tol, w.tree, w.sigma, prec=prec)
+        assert np.all(np.isfinite(u))
+        err = np.abs(u[tg] - uo).max() / np.abs(uo).max()
+        assert err <= 10 * tol, (prec, tol, err, info)
 
 
 @pytest.mark.parametrize("delta", [1e-10, 1e-6, 1e-3, 1e-1, 1.0])

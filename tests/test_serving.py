@@ -88,3 +88,34 @@ def test_plan_cache_reuses_resident_plans():
     for r, u in zip(reqs, outs):
         ua = _alone(r)
         assert np.abs(u - ua).max() <= 10 * r.tol * np.abs(ua).max()
+
+
+def test_large_request_in_the_mix_and_resident_bytes_within_budget():
+    """A 2.09M-point request (the 3D adaptive workload, split precision) arrives among small ones
+    under a budget that cannot hold every plan at once: each result equals the request alone,
+    idle cached plans were evicted to admit requests, and the bytes held on the device (in
+    flight + idle cached) never exceeded the budget."""
+    w = W.config_3d_free_adaptive(seed=0, p=8, delta=1e-3)
+    big = S.Request(d=3, k=w.p, delta=w.delta, tol=1e-6, level=w.tree.level, coord=w.tree.coord,
+                    sigma=w.sigma, bc=0)
+    small = _requests(10, seed=11)
+    big_bytes = F.analyze(3, w.p, w.delta, 1e-6, w.tree.level, w.tree.coord, prec=F.PREC_SPLIT)["device_bytes"]
+    budget = int(big_bytes + 2 * 8 * w.n_points) + (96 << 20)
+    srv = S.Server(hbm_budget_bytes=budget, max_inflight=4, plan_cache_bytes=4 << 30).start()
+    reqs = small[:5] + [big] + small[5:]
+    futs = []
+    for i, r in enumerate(reqs):
+        futs.append(srv.submit(r))
+        if i % 2:
+            time.sleep(0.002)
+    outs = [f.result(timeout=300) for f in futs]
+    again = srv.submit(S.Request(d=3, k=w.p, delta=w.delta, tol=1e-6, level=w.tree.level, coord=w.tree.coord,
+                                 sigma=w.sigma, bc=0)).result(timeout=300)
+    srv.shutdown()
+    st = srv.stats()
+    assert st["peak_resident_bytes"] <= budget
+    assert big.n_points >= 2_000_000
+    for r, u in zip(reqs, outs):
+        ua = _alone(r)
+        assert np.abs(u - ua).max() <= 10 * r.tol * np.abs(ua).max()
+    assert np.abs(again - outs[5]).max() <= 1e-12 * np.abs(outs[5]).max()
