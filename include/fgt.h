@@ -110,6 +110,8 @@ typedef struct {
   int32_t launches;           /* CUDA kernels one execution launches */
   int64_t n_merge_items;      /* hierarchical mode: parents merged from their 2^d children (T_c->p) */
   int64_t n_push_items;       /* hierarchical mode: parents pushed to their 2^d children (T_p->c) */
+  int64_t n_tc_eval_blocks;   /* evaluation blocks whose three contractions all run on tcgen05 */
+  int64_t n_tc_form_blocks;   /* form blocks whose three contractions all run on tcgen05 */
 } fgt_plan_info;
 
 /* Build a plan: validate the tree, choose l_c, n_f (or n_p), build the lists

@@ -46,7 +46,8 @@ class PlanInfo(ctypes.Structure):
                                               "n_form_blocks", "n_direct_pairs", "n_gather_pairs", "form_flops",
                                               "eval_flops", "gather_flops", "direct_flops", "device_bytes")] + \
                [("prec", ctypes.c_int32), ("mode", ctypes.c_int32), ("launches", ctypes.c_int32)] + \
-               [("n_merge_items", ctypes.c_int64), ("n_push_items", ctypes.c_int64)]
+               [("n_merge_items", ctypes.c_int64), ("n_push_items", ctypes.c_int64),
+                ("n_tc_eval_blocks", ctypes.c_int64), ("n_tc_form_blocks", ctypes.c_int64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

@@ -1,6 +1,7 @@
 // Device-side execution descriptor: everything one transform launch sequence
 // needs, filled by the planner and consumed by fgt_kernels.cu.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -17,6 +18,8 @@ struct LaunchRange {
   int big = 0;     // 1: single blocks of K > 16, sigma streamed from global memory in stage 1
   int rows = 0;    // evaluation: rows of a block per CTA
   int tmem_cols = 0;  // tcgen05 evaluation: tensor-memory columns per CTA
+  // tensor: 1 TF32 mma.sync form / evaluation, 2 evaluation stages 2-3 on mma.sync, 3 half-range axis
+  // last, 4 evaluation stage 1 on tcgen05, 7 every evaluation stage on tcgen05 (eval7_kernel)
 };
 
 // One level of the hierarchical merge (child -> parent) or push (parent -> child).
@@ -67,6 +70,11 @@ struct ExecDesc {
   // per transform after the gather); nullptr: the tcgen05 ranges fall back to the CUDA-core kernel
   void *psi_tc = nullptr;
   int64_t n_psi_tc_slots = 0;
+  // all-tcgen05 evaluation (eval7_kernel, split precision, 3D): psi_pitch > 0 stores the incoming
+  // expansions padded, slot s at s * nh * pitch^2 complex values, [m3][m2 < pitch][m1 < pitch] (zero
+  // beyond n1), read through the tensor map psi_map; 0: the slot layout of phi
+  int psi_pitch = 0;
+  alignas(64) CUtensorMap psi_map;
 
   // out->in gather at the cutoff level
   int64_t n_gather = 0;
@@ -268,6 +276,13 @@ inline int eval6_tmem_cols(int n1, int rows) {
   while (c < cols) c *= 2;
   return c <= 512 ? c : 0;
 }
+
+// All-tcgen05 evaluation (eval7_kernel): shared-memory bytes per CTA for K = 8, 16, 32, the padded
+// mode count per full-range axis of its expansion layout, and the tensor map over the padded
+// expansions of e (e.psi, e.psi_pitch, e.nh, e.n_psi_slots set).
+size_t eval7_smem_bytes(int K);
+int eval7_pitch();
+cudaError_t encode_psi_map(ExecDesc &e);
 
 // Shared-memory bytes the form / evaluation kernels need for a block size K.
 size_t form_smem_bytes(int d, int K, int n1, int prec);

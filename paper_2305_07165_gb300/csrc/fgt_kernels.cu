@@ -1528,6 +1528,364 @@ __global__ void __launch_bounds__(256) eval6_kernel(const Block *__restrict__ bl
   eval_stage3_3d<float>(Y2, E1, nr, K, n1, r0, k, nl, lv, u, acc_u);
 }
 
+// ----------------------------------------------------------------------------- evaluation, all contractions on tcgen05 (3D, FP32)
+//
+// u(I3, I2, I1) = Re sum_{m3 >= 0} Eh(I3, m3) sum_m2 E2(I2, m2) sum_m1 E1(I1, m1) psi[m3][m2][m1]
+// (Lemma thm:pweval) as three chained real GEMMs on the fifth-generation tensor cores, one CTA per
+// block of K = 8, 16 or 32 nodes per axis, every product in 3xTF32 (lo*hi + hi*lo + hi*hi of
+// TF32 halves, FP32 accumulators in tensor memory).  The expansion is stored padded for this
+// kernel ("eval7 layout", written by the gather): slot s holds [m3][m2 < 32][m1 < 32] complex
+// values, zero beyond n1, so that one tile of 128 rows (m3, m2) x 64 floats (m1, re/im) is a
+// tensor-map box.  Per chunk of 128/K planes m3:
+//   stage 1  D1[(m3, m2)][(I1, c)]   = sum_{(m1, c')} psi[(m3, m2)][(m1, c')] B1[(I1, c)][(m1, c')]
+//            A from the tensor map (cp.async.bulk.tensor, 128-byte swizzle, two 32-float slabs per
+//            tile through a double buffer), split into TF32 halves in place;
+//   stage 2  D2[(m3, I1)][(I2, c)]   = sum_{(m2, c')} A2[(m3, I1)][(m2, c')] B2[(I2, c)][(m2, c')]
+//            A2 written from D1 by the CUDA cores (tcgen05.ld, split, swizzled stores);
+//   stage 3  D3[(I2, I1)][I3]       += sum_{(m3, c')} A3[(I2, I1)][(m3, c')] B3[I3][(m3, c')]
+//            A3 written from D2, B3 = (Re Eh, -Im Eh): the real part only, accumulated over chunks.
+// B1 / B2 are the real forms of E1 / E2 (rows (I, c) = Re / Im of the product, columns (m, c')),
+// built once per CTA from the FP32 matrices.  Thread 0 issues the tensor-map copies and the MMAs;
+// every wait is bounded and, when one runs out, the CTA drains what it has in flight (bounded),
+// sets the status word (1, or 2 when the drain ran out too), frees its tensor memory and returns.
+namespace e7 {
+constexpr int kP = 32;    // padded modes per full-range axis (n1 <= 32)
+__host__ __device__ constexpr int cm3(int K) { return 128 / K; }          // planes m3 per chunk
+__host__ __device__ constexpr int n12(int K) { return 2 * K; }            // N of stages 1 and 2
+__host__ __device__ constexpr int n3(int K) { return K < 16 ? 16 : K; }   // N of stage 3
+__host__ __device__ constexpr int kd3(int K) { return 256 / K; }          // stage-3 K per chunk (floats)
+__host__ __device__ constexpr int t3(int K) { return K * K > 128 ? K * K / 128 : 1; }  // stage-3 M tiles
+constexpr int kKB3 = 32;  // stage-3 contraction over all chunks (2 nh <= 32 floats)
+__host__ __device__ constexpr size_t off_a23() { return 65536; }
+__host__ __device__ constexpr size_t off_b1() { return 131072; }
+__host__ __device__ constexpr size_t b12_bytes(int K) { return 512u * (size_t)n12(K); }  // 2 slabs, hi + lo
+__host__ __device__ constexpr size_t off_b2(int K) { return off_b1() + b12_bytes(K); }
+__host__ __device__ constexpr size_t off_b3(int K) { return off_b2(K) + b12_bytes(K); }
+__host__ __device__ constexpr size_t off_bar(int K) { return off_b3(K) + 256u * (size_t)n3(K); }
+__host__ __device__ constexpr size_t smem_bytes(int K) { return off_bar(K) + 64 + 1024; }  // 7 barriers, the
+                                                                                           // TMEM slot, alignment
+__host__ __device__ constexpr int tmem_cols(int K) {
+  return (2 * kP + n12(K) + t3(K) * n3(K)) <= 128 ? 128 : (2 * kP + n12(K) + t3(K) * n3(K)) <= 256 ? 256 : 512;
+}
+}  // namespace e7
+
+__device__ int g_tc7_status;  // status word of eval7_kernel (same meaning as g_tc_status)
+
+// K-major operand with 128-byte swizzle (the layout of a tensor-map box of 32 floats x rows with
+// CU_TENSOR_MAP_SWIZZLE_128B): slabs of 32 floats along K, each rows x 128 bytes; in an 8-row atom
+// of 1024 bytes the 16-byte chunk j of row r sits at chunk j ^ (r mod 8).
+__device__ __forceinline__ uint32_t sw128_off(int row, int kk, int rows) {
+  const int slab = kk >> 5, f = kk & 31;
+  return (uint32_t)slab * (uint32_t)rows * 128u + (uint32_t)(row >> 3) * 1024u + (uint32_t)(row & 7) * 128u +
+         ((uint32_t)((f >> 2) ^ (row & 7)) << 4) + (uint32_t)(f & 3) * 4u;
+}
+
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                 // leading byte offset: unused with the 128-byte swizzle along K
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;                 // descriptor version of the sm_100 family
+  d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, uint32_t mbar,
+                                            uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar)
+      : "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t addr, uint32_t (&v)[N]) {
+  if constexpr (N == 8) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(addr));
+  } else if constexpr (N == 16) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(addr));
+  } else {
+    static_assert(N == 32, "tmem_ld: 8, 16 or 32 columns");
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+          "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(addr));
+  }
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// hi / lo TF32 halves of a pair, stored at byte offset o of the hi and lo operand copies
+__device__ __forceinline__ void put_split2(unsigned char *hi, unsigned char *lo, uint32_t o, float a, float b) {
+  uint32_t h0, l0, h1, l1;
+  split_tf32(a, h0, l0);
+  split_tf32(b, h1, l1);
+  *reinterpret_cast<uint2 *>(hi + o) = make_uint2(h0, h1);
+  *reinterpret_cast<uint2 *>(lo + o) = make_uint2(l0, l1);
+}
+
+template <int K>
+__global__ void __launch_bounds__(256, 1) eval7_kernel(const __grid_constant__ CUtensorMap psi_map,
+                                                       const Block *__restrict__ blocks,
+                                                       const int64_t *__restrict__ bleaves,
+                                                       const float2 *__restrict__ Ef, const float2 *__restrict__ Eh,
+                                                       double *__restrict__ u, int k, int n1, int nh) {
+  using namespace e7;
+  constexpr int N12 = n12(K), N3 = n3(K), CM3 = cm3(K), KD3 = kd3(K), T3 = t3(K), R3 = 128 * T3;
+  constexpr int TPC = CM3 / (128 / kP);  // stage-1 tiles (128 / kP planes each) per chunk
+  constexpr int TC = tmem_cols(K);
+  constexpr uint32_t SLAB = 16384;       // one 128-row x 128-byte slab
+  constexpr uint32_t SBO3 = (uint32_t)(KD3 / 4) * 128u, SBO3B = (uint32_t)(kKB3 / 4) * 128u;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *sm = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  const uint32_t sb = smem_addr(sm);
+  const Block blk = blocks[blockIdx.x];
+  const int nl = 1 << blk.dl;
+  const int64_t *lv = bleaves + blk.leaf0;
+  const bool acc_u = (blk.flags & 1) != 0;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, q = warp & 3, hh = warp >> 2;
+  const int nch = (nh + CM3 - 1) / CM3, nloads = nch * TPC * 2;
+  // mbarriers: full[2] (copies landed), empty[2] (stage-1 MMAs of a buffer done), mma2, mma3 (one
+  // commit per chunk each), drain (used once, after a time-out)
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sm + off_bar(K));
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 7);
+  const uint32_t full0 = smem_addr(bars), empty0 = smem_addr(bars + 2), mma2 = smem_addr(bars + 4),
+                 mma3 = smem_addr(bars + 5), drainb = smem_addr(bars + 6);
+  unsigned char *a23h = sm + off_a23(), *a2l = a23h + 2 * SLAB, *a3l = a23h + (size_t)R3 * KD3 * 4;
+  unsigned char *b1h = sm + off_b1(), *b1l = b1h + 256 * N12;
+  unsigned char *b2h = sm + off_b2(K), *b2l = b2h + 256 * N12;
+  unsigned char *b3h = sm + off_b3(K), *b3l = b3h + 128 * N3;
+  if (tid == 0) {
+    for (int b = 0; b < 7; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + b)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&psi_map)) : "memory");
+  }
+  __syncthreads();
+  // load i: chunk i / (2 TPC), tile (i / 2) % TPC of the chunk, slab i % 2, into buffer i % 2
+  auto issue = [&](int i) {
+    const int j = i / (2 * TPC), tl = (i >> 1) % TPC, s = i & 1;
+    const int t = j * TPC + tl;
+    tma_load_3d(sb + (uint32_t)(i & 1) * 2 * SLAB, &psi_map, 32 * s, 128 * t, blk.slot, full0 + 8 * (i & 1), SLAB);
+  };
+  if (tid == 0) {
+    issue(0);
+    if (nloads > 1) issue(1);
+  }
+  // B operands from the block's 1D matrices (real forms, TF32 halves)
+  for (int e = tid; e < K * kP; e += blockDim.x) {  // (I, m): both c rows, both c' columns
+    const int I = e / kP, m = e - I * kP;
+    float2 e1 = make_float2(0.f, 0.f), e2 = e1;
+    if (m < n1) {
+      e1 = Ef[((int64_t)(blk.mat[0] + I / k) * k + I % k) * n1 + m];
+      e2 = Ef[((int64_t)(blk.mat[1] + I / k) * k + I % k) * n1 + m];
+    }
+    if (I < K) {
+      put_split2(b1h, b1l, sw128_off(2 * I, 2 * m, N12), e1.x, -e1.y);
+      put_split2(b1h, b1l, sw128_off(2 * I + 1, 2 * m, N12), e1.y, e1.x);
+      put_split2(b2h, b2l, sw128_off(2 * I, 2 * m, N12), e2.x, -e2.y);
+      put_split2(b2h, b2l, sw128_off(2 * I + 1, 2 * m, N12), e2.y, e2.x);
+    }
+  }
+  for (int e = tid; e < N3 * (kKB3 / 2); e += blockDim.x) {  // (I3, m3)
+    const int I = e / (kKB3 / 2), m = e - I * (kKB3 / 2);
+    float2 eh = make_float2(0.f, 0.f);
+    if (I < K && m < nh) eh = Eh[((int64_t)(blk.mat[2] + I / k) * k + I % k) * nh + m];
+    put_split2(b3h, b3l, umma_off(I, 2 * m, SBO3B), eh.x, -eh.y);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)), "r"(TC));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot, tD1 = tmem, tD2 = tmem + 2 * kP, tD3 = tmem + 2 * kP + N12;
+  const uint32_t id12 = umma_idesc_tf32(128, N12), id3 = umma_idesc_tf32(128, N3);
+  const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+  int issued = nloads < 2 ? nloads : 2;  // loads issued so far (thread 0)
+  int n3c = 0;                           // stage-3 commits issued (thread 0)
+  bool fail = false;
+  // thread 0: issue load x into buffer x % 2 once the MMAs of load x - 2 (the buffer's previous
+  // contents) are done; loads are issued in order, each once
+  auto refill = [&](int x) -> bool {
+    if (x >= nloads || x != issued) return true;
+    if (x >= 2 && !mbar_wait(empty0 + 8 * (x & 1), (uint32_t)(((x - 2) >> 1) & 1))) return false;
+    issue(x);
+    issued = x + 1;
+    return true;
+  };
+  int i = 0;
+  for (int j = 0; j < nch && !fail; ++j) {
+    // ---- stage 1: the chunk's tiles, two slabs each
+    for (int tl = 0; tl < TPC && !fail; ++tl) {
+      for (int s = 0; s < 2; ++s, ++i) {
+        const int b = i & 1;
+        // the other buffer's next load, while this one is split (its MMAs, of load i - 1, run meanwhile)
+        bool ok = tid != 0 || refill(i + 1);
+        ok = ok && mbar_wait(full0 + 8 * b, (uint32_t)((i >> 1) & 1));
+        if (__syncthreads_or(!ok)) { fail = true; break; }
+        uint4 *hp = reinterpret_cast<uint4 *>(sm + (size_t)b * 2 * SLAB), *lp = hp + SLAB / 16;
+        for (int e = tid; e < (int)(SLAB / 16); e += blockDim.x) {
+          const uint4 v = hp[e];
+          uint4 hv, lw;
+          split_tf32(__uint_as_float(v.x), hv.x, lw.x);
+          split_tf32(__uint_as_float(v.y), hv.y, lw.y);
+          split_tf32(__uint_as_float(v.z), hv.z, lw.z);
+          split_tf32(__uint_as_float(v.w), hv.w, lw.w);
+          hp[e] = hv;
+          lp[e] = lw;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+          const uint32_t ah = sb + (uint32_t)b * 2 * SLAB, al = ah + SLAB;
+          const uint32_t bh = smem_addr(b1h) + (uint32_t)s * N12 * 128u, bl = smem_addr(b1l) + (uint32_t)s * N12 * 128u;
+          const uint32_t d = tD1 + (uint32_t)(tl * N12);
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint32_t o = (uint32_t)ks * 32u;
+            umma_tf32(d, umma_desc_sw128(ah + o), umma_desc_sw128(bl + o), id12, (s > 0 || ks > 0) ? 1u : 0u);
+            umma_tf32(d, umma_desc_sw128(ah + o), umma_desc_sw128(bh + o), id12, 1u);
+            umma_tf32(d, umma_desc_sw128(al + o), umma_desc_sw128(bh + o), id12, 1u);
+          }
+          umma_commit(empty0 + 8 * b);
+        }
+      }
+    }
+    if (fail) break;
+    // ---- stage 1 done (the commit of the chunk's last load covers all earlier MMAs)
+    {
+      const int il = i - 1;
+      bool ok = mbar_wait(empty0 + 8 * (il & 1), (uint32_t)((il >> 1) & 1));
+      if (tid == 0 && ok) ok = refill(il + 2);  // the next chunk's first copy runs during stages 2-3
+      if (__syncthreads_or(!ok)) { fail = true; break; }
+    }
+    tc_fence_after();
+    {  // D1 -> A2: warp (q, hh) reads lanes 32q.. (rows (m3, m2)), columns 32 hh .. 32 hh + 31
+      uint32_t v[32];
+      tmem_ld<32>(tD1 + lane_base + (uint32_t)(32 * hh), v);
+      const int l = 32 * q + lane, m2 = l & (kP - 1), mrow = l / kP;
+#pragma unroll
+      for (int p = 0; p < 16; ++p) {
+        const int col = 32 * hh + 2 * p, tl = col / N12, I1 = (col - tl * N12) >> 1;
+        const int m3l = tl * (128 / kP) + mrow;
+        put_split2(a23h, a2l, sw128_off(m3l * K + I1, 2 * m2, 128), __uint_as_float(v[2 * p]),
+                   __uint_as_float(v[2 * p + 1]));
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {  // ---- stage 2
+      const uint32_t ah = smem_addr(a23h), al = smem_addr(a2l), bh = smem_addr(b2h), bl = smem_addr(b2l);
+      for (int ks = 0; ks < 8; ++ks) {
+        const uint32_t oa = (uint32_t)(ks >> 2) * SLAB + (uint32_t)(ks & 3) * 32u;
+        const uint32_t ob = (uint32_t)(ks >> 2) * N12 * 128u + (uint32_t)(ks & 3) * 32u;
+        umma_tf32(tD2, umma_desc_sw128(ah + oa), umma_desc_sw128(bl + ob), id12, ks > 0 ? 1u : 0u);
+        umma_tf32(tD2, umma_desc_sw128(ah + oa), umma_desc_sw128(bh + ob), id12, 1u);
+        umma_tf32(tD2, umma_desc_sw128(al + oa), umma_desc_sw128(bh + ob), id12, 1u);
+      }
+      umma_commit(mma2);
+    }
+    {
+      const bool ok = mbar_wait(mma2, (uint32_t)(j & 1));
+      if (__syncthreads_or(!ok)) { fail = true; break; }
+    }
+    tc_fence_after();
+    {  // D2 -> A3 (over A2, whose MMAs are done): lanes = rows (m3, I1), columns (I2, c) of half hh
+      uint32_t v[K];
+      tmem_ld<K>(tD2 + lane_base + (uint32_t)(K * hh), v);
+      const int l = 32 * q + lane, m3l = l / K, I1 = l - m3l * K;
+#pragma unroll
+      for (int p = 0; p < K / 2; ++p) {
+        const int I2 = hh * (K / 2) + p;
+        put_split2(a23h, a3l, umma_off(I2 * K + I1, 2 * m3l, SBO3), __uint_as_float(v[2 * p]),
+                   __uint_as_float(v[2 * p + 1]));
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {  // ---- stage 3, accumulated over the chunks
+      const uint32_t ah = smem_addr(a23h), al = smem_addr(a3l), bh = smem_addr(b3h), bl = smem_addr(b3l);
+      for (int t = 0; t < T3; ++t)
+        for (int ks = 0; ks < KD3 / 8; ++ks) {
+          const uint32_t oa = (uint32_t)t * 16u * SBO3 + (uint32_t)ks * 256u;
+          const uint32_t ob = (uint32_t)(j * (KD3 / 4) + 2 * ks) * 128u;
+          const uint32_t d = tD3 + (uint32_t)(t * N3), acc = (j > 0 || ks > 0) ? 1u : 0u;
+          umma_tf32(d, umma_desc(ah + oa, SBO3), umma_desc(bl + ob, SBO3B), id3, acc);
+          umma_tf32(d, umma_desc(ah + oa, SBO3), umma_desc(bh + ob, SBO3B), id3, 1u);
+          umma_tf32(d, umma_desc(al + oa, SBO3), umma_desc(bh + ob, SBO3B), id3, 1u);
+        }
+      umma_commit(mma3);
+      ++n3c;
+    }
+  }
+  if (!fail) {
+    const bool ok = mbar_wait(mma3, (uint32_t)((nch - 1) & 1));
+    if (__syncthreads_or(!ok)) fail = true;
+  }
+  if (fail) {
+    // drain (bounded) what may still be in flight: copies not yet waited for, the last MMAs
+    bool drained = true;
+    if (tid == 0) {
+      for (int x = i; x < issued; ++x)
+        if (!mbar_wait(full0 + 8 * (x & 1), (uint32_t)((x >> 1) & 1), 1LL << 28)) drained = false;
+      // one commit on a barrier of its own after everything issued: its completion covers every
+      // earlier MMA of this thread
+      umma_commit(drainb);
+      if (!mbar_wait(drainb, 0u, 1LL << 28)) drained = false;
+      atomicMax(&g_tc7_status, drained ? 1 : 2);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC));
+    return;
+  }
+  tc_fence_after();
+  // ---- D3 -> u: lanes = rows (I2, I1), columns I3 (half hh)
+  const int kp3 = k * k * k;
+#pragma unroll 1
+  for (int t = 0; t < T3; ++t) {
+    uint32_t v[N3 / 2];
+    tmem_ld<N3 / 2>(tD3 + lane_base + (uint32_t)(t * N3 + hh * (N3 / 2)), v);
+    const int row = t * 128 + 32 * q + lane;
+    if (row < K * K) {
+      const int I2 = row / K, I1 = row - I2 * K, o2 = I2 / k, o1 = I1 / k;
+#pragma unroll
+      for (int x = 0; x < N3 / 2; ++x) {
+        const int I3 = hh * (N3 / 2) + x;
+        if (I3 < K) {
+          const int o3 = I3 / k;
+          double *up = u + lv[(o3 * nl + o2) * nl + o1] * kp3 + ((I3 - o3 * k) * k + (I2 - o2 * k)) * k + (I1 - o1 * k);
+          const double val = (double)__uint_as_float(v[x]);
+          if (FGT_OK_PTR(up)) {
+            if (acc_u) atomicAdd(up, val);
+            else *up = val;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC));
+}
+
 // ----------------------------------------------------------------------------- evaluation, half-range axis last (3D)
 //
 // u(I3, I2, I1) = Re sum_{m3 >= 0} Eh(I3, m3) sum_m2 E2(I2, m2) sum_m1 E1(I1, m1) psi[m3][m2][m1]
@@ -2005,7 +2363,8 @@ template <int D, typename R>
 __global__ void __launch_bounds__(256) gather_kernel(const int32_t *__restrict__ dst, const int64_t *__restrict__ ptr,
                               const GatherSrc *__restrict__ src, const typename C2T<R>::T *__restrict__ Pf,
                               const typename C2T<R>::T *__restrict__ Ph, const typename C2T<R>::T *__restrict__ phi,
-                              typename C2T<R>::T *__restrict__ psi, int n1, int nh, int64_t slot_size) {
+                              typename C2T<R>::T *__restrict__ psi, int n1, int nh, int64_t slot_size,
+                              int psi_pitch) {
   using C = typename C2T<R>::T;
   constexpr int MPT = kGatherMpt;
   const int i = blockIdx.x;
@@ -2061,7 +2420,11 @@ __global__ void __launch_bounds__(256) gather_kernel(const int32_t *__restrict__
     if (g1 >= 0) cfma(a2r[j], a2i[j], P2[(g1 % 3) * s2 + m2[j]], C{a1r[j], a1i[j]});
     if (D == 3) {
       if (g2 >= 0) cfma(a3r[j], a3i[j], Ph[g2 * nh + m3[j]], C{a2r[j], a2i[j]});
-      if (ok[j] && FGT_OK_PTR(&out[(int64_t)j * blockDim.x])) out[(int64_t)j * blockDim.x] = C{a3r[j], a3i[j]};
+      C *o = out + (int64_t)j * blockDim.x;
+      if (psi_pitch > 0)  // padded layout of the tcgen05 evaluation: [m3][m2 < pitch][m1 < pitch]
+        o = psi + (int64_t)dst[i] * ((int64_t)nh * psi_pitch * psi_pitch) +
+            ((int64_t)m3[j] * psi_pitch + m2[j]) * psi_pitch + m1[j];
+      if (ok[j] && FGT_OK_PTR(o)) *o = C{a3r[j], a3i[j]};
     } else {
       if (ok[j] && FGT_OK_PTR(&out[(int64_t)j * blockDim.x])) out[(int64_t)j * blockDim.x] = C{a2r[j], a2i[j]};
     }
@@ -2081,7 +2444,7 @@ __global__ void __launch_bounds__(256) gather2_kernel(const GatherSeg *__restric
                                                       const typename C2T<R>::T *__restrict__ Ph,
                                                       const typename C2T<R>::T *__restrict__ phi,
                                                       typename C2T<R>::T *__restrict__ psi, int n1, int nh,
-                                                      int64_t slot_size) {
+                                                      int64_t slot_size, int psi_pitch) {
   using C = typename C2T<R>::T;
   static_assert(W <= kSegW, "run longer than a GatherSeg");
   constexpr int NL = (D == 3) ? 9 : 3;
@@ -2130,7 +2493,12 @@ __global__ void __launch_bounds__(256) gather2_kernel(const GatherSeg *__restric
     cfma(ar, ai, px[0], C{wr[t], wi[t]});
     cfma(ar, ai, px[1], C{wr[t + 1], wi[t + 1]});
     cfma(ar, ai, px[2], C{wr[t + 2], wi[t + 2]});
-    if (FGT_OK_PTR(&psi[(int64_t)sg.tgt[t] * slot_size + idx])) psi[(int64_t)sg.tgt[t] * slot_size + idx] = C{ar, ai};
+    // padded layout of the tcgen05 evaluation when psi_pitch > 0 (3D): [m3][m2 < pitch][m1 < pitch]
+    C *o = (D == 3 && psi_pitch > 0)
+               ? psi + (int64_t)sg.tgt[t] * ((int64_t)nh * psi_pitch * psi_pitch) +
+                     ((int64_t)m3 * psi_pitch + m2) * psi_pitch + m1
+               : psi + (int64_t)sg.tgt[t] * slot_size + idx;
+    if (FGT_OK_PTR(o)) *o = C{ar, ai};
   }
 }
 
@@ -2518,12 +2886,13 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
   if (!e.fourier && e.n_gather > 0) {
     if (e.n_gather_segs > 0) {
       gather2_kernel<D, R, kSegW><<<dim3((unsigned)e.n_gather_segs, tiles), 256, 0, st>>>(
-          e.gather_segs, reinterpret_cast<const C *>(e.Pf), reinterpret_cast<const C *>(e.Ph), phi, psi, n1, nh, ss);
+          e.gather_segs, reinterpret_cast<const C *>(e.Pf), reinterpret_cast<const C *>(e.Ph), phi, psi, n1, nh, ss,
+          e.psi_pitch);
     } else {
       const unsigned gtiles = (unsigned)((ss + 256 * kGatherMpt - 1) / (256 * kGatherMpt));
       gather_kernel<D, R><<<dim3((unsigned)e.n_gather, gtiles), 256, 0, st>>>(
           e.gather_dst, e.gather_ptr, e.gather_src, reinterpret_cast<const C *>(e.Pf),
-          reinterpret_cast<const C *>(e.Ph), phi, psi, n1, nh, ss);
+          reinterpret_cast<const C *>(e.Ph), phi, psi, n1, nh, ss, e.psi_pitch);
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     eval_src = psi;
@@ -2559,6 +2928,16 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   for (const LaunchRange &lr : e.e2_ranges) {  // one launch per block size K
+    if (D == 3 && lr.tensor == 7 && sizeof(R) == 4 && e.psi_pitch == e7::kP) {  // all stages on tcgen05
+      auto k7 = lr.K == 8 ? eval7_kernel<8> : lr.K == 16 ? eval7_kernel<16> : eval7_kernel<32>;
+      if ((err = cudaFuncSetAttribute(k7, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) != cudaSuccess)
+        return err;
+      k7<<<(unsigned)lr.count, 256, lr.smem, es.next()>>>(e.psi_map, e.e2_blocks + lr.first, e.eval_leaves,
+                                                          reinterpret_cast<const float2 *>(e.Ef),
+                                                          reinterpret_cast<const float2 *>(e.Eh), u, e.k, n1, nh);
+      if ((err = cudaGetLastError()) != cudaSuccess) return err;
+      continue;
+    }
     if (D == 3 && lr.tensor == 1 && sizeof(R) == 4) {
       auto tk = (2 * nh <= 32) ? eval3_kernel<4> : eval3_kernel<8>;
       if ((err = cudaFuncSetAttribute(tk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) != cudaSuccess)
@@ -2612,9 +2991,9 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
       continue;
     }
-    // lr.rows rows of a block per CTA (tcgen05 ranges without the operand copy of the expansions, as
-    // in the allocation-free call, take the CUDA-core kernel)
-    const bool tc_fallback = lr.tensor == 4;
+    // lr.rows rows of a block per CTA (tcgen05 ranges without the operand copy or the padded layout
+    // of the expansions, as in the allocation-free call, take the CUDA-core kernel)
+    const bool tc_fallback = lr.tensor == 4 || lr.tensor == 7;
     auto kern = (lr.tensor && !tc_fallback) ? (lr.rows <= 4   ? eval2_kernel<D, R, 4, true>
                              : lr.rows <= 8 ? eval2_kernel<D, R, 8, true>
                                             : eval2_kernel<D, R, 16, true>)
@@ -2695,15 +3074,42 @@ cudaError_t selftest_tc_timeout() {
 }
 
 cudaError_t read_tc_status(int *status) {
-  int v = 0;
+  int v = 0, v7 = 0;
   cudaError_t err = cudaMemcpyFromSymbol(&v, g_tc_status, sizeof(int));
+  if (err == cudaSuccess) err = cudaMemcpyFromSymbol(&v7, g_tc7_status, sizeof(int));
   if (err != cudaSuccess) return err;
-  if (v != 0) {
-    const int zero = 0;
-    if ((err = cudaMemcpyToSymbol(g_tc_status, &zero, sizeof(int))) != cudaSuccess) return err;
-  }
-  *status = v;
+  const int zero = 0;
+  if (v != 0 && (err = cudaMemcpyToSymbol(g_tc_status, &zero, sizeof(int))) != cudaSuccess) return err;
+  if (v7 != 0 && (err = cudaMemcpyToSymbol(g_tc7_status, &zero, sizeof(int))) != cudaSuccess) return err;
+  *status = v > v7 ? v : v7;
   return cudaSuccess;
+}
+
+size_t eval7_smem_bytes(int K) { return e7::smem_bytes(K); }
+int eval7_pitch() { return e7::kP; }
+
+cudaError_t encode_psi_map(ExecDesc &e) {
+  // the padded expansions as a 3D FP32 tensor: (64 floats of m1 re/im, nh * 32 rows (m3, m2), slots)
+  using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode encode = nullptr;
+  if (!encode) {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t err = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (err != cudaSuccess) return err;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<Encode>(fn);
+  }
+  const cuuint64_t P = (cuuint64_t)e.psi_pitch;
+  const cuuint64_t dims[3] = {2 * P, (cuuint64_t)e.nh * P, (cuuint64_t)e.n_psi_slots};
+  const cuuint64_t strides[2] = {2 * P * sizeof(float), (cuuint64_t)e.nh * P * 2 * P * sizeof(float)};
+  const cuuint32_t box[3] = {32, 128, 1}, estr[3] = {1, 1, 1};
+  const CUresult r = encode(&e.psi_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, e.psi, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 // ----------------------------------------------------------------------------- allocation-free variant
@@ -2755,6 +3161,7 @@ cudaError_t run_transform_noalloc(const ExecDesc &e, const double *sigma, double
   f.sigp = nullptr;  // no packed sigma: the form kernels read sigma itself
   f.psi_tc = nullptr;  // no operand copy of the expansions: the CUDA-core evaluation throughout
   f.n_psi_tc_slots = 0;
+  f.psi_pitch = 0;     // and the plain expansion layout (no tensor map over the scratch array)
   f.events = nullptr;
   return run_transform(f, sigma, u, stream);
 }
