@@ -227,8 +227,9 @@ fgt_status fgt_plan_read_profile(fgt_plan *plan, double *ms, int *n_transforms);
 
 /* Output tree (Algorithm 5, tree refinement): evaluate u at the nodes of the leaves of `out`
  * instead of the source tree's own leaves.  Every output leaf must lie inside one source leaf (at
- * its level or finer, levels <= 20) and the output leaves must tile every source leaf without
- * overlap; FGT_ERR_TREE otherwise.  The transform keeps the source tree's interaction lists: an
+ * its level or finer, levels <= 20) and no output leaf may overlap another; they need not cover
+ * the source leaves (u is computed only where asked, as when a refinement round re-evaluates the
+ * subdivided leaves alone); FGT_ERR_TREE otherwise.  The transform keeps the source tree's interaction lists: an
  * output leaf takes the plane-wave expansion and the near-field sources of the source leaf that
  * contains it, through evaluation matrices and near-field tables for its own nodes.  After this
  * call fgt_execute* write u as [out->n_leaves][k^d] (leaf order of `out`); sigma is unchanged.

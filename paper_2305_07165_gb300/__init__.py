@@ -302,9 +302,9 @@ class Plan:
         return (self.n_out_leaves if self.n_out_leaves is not None else self.n_leaves) * self.k ** self.d
 
     def set_output_tree(self, level=None, coord=None):
-        """Evaluate u at the leaves of an output tree whose every leaf lies inside (or equals) one
-        source leaf and which tiles them (fgt_plan_set_output_tree); None restores the source tree.
-        execute() then returns u as [n_out_leaves, k**d]."""
+        """Evaluate u at the leaves of an output tree: non-overlapping boxes, each inside (or equal
+        to) one source leaf, not necessarily covering them (fgt_plan_set_output_tree).  None
+        restores the source tree.  execute() then returns u as [n_out_leaves, k**d]."""
         if level is None:
             _check(lib().fgt_plan_set_output_tree(self._h, None))
             self.n_out_leaves = None

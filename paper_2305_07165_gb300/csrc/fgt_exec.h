@@ -74,7 +74,15 @@ struct ExecDesc {
   // expansions padded, slot s at s * nh * pitch^2 complex values, [m3][m2 < pitch][m1 < pitch] (zero
   // beyond n1), read through the tensor map psi_map; 0: the slot layout of phi
   int psi_pitch = 0;
+  int psi_map_ready = 0;  // 1 once psi_map has been encoded for psi
   alignas(64) CUtensorMap psi_map;
+  // all-tcgen05 form (form7_kernel): the packed density in (J1, J2, J3) order (sig_order 1; 0: the
+  // (J3, J2, J1) order of the CUDA-core forms) read through one tensor map per K = 8, 16, 32
+  int sig_order = 0;
+  int sig_maps_ready = 0;  // 1 once sig_map has been encoded for sigp (the K in use)
+  alignas(64) CUtensorMap sig_map[3];
+  // 1: every form block is the only one of its anchor and stores the whole slot (no clear of phi)
+  int phi_stored = 0;
 
   // out->in gather at the cutoff level
   int64_t n_gather = 0;
@@ -283,6 +291,10 @@ inline int eval6_tmem_cols(int n1, int rows) {
 size_t eval7_smem_bytes(int K);
 int eval7_pitch();
 cudaError_t encode_psi_map(ExecDesc &e);
+// All-tcgen05 form (form7_kernel): shared-memory bytes per CTA, and the tensor maps over the packed
+// density e.sigp (total_floats values) for the block sizes with used[i] (K = 8, 16, 32).
+size_t form7_smem_bytes(int K);
+cudaError_t encode_sig_maps(ExecDesc &e, int64_t total_floats, const bool *used);
 
 // Shared-memory bytes the form / evaluation kernels need for a block size K.
 size_t form_smem_bytes(int d, int K, int n1, int prec);

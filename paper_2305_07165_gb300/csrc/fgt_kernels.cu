@@ -674,11 +674,33 @@ __device__ __forceinline__ void mma3(float (&c)[4], const uint32_t (&ah)[4], con
 // One CTA per block_leaves entry: the leaf's k^3 values, converted to FP32, go to their place in
 // the block's (J3, J2, J1) tile at sigp + block.leaf0 k^3, so that every form CTA that needs
 // the block reads it as one contiguous run.
+// FP64 <-> FP32 conversions on the integer pipes.  GB300 executes F2F conversions involving FP64 on
+// its narrow FP64 pipe (2 results per clock per SM); these take a dozen integer operations instead.
+// Round to nearest even, as the hardware conversion; magnitudes below FP32's normal range (2^-126,
+// far below any value that matters next to |u|) become a signed zero; overflow gives infinity.
+__device__ __forceinline__ float f64_to_f32_int(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b, s = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(s);
+  if (e >= 255) return __uint_as_float(s | 0x7F800000u);
+  const uint32_t m = ((hi & 0xFFFFFu) << 3) | (lo >> 29), rest = lo & 0x1FFFFFFFu;
+  uint32_t r = s | ((uint32_t)e << 23) | m;
+  if (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) r += 1u;  // a carry moves into the exponent
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ double f32_to_f64_int(uint32_t b) {
+  const uint32_t s = b & 0x80000000u, e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+  if (e == 0) return __hiloint2double((int)s, 0);                 // zero; subnormals flushed
+  if (e == 255) return __hiloint2double((int)(s | 0x7FF00000u | (m >> 3)), (int)(m << 29));  // inf / nan
+  return __hiloint2double((int)(s | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
+}
+
 __global__ void __launch_bounds__(256) sigma_pack_kernel(const Block *__restrict__ blocks,
                                                          const int32_t *__restrict__ pack_block,
                                                          const int64_t *__restrict__ bleaves,
                                                          const double *__restrict__ sigma, float *__restrict__ sigp,
-                                                         int k) {
+                                                         int k, int j3_fastest) {
   const int64_t i = blockIdx.x;
   const Block b = blocks[pack_block[i]];
   const int kp = k * k * k, nl = 1 << b.dl, K = b.K;
@@ -686,10 +708,24 @@ __global__ void __launch_bounds__(256) sigma_pack_kernel(const Block *__restrict
   const int o1 = leafi % nl, o2 = (leafi / nl) % nl, o3 = leafi / (nl * nl);
   const double *src = sigma + bleaves[i] * kp;
   float *dst = sigp + b.leaf0 * kp;
-  for (int node = threadIdx.x; node < kp; node += blockDim.x) {
-    const int j1 = node % k, j2 = (node / k) % k, j3 = node / (k * k);
-    float *dp = dst + ((o3 * k + j3) * K + (o2 * k + j2)) * K + (o1 * k + j1);
-    if (FGT_OK_PTR(dp) && FGT_OK_PTR(src + node)) *dp = (float)__ldg(src + node);
+  __shared__ float leaf[kMaxK * kMaxK * kMaxK];  // the leaf's values, node index j1 fastest
+  for (int node = threadIdx.x; node < kp; node += blockDim.x)
+    if (FGT_OK_PTR(src + node)) leaf[node] = f64_to_f32_int(__ldg(src + node));
+  __syncthreads();
+  // written in runs of k consecutive floats: (J3, J2, J1) order for the CUDA-core forms (J1
+  // fastest), (J1, J2, J3) for the tcgen05 form (J3 fastest)
+  for (int t = threadIdx.x; t < kp; t += blockDim.x) {
+    const int a = t % k, bq = (t / k) % k, c = t / (k * k);  // fastest, middle, slowest index of the run order
+    float *dp;
+    float v;
+    if (j3_fastest) {  // a = j3, bq = j2, c = j1
+      dp = dst + ((o1 * k + c) * K + (o2 * k + bq)) * K + (o3 * k + a);
+      v = leaf[(a * k + bq) * k + c];
+    } else {           // a = j1, bq = j2, c = j3
+      dp = dst + ((o3 * k + c) * K + (o2 * k + bq)) * K + (o1 * k + a);
+      v = leaf[t];
+    }
+    if (FGT_OK_PTR(dp)) *dp = v;
   }
 }
 
@@ -1857,33 +1893,346 @@ __global__ void __launch_bounds__(256, 1) eval7_kernel(const __grid_constant__ C
     return;
   }
   tc_fence_after();
-  // ---- D3 -> u: lanes = rows (I2, I1), columns I3 (half hh)
+  // ---- D3 -> u, tile by tile (128 rows (I2, I1) = RI2 values of I2 x all I1): the accumulators are
+  // widened to FP64 on the integer pipes and staged in shared memory (the free copy ring) as
+  // [I3][I2 of the tile][I1], then written in runs of RI2 k consecutive values of u (one leaf row
+  // block per (o1, I3)) with 16-byte stores.  The block's leaves' offsets into u sit in shared memory.
+  constexpr int RI2 = 128 / K < K ? 128 / K : K;  // I2 values per tile
+  double *stage = reinterpret_cast<double *>(sm);   // K * RI2 * K values: at most 32 KB
+  int64_t *lofs = reinterpret_cast<int64_t *>(sm + 32768);
   const int kp3 = k * k * k;
+  for (int e = tid; e < nl * nl * nl; e += blockDim.x) lofs[e] = lv[e] * kp3;
+  __syncthreads();
 #pragma unroll 1
   for (int t = 0; t < T3; ++t) {
-    uint32_t v[N3 / 2];
-    tmem_ld<N3 / 2>(tD3 + lane_base + (uint32_t)(t * N3 + hh * (N3 / 2)), v);
-    const int row = t * 128 + 32 * q + lane;
-    if (row < K * K) {
-      const int I2 = row / K, I1 = row - I2 * K, o2 = I2 / k, o1 = I1 / k;
+    {
+      uint32_t v[N3 / 2];
+      tmem_ld<N3 / 2>(tD3 + lane_base + (uint32_t)(t * N3 + hh * (N3 / 2)), v);
+      const int rl = 32 * q + lane;  // row within the tile: I2l = rl / K, I1 = rl % K
+      if (rl < RI2 * K) {
 #pragma unroll
-      for (int x = 0; x < N3 / 2; ++x) {
-        const int I3 = hh * (N3 / 2) + x;
-        if (I3 < K) {
-          const int o3 = I3 / k;
-          double *up = u + lv[(o3 * nl + o2) * nl + o1] * kp3 + ((I3 - o3 * k) * k + (I2 - o2 * k)) * k + (I1 - o1 * k);
-          const double val = (double)__uint_as_float(v[x]);
-          if (FGT_OK_PTR(up)) {
-            if (acc_u) atomicAdd(up, val);
-            else *up = val;
-          }
+        for (int x = 0; x < N3 / 2; ++x) {
+          const int I3 = hh * (N3 / 2) + x;
+          if (I3 < K) stage[I3 * (RI2 * K) + rl] = f32_to_f64_int(v[x]);
+        }
+      }
+    }
+    __syncthreads();
+    // runs: (I3, o1) -> RI2 rows of k values (I2l, i1), contiguous in u within a leaf; pairs of
+    // values per thread (k even)
+    const int I2base = t * RI2;
+    const int runlen = RI2 * k, nruns = K * nl, npairs = nruns * runlen / 2;
+    for (int e = tid; e < npairs; e += blockDim.x) {
+      const int pe = 2 * e, run = pe / runlen, w = pe - run * runlen;
+      const int I3 = run / nl, o1 = run - I3 * nl, I2l = w / k, i1 = w - I2l * k;
+      const int o3 = I3 / k, I2 = I2base + I2l, o2 = I2 / k;
+      const double v0 = stage[I3 * (RI2 * K) + I2l * K + o1 * k + i1];
+      const double v1 = stage[I3 * (RI2 * K) + I2l * K + o1 * k + i1 + 1];
+      double *up = u + lofs[(o3 * nl + o2) * nl + o1] + ((I3 - o3 * k) * k + (I2 - o2 * k)) * k + i1;
+      if (acc_u) {
+        if (FGT_OK_PTR(up)) atomicAdd(up, v0);
+        if (FGT_OK_PTR(up + 1)) atomicAdd(up + 1, v1);
+      } else if (FGT_OK_BYTES(up, 16)) {
+        *reinterpret_cast<double2 *>(up) = make_double2(v0, v1);
+      }
+    }
+    __syncthreads();
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC));
+}
+
+// ----------------------------------------------------------------------------- form, all contractions on tcgen05 (3D, FP32)
+//
+// phi[m3][m2][m1] (+)= sum_{J3, J2, J1} Fh(m3, J3) F2(m2, J2) F1(m1, J1) sigma(J3, J2, J1)  (Lemma pwbox),
+// one CTA per block of K = 8, 16 or 32 nodes per axis, every product in 3xTF32 with FP32
+// accumulators in tensor memory, contracted x3 first (into the half-range axis), then x2, then x1:
+//   stage 1  D1[(J1, J2)][(m3, c)]  = sum_J3 sigma[(J1, J2)][J3] B1[(m3, c)][J3]        (B1 = Re / Im Fh)
+//            A from the packed FP32 density (rows (J1, J2) of K values, J3 fastest) through a tensor
+//            map with the swizzle of a K-float row (32, 64 or 128 bytes), split into TF32 halves in place;
+//   stage 2  D2[(J1, m3)][(m2, c)]  = sum_{(J2, c')} A2[(J1, m3)][(J2, c')] B2[(m2, c)][(J2, c')]
+//   stage 3  D3[(m2, m3)][(m1, c)] += sum_{(J1, c')} A3[(m2, m3)][(J1, c')] B3[(m1, c)][(J1, c')]
+// in chunks of 8 planes J1 (A2, A3 written from D1, D2 by the CUDA cores), D3 accumulated over the
+// chunks and written to the anchor's slot: stored when the block is its anchor's only one (flags
+// bit 1), added atomically otherwise.  Waits, time-outs and the status word as in eval7_kernel.
+namespace f7 {
+constexpr int kP = 32;    // padded modes per full-range axis (n1 <= 32); m3 < 16
+__host__ __device__ constexpr uint32_t a1_bytes(int K) { return 128u * (uint32_t)K * 4u; }  // one stage-1 tile
+__host__ __device__ constexpr int tpc(int K) { return K >= 16 ? K / 16 : 1; }               // tiles per chunk
+__host__ __device__ constexpr int nchunk(int K) { return K / 8; }                             // chunks of 8 J1
+__host__ __device__ constexpr int kd2(int K) { return 2 * K < 32 ? 32 : 2 * K; }            // stage-2 K, padded
+__host__ __device__ constexpr size_t off_a23(int K) { return 4 * (size_t)a1_bytes(K); }     // ring: 2 x (hi, lo)
+__host__ __device__ constexpr size_t off_b1(int K) { return off_a23(K) + 65536; }
+__host__ __device__ constexpr size_t off_b2(int K) { return off_b1(K) + 256u * (size_t)K; }
+__host__ __device__ constexpr size_t off_b3(int K) { return off_b2(K) + 512u * (size_t)kd2(K); }
+__host__ __device__ constexpr size_t off_bar(int K) { return off_b3(K) + 1024u * (size_t)K; }
+__host__ __device__ constexpr size_t smem_bytes(int K) { return off_bar(K) + 64 + 1024; }
+constexpr int kTmemCols = 512;  // D1 (64), D2 (64), D3 (4 tiles x 64)
+}  // namespace f7
+
+// Descriptor of a K-major operand with a 32-, 64- or 128-byte swizzle (rows of 8, 16 or 32 floats,
+// 8-row atoms), as a tensor map with the matching swizzle leaves it.
+__device__ __forceinline__ uint64_t umma_desc_swz(uint32_t saddr, int row_floats) {
+  const uint32_t rb = (uint32_t)row_floats * 4u;
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(((8u * rb) >> 4) & 0x3FFF) << 32;  // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)(row_floats == 8 ? 6 : row_floats == 16 ? 4 : 2) << 61;  // 32-, 64-, 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar,
+                                            uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+
+__device__ int g_tcf_status;  // status word of form7_kernel (same meaning as g_tc_status)
+
+template <int K>
+__global__ void __launch_bounds__(256, 1) form7_kernel(const __grid_constant__ CUtensorMap sig_map,
+                                                       const Block *__restrict__ blocks,
+                                                       const float2 *__restrict__ Ff, const float2 *__restrict__ Fh,
+                                                       float2 *__restrict__ phi, int k, int n1, int nh,
+                                                       int64_t slot_size) {
+  using namespace f7;
+  constexpr int TPC = tpc(K), NCH = nchunk(K), KD2 = kd2(K), NL = NCH * TPC;
+  constexpr uint32_t A1 = a1_bytes(K);
+  constexpr uint32_t SBOB1 = (uint32_t)(K / 4) * 128u, SBO3 = 4u * 128u, SBOB3 = (uint32_t)(2 * K / 4) * 128u;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *sm = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  const uint32_t sb = smem_addr(sm);
+  const Block blk = blocks[blockIdx.x];
+  const bool sole = (blk.flags & 2) != 0;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, q = warp & 3, hh = warp >> 2;
+  const int row0 = (int)(blk.leaf0 * (int64_t)(k * k * k) / K);  // the block's first K-float row
+  // mbarriers: full[2], empty[2], mma2, mma3, drain
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sm + off_bar(K));
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 7);
+  const uint32_t full0 = smem_addr(bars), empty0 = smem_addr(bars + 2), mma2 = smem_addr(bars + 4),
+                 mma3 = smem_addr(bars + 5), drainb = smem_addr(bars + 6);
+  unsigned char *a23h = sm + off_a23(K), *a2l = a23h + (size_t)128 * KD2 * 4, *a3l = a23h + 512u * 16u * 4u;
+  unsigned char *b1h = sm + off_b1(K), *b1l = b1h + 128u * K;
+  unsigned char *b2h = sm + off_b2(K), *b2l = b2h + 256u * KD2;
+  unsigned char *b3h = sm + off_b3(K), *b3l = b3h + 512u * K;
+  if (tid == 0) {
+    for (int b = 0; b < 7; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bars + b)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&sig_map)) : "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int i) {  // stage-1 tile i (rows row0 + 128 i) into buffer i % 2
+    tma_load_2d(sb + (uint32_t)(i & 1) * 2u * A1, &sig_map, 0, row0 + 128 * i, full0 + 8 * (i & 1), A1);
+  };
+  if (tid == 0) {
+    issue(0);
+    if (NL > 1) issue(1);
+  }
+  // A2 / A3 region zeroed once (the padding columns of A2 for K = 8 are never written)
+  for (int e = tid; e < 65536 / 16; e += blockDim.x) reinterpret_cast<uint4 *>(a23h)[e] = make_uint4(0, 0, 0, 0);
+  // B operands (real forms of the block's 1D form matrices, TF32 halves)
+  for (int e = tid; e < 16 * K; e += blockDim.x) {  // B1[(m3, c)][J3]
+    const int m = e / K, J = e - m * K;
+    float2 f = make_float2(0.f, 0.f);
+    if (m < nh) f = Fh[((int64_t)(blk.mat[2] + J / k) * nh + m) * k + J % k];
+    uint32_t h0, l0, h1, l1;
+    split_tf32(f.x, h0, l0);
+    split_tf32(f.y, h1, l1);
+    *reinterpret_cast<uint32_t *>(b1h + umma_off(2 * m, J, SBOB1)) = h0;
+    *reinterpret_cast<uint32_t *>(b1l + umma_off(2 * m, J, SBOB1)) = l0;
+    *reinterpret_cast<uint32_t *>(b1h + umma_off(2 * m + 1, J, SBOB1)) = h1;
+    *reinterpret_cast<uint32_t *>(b1l + umma_off(2 * m + 1, J, SBOB1)) = l1;
+  }
+  for (int e = tid; e < kP * (KD2 / 2); e += blockDim.x) {  // B2[(m2, c)][(J2, c')], B3[(m1, c)][(J1, c')]
+    const int m = e / (KD2 / 2), J = e - m * (KD2 / 2);
+    float2 f2 = make_float2(0.f, 0.f), f1 = f2;
+    if (m < n1 && J < K) {
+      f2 = Ff[((int64_t)(blk.mat[1] + J / k) * n1 + m) * k + J % k];
+      f1 = Ff[((int64_t)(blk.mat[0] + J / k) * n1 + m) * k + J % k];
+    }
+    put_split2(b2h, b2l, sw128_off(2 * m, 2 * J, 2 * kP), f2.x, -f2.y);
+    put_split2(b2h, b2l, sw128_off(2 * m + 1, 2 * J, 2 * kP), f2.y, f2.x);
+    if (J < K) {
+      put_split2(b3h, b3l, umma_off(2 * m, 2 * J, SBOB3), f1.x, -f1.y);
+      put_split2(b3h, b3l, umma_off(2 * m + 1, 2 * J, SBOB3), f1.y, f1.x);
+    }
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot, tD1 = tmem, tD2 = tmem + 64, tD3 = tmem + 128;
+  const uint32_t id1 = umma_idesc_tf32(128, 32), id2 = umma_idesc_tf32(128, 64);
+  const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+  int issued = NL < 2 ? NL : 2;
+  bool fail = false;
+  auto refill = [&](int x) -> bool {
+    if (x >= NL || x != issued) return true;
+    if (x >= 2 && !mbar_wait(empty0 + 8 * (x & 1), (uint32_t)(((x - 2) >> 1) & 1))) return false;
+    issue(x);
+    issued = x + 1;
+    return true;
+  };
+  int i = 0;
+  for (int c = 0; c < NCH && !fail; ++c) {
+    // ---- stage 1: the chunk's tiles
+    for (int tl = 0; tl < TPC; ++tl, ++i) {
+      const int b = i & 1;
+      bool ok = tid != 0 || refill(i + 1);
+      ok = ok && mbar_wait(full0 + 8 * b, (uint32_t)((i >> 1) & 1));
+      if (__syncthreads_or(!ok)) { fail = true; break; }
+      uint4 *hp = reinterpret_cast<uint4 *>(sm + (size_t)b * 2 * A1), *lp = hp + A1 / 16;
+      for (int e = tid; e < (int)(A1 / 16); e += blockDim.x) {
+        const uint4 v = hp[e];
+        uint4 hv, lw;
+        split_tf32(__uint_as_float(v.x), hv.x, lw.x);
+        split_tf32(__uint_as_float(v.y), hv.y, lw.y);
+        split_tf32(__uint_as_float(v.z), hv.z, lw.z);
+        split_tf32(__uint_as_float(v.w), hv.w, lw.w);
+        hp[e] = hv;
+        lp[e] = lw;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (tid == 0) {
+        const uint32_t ah = sb + (uint32_t)b * 2u * A1, al = ah + A1, bh = smem_addr(b1h), bl = smem_addr(b1l);
+        const uint32_t d = tD1 + (uint32_t)(tl * 32);
+        for (int ks = 0; ks < K / 8; ++ks) {
+          const uint32_t oa = (uint32_t)ks * 32u, ob = (uint32_t)ks * 256u;
+          umma_tf32(d, umma_desc_swz(ah + oa, K), umma_desc(bl + ob, SBOB1), id1, ks > 0 ? 1u : 0u);
+          umma_tf32(d, umma_desc_swz(ah + oa, K), umma_desc(bh + ob, SBOB1), id1, 1u);
+          umma_tf32(d, umma_desc_swz(al + oa, K), umma_desc(bh + ob, SBOB1), id1, 1u);
+        }
+        umma_commit(empty0 + 8 * b);
+      }
+    }
+    if (fail) break;
+    {  // stage 1 of the chunk done; the next chunk's first copy starts
+      const int il = i - 1;
+      bool ok = mbar_wait(empty0 + 8 * (il & 1), (uint32_t)((il >> 1) & 1));
+      if (tid == 0 && ok) ok = refill(il + 2);
+      if (__syncthreads_or(!ok)) { fail = true; break; }
+    }
+    tc_fence_after();
+    // ---- D1 -> A2: lanes = rows (J1, J2) of the chunk's tiles, columns (m3, c) of half hh
+#pragma unroll 1
+    for (int tl = 0; tl < TPC; ++tl) {
+      const int rc = tl * 128 + 32 * q;  // first row of this warp's lanes within the chunk
+      if (rc >= 8 * K) continue;         // K = 8: the tile's second half holds no rows of the block
+      uint32_t v[16];
+      tmem_ld<16>(tD1 + lane_base + (uint32_t)(tl * 32 + 16 * hh), v);
+      const int r = rc + lane, J1l = r / K, J2 = r - J1l * K;
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        const int m3 = 8 * hh + p;
+        put_split2(a23h, a2l, sw128_off(J1l * 16 + m3, 2 * J2, 128), __uint_as_float(v[2 * p]),
+                   __uint_as_float(v[2 * p + 1]));
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {  // ---- stage 2
+      const uint32_t ah = smem_addr(a23h), al = smem_addr(a2l), bh = smem_addr(b2h), bl = smem_addr(b2l);
+      for (int ks = 0; ks < KD2 / 8; ++ks) {
+        const uint32_t oa = (uint32_t)(ks >> 2) * 16384u + (uint32_t)(ks & 3) * 32u;
+        const uint32_t ob = (uint32_t)(ks >> 2) * 8192u + (uint32_t)(ks & 3) * 32u;
+        umma_tf32(tD2, umma_desc_sw128(ah + oa), umma_desc_sw128(bl + ob), id2, ks > 0 ? 1u : 0u);
+        umma_tf32(tD2, umma_desc_sw128(ah + oa), umma_desc_sw128(bh + ob), id2, 1u);
+        umma_tf32(tD2, umma_desc_sw128(al + oa), umma_desc_sw128(bh + ob), id2, 1u);
+      }
+      umma_commit(mma2);
+    }
+    {
+      const bool ok = mbar_wait(mma2, (uint32_t)(c & 1));
+      if (__syncthreads_or(!ok)) { fail = true; break; }
+    }
+    tc_fence_after();
+    {  // ---- D2 -> A3: lanes = rows (J1, m3), columns (m2, c) of half hh
+      uint32_t v[32];
+      tmem_ld<32>(tD2 + lane_base + (uint32_t)(32 * hh), v);
+      const int l = 32 * q + lane, J1l = l >> 4, m3 = l & 15;
+#pragma unroll
+      for (int p = 0; p < 16; ++p) {
+        const int m2 = 16 * hh + p;
+        put_split2(a23h, a3l, umma_off(m2 * 16 + m3, 2 * J1l, SBO3), __uint_as_float(v[2 * p]),
+                   __uint_as_float(v[2 * p + 1]));
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {  // ---- stage 3, accumulated over the chunks
+      const uint32_t ah = smem_addr(a23h), al = smem_addr(a3l), bh = smem_addr(b3h), bl = smem_addr(b3l);
+      for (int t = 0; t < 4; ++t)
+        for (int ks = 0; ks < 2; ++ks) {
+          const uint32_t oa = (uint32_t)t * 16u * SBO3 + (uint32_t)ks * 256u;
+          const uint32_t ob = (uint32_t)(4 * c + 2 * ks) * 128u;
+          const uint32_t d = tD3 + (uint32_t)(t * 64), acc = (c > 0 || ks > 0) ? 1u : 0u;
+          umma_tf32(d, umma_desc(ah + oa, SBO3), umma_desc(bl + ob, SBOB3), id2, acc);
+          umma_tf32(d, umma_desc(ah + oa, SBO3), umma_desc(bh + ob, SBOB3), id2, 1u);
+          umma_tf32(d, umma_desc(al + oa, SBO3), umma_desc(bh + ob, SBOB3), id2, 1u);
+        }
+      umma_commit(mma3);
+    }
+    {  // A3 is overwritten by the next chunk's A2
+      const bool ok = mbar_wait(mma3, (uint32_t)(c & 1));
+      if (__syncthreads_or(!ok)) { fail = true; break; }
+    }
+  }
+  if (fail) {
+    bool drained = true;
+    if (tid == 0) {
+      for (int x = i; x < issued; ++x)
+        if (!mbar_wait(full0 + 8 * (x & 1), (uint32_t)((x >> 1) & 1), 1LL << 28)) drained = false;
+      umma_commit(drainb);
+      if (!mbar_wait(drainb, 0u, 1LL << 28)) drained = false;
+      atomicMax(&g_tcf_status, drained ? 1 : 2);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    return;
+  }
+  tc_fence_after();
+  // ---- D3 -> phi: lanes = rows (m2, m3), columns (m1, c) of half hh
+  float2 *out = phi + (int64_t)blk.slot * slot_size;
+#pragma unroll 1
+  for (int t = 0; t < 4; ++t) {
+    uint32_t v[32];
+    tmem_ld<32>(tD3 + lane_base + (uint32_t)(t * 64 + 32 * hh), v);
+    const int row = t * 128 + 32 * q + lane, m2 = row >> 4, m3 = row & 15;
+    if (m2 < n1 && m3 < nh) {
+      float2 *o = out + ((int64_t)m3 * n1 + m2) * n1;
+#pragma unroll
+      for (int p = 0; p < 16; ++p) {
+        const int m1 = 16 * hh + p;
+        if (m1 < n1 && FGT_OK_PTR(o + m1)) {
+          const float2 val = make_float2(__uint_as_float(v[2 * p]), __uint_as_float(v[2 * p + 1]));
+          if (sole) o[m1] = val;
+          else atomicAdd(o + m1, val);
         }
       }
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
 // ----------------------------------------------------------------------------- evaluation, half-range axis last (3D)
@@ -2822,11 +3171,13 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
   };
   if ((err = fork_near(0)) != cudaSuccess) return err;
   if (e.n_blocks > 0) {
-    // outgoing expansions: zero, then every block adds its contribution
-    if ((err = cudaMemsetAsync(phi, 0, sizeof(C) * ss * e.n_phi_slots, st)) != cudaSuccess) return err;
+    // outgoing expansions: zero, then every block adds its contribution (unless every block is the
+    // only one of its anchor and stores the whole slot)
+    if (!e.phi_stored && (err = cudaMemsetAsync(phi, 0, sizeof(C) * ss * e.n_phi_slots, st)) != cudaSuccess)
+      return err;
     if (D == 3 && sizeof(R) == 4 && e.sigp != nullptr && e.n_pack > 0) {
       sigma_pack_kernel<<<(unsigned)e.n_pack, 256, 0, st>>>(e.blocks, e.pack_block, e.block_leaves, sigma, e.sigp,
-                                                            e.k);
+                                                            e.k, e.sig_order);
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     Spread fs(e, st);
@@ -2841,6 +3192,35 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     for (const LaunchRange &lr : e.f2_ranges) {  // one launch per block size K
+      if (D == 3 && lr.tensor == 7 && sizeof(R) == 4 &&
+          (e.sig_order != 1 || e.sigp == nullptr || !e.sig_maps_ready)) {
+        // without the packed density in its order (the allocation-free call): the register-tiled
+        // tensor-core form, one block per CTA, reading sigma itself, adding into the cleared slot
+        const bool big = lr.K > 16, small_n = n1_pad8(n1) / 4 <= 8;
+        auto fk = big ? (small_n ? form4_kernel<8, true> : form4_kernel<kNbtMax, true>)
+                      : (small_n ? form4_kernel<8, false> : form4_kernel<kNbtMax, false>);
+        const size_t fsm = big ? form4b_bytes(lr.K, n1) : form4_bytes(1, lr.K, n1);
+        if ((err = cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm)) != cudaSuccess)
+          return err;
+        fk<<<(unsigned)(lr.count * ((nh + kSc - 1) / kSc)), 256, fsm, fs.next()>>>(
+            e.f2_blocks, e.f2_gptr + lr.first, e.block_leaves, sigma, nullptr, reinterpret_cast<const float2 *>(e.Ff),
+            reinterpret_cast<const float2 *>(e.Fh), reinterpret_cast<float2 *>(phi), e.k, n1, nh, ss);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        continue;
+      }
+      if (D == 3 && lr.tensor == 7 && sizeof(R) == 4) {  // all stages on tcgen05
+        const int ki = lr.K == 8 ? 0 : lr.K == 16 ? 1 : 2;
+        auto k7 = ki == 0 ? form7_kernel<8> : ki == 1 ? form7_kernel<16> : form7_kernel<32>;
+        if ((err = cudaFuncSetAttribute(k7, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) !=
+            cudaSuccess)
+          return err;
+        k7<<<(unsigned)lr.count, 256, lr.smem, fs.next()>>>(
+            e.sig_map[ki], e.f2_blocks + lr.first, reinterpret_cast<const float2 *>(e.Ff),
+            reinterpret_cast<const float2 *>(e.Fh), reinterpret_cast<float2 *>(phi), e.k, n1, nh, ss);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        continue;
+      }
+      if (D == 3 && lr.tensor == 7) return cudaErrorNotSupported;  // needs the packed density
       if (D == 3 && lr.tensor && sizeof(R) == 4) {
         const bool small_n = n1_pad8(n1) / 4 <= 8;
         auto fk = lr.big ? (small_n ? form4_kernel<8, true> : form4_kernel<kNbtMax, true>)
@@ -2928,7 +3308,8 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   for (const LaunchRange &lr : e.e2_ranges) {  // one launch per block size K
-    if (D == 3 && lr.tensor == 7 && sizeof(R) == 4 && e.psi_pitch == e7::kP) {  // all stages on tcgen05
+    if (D == 3 && lr.tensor == 7 && sizeof(R) == 4 && e.psi_pitch == e7::kP && e.psi_map_ready) {
+      // all stages on tcgen05
       auto k7 = lr.K == 8 ? eval7_kernel<8> : lr.K == 16 ? eval7_kernel<16> : eval7_kernel<32>;
       if ((err = cudaFuncSetAttribute(k7, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) != cudaSuccess)
         return err;
@@ -3074,14 +3455,46 @@ cudaError_t selftest_tc_timeout() {
 }
 
 cudaError_t read_tc_status(int *status) {
-  int v = 0, v7 = 0;
+  int v = 0, v7 = 0, vf = 0;
   cudaError_t err = cudaMemcpyFromSymbol(&v, g_tc_status, sizeof(int));
   if (err == cudaSuccess) err = cudaMemcpyFromSymbol(&v7, g_tc7_status, sizeof(int));
+  if (err == cudaSuccess) err = cudaMemcpyFromSymbol(&vf, g_tcf_status, sizeof(int));
   if (err != cudaSuccess) return err;
   const int zero = 0;
   if (v != 0 && (err = cudaMemcpyToSymbol(g_tc_status, &zero, sizeof(int))) != cudaSuccess) return err;
   if (v7 != 0 && (err = cudaMemcpyToSymbol(g_tc7_status, &zero, sizeof(int))) != cudaSuccess) return err;
-  *status = v > v7 ? v : v7;
+  if (vf != 0 && (err = cudaMemcpyToSymbol(g_tcf_status, &zero, sizeof(int))) != cudaSuccess) return err;
+  *status = std::max(v, std::max(v7, vf));
+  return cudaSuccess;
+}
+
+size_t form7_smem_bytes(int K) { return f7::smem_bytes(K); }
+
+cudaError_t encode_sig_maps(ExecDesc &e, int64_t total_floats, const bool *used) {
+  // the packed density as rows of K floats (K = 8, 16, 32), one tensor map each, with the swizzle
+  // of a K-float row so that a 128-row box lands in the tensor cores' K-major layout
+  using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t err = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (err != cudaSuccess) return err;
+  if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+  Encode encode = reinterpret_cast<Encode>(fn);
+  const int Ks[3] = {8, 16, 32};
+  const CUtensorMapSwizzle sw[3] = {CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_SWIZZLE_128B};
+  for (int i = 0; i < 3; ++i) {
+    if (!used[i]) continue;
+    const cuuint64_t K = (cuuint64_t)Ks[i];
+    const cuuint64_t dims[2] = {K, (cuuint64_t)(total_floats / Ks[i])};
+    const cuuint64_t strides[1] = {K * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)K, 128}, estr[2] = {1, 1};
+    const CUresult r = encode(&e.sig_map[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, e.sigp, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, sw[i], CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
   return cudaSuccess;
 }
 
@@ -3159,9 +3572,13 @@ cudaError_t run_transform_noalloc(const ExecDesc &e, const double *sigma, double
   f.phi = base;
   f.psi = static_cast<unsigned char *>(base) + psi_off;
   f.sigp = nullptr;  // no packed sigma: the form kernels read sigma itself
+  f.sig_order = 0;
+  f.phi_stored = 0;  // and the CUDA-core forms add into a cleared slot
   f.psi_tc = nullptr;  // no operand copy of the expansions: the CUDA-core evaluation throughout
   f.n_psi_tc_slots = 0;
   f.psi_pitch = 0;     // and the plain expansion layout (no tensor map over the scratch array)
+  f.psi_map_ready = 0;
+  f.sig_maps_ready = 0;
   f.events = nullptr;
   return run_transform(f, sigma, u, stream);
 }

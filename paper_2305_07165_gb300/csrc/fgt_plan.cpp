@@ -136,6 +136,7 @@ struct fgt_plan {
   bool eval5 = false;       // 3D: evaluation with the half-range axis contracted last
   bool tc_eval6 = false;    // split precision, 3D, K <= 16: evaluation stage 1 on tcgen05 (FGT_TC_EVAL6=1)
   bool eval7 = false;       // split precision, 3D: every evaluation stage on tcgen05 (eval7_kernel)
+  bool form7 = false;       // split precision, 3D: every form stage on tcgen05 (form7_kernel)
   cudaStream_t side[fgt::kSides] = {};     // near field and concurrent per-size launches
   cudaEvent_t fork_ev[fgt::kSides] = {}, join_ev[fgt::kSides] = {};
   DevPack host_pack;        // host copy of the uploaded lists and tables (kept for host-only plans)
@@ -451,6 +452,8 @@ void fill_flops(fgt_plan &P, const fgt::ExecDesc &ex, const std::vector<fgt::Blo
   for (const fgt::LaunchRange &lr : ex.e2_ranges)
     if (lr.tensor == 7) I.n_tc_eval_blocks += lr.count;
   I.n_tc_form_blocks = 0;
+  for (const fgt::LaunchRange &lr : ex.f2_ranges)
+    if (lr.tensor == 7) I.n_tc_form_blocks += lr.count;
 }
 
 template <typename C>
@@ -691,7 +694,38 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
     std::stable_sort(sorted.begin(), sorted.end(), [](const fgt::Block &a, const fgt::Block &b) {
       return a.K != b.K ? a.K < b.K : a.slot < b.slot;
     });
-    size_t q = 0;
+    // every form stage on tcgen05 (form7_kernel): one block per CTA, all blocks of the plan or none;
+    // a block that is its anchor's only one stores the slot (flags bit 1) instead of adding to it
+    bool use_f7 = P.form7 && d == 3 && P.prec == FGT_PREC_SPLIT && !hier && n1 <= 32 && nh <= 16 && !sorted.empty();
+    for (const fgt::Block &b : sorted)
+      use_f7 = use_f7 && (b.K == 8 || b.K == 16 || b.K == 32) && fgt::form7_smem_bytes(b.K) <= (size_t)smax;
+    ex.sig_order = use_f7 ? 1 : 0;
+    ex.phi_stored = 0;
+    if (use_f7) {
+      std::unordered_map<int32_t, int> per_slot;
+      for (const fgt::Block &b : sorted) per_slot[b.slot]++;
+      bool all_sole = true;
+      for (fgt::Block b : sorted) {
+        const bool sole = per_slot[b.slot] == 1;
+        all_sole = all_sole && sole;
+        b.flags = (b.flags & ~2) | (sole ? 2 : 0);
+        if (ex.f2_ranges.empty() || ex.f2_ranges.back().K != b.K) {
+          fgt::LaunchRange lr;
+          lr.first = (int)f2ptr.size() - 1;
+          lr.count = 0;
+          lr.K = b.K;
+          lr.big = b.K > 16 ? 1 : 0;
+          lr.smem = fgt::form7_smem_bytes(b.K);
+          lr.tensor = 7;
+          ex.f2_ranges.push_back(lr);
+        }
+        f2.push_back(b);
+        f2ptr.push_back((int32_t)f2.size());  // groups of one block
+        ex.f2_ranges.back().count++;
+      }
+      ex.phi_stored = all_sole ? 1 : 0;
+    }
+    size_t q = use_f7 ? sorted.size() : 0;
     while (q < sorted.size()) {
       const int K = sorted[q].K, G = gmax(K);
       if (G == 0) {
@@ -742,7 +776,7 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
     });
     // every evaluation stage on tcgen05 (eval7_kernel): it reads the incoming expansions in a padded
     // layout of its own, so it takes all blocks of the plan or none
-    bool use_e7 = P.eval7 && d == 3 && P.prec == FGT_PREC_SPLIT && !hier && !P.fourier &&
+    bool use_e7 = P.eval7 && d == 3 && P.prec == FGT_PREC_SPLIT && !hier && !P.fourier && k % 2 == 0 &&
                   n1 <= fgt::eval7_pitch() && !P.tc_eval && !P.tc_eval4 && !P.tc_eval6 && !P.eval5 &&
                   !esorted.empty();
     for (const fgt::Block &b : esorted)
@@ -1268,14 +1302,27 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   auto at = [&](size_t off) { return (const void *)((const char *)P.dev + off); };
   ex.phi = P.work;
   ex.psi = (char *)P.work + psi_off;
+  ex.psi_map_ready = 0;
   if (ex.psi_pitch > 0) {
     // the padding of the tcgen05 evaluation's layout is never written: zero it once
     e = cudaMemset(ex.psi, 0, psi_bytes);
     if (e == cudaSuccess) e = fgt::encode_psi_map(ex);
     if (e != cudaSuccess) return cuda_fail(e, "tensor map of the expansions");
+    ex.psi_map_ready = 1;
   }
   ex.sigp = sigp_bytes ? (float *)((char *)P.work + sigp_off) : nullptr;
   ex.psi_tc = ptc_bytes ? (void *)((char *)P.work + ptc_off) : nullptr;
+  ex.sig_maps_ready = 0;
+  if (ex.sig_order == 1) {
+    // the tensor maps over the packed density (its address is set just above)
+    if (!ex.sigp) return fail(FGT_ERR_STATE, "tcgen05 form without a packed density");
+    bool used[3] = {false, false, false};
+    for (const fgt::LaunchRange &lr : ex.f2_ranges)
+      if (lr.tensor == 7) used[lr.K == 8 ? 0 : lr.K == 16 ? 1 : 2] = true;
+    e = fgt::encode_sig_maps(ex, ex.n_pack * (int64_t)P.np(), used);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor maps of the packed density");
+    ex.sig_maps_ready = 1;
+  }
   ex.pack_block = (const int32_t *)at(o_pblock);
   ex.blocks = (const fgt::Block *)at(o_blocks);
   ex.f1_blocks = (const fgt::Block *)at(o_f1);
@@ -1383,6 +1430,9 @@ fgt_status create_impl(int d, double delta, double tol, double eps_pw, int bc, i
     // FGT_EVAL7=0 turns it off
     const char *e7 = std::getenv("FGT_EVAL7");
     P->eval7 = !(e7 && e7[0] == '0');
+    // all three form contractions on tcgen05 (split precision, 3D, K = 8, 16, 32, n1 <= 32): FGT_FORM7=1
+    const char *f7 = std::getenv("FGT_FORM7");
+    P->form7 = f7 && f7[0] == '1';
   }
   P->n_leaves = tree->n_leaves;
   P->leaf_level.assign(tree->leaf_level, tree->leaf_level + tree->n_leaves);
@@ -1611,7 +1661,6 @@ fgt_status fgt_plan_set_output_tree(fgt_plan *plan, const fgt_tree *out) {
   const int64_t n = out->n_leaves;
   std::vector<int64_t> src(n);
   std::unordered_map<uint64_t, int64_t> seen;
-  std::vector<uint64_t> covered(plan->n_leaves, 0);  // volume covered, in units of 2^-(d * 20)
   for (int64_t i = 0; i < n; ++i) {
     const int lt = out->leaf_level[i];
     if (lt < 0 || lt > 20) return fail(FGT_ERR_TREE, "output tree: level out of range [0, 20]");
@@ -1633,7 +1682,6 @@ fgt_status fgt_plan_set_output_tree(fgt_plan *plan, const fgt_tree *out) {
     }
     if (leaf < 0) return fail(FGT_ERR_TREE, "output tree: a leaf is not inside one source leaf");
     src[i] = leaf;
-    covered[leaf] += (uint64_t)1 << (d * (20 - lt));
   }
   for (int64_t i = 0; i < n; ++i) {  // no output leaf inside another
     for (int l = out->leaf_level[i] - 1; l >= plan->leaf_level[src[i]]; --l) {
@@ -1642,9 +1690,8 @@ fgt_status fgt_plan_set_output_tree(fgt_plan *plan, const fgt_tree *out) {
       if (seen.count(box_key(l, q))) return fail(FGT_ERR_TREE, "output tree: overlapping leaves");
     }
   }
-  for (int64_t j = 0; j < plan->n_leaves; ++j)
-    if (covered[j] != (uint64_t)1 << (d * (20 - plan->leaf_level[j])))
-      return fail(FGT_ERR_TREE, "output tree: the leaves do not tile every source leaf");
+  // the output leaves need not cover the source leaves: u is evaluated at the given leaves only
+  // (Algorithm 5 re-evaluates the subdivided leaves alone)
   plan->n_out = n;
   plan->out_level.assign(out->leaf_level, out->leaf_level + n);
   plan->out_coord.assign(out->leaf_coord, out->leaf_coord + n * d);

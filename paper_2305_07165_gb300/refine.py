@@ -5,8 +5,8 @@ sharp feature diffused a short distance can be too sharp for the input grid (Sec
 smooth potential can be over-resolved.  ``refine`` evaluates u on an output tree that starts as
 the source tree and subdivides every leaf whose error monitor (eq. funerr, computed on the GPU by
 ``fgt_leaf_errors``) exceeds eps * ||u||_2, at most down to the source tree's deepest level, until
-no leaf is flagged; each round re-evaluates the transform on the new output tree
-(``fgt_plan_set_output_tree``).  ``coarsen`` walks the levels bottom-up and merges 2^d sibling
+no leaf is flagged; each round evaluates the transform only at the new leaves (an output tree of
+the subdivided leaves' children, ``fgt_plan_set_output_tree``) and keeps the others' values.  ``coarsen`` walks the levels bottom-up and merges 2^d sibling
 leaves into their parent when the parent's values (the children's interpolant at its nodes,
 ``fgt_merge_children``) pass the same monitor.  The tree bookkeeping is host logic; the
 transform, the monitor and the interpolation run in the library's kernels.
@@ -60,25 +60,80 @@ def _children(level, coord, d):
 
 
 def refine(plan, sigma, eps, max_level=None, max_rounds=64):
-    """Algorithm 5.  plan: a Plan on the source tree (its output tree is changed); sigma: CUDA
-    [n_leaves, k**d].  Returns (level, coord, u) of the refined output tree and the number of
-    rounds.  Leaves are not subdivided below max_level (default: the source tree's deepest)."""
+    """Algorithm 5.  plan: a Plan on the source tree (its output tree is changed, and restored to
+    the source tree at the end); sigma: CUDA [n_leaves, k**d].  Returns (level, coord, u) of the
+    refined output tree and the number of rounds.  The first round evaluates u on the source tree;
+    each later round evaluates it only at the children of the leaves flagged in the round before
+    (an output tree of those children alone) and keeps every other leaf's values.  Leaves are not
+    subdivided below max_level (default: the source tree's deepest)."""
+    import torch
     d, k = plan.d, plan.k
     level = np.asarray(plan._src_level, dtype=np.int32).copy()
     coord = np.asarray(plan._src_coord, dtype=np.int32).reshape(-1, d).copy()
     lmax = int(level.max()) if max_level is None else int(max_level)
-    rounds = 0
+    plan.set_output_tree(None)
+    u = plan(sigma)
+    err, sq = leaf_errors(u, d, k)
+    err, sq = err.cpu().numpy(), sq.cpu().numpy()
+    rounds = 1
     while True:
-        plan.set_output_tree(level, coord)
-        u = plan(sigma)
-        rounds += 1
-        err, sq = leaf_errors(u, d, k)
-        flag = (err.cpu().numpy() > eps * _norm(sq, level, d)) & (level < lmax)
+        norm = float(np.sqrt(np.sum(sq * (0.5 * np.ldexp(1.0, -level.astype(np.int64))) ** d)))
+        flag = (err > eps * norm) & (level < lmax)
         if not flag.any() or rounds >= max_rounds:
+            plan.set_output_tree(None)
             return level, coord, u, rounds
         cl, cc = _children(level[flag], coord[flag], d)
-        level = np.concatenate([level[~flag], cl])
-        coord = np.concatenate([coord[~flag], cc])
+        plan.set_output_tree(cl, cc)
+        un = plan(sigma)                      # the new leaves only
+        rounds += 1
+        en, sn = leaf_errors(un, d, k)
+        keep = np.where(~flag)[0]
+        u = torch.cat([u[torch.as_tensor(keep, device=u.device)], un])
+        level = np.concatenate([level[keep], cl])
+        coord = np.concatenate([coord[keep], cc])
+        err = np.concatenate([err[keep], en.cpu().numpy()])
+        sq = np.concatenate([sq[keep], sn.cpu().numpy()])
+
+
+def interpolate(level, coord, u, d, k, points):
+    """The tensor Lagrange interpolant of node values u [n, k**d] (CUDA or numpy; node index t_1
+    fastest, Gauss-Legendre nodes) at points [m, d] of B, on the host.  Returns [m]."""
+    u = u.cpu().numpy() if hasattr(u, "cpu") else np.asarray(u)
+    level = np.asarray(level, dtype=np.int64)
+    coord = np.asarray(coord, dtype=np.int64).reshape(-1, d)
+    x = np.polynomial.legendre.leggauss(k)[0]
+    pts = np.asarray(points, dtype=np.float64).reshape(-1, d)
+    # the leaf containing each point, level by level (keys level * 2^60 + packed coordinates)
+    def pack(l, c):
+        kk = np.asarray(l, dtype=np.int64) << 60
+        for a in range(d):
+            kk = kk | (np.asarray(c[..., a], dtype=np.int64) << (20 * a))
+        return kk
+    keys = pack(level, coord)
+    order = np.argsort(keys)
+    sk = keys[order]
+    leaf = np.full(len(pts), -1, dtype=np.int64)
+    for l in range(int(level.min()), int(level.max()) + 1):
+        todo = leaf < 0
+        if not todo.any():
+            break
+        c = np.minimum(np.floor((pts[todo] + 0.5) * (1 << l)), (1 << l) - 1).astype(np.int64)
+        kq = pack(np.full(len(c), l), c)
+        pos = np.clip(np.searchsorted(sk, kq), 0, len(sk) - 1)
+        hit = sk[pos] == kq
+        idx = np.where(todo)[0]
+        leaf[idx[hit]] = order[pos[hit]]
+    L = np.ldexp(1.0, -level[leaf])
+    s = (pts - (-0.5 + (coord[leaf] + 0.5) * L[:, None])) / (0.5 * L[:, None])
+    vals = u[leaf].reshape((len(pts),) + (k,) * d)          # [m, t_d, ..., t_1]
+    for a in range(d):                                      # contract t_1 (last axis) first
+        lag = np.ones((len(pts), k))
+        for j in range(k):
+            for m in range(k):
+                if m != j:
+                    lag[:, j] *= (s[:, a] - x[m]) / (x[j] - x[m])
+        vals = np.einsum("m...j,mj->m...", vals, lag)
+    return vals
 
 
 def coarsen(level, coord, u, d, k, eps, norm=None):

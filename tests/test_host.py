@@ -268,7 +268,9 @@ def test_tuning_knobs_validated_on_a_host_plan():
 
 
 def test_output_tree_validation():
-    """fgt_plan_set_output_tree accepts refinements that tile the source leaves and refuses the rest."""
+    """fgt_plan_set_output_tree accepts non-overlapping output leaves, each inside one source leaf
+    (they need not cover the source leaves, as in a refinement round that re-evaluates the
+    subdivided leaves alone), and refuses the rest."""
     import ctypes
     lev, crd = np.array([1, 1, 1, 1], dtype=np.int32), np.array([[0, 0], [1, 0], [0, 1], [1, 1]], dtype=np.int32)
     hp = F.HostPlan(2, 4, 1e-2, 1e-6, lev, crd)
@@ -281,7 +283,9 @@ def test_output_tree_validation():
     assert try_tree([2] * 16, kids) == 0                                  # every leaf refined once
     assert try_tree([1, 1, 1] + [2] * 4, crd.tolist()[:3] + kids[12:]) == 0  # one leaf refined
     assert try_tree([0], [[0, 0]]) == 2                                   # coarser than the source
-    assert try_tree([1, 1, 1], crd.tolist()[:3]) == 2                     # a source leaf not covered
+    assert try_tree([1, 1, 1], crd.tolist()[:3]) == 0                     # a source leaf left out: allowed
+    assert try_tree([2] * 4, kids[4:8]) == 0                              # only one leaf's children
+    assert try_tree([2] * 3, kids[4:7]) == 0                              # a source leaf partly covered
     assert try_tree([1, 1, 1, 1, 2], crd.tolist() + [[0, 0]]) == 2         # overlapping leaves
     assert try_tree([1, 1, 1, 1, 1], crd.tolist() + [[0, 0]]) == 2         # repeated leaf
     assert F.lib().fgt_plan_set_output_tree(hp._h, None) == 0
