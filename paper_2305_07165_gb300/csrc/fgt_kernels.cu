@@ -700,9 +700,10 @@ __global__ void __launch_bounds__(256) sigma_pack_kernel(const Block *__restrict
                                                          const int32_t *__restrict__ pack_block,
                                                          const int64_t *__restrict__ bleaves,
                                                          const double *__restrict__ sigma, float *__restrict__ sigp,
-                                                         int k, int j3_fastest) {
+                                                         int k) {
   const int64_t i = blockIdx.x;
   const Block b = blocks[pack_block[i]];
+  const bool j3_fastest = (b.flags & 4) != 0;  // the block is formed by the tcgen05 form
   const int kp = k * k * k, nl = 1 << b.dl, K = b.K;
   const int leafi = (int)(i - b.leaf0);
   const int o1 = leafi % nl, o2 = (leafi / nl) % nl, o3 = leafi / (nl * nl);
@@ -1919,16 +1920,16 @@ __global__ void __launch_bounds__(256, 1) eval7_kernel(const __grid_constant__ C
     }
     __syncthreads();
     // runs: (I3, o1) -> RI2 rows of k values (I2l, i1), contiguous in u within a leaf; pairs of
-    // values per thread (k even)
-    const int I2base = t * RI2;
-    const int runlen = RI2 * k, nruns = K * nl, npairs = nruns * runlen / 2;
+    // values per thread.  k and nl are powers of two here (K = nl k = 8, 16, 32, k even): shifts.
+    const int I2base = t * RI2, lk = __ffs(k) - 1, lnl = blk.dl, lr = __ffs(RI2) - 1 + lk;
+    const int npairs = (K * nl * RI2 * k) >> 1;
     for (int e = tid; e < npairs; e += blockDim.x) {
-      const int pe = 2 * e, run = pe / runlen, w = pe - run * runlen;
-      const int I3 = run / nl, o1 = run - I3 * nl, I2l = w / k, i1 = w - I2l * k;
-      const int o3 = I3 / k, I2 = I2base + I2l, o2 = I2 / k;
-      const double v0 = stage[I3 * (RI2 * K) + I2l * K + o1 * k + i1];
-      const double v1 = stage[I3 * (RI2 * K) + I2l * K + o1 * k + i1 + 1];
-      double *up = u + lofs[(o3 * nl + o2) * nl + o1] + ((I3 - o3 * k) * k + (I2 - o2 * k)) * k + i1;
+      const int pe = 2 * e, run = pe >> lr, w = pe & ((1 << lr) - 1);
+      const int I3 = run >> lnl, o1 = run & (nl - 1), I2l = w >> lk, i1 = w & (k - 1);
+      const int o3 = I3 >> lk, I2 = I2base + I2l, o2 = I2 >> lk;
+      const double2 vv = *reinterpret_cast<const double2 *>(stage + I3 * (RI2 * K) + I2l * K + (o1 << lk) + i1);
+      const double v0 = vv.x, v1 = vv.y;
+      double *up = u + lofs[(((o3 << lnl) + o2) << lnl) + o1] + ((((I3 & (k - 1)) << lk) + (I2 & (k - 1))) << lk) + i1;
       if (acc_u) {
         if (FGT_OK_PTR(up)) atomicAdd(up, v0);
         if (FGT_OK_PTR(up + 1)) atomicAdd(up + 1, v1);
@@ -3177,7 +3178,7 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
       return err;
     if (D == 3 && sizeof(R) == 4 && e.sigp != nullptr && e.n_pack > 0) {
       sigma_pack_kernel<<<(unsigned)e.n_pack, 256, 0, st>>>(e.blocks, e.pack_block, e.block_leaves, sigma, e.sigp,
-                                                            e.k, e.sig_order);
+                                                            e.k);
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     Spread fs(e, st);

@@ -136,7 +136,8 @@ struct fgt_plan {
   bool eval5 = false;       // 3D: evaluation with the half-range axis contracted last
   bool tc_eval6 = false;    // split precision, 3D, K <= 16: evaluation stage 1 on tcgen05 (FGT_TC_EVAL6=1)
   bool eval7 = false;       // split precision, 3D: every evaluation stage on tcgen05 (eval7_kernel)
-  bool form7 = false;       // split precision, 3D: every form stage on tcgen05 (form7_kernel)
+  bool form7 = false;       // split precision, 3D: every form stage on tcgen05 (form7_kernel), K = 16, 32
+  bool form7_k8 = false;    // and for K = 8 blocks
   cudaStream_t side[fgt::kSides] = {};     // near field and concurrent per-size launches
   cudaEvent_t fork_ev[fgt::kSides] = {}, join_ev[fgt::kSides] = {};
   DevPack host_pack;        // host copy of the uploaded lists and tables (kept for host-only plans)
@@ -694,20 +695,32 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
     std::stable_sort(sorted.begin(), sorted.end(), [](const fgt::Block &a, const fgt::Block &b) {
       return a.K != b.K ? a.K < b.K : a.slot < b.slot;
     });
-    // every form stage on tcgen05 (form7_kernel): one block per CTA, all blocks of the plan or none;
-    // a block that is its anchor's only one stores the slot (flags bit 1) instead of adding to it
-    bool use_f7 = P.form7 && d == 3 && P.prec == FGT_PREC_SPLIT && !hier && n1 <= 32 && nh <= 16 && !sorted.empty();
-    for (const fgt::Block &b : sorted)
-      use_f7 = use_f7 && (b.K == 8 || b.K == 16 || b.K == 32) && fgt::form7_smem_bytes(b.K) <= (size_t)smax;
-    ex.sig_order = use_f7 ? 1 : 0;
+    // every form stage on tcgen05 (form7_kernel) for the blocks of the sizes it takes, one block per
+    // CTA: their density is packed in (J1, J2, J3) order (flags bit 2), and a block that is its
+    // anchor's only one stores the slot (flags bit 1) instead of adding to it
+    const bool f7_plan = P.form7 && d == 3 && P.prec == FGT_PREC_SPLIT && !hier && n1 <= 32 && nh <= 16;
+    auto f7_block = [&](int K) {
+      return f7_plan && (K == 16 || K == 32 || (K == 8 && P.form7_k8)) && fgt::form7_smem_bytes(K) <= (size_t)smax;
+    };
+    ex.sig_order = 0;
     ex.phi_stored = 0;
-    if (use_f7) {
+    size_t q = 0;
+    {
       std::unordered_map<int32_t, int> per_slot;
       for (const fgt::Block &b : sorted) per_slot[b.slot]++;
-      bool all_sole = true;
+      bool all_sole = true, any_f7 = false;
+      for (const fgt::Block &b : sorted) all_sole = all_sole && (per_slot[b.slot] == 1 && f7_block(b.K));
+      for (fgt::Block &b : blocks)
+        if (f7_block(b.K)) b.flags |= 4;   // the packing order of its density
+      std::vector<fgt::Block> rest;
       for (fgt::Block b : sorted) {
+        if (!f7_block(b.K)) {
+          rest.push_back(b);
+          continue;
+        }
+        any_f7 = true;
+        b.flags |= 4;
         const bool sole = per_slot[b.slot] == 1;
-        all_sole = all_sole && sole;
         b.flags = (b.flags & ~2) | (sole ? 2 : 0);
         if (ex.f2_ranges.empty() || ex.f2_ranges.back().K != b.K) {
           fgt::LaunchRange lr;
@@ -723,9 +736,10 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
         f2ptr.push_back((int32_t)f2.size());  // groups of one block
         ex.f2_ranges.back().count++;
       }
+      ex.sig_order = any_f7 ? 1 : 0;
       ex.phi_stored = all_sole ? 1 : 0;
+      sorted.swap(rest);  // the other blocks go to the CUDA-core forms below
     }
-    size_t q = use_f7 ? sorted.size() : 0;
     while (q < sorted.size()) {
       const int K = sorted[q].K, G = gmax(K);
       if (G == 0) {
@@ -1430,9 +1444,12 @@ fgt_status create_impl(int d, double delta, double tol, double eps_pw, int bc, i
     // FGT_EVAL7=0 turns it off
     const char *e7 = std::getenv("FGT_EVAL7");
     P->eval7 = !(e7 && e7[0] == '0');
-    // all three form contractions on tcgen05 (split precision, 3D, K = 8, 16, 32, n1 <= 32): FGT_FORM7=1
+    // all three form contractions on tcgen05 (split precision, 3D, n1 <= 32): by default for blocks of
+    // K = 16 and 32 (measured 1.4x faster than the CUDA-core form on the 16.8M-point periodic
+    // workload; for K = 8 blocks slower), FGT_FORM7=1 for K = 8 as well, FGT_FORM7=0 for none
     const char *f7 = std::getenv("FGT_FORM7");
-    P->form7 = f7 && f7[0] == '1';
+    P->form7 = !(f7 && f7[0] == '0');
+    P->form7_k8 = f7 && f7[0] == '1';
   }
   P->n_leaves = tree->n_leaves;
   P->leaf_level.assign(tree->leaf_level, tree->leaf_level + tree->n_leaves);

@@ -82,3 +82,21 @@ def test_all_stage_tcgen05_form_full_size(monkeypatch, which):
     uo = oracle.box_fgt(3, w.p, w.delta, w.periodic, w.tree.level, w.tree.coord, w.sigma, targets=tg)
     assert np.all(np.isfinite(u7))
     assert np.abs(u7[tg] - uo).max() <= 10 * 1e-6 * np.abs(uo).max()
+
+
+def test_default_mixes_tcgen05_and_cuda_core_forms(monkeypatch):
+    """By default the tcgen05 form takes the blocks of K = 16 and 32 and the CUDA-core form the
+    K = 8 ones, in one plan: the density is packed block by block in the order each kernel reads."""
+    monkeypatch.delenv("FGT_FORM7", raising=False)
+    monkeypatch.delenv("FGT_EVAL7", raising=False)
+    tr = _tree("random")
+    sig = W.random_sigma(tr, 8, 44)
+    plan = F.Plan(3, 8, 3e-3, 1e-6, tr.level, tr.coord, prec=F.PREC_SPLIT)
+    info = plan.info()
+    u = plan(torch.from_numpy(sig).cuda()).cpu().numpy()
+    plan.close()
+    assert 0 < info["n_tc_form_blocks"] < info["n_form_blocks"]
+    u0, _, _, _ = _run(monkeypatch, False, tr, 8, 3e-3, sig, eval7=False)
+    assert np.abs(u - u0).max() <= 2e-6 * np.abs(u0).max()
+    uo = oracle.box_fgt(3, 8, 3e-3, False, tr.level, tr.coord, sig)
+    assert np.abs(u - uo).max() <= 10 * 1e-6 * np.abs(uo).max()
