@@ -294,9 +294,29 @@ def run_batched_and_serving(args, F, torch, large=()):
         torch.cuda.synchronize()
         t_serial = e0.elapsed_time(e1) / reps
         t_graph = e1.elapsed_time(e2) / reps
+        # the same transforms as one persistent kernel over a device work queue
+        ref = [o.clone() for o in out]
+        pb = F.Batch(plans, mode=F.BATCH_PERSISTENT)
+        pout = [torch.empty_like(o) for o in out]
+        for _ in range(2):
+            pb(sig, pout)
+        torch.cuda.synchronize()
+        e3, e4 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e3.record(st)
+        for _ in range(reps):
+            pb(sig, pout)
+        e4.record(st)
+        torch.cuda.synchronize()
+        t_pers = e3.elapsed_time(e4) / reps
+        pdiff = max(float((a - r).abs().max() / r.abs().max()) for a, r in zip(pout, ref))
+        pinfo, pstat = pb.info(), pb.status()
+        pb.close()
         from collections import Counter
         res[name] = {"serial_ms": t_serial, "serial_points_per_s": npts / t_serial * 1e3,
                      "batched_ms": t_graph, "batched_points_per_s": npts / t_graph * 1e3,
+                     "persistent_ms": t_pers, "persistent_points_per_s": npts / t_pers * 1e3,
+                     "persistent": {"items": pinfo["items"], "grid": pinfo["grid"], "status": pstat,
+                                    "max_rel_diff_vs_graph": pdiff},
                      "autotune_s": tune_s,
                      "autotuned": {k: dict(Counter(int(t[k]) for t in knobs))
                                    for k in ("form_group", "eval_rows16", "eval_rows_large", "near_phase")}}

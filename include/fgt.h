@@ -47,7 +47,7 @@ typedef enum {
   FGT_ERR_TREE = 2,     /* leaves do not tile B, overlap, or are not 2:1 balanced */
   FGT_ERR_OOM = 3,      /* device or host allocation failed */
   FGT_ERR_CUDA = 4,     /* a CUDA call failed (message has the CUDA error string) */
-  FGT_ERR_TIMEOUT = 5,  /* a bounded device wait gave up (reserved for batched execution) */
+  FGT_ERR_TIMEOUT = 5,  /* a bounded device wait gave up (persistent batches: fgt_batch_status) */
   FGT_ERR_STATE = 6     /* call not valid in the plan's current state */
 } fgt_status;
 
@@ -212,6 +212,29 @@ fgt_status fgt_host_sync(fgt_plan *plan);
  * fgt_execute_batch = create + execute + synchronise `stream` + destroy. */
 typedef struct fgt_batch fgt_batch;
 fgt_status fgt_batch_create(fgt_plan *const *plans, int n, fgt_batch **out);
+
+/* Persistent batched execution (no counterpart in the paper).  fgt_batch_create_mode with
+ * FGT_BATCH_PERSISTENT lists every kernel launch of every transform as items of one device work
+ * queue: an item is one CTA's share of one launch (transform, phase, block, row chunk).
+ * fgt_batch_execute then enqueues ONE persistent kernel (one CTA per SM) whose CTAs pop the items in
+ * order and run them with the same device code as the single-transform kernels.  Items of a phase
+ * (clear, pack, form, gather, evaluate; near field after the clear) wait for their own transform's
+ * previous phase through per-transform counters, every wait bounded (about one second); a wait that
+ * runs out skips its item and sets the batch status word, read and cleared by fgt_batch_status
+ * (0: none ran out, FGT_ERR_TIMEOUT otherwise), so nothing can hang.  The queue uses the CUDA-core
+ * kernels (a plan's tcgen05 ranges take their CUDA-core fallbacks) and the plain expansion layout.
+ * Plans in hierarchical mode or FP64 tensor-core precision are refused with FGT_ERR_ARG.
+ * FGT_BATCH_GRAPH is fgt_batch_create's graph of per-transform branches.  fgt_batch_get_info
+ * returns the mode, the number of queue items and the persistent grid size.
+ * fgt_selftest_batch_timeout runs the persistent kernel on one item whose dependency nothing
+ * satisfies, with a wait of about a millisecond, and returns the status it set (FGT_ERR_TIMEOUT).  Faults
+ * nothing, hangs nothing; synchronous. */
+#define FGT_BATCH_GRAPH 0
+#define FGT_BATCH_PERSISTENT 1
+fgt_status fgt_batch_create_mode(fgt_plan *const *plans, int n, int mode, fgt_batch **out);
+fgt_status fgt_batch_status(fgt_batch *batch, int *status);
+fgt_status fgt_batch_get_info(const fgt_batch *batch, int *mode, int64_t *items, int *grid);
+fgt_status fgt_selftest_batch_timeout(int *status);
 fgt_status fgt_batch_execute(fgt_batch *batch, const double *const *sigma_dev, double *const *u_dev, void *stream);
 void fgt_batch_destroy(fgt_batch *batch);
 fgt_status fgt_execute_batch(fgt_plan *const *plans, const double *const *sigma_dev, double *const *u_dev, int n,

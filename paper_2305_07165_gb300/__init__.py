@@ -105,6 +105,13 @@ def lib():
             L.fgt_execute_noalloc.argtypes = [vp, vp, vp, vp]
             L.fgt_execute_noalloc.restype = ctypes.c_int
             L.fgt_batch_create.argtypes = [vp, i32, vp]
+            L.fgt_batch_create_mode.argtypes = [vp, i32, i32, vp]
+            L.fgt_batch_status.argtypes = [vp, vp]
+            L.fgt_batch_get_info.argtypes = [vp, vp, vp, vp]
+            L.fgt_selftest_batch_timeout.argtypes = [vp]
+            for name in ("fgt_batch_create_mode", "fgt_batch_status", "fgt_batch_get_info",
+                         "fgt_selftest_batch_timeout"):
+                getattr(L, name).restype = ctypes.c_int
             L.fgt_batch_execute.argtypes = [vp, vp, vp, vp]
             L.fgt_batch_destroy.argtypes = [vp]
             L.fgt_batch_destroy.restype = None
@@ -176,6 +183,14 @@ def device_status() -> int:
     (and clears it)."""
     v = ctypes.c_int(0)
     _check(lib().fgt_device_status(ctypes.byref(v)))
+    return v.value
+
+
+def selftest_batch_timeout() -> int:
+    """Runs the persistent batch kernel on one item whose dependency nothing satisfies (a wait of
+    about a millisecond); returns the status it reports (FGT_ERR_TIMEOUT)."""
+    v = ctypes.c_int()
+    _check(lib().fgt_selftest_batch_timeout(ctypes.byref(v)))
     return v.value
 
 
@@ -406,18 +421,38 @@ class Plan:
             pass
 
 
-class Batch:
-    """Independent transforms run as one CUDA graph launch (each transform a parallel branch).
+BATCH_GRAPH, BATCH_PERSISTENT = 0, 1
+ERR_TIMEOUT = 5
 
-    ``batch(sigmas, outs)`` enqueues all transforms on the current stream; the graph is
-    captured on the first call and recaptured only when a tensor pointer changes.
+
+class Batch:
+    """Independent transforms in one launch.
+
+    mode BATCH_GRAPH: one CUDA graph, each transform a parallel branch (captured on the first call,
+    recaptured only when a tensor pointer changes).  mode BATCH_PERSISTENT: one persistent kernel
+    over a device work queue of every transform's (phase, block) items, with per-transform phase
+    counters and bounded waits (``status()`` reports a wait that ran out).  ``batch(sigmas, outs)``
+    enqueues all transforms on the current stream.
     """
 
-    def __init__(self, plans):
+    def __init__(self, plans, mode=BATCH_GRAPH):
         self.plans = list(plans)
+        self.mode = mode
         arr = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
         self._h = ctypes.c_void_p()
-        _check(lib().fgt_batch_create(arr, len(self.plans), ctypes.byref(self._h)))
+        _check(lib().fgt_batch_create_mode(arr, len(self.plans), int(mode), ctypes.byref(self._h)))
+
+    def status(self) -> int:
+        """0, or FGT_ERR_TIMEOUT when a dependency wait of the persistent kernel ran out since the
+        last call (read and cleared; synchronous)."""
+        v = ctypes.c_int()
+        _check(lib().fgt_batch_status(self._h, ctypes.byref(v)))
+        return v.value
+
+    def info(self) -> dict:
+        m, n, g = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int()
+        _check(lib().fgt_batch_get_info(self._h, ctypes.byref(m), ctypes.byref(n), ctypes.byref(g)))
+        return {"mode": m.value, "items": n.value, "grid": g.value}
 
     def execute(self, sigmas, outs, stream=None):
         import torch

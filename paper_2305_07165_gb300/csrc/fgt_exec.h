@@ -137,6 +137,21 @@ constexpr int kCheckRanges = 8;
 cudaError_t set_check_ranges(const void *const *base, const size_t *bytes, int n, cudaStream_t st);
 cudaError_t read_check(unsigned *site, unsigned *count, int *checked);
 
+// Persistent batched execution: the launches of many transforms (fused mode) as items of one device
+// work queue, run by one persistent kernel with per-transform phase counters and bounded waits.
+// batch_queue_create sets *why (and *out = nullptr) when a plan cannot be queued.  wait_clocks bounds
+// every dependency wait (a wait that runs out sets the batch status word to 1).
+struct BatchQueue;
+cudaError_t batch_queue_create(const std::vector<const ExecDesc *> &plans, BatchQueue **out, const char **why);
+cudaError_t batch_queue_run(BatchQueue *q, const double *const *sigma, double *const *u, cudaStream_t st,
+                            long long wait_clocks);
+cudaError_t batch_queue_status(BatchQueue *q, int *status);  // read and clear; synchronous
+size_t batch_queue_items(const BatchQueue *q);
+int batch_queue_grid(const BatchQueue *q);
+void batch_queue_destroy(BatchQueue *q);
+// One item whose dependency nothing satisfies, with a wait of about a millisecond: *status = 1.
+cudaError_t selftest_batch_timeout(int *status);
+
 // Reads and clears the status word of the tcgen05 kernels: 1 when a wait on the tensor cores ran
 // out since the last read (the affected blocks were skipped), else 0.  Synchronous.
 cudaError_t read_tc_status(int *status);

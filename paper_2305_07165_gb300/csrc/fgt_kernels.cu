@@ -84,17 +84,17 @@ __device__ __noinline__ bool chk_bytes(const void *p, size_t n, int site) {
 // ----------------------------------------------------------------------------- form
 
 template <int D, typename R>
-__global__ void __launch_bounds__(256) form_kernel(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
+__device__ __forceinline__ void form_body(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
                                                    const double *__restrict__ sigma,
                                                    const typename C2T<R>::T *__restrict__ Ff,
                                                    const typename C2T<R>::T *__restrict__ Fh,
                                                    typename C2T<R>::T *__restrict__ phi, int k, int n1, int nh,
-                                                   int64_t slot_size, int Kmax) {
+                                                   int64_t slot_size, int Kmax, int bx, int by) {
   using C = typename C2T<R>::T;
   extern __shared__ unsigned char smem_raw[];
   C *Z1 = reinterpret_cast<C *>(smem_raw);
-  const Block blk = blocks[blockIdx.x];
-  const int s = blockIdx.y;  // index along the half-range (last) axis
+  const Block blk = blocks[bx];
+  const int s = by;  // index along the half-range (last) axis
   const int K = blk.K, nl = 1 << blk.dl;
   const int64_t *lv = bleaves + blk.leaf0;
   C *out = phi + (int64_t)blk.slot * slot_size;
@@ -182,19 +182,30 @@ __global__ void __launch_bounds__(256) form_kernel(const Block *__restrict__ blo
   }
 }
 
+
+template <int D, typename R>
+__global__ void __launch_bounds__(256) form_kernel(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
+                                                   const double *__restrict__ sigma,
+                                                   const typename C2T<R>::T *__restrict__ Ff,
+                                                   const typename C2T<R>::T *__restrict__ Fh,
+                                                   typename C2T<R>::T *__restrict__ phi, int k, int n1, int nh,
+                                                   int64_t slot_size, int Kmax) {
+  form_body<D, R>(blocks, bleaves, sigma, Ff, Fh, phi, k, n1, nh, slot_size, Kmax, blockIdx.x, blockIdx.y);
+}
+
 // ----------------------------------------------------------------------------- evaluation
 
 template <int D, typename R>
-__global__ void __launch_bounds__(256) eval_kernel(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
+__device__ __forceinline__ void eval_body(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
                                                    const typename C2T<R>::T *__restrict__ Ef,
                                                    const typename C2T<R>::T *__restrict__ Eh,
                                                    const typename C2T<R>::T *__restrict__ psi, double *__restrict__ u,
-                                                   int k, int n1, int nh, int64_t slot_size) {
+                                                   int k, int n1, int nh, int64_t slot_size, int bx, int by) {
   using C = typename C2T<R>::T;
   extern __shared__ unsigned char smem_raw[];
   C *Y1 = reinterpret_cast<C *>(smem_raw);
-  const Block blk = blocks[blockIdx.x];
-  const int r = blockIdx.y;  // output index along the last axis
+  const Block blk = blocks[bx];
+  const int r = by;  // output index along the last axis
   if (r >= blk.K) return;
   const int K = blk.K, nl = 1 << blk.dl;
   const int64_t *lv = bleaves + blk.leaf0;
@@ -262,6 +273,16 @@ __global__ void __launch_bounds__(256) eval_kernel(const Block *__restrict__ blo
   }
 }
 
+
+template <int D, typename R>
+__global__ void __launch_bounds__(256) eval_kernel(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
+                                                   const typename C2T<R>::T *__restrict__ Ef,
+                                                   const typename C2T<R>::T *__restrict__ Eh,
+                                                   const typename C2T<R>::T *__restrict__ psi, double *__restrict__ u,
+                                                   int k, int n1, int nh, int64_t slot_size) {
+  eval_body<D, R>(blocks, bleaves, Ef, Eh, psi, u, k, n1, nh, slot_size, blockIdx.x, blockIdx.y);
+}
+
 // ----------------------------------------------------------------------------- grouped form
 
 // A CTA takes up to G blocks of one anchor (same K) and one m_d plane: their sigma (converted
@@ -270,16 +291,16 @@ __global__ void __launch_bounds__(256) eval_kernel(const Block *__restrict__ blo
 // coefficient (G times fewer atomics than one CTA per block).  The x_1 matrices are stored transposed ([J][m]) so that
 // threads reading consecutive modes hit consecutive banks.
 template <int D, typename R>
-__global__ void __launch_bounds__(256) form2_kernel(const Block *__restrict__ blocks, const int32_t *__restrict__ gptr,
+__device__ __forceinline__ void form2_body(const Block *__restrict__ blocks, const int32_t *__restrict__ gptr,
                                                     const int64_t *__restrict__ bleaves,
                                                     const double *__restrict__ sigma,
                                                     const typename C2T<R>::T *__restrict__ Ff,
                                                     const typename C2T<R>::T *__restrict__ Fh,
                                                     typename C2T<R>::T *__restrict__ phi, int k, int n1, int nh,
-                                                    int64_t slot_size) {
+                                                    int64_t slot_size, int bx, int by) {
   using C = typename C2T<R>::T;
   extern __shared__ unsigned char smem_raw[];
-  const int b0 = gptr[blockIdx.x], G = gptr[blockIdx.x + 1] - b0;
+  const int b0 = gptr[bx], G = gptr[bx + 1] - b0;
   const Block B0 = blocks[b0];
   const int K = B0.K, nl = 1 << B0.dl;
   const int KK = K * K, npb = (D == 3) ? KK * K : KK, kp = (D == 3) ? k * k * k : k * k;
@@ -318,7 +339,7 @@ __global__ void __launch_bounds__(256) form2_kernel(const Block *__restrict__ bl
   __syncthreads();
   C *out = phi + (int64_t)B0.slot * slot_size;
   {
-    const int s = blockIdx.y;  // one m_d plane per CTA
+    const int s = by;  // one m_d plane per CTA
     if (D == 3) {
       // Z1[g][J2][J1] = sum_J3 Fd[g][s][J3] sig[g][J3][J2][J1]
       for (int e = threadIdx.x; e < G * KK; e += blockDim.x) {
@@ -395,6 +416,18 @@ __global__ void __launch_bounds__(256) form2_kernel(const Block *__restrict__ bl
   }
 }
 
+
+template <int D, typename R>
+__global__ void __launch_bounds__(256) form2_kernel(const Block *__restrict__ blocks, const int32_t *__restrict__ gptr,
+                                                    const int64_t *__restrict__ bleaves,
+                                                    const double *__restrict__ sigma,
+                                                    const typename C2T<R>::T *__restrict__ Ff,
+                                                    const typename C2T<R>::T *__restrict__ Fh,
+                                                    typename C2T<R>::T *__restrict__ phi, int k, int n1, int nh,
+                                                    int64_t slot_size) {
+  form2_body<D, R>(blocks, gptr, bleaves, sigma, Ff, Fh, phi, k, n1, nh, slot_size, blockIdx.x, blockIdx.y);
+}
+
 // ----------------------------------------------------------------------------- register-tiled form (3D)
 //
 // A CTA takes a group of G blocks of one anchor (same K) and a chunk of up to kSc planes m_3.
@@ -447,20 +480,20 @@ __device__ __forceinline__ void zgemm8_dmma(double (&acc)[2 * NBLK][2], const do
 }
 
 template <typename R, bool TC>  // TC (FP64 only): stage 3 on the tensor cores (DMMA)
-__global__ void __launch_bounds__(256) form3_kernel(const Block *__restrict__ blocks, const int32_t *__restrict__ gptr,
+__device__ __forceinline__ void form3_body(const Block *__restrict__ blocks, const int32_t *__restrict__ gptr,
                                                     const int64_t *__restrict__ bleaves,
                                                     const double *__restrict__ sigma,
                                                     const typename C2T<R>::T *__restrict__ Ff,
                                                     const typename C2T<R>::T *__restrict__ Fh,
                                                     typename C2T<R>::T *__restrict__ phi, int k, int n1, int nh,
-                                                    int64_t slot_size) {
+                                                    int64_t slot_size, int bx, int by) {
   using C = typename C2T<R>::T;
   extern __shared__ unsigned char smem_raw[];
-  const int b0 = gptr[blockIdx.x], G = gptr[blockIdx.x + 1] - b0;
+  const int b0 = gptr[bx], G = gptr[bx + 1] - b0;
   const Block B0 = blocks[b0];
   const int K = B0.K, nl = 1 << B0.dl;
   const int KK = K * K, npb = KK * K, kp = k * k * k, GK = G * K, ldz = pad_gk(GK);
-  const int s0 = blockIdx.y * kSc, ns = min(kSc, nh - s0);
+  const int s0 = by * kSc, ns = min(kSc, nh - s0);
   R *sig = reinterpret_cast<R *>(smem_raw);                                   // [G][K^3]
   const size_t sig_bytes = ((size_t)G * npb * sizeof(R) + 15) & ~(size_t)15;
   C *F1t = reinterpret_cast<C *>(smem_raw + sig_bytes);                       // [G K][n1]
@@ -629,6 +662,18 @@ __global__ void __launch_bounds__(256) form3_kernel(const Block *__restrict__ bl
   }
 }
 
+
+template <typename R, bool TC>  // TC (FP64 only): stage 3 on the tensor cores (DMMA)
+__global__ void __launch_bounds__(256) form3_kernel(const Block *__restrict__ blocks, const int32_t *__restrict__ gptr,
+                                                    const int64_t *__restrict__ bleaves,
+                                                    const double *__restrict__ sigma,
+                                                    const typename C2T<R>::T *__restrict__ Ff,
+                                                    const typename C2T<R>::T *__restrict__ Fh,
+                                                    typename C2T<R>::T *__restrict__ phi, int k, int n1, int nh,
+                                                    int64_t slot_size) {
+  form3_body<R, TC>(blocks, gptr, bleaves, sigma, Ff, Fh, phi, k, n1, nh, slot_size, blockIdx.x, blockIdx.y);
+}
+
 // ----------------------------------------------------------------------------- 3xTF32 tensor-core helpers
 //
 // Split-precision contractions on the tensor cores: every FP32 operand x is split into
@@ -696,12 +741,12 @@ __device__ __forceinline__ double f32_to_f64_int(uint32_t b) {
   return __hiloint2double((int)(s | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
 }
 
-__global__ void __launch_bounds__(256) sigma_pack_kernel(const Block *__restrict__ blocks,
+__device__ __forceinline__ void sigma_pack_body(const Block *__restrict__ blocks,
                                                          const int32_t *__restrict__ pack_block,
                                                          const int64_t *__restrict__ bleaves,
                                                          const double *__restrict__ sigma, float *__restrict__ sigp,
-                                                         int k) {
-  const int64_t i = blockIdx.x;
+                                                         int k, int bx, int by) {
+  const int64_t i = bx;
   const Block b = blocks[pack_block[i]];
   const bool j3_fastest = (b.flags & 4) != 0;  // the block is formed by the tcgen05 form
   const int kp = k * k * k, nl = 1 << b.dl, K = b.K;
@@ -730,6 +775,15 @@ __global__ void __launch_bounds__(256) sigma_pack_kernel(const Block *__restrict
   }
 }
 
+
+__global__ void __launch_bounds__(256) sigma_pack_kernel(const Block *__restrict__ blocks,
+                                                         const int32_t *__restrict__ pack_block,
+                                                         const int64_t *__restrict__ bleaves,
+                                                         const double *__restrict__ sigma, float *__restrict__ sigp,
+                                                         int k) {
+  sigma_pack_body(blocks, pack_block, bleaves, sigma, sigp, k, blockIdx.x, blockIdx.y);
+}
+
 // ----------------------------------------------------------------------------- tensor-core form (3D, FP32)
 //
 // Same work split as form3_kernel; stages 1-2 on the CUDA cores, stage 3 (the largest,
@@ -743,19 +797,19 @@ __host__ __device__ inline int ldz4(int GK) { return GK + 2; }       // complex 
 __host__ __device__ inline int ldb4(int GK) { return 2 * GK + 4; }   // uint32 row stride of Bh / Bl
 
 template <int NBT, bool BIG>  // NBT: n-tiles of 8 output columns held in registers (>= 2 n1p / 8)
-__global__ void __launch_bounds__(256, BIG ? 2 : (NBT > 8 ? 2 : 3)) form4_kernel(const Block *__restrict__ blocks, const int32_t *__restrict__ gptr,
+__device__ __forceinline__ void form4_body(const Block *__restrict__ blocks, const int32_t *__restrict__ gptr,
                                                     const int64_t *__restrict__ bleaves,
                                                     const double *__restrict__ sigma, const float *__restrict__ sigp,
                                                     const float2 *__restrict__ Ff, const float2 *__restrict__ Fh,
                                                     float2 *__restrict__ phi, int k, int n1, int nh,
-                                                    int64_t slot_size) {
+                                                    int64_t slot_size, int bx, int by) {
   using R = float;
   using C = float2;
   extern __shared__ __align__(16) unsigned char smem4[];
   // linear grid, plane chunk fastest: the CTAs of one group run close together and share its
   // sigma and matrices in L2
   const int nchunk = (nh + kSc - 1) / kSc;
-  const int grp = (int)(blockIdx.x / nchunk), chunk = (int)(blockIdx.x - (unsigned)grp * nchunk);
+  const int grp = (int)(bx / nchunk), chunk = (int)(bx - (unsigned)grp * nchunk);
   const int b0 = gptr[grp], G = gptr[grp + 1] - b0;
   const Block B0 = blocks[b0];
   const int K = B0.K, nl = 1 << B0.dl;
@@ -1010,6 +1064,17 @@ __global__ void __launch_bounds__(256, BIG ? 2 : (NBT > 8 ? 2 : 3)) form4_kernel
   }
 }
 
+
+template <int NBT, bool BIG>  // NBT: n-tiles of 8 output columns held in registers (>= 2 n1p / 8)
+__global__ void __launch_bounds__(256, BIG ? 2 : (NBT > 8 ? 2 : 3)) form4_kernel(const Block *__restrict__ blocks, const int32_t *__restrict__ gptr,
+                                                    const int64_t *__restrict__ bleaves,
+                                                    const double *__restrict__ sigma, const float *__restrict__ sigp,
+                                                    const float2 *__restrict__ Ff, const float2 *__restrict__ Fh,
+                                                    float2 *__restrict__ phi, int k, int n1, int nh,
+                                                    int64_t slot_size) {
+  form4_body<NBT, BIG>(blocks, gptr, bleaves, sigma, sigp, Ff, Fh, phi, k, n1, nh, slot_size, blockIdx.x, blockIdx.y);
+}
+
 // ----------------------------------------------------------------------------- whole-block evaluation
 
 // Stage 2 of the 3D evaluation on the CUDA cores (shared by the whole-block kernels):
@@ -1147,16 +1212,16 @@ __device__ __forceinline__ void eval_stage3_3d(const typename C2T<R>::T *__restr
 // anchor's incoming expansion is read once per CTA (each thread keeps KM accumulators for its
 // mode column), then the two remaining contractions run from shared memory.
 template <int D, typename R, int KM, bool TC = false>  // TC (FP64, 3D): stages 1-2 on the tensor cores
-__global__ void __launch_bounds__(256) eval2_kernel(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
+__device__ __forceinline__ void eval2_body(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
                                                     const typename C2T<R>::T *__restrict__ Ef,
                                                     const typename C2T<R>::T *__restrict__ Eh,
                                                     const typename C2T<R>::T *__restrict__ psi, double *__restrict__ u,
-                                                    int k, int n1, int nh, int64_t slot_size) {
+                                                    int k, int n1, int nh, int64_t slot_size, int bx, int by) {
   using C = typename C2T<R>::T;
   extern __shared__ unsigned char smem_raw[];
-  const Block blk = blocks[blockIdx.x];
+  const Block blk = blocks[bx];
   const int K = blk.K, nl = 1 << blk.dl;
-  const int r0 = blockIdx.y * KM, nr = min(KM, K - r0);  // rows r0 .. r0 + nr - 1
+  const int r0 = by * KM, nr = min(KM, K - r0);  // rows r0 .. r0 + nr - 1
   if (nr <= 0) return;
   const int RM = min(KM, K);                           // rows the shared arrays are sized for
   const int64_t *lv = bleaves + blk.leaf0;
@@ -1268,6 +1333,16 @@ __global__ void __launch_bounds__(256) eval2_kernel(const Block *__restrict__ bl
       if (FGT_OK_PTR(up)) { if (acc_u) atomicAdd(up, (double)acc); else *up = (double)acc; }
     }
   }
+}
+
+
+template <int D, typename R, int KM, bool TC = false>  // TC (FP64, 3D): stages 1-2 on the tensor cores
+__global__ void __launch_bounds__(256) eval2_kernel(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
+                                                    const typename C2T<R>::T *__restrict__ Ef,
+                                                    const typename C2T<R>::T *__restrict__ Eh,
+                                                    const typename C2T<R>::T *__restrict__ psi, double *__restrict__ u,
+                                                    int k, int n1, int nh, int64_t slot_size) {
+  eval2_body<D, R, KM, TC>(blocks, bleaves, Ef, Eh, psi, u, k, n1, nh, slot_size, blockIdx.x, blockIdx.y);
 }
 
 // ----------------------------------------------------------------------------- tcgen05 helpers
@@ -2246,16 +2321,16 @@ __global__ void __launch_bounds__(256, 1) form7_kernel(const __grid_constant__ C
 //   stage 2: T2[r][I2][m3] = sum_m2 E2(I2, m2) T1[r][m3][m2]       (4 x 4 register tiles)
 //   stage 3: u = Re sum_m3 Eh(I3, m3) T2[r][I2][m3]                (4 x 4 register tiles)
 template <typename R, int RC>
-__global__ void __launch_bounds__(256) eval5_kernel(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
+__device__ __forceinline__ void eval5_body(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
                                                     const typename C2T<R>::T *__restrict__ Ef,
                                                     const typename C2T<R>::T *__restrict__ Eh,
                                                     const typename C2T<R>::T *__restrict__ psi, double *__restrict__ u,
-                                                    int k, int n1, int nh, int64_t slot_size) {
+                                                    int k, int n1, int nh, int64_t slot_size, int bx, int by) {
   using C = typename C2T<R>::T;
   extern __shared__ __align__(16) unsigned char smem_e5[];
-  const Block blk = blocks[blockIdx.x];
+  const Block blk = blocks[bx];
   const int K = blk.K, nl = 1 << blk.dl;
-  const int i0 = blockIdx.y * RC, nr = min(RC, K - i0);  // rows I1 = i0 .. i0 + nr - 1
+  const int i0 = by * RC, nr = min(RC, K - i0);  // rows I1 = i0 .. i0 + nr - 1
   if (nr <= 0) return;
   const int64_t *lv = bleaves + blk.leaf0;
   const C *ps = psi + (int64_t)blk.slot * slot_size;
@@ -2390,6 +2465,16 @@ __global__ void __launch_bounds__(256) eval5_kernel(const Block *__restrict__ bl
   }
 }
 
+
+template <typename R, int RC>
+__global__ void __launch_bounds__(256) eval5_kernel(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
+                                                    const typename C2T<R>::T *__restrict__ Ef,
+                                                    const typename C2T<R>::T *__restrict__ Eh,
+                                                    const typename C2T<R>::T *__restrict__ psi, double *__restrict__ u,
+                                                    int k, int n1, int nh, int64_t slot_size) {
+  eval5_body<R, RC>(blocks, bleaves, Ef, Eh, psi, u, k, n1, nh, slot_size, blockIdx.x, blockIdx.y);
+}
+
 // ----------------------------------------------------------------------------- tensor-core evaluation, stages 2-3 (3D, FP32)
 //
 // eval2_kernel's work split (KM rows of a block per CTA, psi read once in stage 1 on the CUDA
@@ -2400,15 +2485,15 @@ __global__ void __launch_bounds__(256) eval5_kernel(const Block *__restrict__ bl
 //     carries (Re E1, -Im E1) on the interleaved index of m1.
 // One warp per (row, 16-row tile); operands are split into TF32 hi / lo as they are loaded.
 template <int NBT, int KM>  // NBT: n-tiles of 8 stage-2 columns in registers (>= 2 ceil(n1/8)); KM rows per CTA
-__global__ void __launch_bounds__(256) eval4_kernel(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
+__device__ __forceinline__ void eval4_body(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
                                                     const float2 *__restrict__ Ef, const float2 *__restrict__ Eh,
                                                     const float2 *__restrict__ psi, double *__restrict__ u, int k,
-                                                    int n1, int nh, int64_t slot_size) {
+                                                    int n1, int nh, int64_t slot_size, int bx, int by) {
   using C = float2;
   extern __shared__ __align__(16) unsigned char smem_e4[];
-  const Block blk = blocks[blockIdx.x];
+  const Block blk = blocks[bx];
   const int K = blk.K, nl = 1 << blk.dl;
-  const int r0 = blockIdx.y * KM, nr = min(KM, K - r0);
+  const int r0 = by * KM, nr = min(KM, K - r0);
   if (nr <= 0) return;
   const int RM = min(KM, K);
   const int64_t *lv = bleaves + blk.leaf0;
@@ -2573,6 +2658,15 @@ __global__ void __launch_bounds__(256) eval4_kernel(const Block *__restrict__ bl
   }
 }
 
+
+template <int NBT, int KM>  // NBT: n-tiles of 8 stage-2 columns in registers (>= 2 ceil(n1/8)); KM rows per CTA
+__global__ void __launch_bounds__(256) eval4_kernel(const Block *__restrict__ blocks, const int64_t *__restrict__ bleaves,
+                                                    const float2 *__restrict__ Ef, const float2 *__restrict__ Eh,
+                                                    const float2 *__restrict__ psi, double *__restrict__ u, int k,
+                                                    int n1, int nh, int64_t slot_size) {
+  eval4_body<NBT, KM>(blocks, bleaves, Ef, Eh, psi, u, k, n1, nh, slot_size, blockIdx.x, blockIdx.y);
+}
+
 // ----------------------------------------------------------------------------- tensor-core evaluation (3D, FP32)
 //
 // eval2_kernel with its first contraction, Y1 (K x n1^2) = Ed (K x nh) psi (nh x n1^2), on the
@@ -2710,15 +2804,15 @@ __device__ __forceinline__ void mode_index(int64_t idx, int n1, int &m1, int &m2
 constexpr int kGatherMpt = 4;
 
 template <int D, typename R>
-__global__ void __launch_bounds__(256) gather_kernel(const int32_t *__restrict__ dst, const int64_t *__restrict__ ptr,
+__device__ __forceinline__ void gather_body(const int32_t *__restrict__ dst, const int64_t *__restrict__ ptr,
                               const GatherSrc *__restrict__ src, const typename C2T<R>::T *__restrict__ Pf,
                               const typename C2T<R>::T *__restrict__ Ph, const typename C2T<R>::T *__restrict__ phi,
                               typename C2T<R>::T *__restrict__ psi, int n1, int nh, int64_t slot_size,
-                              int psi_pitch) {
+                              int psi_pitch, int bx, int by) {
   using C = typename C2T<R>::T;
   constexpr int MPT = kGatherMpt;
-  const int i = blockIdx.x;
-  const int64_t base = (int64_t)blockIdx.y * blockDim.x * MPT + threadIdx.x;
+  const int i = bx;
+  const int64_t base = (int64_t)by * blockDim.x * MPT + threadIdx.x;
   int m1[MPT], m2[MPT], m3[MPT];
   bool ok[MPT];
 #pragma unroll
@@ -2781,6 +2875,16 @@ __global__ void __launch_bounds__(256) gather_kernel(const int32_t *__restrict__
   }
 }
 
+
+template <int D, typename R>
+__global__ void __launch_bounds__(256) gather_kernel(const int32_t *__restrict__ dst, const int64_t *__restrict__ ptr,
+                              const GatherSrc *__restrict__ src, const typename C2T<R>::T *__restrict__ Pf,
+                              const typename C2T<R>::T *__restrict__ Ph, const typename C2T<R>::T *__restrict__ phi,
+                              typename C2T<R>::T *__restrict__ psi, int n1, int nh, int64_t slot_size,
+                              int psi_pitch) {
+  gather_body<D, R>(dst, ptr, src, Pf, Ph, phi, psi, n1, nh, slot_size, psi_pitch, blockIdx.x, blockIdx.y);
+}
+
 // Separable form of the same gather.  A CTA takes one run of up to W target boxes along x_1
 // (fixed x_2, x_3) and 256 consecutive modes.  The phase factors are per axis, so the sum over the
 // 3^(d-1) neighbouring lines (o_2, o_3) is taken first, position by position along the run
@@ -2789,23 +2893,23 @@ __global__ void __launch_bounds__(256) gather_kernel(const int32_t *__restrict__
 // against 27 + 9 + 3 per target for gather_kernel.  Used in split precision (FP32); the FP64
 // expansions keep gather_kernel, which measured faster there (fewer registers per mode).
 template <int D, typename R, int W>
-__global__ void __launch_bounds__(256) gather2_kernel(const GatherSeg *__restrict__ segs,
+__device__ __forceinline__ void gather2_body(const GatherSeg *__restrict__ segs,
                                                       const typename C2T<R>::T *__restrict__ Pf,
                                                       const typename C2T<R>::T *__restrict__ Ph,
                                                       const typename C2T<R>::T *__restrict__ phi,
                                                       typename C2T<R>::T *__restrict__ psi, int n1, int nh,
-                                                      int64_t slot_size, int psi_pitch) {
+                                                      int64_t slot_size, int psi_pitch, int bx, int by) {
   using C = typename C2T<R>::T;
   static_assert(W <= kSegW, "run longer than a GatherSeg");
   constexpr int NL = (D == 3) ? 9 : 3;
   __shared__ GatherSeg sg;
   {
-    const int32_t *g = reinterpret_cast<const int32_t *>(segs + blockIdx.x);
+    const int32_t *g = reinterpret_cast<const int32_t *>(segs + bx);
     int32_t *sd = reinterpret_cast<int32_t *>(&sg);
     for (int e = threadIdx.x; e < (int)(sizeof(GatherSeg) / sizeof(int32_t)); e += blockDim.x) sd[e] = g[e];
   }
   __syncthreads();
-  const int64_t idx = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+  const int64_t idx = (int64_t)by * blockDim.x + threadIdx.x;
   if (idx >= slot_size) return;
   int m1, m2, m3;
   mode_index<D>(idx, n1, m1, m2, m3);
@@ -2850,6 +2954,17 @@ __global__ void __launch_bounds__(256) gather2_kernel(const GatherSeg *__restric
                : psi + (int64_t)sg.tgt[t] * slot_size + idx;
     if (FGT_OK_PTR(o)) *o = C{ar, ai};
   }
+}
+
+
+template <int D, typename R, int W>
+__global__ void __launch_bounds__(256) gather2_kernel(const GatherSeg *__restrict__ segs,
+                                                      const typename C2T<R>::T *__restrict__ Pf,
+                                                      const typename C2T<R>::T *__restrict__ Ph,
+                                                      const typename C2T<R>::T *__restrict__ phi,
+                                                      typename C2T<R>::T *__restrict__ psi, int n1, int nh,
+                                                      int64_t slot_size, int psi_pitch) {
+  gather2_body<D, R, W>(segs, Pf, Ph, phi, psi, n1, nh, slot_size, psi_pitch, blockIdx.x, blockIdx.y);
 }
 
 // phi[parent] = sum_children T_c->p(child) phi[child]
@@ -2911,15 +3026,15 @@ __global__ void push_kernel(const TreeShift *__restrict__ items, const typename 
 // are staged in shared memory.  Each row of a table is applied over its band only (the columns
 // whose entries matter): the full row for wide Gaussians, a few columns as delta -> 0.
 template <int D>
-__global__ void __launch_bounds__(128) near2_kernel(const NearPair *__restrict__ pairs, const double *__restrict__ tab,
+__device__ __forceinline__ void near2_body(const NearPair *__restrict__ pairs, const double *__restrict__ tab,
                                                     const int16_t *__restrict__ band,
-                                                    const double *__restrict__ sigma, double *__restrict__ u, int k) {
+                                                    const double *__restrict__ sigma, double *__restrict__ u, int k, int bx, int by) {
   extern __shared__ double sm[];
   const int kk = k * k;
   const int np = (D == 3) ? kk * k : kk;
   double *s0 = sm, *A = sm + np, *B = A + np, *T = B + np;
   int16_t *bd = reinterpret_cast<int16_t *>(T + D * kk);  // [D][k][2]
-  const NearPair pr = pairs[blockIdx.x];
+  const NearPair pr = pairs[bx];
   const double *sg = sigma + pr.src * np;
   for (int e = threadIdx.x; e < np; e += blockDim.x) s0[e] = FGT_OK_PTR(sg + e) ? __ldg(sg + e) : 0.0;
   for (int e = threadIdx.x; e < D * kk; e += blockDim.x) {
@@ -2978,6 +3093,14 @@ __global__ void __launch_bounds__(128) near2_kernel(const NearPair *__restrict__
       if (FGT_OK_PTR(ut + e)) atomicAdd(ut + e, a);
     }
   }
+}
+
+
+template <int D>
+__global__ void __launch_bounds__(128) near2_kernel(const NearPair *__restrict__ pairs, const double *__restrict__ tab,
+                                                    const int16_t *__restrict__ band,
+                                                    const double *__restrict__ sigma, double *__restrict__ u, int k) {
+  near2_body<D>(pairs, tab, band, sigma, u, k, blockIdx.x, blockIdx.y);
 }
 
 template <int D>
@@ -3411,6 +3534,455 @@ int launches_per_transform(const ExecDesc &e) {
   if (!e.fourier && e.n_gather > 0) n += 1;
   if (e.n_near_pairs > 0) n += 1;
   return n;
+}
+
+// ----------------------------------------------------------------------------- persistent batched execution
+//
+// Many independent transforms in ONE launch: every CTA of a persistent grid pops items from a device
+// work queue, one item being one CTA's share of a kernel launch of one transform (a (transform,
+// phase, block, row chunk) unit), runs it with the same device code as that kernel (the *_body
+// functions), and counts it done in its transform's counter for the phase.  Items of a phase wait,
+// with a bounded spin, until their transform's previous phase is complete (the queue lists every
+// phase of every transform before the next phase, so an item only ever waits for items popped
+// before it, by CTAs that are running).  A wait that runs out records kBatchTimeout in the batch's
+// status word and the item is skipped (its result is then wrong, and the status says so), so
+// nothing can hang.  Phases: 0 clear u / phi, 1 pack the FP32 density, 2 form, 3 gather,
+// 4 evaluation, 5 near field (needs phase 0 only).  The items use the CUDA-core kernels (the tcgen05
+// ranges of a plan take their CUDA-core fallbacks) and the plain expansion layout.
+struct BatchDesc {
+  int d, k, n1, nh, f32, Kmax_f1;
+  int64_t ss, n_points, phi_elems;
+  const double *sigma;
+  double *u;
+  void *phi, *psi, *eval_src;
+  float *sigp;
+  const Block *blocks, *f1_blocks, *f2_blocks, *e1_blocks, *e2_blocks;
+  const int32_t *f2_gptr, *pack_block;
+  const int64_t *block_leaves, *eval_leaves;
+  const void *Ff, *Fh, *Ef, *Eh, *Pf, *Ph;
+  const int32_t *gather_dst;
+  const int64_t *gather_ptr;
+  const GatherSrc *gather_src;
+  const GatherSeg *gather_segs;
+  const NearPair *near_pairs;
+  const double *near_tab;
+  const int16_t *near_band;
+};
+
+struct BatchItem {
+  int16_t kind, var;  // body and template variant
+  int16_t phase, dep; // the phase counter it completes, the one it waits for (-1: none)
+  int32_t t;          // transform
+  int32_t first;      // first group / block of the item's launch range
+  int32_t bx, by;     // its block index in that launch
+  int32_t need;       // items the dep counter must count
+  int32_t nb;         // consecutive block indices bx .. bx + nb - 1 of the launch
+};
+
+constexpr int kBatchPhases = 6;
+constexpr int kZeroChunk = 1 << 15;     // elements cleared per item
+constexpr int kBatchTimeout = 1;        // status word value of a wait that ran out
+enum : int16_t { BK_ZERO_U = 1, BK_ZERO_PHI, BK_PACK, BK_FORM1, BK_FORM2, BK_FORM3, BK_FORM4, BK_GATHER, BK_GATHER2,
+                 BK_EVAL1, BK_EVAL2, BK_EVAL5, BK_EVAL4, BK_NEAR, BK_NEVER };
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <int D, typename R>
+__device__ __forceinline__ void batch_item_typed(const BatchDesc &b, const BatchItem &w) {
+  using C = typename C2T<R>::T;
+  const C *Ff = static_cast<const C *>(b.Ff), *Fh = static_cast<const C *>(b.Fh);
+  const C *Ef = static_cast<const C *>(b.Ef), *Eh = static_cast<const C *>(b.Eh);
+  const C *Pf = static_cast<const C *>(b.Pf), *Ph = static_cast<const C *>(b.Ph);
+  C *phi = static_cast<C *>(b.phi), *psi = static_cast<C *>(b.psi);
+  const C *src = static_cast<const C *>(b.eval_src);
+  const int v = w.var >> 2;
+  switch (w.kind) {
+    case BK_FORM1:
+      form_body<D, R>(b.f1_blocks, b.block_leaves, b.sigma, Ff, Fh, phi, b.k, b.n1, b.nh, b.ss, b.Kmax_f1, w.bx, w.by);
+      break;
+    case BK_FORM2:
+      if constexpr (D == 2)
+        form2_body<2, R>(b.f2_blocks, b.f2_gptr + w.first, b.block_leaves, b.sigma, Ff, Fh, phi, b.k, b.n1, b.nh, b.ss,
+                         w.bx, w.by);
+      break;
+    case BK_FORM3:
+      if constexpr (D == 3)
+        form3_body<R, false>(b.f2_blocks, b.f2_gptr + w.first, b.block_leaves, b.sigma, Ff, Fh, phi, b.k, b.n1, b.nh,
+                             b.ss, w.bx, w.by);
+      break;
+    case BK_FORM4:
+      if constexpr (D == 3 && sizeof(R) == 4) {
+        const float *sp = (v & 4) ? nullptr : b.sigp;
+        if (v & 1) {
+          if (v & 2) form4_body<8, true>(b.f2_blocks, b.f2_gptr + w.first, b.block_leaves, b.sigma, sp, Ff, Fh, phi, b.k, b.n1, b.nh, b.ss, w.bx, 0);
+          else form4_body<8, false>(b.f2_blocks, b.f2_gptr + w.first, b.block_leaves, b.sigma, sp, Ff, Fh, phi, b.k, b.n1, b.nh, b.ss, w.bx, 0);
+        } else {
+          if (v & 2) form4_body<kNbtMax, true>(b.f2_blocks, b.f2_gptr + w.first, b.block_leaves, b.sigma, sp, Ff, Fh, phi, b.k, b.n1, b.nh, b.ss, w.bx, 0);
+          else form4_body<kNbtMax, false>(b.f2_blocks, b.f2_gptr + w.first, b.block_leaves, b.sigma, sp, Ff, Fh, phi, b.k, b.n1, b.nh, b.ss, w.bx, 0);
+        }
+      }
+      break;
+    case BK_GATHER:
+      gather_body<D, R>(b.gather_dst, b.gather_ptr, b.gather_src, Pf, Ph, phi, psi, b.n1, b.nh, b.ss, 0, w.bx, w.by);
+      break;
+    case BK_GATHER2:
+      if constexpr (sizeof(R) == 4)
+        gather2_body<D, R, kSegW>(b.gather_segs, Pf, Ph, phi, psi, b.n1, b.nh, b.ss, 0, w.bx, w.by);
+      break;
+    case BK_EVAL1:
+      eval_body<D, R>(b.e1_blocks, b.eval_leaves, Ef, Eh, src, b.u, b.k, b.n1, b.nh, b.ss, w.bx, w.by);
+      break;
+    case BK_EVAL2: {
+      const Block *bl = b.e2_blocks + w.first;
+      if (v == 0) eval2_body<D, R, 4, false>(bl, b.eval_leaves, Ef, Eh, src, b.u, b.k, b.n1, b.nh, b.ss, w.bx, w.by);
+      else if (v == 1) eval2_body<D, R, 8, false>(bl, b.eval_leaves, Ef, Eh, src, b.u, b.k, b.n1, b.nh, b.ss, w.bx, w.by);
+      else eval2_body<D, R, 16, false>(bl, b.eval_leaves, Ef, Eh, src, b.u, b.k, b.n1, b.nh, b.ss, w.bx, w.by);
+      break;
+    }
+    case BK_EVAL5:
+      if constexpr (D == 3 && sizeof(R) == 8) {
+        const Block *bl = b.e2_blocks + w.first;
+        switch (v) {
+          case 0: eval5_body<R, 1>(bl, b.eval_leaves, Ef, Eh, src, b.u, b.k, b.n1, b.nh, b.ss, w.bx, w.by); break;
+          case 1: eval5_body<R, 2>(bl, b.eval_leaves, Ef, Eh, src, b.u, b.k, b.n1, b.nh, b.ss, w.bx, w.by); break;
+          case 2: eval5_body<R, 4>(bl, b.eval_leaves, Ef, Eh, src, b.u, b.k, b.n1, b.nh, b.ss, w.bx, w.by); break;
+          case 3: eval5_body<R, 8>(bl, b.eval_leaves, Ef, Eh, src, b.u, b.k, b.n1, b.nh, b.ss, w.bx, w.by); break;
+          default: eval5_body<R, 16>(bl, b.eval_leaves, Ef, Eh, src, b.u, b.k, b.n1, b.nh, b.ss, w.bx, w.by); break;
+        }
+      }
+      break;
+    case BK_EVAL4:
+      if constexpr (D == 3 && sizeof(R) == 4) {
+        const Block *bl = b.e2_blocks + w.first;
+        const int km = v >> 1;
+        if (v & 1) {
+          if (km == 0) eval4_body<8, 4>(bl, b.eval_leaves, Ef, Eh, src, b.u, b.k, b.n1, b.nh, b.ss, w.bx, w.by);
+          else if (km == 1) eval4_body<8, 8>(bl, b.eval_leaves, Ef, Eh, src, b.u, b.k, b.n1, b.nh, b.ss, w.bx, w.by);
+          else eval4_body<8, 16>(bl, b.eval_leaves, Ef, Eh, src, b.u, b.k, b.n1, b.nh, b.ss, w.bx, w.by);
+        } else {
+          if (km == 0) eval4_body<kNbtMax, 4>(bl, b.eval_leaves, Ef, Eh, src, b.u, b.k, b.n1, b.nh, b.ss, w.bx, w.by);
+          else if (km == 1) eval4_body<kNbtMax, 8>(bl, b.eval_leaves, Ef, Eh, src, b.u, b.k, b.n1, b.nh, b.ss, w.bx, w.by);
+          else eval4_body<kNbtMax, 16>(bl, b.eval_leaves, Ef, Eh, src, b.u, b.k, b.n1, b.nh, b.ss, w.bx, w.by);
+        }
+      }
+      break;
+    case BK_NEAR:
+      near2_body<D>(b.near_pairs, b.near_tab, b.near_band, b.sigma, b.u, b.k, w.bx, 0);
+      break;
+    default:
+      break;
+  }
+}
+
+__global__ void __launch_bounds__(256, 2) batch_persistent_kernel(const BatchItem *__restrict__ items, int n_items,
+                                                                  const BatchDesc *__restrict__ descs,
+                                                                  unsigned *__restrict__ counters,
+                                                                  unsigned *__restrict__ head, int *__restrict__ status,
+                                                                  long long wait_clocks) {
+  __shared__ int s_item, s_skip;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) s_item = (int)atomicAdd(head, 1u);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= n_items) break;
+    const BatchItem w = items[it];
+    if (tid == 0) {
+      int skip = 0;
+      if (w.dep >= 0) {
+        const unsigned *c = counters + (size_t)w.t * kBatchPhases + w.dep;
+        const long long t0 = clock64();
+        while (ld_acquire_u32(c) < (unsigned)w.need) {
+          if (clock64() - t0 > wait_clocks) {  // the phase it needs never completed: report, skip
+            atomicMax(status, kBatchTimeout);
+            skip = 1;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      s_skip = skip;
+    }
+    __syncthreads();
+    const BatchItem w0 = w;
+    for (int j = 0; j < w0.nb && !s_skip; ++j) {
+      if (j > 0) __syncthreads();  // the previous block's shared memory is free
+      BatchItem w = w0;
+      w.bx = w0.bx + j;
+      const BatchDesc &b = descs[w.t];
+      if (w.kind == BK_ZERO_U || w.kind == BK_ZERO_PHI) {
+        // clear a chunk of u (doubles) or of the outgoing expansions (complex values, as uint2 words
+        // of 8 bytes: FP32 complex, or halves of an FP64 complex)
+        const int64_t n = w.kind == BK_ZERO_U ? b.n_points : b.phi_elems * (b.f32 ? 1 : 2);
+        const int64_t lo = (int64_t)w.bx * kZeroChunk, hi = min(n, lo + kZeroChunk);
+        uint2 *p = w.kind == BK_ZERO_U ? reinterpret_cast<uint2 *>(b.u) : static_cast<uint2 *>(b.phi);
+        for (int64_t e = lo + tid; e < hi; e += blockDim.x) p[e] = make_uint2(0u, 0u);
+      } else if (w.kind == BK_PACK) {
+        sigma_pack_body(b.blocks, b.pack_block, b.block_leaves, b.sigma, b.sigp, b.k, w.bx, 0);
+      } else {
+        const bool f32 = (w.var & 1) != 0, d3 = (w.var & 2) != 0;
+        if (d3) {
+          if (f32) batch_item_typed<3, float>(b, w);
+          else batch_item_typed<3, double>(b, w);
+        } else {
+          if (f32) batch_item_typed<2, float>(b, w);
+          else batch_item_typed<2, double>(b, w);
+        }
+      }
+    }
+    __syncthreads();  // the item's writes are done (and s_item may be rewritten)
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(counters + (size_t)w.t * kBatchPhases + w.phase, 1u);
+    }
+  }
+}
+
+struct BatchQueue {
+  std::vector<BatchItem> items;
+  std::vector<BatchDesc> descs;
+  size_t smem = 0;
+  BatchItem *d_items = nullptr;
+  BatchDesc *d_descs = nullptr;
+  unsigned *d_counters = nullptr;  // [n][kBatchPhases], then the queue head
+  int *d_status = nullptr;
+  int grid = 0;
+  std::vector<const double *> sig;
+  std::vector<double *> u;
+  ~BatchQueue() {
+    cudaFree(d_items);
+    cudaFree(d_descs);
+    cudaFree(d_counters);
+    cudaFree(d_status);
+  }
+};
+
+namespace {
+// The launches of one transform (fused mode) as queue items, following run_typed's choices with the
+// CUDA-core kernel wherever it takes a tcgen05 one.  Returns nullptr or why the plan cannot be queued.
+const char *queue_transform(const ExecDesc &e, int t, std::vector<BatchItem> (&ph)[kBatchPhases], size_t &smem,
+                            BatchDesc &bd) {
+  if (!e.merge.empty() || !e.push.empty()) return "hierarchical mode";
+  if (e.tc64) return "FP64 tensor-core precision";
+  const int D = e.d, n1 = e.n1, nh = e.nh;
+  const bool f32 = e.prec == 1;
+  const int vbase = (f32 ? 1 : 0) | (D == 3 ? 2 : 0);
+  const size_t csz = f32 ? sizeof(float2) : sizeof(double2);
+  int count[kBatchPhases] = {};
+  auto add = [&](int phase, int16_t kind, int var, int first, int gx, int gy, size_t sm) {
+    // a few consecutive blocks of the launch per item (fewer queue pops and dependency checks)
+    const int g = gx >= 16 ? 4 : gx >= 8 ? 2 : 1;
+    for (int y = 0; y < gy; ++y)
+      for (int x = 0; x < gx; x += g) {
+        BatchItem w{};
+        w.kind = kind;
+        w.var = (int16_t)(vbase | (var << 2));
+        w.phase = (int16_t)phase;
+        w.t = t;
+        w.first = first;
+        w.bx = x;
+        w.by = y;
+        w.nb = std::min(g, gx - x);
+        ph[phase].push_back(w);
+        ++count[phase];
+      }
+    smem = std::max(smem, sm);
+  };
+  const int64_t ss = e.slot_size;
+  if (e.zero_u) add(0, BK_ZERO_U, 0, 0, (int)((e.n_points + kZeroChunk - 1) / kZeroChunk), 1, 0);
+  const int64_t phi_words = e.n_phi_slots * ss * (f32 ? 1 : 2);
+  if (e.n_blocks > 0) add(0, BK_ZERO_PHI, 0, 0, (int)((phi_words + kZeroChunk - 1) / kZeroChunk), 1, 0);
+  if (D == 3 && f32 && e.sigp != nullptr && e.n_pack > 0) add(1, BK_PACK, 0, 0, (int)e.n_pack, 1, 0);
+  if (e.n_f1 > 0) add(2, BK_FORM1, 0, 0, (int)e.n_f1, nh, form_smem_bytes(D, e.Kmax_f1, n1, f32));
+  for (const LaunchRange &lr : e.f2_ranges) {
+    const int chunks = (nh + kSc - 1) / kSc;
+    if (D == 3 && f32 && (lr.tensor == 7 || lr.tensor == 1)) {
+      const bool big = lr.K > 16, small_n = n1_pad8(n1) / 4 <= 8;
+      // tcgen05 ranges: the register-tiled form, reading sigma itself (their blocks' packed copy
+      // is in the tcgen05 order)
+      const bool own = lr.tensor == 7 || e.sigp == nullptr;
+      const size_t sm = lr.tensor == 7 ? (big ? form4b_bytes(lr.K, n1) : form4_bytes(1, lr.K, n1)) : lr.smem;
+      add(2, BK_FORM4, (small_n ? 1 : 0) | ((lr.tensor == 7 ? big : lr.big) ? 2 : 0) | (own ? 4 : 0), lr.first,
+          lr.count * chunks, 1, sm);
+    } else if (D == 3) {
+      add(2, BK_FORM3, 0, lr.first, lr.count, chunks, lr.smem);
+    } else {
+      add(2, BK_FORM2, 0, lr.first, lr.count, nh, lr.smem);
+    }
+  }
+  if (!e.fourier && e.n_gather > 0) {
+    if (e.n_gather_segs > 0) {
+      if (!f32) return "gather runs in FP64";
+      add(3, BK_GATHER2, 0, 0, (int)e.n_gather_segs, (int)((ss + 255) / 256), 0);
+    } else {
+      add(3, BK_GATHER, 0, 0, (int)e.n_gather, (int)((ss + 256 * kGatherMpt - 1) / (256 * kGatherMpt)), 0);
+    }
+  }
+  if (e.n_e1 > 0) add(4, BK_EVAL1, 0, 0, (int)e.n_e1, e.Kmax_e1, eval_smem_bytes(D, e.Kmax_e1, n1, f32));
+  for (const LaunchRange &lr : e.e2_ranges) {
+    if (lr.tensor == 1) return "tensor-core evaluation variant";
+    const int rows = lr.rows <= 4 ? 4 : lr.rows <= 8 ? 8 : 16, kmv = rows == 4 ? 0 : rows == 8 ? 1 : 2;
+    if (lr.tensor == 3) {
+      if (f32) return "FP32 half-range-last evaluation";
+      const int rc = lr.rows <= 1 ? 1 : lr.rows <= 2 ? 2 : lr.rows <= 4 ? 4 : lr.rows <= 8 ? 8 : 16;
+      const int rv = rc == 1 ? 0 : rc == 2 ? 1 : rc == 4 ? 2 : rc == 8 ? 3 : 4;
+      add(4, BK_EVAL5, rv, lr.first, lr.count, (lr.K + rc - 1) / rc, lr.smem);
+    } else if (lr.tensor == 2) {
+      const bool small_n = 2 * ((n1 + 7) / 8) <= 8;
+      add(4, BK_EVAL4, (small_n ? 1 : 0) | (kmv << 1), lr.first, lr.count, (lr.K + rows - 1) / rows, lr.smem);
+    } else {
+      // the CUDA-core whole-block kernel, also for the tcgen05 ranges (4, 7)
+      const size_t sm = (lr.tensor == 4 || lr.tensor == 7) ? eval2_bytes(D, lr.K, n1, nh, csz, rows) : lr.smem;
+      add(4, BK_EVAL2, kmv, lr.first, lr.count, (lr.K + rows - 1) / rows, sm);
+    }
+  }
+  if (e.n_near_pairs > 0) {
+    const int np = D == 3 ? e.k * e.k * e.k : e.k * e.k;
+    const size_t nsm = sizeof(double) * (3 * (size_t)np + (size_t)D * e.k * e.k) + sizeof(int16_t) * 2 * D * e.k;
+    add(5, BK_NEAR, 0, 0, (int)e.n_near_pairs, 1, nsm);
+  }
+  // dependencies: each phase waits for the latest earlier phase of the chain 0 -> 1 -> 2 -> 3 -> 4 that
+  // has items; the near field for phase 0 only
+  auto dep_of = [&](int phase) -> int {
+    if (phase == 5) return count[0] ? 0 : -1;
+    for (int q = phase - 1; q >= 0; --q)
+      if (count[q]) return q;
+    return -1;
+  };
+  for (int q = 0; q < kBatchPhases; ++q) {
+    const int dq = dep_of(q);
+    for (size_t i = ph[q].size() - count[q]; i < ph[q].size(); ++i) {
+      ph[q][i].dep = (int16_t)dq;
+      ph[q][i].need = dq >= 0 ? count[dq] : 0;
+    }
+  }
+  bd = BatchDesc{};
+  bd.d = D; bd.k = e.k; bd.n1 = n1; bd.nh = nh; bd.f32 = f32; bd.Kmax_f1 = e.Kmax_f1;
+  bd.ss = ss; bd.n_points = e.n_points; bd.phi_elems = e.n_phi_slots * ss;
+  bd.phi = e.phi; bd.psi = e.psi; bd.eval_src = (!e.fourier && e.n_gather > 0) ? e.psi : e.phi;
+  bd.sigp = e.sigp;
+  bd.blocks = e.blocks; bd.f1_blocks = e.f1_blocks; bd.f2_blocks = e.f2_blocks; bd.e1_blocks = e.e1_blocks;
+  bd.e2_blocks = e.e2_blocks; bd.f2_gptr = e.f2_gptr; bd.pack_block = e.pack_block;
+  bd.block_leaves = e.block_leaves; bd.eval_leaves = e.eval_leaves;
+  bd.Ff = e.Ff; bd.Fh = e.Fh; bd.Ef = e.Ef; bd.Eh = e.Eh; bd.Pf = e.Pf; bd.Ph = e.Ph;
+  bd.gather_dst = e.gather_dst; bd.gather_ptr = e.gather_ptr; bd.gather_src = e.gather_src;
+  bd.gather_segs = e.gather_segs;
+  bd.near_pairs = e.near_pairs; bd.near_tab = e.near_tab; bd.near_band = e.near_band;
+  return nullptr;
+}
+}  // namespace
+
+cudaError_t batch_queue_create(const std::vector<const ExecDesc *> &plans, BatchQueue **out, const char **why) {
+  *out = nullptr;
+  *why = nullptr;
+  auto *q = new (std::nothrow) BatchQueue();
+  if (!q) return cudaErrorMemoryAllocation;
+  std::vector<BatchItem> ph[kBatchPhases];
+  q->descs.resize(plans.size());
+  for (size_t t = 0; t < plans.size(); ++t) {
+    const char *w = queue_transform(*plans[t], (int)t, ph, q->smem, q->descs[t]);
+    if (w) {
+      *why = w;
+      delete q;
+      return cudaSuccess;
+    }
+  }
+  // phase-major order: every transform's clears, packs, forms, near fields, gathers, evaluations
+  for (int p : {0, 1, 2, 5, 3, 4}) q->items.insert(q->items.end(), ph[p].begin(), ph[p].end());
+  if (q->items.size() > (size_t)INT32_MAX) { delete q; return cudaErrorInvalidValue; }
+  cudaError_t err = cudaFuncSetAttribute(batch_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)q->smem);
+  int per_sm = 0, dev = 0, sms = 0;
+  if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persistent_kernel, 256, q->smem);
+  if (err == cudaSuccess) err = cudaGetDevice(&dev);
+  if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (err == cudaSuccess && per_sm < 1) err = cudaErrorInvalidConfiguration;
+  q->grid = (int)std::min<size_t>(q->items.size(), (size_t)std::max(1, per_sm) * (size_t)sms);
+  if (err == cudaSuccess) err = cudaMalloc(&q->d_items, sizeof(BatchItem) * std::max<size_t>(1, q->items.size()));
+  if (err == cudaSuccess) err = cudaMalloc(&q->d_descs, sizeof(BatchDesc) * std::max<size_t>(1, q->descs.size()));
+  if (err == cudaSuccess) err = cudaMalloc(&q->d_counters, sizeof(unsigned) * (plans.size() * kBatchPhases + 1));
+  if (err == cudaSuccess) err = cudaMalloc(&q->d_status, sizeof(int));
+  if (err == cudaSuccess && !q->items.empty())
+    err = cudaMemcpy(q->d_items, q->items.data(), sizeof(BatchItem) * q->items.size(), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemset(q->d_status, 0, sizeof(int));
+  if (err != cudaSuccess) { delete q; return err; }
+  q->sig.assign(plans.size(), nullptr);
+  q->u.assign(plans.size(), nullptr);
+  *out = q;
+  return cudaSuccess;
+}
+
+cudaError_t batch_queue_run(BatchQueue *q, const double *const *sigma, double *const *u, cudaStream_t st,
+                            long long wait_clocks) {
+  bool same = true;
+  for (size_t t = 0; t < q->descs.size(); ++t) {
+    if (q->sig[t] != sigma[t] || q->u[t] != u[t]) same = false;
+    q->sig[t] = sigma[t];
+    q->u[t] = u[t];
+    q->descs[t].sigma = sigma[t];
+    q->descs[t].u = u[t];
+  }
+  cudaError_t err = cudaSuccess;
+  if (!same)  // the descriptors hold the buffers: uploaded when a pointer changes
+    err = cudaMemcpyAsync(q->d_descs, q->descs.data(), sizeof(BatchDesc) * q->descs.size(), cudaMemcpyHostToDevice, st);
+  if (err == cudaSuccess)
+    err = cudaMemsetAsync(q->d_counters, 0, sizeof(unsigned) * (q->descs.size() * kBatchPhases + 1), st);
+  if (err != cudaSuccess) return err;
+  if (q->items.empty()) return cudaSuccess;
+  batch_persistent_kernel<<<q->grid, 256, q->smem, st>>>(q->d_items, (int)q->items.size(), q->d_descs, q->d_counters,
+                                                         q->d_counters + q->descs.size() * kBatchPhases, q->d_status,
+                                                         wait_clocks);
+  return cudaGetLastError();
+}
+
+cudaError_t batch_queue_status(BatchQueue *q, int *status) {
+  int v = 0;
+  cudaError_t err = cudaMemcpy(&v, q->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (err == cudaSuccess && v != 0) err = cudaMemset(q->d_status, 0, sizeof(int));
+  *status = v;
+  return err;
+}
+
+size_t batch_queue_items(const BatchQueue *q) { return q->items.size(); }
+int batch_queue_grid(const BatchQueue *q) { return q->grid; }
+void batch_queue_destroy(BatchQueue *q) { delete q; }
+
+// A queue of one item whose dependency (a counter nothing increments) cannot be met: its bounded wait
+// (wait_clocks) runs out and the status word reports it.  Faults nothing, hangs nothing.
+cudaError_t selftest_batch_timeout(int *status) {
+  BatchItem w{};
+  w.kind = BK_NEVER;
+  w.phase = 1;
+  w.dep = 0;
+  w.need = 1;
+  w.nb = 1;
+  BatchItem *di = nullptr;
+  BatchDesc *dd = nullptr;
+  unsigned *dc = nullptr;
+  int *ds = nullptr;
+  cudaError_t err = cudaMalloc(&di, sizeof(BatchItem));
+  if (err == cudaSuccess) err = cudaMalloc(&dd, sizeof(BatchDesc));
+  if (err == cudaSuccess) err = cudaMalloc(&dc, sizeof(unsigned) * (kBatchPhases + 1));
+  if (err == cudaSuccess) err = cudaMalloc(&ds, sizeof(int));
+  if (err == cudaSuccess) err = cudaMemcpy(di, &w, sizeof(BatchItem), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemset(dd, 0, sizeof(BatchDesc));
+  if (err == cudaSuccess) err = cudaMemset(dc, 0, sizeof(unsigned) * (kBatchPhases + 1));
+  if (err == cudaSuccess) err = cudaMemset(ds, 0, sizeof(int));
+  if (err == cudaSuccess) {
+    batch_persistent_kernel<<<1, 256, 0>>>(di, 1, dd, dc, dc + kBatchPhases, ds, 1LL << 21);  // about a millisecond
+    err = cudaGetLastError();
+  }
+  if (err == cudaSuccess) err = cudaDeviceSynchronize();
+  if (err == cudaSuccess) err = cudaMemcpy(status, ds, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(di);
+  cudaFree(dd);
+  cudaFree(dc);
+  cudaFree(ds);
+  return err;
 }
 
 cudaError_t run_transform(const ExecDesc &e, const double *sigma, double *u, cudaStream_t stream) {

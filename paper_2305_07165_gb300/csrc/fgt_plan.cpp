@@ -2286,6 +2286,8 @@ fgt_status fgt_legendre_fourier_integrals(double t, int nmax, double *re, double
 // pointers change.
 
 struct fgt_batch {
+  int mode = FGT_BATCH_GRAPH;
+  fgt::BatchQueue *queue = nullptr;    // persistent mode: the device work queue
   std::vector<fgt_plan *> plans;
   std::vector<cudaStream_t> streams;   // branch streams used while capturing
   cudaStream_t cap = nullptr;          // capture origin
@@ -2294,6 +2296,7 @@ struct fgt_batch {
   std::vector<const double *> sig;
   std::vector<double *> u;
   ~fgt_batch() {
+    if (queue) fgt::batch_queue_destroy(queue);
     if (exec) cudaGraphExecDestroy(exec);
     for (cudaEvent_t e : events) cudaEventDestroy(e);
     for (cudaStream_t s : streams) cudaStreamDestroy(s);
@@ -2344,7 +2347,12 @@ fgt_status batch_capture(fgt_batch *b) {
 extern "C" {
 
 fgt_status fgt_batch_create(fgt_plan *const *plans, int n, fgt_batch **out) {
+  return fgt_batch_create_mode(plans, n, FGT_BATCH_GRAPH, out);
+}
+
+fgt_status fgt_batch_create_mode(fgt_plan *const *plans, int n, int mode, fgt_batch **out) {
   if (!out || !plans || n < 1) return fail(FGT_ERR_ARG, "bad batch arguments");
+  if (mode != FGT_BATCH_GRAPH && mode != FGT_BATCH_PERSISTENT) return fail(FGT_ERR_ARG, "bad batch mode");
   *out = nullptr;
   // every transform of the batch writes its plan's workspace and records its plan's side-stream
   // events: a plan listed twice would have two branches racing on them
@@ -2364,6 +2372,19 @@ fgt_status fgt_batch_create(fgt_plan *const *plans, int n, fgt_batch **out) {
       if (s != FGT_OK) { delete b; return s; }
     }
     b->plans.push_back(p);
+  }
+  b->mode = mode;
+  if (mode == FGT_BATCH_PERSISTENT) {
+    std::vector<const fgt::ExecDesc *> ex;
+    for (fgt_plan *p : b->plans) ex.push_back(&p->ex);
+    const char *why = nullptr;
+    cudaError_t ce = fgt::batch_queue_create(ex, &b->queue, &why);
+    if (ce != cudaSuccess) { delete b; return cuda_fail(ce, "persistent batch queue"); }
+    if (why) { delete b; return fail(FGT_ERR_ARG, std::string("persistent batch: a plan uses ") + why); }
+    b->sig.assign(n, nullptr);
+    b->u.assign(n, nullptr);
+    *out = b;
+    return FGT_OK;
   }
   // 16 capture streams: transforms sharing a stream are chained in the graph, so at most 16 run
   // at once; one stream per transform (every branch free) measured 1.9x slower on 256 transforms
@@ -2395,6 +2416,12 @@ fgt_status fgt_batch_execute(fgt_batch *b, const double *const *sigma_dev, doubl
     if (b->plans[i]->dirty) return fail(FGT_ERR_STATE, "a batch plan changed mode or precision; rebuild the batch");
     if (b->sig[i] != sigma_dev[i] || b->u[i] != u_dev[i]) same = false;
   }
+  if (b->mode == FGT_BATCH_PERSISTENT) {
+    cudaError_t ce = fgt::set_check_ranges(nullptr, nullptr, 0, (cudaStream_t)stream);
+    if (ce == cudaSuccess) ce = fgt::batch_queue_run(b->queue, sigma_dev, u_dev, (cudaStream_t)stream, 1LL << 31);
+    if (ce != cudaSuccess) return cuda_fail(ce, "persistent batch launch");
+    return FGT_OK;
+  }
   if (!same) {
     for (size_t i = 0; i < b->plans.size(); ++i) {
       b->sig[i] = sigma_dev[i];
@@ -2411,6 +2438,34 @@ fgt_status fgt_batch_execute(fgt_batch *b, const double *const *sigma_dev, doubl
 }
 
 void fgt_batch_destroy(fgt_batch *b) { delete b; }
+
+fgt_status fgt_batch_status(fgt_batch *b, int *status) {
+  if (!b || !status) return fail(FGT_ERR_ARG, "NULL argument");
+  *status = 0;
+  if (b->mode != FGT_BATCH_PERSISTENT) return FGT_OK;
+  int word = 0;
+  cudaError_t e = fgt::batch_queue_status(b->queue, &word);
+  if (e != cudaSuccess) return cuda_fail(e, "batch status");
+  *status = word ? FGT_ERR_TIMEOUT : 0;
+  return FGT_OK;
+}
+
+fgt_status fgt_batch_get_info(const fgt_batch *b, int *mode, int64_t *items, int *grid) {
+  if (!b) return fail(FGT_ERR_ARG, "NULL batch");
+  if (mode) *mode = b->mode;
+  if (items) *items = b->queue ? (int64_t)fgt::batch_queue_items(b->queue) : 0;
+  if (grid) *grid = b->queue ? fgt::batch_queue_grid(b->queue) : 0;
+  return FGT_OK;
+}
+
+fgt_status fgt_selftest_batch_timeout(int *status) {
+  if (!status) return fail(FGT_ERR_ARG, "NULL argument");
+  int word = 0;
+  cudaError_t e = fgt::selftest_batch_timeout(&word);
+  if (e != cudaSuccess) return cuda_fail(e, "batch time-out self-test");
+  *status = word ? FGT_ERR_TIMEOUT : 0;
+  return FGT_OK;
+}
 
 fgt_status fgt_execute_batch(fgt_plan *const *plans, const double *const *sigma_dev, double *const *u_dev, int n,
                              void *stream) {

@@ -50,3 +50,43 @@ def test_batch_matches_single_transforms():
     b.close()
     for p in plans:
         p.close()
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_persistent_batch_matches_single_transforms(seed):
+    """The batch as ONE persistent kernel over a device queue of every transform's (phase, block)
+    items: each result equals its transform run alone (FP64 to rounding; split precision to the
+    FP32 level, the queue using the CUDA-core kernels where a plan alone takes the tcgen05 ones),
+    repeatedly and after new buffers, and no dependency wait ran out."""
+    mix = _mix(16, seed=seed)
+    plans = [m[0] for m in mix]
+    sig = [m[1] for m in mix]
+    ref = [p(s).clone() for p, s in zip(plans, sig)]
+    b = F.Batch(plans, mode=F.BATCH_PERSISTENT)
+    info = b.info()
+    assert info["mode"] == F.BATCH_PERSISTENT and info["items"] > len(plans) and info["grid"] >= 1
+    for outs in ([torch.full_like(s, float("nan")) for s in sig], [torch.empty_like(s) for s in sig]):
+        for _ in range(2):
+            b(sig, outs)
+        torch.cuda.synchronize()
+        assert b.status() == 0
+        for (p, s, tol), r, o in zip(mix, ref, outs):
+            bound = (1e-12 if p.info()["prec"] == F.PREC_FP64 else 2e-6) * r.abs().max().item()
+            assert (o - r).abs().max().item() <= bound
+    b.close()
+    for p in plans:
+        p.close()
+
+
+def test_persistent_batch_wait_time_out_is_reported():
+    """A dependency wait of the persistent kernel that runs out (a counter nothing increments, a
+    limit of about a millisecond) reports FGT_ERR_TIMEOUT instead of hanging."""
+    assert F.selftest_batch_timeout() == F.ERR_TIMEOUT
+
+
+def test_persistent_batch_refuses_hierarchical_plans():
+    tr = W.random_balanced_tree(2, 3, max_level=3, min_level=1)
+    p = F.Plan(2, 4, 1e-2, 1e-6, tr.level, tr.coord, mode=F.MODE_HIERARCHICAL)
+    with pytest.raises(F.FGTError, match="hierarchical"):
+        F.Batch([p], mode=F.BATCH_PERSISTENT)
+    p.close()
