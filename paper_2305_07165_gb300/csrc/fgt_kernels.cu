@@ -755,6 +755,34 @@ __device__ __forceinline__ void sigma_pack_body(const Block *__restrict__ blocks
   const double *src = sigma + bleaves[i] * kp;
   float *dst = sigp + b.leaf0 * kp;
   __shared__ float leaf[kMaxK * kMaxK * kMaxK];  // the leaf's values, node index j1 fastest
+  if (k == 8) {
+    // k = 8 (K = nl 8, a power of two): shifts, and the staging rows padded to 65 floats per j3 plane
+    // so that reading along j3 (stride 65) or along j1 (stride 1) is free of bank conflicts
+    for (int n2 = threadIdx.x; n2 < 256; n2 += blockDim.x) {
+      const int node = 2 * n2;
+      double2 v = make_double2(0.0, 0.0);
+      if (FGT_OK_BYTES(src + node, 16)) v = __ldg(reinterpret_cast<const double2 *>(src + node));
+      const int j3 = node >> 6, r = node & 63;
+      leaf[j3 * 65 + r] = f64_to_f32_int(v.x);
+      leaf[j3 * 65 + r + 1] = f64_to_f32_int(v.y);
+    }
+    __syncthreads();
+    const int lK = __ffs(K) - 1;
+    for (int t = threadIdx.x; t < 512; t += blockDim.x) {
+      const int a = t & 7, bq = (t >> 3) & 7, c = t >> 6;  // fastest, middle, slowest index of the run order
+      float *dp;
+      float v;
+      if (j3_fastest) {  // a = j3, bq = j2, c = j1
+        dp = dst + (((((o1 << 3) + c) << lK) + (o2 << 3) + bq) << lK) + (o3 << 3) + a;
+        v = leaf[a * 65 + (bq << 3) + c];
+      } else {           // a = j1, bq = j2, c = j3
+        dp = dst + (((((o3 << 3) + c) << lK) + (o2 << 3) + bq) << lK) + (o1 << 3) + a;
+        v = leaf[c * 65 + (bq << 3) + a];
+      }
+      if (FGT_OK_PTR(dp)) *dp = v;
+    }
+    return;
+  }
   for (int node = threadIdx.x; node < kp; node += blockDim.x)
     if (FGT_OK_PTR(src + node)) leaf[node] = f64_to_f32_int(__ldg(src + node));
   __syncthreads();
@@ -1713,7 +1741,11 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
 
 template <int N>
 __device__ __forceinline__ void tmem_ld(uint32_t addr, uint32_t (&v)[N]) {
-  if constexpr (N == 8) {
+  if constexpr (N == 4) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                 : "r"(addr));
+  } else if constexpr (N == 8) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                  : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
                  : "r"(addr));
@@ -1724,7 +1756,7 @@ __device__ __forceinline__ void tmem_ld(uint32_t addr, uint32_t (&v)[N]) {
           "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
         : "r"(addr));
   } else {
-    static_assert(N == 32, "tmem_ld: 8, 16 or 32 columns");
+    static_assert(N == 32, "tmem_ld: 4, 8, 16 or 32 columns");
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
         "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -1746,8 +1778,8 @@ __device__ __forceinline__ void put_split2(unsigned char *hi, unsigned char *lo,
   *reinterpret_cast<uint2 *>(lo + o) = make_uint2(l0, l1);
 }
 
-template <int K>
-__global__ void __launch_bounds__(256, 1) eval7_kernel(const __grid_constant__ CUtensorMap psi_map,
+template <int K, int NW>  // NW warps: 4 per TMEM lane quarter x NW / 4 column shares
+__global__ void __launch_bounds__(NW * 32, 1) eval7_kernel(const __grid_constant__ CUtensorMap psi_map,
                                                        const Block *__restrict__ blocks,
                                                        const int64_t *__restrict__ bleaves,
                                                        const float2 *__restrict__ Ef, const float2 *__restrict__ Eh,
@@ -1755,6 +1787,8 @@ __global__ void __launch_bounds__(256, 1) eval7_kernel(const __grid_constant__ C
   using namespace e7;
   constexpr int N12 = n12(K), N3 = n3(K), CM3 = cm3(K), KD3 = kd3(K), T3 = t3(K), R3 = 128 * T3;
   constexpr int TPC = CM3 / (128 / kP);  // stage-1 tiles (128 / kP planes each) per chunk
+  // accumulator columns a warp reads back: NW / 4 warps share each TMEM lane quarter
+  constexpr int CQ = NW / 4, C1 = 2 * kP / CQ, C2 = N12 / CQ, C3 = N3 / CQ;
   constexpr int TC = tmem_cols(K);
   constexpr uint32_t SLAB = 16384;       // one 128-row x 128-byte slab
   constexpr uint32_t SBO3 = (uint32_t)(KD3 / 4) * 128u, SBO3B = (uint32_t)(kKB3 / 4) * 128u;
@@ -1765,7 +1799,7 @@ __global__ void __launch_bounds__(256, 1) eval7_kernel(const __grid_constant__ C
   const int nl = 1 << blk.dl;
   const int64_t *lv = bleaves + blk.leaf0;
   const bool acc_u = (blk.flags & 1) != 0;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, q = warp & 3, hh = warp >> 2;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, q = warp & 3, hh = warp >> 2;  // hh: column quarter
   const int nch = (nh + CM3 - 1) / CM3, nloads = nch * TPC * 2;
   // mbarriers: full[2] (copies landed), empty[2] (stage-1 MMAs of a buffer done), mma2, mma3 (one
   // commit per chunk each), drain (used once, after a time-out)
@@ -1885,13 +1919,13 @@ __global__ void __launch_bounds__(256, 1) eval7_kernel(const __grid_constant__ C
       if (__syncthreads_or(!ok)) { fail = true; break; }
     }
     tc_fence_after();
-    {  // D1 -> A2: warp (q, hh) reads lanes 32q.. (rows (m3, m2)), columns 32 hh .. 32 hh + 31
-      uint32_t v[32];
-      tmem_ld<32>(tD1 + lane_base + (uint32_t)(32 * hh), v);
+    {  // D1 -> A2: warp (q, hh) reads lanes 32q.. (rows (m3, m2)), its share of the 64 columns
+      uint32_t v[C1];
+      tmem_ld<C1>(tD1 + lane_base + (uint32_t)(C1 * hh), v);
       const int l = 32 * q + lane, m2 = l & (kP - 1), mrow = l / kP;
 #pragma unroll
-      for (int p = 0; p < 16; ++p) {
-        const int col = 32 * hh + 2 * p, tl = col / N12, I1 = (col - tl * N12) >> 1;
+      for (int p = 0; p < C1 / 2; ++p) {
+        const int col = C1 * hh + 2 * p, tl = col / N12, I1 = (col - tl * N12) >> 1;
         const int m3l = tl * (128 / kP) + mrow;
         put_split2(a23h, a2l, sw128_off(m3l * K + I1, 2 * m2, 128), __uint_as_float(v[2 * p]),
                    __uint_as_float(v[2 * p + 1]));
@@ -1917,13 +1951,13 @@ __global__ void __launch_bounds__(256, 1) eval7_kernel(const __grid_constant__ C
       if (__syncthreads_or(!ok)) { fail = true; break; }
     }
     tc_fence_after();
-    {  // D2 -> A3 (over A2, whose MMAs are done): lanes = rows (m3, I1), columns (I2, c) of half hh
-      uint32_t v[K];
-      tmem_ld<K>(tD2 + lane_base + (uint32_t)(K * hh), v);
+    {  // D2 -> A3 (over A2, whose MMAs are done): lanes = rows (m3, I1), columns (I2, c) of share hh
+      uint32_t v[C2];
+      tmem_ld<C2>(tD2 + lane_base + (uint32_t)(C2 * hh), v);
       const int l = 32 * q + lane, m3l = l / K, I1 = l - m3l * K;
 #pragma unroll
-      for (int p = 0; p < K / 2; ++p) {
-        const int I2 = hh * (K / 2) + p;
+      for (int p = 0; p < C2 / 2; ++p) {
+        const int I2 = hh * (C2 / 2) + p;
         put_split2(a23h, a3l, umma_off(I2 * K + I1, 2 * m3l, SBO3), __uint_as_float(v[2 * p]),
                    __uint_as_float(v[2 * p + 1]));
       }
@@ -1982,13 +2016,13 @@ __global__ void __launch_bounds__(256, 1) eval7_kernel(const __grid_constant__ C
 #pragma unroll 1
   for (int t = 0; t < T3; ++t) {
     {
-      uint32_t v[N3 / 2];
-      tmem_ld<N3 / 2>(tD3 + lane_base + (uint32_t)(t * N3 + hh * (N3 / 2)), v);
+      uint32_t v[C3];
+      tmem_ld<C3>(tD3 + lane_base + (uint32_t)(t * N3 + hh * C3), v);
       const int rl = 32 * q + lane;  // row within the tile: I2l = rl / K, I1 = rl % K
       if (rl < RI2 * K) {
 #pragma unroll
-        for (int x = 0; x < N3 / 2; ++x) {
-          const int I3 = hh * (N3 / 2) + x;
+        for (int x = 0; x < C3; ++x) {
+          const int I3 = hh * C3 + x;
           if (I3 < K) stage[I3 * (RI2 * K) + rl] = f32_to_f64_int(v[x]);
         }
       }
@@ -2071,14 +2105,16 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
 
 __device__ int g_tcf_status;  // status word of form7_kernel (same meaning as g_tc_status)
 
-template <int K>
-__global__ void __launch_bounds__(256, 1) form7_kernel(const __grid_constant__ CUtensorMap sig_map,
+template <int K, int NW>  // NW warps: 4 per TMEM lane quarter x NW / 4 column shares
+__global__ void __launch_bounds__(NW * 32, 1) form7_kernel(const __grid_constant__ CUtensorMap sig_map,
                                                        const Block *__restrict__ blocks,
                                                        const float2 *__restrict__ Ff, const float2 *__restrict__ Fh,
                                                        float2 *__restrict__ phi, int k, int n1, int nh,
                                                        int64_t slot_size) {
   using namespace f7;
   constexpr int TPC = tpc(K), NCH = nchunk(K), KD2 = kd2(K), NL = NCH * TPC;
+  // accumulator columns a warp reads back: NW / 4 warps share each TMEM lane quarter
+  constexpr int CQ = NW / 4, C1 = 32 / CQ, C2 = 64 / CQ;
   constexpr uint32_t A1 = a1_bytes(K);
   constexpr uint32_t SBOB1 = (uint32_t)(K / 4) * 128u, SBO3 = 4u * 128u, SBOB3 = (uint32_t)(2 * K / 4) * 128u;
   extern __shared__ unsigned char smem_raw[];
@@ -2208,12 +2244,12 @@ __global__ void __launch_bounds__(256, 1) form7_kernel(const __grid_constant__ C
     for (int tl = 0; tl < TPC; ++tl) {
       const int rc = tl * 128 + 32 * q;  // first row of this warp's lanes within the chunk
       if (rc >= 8 * K) continue;         // K = 8: the tile's second half holds no rows of the block
-      uint32_t v[16];
-      tmem_ld<16>(tD1 + lane_base + (uint32_t)(tl * 32 + 16 * hh), v);
+      uint32_t v[C1];
+      tmem_ld<C1>(tD1 + lane_base + (uint32_t)(tl * 32 + C1 * hh), v);
       const int r = rc + lane, J1l = r / K, J2 = r - J1l * K;
 #pragma unroll
-      for (int p = 0; p < 8; ++p) {
-        const int m3 = 8 * hh + p;
+      for (int p = 0; p < C1 / 2; ++p) {
+        const int m3 = (C1 / 2) * hh + p;
         put_split2(a23h, a2l, sw128_off(J1l * 16 + m3, 2 * J2, 128), __uint_as_float(v[2 * p]),
                    __uint_as_float(v[2 * p + 1]));
       }
@@ -2238,13 +2274,13 @@ __global__ void __launch_bounds__(256, 1) form7_kernel(const __grid_constant__ C
       if (__syncthreads_or(!ok)) { fail = true; break; }
     }
     tc_fence_after();
-    {  // ---- D2 -> A3: lanes = rows (J1, m3), columns (m2, c) of half hh
-      uint32_t v[32];
-      tmem_ld<32>(tD2 + lane_base + (uint32_t)(32 * hh), v);
+    {  // ---- D2 -> A3: lanes = rows (J1, m3), columns (m2, c) of quarter hh
+      uint32_t v[C2];
+      tmem_ld<C2>(tD2 + lane_base + (uint32_t)(C2 * hh), v);
       const int l = 32 * q + lane, J1l = l >> 4, m3 = l & 15;
 #pragma unroll
-      for (int p = 0; p < 16; ++p) {
-        const int m2 = 16 * hh + p;
+      for (int p = 0; p < C2 / 2; ++p) {
+        const int m2 = (C2 / 2) * hh + p;
         put_split2(a23h, a3l, umma_off(m2 * 16 + m3, 2 * J1l, SBO3), __uint_as_float(v[2 * p]),
                    __uint_as_float(v[2 * p + 1]));
       }
@@ -2290,14 +2326,14 @@ __global__ void __launch_bounds__(256, 1) form7_kernel(const __grid_constant__ C
   float2 *out = phi + (int64_t)blk.slot * slot_size;
 #pragma unroll 1
   for (int t = 0; t < 4; ++t) {
-    uint32_t v[32];
-    tmem_ld<32>(tD3 + lane_base + (uint32_t)(t * 64 + 32 * hh), v);
+    uint32_t v[C2];
+    tmem_ld<C2>(tD3 + lane_base + (uint32_t)(t * 64 + C2 * hh), v);
     const int row = t * 128 + 32 * q + lane, m2 = row >> 4, m3 = row & 15;
     if (m2 < n1 && m3 < nh) {
       float2 *o = out + ((int64_t)m3 * n1 + m2) * n1;
 #pragma unroll
-      for (int p = 0; p < 16; ++p) {
-        const int m1 = 16 * hh + p;
+      for (int p = 0; p < C2 / 2; ++p) {
+        const int m1 = (C2 / 2) * hh + p;
         if (m1 < n1 && FGT_OK_PTR(o + m1)) {
           const float2 val = make_float2(__uint_as_float(v[2 * p]), __uint_as_float(v[2 * p + 1]));
           if (sole) o[m1] = val;
@@ -3334,11 +3370,11 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
       }
       if (D == 3 && lr.tensor == 7 && sizeof(R) == 4) {  // all stages on tcgen05
         const int ki = lr.K == 8 ? 0 : lr.K == 16 ? 1 : 2;
-        auto k7 = ki == 0 ? form7_kernel<8> : ki == 1 ? form7_kernel<16> : form7_kernel<32>;
+        auto k7 = ki == 0 ? form7_kernel<8, 16> : ki == 1 ? form7_kernel<16, 16> : form7_kernel<32, 16>;
         if ((err = cudaFuncSetAttribute(k7, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) !=
             cudaSuccess)
           return err;
-        k7<<<(unsigned)lr.count, 256, lr.smem, fs.next()>>>(
+        k7<<<(unsigned)lr.count, 512, lr.smem, fs.next()>>>(
             e.sig_map[ki], e.f2_blocks + lr.first, reinterpret_cast<const float2 *>(e.Ff),
             reinterpret_cast<const float2 *>(e.Fh), reinterpret_cast<float2 *>(phi), e.k, n1, nh, ss);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
@@ -3434,10 +3470,13 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
   for (const LaunchRange &lr : e.e2_ranges) {  // one launch per block size K
     if (D == 3 && lr.tensor == 7 && sizeof(R) == 4 && e.psi_pitch == e7::kP && e.psi_map_ready) {
       // all stages on tcgen05
-      auto k7 = lr.K == 8 ? eval7_kernel<8> : lr.K == 16 ? eval7_kernel<16> : eval7_kernel<32>;
+      // 16 warps for K = 32 blocks, 8 for the smaller ones (measured: the extra warps hide the latency
+      // of the large blocks' phases, and cost more in barriers than they gain on small blocks)
+      auto k7 = lr.K == 8 ? eval7_kernel<8, 8> : lr.K == 16 ? eval7_kernel<16, 8> : eval7_kernel<32, 16>;
+      const unsigned nt = lr.K == 32 ? 512 : 256;
       if ((err = cudaFuncSetAttribute(k7, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr.smem)) != cudaSuccess)
         return err;
-      k7<<<(unsigned)lr.count, 256, lr.smem, es.next()>>>(e.psi_map, e.e2_blocks + lr.first, e.eval_leaves,
+      k7<<<(unsigned)lr.count, nt, lr.smem, es.next()>>>(e.psi_map, e.e2_blocks + lr.first, e.eval_leaves,
                                                           reinterpret_cast<const float2 *>(e.Ef),
                                                           reinterpret_cast<const float2 *>(e.Eh), u, e.k, n1, nh);
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
