@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -113,7 +114,16 @@ class ClockSampler:
 # (dram__bytes_read.sum + dram__bytes_write.sum of one capture), with the profile summary that
 # holds the capture.  Keyed by (workload, form, phase); an entry is removed whenever the
 # kernels of that phase change, and phases without a current capture report null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    ("periodic3d", "fp64_tol1e-10", "form"): {
+        "bytes": 2150.2e6, "source": "profiles/fp64_kernels_periodic3d.md (form_kernel<3,double>, 1 launch a step)"},
+    ("periodic3d", "fp64_tol1e-10", "evaluate"): {
+        "bytes": 4447.0e6, "source": "profiles/fp64_kernels_periodic3d.md (eval5_kernel<double,1>, 1 launch a step)"},
+    ("periodic3d", "split_tol1e-6", "form"): {
+        "bytes": 251.9e6, "source": "profiles/tcgen05_kernels_periodic3d.md (sigma_pack_kernel + form7_kernel<32,16>)"},
+    ("periodic3d", "split_tol1e-6", "evaluate"): {
+        "bytes": 138.1e6, "source": "profiles/tcgen05_kernels_periodic3d.md (eval7_kernel<32,16>)"},
+}
 
 
 def peaks():
@@ -249,12 +259,36 @@ def oracle_sample(w, n, seed):
     return sample, u
 
 
-def error_vs_oracle(u_all, sample, u_or, tol):
-    """max |u - u_oracle| / max |u_oracle| on the sample (acceptance: 10 tol)."""
+def kernel_l1(d, delta, periodic):
+    """max over x of the integral of G(x - y; delta) over y in B: sqrt(pi delta) per axis for the
+    periodic kernel (one period), sqrt(pi delta) erf(1 / (2 sqrt(delta))) for the free one (x at the
+    centre).  |u(x)| <= ||sigma||_inf times this for every density."""
+    a = math.sqrt(math.pi * delta) * (1.0 if periodic else math.erf(0.5 / math.sqrt(delta)))
+    return a ** d
+
+
+def error_vs_oracle(u_all, sample, u_or, tol, w=None):
+    """max |u - u_oracle| / max |u_oracle| on the sample (acceptance: 10 tol).
+
+    Theorem 1 bounds the kernel's error in absolute terms, so the transform's error scales with
+    ||sigma||_inf ||G||_1, not with |u|.  When the exact transform is itself below tol times that
+    scale (the periodic trig density at large delta: u = (pi delta)^{d/2} exp(-d pi^2 delta n_p^2)
+    sigma_p), max |u| holds only rounding and the row is judged against ||sigma||_inf ||G||_1
+    instead ("degenerate")."""
     u = u_all.reshape(-1, u_or.shape[1])[sample]
-    e = float(np.abs(u - u_or).max() / np.abs(u_or).max())
-    return {"max_abs_over_max_u": e, "bound": 10 * tol, "within_bound": bool(e <= 10 * tol),
-            "sample_leaves": int(len(sample))}
+    err = float(np.abs(u - u_or).max())
+    umax = float(np.abs(u_or).max())
+    e = err / umax if umax > 0 else math.inf
+    out = {"max_abs_over_max_u": e, "bound": 10 * tol, "within_bound": bool(e <= 10 * tol),
+           "sample_leaves": int(len(sample))}
+    if w is not None:
+        floor = float(np.abs(w.sigma).max()) * kernel_l1(w.d, w.delta, w.periodic)
+        es = err / floor
+        out["max_abs_over_sigma_g1"] = es
+        if umax < tol * floor:
+            out["degenerate"] = "max|u| below tol ||sigma||_inf ||G||_1; judged on that scale"
+            out["within_bound"] = bool(es <= 10 * tol)
+    return out
 
 
 def run_batched_and_serving(args, F, torch, large=()):
@@ -391,7 +425,7 @@ def run_sweeps(args, F, torch, w_adapt, flush):
         ms = float(t.mean())
         row = {"ms_per_step": ms, "points_per_s": w.n_points / ms * 1e3, "steps": steps,
                "cutoff_level": info["cutoff_level"], "n_f": info["n_f"]}
-        row["error_vs_oracle"] = error_vs_oracle(outt.cpu().numpy(), ref[0], ref[1], tol)
+        row["error_vs_oracle"] = error_vs_oracle(outt.cpu().numpy(), ref[0], ref[1], tol, w)
         return row
 
     import dataclasses
@@ -736,7 +770,7 @@ def main():
         h2["plan"].close()
         ref2 = oracle_sample(w2, 48, 5)
         for fname, ftol, _ in forms:
-            r2[fname]["error_vs_oracle"] = error_vs_oracle(u2[fname], ref2[0], ref2[1], ftol)
+            r2[fname]["error_vs_oracle"] = error_vs_oracle(u2[fname], ref2[0], ref2[1], ftol, w2)
         del u2
         adaptive = {"workload": workload_text(w2), "forms": r2}
     if not args.no_batch and rank == 0:
@@ -791,7 +825,7 @@ def main():
                              "rate extrapolated linearly to the whole workload"}
             # every form's result on the same sample, against the oracle (acceptance: 10 tol)
             for fname, ftol, _ in forms:
-                results[fname]["error_vs_oracle"] = error_vs_oracle(u_forms[fname], sample, u_or, ftol)
+                results[fname]["error_vs_oracle"] = error_vs_oracle(u_forms[fname], sample, u_or, ftol, w)
             err = dict(results[head["name"]]["error_vs_oracle"], sample=cpu["sample"])
         hr = results[head["name"]]
         line = {

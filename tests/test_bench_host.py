@@ -58,6 +58,43 @@ def test_error_vs_oracle_row(bench):
     assert r["sample_leaves"] == 3
 
 
+def test_kernel_l1_against_quadrature(bench):
+    """max_x of the integral of G over B: free kernel at the centre, periodic kernel over one period
+    (image sum), by composite Gauss-Legendre quadrature."""
+    import math
+    import numpy as np
+    x, wq = np.polynomial.legendre.leggauss(200)
+    y, wy = 0.5 * x, 0.5 * wq
+    for delta in (1e-3, 0.1, 1.0, 4.0):
+        free = float((np.exp(-y ** 2 / delta) * wy).sum())
+        per = float(sum((np.exp(-(y + n) ** 2 / delta) * wy).sum() for n in range(-12, 13)))
+        for d in (1, 2, 3):
+            assert abs(bench.kernel_l1(d, delta, False) - free ** d) <= 1e-12 * free ** d
+            assert abs(bench.kernel_l1(d, delta, True) - per ** d) <= 1e-12 * per ** d
+    assert abs(bench.kernel_l1(3, 1.0, True) - math.pi ** 1.5) < 1e-12
+
+
+def test_error_vs_oracle_degenerate_scale(bench):
+    """Periodic trig density at delta = 1: the exact u is (pi delta)^{3/2} exp(-3 pi^2 delta n_p^2)
+    sigma_p, far below rounding, so the error is judged on ||sigma||_inf ||G||_1; a genuinely
+    wrong result on that scale still fails."""
+    import types
+    import numpy as np
+    w = types.SimpleNamespace(d=3, delta=1.0, periodic=True, sigma=np.array([[1.0, -1.0]]))
+    u_or = np.full((2, 8), 1e-200)
+    u = np.full((2, 8), 3e-17)
+    r = bench.error_vs_oracle(u.reshape(-1), np.array([0, 1]), u_or, 1e-6, w)
+    assert r["max_abs_over_max_u"] > 1 and "degenerate" in r and r["within_bound"]
+    u[1, 3] = 1e-3
+    assert not bench.error_vs_oracle(u.reshape(-1), np.array([0, 1]), u_or, 1e-6, w)["within_bound"]
+    # a non-degenerate row keeps the max |u| scale
+    u_or = np.ones((2, 8))
+    u = np.ones((2, 8))
+    u[0, 0] += 2e-5
+    r = bench.error_vs_oracle(u.reshape(-1), np.array([0, 1]), u_or, 1e-6, w)
+    assert "degenerate" not in r and not r["within_bound"]
+
+
 def test_derived_alu_peaks(bench):
     # 152 SMs at 2.07 GHz: 2 FP64 FMA / clock / SM and 128 FP32 lanes, 2 flops per FMA
     assert abs(bench.FP64_PEAK_TFLOPS - 1.25856) < 1e-9
