@@ -44,6 +44,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # 3xTF32 spends three TF32 products on each FP32-accurate product
 TF32_PER_BF16 = 0.5
 SPLIT_PRODUCTS = 3
+SLICE_PRODUCTS = 21   # BF16 slice products per FP64 product in the sliced FP64 tensor-core stages
 FALLBACK_BF16_TFLOPS = 1900.0
 L2_FLUSH_BYTES = 256 << 20
 
@@ -143,6 +144,13 @@ def split_tensor_peak_tflops():
     return pk["bf16_tflops"] * TF32_PER_BF16 / SPLIT_PRODUCTS, pk["source"]
 
 
+def sliced_tensor_peak_tflops():
+    """Roofline of the sliced FP64 tensor-core stages (precision FP64_TC, 3D): the BF16 tensor pipe
+    (measured burst rate) divided by the 21 BF16 slice products of each FP64 product."""
+    pk = peaks()
+    return pk["bf16_tflops"] / SLICE_PRODUCTS, pk["source"]
+
+
 def roofline_of(info, prof, nprof, prec, traffic_key=None):
     """Dominant phase of one form (per-phase CUDA events over the timed region) against the peak
     it is bound by: algorithmic flops of the phase / its average time per step.  FP64 forms: the
@@ -153,10 +161,17 @@ def roofline_of(info, prof, nprof, prec, traffic_key=None):
                    "near": info["direct_flops"], "merge": 0, "push": 0}
     n = max(nprof, 1)
     tpk, tsrc = split_tensor_peak_tflops()
+    spk, ssrc = sliced_tensor_peak_tflops()
+    sliced = info.get("n_sliced_jobs", 0) > 0
+
+    def on_tensor(ph):
+        return (prec == 1 and ph in ("form", "evaluate", "gather")) or (sliced and ph in ("form", "evaluate"))
 
     def peak_of(ph):
         if prec == 1 and ph in ("form", "evaluate", "gather"):
             return tpk, (f"{tsrc}: BF16 burst x {TF32_PER_BF16} (TF32/BF16) / {SPLIT_PRODUCTS} (3xTF32)")
+        if sliced and ph in ("form", "evaluate"):
+            return spk, f"{ssrc}: BF16 burst / {SLICE_PRODUCTS} (BF16 slice products per FP64 product)"
         return FP64_PEAK_TFLOPS, "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"
 
     dom = max(prof, key=lambda k: prof[k])
@@ -173,13 +188,17 @@ def roofline_of(info, prof, nprof, prec, traffic_key=None):
             phases[ph] = {"ms": t, "achieved_tflops": a, "peak_tflops": pk, "frac": a / pk}
             if prec == 1 and ph in ("form", "evaluate", "gather"):
                 phases[ph]["frac_of_fp32_cuda_core"] = a / FP32_PEAK_TFLOPS
-    out = {"bound": "tensor" if (prec == 1 and dom in ("form", "evaluate", "gather")) else "alu",
+            if sliced and ph in ("form", "evaluate"):
+                phases[ph]["frac_of_fp64_alu"] = a / FP64_PEAK_TFLOPS
+    out = {"bound": "tensor" if on_tensor(dom) else "alu",
            "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
            "frac": achieved / peak, "traffic": traffic["bytes"] if traffic else None,
            "traffic_source": traffic["source"] if traffic else None, "phases": phases,
            "peak_source": src, "phase_ms_per_step": {k: v / n for k, v in prof.items()}}
-    if out["bound"] == "tensor":
+    if out["bound"] == "tensor" and prec == 1:
         out["frac_of_fp32_cuda_core"] = achieved / FP32_PEAK_TFLOPS
+    elif out["bound"] == "tensor":
+        out["frac_of_fp64_alu"] = achieved / FP64_PEAK_TFLOPS
     return out
 
 

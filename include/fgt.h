@@ -58,10 +58,17 @@ typedef enum { FGT_BC_FREE = 0, FGT_BC_PERIODIC = 1 } fgt_bc;
  * FGT_PREC_SPLIT: contractions and stored expansions in FP32 (accepted only
  *   when tol >= 1e-7); the near-field 1D tables, the tables' construction and
  *   the final per-leaf accumulation stay FP64.
- * FGT_PREC_FP64_TC: as FGT_PREC_FP64, with the 3D form's last contraction and
- *   the 3D evaluation's first two contractions on the FP64 tensor cores (DMMA);
- *   FP64 products throughout, only the order of the sums differs.  2D plans and
- *   the kernels without a DMMA form run as FGT_PREC_FP64. */
+ * FGT_PREC_FP64_TC: FP64-accurate contractions on the tensor cores.  3D plans in
+ *   the fused mode with n_f <= 80 (the plane-wave modes per axis of Section 2.1)
+ *   run every contraction of the form and the evaluation (Lemmas pwbox and
+ *   pweval) on the BF16 tensor pipe: each FP64 operand is rounded to 47 bits
+ *   against its row's (column's) largest exponent and cut into six 8-bit
+ *   digits, the digit products are summed exactly in FP32 and recombined in
+ *   64-bit integers (error about 2^-46 of the sum of |products|); gather, near
+ *   field and accumulation stay FP64.  FGT_OZAKI=0 in the environment at plan
+ *   creation, and the allocation-free call, use the FP64 tensor cores (DMMA)
+ *   for the 3D form's last and the evaluation's first two contractions instead.
+ *   2D plans and the kernels without either form run as FGT_PREC_FP64. */
 typedef enum { FGT_PREC_FP64 = 0, FGT_PREC_SPLIT = 1, FGT_PREC_FP64_TC = 2 } fgt_prec;
 
 /* How the plane-wave hierarchy of Algorithm 4 is executed.
@@ -112,6 +119,7 @@ typedef struct {
   int64_t n_push_items;       /* hierarchical mode: parents pushed to their 2^d children (T_p->c) */
   int64_t n_tc_eval_blocks;   /* evaluation blocks whose three contractions all run on tcgen05 */
   int64_t n_tc_form_blocks;   /* form blocks whose three contractions all run on tcgen05 */
+  int64_t n_sliced_jobs;      /* FP64_TC, 3D: CTAs of the six sliced FP64 tensor-core stages per execution (0: not used) */
 } fgt_plan_info;
 
 /* Build a plan: validate the tree, choose l_c, n_f (or n_p), build the lists
@@ -136,7 +144,8 @@ fgt_status fgt_plan_create_host(int d, double delta, double tol, double eps_pw, 
 
 /* Borrow a host-only plan's array by name ("blocks", "block_leaves", "Ff", "Fh", "Ef", "Eh",
  * "gather_dst", "gather_ptr", "gather_src", "Pf", "Ph", "near_tgt", "near_flags", "near_ptr",
- * "near_src", "near_tab", "merge<i>_items|qf|qh", "push<i>_items|qf|qh").  The pointer stays
+ * "near_src", "near_tab", "merge<i>_items|qf|qh", "push<i>_items|qf|qh", and for the sliced FP64
+ * tensor-core stages "oz_jobs<kind>", "oz_btab", "oz_bexp", "eval_blocks").  The pointer stays
  * valid until the plan is destroyed or re-planned.  FGT_ERR_STATE for device plans. */
 fgt_status fgt_plan_host_array(const fgt_plan *plan, const char *name, const void **data, size_t *bytes);
 

@@ -47,7 +47,8 @@ class PlanInfo(ctypes.Structure):
                                               "eval_flops", "gather_flops", "direct_flops", "device_bytes")] + \
                [("prec", ctypes.c_int32), ("mode", ctypes.c_int32), ("launches", ctypes.c_int32)] + \
                [("n_merge_items", ctypes.c_int64), ("n_push_items", ctypes.c_int64),
-                ("n_tc_eval_blocks", ctypes.c_int64), ("n_tc_form_blocks", ctypes.c_int64)]
+                ("n_tc_eval_blocks", ctypes.c_int64), ("n_tc_form_blocks", ctypes.c_int64),
+                ("n_sliced_jobs", ctypes.c_int64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

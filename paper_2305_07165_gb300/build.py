@@ -1,7 +1,7 @@
 """Builds libfgt.so in-tree with nvcc for sm_103a (GB300), and libfgt_checked.so (the same
 library with bounds-checked kernels).
 
-Four translation units (the kernels twice) are compiled in parallel, then linked with the CUDA
+Five translation units (the kernels twice) are compiled in parallel, then linked with the CUDA
 runtime.  Used by ``__graft_entry__.build()`` and on first import of the
 package when the library is missing or older than its sources.
 """
@@ -18,8 +18,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libfgt.so")
 CHECKED_LIB = os.path.join(HERE, "libfgt_checked.so")  # kernels built with -DFGT_CHECKED
 OBJDIR = os.path.join(HERE, "_build")
-SOURCES = ["fgt_kernels.cu", "fgt_plan.cpp", "fgt_tables.cpp"]
-HEADERS = ["fgt_internal.h", "fgt_exec.h", "fgt_tables.h"]
+SOURCES = ["fgt_kernels.cu", "fgt_plan.cpp", "fgt_tables.cpp", "fgt_ozaki.cu"]
+HEADERS = ["fgt_internal.h", "fgt_exec.h", "fgt_tables.h", "fgt_tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

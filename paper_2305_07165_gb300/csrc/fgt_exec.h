@@ -75,14 +75,28 @@ struct ExecDesc {
   // beyond n1), read through the tensor map psi_map; 0: the slot layout of phi
   int psi_pitch = 0;
   int psi_map_ready = 0;  // 1 once psi_map has been encoded for psi
-  alignas(64) CUtensorMap psi_map;
+  CUtensorMap psi_map;  // 64-byte aligned by its type
   // all-tcgen05 form (form7_kernel): the packed density in (J1, J2, J3) order (sig_order 1; 0: the
   // (J3, J2, J1) order of the CUDA-core forms) read through one tensor map per K = 8, 16, 32
   int sig_order = 0;
   int sig_maps_ready = 0;  // 1 once sig_map has been encoded for sigp (the K in use)
-  alignas(64) CUtensorMap sig_map[3];
+  CUtensorMap sig_map[3];
   // 1: every form block is the only one of its anchor and stores the whole slot (no clear of phi)
   int phi_stored = 0;
+
+  // FP64-accurate form and evaluation on the BF16 tensor cores (precision FP64_TC, 3D, fused mode):
+  // six contraction stages (form: x3, x2, x1; evaluation: m1, m2, m3), one launch each over its
+  // jobs, every operand cut into six 8-bit slices with exact FP32 accumulation of the slice products
+  // (oz_stage_kernel).  The stages pass their FP64 intermediates through oz_x / oz_y; without them
+  // (the allocation-free call) the FP64 kernels of the block lists above run instead.
+  int oz = 0;
+  int oz_sole = 0;                      // every form block stores its anchor's slot (no clear of phi)
+  const OzJob *oz_jobs[6] = {};
+  int64_t oz_njobs[6] = {};
+  const unsigned char *oz_btab = nullptr;  // the sliced 1D matrices (BF16 digit planes)
+  const int32_t *oz_bexp = nullptr;        // their column exponents
+  const Block *eval_blocks = nullptr;      // the evaluation's blocks (the jobs of stages 3-5 index them)
+  double *oz_x = nullptr, *oz_y = nullptr;
 
   // out->in gather at the cutoff level
   int64_t n_gather = 0;
@@ -151,6 +165,34 @@ int batch_queue_grid(const BatchQueue *q);
 void batch_queue_destroy(BatchQueue *q);
 // One item whose dependency nothing satisfies, with a wait of about a millisecond: *status = 1.
 cudaError_t selftest_batch_timeout(int *status);
+
+// Sliced FP64 tensor-core contraction stages (fgt_ozaki.cu).  Stage kinds 0-2: the form's
+// contractions over x3, x2, x1; 3-5: the evaluation's over m1, m2, m3.  Per block of K nodes a
+// side: R rows, Q contraction length, N columns, split into P parts of Nc (padded to Np) columns,
+// nks k-steps of 16.
+constexpr int kOzSlices = 6;
+constexpr int kOzMaxNp = 80;
+struct OzDims { int R, Q, N, P, Nc, Np, nks; };
+inline __host__ __device__ OzDims oz_dims(int kind, int K, int n1, int nh) {
+  OzDims d{};
+  switch (kind) {
+    case 0: d.R = K * K; d.Q = K; d.N = 2 * nh; break;
+    case 1: d.R = nh * K; d.Q = 2 * K; d.N = 2 * n1; break;
+    case 2: d.R = nh * n1; d.Q = 2 * K; d.N = 2 * n1; break;
+    case 3: d.R = nh * n1; d.Q = 2 * n1; d.N = 2 * K; break;
+    case 4: d.R = K * nh; d.Q = 2 * n1; d.N = 2 * K; break;
+    default: d.R = K * K; d.Q = 2 * nh; d.N = K; break;
+  }
+  d.P = (d.N + kOzMaxNp - 1) / kOzMaxNp;
+  d.Nc = (d.N + d.P - 1) / d.P;
+  d.Np = (d.Nc + 15) / 16 * 16;
+  d.nks = (d.Q + 15) / 16;
+  return d;
+}
+// Enqueue stage `kind` over its jobs: src -> dst (sigma -> oz_x -> oz_y -> phi; psi -> oz_x -> oz_y -> u).
+cudaError_t run_oz_stage(const ExecDesc &e, int kind, const double *src, double *dst, cudaStream_t st);
+// Reads and clears the status word of the sliced stages (1: a wait ran out, 2: its drain as well).
+cudaError_t read_oz_status(int *status);
 
 // Reads and clears the status word of the tcgen05 kernels: 1 when a wait on the tensor cores ran
 // out since the last read (the affected blocks were skipped), else 0.  Synchronous.

@@ -22,6 +22,18 @@ struct Block {
   int64_t leaf0;     // offset into the block-leaf index array; leaves ordered (o_d,..,o_1), o_1 fastest
 };
 
+// One CTA of an FP64-accurate tensor-core contraction stage (the sliced form and evaluation):
+// row tile `tile` (128 rows) and column part `part` of block `blk`'s stage matrix product.
+struct OzJob {
+  int32_t blk;       // index into the plan's blocks
+  int16_t tile;      // 128-row tile of the stage's rows
+  int16_t part;      // column part (at most 80 columns each)
+  int64_t scr;       // offset (doubles) of the block's intermediates in the two scratch arrays
+  int64_t boff;      // byte offset of the block's sliced 1D matrix for this stage
+  int32_t eoff;      // offset of its column exponents
+  int32_t flags;     // bit 0: add into the output (another block writes the same slot / leaf)
+};
+
 // One out->in translation source at the cutoff level.
 struct GatherSrc {
   int32_t slot;      // source outgoing slot

@@ -25,6 +25,7 @@
 
 #include "fgt_exec.h"
 #include "fgt_tables.h"
+#include "fgt_tc.cuh"
 
 namespace fgt {
 
@@ -1384,15 +1385,6 @@ __global__ void __launch_bounds__(256) eval2_kernel(const Block *__restrict__ bl
 
 __device__ int g_tc_status;  // set to 1 when a wait on the tensor cores ran out (read by fgt_device_status)
 
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t sbo) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)(128 >> 4) << 16;                  // leading byte offset: next core matrix along K
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;        // stride byte offset: next 8-row group
-  d |= (uint64_t)1 << 46;                            // descriptor version of the sm_100 family
-  return d;                                          // base offset 0, no swizzle
-}
 
 // Instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both K-major, M x N.
 __host__ __device__ constexpr uint32_t umma_idesc_tf32(int M, int N) {
@@ -1411,25 +1403,7 @@ __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a, uint64_t 
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ void umma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
-}
 
-// Waits for the completion of the mbarrier phase of the given parity; gives up after `limit`
-// clocks (by default 2^31, about one second) and returns false.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit = 1LL << 31) {
-  const long long t0 = clock64();
-  for (;;) {
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if (clock64() - t0 > limit) return false;
-  }
-}
 
 // Self-test of the time-out path: one thread waits, `clocks` at most, on an mbarrier that nothing
 // completes, and sets the status word as the tensor-core kernels do when their waits run out.
@@ -1440,18 +1414,7 @@ __global__ void wait_timeout_selftest_kernel(long long clocks) {
   if (!mbar_wait(smem_addr(&bar), 0, clocks)) atomicExch(&g_tc_status, 1);
 }
 
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Bulk asynchronous copy (the copy engine of the sm_90+ memory system): `bytes` (a multiple of 16,
-// both addresses 16-byte aligned) from global to shared memory, completing on an mbarrier that
-// the issuing thread armed for that many bytes.
-__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(mbar)
-               : "memory");
-}
 
 // ----------------------------------------------------------------------------- expansions in tcgen05 operand layout
 //
@@ -1739,35 +1702,6 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
       : "memory");
 }
 
-template <int N>
-__device__ __forceinline__ void tmem_ld(uint32_t addr, uint32_t (&v)[N]) {
-  if constexpr (N == 4) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
-                 : "r"(addr));
-  } else if constexpr (N == 8) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                 : "r"(addr));
-  } else if constexpr (N == 16) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-        : "r"(addr));
-  } else {
-    static_assert(N == 32, "tmem_ld: 4, 8, 16 or 32 columns");
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
-        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
-          "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(addr));
-  }
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 
 // hi / lo TF32 halves of a pair, stored at byte offset o of the hi and lo operand copies
 __device__ __forceinline__ void put_split2(unsigned char *hi, unsigned char *lo, uint32_t o, float a, float b) {
@@ -3014,18 +2948,30 @@ __global__ void merge_kernel(const TreeShift *__restrict__ items, const typename
   const TreeShift it = items[blockIdx.x];
   int m1, m2, m3;
   mode_index<D>(idx, n1, m1, m2, m3);
-  R ar = 0, ai = 0;
-  for (int c = 0; c < (1 << D); ++c) {
-    const int b1 = c & 1, b2 = (c >> 1) & 1, b3 = (c >> 2) & 1;
-    C ph = qf[b1 * n1 + m1];
-    if (D == 3) {
-      ph = cmul(ph, qf[b2 * n1 + m2]);
-      ph = cmul(ph, qh[b3 * nh + m3]);
-    } else {
-      ph = cmul(ph, qh[b2 * nh + m2]);
+  // the phase is a product of one factor per axis, so the 2^d children are combined axis by axis:
+  // pairs along x_1, then along x_2, then along the last (half-range) axis -- 14 complex products
+  // per mode in 3D instead of 8 phase builds (16 products) and 8 applications
+  const C q10 = qf[m1], q11 = qf[n1 + m1];
+  const int ml = (D == 3) ? m3 : m2;  // last axis: half range
+  const C ql0 = qh[ml], ql1 = qh[nh + ml];
+  C w[2];
+#pragma unroll
+  for (int bl = 0; bl < 2; ++bl) {          // last-axis half (child bit d - 1)
+    R sr = 0, si = 0;
+#pragma unroll
+    for (int b2 = 0; b2 < (D == 3 ? 2 : 1); ++b2) {
+      const int c0 = (D == 3) ? ((b2 << 1) | (bl << 2)) : (bl << 1);
+      R tr = 0, ti = 0;                      // x_1 pair (child bit 0)
+      cfma(tr, ti, q10, phi[(int64_t)it.child[c0] * slot_size + idx]);
+      cfma(tr, ti, q11, phi[(int64_t)it.child[c0 | 1] * slot_size + idx]);
+      if (D == 3) cfma(sr, si, qf[b2 * n1 + m2], C{tr, ti});  // x_2 pair (child bit 1)
+      else { sr = tr; si = ti; }
     }
-    cfma(ar, ai, ph, phi[(int64_t)it.child[c] * slot_size + idx]);
+    w[bl] = C{sr, si};
   }
+  R ar = 0, ai = 0;
+  cfma(ar, ai, ql0, w[0]);
+  cfma(ar, ai, ql1, w[1]);
   if (FGT_OK_PTR(&phi[(int64_t)it.parent * slot_size + idx])) phi[(int64_t)it.parent * slot_size + idx] = C{ar, ai};
 }
 
@@ -3041,16 +2987,21 @@ __global__ void push_kernel(const TreeShift *__restrict__ items, const typename 
   int m1, m2, m3;
   mode_index<D>(idx, n1, m1, m2, m3);
   const C v = psi[(int64_t)it.parent * slot_size + idx];
-  for (int c = 0; c < (1 << D); ++c) {
-    const int b1 = c & 1, b2 = (c >> 1) & 1, b3 = (c >> 2) & 1;
-    C ph = qf[b1 * n1 + m1];
-    if (D == 3) {
-      ph = cmul(ph, qf[b2 * n1 + m2]);
-      ph = cmul(ph, qh[b3 * nh + m3]);
-    } else {
-      ph = cmul(ph, qh[b2 * nh + m2]);
+  // the phase axis by axis: the last (half-range) axis, then x_2, then x_1 -- 14 complex products
+  // per mode in 3D instead of 8 phase builds and 8 applications
+  const int ml = (D == 3) ? m3 : m2;
+  const C q10 = qf[m1], q11 = qf[n1 + m1];
+#pragma unroll
+  for (int bl = 0; bl < 2; ++bl) {
+    const C wl = cmul(qh[bl * nh + ml], v);
+#pragma unroll
+    for (int b2 = 0; b2 < (D == 3 ? 2 : 1); ++b2) {
+      const C w2 = (D == 3) ? cmul(qf[b2 * n1 + m2], wl) : wl;
+      const int c0 = (D == 3) ? ((b2 << 1) | (bl << 2)) : (bl << 1);
+      C *o0 = &psi[(int64_t)it.child[c0] * slot_size + idx], *o1 = &psi[(int64_t)it.child[c0 | 1] * slot_size + idx];
+      if (FGT_OK_PTR(o0)) *o0 = cmul(q10, w2);
+      if (FGT_OK_PTR(o1)) *o1 = cmul(q11, w2);
     }
-    if (FGT_OK_PTR(&psi[(int64_t)it.child[c] * slot_size + idx])) psi[(int64_t)it.child[c] * slot_size + idx] = cmul(ph, v);
   }
 }
 
@@ -3333,8 +3284,17 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
   if (e.n_blocks > 0) {
     // outgoing expansions: zero, then every block adds its contribution (unless every block is the
     // only one of its anchor and stores the whole slot)
-    if (!e.phi_stored && (err = cudaMemsetAsync(phi, 0, sizeof(C) * ss * e.n_phi_slots, st)) != cudaSuccess)
+    // FP64 on the BF16 tensor cores by exact slicing: three contraction stages through the scratch
+    // arrays (their absence -- the allocation-free call -- leaves the FP64 kernels below)
+    const bool oz_form = D == 3 && sizeof(R) == 8 && e.oz && e.oz_x != nullptr;
+    if (!(oz_form ? e.oz_sole : e.phi_stored) &&
+        (err = cudaMemsetAsync(phi, 0, sizeof(C) * ss * e.n_phi_slots, st)) != cudaSuccess)
       return err;
+    if (oz_form) {
+      if ((err = run_oz_stage(e, 0, sigma, e.oz_x, st)) != cudaSuccess) return err;
+      if ((err = run_oz_stage(e, 1, e.oz_x, e.oz_y, st)) != cudaSuccess) return err;
+      if ((err = run_oz_stage(e, 2, e.oz_y, reinterpret_cast<double *>(phi), st)) != cudaSuccess) return err;
+    } else {
     if (D == 3 && sizeof(R) == 4 && e.sigp != nullptr && e.n_pack > 0) {
       sigma_pack_kernel<<<(unsigned)e.n_pack, 256, 0, st>>>(e.blocks, e.pack_block, e.block_leaves, sigma, e.sigp,
                                                             e.k);
@@ -3410,6 +3370,7 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     if ((err = fs.join()) != cudaSuccess) return err;
+    }
   }
   mark(0, 1);
   mark(1, 0);
@@ -3456,8 +3417,14 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
                                      static_cast<unsigned char *>(e.psi_tc), n1, nh, ss, e.n_psi_tc_slots);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
+  const bool oz_eval = D == 3 && sizeof(R) == 8 && e.oz && e.oz_x != nullptr;
+  if (oz_eval) {
+    if ((err = run_oz_stage(e, 3, reinterpret_cast<const double *>(eval_src), e.oz_x, st)) != cudaSuccess) return err;
+    if ((err = run_oz_stage(e, 4, e.oz_x, e.oz_y, st)) != cudaSuccess) return err;
+    if ((err = run_oz_stage(e, 5, e.oz_y, u, st)) != cudaSuccess) return err;
+  }
   Spread es(e, st);
-  if (e.n_e1 > 0) {
+  if (e.n_e1 > 0 && !oz_eval) {
     const size_t esm = eval_smem_bytes(D, e.Kmax_e1, n1, sizeof(R) == 4);
     if ((err = cudaFuncSetAttribute(eval_kernel<D, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm)) !=
         cudaSuccess)
@@ -3468,6 +3435,7 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   for (const LaunchRange &lr : e.e2_ranges) {  // one launch per block size K
+    if (oz_eval) break;
     if (D == 3 && lr.tensor == 7 && sizeof(R) == 4 && e.psi_pitch == e7::kP && e.psi_map_ready) {
       // all stages on tcgen05
       // 16 warps for K = 32 blocks, 8 for the smaller ones (measured: the extra warps hide the latency
@@ -3567,7 +3535,11 @@ int launches_per_transform(const ExecDesc &e) {
   int n = 0;
   n += (e.d == 3 && e.prec == 1 && e.n_pack > 0);  // sigma packing
   n += (e.d == 3 && e.prec == 1 && e.n_psi_tc_slots > 0);  // tcgen05 operand copy of the expansions
-  n += (e.n_f1 > 0) + (int)e.f2_ranges.size() + (e.n_e1 > 0) + (int)e.e2_ranges.size();  // form + evaluate
+  if (e.d == 3 && e.prec == 0 && e.oz) {  // sliced FP64 tensor-core stages
+    for (int kind = 0; kind < 6; ++kind) n += e.oz_njobs[kind] > 0;
+  } else {
+    n += (e.n_f1 > 0) + (int)e.f2_ranges.size() + (e.n_e1 > 0) + (int)e.e2_ranges.size();  // form + evaluate
+  }
   for (const ShiftStep &s : e.merge) n += s.n > 0;
   for (const ShiftStep &s : e.push) n += s.n > 0;
   if (!e.fourier && e.n_gather > 0) n += 1;
@@ -4076,7 +4048,9 @@ cudaError_t read_tc_status(int *status) {
   if (v != 0 && (err = cudaMemcpyToSymbol(g_tc_status, &zero, sizeof(int))) != cudaSuccess) return err;
   if (v7 != 0 && (err = cudaMemcpyToSymbol(g_tc7_status, &zero, sizeof(int))) != cudaSuccess) return err;
   if (vf != 0 && (err = cudaMemcpyToSymbol(g_tcf_status, &zero, sizeof(int))) != cudaSuccess) return err;
-  *status = std::max(v, std::max(v7, vf));
+  int vo = 0;
+  if ((err = read_oz_status(&vo)) != cudaSuccess) return err;
+  *status = std::max(std::max(v, vo), std::max(v7, vf));
   return cudaSuccess;
 }
 
@@ -4191,6 +4165,8 @@ cudaError_t run_transform_noalloc(const ExecDesc &e, const double *sigma, double
   f.psi_pitch = 0;     // and the plain expansion layout (no tensor map over the scratch array)
   f.psi_map_ready = 0;
   f.sig_maps_ready = 0;
+  f.oz = 0;            // no sliced tensor-core stages (their intermediates live in the plan's workspace)
+  f.oz_x = f.oz_y = nullptr;
   f.events = nullptr;
   return run_transform(f, sigma, u, stream);
 }

@@ -25,6 +25,7 @@
 #include <new>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <unordered_map>
 #include <unordered_set>
 #include <vector>
@@ -138,6 +139,7 @@ struct fgt_plan {
   bool eval7 = false;       // split precision, 3D: every evaluation stage on tcgen05 (eval7_kernel)
   bool form7 = false;       // split precision, 3D: every form stage on tcgen05 (form7_kernel), K = 16, 32
   bool form7_k8 = false;    // and for K = 8 blocks
+  bool ozaki = true;        // FP64_TC, 3D: form and evaluation as sliced FP64 stages on the BF16 tensor cores
   cudaStream_t side[fgt::kSides] = {};     // near field and concurrent per-size launches
   cudaEvent_t fork_ev[fgt::kSides] = {}, join_ev[fgt::kSides] = {};
   DevPack host_pack;        // host copy of the uploaded lists and tables (kept for host-only plans)
@@ -427,6 +429,7 @@ void fill_flops(fgt_plan &P, const fgt::ExecDesc &ex, const std::vector<fgt::Blo
   // evaluation flops in the contraction order of the kernel that takes the block: the half-range
   // axis last (eval5 ranges) or first (all others)
   auto half_range_last = [&](int64_t K) {
+    if (ex.oz) return true;  // the sliced stages contract m1, m2, then m3
     for (const fgt::LaunchRange &lr : ex.e2_ranges)
       if (lr.K == K) return lr.tensor == 3 || lr.tensor == 7;
     return false;
@@ -455,6 +458,9 @@ void fill_flops(fgt_plan &P, const fgt::ExecDesc &ex, const std::vector<fgt::Blo
   I.n_tc_form_blocks = 0;
   for (const fgt::LaunchRange &lr : ex.f2_ranges)
     if (lr.tensor == 7) I.n_tc_form_blocks += lr.count;
+  I.n_sliced_jobs = 0;
+  if (ex.oz)
+    for (int kind = 0; kind < 6; ++kind) I.n_sliced_jobs += ex.oz_njobs[kind];
 }
 
 template <typename C>
@@ -886,6 +892,147 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   ex.Kmax_e1 = Ke1;
   ex.n_e2 = (int64_t)e2.size();
 
+  // ---- FP64 on the BF16 tensor cores by exact slicing (precision FP64_TC, 3D, fused mode): the
+  // form's and the evaluation's contractions as six stages of the sliced-stage kernel.  Each block's
+  // 1D matrix of a stage, in the real form of its complex contraction, is cut here once into six
+  // balanced 8-bit digits per entry against its column's largest exponent (exact: a 47-bit rounding
+  // of each entry, then integer digits), laid out as the kernel's bulk copies read it: per column
+  // part and 16-deep step, six BF16 planes in the K-major core-matrix layout.  The block lists above
+  // stay, for the allocation-free call.
+  std::vector<fgt::OzJob> ozjobs[6];
+  std::vector<unsigned char> oztab;
+  std::vector<int32_t> ozexp;
+  int64_t oz_scr = 0;  // doubles per scratch array
+  ex.oz = 0;
+  ex.oz_sole = 0;
+  if constexpr (std::is_same<C, double2>::value) {
+    if (P.prec == FGT_PREC_FP64_TC && P.ozaki && d == 3 && !hier && !P.fourier && n1 <= 80 && !blocks.empty()) {
+      ex.oz = 1;
+      std::map<std::tuple<int, int, int>, std::pair<int64_t, int32_t>> cls;
+      std::vector<double> Bm;
+      auto table = [&](int kind, int K, int mat) -> std::pair<int64_t, int32_t> {
+        const auto key = std::make_tuple(kind, K, mat);
+        auto it = cls.find(key);
+        if (it != cls.end()) return it->second;
+        const fgt::OzDims dm = fgt::oz_dims(kind, K, n1, nh);
+        Bm.assign((size_t)dm.Q * dm.N, 0.0);
+        auto B = [&](int q, int n) -> double & { return Bm[(size_t)q * dm.N + n]; };
+        if (kind == 0) {  // x3, half range: q = J3, n = (m3, c); sigma is real
+          for (int J = 0; J < K; ++J)
+            for (int m = 0; m < nh; ++m) {
+              const C f = Fh[((size_t)(mat + J / k) * nh + m) * k + J % k];
+              B(J, 2 * m) = f.x;
+              B(J, 2 * m + 1) = f.y;
+            }
+        } else if (kind <= 2) {  // x2 / x1: q = (c, J), n = (m, c')
+          for (int J = 0; J < K; ++J)
+            for (int m = 0; m < n1; ++m) {
+              const C f = Ff[((size_t)(mat + J / k) * n1 + m) * k + J % k];
+              B(J, 2 * m) = f.x;
+              B(K + J, 2 * m) = -f.y;
+              B(J, 2 * m + 1) = f.y;
+              B(K + J, 2 * m + 1) = f.x;
+            }
+        } else if (kind <= 4) {  // m1: q = (m, c), n = (c', I); m2: q = (c, m), n = (c', I)
+          for (int I = 0; I < K; ++I)
+            for (int m = 0; m < n1; ++m) {
+              const C e = Ef[((size_t)(mat + I / k) * k + I % k) * n1 + m];
+              const int q0 = kind == 3 ? 2 * m : m, q1 = kind == 3 ? 2 * m + 1 : n1 + m;
+              B(q0, I) = e.x;
+              B(q1, I) = -e.y;
+              B(q0, K + I) = e.y;
+              B(q1, K + I) = e.x;
+            }
+        } else {  // m3, half range, real part: q = (c, m3), n = I3
+          for (int I = 0; I < K; ++I)
+            for (int m = 0; m < nh; ++m) {
+              const C e = Eh[((size_t)(mat + I / k) * k + I % k) * nh + m];
+              B(m, I) = e.x;
+              B(nh + m, I) = -e.y;
+            }
+        }
+        const int64_t boff = (int64_t)oztab.size();
+        const int32_t eoff = (int32_t)ozexp.size();
+        const size_t bbytes = (size_t)fgt::kOzSlices * dm.Np * 32;
+        oztab.resize(oztab.size() + (size_t)dm.P * dm.nks * bbytes, 0);
+        for (int pt = 0; pt < dm.P; ++pt)
+          for (int nl = 0; nl < dm.Np; ++nl) {
+            const int c = pt * dm.Nc + nl;
+            const bool valid = nl < dm.Nc && c < dm.N;
+            double mx = 0.0;
+            if (valid)
+              for (int q = 0; q < dm.Q; ++q) mx = std::max(mx, std::fabs(B(q, c)));
+            int f = 0;
+            if (mx > 0) std::frexp(mx, &f);  // |B(q, c)| < 2^f
+            ozexp.push_back(f);
+            if (mx == 0) continue;
+            for (int q = 0; q < dm.Q; ++q) {
+              long long v = std::llrint(std::ldexp(B(q, c), 47 - f));  // |v| <= 2^47, exact scaling
+              int dg[fgt::kOzSlices];
+              for (int sl = fgt::kOzSlices - 1; sl >= 1; --sl) {
+                const int lo = (int)((v + 128) & 255) - 128;
+                dg[sl] = lo;
+                v = (v - lo) / 256;
+              }
+              dg[0] = (int)v;
+              const int ks = q / 16, kk = q % 16;
+              for (int sl = 0; sl < fgt::kOzSlices; ++sl) {
+                const float fv = (float)dg[sl];
+                uint32_t bits;
+                std::memcpy(&bits, &fv, 4);
+                const uint16_t h = (uint16_t)(bits >> 16);  // exact: |digit| <= 128
+                const size_t off = (size_t)boff + ((size_t)(pt * dm.nks + ks) * fgt::kOzSlices + sl) * dm.Np * 32 +
+                                   (size_t)(nl >> 3) * 256 + (size_t)(kk >> 3) * 128 + (size_t)(nl & 7) * 16 +
+                                   (size_t)(kk & 7) * 2;
+                std::memcpy(&oztab[off], &h, 2);
+              }
+            }
+          }
+        cls[key] = {boff, eoff};
+        return {boff, eoff};
+      };
+      auto add_jobs = [&](int kind, int32_t bi, const fgt::Block &B, int64_t scr, int flags) {
+        const int mat = B.mat[(kind == 0 || kind == 5) ? 2 : (kind == 1 || kind == 4) ? 1 : 0];
+        const auto tb = table(kind, B.K, mat);
+        const fgt::OzDims dm = fgt::oz_dims(kind, B.K, n1, nh);
+        for (int t = 0; t < (dm.R + 127) / 128; ++t)
+          for (int pt = 0; pt < dm.P; ++pt) {
+            fgt::OzJob j{};
+            j.blk = bi;
+            j.tile = (int16_t)t;
+            j.part = (int16_t)pt;
+            j.scr = scr;
+            j.boff = tb.first + (int64_t)pt * dm.nks * fgt::kOzSlices * dm.Np * 32;
+            j.eoff = tb.second + pt * dm.Np;
+            j.flags = flags;
+            ozjobs[kind].push_back(j);
+          }
+      };
+      // per-block intermediates: the form's and the evaluation's stages reuse the same two arrays
+      std::unordered_map<int32_t, int> per_slot;
+      for (const fgt::Block &b : blocks) per_slot[b.slot]++;
+      bool all_sole = true;
+      int64_t sf = 0, se = 0;
+      for (size_t b = 0; b < blocks.size(); ++b) {
+        const fgt::Block &B = blocks[b];
+        const int64_t K = B.K;
+        const bool sole = per_slot[B.slot] == 1;
+        all_sole = all_sole && sole;
+        for (int kind = 0; kind < 3; ++kind) add_jobs(kind, (int32_t)b, B, sf, (kind == 2 && !sole) ? 1 : 0);
+        sf += std::max<int64_t>(2 * nh * K * K, 2 * (int64_t)n1 * nh * K);
+      }
+      for (size_t b = 0; b < eblocks.size(); ++b) {
+        const fgt::Block &B = eblocks[b];
+        const int64_t K = B.K;
+        for (int kind = 3; kind < 6; ++kind) add_jobs(kind, (int32_t)b, B, se, kind == 5 ? (B.flags & 1) : 0);
+        se += std::max<int64_t>(2 * K * nh * n1, 2 * K * K * nh);
+      }
+      oz_scr = std::max(sf, se);
+      ex.oz_sole = all_sole ? 1 : 0;
+      for (int kind = 0; kind < 6; ++kind) ex.oz_njobs[kind] = (int64_t)ozjobs[kind].size();
+    }
+  }
+
   // ---- out->in gather at the cutoff level (P-list)
   std::vector<int32_t> gdst;
   std::vector<int64_t> gptr(1, 0);
@@ -1250,6 +1397,10 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
                o_nptr = pack.add("near_ptr", nptr), o_nsrc = pack.add("near_src", nsrc),
                o_ntab = pack.add("near_tab", ntab), o_npairs = pack.add("near_pairs", npairs);
   const size_t o_nband = pack.add("near_band", nband);
+  size_t o_ozj[6];
+  for (int kind = 0; kind < 6; ++kind) o_ozj[kind] = pack.add("oz_jobs" + std::to_string(kind), ozjobs[kind]);
+  const size_t o_oztab = pack.add("oz_btab", oztab), o_ozexp = pack.add("oz_bexp", ozexp);
+  const size_t o_eblocks = pack.add("eval_blocks", eblocks);
   std::vector<std::tuple<size_t, size_t, size_t, int64_t>> step_off;  // items, qf, qh, n
   for (size_t i = 0; i < merge_h.size(); ++i) {
     auto &s = merge_h[i];
@@ -1277,13 +1428,16 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   const size_t ptc_off = (sigp_off + sigp_bytes + 255) & ~(size_t)255;
   const size_t ptc_bytes = use_tc6 ? fgt::eval6_slot_bytes(n1, nh) * (size_t)tc6_slots : 0;
   ex.n_psi_tc_slots = use_tc6 ? tc6_slots : 0;
+  // sliced FP64 stages: their two intermediate arrays
+  const size_t oz_off = (ptc_off + ptc_bytes + 255) & ~(size_t)255;
+  const size_t oz_bytes = 2 * sizeof(double) * (size_t)oz_scr;
   fill_flops(P, ex, blocks, merge_h.size() + push_h.size() ? [&] {
     int64_t sf = 0;
     for (auto &s : merge_h) sf += 8 * (int64_t)s.items.size() * nc * ex.slot_size;
     for (auto &s : push_h) sf += 8 * (int64_t)s.items.size() * nc * ex.slot_size;
     return sf;
   }() : 0, anchors.size());
-  P.info.device_bytes = (int64_t)(pack.size + ptc_off + ptc_bytes);
+  P.info.device_bytes = (int64_t)(pack.size + oz_off + oz_bytes);
   P.info.n_merge_items = P.info.n_push_items = 0;
   for (auto &s : merge_h) P.info.n_merge_items += (int64_t)s.items.size();
   for (auto &s : push_h) P.info.n_push_items += (int64_t)s.items.size();
@@ -1303,14 +1457,15 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
       e = cudaMemcpy((char *)P.dev + pt.first, pt.second.data(), pt.second.size(), cudaMemcpyHostToDevice);
       if (e != cudaSuccess) return cuda_fail(e, "upload");
     }
-  P.work_bytes = ptc_off + ptc_bytes;
+  P.work_bytes = oz_off + oz_bytes;
   if (P.work_bytes) {
     e = cudaMalloc(&P.work, P.work_bytes);
     if (e != cudaSuccess) {
       P.work = nullptr;
+      const size_t want = P.work_bytes;
       P.work_bytes = 0;
       cudaGetLastError();
-      return fail(FGT_ERR_OOM, "expansion workspace of " + std::to_string(ptc_off + ptc_bytes) + " bytes");
+      return fail(FGT_ERR_OOM, "expansion workspace of " + std::to_string(want) + " bytes");
     }
   }
   auto at = [&](size_t off) { return (const void *)((const char *)P.dev + off); };
@@ -1326,6 +1481,12 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   }
   ex.sigp = sigp_bytes ? (float *)((char *)P.work + sigp_off) : nullptr;
   ex.psi_tc = ptc_bytes ? (void *)((char *)P.work + ptc_off) : nullptr;
+  ex.oz_x = oz_bytes ? (double *)((char *)P.work + oz_off) : nullptr;
+  ex.oz_y = oz_bytes ? ex.oz_x + oz_scr : nullptr;
+  for (int kind = 0; kind < 6; ++kind) ex.oz_jobs[kind] = (const fgt::OzJob *)at(o_ozj[kind]);
+  ex.oz_btab = (const unsigned char *)at(o_oztab);
+  ex.oz_bexp = (const int32_t *)at(o_ozexp);
+  ex.eval_blocks = (const fgt::Block *)at(o_eblocks);
   ex.sig_maps_ready = 0;
   if (ex.sig_order == 1) {
     // the tensor maps over the packed density (its address is set just above)
@@ -1450,6 +1611,10 @@ fgt_status create_impl(int d, double delta, double tol, double eps_pw, int bc, i
     const char *f7 = std::getenv("FGT_FORM7");
     P->form7 = !(f7 && f7[0] == '0');
     P->form7_k8 = f7 && f7[0] == '1';
+    // FP64-accurate form and evaluation on the BF16 tensor cores by exact slicing (precision
+    // FP64_TC, 3D, fused mode, n1 <= 80): the default there; FGT_OZAKI=0 keeps the DMMA kernels
+    const char *oz = std::getenv("FGT_OZAKI");
+    P->ozaki = !(oz && oz[0] == '0');
   }
   P->n_leaves = tree->n_leaves;
   P->leaf_level.assign(tree->leaf_level, tree->leaf_level + tree->n_leaves);

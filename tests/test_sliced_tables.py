@@ -1,0 +1,108 @@
+"""The planner's side of the sliced FP64 tensor-core stages (precision FP64_TC, 3D), on the CPU: the
+digit planes of every stage's 1D matrix, read back from a host-only plan, reconstruct the real form
+of the block's complex 1D matrix (rebuilt here from the plan's FP64 tables) to the 47-bit rounding
+the slicing promises, every digit is a balanced 8-bit one, padding is zero, and the jobs cover
+every (row, column) of every stage of every block exactly once."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+F = pytest.importorskip("paper_2305_07165_gb300")
+
+BLOCK = np.dtype([("slot", "<i4"), ("K", "<i4"), ("dl", "<i4"), ("flags", "<i4"), ("mat", "<i4", 3),
+                  ("pad", "<i4"), ("leaf0", "<i8")])
+JOB = np.dtype([("blk", "<i4"), ("tile", "<i2"), ("part", "<i2"), ("scr", "<i8"), ("boff", "<i8"),
+                ("eoff", "<i4"), ("flags", "<i4")])
+S = 6
+
+
+def dims(kind, K, n1, nh):
+    R, Q, N = {0: (K * K, K, 2 * nh), 1: (nh * K, 2 * K, 2 * n1), 2: (nh * n1, 2 * K, 2 * n1),
+               3: (nh * n1, 2 * n1, 2 * K), 4: (K * nh, 2 * n1, 2 * K), 5: (K * K, 2 * nh, K)}[kind]
+    P = -(-N // 80)
+    Nc = -(-N // P)
+    return R, Q, N, P, Nc, -(-Nc // 16) * 16, -(-Q // 16)
+
+
+def real_form(kind, blk, k, n1, nh, tab):
+    """The stage's 1D matrix as a real Q x N matrix: complex entries a + ib act on (re, im) pairs
+    as [[a, b], [-b, a]] (column c' of the output, row c of the input)."""
+    K = int(blk["K"])
+    axis = {0: 2, 1: 1, 2: 0, 3: 0, 4: 1, 5: 2}[kind]
+    mat = int(blk["mat"][axis])
+    R, Q, N, *_ = dims(kind, K, n1, nh)
+    B = np.zeros((Q, N))
+    if kind <= 2:
+        n = nh if kind == 0 else n1
+        T = tab["Fh"] if kind == 0 else tab["Ff"]
+        M = np.array([[T[((mat + J // k) * n + m) * k + J % k] for J in range(K)] for m in range(n)])  # [m][J]
+        if kind == 0:
+            B[:, 0::2], B[:, 1::2] = M.real.T, M.imag.T
+        else:
+            B[:K, 0::2], B[K:, 0::2], B[:K, 1::2], B[K:, 1::2] = M.real.T, -M.imag.T, M.imag.T, M.real.T
+    else:
+        n = nh if kind == 5 else n1
+        T = tab["Eh"] if kind == 5 else tab["Ef"]
+        M = np.array([[T[((mat + I // k) * k + I % k) * n + m] for m in range(n)] for I in range(K)])  # [I][m]
+        if kind == 3:
+            B[0::2, :K], B[1::2, :K], B[0::2, K:], B[1::2, K:] = M.real.T, -M.imag.T, M.imag.T, M.real.T
+        elif kind == 4:
+            B[:n1, :K], B[n1:, :K], B[:n1, K:], B[n1:, K:] = M.real.T, -M.imag.T, M.imag.T, M.real.T
+        else:
+            B[:nh], B[nh:] = M.real.T, -M.imag.T
+    return B
+
+
+def bf16_to_float(h):
+    return (h.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("name,k,delta,tol,bc", [("random", 4, 1e-3, 1e-10, 0), ("uniformp", 3, 1e-3, 1e-10, 1),
+                                                 ("random", 6, 1e-2, 1e-6, 0)])
+def test_sliced_digit_tables(name, k, delta, tol, bc):
+    tr = (W.uniform_tree(3, 3, periodic=True) if name == "uniformp"
+          else W.random_balanced_tree(3, 21, max_level=4, min_level=2, split_prob=0.25))
+    hp = F.HostPlan(3, k, delta, tol, tr.level, tr.coord, bc=bc, prec=F.PREC_FP64_TC)
+    info = hp.info()
+    n1, nh = info["modes_1d"], info["modes_half"]
+    assert info["n_sliced_jobs"] > 0
+    tab = {nm: hp.array(nm, np.complex128) for nm in ("Ff", "Fh", "Ef", "Eh")}
+    btab = hp.array("oz_btab", np.uint16)
+    bexp = hp.array("oz_bexp", np.int32)
+    blocks = {0: hp.array("blocks", BLOCK), 1: hp.array("eval_blocks", BLOCK)}
+    total = 0
+    for kind in range(6):
+        jobs = hp.array(f"oz_jobs{kind}", JOB)
+        blks = blocks[0 if kind < 3 else 1]
+        covered, checked = {}, set()
+        for j in jobs:
+            b = blks[j["blk"]]
+            K = int(b["K"])
+            R, Q, N, P, Nc, Np, nks = dims(kind, K, n1, nh)
+            assert 0 <= j["tile"] < -(-R // 128) and 0 <= j["part"] < P
+            covered.setdefault(int(j["blk"]), set()).add((int(j["tile"]), int(j["part"])))
+            if (int(j["boff"]), int(j["eoff"])) in checked:   # tiles of a block share its table
+                continue
+            checked.add((int(j["boff"]), int(j["eoff"])))
+            B = real_form(kind, b, k, n1, nh, tab)
+            Bp = np.zeros((nks * 16, Np))                     # this part's columns, padded
+            c = int(j["part"]) * Nc + np.arange(Np)
+            ok = (np.arange(Np) < Nc) & (c < N)
+            Bp[:Q, ok] = B[:, c[ok]]
+            f = bexp[j["eoff"]: j["eoff"] + Np].astype(np.int64)
+            q = np.arange(nks * 16)[:, None]
+            nl = np.arange(Np)[None, :]
+            ks, kk = q // 16, q % 16
+            off = (ks * S * Np * 16 + (nl >> 3) * 128 + (kk >> 3) * 64 + (nl & 7) * 8 + (kk & 7))   # plane 0
+            base = int(j["boff"]) // 2
+            d = np.stack([bf16_to_float(btab[base + off + s * Np * 16]) for s in range(S)])
+            assert np.all(d == np.round(d)) and np.all(np.abs(d) <= 128)
+            val = np.ldexp(np.tensordot(2.0 ** (-7 - 8 * np.arange(S)), d, axes=1), f[None, :])
+            assert np.all(np.abs(val - Bp) <= np.ldexp(1.0, f - 48)[None, :]), kind
+        for bi in range(len(blks)):
+            R, Q, N, P, *_ = dims(kind, int(blks[bi]["K"]), n1, nh)
+            assert covered.get(bi) == {(t, p) for t in range(-(-R // 128)) for p in range(P)}
+        total += len(jobs)
+    assert total == info["n_sliced_jobs"]
+    hp.close()
