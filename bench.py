@@ -57,7 +57,7 @@ WORKLOADS = {
 FORMS = {"split": ("split_tol1e-6", 1e-6, 1), "fp64": ("fp64_tol1e-6", 1e-6, 0),
          "fp64_1e-10": ("fp64_tol1e-10", 1e-10, 0), "fp64tc": ("fp64tc_tol1e-6", 1e-6, 2),
          "fp64tc_1e-10": ("fp64tc_tol1e-10", 1e-10, 2)}
-DEFAULT_FORMS = "fp64_1e-10,split,fp64,fp64tc_1e-10,fp64tc"
+DEFAULT_FORMS = "fp64tc_1e-10,fp64_1e-10,split,fp64,fp64tc"
 
 
 def workload(name="adaptive3d"):
@@ -518,7 +518,8 @@ def run_forms(args, F, torch, w, forms, flush, steps, warmup, world, local, cloc
                              ms_per_step=tot / steps, p50_ms=float(np.percentile(times, 50)),
                              p99_ms=float(np.percentile(times, 99)), steps=steps, cutoff_level=info["cutoff_level"],
                              n_f=info["n_f"], launches=info["launches"], tol=tol,
-                             dtype="f32" if prec == 1 else "f64", roofline=rl, tuning=tuned)
+                             dtype="f32" if prec == 1 else "f64", roofline=rl, tuning=tuned,
+                             arithmetic=arithmetic_of(prec, info))
     # the forms against the plain FP64 form at the same tolerance (the metric's comparison)
     for name, tol, prec in forms:
         base = "fp64_tol1e-10" if tol <= 1e-10 else "fp64_tol1e-6"
@@ -684,6 +685,19 @@ def run_point_fgt(F, torch):
             plan.close()
         out[name] = row
     return out
+
+
+def arithmetic_of(prec, info):
+    """What the form's contractions compute in (the dtype key names the expansions' type)."""
+    if prec == 1:
+        return "split: FP32 expansions, contractions as 3xTF32 tensor-core products (FP32-accurate); near field FP64"
+    if prec == 2 and info.get("n_sliced_jobs", 0) > 0:
+        return ("FP64 expansions; form and evaluation contractions as exact sums of BF16 digit products on the "
+                "tensor cores (operands rounded to 47 bits, six 8-bit digits each, FP32 accumulation exact, "
+                "64-bit integer recombination); gather and near field FP64")
+    if prec == 2:
+        return "FP64 throughout, some contractions on the FP64 tensor cores (DMMA)"
+    return "FP64 throughout (CUDA cores)"
 
 
 def metric_name(w, form="fp64_tol1e-10"):

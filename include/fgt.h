@@ -143,7 +143,8 @@ fgt_status fgt_plan_create_host(int d, double delta, double tol, double eps_pw, 
                                 const fgt_tree *tree, fgt_plan **out);
 
 /* Borrow a host-only plan's array by name ("blocks", "block_leaves", "Ff", "Fh", "Ef", "Eh",
- * "gather_dst", "gather_ptr", "gather_src", "Pf", "Ph", "near_tgt", "near_flags", "near_ptr",
+ * "gather_dst", "gather_ptr", "gather_src", "gather_segs", "gather_grid", "Pf", "Ph", "near_tgt",
+ * "near_flags", "near_ptr",
  * "near_src", "near_tab", "merge<i>_items|qf|qh", "push<i>_items|qf|qh", and for the sliced FP64
  * tensor-core stages "oz_jobs<kind>", "oz_btab", "oz_bexp", "eval_blocks").  The pointer stays
  * valid until the plan is destroyed or re-planned.  FGT_ERR_STATE for device plans. */

@@ -87,12 +87,16 @@ struct ExecDesc {
   // FP64-accurate form and evaluation on the BF16 tensor cores (precision FP64_TC, 3D, fused mode):
   // six contraction stages (form: x3, x2, x1; evaluation: m1, m2, m3), one launch each over its
   // jobs, every operand cut into six 8-bit slices with exact FP32 accumulation of the slice products
-  // (oz_stage_kernel).  The stages pass their FP64 intermediates through oz_x / oz_y; without them
+  // (oz_slice_kernel + oz_mma_kernel).  The stages pass their FP64 intermediates through oz_x / oz_y; without them
   // (the allocation-free call) the FP64 kernels of the block lists above run instead.
   int oz = 0;
   int oz_sole = 0;                      // every form block stores its anchor's slot (no clear of phi)
-  const OzJob *oz_jobs[6] = {};
+  const OzJob *oz_jobs[6] = {};           // products: (block, tile, part)
   int64_t oz_njobs[6] = {};
+  const OzJob *oz_sjobs[6] = {};          // slicing: (block, tile)
+  int64_t oz_nsjobs[6] = {};
+  unsigned char *oz_dig = nullptr;        // the current stage's operand digit planes
+  int *oz_rexp = nullptr;                 // and its row exponents
   const unsigned char *oz_btab = nullptr;  // the sliced 1D matrices (BF16 digit planes)
   const int32_t *oz_bexp = nullptr;        // their column exponents
   const Block *eval_blocks = nullptr;      // the evaluation's blocks (the jobs of stages 3-5 index them)
@@ -106,6 +110,11 @@ struct ExecDesc {
   const void *Pf = nullptr, *Ph = nullptr;   // [3][n1], [3][nh]
   const GatherSeg *gather_segs = nullptr;    // separable form of the same gather
   int64_t n_gather_segs = 0;
+  int seg_w = 0;                             // target boxes per run (min(kSegW, boxes a side at l_c))
+  // every box of the cutoff level an anchor (3D, 4 or 8 boxes a side): the stencil form of the gather
+  // over the grid, gather_grid[(x3 nb + x2) nb + x1] = slot of box (x1, x2, x3); grid_nb = 0: not used
+  int grid_nb = 0, grid_periodic = 0;
+  const int32_t *gather_grid = nullptr;
 
   // hierarchical mode (empty in fused mode); merge in execution order (fine -> coarse)
   std::vector<ShiftStep> merge, push;
@@ -171,7 +180,7 @@ cudaError_t selftest_batch_timeout(int *status);
 // side: R rows, Q contraction length, N columns, split into P parts of Nc (padded to Np) columns,
 // nks k-steps of 16.
 constexpr int kOzSlices = 6;
-constexpr int kOzMaxNp = 80;
+constexpr int kOzMaxNp = 32;  // columns per part: 6 accumulators x 32 TMEM columns, two CTAs an SM
 struct OzDims { int R, Q, N, P, Nc, Np, nks; };
 inline __host__ __device__ OzDims oz_dims(int kind, int K, int n1, int nh) {
   OzDims d{};

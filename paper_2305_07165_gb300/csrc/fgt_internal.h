@@ -23,15 +23,19 @@ struct Block {
 };
 
 // One CTA of an FP64-accurate tensor-core contraction stage (the sliced form and evaluation):
-// row tile `tile` (128 rows) and column part `part` of block `blk`'s stage matrix product.
+// row tile `tile` (128 rows) and column part `part` of block `blk`'s stage matrix product (the
+// slicing of the operand takes one CTA per (block, tile): the same struct with part 0).
 struct OzJob {
   int32_t blk;       // index into the plan's blocks
   int16_t tile;      // 128-row tile of the stage's rows
-  int16_t part;      // column part (at most 80 columns each)
+  int16_t part;      // column part (at most 32 columns each)
   int64_t scr;       // offset (doubles) of the block's intermediates in the two scratch arrays
-  int64_t boff;      // byte offset of the block's sliced 1D matrix for this stage
-  int32_t eoff;      // offset of its column exponents
+  int64_t boff;      // byte offset of the block's sliced 1D matrix for this stage (this part)
+  int64_t aoff;      // byte offset of the tile's sliced operand (digit planes) in the digit array
+  int32_t eoff;      // offset of the 1D matrix's column exponents (this part)
+  int32_t roff;      // offset of the tile's 128 row exponents
   int32_t flags;     // bit 0: add into the output (another block writes the same slot / leaf)
+  int32_t pad;
 };
 
 // One out->in translation source at the cutoff level.

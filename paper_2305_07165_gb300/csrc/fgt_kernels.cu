@@ -742,6 +742,66 @@ __device__ __forceinline__ double f32_to_f64_int(uint32_t b) {
   return __hiloint2double((int)(s | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
 }
 
+// ---- double-float arithmetic: a value as the unevaluated sum hi + lo of two FP32 numbers (about
+// 48 significant bits), on GB300's FP32 pipes (64 times the FP64 rate).  The error-free sum of
+// Knuth and the FMA product error (the exact a*b - RN(a*b)) give a fused multiply-add whose error
+// is about 2^-47 of its terms; conversions to and from FP64 use integer operations only.
+struct dfl {
+  float hi, lo;
+};
+
+// x rounded to 24 bits (hi) and the rest (lo, rounded to 24 bits: |lo| <= 2^-24 |hi|); zero when
+// |x| < 2^-126 (subnormal FP32 range), lo zero when it would be.
+__device__ __forceinline__ dfl dfl_from_f64(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e - 896 <= 0 || e - 896 >= 255) return dfl{0.f, 0.f};
+  const unsigned s = (unsigned)(b >> 63) << 31;
+  const long long m = (long long)((b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52));  // x = m 2^(e - 1075)
+  const long long mh = (m + (1LL << 28)) >> 29;                              // 24 bits, or 2^24 on a carry
+  const int r = (int)(m - (mh << 29));                                       // |r| <= 2^28
+  // mh - 2^23 is the mantissa field; a carry (mh = 2^24) moves into the exponent
+  const float h = __uint_as_float((s | ((unsigned)(e - 896) << 23)) + (unsigned)(mh - (1LL << 23)));
+  float lo = 0.f;
+  if (e - 948 >= 1 && r != 0) {
+    const float sc = __uint_as_float((unsigned)(e - 948) << 23);  // 2^(e - 1075)
+    lo = (float)r * sc;
+    if (s) lo = -lo;
+  }
+  return dfl{h, lo};
+}
+
+// hi + lo rounded to FP64 (integer operations).
+__device__ __forceinline__ double dfl_to_f64(dfl a) {
+  const uint32_t bh = __float_as_uint(a.hi), bl = __float_as_uint(a.lo);
+  const int eh = (int)((bh >> 23) & 0xFF), el = (int)((bl >> 23) & 0xFF);
+  if (eh == 0) return f32_to_f64_int(bl);
+  long long Mh = (long long)((bh & 0x7FFFFF) | 0x800000);
+  if (bh >> 31) Mh = -Mh;
+  long long V = Mh << 29;  // value = V 2^(eh - 150 - 29)
+  if (el != 0) {
+    long long Ml = (long long)((bl & 0x7FFFFF) | 0x800000);
+    if (bl >> 31) Ml = -Ml;
+    const int d = eh - el;  // lo's units below hi's
+    if (d <= 29) V += Ml << (29 - d);
+    else if (d < 29 + 26) V += (Ml + (1LL << (d - 30))) >> (d - 29);
+  }
+  return i64_to_f64_scaled(V, eh - 150 - 29);
+}
+
+// a b + c in double-float
+__device__ __forceinline__ dfl dfl_fma(dfl a, dfl b, dfl c) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const float sm = p + c.hi, bb = sm - p;
+  float t = (p - (sm - bb)) + (c.hi - bb);
+  t += e + c.lo;
+  const float hi = sm + t;
+  return dfl{hi, t - (hi - sm)};
+}
+
 __device__ __forceinline__ void sigma_pack_body(const Block *__restrict__ blocks,
                                                          const int32_t *__restrict__ pack_block,
                                                          const int64_t *__restrict__ bleaves,
@@ -2860,8 +2920,8 @@ __global__ void __launch_bounds__(256) gather_kernel(const int32_t *__restrict__
 // 3^(d-1) neighbouring lines (o_2, o_3) is taken first, position by position along the run
 // (w_i = sum_lines P_2(o_2) P_3(o_3) phi[line][i], each of the W + 2 sources loaded once), and the
 // x_1 factor last, as a 3-point stencil over w: 9 (W + 2) + 3 W complex products per run in 3D,
-// against 27 + 9 + 3 per target for gather_kernel.  Used in split precision (FP32); the FP64
-// expansions keep gather_kernel, which measured faster there (fewer registers per mode).
+// against 27 + 9 + 3 per target for gather_kernel.  The default in every precision (W = 4 when the
+// cutoff level has at most 4 boxes a side); FP64 plans built with FGT_GATHER2=0 keep gather_kernel.
 template <int D, typename R, int W>
 __device__ __forceinline__ void gather2_body(const GatherSeg *__restrict__ segs,
                                                       const typename C2T<R>::T *__restrict__ Pf,
@@ -2936,6 +2996,112 @@ __global__ void __launch_bounds__(256) gather2_kernel(const GatherSeg *__restric
                                                       int64_t slot_size, int psi_pitch) {
   gather2_body<D, R, W>(segs, Pf, Ph, phi, psi, n1, nh, slot_size, psi_pitch, blockIdx.x, blockIdx.y);
 }
+
+// The same gather for FP64 expansions when every box of the cutoff level is an anchor (3D, NB = 4
+// or 8 boxes a side): the phase is a product of one factor per axis and the sources of a target are
+// its 3^3 neighbours on the grid, so the sum is a separable 3-point stencil per mode, applied axis by
+// axis -- 3 + 3 + 3 complex products per mode and box instead of 27 + 9 + 3 (gather_kernel) or about
+// 16 (gather2).  A CTA holds MT consecutive modes of the whole grid in shared memory (ping-pong
+// buffers), loads them once (MT contiguous values a slot), runs the three passes (neighbours wrapped
+// when periodic, absent in free space) and writes psi once; each thread keeps one mode's nine phase
+// factors.  DF (the FP64-TC plans): the products in double-float arithmetic on the FP32 pipes
+// (about 2^-47 per operation, far inside the FP64 tolerances), the expansions and phases split into
+// FP32 pairs on load and rounded back to FP64 on store with integer operations; otherwise FP64
+// arithmetic (FP64-pipe bound).
+template <int NB, int MT, bool DF>
+__global__ void __launch_bounds__(256) gather3_kernel(const int32_t *__restrict__ gslot, const double2 *__restrict__ Pf,
+                                                      const double2 *__restrict__ Ph, const double2 *__restrict__ phi,
+                                                      double2 *__restrict__ psi, int n1, int nh, int64_t slot_size,
+                                                      int periodic) {
+  static_assert(256 % MT == 0, "modes per CTA must divide the block");
+  constexpr int NBOX = NB * NB * NB, BSTEP = 256 / MT;
+  extern __shared__ __align__(16) unsigned char g3_raw[];
+  // [2][NBOX][MT]: DF (re.hi, re.lo, im.hi, im.lo) as float4, else the double2 itself
+  float4 *buf = reinterpret_cast<float4 *>(g3_raw);
+  double2 *bufd = reinterpret_cast<double2 *>(g3_raw);
+  const int j = threadIdx.x % MT, b0 = threadIdx.x / MT;
+  const int64_t m = (int64_t)blockIdx.x * MT + j;
+  const bool live = m < slot_size;
+  int m1 = 0, m2 = 0, m3 = 0;
+  mode_index<3>(live ? m : 0, n1, m1, m2, m3);
+  double2 P[3][3];  // [axis][o + 1]
+#pragma unroll
+  for (int o = 0; o < 3; ++o) {
+    P[0][o] = Pf[o * n1 + m1];
+    P[1][o] = Pf[o * n1 + m2];
+    P[2][o] = Ph[o * nh + m3];
+  }
+  dfl pr[3][3], pi[3][3];
+  if constexpr (DF) {
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+      for (int o = 0; o < 3; ++o) {
+        pr[ax][o] = dfl_from_f64(P[ax][o].x);
+        pi[ax][o] = dfl_from_f64(P[ax][o].y);
+      }
+  }
+  for (int b = b0; b < NBOX; b += BSTEP) {
+    const double2 x = live ? phi[(int64_t)__ldg(gslot + b) * slot_size + m] : make_double2(0.0, 0.0);
+    if constexpr (DF) {
+      const dfl re = dfl_from_f64(x.x), im = dfl_from_f64(x.y);
+      buf[b * MT + j] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    } else {
+      bufd[b * MT + j] = x;
+    }
+  }
+  __syncthreads();
+  int cur = 0;
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const int stride = ax == 0 ? 1 : ax == 1 ? NB : NB * NB;
+    const int ib = cur * NBOX * MT, ob = (1 - cur) * NBOX * MT;
+    for (int b = b0; b < NBOX; b += BSTEP) {
+      const int x = (b / stride) % NB;
+      dfl ar{0.f, 0.f}, ai{0.f, 0.f};
+      double dr = 0.0, di = 0.0;
+#pragma unroll
+      for (int o = -1; o <= 1; ++o) {
+        int xs = x + o;
+        if (xs < 0 || xs >= NB) {
+          if (!periodic) continue;
+          xs = (xs + NB) % NB;
+        }
+        const int src = ib + (b + (xs - x) * stride) * MT + j;
+        if constexpr (DF) {
+          const float4 v = buf[src];
+          const dfl vr{v.x, v.y}, vi{v.z, v.w}, qr = pr[ax][o + 1], qi = pi[ax][o + 1];
+          const dfl nqi{-qi.hi, -qi.lo};
+          ar = dfl_fma(qr, vr, ar);  // (qr + i qi)(vr + i vi)
+          ar = dfl_fma(nqi, vi, ar);
+          ai = dfl_fma(qr, vi, ai);
+          ai = dfl_fma(qi, vr, ai);
+        } else {
+          cfma(dr, di, P[ax][o + 1], bufd[src]);
+        }
+      }
+      if constexpr (DF) buf[ob + b * MT + j] = make_float4(ar.hi, ar.lo, ai.hi, ai.lo);
+      else bufd[ob + b * MT + j] = make_double2(dr, di);
+    }
+    __syncthreads();
+    cur = 1 - cur;
+  }
+  if (!live) return;
+  for (int b = b0; b < NBOX; b += BSTEP) {
+    const int src = cur * NBOX * MT + b * MT + j;
+    double2 *o = psi + (int64_t)__ldg(gslot + b) * slot_size + m;
+    double2 r;
+    if constexpr (DF) {
+      const float4 v = buf[src];
+      r = make_double2(dfl_to_f64(dfl{v.x, v.y}), dfl_to_f64(dfl{v.z, v.w}));
+    } else {
+      r = bufd[src];
+    }
+    if (FGT_OK_PTR(o)) *o = r;
+  }
+}
+
+constexpr int gather3_mt(int nb) { return nb == 4 ? 16 : 4; }
 
 // phi[parent] = sum_children T_c->p(child) phi[child]
 template <int D, typename R>
@@ -3385,8 +3551,24 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
   mark(2, 0);
   const C *eval_src = phi;
   if (!e.fourier && e.n_gather > 0) {
-    if (e.n_gather_segs > 0) {
-      gather2_kernel<D, R, kSegW><<<dim3((unsigned)e.n_gather_segs, tiles), 256, 0, st>>>(
+    if (D == 3 && sizeof(R) == 8 && (e.grid_nb == 4 || e.grid_nb == 8) && e.gather_grid != nullptr &&
+        e.psi_pitch == 0) {
+      // FP64, every box of the cutoff level an anchor: the stencil form, axis by axis
+      const int nb = e.grid_nb, mt = gather3_mt(nb);
+      // FP64-TC plans: double-float products; FP64 plans: FP64 products
+      auto g3 = e.tc64 ? (nb == 4 ? gather3_kernel<4, gather3_mt(4), true> : gather3_kernel<8, gather3_mt(8), true>)
+                       : (nb == 4 ? gather3_kernel<4, gather3_mt(4), false> : gather3_kernel<8, gather3_mt(8), false>);
+      const size_t gsm = 2 * sizeof(float4) * (size_t)nb * nb * nb * mt;
+      if ((err = cudaFuncSetAttribute(g3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm)) != cudaSuccess)
+        return err;
+      g3<<<(unsigned)((ss + mt - 1) / mt), 256, gsm, st>>>(
+          e.gather_grid, reinterpret_cast<const double2 *>(e.Pf), reinterpret_cast<const double2 *>(e.Ph),
+          reinterpret_cast<const double2 *>(phi), reinterpret_cast<double2 *>(psi), n1, nh, ss, e.grid_periodic);
+    } else if (e.n_gather_segs > 0) {
+      // runs of at most 4 targets (4 boxes a side at the cutoff level): the 4-wide kernel, which
+      // does not spend products on the empty positions of an 8-wide run
+      auto g2 = (e.seg_w > 0 && e.seg_w <= 4) ? gather2_kernel<D, R, 4> : gather2_kernel<D, R, kSegW>;
+      g2<<<dim3((unsigned)e.n_gather_segs, tiles), 256, 0, st>>>(
           e.gather_segs, reinterpret_cast<const C *>(e.Pf), reinterpret_cast<const C *>(e.Ph), phi, psi, n1, nh, ss,
           e.psi_pitch);
     } else {
@@ -3536,7 +3718,7 @@ int launches_per_transform(const ExecDesc &e) {
   n += (e.d == 3 && e.prec == 1 && e.n_pack > 0);  // sigma packing
   n += (e.d == 3 && e.prec == 1 && e.n_psi_tc_slots > 0);  // tcgen05 operand copy of the expansions
   if (e.d == 3 && e.prec == 0 && e.oz) {  // sliced FP64 tensor-core stages
-    for (int kind = 0; kind < 6; ++kind) n += e.oz_njobs[kind] > 0;
+    for (int kind = 0; kind < 6; ++kind) n += 2 * (e.oz_njobs[kind] > 0);  // slicing + products
   } else {
     n += (e.n_f1 > 0) + (int)e.f2_ranges.size() + (e.n_e1 > 0) + (int)e.e2_ranges.size();  // form + evaluate
   }
@@ -3559,7 +3741,8 @@ int launches_per_transform(const ExecDesc &e) {
 // status word and the item is skipped (its result is then wrong, and the status says so), so
 // nothing can hang.  Phases: 0 clear u / phi, 1 pack the FP32 density, 2 form, 3 gather,
 // 4 evaluation, 5 near field (needs phase 0 only).  The items use the CUDA-core kernels (the tcgen05
-// ranges of a plan take their CUDA-core fallbacks) and the plain expansion layout.
+// ranges of a plan take their CUDA-core fallbacks), the plain expansion layout and, for FP64 plans,
+// the per-anchor gather (the run form's registers would lower the persistent kernel's occupancy).
 struct BatchDesc {
   int d, k, n1, nh, f32, Kmax_f1;
   int64_t ss, n_points, phi_elems;
@@ -3826,8 +4009,7 @@ const char *queue_transform(const ExecDesc &e, int t, std::vector<BatchItem> (&p
     }
   }
   if (!e.fourier && e.n_gather > 0) {
-    if (e.n_gather_segs > 0) {
-      if (!f32) return "gather runs in FP64";
+    if (e.n_gather_segs > 0 && f32) {
       add(3, BK_GATHER2, 0, 0, (int)e.n_gather_segs, (int)((ss + 255) / 256), 0);
     } else {
       add(3, BK_GATHER, 0, 0, (int)e.n_gather, (int)((ss + 256 * kGatherMpt - 1) / (256 * kGatherMpt)), 0);

@@ -16,16 +16,23 @@
 //   - C[r][n] = 2^(e_r + f_n - 14) sum_D 2^(-8 D) P_D is recombined in a 64-bit integer and
 //     rounded to FP64 once.
 // The products dropped (s + t >= 6) and the two 47-bit roundings bound the error of C[r][n] by
-// about 2^-46 sum_q |A[r][q]| |B[q][n]| -- FP64 quality for a contraction, and 21 BF16 MMAs per
-// 16-deep step where a 3xTF32 product needs 3.
+// about 2^-46 sum_q |A[r][q]| |B[q][n]| -- FP64 quality for a contraction, for 21 BF16 products per
+// FP64 product where a 3xTF32 product needs 3 TF32 ones.
 //
 // Each stage is one contraction of the block's separable product (form: x3, x2, x1; evaluation:
-// m1, m2, m3, the last one keeping the real part), one launch over (block, 128-row tile, column
-// part) jobs.  A CTA streams its rows' FP64 operand through four pipeline stages: sixteen warps
-// read and slice 128 x 16 tiles into shared memory (the K-major no-swizzle operand layout), one
-// thread copies the pre-sliced 1D matrix of each 16-deep step with bulk asynchronous copies and
-// issues the MMAs; the epilogue reads the six accumulators, recombines and writes FP64 in the
-// layout the next stage reads (rows fastest, so that the warp's stores are contiguous).
+// m1, m2, m3, the last one keeping the real part) and takes two launches:
+//   - oz_slice_kernel, one CTA per (block, 128-row tile): the rows' exponents and the operand's six
+//     digit planes per 16-deep step, written once (a tile's columns are split into parts, and every
+//     part reads the same planes) in the tensor cores' K-major core-matrix layout;
+//   - oz_mma_kernel, persistent, one CTA per SM over the (block, tile, column part of <= 32 columns)
+//     jobs: a copy warp streams the tile's digit planes and the 1D matrix's of each step with bulk
+//     asynchronous copies into a 4-stage ring; an MMA warp issues 6 MMAs a step -- A's digit plane s
+//     against B's planes 0 .. 5 - s, stored one after another along N, in one MMA of N = (6 - s) 32
+//     into accumulators s .. 5 -- so each A plane is read once a step (21 separate MMAs would read it
+//     21 times), into one of two accumulator sets; sixteen warps drain the other set (recombine,
+//     write FP64 in the layout the next stage's slicing reads, rows fastest), so a job's epilogue
+//     runs beside the next job's products.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,17 +48,16 @@ __device__ int g_oz_status;  // 1: a wait ran out (the CTA skipped its outputs),
 namespace {
 
 constexpr int kNst = 4;                          // pipeline stages (16-deep steps in flight)
-constexpr int kWarps = 16;                       // slicing / epilogue warps; one more issues copies + MMAs
-constexpr int kThreads = (kWarps + 1) * 32;
+constexpr int kWarps = 16;                       // slicing / epilogue warps; two more copy and issue MMAs
+constexpr int kThreads = (kWarps + 2) * 32;
 constexpr uint32_t kAPlane = 128 * 16 * 2;       // one digit plane of a 128 x 16 A tile (BF16)
 constexpr uint32_t kAStage = kOzSlices * kAPlane;
 constexpr uint32_t kBStage = kOzSlices * kOzMaxNp * 32;
-constexpr uint32_t kTmemCols = 512;              // 6 accumulators x Np <= 480 columns
-constexpr size_t kSmemBytes =
-    (size_t)kNst * (kAStage + kBStage) + 128 * sizeof(int) + kOzMaxNp * sizeof(int) + (3 * kNst + 1) * 8 + 16;
+constexpr uint32_t kAccCols = 256;               // one accumulator set: 6 x Np <= 192 columns
+constexpr uint32_t kTmemCols = 2 * kAccCols;     // two sets: one job's epilogue beside the next one's MMAs
+constexpr size_t kSmemBytes = (size_t)kNst * (kAStage + kBStage) + (2 * kNst + 4) * 8 + 16;
 
 struct OzArgs {
-  const OzJob *jobs;
   const Block *blocks;
   const int64_t *leaves;
   const double *src;
@@ -84,10 +90,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 // Biased exponent field of x (0 for zero and subnormal values, which slice to zero).
 __device__ __forceinline__ int exp_field(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
 
-// The six digits of x against its row's largest biased exponent ebr, as BF16 bit patterns:
-// n = round(x 2^(47 - e_r)), e_r = ebr - 1022 (so |n| <= 2^47), n = sum_s d_s 2^(8 (5 - s)) with
-// balanced digits.  Integer arithmetic only: GB300's FP64 conversions run on the narrow FP64 pipe.
-__device__ __forceinline__ void slice6(double x, int ebr, uint32_t (&h)[kOzSlices]) {
+// The six digits of x against its row's largest biased exponent ebr: n = round(x 2^(47 - e_r)),
+// e_r = ebr - 1022 (so |n| <= 2^47), n = sum_s d_s 2^(8 (5 - s)) with |d_s| <= 128.  Integer
+// arithmetic only (GB300's FP64 conversions run on the narrow FP64 pipe), and 32-bit after one split:
+// n = H 2^24 + L with L the sign-extended low 24 bits, then three balanced base-256 digits of each
+// half (the top digit of each absorbs the last carry: |L| <= 2^23 and |H| <= 2^23 + 1 keep it
+// within +-128).
+__device__ __forceinline__ void slice6(double x, int ebr, int (&dg)[kOzSlices]) {
   const long long b = __double_as_longlong(x);
   const int eb = (int)((b >> 52) & 0x7FF);
   const int sh = ebr - eb + 6;  // >= 6: ebr is the row's largest
@@ -97,37 +106,25 @@ __device__ __forceinline__ void slice6(double x, int ebr, uint32_t (&h)[kOzSlice
     n = (m + (1LL << (sh - 1))) >> sh;
     if (b < 0) n = -n;
   }
-  int dg[kOzSlices];
-#pragma unroll
-  for (int s = kOzSlices - 1; s >= 1; --s) {
-    const int lo = (((int)n + 128) & 255) - 128;  // balanced digit of n mod 256
-    dg[s] = lo;
-    n = (n - lo) >> 8;
-  }
-  dg[0] = (int)n;
-#pragma unroll
-  for (int s = 0; s < kOzSlices; ++s)  // small integer -> FP32 (exact) -> its upper half, the BF16
-    h[s] = __float_as_uint(__int_as_float(0x4B400000 + dg[s]) - 12582912.0f) >> 16;
+  int L = (int)((unsigned)n << 8) >> 8;
+  int H = (int)((n - L) >> 24);
+  dg[5] = (int)(signed char)L;
+  L = (L - dg[5]) >> 8;
+  dg[4] = (int)(signed char)L;
+  dg[3] = (L - dg[4]) >> 8;
+  dg[2] = (int)(signed char)H;
+  H = (H - dg[2]) >> 8;
+  dg[1] = (int)(signed char)H;
+  dg[0] = (H - dg[1]) >> 8;
 }
 
-// v 2^sc rounded to FP64 (nearest, ties to even), with integer operations.
-__device__ __forceinline__ double i64_to_f64_scaled(long long v, int sc) {
-  if (v == 0) return 0.0;
-  const unsigned long long sg = v < 0 ? (1ULL << 63) : 0ULL;
-  unsigned long long a = v < 0 ? 0ULL - (unsigned long long)v : (unsigned long long)v;
-  const int lz = __clzll((long long)a);
-  a <<= lz;
-  unsigned long long m = a >> 11;
-  const unsigned rem = (unsigned)(a & 0x7FF);
-  if (rem > 0x400u || (rem == 0x400u && (m & 1ULL))) ++m;
-  int E = 1023 + 63 - lz + sc;
-  if (m >> 53) {
-    m >>= 1;
-    ++E;
-  }
-  if (E <= 0) return __longlong_as_double((long long)sg);
-  if (E >= 2047) return __longlong_as_double((long long)(sg | 0x7FF0000000000000ULL));
-  return __longlong_as_double((long long)(sg | ((unsigned long long)E << 52) | (m & 0xFFFFFFFFFFFFFULL)));
+// Two digits (|d| <= 128) as a BF16 pair, d0 in the low half: small integer -> FP32 (exact, by the
+// 1.5 2^23 offset) -> BF16 (exact: at most 8 significant bits).
+__device__ __forceinline__ uint32_t bf16_pair(int d0, int d1) {
+  const float f0 = __int_as_float(0x4B400000 + d0) - 12582912.0f;
+  const float f1 = __int_as_float(0x4B400000 + d1) - 12582912.0f;
+  const __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
+  return *reinterpret_cast<const uint32_t *>(&h);
 }
 
 // Stage layouts (block of K nodes a side, leaves of k nodes, nl = K / k leaves a side):
@@ -213,36 +210,94 @@ __device__ __forceinline__ void store_out(int r, int n, double v, const OzJob &j
   }
 }
 
+// Slicing: one CTA per (block, 128-row tile).  Sixteen warps, 8 rows each, 4 lanes a row; every
+// thread finds its row's largest exponent (with its 3 partner lanes), then cuts its elements into
+// the six digit planes of each 16-deep step, in the tensor cores' K-major core-matrix layout
+// (conflict-free, coalesced 4-byte stores: a warp writes one 128-byte core-matrix row set).
 template <int KIND>
-__global__ void __launch_bounds__(kThreads, 1) oz_stage_kernel(const OzArgs a) {
-  extern __shared__ __align__(1024) unsigned char sm_oz[];
-  unsigned char *sA = sm_oz;
-  unsigned char *sB = sm_oz + kNst * kAStage;
-  int *rowexp = reinterpret_cast<int *>(sB + kNst * kBStage);
-  int *colexp = rowexp + 128;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(colexp + kOzMaxNp);
-  uint64_t *afull = bars, *bfull = bars + kNst, *empty = bars + 2 * kNst, *done = bars + 3 * kNst;
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
-
-  const OzJob job = a.jobs[blockIdx.x];
+__global__ void __launch_bounds__(kWarps * 32) oz_slice_kernel(const OzArgs a, const OzJob *__restrict__ sjobs,
+                                                               unsigned char *__restrict__ dig,
+                                                               int *__restrict__ rexp) {
+  const OzJob job = sjobs[blockIdx.x];
   const Block blk = a.blocks[job.blk];
   const OzDims dm = oz_dims(KIND, blk.K, a.n1, a.nh);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t *lv = a.leaves + blk.leaf0;
-  const int r0 = (int)job.tile * 128;
-  const int c0 = (int)job.part * dm.Nc;
-  const int ncol = min(dm.Nc, dm.N - c0);
-  const int Np = dm.Np;
-  const uint32_t bbytes = (uint32_t)(kOzSlices * Np * 32);
+  const int rl = 8 * warp + (lane >> 2), sub = lane & 3;
+  const int rg = (int)job.tile * 128 + rl;
+  const bool rvalid = rg < dm.R;
+  const RowAddr ra = row_addr<KIND>(rvalid ? rg : 0, job, blk, a);
+  int ebr = 0;
+  if (rvalid)
+    for (int q = 2 * sub; q < dm.Q; q += 8) {
+      ebr = max(ebr, exp_field(__ldg(a.src + a_index<KIND>(ra, q, lv, blk, a))));
+      if (q + 1 < dm.Q) ebr = max(ebr, exp_field(__ldg(a.src + a_index<KIND>(ra, q + 1, lv, blk, a))));
+    }
+  ebr = max(ebr, __shfl_xor_sync(0xffffffffu, ebr, 1));
+  ebr = max(ebr, __shfl_xor_sync(0xffffffffu, ebr, 2));
+  if (sub == 0) rexp[job.roff + rl] = ebr;
+  unsigned char *out = dig + job.aoff;
+  const uint32_t off0 = (uint32_t)(rl >> 3) * 256u + (uint32_t)(rl & 7) * 16u + (uint32_t)sub * 4u;
+#pragma unroll 2
+  for (int ks = 0; ks < dm.nks; ++ks) {
+#pragma unroll
+    for (int kg = 0; kg < 2; ++kg) {
+      const int q = ks * 16 + kg * 8 + 2 * sub;
+      const double x0 = (rvalid && q < dm.Q) ? __ldg(a.src + a_index<KIND>(ra, q, lv, blk, a)) : 0.0;
+      const double x1 = (rvalid && q + 1 < dm.Q) ? __ldg(a.src + a_index<KIND>(ra, q + 1, lv, blk, a)) : 0.0;
+      int g0[kOzSlices], g1[kOzSlices];
+      slice6(x0, ebr, g0);
+      slice6(x1, ebr, g1);
+      unsigned char *o = out + (size_t)ks * kAStage + off0 + (uint32_t)kg * 128u;
+#pragma unroll
+      for (int sl = 0; sl < kOzSlices; ++sl) *reinterpret_cast<uint32_t *>(o + sl * kAPlane) = bf16_pair(g0[sl], g1[sl]);
+    }
+  }
+}
+
+// Bounded wait for a phase that other warps complete: like mbar_wait, but each try may suspend the
+// thread for up to about 0.1 ms, so that waiting warps do not take issue slots from working ones.
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t mbar, uint32_t parity, long long limit = 1LL << 31) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity), "r"(100000u)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > limit) return false;
+  }
+}
+
+// Products: a persistent kernel, one CTA per SM over the stage's (block, tile, column part) jobs
+// (job j = blockIdx.x + i gridDim.x).  Warp 16 copies the digit planes of every step of every job
+// into a 4-stage ring (bulk copies, complete_tx on the stage's `full` barrier), warp 17 issues the
+// MMAs into one of two accumulator sets in tensor memory (job i in set i mod 2), and sixteen warps
+// drain the other set meanwhile: the epilogue of one job overlaps the products of the next.
+template <int KIND>
+__global__ void __launch_bounds__(kThreads, 1) oz_mma_kernel(const OzArgs a, const OzJob *__restrict__ jobs,
+                                                              int64_t njobs, const unsigned char *__restrict__ dig,
+                                                              const int *__restrict__ rexp) {
+  extern __shared__ __align__(1024) unsigned char sm_oz[];
+  unsigned char *sA = sm_oz;
+  unsigned char *sB = sm_oz + kNst * kAStage;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sB + kNst * kBStage);
+  uint64_t *full = bars, *empty = bars + kNst, *tfull = bars + 2 * kNst, *tempty = tfull + 2;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(tempty + 2);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == kWarps * 32) {
     for (int i = 0; i < kNst; ++i) {
-      mbar_init(afull + i, kWarps);
-      mbar_init(bfull + i, 1);
+      mbar_init(full + i, 2);  // the two bulk copies' expect_tx arrivals
       mbar_init(empty + i, 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull + b, 1);        // the MMAs of a job, committed
+      mbar_init(tempty + b, kWarps);  // every epilogue warp done reading the set
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *abort_flag = 0;
   }
@@ -251,128 +306,106 @@ __global__ void __launch_bounds__(kThreads, 1) oz_stage_kernel(const OzArgs a) {
                  "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  for (int i = threadIdx.x; i < kOzMaxNp; i += blockDim.x) colexp[i] = i < ncol ? __ldg(a.bexp + job.eoff + i) : 0;
-
-  // this thread's row for the operand pass: 8 rows a warp, 4 lanes a row (q = 8 i + 2 sub + {0, 1})
-  const int rl = 8 * (warp & (kWarps - 1)) + (lane >> 2), sub = lane & 3;
-  const int rg = r0 + rl;
-  const bool rvalid = warp < kWarps && rg < dm.R;
-  const RowAddr ra = row_addr<KIND>(rvalid ? rg : 0, job, blk, a);
-  int ebr = 0;
-  if (warp < kWarps) {
-    if (rvalid)
-      for (int q = 2 * sub; q < dm.Q; q += 8) {
-        ebr = max(ebr, exp_field(__ldg(a.src + a_index<KIND>(ra, q, lv, blk, a))));
-        if (q + 1 < dm.Q) ebr = max(ebr, exp_field(__ldg(a.src + a_index<KIND>(ra, q + 1, lv, blk, a))));
-      }
-    ebr = max(ebr, __shfl_xor_sync(0xffffffffu, ebr, 1));
-    ebr = max(ebr, __shfl_xor_sync(0xffffffffu, ebr, 2));
-    if (sub == 0) rowexp[rl] = ebr;
-  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tslot;
+  const int nmine = njobs > blockIdx.x ? (int)((njobs - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
 
-  if (warp < kWarps) {
-    // ---- slicing: the rows' 16-deep steps into the digit planes of the ring
-    for (int ks = 0; ks < dm.nks; ++ks) {
-      const int st = ks % kNst;
-      int ok = 1;
-      if (lane == 0) {
-        if (ks >= kNst) ok = mbar_wait(smem_addr(empty + st), (uint32_t)((ks / kNst - 1) & 1)) ? 1 : 0;
+  if (warp == kWarps) {
+    // ---- copies: every step of every job, in order, through the ring
+    if (lane == 0) {
+      int g = 0;  // steps issued so far (all jobs)
+      for (int li = 0; li < nmine && !*abort_flag; ++li) {
+        const OzJob job = jobs[blockIdx.x + (int64_t)li * gridDim.x];
+        const OzDims dm = oz_dims(KIND, a.blocks[job.blk].K, a.n1, a.nh);
+        const uint32_t bbytes = (uint32_t)(kOzSlices * dm.Np * 32);
+        for (int ks = 0; ks < dm.nks; ++ks, ++g) {
+          const int st = g % kNst;
+          if (g >= kNst && !mbar_wait(smem_addr(empty + st), (uint32_t)((g / kNst - 1) & 1))) {
+            *abort_flag = 1;
+            atomicMax(&g_oz_status, 1);
+            break;
+          }
+          bulk_copy_g2s(smem_addr(sA + st * kAStage), dig + job.aoff + (size_t)ks * kAStage, kAStage,
+                        smem_addr(full + st));
+          bulk_copy_g2s(smem_addr(sB + st * kBStage), a.btab + job.boff + (size_t)ks * bbytes, bbytes,
+                        smem_addr(full + st));
+        }
+      }
+      // the copies in flight land before the CTA's shared memory is released: the last kNst steps'
+      // `full` phases (the MMA warp waits for them too unless it gave up)
+      for (int h = max(0, g - kNst); h < g; ++h)
+        if (!mbar_wait(smem_addr(full + h % kNst), (uint32_t)((h / kNst) & 1))) atomicMax(&g_oz_status, 2);
+    }
+  } else if (warp == kWarps + 1) {
+    // ---- products: 6 MMAs a step (A's plane s against B's planes 0 .. 5 - s, one N = (6 - s) Np MMA)
+    if (lane == 0) {
+      int g = 0;
+      for (int li = 0; li < nmine && !*abort_flag; ++li) {
+        const OzJob job = jobs[blockIdx.x + (int64_t)li * gridDim.x];
+        const OzDims dm = oz_dims(KIND, a.blocks[job.blk].K, a.n1, a.nh);
+        const int b = li & 1;
+        if (li >= 2 && !mbar_wait(smem_addr(tempty + b), (uint32_t)((li / 2 - 1) & 1))) {
+          *abort_flag = 1;
+          atomicMax(&g_oz_status, 1);
+          break;
+        }
+        tc_fence_after();
+        uint32_t idesc[kOzSlices];
+#pragma unroll
+        for (int s = 0; s < kOzSlices; ++s) idesc[s] = idesc_bf16(128, (kOzSlices - s) * dm.Np);
+        const uint32_t d0 = tmem + (uint32_t)(b * kAccCols);
+        bool ok = true;
+        for (int ks = 0; ks < dm.nks; ++ks, ++g) {
+          const int st = g % kNst;
+          if (!mbar_wait(smem_addr(full + st), (uint32_t)((g / kNst) & 1))) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t aa = smem_addr(sA + st * kAStage), ba = smem_addr(sB + st * kBStage);
+#pragma unroll
+          for (int s = 0; s < kOzSlices; ++s)
+            umma_bf16(d0 + (uint32_t)(s * dm.Np), umma_desc(aa + s * kAPlane, 256), umma_desc(ba, 256), idesc[s],
+                      (ks > 0 || s > 0) ? 1u : 0u);
+          umma_commit(smem_addr(empty + st));
+        }
         if (!ok) {
           *abort_flag = 1;
           atomicMax(&g_oz_status, 1);
         }
-        ok = ok && !*abort_flag;
+        umma_commit(smem_addr(tfull + b));  // this job's accumulators are complete (or abandoned)
+        if (!ok) break;
       }
-      if (!__shfl_sync(0xffffffffu, ok, 0)) break;
-      unsigned char *as = sA + st * kAStage;
-#pragma unroll
-      for (int kg = 0; kg < 2; ++kg) {
-        const int q = ks * 16 + kg * 8 + 2 * sub;
-        const double x0 = (rvalid && q < dm.Q) ? __ldg(a.src + a_index<KIND>(ra, q, lv, blk, a)) : 0.0;
-        const double x1 = (rvalid && q + 1 < dm.Q) ? __ldg(a.src + a_index<KIND>(ra, q + 1, lv, blk, a)) : 0.0;
-        uint32_t h0[kOzSlices], h1[kOzSlices];
-        slice6(x0, ebr, h0);
-        slice6(x1, ebr, h1);
-        // K-major core-matrix layout: 8-row groups 256 bytes apart, the two 8-deep halves 128
-        const uint32_t off = (uint32_t)(rl >> 3) * 256u + (uint32_t)kg * 128u + (uint32_t)(rl & 7) * 16u + (uint32_t)sub * 4u;
-#pragma unroll
-        for (int s = 0; s < kOzSlices; ++s) *reinterpret_cast<uint32_t *>(as + s * kAPlane + off) = h0[s] | (h1[s] << 16);
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> the MMAs' reads
-      __syncwarp();
-      if (lane == 0) mbar_arrive(afull + st);
     }
-  } else if (lane == 0) {
-    // ---- the 1D matrix's digit planes by bulk copies, and the MMAs
-    const unsigned char *bsrc = a.btab + job.boff;
-    const int nks = dm.nks;
-    int issued = 0;
-    for (; issued < min(kNst, nks); ++issued)
-      bulk_copy_g2s(smem_addr(sB + issued * kBStage), bsrc + (size_t)issued * bbytes, bbytes, smem_addr(bfull + issued));
-    const uint32_t idesc = idesc_bf16(128, Np);
-    bool ok = true;
-    int ks = 0;
-    for (; ks < nks; ++ks) {
-      const int st = ks % kNst;
-      const uint32_t par = (uint32_t)((ks / kNst) & 1);
-      if (!mbar_wait(smem_addr(bfull + st), par) || !mbar_wait(smem_addr(afull + st), par)) {
-        ok = false;
+  } else {
+    // ---- epilogue: six accumulators per output -> 64-bit integer -> FP64, in the next stage's layout
+    const int lq = warp & 3, cg = warp >> 2;  // TMEM lane quarter, column quarter
+    const int r = lq * 32 + lane;
+    for (int li = 0; li < nmine; ++li) {
+      const OzJob job = jobs[blockIdx.x + (int64_t)li * gridDim.x];
+      const Block blk = a.blocks[job.blk];
+      const OzDims dm = oz_dims(KIND, blk.K, a.n1, a.nh);
+      const int b = li & 1;
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait_sleep(smem_addr(tfull + b), (uint32_t)((li / 2) & 1)) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      tc_fence_after();
+      if (!ok) {
+        if (lane == 0) atomicMax(&g_oz_status, 2);
         break;
       }
-      tc_fence_after();
-      const uint32_t aa = smem_addr(sA + st * kAStage), ba = smem_addr(sB + st * kBStage);
-#pragma unroll
-      for (int s = 0; s < kOzSlices; ++s)
-#pragma unroll
-        for (int t = 0; t < kOzSlices - s; ++t)
-          umma_bf16(tmem + (uint32_t)((s + t) * Np), umma_desc(aa + s * kAPlane, 256),
-                    umma_desc(ba + (uint32_t)(t * Np * 32), 256), idesc, (ks > 0 || s > 0) ? 1u : 0u);
-      umma_commit(smem_addr(empty + st));
-      // refill the stage the previous step used, once its MMAs are done
-      const int kn = ks + kNst - 1;
-      if (ks >= 1 && kn < nks) {
-        const int sp = (ks - 1) % kNst;
-        if (!mbar_wait(smem_addr(empty + sp), (uint32_t)(((ks - 1) / kNst) & 1))) {
-          ok = false;
-          ++ks;
-          break;
-        }
-        bulk_copy_g2s(smem_addr(sB + sp * kBStage), bsrc + (size_t)kn * bbytes, bbytes, smem_addr(bfull + sp));
-        ++issued;
-      }
-    }
-    if (!ok) {
-      *abort_flag = 1;
-      __threadfence_block();
-      atomicMax(&g_oz_status, 1);
-    }
-    umma_commit(smem_addr(done));  // completes when every MMA issued above has
-    if (!ok)  // the copies still in flight land before the CTA's shared memory is released
-      for (int i = ks; i < issued; ++i)
-        if (!mbar_wait(smem_addr(bfull + i % kNst), (uint32_t)((i / kNst) & 1))) atomicMax(&g_oz_status, 2);
-  }
-
-  // ---- epilogue: six accumulators per output -> 64-bit integer -> FP64, in the next stage's layout
-  if (warp < kWarps) {
-    int ok = 1;
-    if (lane == 0) ok = mbar_wait(smem_addr(done), 0) ? 1 : 0;
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    tc_fence_after();
-    if (!ok) {
-      if (lane == 0) atomicMax(&g_oz_status, 2);
-    } else if (!__shfl_sync(0xffffffffu, *abort_flag, 0)) {
-      const int lq = warp & 3, cg = warp >> 2, cw = Np / 4;  // lane quarter, column quarter
-      const int r = lq * 32 + lane, rgl = r0 + r;
-      const int sc0 = rowexp[r] - 1022 - 54;
-      const uint32_t tl = tmem + ((uint32_t)(lq * 32) << 16);
+      if (__shfl_sync(0xffffffffu, *abort_flag, 0)) break;
+      const int64_t *lv = a.leaves + blk.leaf0;
+      const int r0 = (int)job.tile * 128, c0 = (int)job.part * dm.Nc, ncol = min(dm.Nc, dm.N - c0);
+      const int rgl = r0 + r, cw = dm.Np / 4;
+      const int sc0 = __ldg(rexp + job.roff + r) - 1022 - 54;
+      const uint32_t tl = tmem + (uint32_t)(b * kAccCols) + ((uint32_t)(lq * 32) << 16);
       for (int c = cg * cw; c < (cg + 1) * cw; c += 4) {
         uint32_t v[kOzSlices][4];
 #pragma unroll
-        for (int D = 0; D < kOzSlices; ++D) tmem_ld<4>(tl + (uint32_t)(D * Np + c), v[D]);
+        for (int D = 0; D < kOzSlices; ++D) tmem_ld<4>(tl + (uint32_t)(D * dm.Np + c), v[D]);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int cl = c + j;
@@ -380,10 +413,14 @@ __global__ void __launch_bounds__(kThreads, 1) oz_stage_kernel(const OzArgs a) {
             long long V = 0;
 #pragma unroll
             for (int D = 0; D < kOzSlices; ++D) V = V * 256 + (long long)__float2int_rn(__uint_as_float(v[D][j]));
-            store_out<KIND>(rgl, c0 + cl, i64_to_f64_scaled(V, sc0 + colexp[cl]), job, blk, dm, lv, a);
+            store_out<KIND>(rgl, c0 + cl, i64_to_f64_scaled(V, sc0 + __ldg(a.bexp + job.eoff + cl)), job, blk, dm, lv,
+                            a);
           }
         }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty + b);
     }
   }
   tc_fence_before();
@@ -392,11 +429,19 @@ __global__ void __launch_bounds__(kThreads, 1) oz_stage_kernel(const OzArgs a) {
 }
 
 template <int KIND>
-cudaError_t launch_kind(const OzArgs &a, int64_t njobs, cudaStream_t st) {
-  cudaError_t err = cudaFuncSetAttribute(oz_stage_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemBytes);
+cudaError_t launch_kind(const OzArgs &a, const ExecDesc &e, cudaStream_t st) {
+  const int64_t ns = e.oz_nsjobs[KIND], nj = e.oz_njobs[KIND];
+  oz_slice_kernel<KIND><<<(unsigned)ns, kWarps * 32, 0, st>>>(a, e.oz_sjobs[KIND], e.oz_dig, e.oz_rexp);
+  cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  oz_stage_kernel<KIND><<<(unsigned)njobs, kThreads, kSmemBytes, st>>>(a);
+  if ((err = cudaFuncSetAttribute(oz_mma_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSmemBytes)) != cudaSuccess)
+    return err;
+  int dev = 0, nsm = 0;
+  if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+  if ((err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+  const unsigned grid = (unsigned)std::min<int64_t>(nj, std::max(nsm, 1));
+  oz_mma_kernel<KIND><<<grid, kThreads, kSmemBytes, st>>>(a, e.oz_jobs[KIND], nj, e.oz_dig, e.oz_rexp);
   return cudaGetLastError();
 }
 
@@ -406,15 +451,16 @@ cudaError_t run_oz_stage(const ExecDesc &e, int kind, const double *src, double 
   if (kind < 0 || kind > 5) return cudaErrorInvalidValue;
   const int64_t nj = e.oz_njobs[kind];
   if (nj == 0) return cudaSuccess;
-  OzArgs a{e.oz_jobs[kind], kind < 3 ? e.blocks : e.eval_blocks, kind < 3 ? e.block_leaves : e.eval_leaves,
+  if (e.oz_dig == nullptr || e.oz_rexp == nullptr) return cudaErrorInvalidValue;
+  OzArgs a{kind < 3 ? e.blocks : e.eval_blocks, kind < 3 ? e.block_leaves : e.eval_leaves,
            src, dst, e.oz_btab, e.oz_bexp, e.k, e.n1, e.nh, e.slot_size};
   switch (kind) {
-    case 0: return launch_kind<0>(a, nj, st);
-    case 1: return launch_kind<1>(a, nj, st);
-    case 2: return launch_kind<2>(a, nj, st);
-    case 3: return launch_kind<3>(a, nj, st);
-    case 4: return launch_kind<4>(a, nj, st);
-    default: return launch_kind<5>(a, nj, st);
+    case 0: return launch_kind<0>(a, e, st);
+    case 1: return launch_kind<1>(a, e, st);
+    case 2: return launch_kind<2>(a, e, st);
+    case 3: return launch_kind<3>(a, e, st);
+    case 4: return launch_kind<4>(a, e, st);
+    default: return launch_kind<5>(a, e, st);
   }
 }
 

@@ -140,6 +140,8 @@ struct fgt_plan {
   bool form7 = false;       // split precision, 3D: every form stage on tcgen05 (form7_kernel), K = 16, 32
   bool form7_k8 = false;    // and for K = 8 blocks
   bool ozaki = true;        // FP64_TC, 3D: form and evaluation as sliced FP64 stages on the BF16 tensor cores
+  bool gather2_fp64 = true;   // FP64 expansions: the run-form gather too (FGT_GATHER2=0: the per-anchor one)
+  bool gather3 = true;        // 3D, every cutoff-level box an anchor: the stencil-form gather (FGT_GATHER3=0: off)
   cudaStream_t side[fgt::kSides] = {};     // near field and concurrent per-size launches
   cudaEvent_t fork_ev[fgt::kSides] = {}, join_ev[fgt::kSides] = {};
   DevPack host_pack;        // host copy of the uploaded lists and tables (kept for host-only plans)
@@ -899,10 +901,11 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   // of each entry, then integer digits), laid out as the kernel's bulk copies read it: per column
   // part and 16-deep step, six BF16 planes in the K-major core-matrix layout.  The block lists above
   // stay, for the allocation-free call.
-  std::vector<fgt::OzJob> ozjobs[6];
+  std::vector<fgt::OzJob> ozjobs[6], ozsjobs[6];
   std::vector<unsigned char> oztab;
   std::vector<int32_t> ozexp;
   int64_t oz_scr = 0;  // doubles per scratch array
+  int64_t oz_dig = 0, oz_rexp = 0;  // bytes of the digit planes, row exponents of the largest stage
   ex.oz = 0;
   ex.oz_sole = 0;
   if constexpr (std::is_same<C, double2>::value) {
@@ -991,22 +994,29 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
         cls[key] = {boff, eoff};
         return {boff, eoff};
       };
+      int64_t dig_at[6] = {0, 0, 0, 0, 0, 0}, rexp_at[6] = {0, 0, 0, 0, 0, 0};
       auto add_jobs = [&](int kind, int32_t bi, const fgt::Block &B, int64_t scr, int flags) {
         const int mat = B.mat[(kind == 0 || kind == 5) ? 2 : (kind == 1 || kind == 4) ? 1 : 0];
         const auto tb = table(kind, B.K, mat);
         const fgt::OzDims dm = fgt::oz_dims(kind, B.K, n1, nh);
-        for (int t = 0; t < (dm.R + 127) / 128; ++t)
+        for (int t = 0; t < (dm.R + 127) / 128; ++t) {
+          fgt::OzJob j{};
+          j.blk = bi;
+          j.tile = (int16_t)t;
+          j.scr = scr;
+          j.aoff = dig_at[kind];
+          j.roff = (int32_t)rexp_at[kind];
+          j.flags = flags;
+          ozsjobs[kind].push_back(j);  // slicing: part 0 stands for the tile
           for (int pt = 0; pt < dm.P; ++pt) {
-            fgt::OzJob j{};
-            j.blk = bi;
-            j.tile = (int16_t)t;
             j.part = (int16_t)pt;
-            j.scr = scr;
             j.boff = tb.first + (int64_t)pt * dm.nks * fgt::kOzSlices * dm.Np * 32;
             j.eoff = tb.second + pt * dm.Np;
-            j.flags = flags;
             ozjobs[kind].push_back(j);
           }
+          dig_at[kind] += (int64_t)dm.nks * fgt::kOzSlices * 128 * 16 * 2;
+          rexp_at[kind] += 128;
+        }
       };
       // per-block intermediates: the form's and the evaluation's stages reuse the same two arrays
       std::unordered_map<int32_t, int> per_slot;
@@ -1029,7 +1039,12 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
       }
       oz_scr = std::max(sf, se);
       ex.oz_sole = all_sole ? 1 : 0;
-      for (int kind = 0; kind < 6; ++kind) ex.oz_njobs[kind] = (int64_t)ozjobs[kind].size();
+      for (int kind = 0; kind < 6; ++kind) {
+        ex.oz_njobs[kind] = (int64_t)ozjobs[kind].size();
+        ex.oz_nsjobs[kind] = (int64_t)ozsjobs[kind].size();
+        oz_dig = std::max(oz_dig, dig_at[kind]);
+        oz_rexp = std::max(oz_rexp, rexp_at[kind]);
+      }
     }
   }
 
@@ -1070,11 +1085,14 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   }
   ex.n_gather = (int64_t)gdst.size();
   P.n_gather_pairs = (int64_t)gsrc.size();
-  // split precision: the same gather in separable form, runs of kSegW target boxes along x_1,
-  // each with the 3^(d-1) neighbouring source lines (one launch item per run)
+  // the same gather in separable form (all precisions; FP64 with FGT_GATHER2=0 keeps the other),
+  // runs of kSegW target boxes along x_1, each with the 3^(d-1) neighbouring source lines (one
+  // launch item per run)
   std::vector<fgt::GatherSeg> gsegs;
-  if (P.prec == FGT_PREC_SPLIT && !P.fourier && !anchors.empty()) {
+  ex.seg_w = 0;
+  if ((P.prec == FGT_PREC_SPLIT || P.gather2_fp64) && !P.fourier && !anchors.empty()) {
     const int nb = 1 << P.lc, sw = std::min(fgt::kSegW, nb);
+    ex.seg_w = sw;
     std::map<std::array<int32_t, 3>, size_t> seg_of;
     auto slot_at = [&](int32_t x, int32_t y, int32_t z) -> int32_t {
       int32_t q[3] = {x, y, z};
@@ -1110,6 +1128,25 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
     }
   }
   ex.n_gather_segs = (int64_t)gsegs.size();
+  // FP64 expansions, every box of the cutoff level an anchor (3D, 4 or 8 boxes a side): the stencil
+  // form of the gather over the whole grid (measured 2.0x faster than the run form on the
+  // 16.8M-point periodic workload at tol 1e-10, 1.6x on the adaptive one; in FP32 the run form
+  // measured faster, 0.064 against 0.075 ms); FGT_GATHER3=0 keeps the run form
+  std::vector<int32_t> ggrid;
+  ex.grid_nb = 0;
+  ex.grid_periodic = per ? 1 : 0;
+  if (d == 3 && !P.fourier && P.gather3 && !P.f32() && !hier && (P.lc == 2 || P.lc == 3)) {
+    const int nb = 1 << P.lc;
+    ggrid.assign((size_t)nb * nb * nb, -1);
+    bool full = (int64_t)anchors.size() == (int64_t)nb * nb * nb;
+    for (int32_t T : anchors) {
+      const Box &Tb = P.boxes[T];
+      ggrid[((size_t)Tb.c[2] * nb + Tb.c[1]) * nb + Tb.c[0]] = Tb.slot;
+    }
+    for (int32_t v : ggrid) full = full && v >= 0;
+    if (full) ex.grid_nb = nb;
+    else ggrid.clear();
+  }
   // phase vectors of T_out->in: S = T + o (box units) gives c_T - c_S = -o L_c
   std::vector<C> Pf, Ph;
   {
@@ -1397,10 +1434,14 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
                o_nptr = pack.add("near_ptr", nptr), o_nsrc = pack.add("near_src", nsrc),
                o_ntab = pack.add("near_tab", ntab), o_npairs = pack.add("near_pairs", npairs);
   const size_t o_nband = pack.add("near_band", nband);
-  size_t o_ozj[6];
-  for (int kind = 0; kind < 6; ++kind) o_ozj[kind] = pack.add("oz_jobs" + std::to_string(kind), ozjobs[kind]);
+  size_t o_ozj[6], o_ozs[6];
+  for (int kind = 0; kind < 6; ++kind) {
+    o_ozj[kind] = pack.add("oz_jobs" + std::to_string(kind), ozjobs[kind]);
+    o_ozs[kind] = pack.add("oz_slice_jobs" + std::to_string(kind), ozsjobs[kind]);
+  }
   const size_t o_oztab = pack.add("oz_btab", oztab), o_ozexp = pack.add("oz_bexp", ozexp);
   const size_t o_eblocks = pack.add("eval_blocks", eblocks);
+  const size_t o_ggrid = pack.add("gather_grid", ggrid);
   std::vector<std::tuple<size_t, size_t, size_t, int64_t>> step_off;  // items, qf, qh, n
   for (size_t i = 0; i < merge_h.size(); ++i) {
     auto &s = merge_h[i];
@@ -1430,7 +1471,10 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   ex.n_psi_tc_slots = use_tc6 ? tc6_slots : 0;
   // sliced FP64 stages: their two intermediate arrays
   const size_t oz_off = (ptc_off + ptc_bytes + 255) & ~(size_t)255;
-  const size_t oz_bytes = 2 * sizeof(double) * (size_t)oz_scr;
+  const size_t oz_x_bytes = 2 * sizeof(double) * (size_t)oz_scr;
+  const size_t oz_dig_off = (oz_off + oz_x_bytes + 1023) & ~(size_t)1023;
+  const size_t oz_rexp_off = (oz_dig_off + (size_t)oz_dig + 255) & ~(size_t)255;
+  const size_t oz_bytes = oz_scr > 0 ? oz_rexp_off + sizeof(int) * (size_t)oz_rexp - oz_off : 0;
   fill_flops(P, ex, blocks, merge_h.size() + push_h.size() ? [&] {
     int64_t sf = 0;
     for (auto &s : merge_h) sf += 8 * (int64_t)s.items.size() * nc * ex.slot_size;
@@ -1483,10 +1527,16 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   ex.psi_tc = ptc_bytes ? (void *)((char *)P.work + ptc_off) : nullptr;
   ex.oz_x = oz_bytes ? (double *)((char *)P.work + oz_off) : nullptr;
   ex.oz_y = oz_bytes ? ex.oz_x + oz_scr : nullptr;
-  for (int kind = 0; kind < 6; ++kind) ex.oz_jobs[kind] = (const fgt::OzJob *)at(o_ozj[kind]);
+  ex.oz_dig = oz_bytes ? (unsigned char *)P.work + oz_dig_off : nullptr;
+  ex.oz_rexp = oz_bytes ? (int *)((char *)P.work + oz_rexp_off) : nullptr;
+  for (int kind = 0; kind < 6; ++kind) {
+    ex.oz_jobs[kind] = (const fgt::OzJob *)at(o_ozj[kind]);
+    ex.oz_sjobs[kind] = (const fgt::OzJob *)at(o_ozs[kind]);
+  }
   ex.oz_btab = (const unsigned char *)at(o_oztab);
   ex.oz_bexp = (const int32_t *)at(o_ozexp);
   ex.eval_blocks = (const fgt::Block *)at(o_eblocks);
+  ex.gather_grid = ex.grid_nb > 0 ? (const int32_t *)at(o_ggrid) : nullptr;
   ex.sig_maps_ready = 0;
   if (ex.sig_order == 1) {
     // the tensor maps over the packed density (its address is set just above)
@@ -1615,6 +1665,13 @@ fgt_status create_impl(int d, double delta, double tol, double eps_pw, int bc, i
     // FP64_TC, 3D, fused mode, n1 <= 80): the default there; FGT_OZAKI=0 keeps the DMMA kernels
     const char *oz = std::getenv("FGT_OZAKI");
     P->ozaki = !(oz && oz[0] == '0');
+    // the run-form gather for the FP64 expansions too (measured 2.0x faster than the per-anchor
+    // gather on the 16.8M-point periodic workload at tol 1e-10, 1.7x on the 2.09M-point adaptive
+    // one); FGT_GATHER2=0 keeps the per-anchor kernel
+    const char *g2 = std::getenv("FGT_GATHER2");
+    P->gather2_fp64 = !(g2 && g2[0] == '0');
+    const char *g3 = std::getenv("FGT_GATHER3");
+    P->gather3 = !(g3 && g3[0] == '0');
   }
   P->n_leaves = tree->n_leaves;
   P->leaf_level.assign(tree->leaf_level, tree->leaf_level + tree->n_leaves);

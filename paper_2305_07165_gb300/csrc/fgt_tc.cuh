@@ -1,6 +1,7 @@
-// Fifth-generation tensor-core helpers shared by the kernel translation units: shared-memory
-// addresses, matrix descriptors of the K-major no-swizzle operand layout, MMA commit, bounded
-// mbarrier waits, tensor-memory fences and loads, bulk asynchronous copies (sm_100 family, PTX).
+// Helpers shared by the kernel translation units: fifth-generation tensor-core plumbing (shared-
+// memory addresses, matrix descriptors of the K-major no-swizzle operand layout, MMA commit,
+// bounded mbarrier waits, tensor-memory fences and loads, bulk asynchronous copies; sm_100 family,
+// PTX) and an integer-pipe int64 -> FP64 conversion.
 #pragma once
 #include <cstdint>
 
@@ -77,6 +78,26 @@ __device__ __forceinline__ void tmem_ld(uint32_t addr, uint32_t (&v)[N]) {
         : "r"(addr));
   }
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// v 2^sc rounded to FP64 (nearest, ties to even), with integer operations.
+__device__ __forceinline__ double i64_to_f64_scaled(long long v, int sc) {
+  if (v == 0) return 0.0;
+  const unsigned long long sg = v < 0 ? (1ULL << 63) : 0ULL;
+  unsigned long long a = v < 0 ? 0ULL - (unsigned long long)v : (unsigned long long)v;
+  const int lz = __clzll((long long)a);
+  a <<= lz;
+  unsigned long long m = a >> 11;
+  const unsigned rem = (unsigned)(a & 0x7FF);
+  if (rem > 0x400u || (rem == 0x400u && (m & 1ULL))) ++m;
+  int E = 1023 + 63 - lz + sc;
+  if (m >> 53) {
+    m >>= 1;
+    ++E;
+  }
+  if (E <= 0) return __longlong_as_double((long long)sg);
+  if (E >= 2047) return __longlong_as_double((long long)(sg | 0x7FF0000000000000ULL));
+  return __longlong_as_double((long long)(sg | ((unsigned long long)E << 52) | (m & 0xFFFFFFFFFFFFFULL)));
 }
 
 }  // namespace fgt

@@ -59,7 +59,7 @@ def test_sliced_fp64_tensor_core(monkeypatch, name, p, delta, tol, bc):
     u0, _, info0, _ = _u(monkeypatch, True, tr, p, delta, tol, sig, bc, prec=F.PREC_FP64)
     scale = np.abs(u0).max()
     assert np.abs(u - u0).max() <= 1e-12 * scale
-    assert np.abs(u2 - u).max() <= 1e-14 * scale   # the second call rewrites, it does not accumulate
+    assert np.abs(u2 - u).max() <= 1e-12 * scale   # rewrites (atomic sums differ in order), does not accumulate
     if un is not None:  # the allocation-free call keeps the FP64 (DMMA) kernels
         assert np.abs(un - u0).max() <= 1e-12 * scale
     # fewer launches than the FP64 path is not implied; the sliced path is six stage launches

@@ -13,14 +13,14 @@ F = pytest.importorskip("paper_2305_07165_gb300")
 BLOCK = np.dtype([("slot", "<i4"), ("K", "<i4"), ("dl", "<i4"), ("flags", "<i4"), ("mat", "<i4", 3),
                   ("pad", "<i4"), ("leaf0", "<i8")])
 JOB = np.dtype([("blk", "<i4"), ("tile", "<i2"), ("part", "<i2"), ("scr", "<i8"), ("boff", "<i8"),
-                ("eoff", "<i4"), ("flags", "<i4")])
+                ("aoff", "<i8"), ("eoff", "<i4"), ("roff", "<i4"), ("flags", "<i4"), ("pad", "<i4")])
 S = 6
 
 
 def dims(kind, K, n1, nh):
     R, Q, N = {0: (K * K, K, 2 * nh), 1: (nh * K, 2 * K, 2 * n1), 2: (nh * n1, 2 * K, 2 * n1),
                3: (nh * n1, 2 * n1, 2 * K), 4: (K * nh, 2 * n1, 2 * K), 5: (K * K, 2 * nh, K)}[kind]
-    P = -(-N // 80)
+    P = -(-N // 32)
     Nc = -(-N // P)
     return R, Q, N, P, Nc, -(-Nc // 16) * 16, -(-Q // 16)
 
@@ -100,6 +100,15 @@ def test_sliced_digit_tables(name, k, delta, tol, bc):
             assert np.all(d == np.round(d)) and np.all(np.abs(d) <= 128)
             val = np.ldexp(np.tensordot(2.0 ** (-7 - 8 * np.arange(S)), d, axes=1), f[None, :])
             assert np.all(np.abs(val - Bp) <= np.ldexp(1.0, f - 48)[None, :]), kind
+        sj = hp.array(f"oz_slice_jobs{kind}", JOB)
+        assert {(int(j["blk"]), int(j["tile"])) for j in sj} == {(b, t) for b, ts in covered.items() for t, _ in ts}
+        assert len(sj) == len({(int(j["blk"]), int(j["tile"])) for j in sj})
+        ends = sorted((int(j["aoff"]), int(j["aoff"]) + dims(kind, int(blks[j["blk"]]["K"]), n1, nh)[6] * S * 4096)
+                      for j in sj)
+        assert all(a1 <= b0 for (_, a1), (b0, _) in zip(ends, ends[1:]))      # digit planes do not overlap
+        for j in jobs:   # the products read their tile's planes and exponents
+            m = sj[(sj["blk"] == j["blk"]) & (sj["tile"] == j["tile"])][0]
+            assert (j["aoff"], j["roff"]) == (m["aoff"], m["roff"])
         for bi in range(len(blks)):
             R, Q, N, P, *_ = dims(kind, int(blks[bi]["K"]), n1, nh)
             assert covered.get(bi) == {(t, p) for t in range(-(-R // 128)) for p in range(P)}
