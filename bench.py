@@ -116,6 +116,10 @@ class ClockSampler:
 # holds the capture.  Keyed by (workload, form, phase); an entry is removed whenever the
 # kernels of that phase change, and phases without a current capture report null.
 NCU_TRAFFIC = {
+    ("periodic3d", "fp64tc_tol1e-10", "evaluate"): {
+        "bytes": 2090.9e6, "source": "profiles/sliced_fp64_kernels_periodic3d.md (oz_slice_kernel + oz_mma_kernel, stages 3-5)"},
+    ("periodic3d", "fp64tc_tol1e-10", "form"): {
+        "bytes": 1937.3e6, "source": "profiles/sliced_fp64_kernels_periodic3d.md (oz_slice_kernel + oz_mma_kernel, stages 0-2)"},
     ("periodic3d", "fp64_tol1e-10", "form"): {
         "bytes": 2150.2e6, "source": "profiles/fp64_kernels_periodic3d.md (form_kernel<3,double>, 1 launch a step)"},
     ("periodic3d", "fp64_tol1e-10", "evaluate"): {
