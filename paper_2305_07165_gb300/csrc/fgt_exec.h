@@ -100,6 +100,7 @@ struct ExecDesc {
   const unsigned char *oz_btab = nullptr;  // the sliced 1D matrices (BF16 digit planes)
   const int32_t *oz_bexp = nullptr;        // their column exponents
   const Block *eval_blocks = nullptr;      // the evaluation's blocks (the jobs of stages 3-5 index them)
+  const OzGroup *oz_groups = nullptr;      // stage 2's block groups (its jobs index them)
   double *oz_x = nullptr, *oz_y = nullptr;
 
   // out->in gather at the cutoff level
@@ -196,6 +197,13 @@ inline __host__ __device__ OzDims oz_dims(int kind, int K, int n1, int nh) {
   d.Nc = (d.N + d.P - 1) / d.P;
   d.Np = (d.Nc + 15) / 16 * 16;
   d.nks = (d.Q + 15) / 16;
+  return d;
+}
+// Stage 2 over a group of blocks: the concatenated contraction length Q replaces 2 K.
+inline __host__ __device__ OzDims oz_dims_group(int n1, int nh, int Q) {
+  OzDims d = oz_dims(2, 8, n1, nh);
+  d.Q = Q;
+  d.nks = (Q + 15) / 16;
   return d;
 }
 // Enqueue stage `kind` over its jobs: src -> dst (sigma -> oz_x -> oz_y -> phi; psi -> oz_x -> oz_y -> u).

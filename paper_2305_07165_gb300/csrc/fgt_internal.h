@@ -38,6 +38,21 @@ struct OzJob {
   int32_t pad;
 };
 
+// The form's last sliced stage (the x1 contraction into the anchor's slot) for up to kOzGroupMax
+// blocks of one anchor at once: their contractions concatenated (q0[j] .. q0[j+1] is member j's,
+// 2 K_j long), so that the slot is written once per group instead of once per block.  The jobs of
+// that stage index these groups instead of blocks.
+constexpr int kOzGroupMax = 10;
+struct OzGroup {
+  int32_t slot;
+  int32_t n;                         // members
+  int32_t K[kOzGroupMax];
+  int32_t q0[kOzGroupMax + 1];       // q0[n] = the concatenated length (<= 160, the exactness bound)
+  int32_t blk[kOzGroupMax];          // members (indices into the plan's blocks)
+  int32_t pad;
+  int64_t scr[kOzGroupMax];          // members' offsets in the intermediate arrays
+};
+
 // One out->in translation source at the cutoff level.
 struct GatherSrc {
   int32_t slot;      // source outgoing slot

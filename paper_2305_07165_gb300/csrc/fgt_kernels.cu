@@ -824,7 +824,10 @@ __device__ __forceinline__ void sigma_pack_body(const Block *__restrict__ blocks
       double2 v = make_double2(0.0, 0.0);
       if (FGT_OK_BYTES(src + node, 16)) v = __ldg(reinterpret_cast<const double2 *>(src + node));
       const int j3 = node >> 6, r = node & 63;
-      leaf[j3 * 65 + r] = f64_to_f32_int(v.x);
+      // one value through the FP64 pipe's conversion, one through the integer pipes: the two run
+      // side by side (all on the integer pipes, the pack was issue-bound; all on the FP64 pipe, that
+      // narrow pipe would be the limit)
+      leaf[j3 * 65 + r] = __double2float_rn(v.x);
       leaf[j3 * 65 + r + 1] = f64_to_f32_int(v.y);
     }
     __syncthreads();

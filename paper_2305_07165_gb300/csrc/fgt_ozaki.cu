@@ -26,7 +26,7 @@
 //     part reads the same planes) in the tensor cores' K-major core-matrix layout;
 //   - oz_mma_kernel, persistent, one CTA per SM over the (block, tile, column part of <= 32 columns)
 //     jobs: a copy warp streams the tile's digit planes and the 1D matrix's of each step with bulk
-//     asynchronous copies into a 4-stage ring; an MMA warp issues 6 MMAs a step -- A's digit plane s
+//     asynchronous copies into a 6-stage ring; an MMA warp issues 6 MMAs a step -- A's digit plane s
 //     against B's planes 0 .. 5 - s, stored one after another along N, in one MMA of N = (6 - s) 32
 //     into accumulators s .. 5 -- so each A plane is read once a step (21 separate MMAs would read it
 //     21 times), into one of two accumulator sets; sixteen warps drain the other set (recombine,
@@ -47,7 +47,7 @@ __device__ int g_oz_status;  // 1: a wait ran out (the CTA skipped its outputs),
 
 namespace {
 
-constexpr int kNst = 4;                          // pipeline stages (16-deep steps in flight)
+constexpr int kNst = 6;                          // pipeline stages (16-deep steps in flight: covers the DRAM latency)
 constexpr int kWarps = 16;                       // slicing / epilogue warps; two more copy and issue MMAs
 constexpr int kThreads = (kWarps + 2) * 32;
 constexpr uint32_t kAPlane = 128 * 16 * 2;       // one digit plane of a 128 x 16 A tile (BF16)
@@ -59,14 +59,22 @@ constexpr size_t kSmemBytes = (size_t)kNst * (kAStage + kBStage) + (2 * kNst + 4
 
 struct OzArgs {
   const Block *blocks;
+  const OzGroup *groups;  // stage 2: its jobs' block groups
   const int64_t *leaves;
   const double *src;
   double *dst;
   const unsigned char *btab;
   const int32_t *bexp;
   int k, n1, nh;
+  int lk;      // log2 k when k is a power of two (divisions by k and K become shifts), else -1
   int64_t ss;  // complex values per expansion slot
 };
+
+// x / k and x / K (K = 2^dl k) by shifts when k is a power of two
+__device__ __forceinline__ int div_k(int x, const OzArgs &a) { return a.lk >= 0 ? (x >> a.lk) : x / a.k; }
+__device__ __forceinline__ int div_K(int x, const Block &blk, const OzArgs &a) {
+  return a.lk >= 0 ? (x >> (a.lk + blk.dl)) : x / blk.K;
+}
 
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
@@ -145,22 +153,22 @@ __device__ __forceinline__ RowAddr row_addr(int r, const OzJob &job, const Block
   const int K = blk.K, k = a.k, n1 = a.n1, nh = a.nh, nl = 1 << blk.dl;
   RowAddr ra{0, 0, 0};
   if constexpr (KIND == 0) {
-    const int J2 = r / K, J1 = r - J2 * K, o2 = J2 / k, o1 = J1 / k;
+    const int J2 = div_K(r, blk, a), J1 = r - J2 * K, o2 = div_k(J2, a), o1 = div_k(J1, a);
     ra.a = o2 * nl + o1;
     ra.b = (J2 - o2 * k) * k + (J1 - o1 * k);
   } else if constexpr (KIND == 1) {
-    const int m3 = r / K, J1 = r - m3 * K;
+    const int m3 = div_K(r, blk, a), J1 = r - m3 * K;
     ra.base = job.scr + (int64_t)m3 * 2 * K * K + J1;
-  } else if constexpr (KIND == 2) {
-    const int m3 = r / n1, m2 = r - m3 * n1;
-    ra.base = job.scr + (int64_t)m2 * 2 * nh * K + (int64_t)m3 * K;
+  } else if constexpr (KIND == 2) {  // a group of blocks: the member's base is found per q
+    ra.a = r / n1;                  // m3
+    ra.b = r - ra.a * n1;           // m2
   } else if constexpr (KIND == 3) {
     ra.base = (int64_t)blk.slot * 2 * a.ss + (int64_t)r * 2 * n1;
   } else if constexpr (KIND == 4) {
     const int I1 = r / nh, m3 = r - I1 * nh;
     ra.base = job.scr + (int64_t)I1 * nh * n1 + (int64_t)m3 * n1;
   } else {
-    const int I2 = r / K, I1 = r - I2 * K;
+    const int I2 = div_K(r, blk, a), I1 = r - I2 * K;
     ra.base = job.scr + (int64_t)I2 * K * nh + (int64_t)I1 * nh;
   }
   return ra;
@@ -168,17 +176,19 @@ __device__ __forceinline__ RowAddr row_addr(int r, const OzJob &job, const Block
 
 template <int KIND>
 __device__ __forceinline__ int64_t a_index(const RowAddr &ra, int q, const int64_t *lv, const Block &blk,
-                                           const OzArgs &a) {
+                                           const OzArgs &a, const OzGroup *g = nullptr) {
   const int K = blk.K, k = a.k, n1 = a.n1, nh = a.nh, nl = 1 << blk.dl;
   if constexpr (KIND == 0) {
-    const int o3 = q / k, j3 = q - o3 * k;
+    const int o3 = div_k(q, a), j3 = q - o3 * k;
     return __ldg(lv + (int64_t)o3 * nl * nl + ra.a) * (int64_t)k * k * k + (int64_t)j3 * k * k + ra.b;
   } else if constexpr (KIND == 1) {
     const int c = q >= K, J2 = q - c * K;
     return ra.base + (int64_t)c * K * K + (int64_t)J2 * K;
   } else if constexpr (KIND == 2) {
-    const int c = q >= K, J1 = q - c * K;
-    return ra.base + (int64_t)c * nh * K + J1;
+    int j = 0;  // the member whose contraction holds q
+    while (j + 1 < g->n && q >= g->q0[j + 1]) ++j;
+    const int Kj = g->K[j], ql = q - g->q0[j], c = ql >= Kj, J1 = ql - c * Kj;
+    return g->scr[j] + ((int64_t)ra.b * 2 + c) * nh * Kj + (int64_t)ra.a * Kj + J1;
   } else if constexpr (KIND == 3) {
     return ra.base + q;
   } else if constexpr (KIND == 4) {
@@ -192,21 +202,32 @@ __device__ __forceinline__ int64_t a_index(const RowAddr &ra, int q, const int64
 
 template <int KIND>
 __device__ __forceinline__ void store_out(int r, int n, double v, const OzJob &job, const Block &blk,
-                                          const OzDims &dm, const int64_t *lv, const OzArgs &a) {
+                                          const OzDims &dm, const int64_t *lv, const OzArgs &a, int slot = 0) {
   if constexpr (KIND == 2) {
-    double *p = a.dst + (int64_t)blk.slot * 2 * a.ss + (int64_t)r * 2 * a.n1 + n;
+    double *p = a.dst + (int64_t)slot * 2 * a.ss + (int64_t)r * 2 * a.n1 + n;
     if (job.flags & 1) atomicAdd(p, v);
     else *p = v;
   } else if constexpr (KIND == 5) {
     const int K = blk.K, k = a.k, nl = 1 << blk.dl;
-    const int I2 = r / K, I1 = r - I2 * K, I3 = n;
-    const int o1 = I1 / k, o2 = I2 / k, o3 = I3 / k;
+    const int I2 = div_K(r, blk, a), I1 = r - I2 * K, I3 = n;
+    const int o1 = div_k(I1, a), o2 = div_k(I2, a), o3 = div_k(I3, a);
     double *p = a.dst + __ldg(lv + ((int64_t)o3 * nl + o2) * nl + o1) * (int64_t)k * k * k +
                 ((int64_t)(I3 - o3 * k) * k + (I2 - o2 * k)) * k + (I1 - o1 * k);
     if (job.flags & 1) atomicAdd(p, v);
     else *p = v;
   } else {
     a.dst[job.scr + (int64_t)n * dm.R + r] = v;
+  }
+}
+
+// A job's stage dimensions: its block's, or for stage 2 its group's (the concatenated contraction).
+template <int KIND>
+__device__ __forceinline__ OzDims job_dims(const OzJob &job, const OzArgs &a) {
+  if constexpr (KIND == 2) {
+    const OzGroup *g = a.groups + job.blk;
+    return oz_dims_group(a.n1, a.nh, __ldg(&g->q0[__ldg(&g->n)]));
+  } else {
+    return oz_dims(KIND, __ldg(&a.blocks[job.blk].K), a.n1, a.nh);
   }
 }
 
@@ -219,8 +240,17 @@ __global__ void __launch_bounds__(kWarps * 32) oz_slice_kernel(const OzArgs a, c
                                                                unsigned char *__restrict__ dig,
                                                                int *__restrict__ rexp) {
   const OzJob job = sjobs[blockIdx.x];
-  const Block blk = a.blocks[job.blk];
-  const OzDims dm = oz_dims(KIND, blk.K, a.n1, a.nh);
+  __shared__ OzGroup grp;  // stage 2: the job's group of blocks
+  Block blk{};
+  OzDims dm;
+  if constexpr (KIND == 2) {
+    if (threadIdx.x == 0) grp = a.groups[job.blk];
+    __syncthreads();
+    dm = oz_dims_group(a.n1, a.nh, grp.q0[grp.n]);
+  } else {
+    blk = a.blocks[job.blk];
+    dm = oz_dims(KIND, blk.K, a.n1, a.nh);
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t *lv = a.leaves + blk.leaf0;
   const int rl = 8 * warp + (lane >> 2), sub = lane & 3;
@@ -230,8 +260,8 @@ __global__ void __launch_bounds__(kWarps * 32) oz_slice_kernel(const OzArgs a, c
   int ebr = 0;
   if (rvalid)
     for (int q = 2 * sub; q < dm.Q; q += 8) {
-      ebr = max(ebr, exp_field(__ldg(a.src + a_index<KIND>(ra, q, lv, blk, a))));
-      if (q + 1 < dm.Q) ebr = max(ebr, exp_field(__ldg(a.src + a_index<KIND>(ra, q + 1, lv, blk, a))));
+      ebr = max(ebr, exp_field(__ldg(a.src + a_index<KIND>(ra, q, lv, blk, a, &grp))));
+      if (q + 1 < dm.Q) ebr = max(ebr, exp_field(__ldg(a.src + a_index<KIND>(ra, q + 1, lv, blk, a, &grp))));
     }
   ebr = max(ebr, __shfl_xor_sync(0xffffffffu, ebr, 1));
   ebr = max(ebr, __shfl_xor_sync(0xffffffffu, ebr, 2));
@@ -243,8 +273,8 @@ __global__ void __launch_bounds__(kWarps * 32) oz_slice_kernel(const OzArgs a, c
 #pragma unroll
     for (int kg = 0; kg < 2; ++kg) {
       const int q = ks * 16 + kg * 8 + 2 * sub;
-      const double x0 = (rvalid && q < dm.Q) ? __ldg(a.src + a_index<KIND>(ra, q, lv, blk, a)) : 0.0;
-      const double x1 = (rvalid && q + 1 < dm.Q) ? __ldg(a.src + a_index<KIND>(ra, q + 1, lv, blk, a)) : 0.0;
+      const double x0 = (rvalid && q < dm.Q) ? __ldg(a.src + a_index<KIND>(ra, q, lv, blk, a, &grp)) : 0.0;
+      const double x1 = (rvalid && q + 1 < dm.Q) ? __ldg(a.src + a_index<KIND>(ra, q + 1, lv, blk, a, &grp)) : 0.0;
       int g0[kOzSlices], g1[kOzSlices];
       slice6(x0, ebr, g0);
       slice6(x1, ebr, g1);
@@ -273,7 +303,7 @@ __device__ __forceinline__ bool mbar_wait_sleep(uint32_t mbar, uint32_t parity, 
 
 // Products: a persistent kernel, one CTA per SM over the stage's (block, tile, column part) jobs
 // (job j = blockIdx.x + i gridDim.x).  Warp 16 copies the digit planes of every step of every job
-// into a 4-stage ring (bulk copies, complete_tx on the stage's `full` barrier), warp 17 issues the
+// into a 6-stage ring (bulk copies, complete_tx on the stage's `full` barrier), warp 17 issues the
 // MMAs into one of two accumulator sets in tensor memory (job i in set i mod 2), and sixteen warps
 // drain the other set meanwhile: the epilogue of one job overlaps the products of the next.
 template <int KIND>
@@ -318,7 +348,7 @@ __global__ void __launch_bounds__(kThreads, 1) oz_mma_kernel(const OzArgs a, con
       int g = 0;  // steps issued so far (all jobs)
       for (int li = 0; li < nmine && !*abort_flag; ++li) {
         const OzJob job = jobs[blockIdx.x + (int64_t)li * gridDim.x];
-        const OzDims dm = oz_dims(KIND, a.blocks[job.blk].K, a.n1, a.nh);
+        const OzDims dm = job_dims<KIND>(job, a);
         const uint32_t bbytes = (uint32_t)(kOzSlices * dm.Np * 32);
         for (int ks = 0; ks < dm.nks; ++ks, ++g) {
           const int st = g % kNst;
@@ -344,7 +374,7 @@ __global__ void __launch_bounds__(kThreads, 1) oz_mma_kernel(const OzArgs a, con
       int g = 0;
       for (int li = 0; li < nmine && !*abort_flag; ++li) {
         const OzJob job = jobs[blockIdx.x + (int64_t)li * gridDim.x];
-        const OzDims dm = oz_dims(KIND, a.blocks[job.blk].K, a.n1, a.nh);
+        const OzDims dm = job_dims<KIND>(job, a);
         const int b = li & 1;
         if (li >= 2 && !mbar_wait(smem_addr(tempty + b), (uint32_t)((li / 2 - 1) & 1))) {
           *abort_flag = 1;
@@ -385,8 +415,9 @@ __global__ void __launch_bounds__(kThreads, 1) oz_mma_kernel(const OzArgs a, con
     const int r = lq * 32 + lane;
     for (int li = 0; li < nmine; ++li) {
       const OzJob job = jobs[blockIdx.x + (int64_t)li * gridDim.x];
-      const Block blk = a.blocks[job.blk];
-      const OzDims dm = oz_dims(KIND, blk.K, a.n1, a.nh);
+      const Block blk = KIND == 2 ? Block{} : a.blocks[job.blk];
+      const OzDims dm = job_dims<KIND>(job, a);
+      const int slot = KIND == 2 ? __ldg(&a.groups[job.blk].slot) : blk.slot;
       const int b = li & 1;
       int ok = 1;
       if (lane == 0) ok = mbar_wait_sleep(smem_addr(tfull + b), (uint32_t)((li / 2) & 1)) ? 1 : 0;
@@ -399,28 +430,35 @@ __global__ void __launch_bounds__(kThreads, 1) oz_mma_kernel(const OzArgs a, con
       if (__shfl_sync(0xffffffffu, *abort_flag, 0)) break;
       const int64_t *lv = a.leaves + blk.leaf0;
       const int r0 = (int)job.tile * 128, c0 = (int)job.part * dm.Nc, ncol = min(dm.Nc, dm.N - c0);
-      const int rgl = r0 + r, cw = dm.Np / 4;
+      const int rgl = r0 + r, cw = dm.Np / 4, cbeg = cg * cw;  // cw = 4 or 8 columns a warp
       const int sc0 = __ldg(rexp + job.roff + r) - 1022 - 54;
-      const uint32_t tl = tmem + (uint32_t)(b * kAccCols) + ((uint32_t)(lq * 32) << 16);
-      for (int c = cg * cw; c < (cg + 1) * cw; c += 4) {
-        uint32_t v[kOzSlices][4];
+      const uint32_t tl = tmem + (uint32_t)(b * kAccCols) + ((uint32_t)(lq * 32) << 16) + (uint32_t)cbeg;
+      uint32_t v[kOzSlices][8];
+      if (cw == 8) {
 #pragma unroll
-        for (int D = 0; D < kOzSlices; ++D) tmem_ld<4>(tl + (uint32_t)(D * dm.Np + c), v[D]);
+        for (int D = 0; D < kOzSlices; ++D) tmem_ld8_nw(tl + (uint32_t)(D * dm.Np), v[D]);
+      } else {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int cl = c + j;
-          if (rgl < dm.R && cl < ncol) {
-            long long V = 0;
-#pragma unroll
-            for (int D = 0; D < kOzSlices; ++D) V = V * 256 + (long long)__float2int_rn(__uint_as_float(v[D][j]));
-            store_out<KIND>(rgl, c0 + cl, i64_to_f64_scaled(V, sc0 + __ldg(a.bexp + job.eoff + cl)), job, blk, dm, lv,
-                            a);
-          }
-        }
+        for (int D = 0; D < kOzSlices; ++D) tmem_ld4_nw(tl + (uint32_t)(D * dm.Np), v[D]);
       }
+      tmem_wait_ld();
+      // the accumulator set is in registers: hand it back to the MMA warp before the arithmetic
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty + b);
+      if (rgl < dm.R) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int cl = cbeg + j;
+          if (j < cw && cl < ncol) {
+            long long V = 0;
+#pragma unroll
+            for (int D = 0; D < kOzSlices; ++D) V = V * 256 + (long long)__float2int_rn(__uint_as_float(v[D][j]));
+            store_out<KIND>(rgl, c0 + cl, i64_to_f64_scaled(V, sc0 + __ldg(a.bexp + job.eoff + cl)), job, blk, dm,
+                            lv, a, slot);
+          }
+        }
+      }
     }
   }
   tc_fence_before();
@@ -452,8 +490,11 @@ cudaError_t run_oz_stage(const ExecDesc &e, int kind, const double *src, double 
   const int64_t nj = e.oz_njobs[kind];
   if (nj == 0) return cudaSuccess;
   if (e.oz_dig == nullptr || e.oz_rexp == nullptr) return cudaErrorInvalidValue;
-  OzArgs a{kind < 3 ? e.blocks : e.eval_blocks, kind < 3 ? e.block_leaves : e.eval_leaves,
-           src, dst, e.oz_btab, e.oz_bexp, e.k, e.n1, e.nh, e.slot_size};
+  int lk = -1;
+  for (int t = 0; t < 8; ++t)
+    if ((1 << t) == e.k) lk = t;
+  OzArgs a{kind < 3 ? e.blocks : e.eval_blocks, e.oz_groups, kind < 3 ? e.block_leaves : e.eval_leaves,
+           src, dst, e.oz_btab, e.oz_bexp, e.k, e.n1, e.nh, lk, e.slot_size};
   switch (kind) {
     case 0: return launch_kind<0>(a, e, st);
     case 1: return launch_kind<1>(a, e, st);

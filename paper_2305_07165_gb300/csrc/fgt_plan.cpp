@@ -902,6 +902,7 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   // part and 16-deep step, six BF16 planes in the K-major core-matrix layout.  The block lists above
   // stay, for the allocation-free call.
   std::vector<fgt::OzJob> ozjobs[6], ozsjobs[6];
+  std::vector<fgt::OzGroup> ozgroups;
   std::vector<unsigned char> oztab;
   std::vector<int32_t> ozexp;
   int64_t oz_scr = 0;  // doubles per scratch array
@@ -913,6 +914,49 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
       ex.oz = 1;
       std::map<std::tuple<int, int, int>, std::pair<int64_t, int32_t>> cls;
       std::vector<double> Bm;
+      // the digit planes of Bm (dm.Q x dm.N, row-major) in the layout the products kernel copies:
+      // per column part and 16-deep step, six BF16 planes of Np rows in the K-major core-matrix layout
+      auto slice_bm = [&](const fgt::OzDims &dm) -> std::pair<int64_t, int32_t> {
+        auto B = [&](int q, int n) -> double & { return Bm[(size_t)q * dm.N + n]; };
+        const int64_t boff = (int64_t)oztab.size();
+        const int32_t eoff = (int32_t)ozexp.size();
+        const size_t bbytes = (size_t)fgt::kOzSlices * dm.Np * 32;
+        oztab.resize(oztab.size() + (size_t)dm.P * dm.nks * bbytes, 0);
+        for (int pt = 0; pt < dm.P; ++pt)
+          for (int nl = 0; nl < dm.Np; ++nl) {
+            const int c = pt * dm.Nc + nl;
+            const bool valid = nl < dm.Nc && c < dm.N;
+            double mx = 0.0;
+            if (valid)
+              for (int q = 0; q < dm.Q; ++q) mx = std::max(mx, std::fabs(B(q, c)));
+            int f = 0;
+            if (mx > 0) std::frexp(mx, &f);  // |B(q, c)| < 2^f
+            ozexp.push_back(f);
+            if (mx == 0) continue;
+            for (int q = 0; q < dm.Q; ++q) {
+              long long v = std::llrint(std::ldexp(B(q, c), 47 - f));  // |v| <= 2^47, exact scaling
+              int dg[fgt::kOzSlices];
+              for (int sl = fgt::kOzSlices - 1; sl >= 1; --sl) {
+                const int lo = (int)((v + 128) & 255) - 128;
+                dg[sl] = lo;
+                v = (v - lo) / 256;
+              }
+              dg[0] = (int)v;
+              const int ks = q / 16, kk = q % 16;
+              for (int sl = 0; sl < fgt::kOzSlices; ++sl) {
+                const float fv = (float)dg[sl];
+                uint32_t bits;
+                std::memcpy(&bits, &fv, 4);
+                const uint16_t h = (uint16_t)(bits >> 16);  // exact: |digit| <= 128
+                const size_t off = (size_t)boff + ((size_t)(pt * dm.nks + ks) * fgt::kOzSlices + sl) * dm.Np * 32 +
+                                   (size_t)(nl >> 3) * 256 + (size_t)(kk >> 3) * 128 + (size_t)(nl & 7) * 16 +
+                                   (size_t)(kk & 7) * 2;
+                std::memcpy(&oztab[off], &h, 2);
+              }
+            }
+          }
+        return {boff, eoff};
+      };
       auto table = [&](int kind, int K, int mat) -> std::pair<int64_t, int32_t> {
         const auto key = std::make_tuple(kind, K, mat);
         auto it = cls.find(key);
@@ -954,82 +998,140 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
               B(nh + m, I) = -e.y;
             }
         }
-        const int64_t boff = (int64_t)oztab.size();
-        const int32_t eoff = (int32_t)ozexp.size();
-        const size_t bbytes = (size_t)fgt::kOzSlices * dm.Np * 32;
-        oztab.resize(oztab.size() + (size_t)dm.P * dm.nks * bbytes, 0);
-        for (int pt = 0; pt < dm.P; ++pt)
-          for (int nl = 0; nl < dm.Np; ++nl) {
-            const int c = pt * dm.Nc + nl;
-            const bool valid = nl < dm.Nc && c < dm.N;
-            double mx = 0.0;
-            if (valid)
-              for (int q = 0; q < dm.Q; ++q) mx = std::max(mx, std::fabs(B(q, c)));
-            int f = 0;
-            if (mx > 0) std::frexp(mx, &f);  // |B(q, c)| < 2^f
-            ozexp.push_back(f);
-            if (mx == 0) continue;
-            for (int q = 0; q < dm.Q; ++q) {
-              long long v = std::llrint(std::ldexp(B(q, c), 47 - f));  // |v| <= 2^47, exact scaling
-              int dg[fgt::kOzSlices];
-              for (int sl = fgt::kOzSlices - 1; sl >= 1; --sl) {
-                const int lo = (int)((v + 128) & 255) - 128;
-                dg[sl] = lo;
-                v = (v - lo) / 256;
-              }
-              dg[0] = (int)v;
-              const int ks = q / 16, kk = q % 16;
-              for (int sl = 0; sl < fgt::kOzSlices; ++sl) {
-                const float fv = (float)dg[sl];
-                uint32_t bits;
-                std::memcpy(&bits, &fv, 4);
-                const uint16_t h = (uint16_t)(bits >> 16);  // exact: |digit| <= 128
-                const size_t off = (size_t)boff + ((size_t)(pt * dm.nks + ks) * fgt::kOzSlices + sl) * dm.Np * 32 +
-                                   (size_t)(nl >> 3) * 256 + (size_t)(kk >> 3) * 128 + (size_t)(nl & 7) * 16 +
-                                   (size_t)(kk & 7) * 2;
-                std::memcpy(&oztab[off], &h, 2);
-              }
-            }
-          }
-        cls[key] = {boff, eoff};
-        return {boff, eoff};
+        const auto r = slice_bm(dm);
+        cls[key] = r;
+        return r;
       };
       int64_t dig_at[6] = {0, 0, 0, 0, 0, 0}, rexp_at[6] = {0, 0, 0, 0, 0, 0};
+      // the evaluation's first stage reads the anchor's incoming expansion, the same for every block of
+      // the anchor: it is sliced once per anchor, and each block's products read those digit planes
+      std::unordered_map<int32_t, std::pair<int64_t, int32_t>> slot_digits;
       auto add_jobs = [&](int kind, int32_t bi, const fgt::Block &B, int64_t scr, int flags) {
         const int mat = B.mat[(kind == 0 || kind == 5) ? 2 : (kind == 1 || kind == 4) ? 1 : 0];
         const auto tb = table(kind, B.K, mat);
         const fgt::OzDims dm = fgt::oz_dims(kind, B.K, n1, nh);
-        for (int t = 0; t < (dm.R + 127) / 128; ++t) {
+        const int ntile = (dm.R + 127) / 128;
+        const int64_t tile_bytes = (int64_t)dm.nks * fgt::kOzSlices * 128 * 16 * 2;
+        int64_t a0 = dig_at[kind];
+        int32_t r0 = (int32_t)rexp_at[kind];
+        bool slice = true;
+        if (kind == 3) {
+          auto it = slot_digits.find(B.slot);
+          if (it != slot_digits.end()) {
+            a0 = it->second.first;
+            r0 = it->second.second;
+            slice = false;
+          } else {
+            slot_digits[B.slot] = {a0, r0};
+          }
+        }
+        for (int t = 0; t < ntile; ++t) {
           fgt::OzJob j{};
           j.blk = bi;
           j.tile = (int16_t)t;
           j.scr = scr;
-          j.aoff = dig_at[kind];
-          j.roff = (int32_t)rexp_at[kind];
+          j.aoff = a0 + t * tile_bytes;
+          j.roff = r0 + 128 * t;
           j.flags = flags;
-          ozsjobs[kind].push_back(j);  // slicing: part 0 stands for the tile
+          if (slice) ozsjobs[kind].push_back(j);  // slicing: part 0 stands for the tile
           for (int pt = 0; pt < dm.P; ++pt) {
             j.part = (int16_t)pt;
             j.boff = tb.first + (int64_t)pt * dm.nks * fgt::kOzSlices * dm.Np * 32;
             j.eoff = tb.second + pt * dm.Np;
             ozjobs[kind].push_back(j);
           }
-          dig_at[kind] += (int64_t)dm.nks * fgt::kOzSlices * 128 * 16 * 2;
-          rexp_at[kind] += 128;
+        }
+        if (slice) {
+          dig_at[kind] += ntile * tile_bytes;
+          rexp_at[kind] += 128 * ntile;
         }
       };
       // per-block intermediates: the form's and the evaluation's stages reuse the same two arrays
-      std::unordered_map<int32_t, int> per_slot;
-      for (const fgt::Block &b : blocks) per_slot[b.slot]++;
       bool all_sole = true;
       int64_t sf = 0, se = 0;
+      // stage 2 (x1, into the slot) by groups of the anchor's consecutive blocks, their contractions
+      // concatenated up to 160 (the exactness bound) and kOzGroupMax members
+      std::vector<fgt::OzGroup> groups;
+      std::map<std::vector<int32_t>, std::pair<int64_t, int32_t>> gcls;
+      auto group_table = [&](const fgt::OzGroup &g, const std::vector<int32_t> &mats) {
+        std::vector<int32_t> key;
+        for (int m = 0; m < g.n; ++m) {
+          key.push_back(g.K[m]);
+          key.push_back(mats[m]);
+        }
+        auto it = gcls.find(key);
+        if (it != gcls.end()) return it->second;
+        const fgt::OzDims dm = fgt::oz_dims_group(n1, nh, g.q0[g.n]);
+        Bm.assign((size_t)dm.Q * dm.N, 0.0);
+        auto B = [&](int q, int n) -> double & { return Bm[(size_t)q * dm.N + n]; };
+        for (int m = 0; m < g.n; ++m) {  // member m: rows q0 + (c, J1) as in its own stage-2 matrix
+          const int K = g.K[m], q0 = g.q0[m], mat = mats[m];
+          for (int J = 0; J < K; ++J)
+            for (int mm = 0; mm < n1; ++mm) {
+              const C f = Ff[((size_t)(mat + J / k) * n1 + mm) * k + J % k];
+              B(q0 + J, 2 * mm) = f.x;
+              B(q0 + K + J, 2 * mm) = -f.y;
+              B(q0 + J, 2 * mm + 1) = f.y;
+              B(q0 + K + J, 2 * mm + 1) = f.x;
+            }
+        }
+        const auto r = slice_bm(dm);
+        gcls[key] = r;
+        return r;
+      };
+      std::vector<int64_t> block_scr(blocks.size());
       for (size_t b = 0; b < blocks.size(); ++b) {
         const fgt::Block &B = blocks[b];
         const int64_t K = B.K;
-        const bool sole = per_slot[B.slot] == 1;
-        all_sole = all_sole && sole;
-        for (int kind = 0; kind < 3; ++kind) add_jobs(kind, (int32_t)b, B, sf, (kind == 2 && !sole) ? 1 : 0);
+        block_scr[b] = sf;
+        for (int kind = 0; kind < 2; ++kind) add_jobs(kind, (int32_t)b, B, sf, 0);
         sf += std::max<int64_t>(2 * nh * K * K, 2 * (int64_t)n1 * nh * K);
+      }
+      std::vector<std::vector<int32_t>> gmats;
+      for (size_t b = 0; b < blocks.size();) {
+        fgt::OzGroup g{};
+        g.slot = blocks[b].slot;
+        std::vector<int32_t> mats;
+        while (b < blocks.size() && blocks[b].slot == g.slot && g.n < fgt::kOzGroupMax &&
+               g.q0[g.n] + 2 * blocks[b].K <= 160) {
+          g.K[g.n] = blocks[b].K;
+          g.blk[g.n] = (int32_t)b;
+          g.scr[g.n] = block_scr[b];
+          g.q0[g.n + 1] = g.q0[g.n] + 2 * blocks[b].K;
+          mats.push_back(blocks[b].mat[0]);
+          ++g.n;
+          ++b;
+        }
+        groups.push_back(g);
+        gmats.push_back(mats);
+      }
+      std::unordered_map<int32_t, int> groups_per_slot;
+      for (const fgt::OzGroup &g : groups) groups_per_slot[g.slot]++;
+      for (size_t gi = 0; gi < groups.size(); ++gi) {
+        const fgt::OzGroup &g = groups[gi];
+        const bool sole = groups_per_slot[g.slot] == 1;
+        all_sole = all_sole && sole;
+        const auto tb = group_table(g, gmats[gi]);
+        const fgt::OzDims dm = fgt::oz_dims_group(n1, nh, g.q0[g.n]);
+        const int ntile = (dm.R + 127) / 128;
+        const int64_t tile_bytes = (int64_t)dm.nks * fgt::kOzSlices * 128 * 16 * 2;
+        for (int t = 0; t < ntile; ++t) {
+          fgt::OzJob j{};
+          j.blk = (int32_t)gi;
+          j.tile = (int16_t)t;
+          j.aoff = dig_at[2] + t * tile_bytes;
+          j.roff = (int32_t)rexp_at[2] + 128 * t;
+          j.flags = sole ? 0 : 1;
+          ozsjobs[2].push_back(j);
+          for (int pt = 0; pt < dm.P; ++pt) {
+            j.part = (int16_t)pt;
+            j.boff = tb.first + (int64_t)pt * dm.nks * fgt::kOzSlices * dm.Np * 32;
+            j.eoff = tb.second + pt * dm.Np;
+            ozjobs[2].push_back(j);
+          }
+        }
+        dig_at[2] += ntile * tile_bytes;
+        rexp_at[2] += 128 * ntile;
       }
       for (size_t b = 0; b < eblocks.size(); ++b) {
         const fgt::Block &B = eblocks[b];
@@ -1039,6 +1141,7 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
       }
       oz_scr = std::max(sf, se);
       ex.oz_sole = all_sole ? 1 : 0;
+      ozgroups = groups;
       for (int kind = 0; kind < 6; ++kind) {
         ex.oz_njobs[kind] = (int64_t)ozjobs[kind].size();
         ex.oz_nsjobs[kind] = (int64_t)ozsjobs[kind].size();
@@ -1441,6 +1544,7 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   }
   const size_t o_oztab = pack.add("oz_btab", oztab), o_ozexp = pack.add("oz_bexp", ozexp);
   const size_t o_eblocks = pack.add("eval_blocks", eblocks);
+  const size_t o_ozg = pack.add("oz_groups", ozgroups);
   const size_t o_ggrid = pack.add("gather_grid", ggrid);
   std::vector<std::tuple<size_t, size_t, size_t, int64_t>> step_off;  // items, qf, qh, n
   for (size_t i = 0; i < merge_h.size(); ++i) {
@@ -1536,6 +1640,7 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   ex.oz_btab = (const unsigned char *)at(o_oztab);
   ex.oz_bexp = (const int32_t *)at(o_ozexp);
   ex.eval_blocks = (const fgt::Block *)at(o_eblocks);
+  ex.oz_groups = (const fgt::OzGroup *)at(o_ozg);
   ex.gather_grid = ex.grid_nb > 0 ? (const int32_t *)at(o_ggrid) : nullptr;
   ex.sig_maps_ready = 0;
   if (ex.sig_order == 1) {

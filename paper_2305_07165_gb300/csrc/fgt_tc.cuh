@@ -50,6 +50,20 @@ __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uin
                : "memory");
 }
 
+// tcgen05.ld of 4 or 8 consecutive columns for the warp's 32 lanes, without the wait (several loads
+// in flight, then one tmem_wait_ld before the registers are read)
+__device__ __forceinline__ void tmem_ld4_nw(uint32_t addr, uint32_t *v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+               : "r"(addr));
+}
+__device__ __forceinline__ void tmem_ld8_nw(uint32_t addr, uint32_t *v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(addr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 template <int N>
 __device__ __forceinline__ void tmem_ld(uint32_t addr, uint32_t (&v)[N]) {
   if constexpr (N == 4) {

@@ -2,7 +2,8 @@
 digit planes of every stage's 1D matrix, read back from a host-only plan, reconstruct the real form
 of the block's complex 1D matrix (rebuilt here from the plan's FP64 tables) to the 47-bit rounding
 the slicing promises, every digit is a balanced 8-bit one, padding is zero, and the jobs cover
-every (row, column) of every stage of every block exactly once."""
+every (row, column) of every stage of every block exactly once.  The form's last stage runs over
+groups of an anchor's blocks (their contractions concatenated), which must take every block once."""
 import numpy as np
 import pytest
 
@@ -14,6 +15,8 @@ BLOCK = np.dtype([("slot", "<i4"), ("K", "<i4"), ("dl", "<i4"), ("flags", "<i4")
                   ("pad", "<i4"), ("leaf0", "<i8")])
 JOB = np.dtype([("blk", "<i4"), ("tile", "<i2"), ("part", "<i2"), ("scr", "<i8"), ("boff", "<i8"),
                 ("aoff", "<i8"), ("eoff", "<i4"), ("roff", "<i4"), ("flags", "<i4"), ("pad", "<i4")])
+GROUP = np.dtype([("slot", "<i4"), ("n", "<i4"), ("K", "<i4", 10), ("q0", "<i4", 11), ("blk", "<i4", 10),
+                  ("pad", "<i4"), ("scr", "<i8", 10)])
 S = 6
 
 
@@ -54,6 +57,18 @@ def real_form(kind, blk, k, n1, nh, tab):
     return B
 
 
+def group_form(g, blocks, k, n1, nh, tab):
+    """Stage 2 over a group: the members' real-form matrices stacked along the contraction."""
+    Q = int(g["q0"][g["n"]])
+    B = np.zeros((Q, 2 * n1))
+    for m in range(int(g["n"])):
+        b = blocks[g["blk"][m]]
+        assert int(b["K"]) == int(g["K"][m]) and int(b["slot"]) == int(g["slot"])
+        q0 = int(g["q0"][m])
+        B[q0:q0 + 2 * int(b["K"])] = real_form(2, b, k, n1, nh, tab)
+    return B
+
+
 def bf16_to_float(h):
     return (h.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
 
@@ -72,20 +87,32 @@ def test_sliced_digit_tables(name, k, delta, tol, bc):
     bexp = hp.array("oz_bexp", np.int32)
     blocks = {0: hp.array("blocks", BLOCK), 1: hp.array("eval_blocks", BLOCK)}
     total = 0
+    groups = hp.array("oz_groups", GROUP)
+    # the groups of stage 2 take every form block once, members of one slot, contraction <= 160
+    members = sorted(int(b) for g in groups for b in g["blk"][: g["n"]])
+    assert members == list(range(len(blocks[0])))
+    for g in groups:
+        assert 1 <= g["n"] <= 10 and g["q0"][0] == 0 and g["q0"][g["n"]] <= 160
+        assert all(g["q0"][m + 1] - g["q0"][m] == 2 * g["K"][m] for m in range(g["n"]))
     for kind in range(6):
         jobs = hp.array(f"oz_jobs{kind}", JOB)
-        blks = blocks[0 if kind < 3 else 1]
+        blks = groups if kind == 2 else blocks[0 if kind < 3 else 1]
         covered, checked = {}, set()
         for j in jobs:
             b = blks[j["blk"]]
-            K = int(b["K"])
-            R, Q, N, P, Nc, Np, nks = dims(kind, K, n1, nh)
+            if kind == 2:
+                R, Q, N, P, Nc, Np, nks = dims(2, 8, n1, nh)
+                Q = int(b["q0"][b["n"]])
+                nks = -(-Q // 16)
+            else:
+                K = int(b["K"])
+                R, Q, N, P, Nc, Np, nks = dims(kind, K, n1, nh)
             assert 0 <= j["tile"] < -(-R // 128) and 0 <= j["part"] < P
             covered.setdefault(int(j["blk"]), set()).add((int(j["tile"]), int(j["part"])))
             if (int(j["boff"]), int(j["eoff"])) in checked:   # tiles of a block share its table
                 continue
             checked.add((int(j["boff"]), int(j["eoff"])))
-            B = real_form(kind, b, k, n1, nh, tab)
+            B = group_form(b, blocks[0], k, n1, nh, tab) if kind == 2 else real_form(kind, b, k, n1, nh, tab)
             Bp = np.zeros((nks * 16, Np))                     # this part's columns, padded
             c = int(j["part"]) * Nc + np.arange(Np)
             ok = (np.arange(Np) < Nc) & (c < N)
@@ -101,16 +128,23 @@ def test_sliced_digit_tables(name, k, delta, tol, bc):
             val = np.ldexp(np.tensordot(2.0 ** (-7 - 8 * np.arange(S)), d, axes=1), f[None, :])
             assert np.all(np.abs(val - Bp) <= np.ldexp(1.0, f - 48)[None, :]), kind
         sj = hp.array(f"oz_slice_jobs{kind}", JOB)
-        assert {(int(j["blk"]), int(j["tile"])) for j in sj} == {(b, t) for b, ts in covered.items() for t, _ in ts}
-        assert len(sj) == len({(int(j["blk"]), int(j["tile"])) for j in sj})
-        ends = sorted((int(j["aoff"]), int(j["aoff"]) + dims(kind, int(blks[j["blk"]]["K"]), n1, nh)[6] * S * 4096)
-                      for j in sj)
+        # the first evaluation stage slices each anchor's expansion once (the operand is the slot);
+        # every other stage slices each block's own operand
+        owner = (lambda b: int(blks[b]["slot"])) if kind == 3 else (lambda b: int(b))
+        assert ({(owner(j["blk"]), int(j["tile"])) for j in sj} ==
+                {(owner(b), t) for b, ts in covered.items() for t, _ in ts})
+        assert len(sj) == len({(owner(j["blk"]), int(j["tile"])) for j in sj})
+        def steps(bi):
+            if kind == 2:
+                return -(-int(blks[bi]["q0"][blks[bi]["n"]]) // 16)
+            return dims(kind, int(blks[bi]["K"]), n1, nh)[6]
+        ends = sorted((int(j["aoff"]), int(j["aoff"]) + steps(j["blk"]) * S * 4096) for j in sj)
         assert all(a1 <= b0 for (_, a1), (b0, _) in zip(ends, ends[1:]))      # digit planes do not overlap
+        where = {(owner(x["blk"]), int(x["tile"])): (int(x["aoff"]), int(x["roff"])) for x in sj}
         for j in jobs:   # the products read their tile's planes and exponents
-            m = sj[(sj["blk"] == j["blk"]) & (sj["tile"] == j["tile"])][0]
-            assert (j["aoff"], j["roff"]) == (m["aoff"], m["roff"])
+            assert (int(j["aoff"]), int(j["roff"])) == where[(owner(j["blk"]), int(j["tile"]))]
         for bi in range(len(blks)):
-            R, Q, N, P, *_ = dims(kind, int(blks[bi]["K"]), n1, nh)
+            R, Q, N, P, *_ = dims(kind, 8 if kind == 2 else int(blks[bi]["K"]), n1, nh)
             assert covered.get(bi) == {(t, p) for t in range(-(-R // 128)) for p in range(P)}
         total += len(jobs)
     assert total == info["n_sliced_jobs"]
