@@ -568,7 +568,8 @@ def run_hierarchical(F, torch, w, sigma, out, flush):
             ms = prof.get(ph, 0.0) / max(nprof, 1)
             nbytes = n_items * (2 ** w.d + 1) * slot_bytes
             gbs = nbytes / (ms / 1e3) / 1e9 if ms > 0 else None
-            row[ph] = {"ms": ms, "bytes": nbytes, "achieved_gbs": gbs, "frac": gbs / peak if gbs else None}
+            row[ph] = {"ms": ms, "bytes": nbytes, "bytes_kind": "algorithmic (2^d child slots + the parent's, "
+                       "per item)", "achieved_gbs": gbs, "frac": gbs / peak if gbs else None}
         res[name] = row
     return res
 

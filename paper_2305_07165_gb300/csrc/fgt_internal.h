@@ -35,7 +35,8 @@ struct OzJob {
   int32_t eoff;      // offset of the 1D matrix's column exponents (this part)
   int32_t roff;      // offset of the tile's 128 row exponents
   int32_t flags;     // bit 0: add into the output (another block writes the same slot / leaf)
-  int32_t pad;
+  int16_t nks;       // 16-deep steps of the contraction (copied here so that the copy and MMA warps
+  int16_t np;        //   need no dependent loads), and the part's padded column count
 };
 
 // The form's last sliced stage (the x1 contraction into the anchor's slot) for up to kOzGroupMax

@@ -789,6 +789,16 @@ __device__ __forceinline__ double dfl_to_f64(dfl a) {
   return i64_to_f64_scaled(V, eh - 150 - 29);
 }
 
+// a + b in double-float
+__device__ __forceinline__ dfl dfl_add(dfl a, dfl b) {
+  const float sm = a.hi + b.hi, bb = sm - a.hi;
+  float t = (a.hi - (sm - bb)) + (b.hi - bb);
+  t += a.lo + b.lo;
+  const float hi = sm + t;
+  return dfl{hi, t - (hi - sm)};
+}
+__device__ __forceinline__ dfl dfl_neg(dfl a) { return dfl{-a.hi, -a.lo}; }
+
 // a b + c in double-float
 __device__ __forceinline__ dfl dfl_fma(dfl a, dfl b, dfl c) {
   const float p = a.hi * b.hi;
@@ -3000,6 +3010,74 @@ __global__ void __launch_bounds__(256) gather2_kernel(const GatherSeg *__restric
   gather2_body<D, R, W>(segs, Pf, Ph, phi, psi, n1, nh, slot_size, psi_pitch, blockIdx.x, blockIdx.y);
 }
 
+// The run form (gather2) for FP64 expansions with double-float products (FP64-TC plans, 3D): the
+// phases of each line (o_2, o_3) formed in FP64, every factor and source split into FP32 pairs with
+// integer operations, the 9 (W + 2) + 3 W complex products on the FP32 pipes (about 2^-47 each), the
+// result rounded back to FP64.  Used where the stencil form does not apply (the cutoff grid not
+// full, or more than 8 boxes a side).
+template <int W>
+__global__ void __launch_bounds__(256) gather2df_kernel(const GatherSeg *__restrict__ segs,
+                                                        const double2 *__restrict__ Pf, const double2 *__restrict__ Ph,
+                                                        const double2 *__restrict__ phi, double2 *__restrict__ psi,
+                                                        int n1, int nh, int64_t slot_size) {
+  static_assert(W <= kSegW, "run longer than a GatherSeg");
+  __shared__ GatherSeg sg;
+  {
+    const int32_t *g = reinterpret_cast<const int32_t *>(segs + blockIdx.x);
+    int32_t *sd = reinterpret_cast<int32_t *>(&sg);
+    for (int e = threadIdx.x; e < (int)(sizeof(GatherSeg) / sizeof(int32_t)); e += blockDim.x) sd[e] = g[e];
+  }
+  __syncthreads();
+  const int64_t idx = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+  if (idx >= slot_size) return;
+  int m1, m2, m3;
+  mode_index<3>(idx, n1, m1, m2, m3);
+  dfl wr[W + 2], wi[W + 2];
+#pragma unroll
+  for (int i = 0; i < W + 2; ++i) wr[i] = wi[i] = dfl{0.f, 0.f};
+#pragma unroll
+  for (int l = 0; l < 9; ++l) {
+    const int32_t *sl = sg.src[l];
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < W + 2; ++i) any = any || sl[i] >= 0;
+    if (!any) continue;
+    double2 f;
+    {
+      const double2 py = Pf[(l % 3) * n1 + m2], pz = Ph[(l / 3) * nh + m3];
+      f = make_double2(py.x * pz.x - py.y * pz.y, py.x * pz.y + py.y * pz.x);
+    }
+    const dfl fr = dfl_from_f64(f.x), fi = dfl_from_f64(f.y), nfi = dfl_neg(fi);
+#pragma unroll
+    for (int i = 0; i < W + 2; ++i) {
+      if (sl[i] < 0) continue;
+      const double2 v = phi[(int64_t)sl[i] * slot_size + idx];
+      const dfl vr = dfl_from_f64(v.x), vi = dfl_from_f64(v.y);
+      wr[i] = dfl_fma(nfi, vi, dfl_fma(fr, vr, wr[i]));
+      wi[i] = dfl_fma(fi, vr, dfl_fma(fr, vi, wi[i]));
+    }
+  }
+  dfl pxr[3], pxi[3];
+#pragma unroll
+  for (int o = 0; o < 3; ++o) {
+    const double2 p = Pf[o * n1 + m1];
+    pxr[o] = dfl_from_f64(p.x);
+    pxi[o] = dfl_from_f64(p.y);
+  }
+#pragma unroll
+  for (int t = 0; t < W; ++t) {
+    if (sg.tgt[t] < 0) continue;
+    dfl ar{0.f, 0.f}, ai{0.f, 0.f};
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {  // source x0 - 1 + t + o seen from target x0 + t
+      ar = dfl_fma(dfl_neg(pxi[o]), wi[t + o], dfl_fma(pxr[o], wr[t + o], ar));
+      ai = dfl_fma(pxi[o], wr[t + o], dfl_fma(pxr[o], wi[t + o], ai));
+    }
+    double2 *op = psi + (int64_t)sg.tgt[t] * slot_size + idx;
+    if (FGT_OK_PTR(op)) *op = make_double2(dfl_to_f64(ar), dfl_to_f64(ai));
+  }
+}
+
 // The same gather for FP64 expansions when every box of the cutoff level is an anchor (3D, NB = 4
 // or 8 boxes a side): the phase is a product of one factor per axis and the sources of a target are
 // its 3^3 neighbours on the grid, so the sum is a separable 3-point stencil per mode, applied axis by
@@ -3015,7 +3093,7 @@ template <int NB, int MT, bool DF>
 __global__ void __launch_bounds__(256) gather3_kernel(const int32_t *__restrict__ gslot, const double2 *__restrict__ Pf,
                                                       const double2 *__restrict__ Ph, const double2 *__restrict__ phi,
                                                       double2 *__restrict__ psi, int n1, int nh, int64_t slot_size,
-                                                      int periodic) {
+                                                      int periodic, int sym) {
   static_assert(256 % MT == 0, "modes per CTA must divide the block");
   constexpr int NBOX = NB * NB * NB, BSTEP = 256 / MT;
   extern __shared__ __align__(16) unsigned char g3_raw[];
@@ -3061,6 +3139,25 @@ __global__ void __launch_bounds__(256) gather3_kernel(const int32_t *__restrict_
     const int ib = cur * NBOX * MT, ob = (1 - cur) * NBOX * MT;
     for (int b = b0; b < NBOX; b += BSTEP) {
       const int x = (b / stride) % NB;
+      if constexpr (DF) {
+        if (sym) {
+          // P(0) = 1 and P(+1) = conj P(-1) = (pr, -pi): P(-1) l + P(+1) r = pr (l + r) + i pi (l - r),
+          // 4 double-float products instead of 12
+          const int xl = x - 1, xr = x + 1;
+          float4 l = make_float4(0.f, 0.f, 0.f, 0.f), r = l;
+          if (xl >= 0 || periodic) l = buf[ib + (b + (((xl + NB) % NB) - x) * stride) * MT + j];
+          if (xr < NB || periodic) r = buf[ib + (b + (((xr + NB) % NB) - x) * stride) * MT + j];
+          const float4 c = buf[ib + b * MT + j];
+          const dfl sr = dfl_add(dfl{l.x, l.y}, dfl{r.x, r.y}), si = dfl_add(dfl{l.z, l.w}, dfl{r.z, r.w});
+          const dfl dr_ = dfl_add(dfl{l.x, l.y}, dfl_neg(dfl{r.x, r.y}));
+          const dfl di_ = dfl_add(dfl{l.z, l.w}, dfl_neg(dfl{r.z, r.w}));
+          const dfl qr = pr[ax][0], qi = pi[ax][0];
+          const dfl orr = dfl_fma(dfl_neg(qi), di_, dfl_fma(qr, sr, dfl{c.x, c.y}));
+          const dfl oii = dfl_fma(qi, dr_, dfl_fma(qr, si, dfl{c.z, c.w}));
+          buf[ob + b * MT + j] = make_float4(orr.hi, orr.lo, oii.hi, oii.lo);
+          continue;
+        }
+      }
       dfl ar{0.f, 0.f}, ai{0.f, 0.f};
       double dr = 0.0, di = 0.0;
 #pragma unroll
@@ -3252,6 +3349,63 @@ __device__ __forceinline__ void near2_body(const NearPair *__restrict__ pairs, c
 }
 
 
+// The same 3D near field with double-float products (FP64-TC plans): σ and the three tables split
+// into FP32 pairs on load (integer operations), the three passes on the FP32 pipes (about 2^-47 a
+// product), each result rounded back to FP64 for the atomic addition into u.
+__global__ void __launch_bounds__(128) near2df_kernel(const NearPair *__restrict__ pairs,
+                                                      const double *__restrict__ tab,
+                                                      const int16_t *__restrict__ band,
+                                                      const double *__restrict__ sigma, double *__restrict__ u, int k) {
+  extern __shared__ float2 smf[];
+  const int kk = k * k, np = kk * k;
+  float2 *s0 = smf, *A = smf + np, *B = A + np, *T = B + np;
+  int16_t *bd = reinterpret_cast<int16_t *>(T + 3 * kk);  // [3][k][2]
+  const NearPair pr = pairs[blockIdx.x];
+  const double *sg = sigma + pr.src * np;
+  auto put = [](float2 *p, double x) {
+    const dfl v = dfl_from_f64(x);
+    *p = make_float2(v.hi, v.lo);
+  };
+  for (int e = threadIdx.x; e < np; e += blockDim.x) put(s0 + e, FGT_OK_PTR(sg + e) ? __ldg(sg + e) : 0.0);
+  for (int e = threadIdx.x; e < 3 * kk; e += blockDim.x) {
+    const int a = e / kk;
+    put(T + e, __ldg(tab + (int64_t)pr.tab[a] * kk + (e - a * kk)));
+  }
+  for (int e = threadIdx.x; e < 3 * 2 * k; e += blockDim.x) {
+    const int a = e / (2 * k);
+    bd[e] = __ldg(band + (int64_t)pr.tab[a] * 2 * k + (e - a * 2 * k));
+  }
+  __syncthreads();
+  auto ld = [](const float2 *p) { const float2 v = *p; return dfl{v.x, v.y}; };
+  for (int e = threadIdx.x; e < np; e += blockDim.x) {  // A[j3][j2][t1] = sum_j1 T1[t1][j1] s0[j3][j2][j1]
+    const int row = e / k, t1 = e - row * k;
+    const float2 *sp = s0 + row * k, *tp = T + t1 * k;
+    dfl a{0.f, 0.f};
+    for (int j = bd[2 * t1]; j <= bd[2 * t1 + 1]; ++j) a = dfl_fma(ld(tp + j), ld(sp + j), a);
+    A[e] = make_float2(a.hi, a.lo);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < np; e += blockDim.x) {  // B[j3][t2][t1] = sum_j2 T2[t2][j2] A[j3][j2][t1]
+    const int j3 = e / kk, rem = e - j3 * kk, t2 = rem / k, t1 = rem - t2 * k;
+    const float2 *tp = T + kk + t2 * k, *ap = A + j3 * kk + t1;
+    const int16_t *b2 = bd + 2 * k + 2 * t2;
+    dfl a{0.f, 0.f};
+    for (int j = b2[0]; j <= b2[1]; ++j) a = dfl_fma(ld(tp + j), ld(ap + j * k), a);
+    B[e] = make_float2(a.hi, a.lo);
+  }
+  __syncthreads();
+  double *ut = u + pr.tgt * np;
+  for (int e = threadIdx.x; e < np; e += blockDim.x) {  // u[t3][t2][t1] += sum_j3 T3[t3][j3] B[j3][t2][t1]
+    const int t3 = e / kk, rem = e - t3 * kk;
+    const float2 *tp = T + 2 * kk + t3 * k, *bp = B + rem;
+    const int16_t *b3 = bd + 4 * k + 2 * t3;
+    if (b3[1] < b3[0]) continue;
+    dfl a{0.f, 0.f};
+    for (int j = b3[0]; j <= b3[1]; ++j) a = dfl_fma(ld(tp + j), ld(bp + j * kk), a);
+    if (FGT_OK_PTR(ut + e)) atomicAdd(ut + e, dfl_to_f64(a));
+  }
+}
+
 template <int D>
 __global__ void __launch_bounds__(128) near2_kernel(const NearPair *__restrict__ pairs, const double *__restrict__ tab,
                                                     const int16_t *__restrict__ band,
@@ -3428,10 +3582,16 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
   auto launch_near = [&](cudaStream_t ns) -> cudaError_t {
     const int np = D == 3 ? e.k * e.k * e.k : e.k * e.k;
     const size_t nsm = sizeof(double) * (3 * (size_t)np + (size_t)D * e.k * e.k) + sizeof(int16_t) * 2 * D * e.k;
-    cudaError_t r = cudaFuncSetAttribute(near2_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nsm);
+    // FP64-TC plans in 3D: the near field's products in double-float arithmetic (same shared memory)
+    const bool df = D == 3 && e.tc64 != 0;
+    cudaError_t r = df ? cudaFuncSetAttribute(near2df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nsm)
+                       : cudaFuncSetAttribute(near2_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nsm);
     if (r != cudaSuccess) return r;
     if (e.events) cudaEventRecord(e.events[10], ns);
-    near2_kernel<D><<<(unsigned)e.n_near_pairs, 128, nsm, ns>>>(e.near_pairs, e.near_tab, e.near_band, sigma, u, e.k);
+    if (df)
+      near2df_kernel<<<(unsigned)e.n_near_pairs, 128, nsm, ns>>>(e.near_pairs, e.near_tab, e.near_band, sigma, u, e.k);
+    else
+      near2_kernel<D><<<(unsigned)e.n_near_pairs, 128, nsm, ns>>>(e.near_pairs, e.near_tab, e.near_band, sigma, u, e.k);
     r = cudaGetLastError();
     if (e.events) cudaEventRecord(e.events[11], ns);
     return r;
@@ -3566,7 +3726,14 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
         return err;
       g3<<<(unsigned)((ss + mt - 1) / mt), 256, gsm, st>>>(
           e.gather_grid, reinterpret_cast<const double2 *>(e.Pf), reinterpret_cast<const double2 *>(e.Ph),
-          reinterpret_cast<const double2 *>(phi), reinterpret_cast<double2 *>(psi), n1, nh, ss, e.grid_periodic);
+          reinterpret_cast<const double2 *>(phi), reinterpret_cast<double2 *>(psi), n1, nh, ss, e.grid_periodic,
+          e.gather_sym);
+    } else if (D == 3 && sizeof(R) == 8 && e.tc64 && e.n_gather_segs > 0 && e.psi_pitch == 0) {
+      // FP64-TC: the run form with double-float products
+      auto g2 = (e.seg_w > 0 && e.seg_w <= 4) ? gather2df_kernel<4> : gather2df_kernel<kSegW>;
+      g2<<<dim3((unsigned)e.n_gather_segs, tiles), 256, 0, st>>>(
+          e.gather_segs, reinterpret_cast<const double2 *>(e.Pf), reinterpret_cast<const double2 *>(e.Ph),
+          reinterpret_cast<const double2 *>(phi), reinterpret_cast<double2 *>(psi), n1, nh, ss);
     } else if (e.n_gather_segs > 0) {
       // runs of at most 4 targets (4 boxes a side at the cutoff level): the 4-wide kernel, which
       // does not spend products on the empty positions of an 8-wide run

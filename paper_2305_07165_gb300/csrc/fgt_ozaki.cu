@@ -145,13 +145,14 @@ __device__ __forceinline__ uint32_t bf16_pair(int d0, int d1) {
 // Row r's fixed part of its operand addresses, then the element index of q.
 struct RowAddr {
   int64_t base;
-  int a, b;  // kind 0: leaf index part (o2 nl + o1) and node offset (j2 k + j1)
+  int a, b;  // kind 0: leaf index part (o2 nl + o1) and node offset (j2 k + j1); kind 2: m3, m2
+  int K;     // kind 2, a group of one block: its K (base is then the row's base), else 0
 };
 
 template <int KIND>
 __device__ __forceinline__ RowAddr row_addr(int r, const OzJob &job, const Block &blk, const OzArgs &a) {
   const int K = blk.K, k = a.k, n1 = a.n1, nh = a.nh, nl = 1 << blk.dl;
-  RowAddr ra{0, 0, 0};
+  RowAddr ra{0, 0, 0, 0};
   if constexpr (KIND == 0) {
     const int J2 = div_K(r, blk, a), J1 = r - J2 * K, o2 = div_k(J2, a), o1 = div_k(J1, a);
     ra.a = o2 * nl + o1;
@@ -185,6 +186,10 @@ __device__ __forceinline__ int64_t a_index(const RowAddr &ra, int q, const int64
     const int c = q >= K, J2 = q - c * K;
     return ra.base + (int64_t)c * K * K + (int64_t)J2 * K;
   } else if constexpr (KIND == 2) {
+    if (ra.K > 0) {  // one member: as for a single block
+      const int c = q >= ra.K, J1 = q - c * ra.K;
+      return ra.base + (int64_t)c * nh * ra.K + J1;
+    }
     int j = 0;  // the member whose contraction holds q
     while (j + 1 < g->n && q >= g->q0[j + 1]) ++j;
     const int Kj = g->K[j], ql = q - g->q0[j], c = ql >= Kj, J1 = ql - c * Kj;
@@ -256,7 +261,13 @@ __global__ void __launch_bounds__(kWarps * 32) oz_slice_kernel(const OzArgs a, c
   const int rl = 8 * warp + (lane >> 2), sub = lane & 3;
   const int rg = (int)job.tile * 128 + rl;
   const bool rvalid = rg < dm.R;
-  const RowAddr ra = row_addr<KIND>(rvalid ? rg : 0, job, blk, a);
+  RowAddr ra = row_addr<KIND>(rvalid ? rg : 0, job, blk, a);
+  if constexpr (KIND == 2) {
+    if (grp.n == 1) {
+      ra.K = grp.K[0];
+      ra.base = grp.scr[0] + ((int64_t)ra.b * 2 * a.nh + ra.a) * ra.K;  // (m2 2 nh + m3) K
+    }
+  }
   int ebr = 0;
   if (rvalid)
     for (int q = 2 * sub; q < dm.Q; q += 8) {
@@ -346,11 +357,12 @@ __global__ void __launch_bounds__(kThreads, 1) oz_mma_kernel(const OzArgs a, con
     // ---- copies: every step of every job, in order, through the ring
     if (lane == 0) {
       int g = 0;  // steps issued so far (all jobs)
+      OzJob next = nmine > 0 ? jobs[blockIdx.x] : OzJob{};
       for (int li = 0; li < nmine && !*abort_flag; ++li) {
-        const OzJob job = jobs[blockIdx.x + (int64_t)li * gridDim.x];
-        const OzDims dm = job_dims<KIND>(job, a);
-        const uint32_t bbytes = (uint32_t)(kOzSlices * dm.Np * 32);
-        for (int ks = 0; ks < dm.nks; ++ks, ++g) {
+        const OzJob job = next;
+        if (li + 1 < nmine) next = jobs[blockIdx.x + (int64_t)(li + 1) * gridDim.x];  // in flight meanwhile
+        const uint32_t bbytes = (uint32_t)(kOzSlices * job.np * 32);
+        for (int ks = 0; ks < job.nks; ++ks, ++g) {
           const int st = g % kNst;
           if (g >= kNst && !mbar_wait(smem_addr(empty + st), (uint32_t)((g / kNst - 1) & 1))) {
             *abort_flag = 1;
@@ -372,9 +384,11 @@ __global__ void __launch_bounds__(kThreads, 1) oz_mma_kernel(const OzArgs a, con
     // ---- products: 6 MMAs a step (A's plane s against B's planes 0 .. 5 - s, one N = (6 - s) Np MMA)
     if (lane == 0) {
       int g = 0;
+      OzJob next = nmine > 0 ? jobs[blockIdx.x] : OzJob{};
       for (int li = 0; li < nmine && !*abort_flag; ++li) {
-        const OzJob job = jobs[blockIdx.x + (int64_t)li * gridDim.x];
-        const OzDims dm = job_dims<KIND>(job, a);
+        const OzJob job = next;
+        if (li + 1 < nmine) next = jobs[blockIdx.x + (int64_t)(li + 1) * gridDim.x];
+        const int Np = job.np, nks = job.nks;
         const int b = li & 1;
         if (li >= 2 && !mbar_wait(smem_addr(tempty + b), (uint32_t)((li / 2 - 1) & 1))) {
           *abort_flag = 1;
@@ -384,10 +398,10 @@ __global__ void __launch_bounds__(kThreads, 1) oz_mma_kernel(const OzArgs a, con
         tc_fence_after();
         uint32_t idesc[kOzSlices];
 #pragma unroll
-        for (int s = 0; s < kOzSlices; ++s) idesc[s] = idesc_bf16(128, (kOzSlices - s) * dm.Np);
+        for (int s = 0; s < kOzSlices; ++s) idesc[s] = idesc_bf16(128, (kOzSlices - s) * Np);
         const uint32_t d0 = tmem + (uint32_t)(b * kAccCols);
         bool ok = true;
-        for (int ks = 0; ks < dm.nks; ++ks, ++g) {
+        for (int ks = 0; ks < nks; ++ks, ++g) {
           const int st = g % kNst;
           if (!mbar_wait(smem_addr(full + st), (uint32_t)((g / kNst) & 1))) {
             ok = false;
@@ -397,7 +411,7 @@ __global__ void __launch_bounds__(kThreads, 1) oz_mma_kernel(const OzArgs a, con
           const uint32_t aa = smem_addr(sA + st * kAStage), ba = smem_addr(sB + st * kBStage);
 #pragma unroll
           for (int s = 0; s < kOzSlices; ++s)
-            umma_bf16(d0 + (uint32_t)(s * dm.Np), umma_desc(aa + s * kAPlane, 256), umma_desc(ba, 256), idesc[s],
+            umma_bf16(d0 + (uint32_t)(s * Np), umma_desc(aa + s * kAPlane, 256), umma_desc(ba, 256), idesc[s],
                       (ks > 0 || s > 0) ? 1u : 0u);
           umma_commit(smem_addr(empty + st));
         }

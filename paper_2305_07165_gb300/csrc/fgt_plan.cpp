@@ -1033,6 +1033,8 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
           j.aoff = a0 + t * tile_bytes;
           j.roff = r0 + 128 * t;
           j.flags = flags;
+          j.nks = (int16_t)dm.nks;
+          j.np = (int16_t)dm.Np;
           if (slice) ozsjobs[kind].push_back(j);  // slicing: part 0 stands for the tile
           for (int pt = 0; pt < dm.P; ++pt) {
             j.part = (int16_t)pt;
@@ -1122,6 +1124,8 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
           j.aoff = dig_at[2] + t * tile_bytes;
           j.roff = (int32_t)rexp_at[2] + 128 * t;
           j.flags = sole ? 0 : 1;
+          j.nks = (int16_t)dm.nks;
+          j.np = (int16_t)dm.Np;
           ozsjobs[2].push_back(j);
           for (int pt = 0; pt < dm.P; ++pt) {
             j.part = (int16_t)pt;
@@ -1265,6 +1269,16 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
         Ph.push_back(C{(decltype(C::x))v.real(), (decltype(C::x))v.imag()});
       }
   }
+
+  // the stencil gather's symmetric form needs the offset-0 factors to be 1 and the +1 factors the
+  // conjugates of the -1 ones, exactly (true of polar(1, +-theta), checked rather than assumed)
+  ex.gather_sym = 1;
+  for (int a = 0; a < n1; ++a)
+    ex.gather_sym &= (Pf[(size_t)n1 + a].x == 1 && Pf[(size_t)n1 + a].y == 0 && Pf[(size_t)2 * n1 + a].x == Pf[a].x &&
+                      Pf[(size_t)2 * n1 + a].y == -Pf[a].y) ? 1 : 0;
+  for (int b = 0; b < nh; ++b)
+    ex.gather_sym &= (Ph[(size_t)nh + b].x == 1 && Ph[(size_t)nh + b].y == 0 && Ph[(size_t)2 * nh + b].x == Ph[b].x &&
+                      Ph[(size_t)2 * nh + b].y == -Ph[b].y) ? 1 : 0;
 
   // ---- hierarchical merge / push lists and phases
   struct StepHost { std::vector<fgt::TreeShift> items; std::vector<C> qf, qh; };

@@ -14,7 +14,7 @@ F = pytest.importorskip("paper_2305_07165_gb300")
 BLOCK = np.dtype([("slot", "<i4"), ("K", "<i4"), ("dl", "<i4"), ("flags", "<i4"), ("mat", "<i4", 3),
                   ("pad", "<i4"), ("leaf0", "<i8")])
 JOB = np.dtype([("blk", "<i4"), ("tile", "<i2"), ("part", "<i2"), ("scr", "<i8"), ("boff", "<i8"),
-                ("aoff", "<i8"), ("eoff", "<i4"), ("roff", "<i4"), ("flags", "<i4"), ("pad", "<i4")])
+                ("aoff", "<i8"), ("eoff", "<i4"), ("roff", "<i4"), ("flags", "<i4"), ("nks", "<i2"), ("np", "<i2")])
 GROUP = np.dtype([("slot", "<i4"), ("n", "<i4"), ("K", "<i4", 10), ("q0", "<i4", 11), ("blk", "<i4", 10),
                   ("pad", "<i4"), ("scr", "<i8", 10)])
 S = 6
@@ -108,6 +108,7 @@ def test_sliced_digit_tables(name, k, delta, tol, bc):
                 K = int(b["K"])
                 R, Q, N, P, Nc, Np, nks = dims(kind, K, n1, nh)
             assert 0 <= j["tile"] < -(-R // 128) and 0 <= j["part"] < P
+            assert (int(j["nks"]), int(j["np"])) == (nks, Np)   # the warps' copies of the step counts
             covered.setdefault(int(j["blk"]), set()).add((int(j["tile"]), int(j["part"])))
             if (int(j["boff"]), int(j["eoff"])) in checked:   # tiles of a block share its table
                 continue
