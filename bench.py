@@ -23,6 +23,7 @@ independent replicas (weak scaling) and rank 0 reports the whole-job rate.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -40,6 +41,10 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # 152 SMs x 2 FP64 FMA/clk (x2 flops) x 2.07 GHz, and 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Double-float (FP32 pair) arithmetic of the FP64_TC gather and near field: one FP64-accurate
+# fused multiply-add (2 flops) takes 15 FP32 instructions (exact product by FMA, two-sum, renormalise)
+DF_INSTR_PER_FMA = 15
+DF_PEAK_TFLOPS = FP32_PEAK_TFLOPS / DF_INSTR_PER_FMA
 # TF32 runs at half the dense BF16 rate on this tensor core (nominal 1.1 against 2.25 PFLOP/s);
 # 3xTF32 spends three TF32 products on each FP32-accurate product
 TF32_PER_BF16 = 0.5
@@ -52,6 +57,8 @@ L2_FLUSH_BYTES = 256 << 20
 WORKLOADS = {
     "periodic3d": lambda W: W.config_3d_periodic_uniform(seed=0),
     "adaptive3d": lambda W: W.config_3d_free_adaptive(seed=0, p=8, delta=1e-3),
+    # the same tree and density at delta 1e-4 (a 16^3 cutoff grid, a third of its boxes anchors)
+    "adaptive3d_d1e-4": lambda W: dataclasses.replace(W.config_3d_free_adaptive(seed=0, p=8, delta=1e-3), delta=1e-4),
     "uniform2d": lambda W: W.config_2d_free_uniform(seed=0),
 }
 FORMS = {"split": ("split_tol1e-6", 1e-6, 1), "fp64": ("fp64_tol1e-6", 1e-6, 0),
@@ -117,9 +124,9 @@ class ClockSampler:
 # kernels of that phase change, and phases without a current capture report null.
 NCU_TRAFFIC = {
     ("periodic3d", "fp64tc_tol1e-10", "evaluate"): {
-        "bytes": 2090.9e6, "source": "profiles/sliced_fp64_kernels_periodic3d.md (oz_slice_kernel + oz_mma_kernel, stages 3-5)"},
+        "bytes": 2087.4e6, "source": "profiles/sliced_fp64_kernels_periodic3d.md (oz_slice_kernel + oz_mma_kernel, stages 3-5)"},
     ("periodic3d", "fp64tc_tol1e-10", "form"): {
-        "bytes": 1937.3e6, "source": "profiles/sliced_fp64_kernels_periodic3d.md (oz_slice_kernel + oz_mma_kernel, stages 0-2)"},
+        "bytes": 1977.2e6, "source": "profiles/sliced_fp64_kernels_periodic3d.md (oz_slice_kernel + oz_mma_kernel, stages 0-2)"},
     ("periodic3d", "fp64_tol1e-10", "form"): {
         "bytes": 2150.2e6, "source": "profiles/fp64_kernels_periodic3d.md (form_kernel<3,double>, 1 launch a step)"},
     ("periodic3d", "fp64_tol1e-10", "evaluate"): {
@@ -167,6 +174,7 @@ def roofline_of(info, prof, nprof, prec, traffic_key=None):
     tpk, tsrc = split_tensor_peak_tflops()
     spk, ssrc = sliced_tensor_peak_tflops()
     sliced = info.get("n_sliced_jobs", 0) > 0
+    d3 = info.get("d", 3) == 3
 
     def on_tensor(ph):
         return (prec == 1 and ph in ("form", "evaluate", "gather")) or (sliced and ph in ("form", "evaluate"))
@@ -176,6 +184,9 @@ def roofline_of(info, prof, nprof, prec, traffic_key=None):
             return tpk, (f"{tsrc}: BF16 burst x {TF32_PER_BF16} (TF32/BF16) / {SPLIT_PRODUCTS} (3xTF32)")
         if sliced and ph in ("form", "evaluate"):
             return spk, f"{ssrc}: BF16 burst / {SLICE_PRODUCTS} (BF16 slice products per FP64 product)"
+        if sliced and d3 and ph in ("gather", "near"):
+            return DF_PEAK_TFLOPS, (f"derived: FP32 CUDA-core peak / {DF_INSTR_PER_FMA} "
+                                    "(FP32 instructions per double-float FMA)")
         return FP64_PEAK_TFLOPS, "derived: 152 SMs x 2 FP64 FMA/clk x 2 x 2.07 GHz"
 
     dom = max(prof, key=lambda k: prof[k])
@@ -192,7 +203,7 @@ def roofline_of(info, prof, nprof, prec, traffic_key=None):
             phases[ph] = {"ms": t, "achieved_tflops": a, "peak_tflops": pk, "frac": a / pk}
             if prec == 1 and ph in ("form", "evaluate", "gather"):
                 phases[ph]["frac_of_fp32_cuda_core"] = a / FP32_PEAK_TFLOPS
-            if sliced and ph in ("form", "evaluate"):
+            if sliced and (ph in ("form", "evaluate") or (d3 and ph in ("gather", "near"))):
                 phases[ph]["frac_of_fp64_alu"] = a / FP64_PEAK_TFLOPS
     out = {"bound": "tensor" if on_tensor(dom) else "alu",
            "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -699,7 +710,8 @@ def arithmetic_of(prec, info):
     if prec == 2 and info.get("n_sliced_jobs", 0) > 0:
         return ("FP64 expansions; form and evaluation contractions as exact sums of BF16 digit products on the "
                 "tensor cores (operands rounded to 47 bits, six 8-bit digits each, FP32 accumulation exact, "
-                "64-bit integer recombination); gather and near field FP64")
+                "64-bit integer recombination); gather and near field in double-float arithmetic on the FP32 pipes "
+                "(FP64 in, FP64 out)")
     if prec == 2:
         return "FP64 throughout, some contractions on the FP64 tensor cores (DMMA)"
     return "FP64 throughout (CUDA cores)"

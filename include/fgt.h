@@ -147,7 +147,9 @@ fgt_status fgt_plan_create_host(int d, double delta, double tol, double eps_pw, 
  * "gather_dst", "gather_ptr", "gather_src", "gather_segs", "gather_grid", "Pf", "Ph", "near_tgt",
  * "near_flags", "near_ptr",
  * "near_src", "near_tab", "merge<i>_items|qf|qh", "push<i>_items|qf|qh", and for the sliced FP64
- * tensor-core stages "oz_jobs<kind>", "oz_btab", "oz_bexp", "eval_blocks").  The pointer stays
+ * tensor-core stages "oz_jobs<kind>", "oz_btab", "oz_bexp", "eval_blocks").  "gather_grid", where
+ * the plan gathers in stencil form, holds the expansion slot of each box of the cutoff grid (int32,
+ * x1 fastest, -1 where a box has no outgoing expansion).  The pointer stays
  * valid until the plan is destroyed or re-planned.  FGT_ERR_STATE for device plans. */
 fgt_status fgt_plan_host_array(const fgt_plan *plan, const char *name, const void **data, size_t *bytes);
 

@@ -3010,6 +3010,115 @@ __global__ void __launch_bounds__(256) gather2_kernel(const GatherSeg *__restric
   gather2_body<D, R, W>(segs, Pf, Ph, phi, psi, n1, nh, slot_size, psi_pitch, blockIdx.x, blockIdx.y);
 }
 
+// The stencil form of the gather over a cutoff grid of NB^3 boxes whether or not every box is an
+// anchor (FP64-TC plans, 3D, NB = 4, 8 or 16): MT modes of the grid in shared memory (boxes without an
+// outgoing expansion hold zero, which is what the source lists leave out), double-float arithmetic
+// in the symmetric form (P(0) = 1, P(+1) = conj P(-1)), each pass a thread per grid line holding the
+// line's NB values in registers and writing the stencil back in place.  Every slot is read once
+// and written once per mode, where the per-anchor and run forms read each source up to 27 and 9
+// times; the price is the stencil over the empty boxes, 3 x 8 double-float products per box.
+// Layout: the box slot table, then per mode the boxes with one float4 of padding after each x1 row
+// (box b at b + b / NB), so that the x1 lines of consecutive threads fall in different banks.
+constexpr int kGridThreads = 512;
+template <int NB, int MT>
+constexpr size_t gathergrid_smem() {
+  return sizeof(int32_t) * (NB * NB * NB + NB * NB) + sizeof(float4) * (size_t)MT * (NB * NB * NB + NB * NB);
+}
+template <int NB, int MT>
+__global__ void __launch_bounds__(kGridThreads, 1) gathergrid_df_kernel(const int32_t *__restrict__ gslot,
+                                                                        const double2 *__restrict__ Pf,
+                                                                        const double2 *__restrict__ Ph,
+                                                                        const double2 *__restrict__ phi,
+                                                                        double2 *__restrict__ psi, int n1, int nh,
+                                                                        int64_t slot_size, int periodic) {
+  constexpr int NBOX = NB * NB * NB, NL = NB * NB, PN = NBOX + NL, U = 8;
+  static_assert(((NBOX + NL) * sizeof(int32_t)) % 16 == 0, "the tables must keep the float4 rows aligned");
+  extern __shared__ __align__(16) unsigned char gg_raw[];
+  int32_t *sslot = reinterpret_cast<int32_t *>(gg_raw);
+  int32_t *sline = sslot + NBOX;  // per (x1, x2): does the line along x3 hold an anchor
+  float4 *gbuf = reinterpret_cast<float4 *>(gg_raw + sizeof(int32_t) * (NBOX + NL));  // [MT][PN]
+  for (int b = threadIdx.x; b < NBOX; b += blockDim.x) sslot[b] = __ldg(gslot + b);
+  __syncthreads();
+  for (int l = threadIdx.x; l < NL; l += blockDim.x) {
+    int any = 0;
+    for (int x3 = 0; x3 < NB; ++x3) any |= sslot[x3 * NL + l] >= 0;
+    sline[l] = any;
+  }
+  __syncthreads();
+  const int64_t m0 = (int64_t)blockIdx.x * MT;
+  // MT consecutive modes of a box together; U independent loads in flight per thread
+  for (int e0 = threadIdx.x; e0 < MT * NBOX; e0 += U * blockDim.x) {
+    double2 x[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      x[u] = make_double2(0.0, 0.0);
+      if (e < MT * NBOX) {
+        const int j = e % MT, b = e / MT, sl = sslot[b];
+        if (sl >= 0 && m0 + j < slot_size) x[u] = phi[(int64_t)sl * slot_size + m0 + j];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e < MT * NBOX) {
+        const int j = e % MT, b = e / MT;
+        const dfl re = dfl_from_f64(x[u].x), im = dfl_from_f64(x[u].y);
+        gbuf[j * PN + b + b / NB] = make_float4(re.hi, re.lo, im.hi, im.lo);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int ax = 0; ax < 3; ++ax) {
+    // padded offsets of the line elements: x1 rows NB + 1 apart, x3 planes NL + NB apart
+    const int stride = ax == 0 ? 1 : ax == 1 ? NB + 1 : NL + NB;
+    for (int L = threadIdx.x; L < MT * NL; L += blockDim.x) {
+      const int j = L / NL, l = L - j * NL;
+      const int64_t m = m0 + j;
+      if (m >= slot_size) continue;
+      // the last pass writes only what the store reads: lines along x3 without an anchor are skipped
+      if (ax == 2 && !sline[l]) continue;
+      // the line's first element: l numbers the other two coordinates, the lower one fastest
+      const int lo = l % NB, hi = l / NB;
+      float4 *ln = gbuf + j * PN + (ax == 0 ? l * (NB + 1) : ax == 1 ? hi * (NL + NB) + lo : hi * (NB + 1) + lo);
+      float4 v[NB];
+      bool live = false;
+#pragma unroll
+      for (int x = 0; x < NB; ++x) {
+        v[x] = ln[x * stride];
+        live |= (v[x].x != 0.f) | (v[x].z != 0.f);  // a double-float value is zero iff its high part is
+      }
+      if (!live) continue;  // a line of zeros (empty boxes) stays zero
+      int m1, m2, m3;
+      mode_index<3>(m, n1, m1, m2, m3);
+      const double2 p = ax == 0 ? Pf[m1] : ax == 1 ? Pf[m2] : Ph[m3];  // P(-1) of this axis
+      const dfl qr = dfl_from_f64(p.x), qi = dfl_from_f64(p.y), nqi = dfl_neg(qi);
+#pragma unroll
+      for (int x = 0; x < NB; ++x) {
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 lf = x > 0 ? v[x - 1] : (periodic ? v[NB - 1] : zero);
+        const float4 rt = x < NB - 1 ? v[x + 1] : (periodic ? v[0] : zero);
+        const dfl sr = dfl_add(dfl{lf.x, lf.y}, dfl{rt.x, rt.y}), si = dfl_add(dfl{lf.z, lf.w}, dfl{rt.z, rt.w});
+        const dfl dr = dfl_add(dfl{lf.x, lf.y}, dfl{-rt.x, -rt.y}), di = dfl_add(dfl{lf.z, lf.w}, dfl{-rt.z, -rt.w});
+        const dfl o_r = dfl_fma(nqi, di, dfl_fma(qr, sr, dfl{v[x].x, v[x].y}));
+        const dfl o_i = dfl_fma(qi, dr, dfl_fma(qr, si, dfl{v[x].z, v[x].w}));
+        ln[x * stride] = make_float4(o_r.hi, o_r.lo, o_i.hi, o_i.lo);
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < MT * NBOX; e += blockDim.x) {
+    const int j = e % MT, b = e / MT;
+    const int64_t m = m0 + j;
+    const int sl = sslot[b];
+    if (sl < 0 || m >= slot_size) continue;
+    const float4 v = gbuf[j * PN + b + b / NB];
+    double2 *o = psi + (int64_t)sl * slot_size + m;
+    if (FGT_OK_PTR(o)) *o = make_double2(dfl_to_f64(dfl{v.x, v.y}), dfl_to_f64(dfl{v.z, v.w}));
+  }
+}
+
 // The run form (gather2) for FP64 expansions with double-float products (FP64-TC plans, 3D): the
 // phases of each line (o_2, o_3) formed in FP64, every factor and source split into FP32 pairs with
 // integer operations, the 9 (W + 2) + 3 W complex products on the FP32 pipes (about 2^-47 each), the
@@ -3714,8 +3823,21 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
   mark(2, 0);
   const C *eval_src = phi;
   if (!e.fourier && e.n_gather > 0) {
-    if (D == 3 && sizeof(R) == 8 && (e.grid_nb == 4 || e.grid_nb == 8) && e.gather_grid != nullptr &&
-        e.psi_pitch == 0) {
+    if (D == 3 && sizeof(R) == 8 && e.tc64 && e.grid_sparse && e.gather_sym && e.gather_grid != nullptr &&
+        e.psi_pitch == 0 && (e.grid_nb == 4 || e.grid_nb == 8 || e.grid_nb == 16)) {
+      // FP64-TC, a cutoff grid with empty boxes: the in-place line stencil over the whole grid
+      const int nb = e.grid_nb, mt = nb == 4 ? 176 : nb == 8 ? 24 : 3;
+      auto gk = nb == 4 ? gathergrid_df_kernel<4, 176> : nb == 8 ? gathergrid_df_kernel<8, 24>
+                                                                 : gathergrid_df_kernel<16, 3>;
+      const size_t gsm = nb == 4 ? gathergrid_smem<4, 176>() : nb == 8 ? gathergrid_smem<8, 24>()
+                                                                       : gathergrid_smem<16, 3>();
+      if ((err = cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm)) != cudaSuccess)
+        return err;
+      gk<<<(unsigned)((ss + mt - 1) / mt), kGridThreads, gsm, st>>>(
+          e.gather_grid, reinterpret_cast<const double2 *>(e.Pf), reinterpret_cast<const double2 *>(e.Ph),
+          reinterpret_cast<const double2 *>(phi), reinterpret_cast<double2 *>(psi), n1, nh, ss, e.grid_periodic);
+    } else if (D == 3 && sizeof(R) == 8 && (e.grid_nb == 4 || e.grid_nb == 8) && !e.grid_sparse &&
+               e.gather_grid != nullptr && e.psi_pitch == 0) {
       // FP64, every box of the cutoff level an anchor: the stencil form, axis by axis
       const int nb = e.grid_nb, mt = gather3_mt(nb);
       // FP64-TC plans: double-float products; FP64 plans: FP64 products

@@ -1242,7 +1242,12 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   std::vector<int32_t> ggrid;
   ex.grid_nb = 0;
   ex.grid_periodic = per ? 1 : 0;
-  if (d == 3 && !P.fourier && P.gather3 && !P.f32() && !hier && (P.lc == 2 || P.lc == 3)) {
+  // FP64-TC plans also take the cutoff grids with empty boxes (4, 8 or 16 boxes a side): the line
+  // stencil over the whole grid reads every slot once per mode
+  ex.grid_sparse = 0;
+  const bool sparse_ok = P.prec == FGT_PREC_FP64_TC && (P.lc >= 2 && P.lc <= 4);
+  if (d == 3 && !P.fourier && P.gather3 && !P.f32() && !hier && ((P.lc == 2 || P.lc == 3) || sparse_ok) &&
+      !anchors.empty()) {
     const int nb = 1 << P.lc;
     ggrid.assign((size_t)nb * nb * nb, -1);
     bool full = (int64_t)anchors.size() == (int64_t)nb * nb * nb;
@@ -1251,8 +1256,14 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
       ggrid[((size_t)Tb.c[2] * nb + Tb.c[1]) * nb + Tb.c[0]] = Tb.slot;
     }
     for (int32_t v : ggrid) full = full && v >= 0;
-    if (full) ex.grid_nb = nb;
-    else ggrid.clear();
+    if (full && P.lc <= 3) {
+      ex.grid_nb = nb;
+    } else if (sparse_ok) {
+      ex.grid_nb = nb;
+      ex.grid_sparse = 1;
+    } else {
+      ggrid.clear();
+    }
   }
   // phase vectors of T_out->in: S = T + o (box units) gives c_T - c_S = -o L_c
   std::vector<C> Pf, Ph;

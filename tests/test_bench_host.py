@@ -36,6 +36,17 @@ def test_roofline_phases_and_dominant_phase(bench):
     r64 = bench.roofline_of(info, prof, 4, 0)
     assert r64["bound"] == "alu" and r64["peak"] == bench.FP64_PEAK_TFLOPS
     assert all(v["peak_tflops"] == bench.FP64_PEAK_TFLOPS for v in r64["phases"].values())
+    # FP64_TC in 3D: form and evaluation against the sliced tensor roofline, gather and near field
+    # (double-float on the FP32 pipes) against the FP32 instruction rate / 15 per double-float FMA
+    spk, _ = bench.sliced_tensor_peak_tflops()
+    rtc = bench.roofline_of(dict(info, d=3, n_sliced_jobs=12), prof, 4, 2)
+    assert rtc["kernel"] == "evaluate" and rtc["bound"] == "tensor" and rtc["peak"] == spk
+    assert rtc["phases"]["gather"]["peak_tflops"] == rtc["phases"]["near"]["peak_tflops"] == bench.DF_PEAK_TFLOPS
+    assert abs(bench.DF_PEAK_TFLOPS - bench.FP32_PEAK_TFLOPS / 15) < 1e-12
+    assert "frac_of_fp64_alu" in rtc["phases"]["gather"]
+    # FP64_TC without sliced stages (2D): FP64 peaks throughout
+    r2 = bench.roofline_of(dict(info, d=2, n_sliced_jobs=0), prof, 4, 2)
+    assert all(v["peak_tflops"] == bench.FP64_PEAK_TFLOPS for v in r2["phases"].values())
 
 
 def test_split_tensor_peak(bench, tmp_path, monkeypatch):

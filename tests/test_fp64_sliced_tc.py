@@ -41,12 +41,16 @@ CASES = [
     ("random", 6, 1e-3, 1e-10, 0),      # K = 6 .. 24 mixed, several blocks per anchor
     ("randomp", 4, 1e-3, 1e-10, 1),
     ("uniform4", 4, 1e-2, 1e-10, 0),    # K = 64 blocks (k = 4, 16 leaves a side)
+    ("random5", 4, 1e-4, 1e-10, 0),     # cutoff level 4 with empty boxes: the line-stencil gather
+    ("random5p", 4, 1e-4, 1e-10, 1),
 ]
 
 
 def _tree(name):
     if name.startswith("uniform"):
         return W.uniform_tree(3, int(name[7]), periodic=name.endswith("p"))
+    if name.startswith("random5"):
+        return W.random_balanced_tree(3, 32, max_level=5, min_level=3, split_prob=0.15, periodic=name.endswith("p"))
     return W.random_balanced_tree(3, 31, max_level=4, min_level=2, split_prob=0.3, periodic=name.endswith("p"))
 
 

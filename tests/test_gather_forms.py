@@ -21,10 +21,18 @@ def modes(n1, nh):
     return m1.ravel(), m2.ravel(), m3.ravel()
 
 
-@pytest.mark.parametrize("bc,level,delta,lc", [(1, 4, 2e-3, 2), (0, 4, 2e-3, 2), (1, 4, 1e-3, 3), (0, 4, 1e-3, 3)])
+@pytest.mark.parametrize("bc,level,delta,lc", [(1, 4, 2e-3, 2), (0, 4, 2e-3, 2), (1, 4, 1e-3, 3), (0, 4, 1e-3, 3),
+                                               (0, -5, 1e-4, 4), (1, -5, 1e-4, 4)])
 def test_gather_forms_agree(bc, level, delta, lc):
-    tr = W.uniform_tree(3, level, periodic=bool(bc))
-    hp = F.HostPlan(3, 2, delta, 1e-6, tr.level, tr.coord, bc=bc, prec=F.PREC_FP64)
+    """level > 0: a uniform tree (every cutoff box an anchor); level < 0: a random tree to depth
+    -level, whose cutoff grid has empty boxes (an FP64_TC plan: the grid form with zeros there)."""
+    if level > 0:
+        tr = W.uniform_tree(3, level, periodic=bool(bc))
+        prec = F.PREC_FP64
+    else:
+        tr = W.random_balanced_tree(3, 32, max_level=-level, min_level=3, split_prob=0.15, periodic=bool(bc))
+        prec = F.PREC_FP64_TC
+    hp = F.HostPlan(3, 2, delta, 1e-6, tr.level, tr.coord, bc=bc, prec=prec)
     info = hp.info()
     n1, nh = info["modes_1d"], info["modes_half"]
     assert info["cutoff_level"] == lc
@@ -62,8 +70,8 @@ def test_gather_forms_agree(bc, level, delta, lc):
     assert np.allclose(run, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
     # the stencil form over the full grid: axis by axis, neighbours wrapped (periodic) or absent
     grid = hp.array("gather_grid", np.int32)
-    assert grid.size == nb ** 3 and sorted(grid.tolist()) == list(range(nslot))
-    buf = phi[grid]                                       # [box][mode], box = (x3 nb + x2) nb + x1
+    assert grid.size == nb ** 3 and sorted(v for v in grid.tolist() if v >= 0) == list(range(nslot))
+    buf = np.where((grid >= 0)[:, None], phi[np.maximum(grid, 0)], 0)   # [box][mode], zero where empty
     for ax, P, m in ((0, Pf, m1), (1, Pf, m2), (2, Ph, m3)):
         stride = nb ** ax
         out = np.zeros_like(buf)
@@ -78,6 +86,6 @@ def test_gather_forms_agree(bc, level, delta, lc):
                 out[b] += P[o + 1, m] * buf[b + (xs - x) * stride]
         buf = out
     sten = np.empty_like(phi)
-    sten[grid] = buf
+    sten[grid[grid >= 0]] = buf[grid >= 0]
     assert np.allclose(sten, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
     hp.close()
