@@ -3022,7 +3022,7 @@ __global__ void __launch_bounds__(256) gather2_kernel(const GatherSeg *__restric
 constexpr int kGridThreads = 512;
 template <int NB, int MT>
 constexpr size_t gathergrid_smem() {
-  return sizeof(int32_t) * (NB * NB * NB + NB * NB) + sizeof(float4) * (size_t)MT * (NB * NB * NB + NB * NB);
+  return sizeof(int32_t) * NB * NB * NB + sizeof(float4) * (size_t)MT * (NB * NB * NB + NB * NB);
 }
 template <int NB, int MT>
 __global__ void __launch_bounds__(kGridThreads, 1) gathergrid_df_kernel(const int32_t *__restrict__ gslot,
@@ -3032,18 +3032,11 @@ __global__ void __launch_bounds__(kGridThreads, 1) gathergrid_df_kernel(const in
                                                                         double2 *__restrict__ psi, int n1, int nh,
                                                                         int64_t slot_size, int periodic) {
   constexpr int NBOX = NB * NB * NB, NL = NB * NB, PN = NBOX + NL, U = 8;
-  static_assert(((NBOX + NL) * sizeof(int32_t)) % 16 == 0, "the tables must keep the float4 rows aligned");
+  static_assert((NBOX * sizeof(int32_t)) % 16 == 0, "the slot table must keep the float4 rows aligned");
   extern __shared__ __align__(16) unsigned char gg_raw[];
   int32_t *sslot = reinterpret_cast<int32_t *>(gg_raw);
-  int32_t *sline = sslot + NBOX;  // per (x1, x2): does the line along x3 hold an anchor
-  float4 *gbuf = reinterpret_cast<float4 *>(gg_raw + sizeof(int32_t) * (NBOX + NL));  // [MT][PN]
+  float4 *gbuf = reinterpret_cast<float4 *>(gg_raw + sizeof(int32_t) * NBOX);  // [MT][PN]
   for (int b = threadIdx.x; b < NBOX; b += blockDim.x) sslot[b] = __ldg(gslot + b);
-  __syncthreads();
-  for (int l = threadIdx.x; l < NL; l += blockDim.x) {
-    int any = 0;
-    for (int x3 = 0; x3 < NB; ++x3) any |= sslot[x3 * NL + l] >= 0;
-    sline[l] = any;
-  }
   __syncthreads();
   const int64_t m0 = (int64_t)blockIdx.x * MT;
   // MT consecutive modes of a box together; U independent loads in flight per thread
@@ -3077,22 +3070,15 @@ __global__ void __launch_bounds__(kGridThreads, 1) gathergrid_df_kernel(const in
       const int j = L / NL, l = L - j * NL;
       const int64_t m = m0 + j;
       if (m >= slot_size) continue;
-      // the last pass writes only what the store reads: lines along x3 without an anchor are skipped
-      if (ax == 2 && !sline[l]) continue;
+      int m1, m2, m3;
+      mode_index<3>(m, n1, m1, m2, m3);
+      const double2 p = ax == 0 ? Pf[m1] : ax == 1 ? Pf[m2] : Ph[m3];  // P(-1) of this axis, in flight
       // the line's first element: l numbers the other two coordinates, the lower one fastest
       const int lo = l % NB, hi = l / NB;
       float4 *ln = gbuf + j * PN + (ax == 0 ? l * (NB + 1) : ax == 1 ? hi * (NL + NB) + lo : hi * (NB + 1) + lo);
       float4 v[NB];
-      bool live = false;
 #pragma unroll
-      for (int x = 0; x < NB; ++x) {
-        v[x] = ln[x * stride];
-        live |= (v[x].x != 0.f) | (v[x].z != 0.f);  // a double-float value is zero iff its high part is
-      }
-      if (!live) continue;  // a line of zeros (empty boxes) stays zero
-      int m1, m2, m3;
-      mode_index<3>(m, n1, m1, m2, m3);
-      const double2 p = ax == 0 ? Pf[m1] : ax == 1 ? Pf[m2] : Ph[m3];  // P(-1) of this axis
+      for (int x = 0; x < NB; ++x) v[x] = ln[x * stride];
       const dfl qr = dfl_from_f64(p.x), qi = dfl_from_f64(p.y), nqi = dfl_neg(qi);
 #pragma unroll
       for (int x = 0; x < NB; ++x) {
