@@ -115,7 +115,7 @@ struct ExecDesc {
   // every box of the cutoff level an anchor (3D, 4 or 8 boxes a side): the stencil form of the gather
   // over the grid, gather_grid[(x3 nb + x2) nb + x1] = slot of box (x1, x2, x3); grid_nb = 0: not used
   int grid_nb = 0, grid_periodic = 0;
-  int grid_sparse = 0;  // gather_grid has boxes without an anchor (-1): the FP64-TC line-stencil kernel
+  int grid_lines = 0;  // FP64-TC, gather_grid with boxes without an anchor (-1): the line-stencil kernel
   int gather_sym = 0;  // the phase factors have P(0) = 1 and P(+1) = conj P(-1) exactly (checked at plan time)
   const int32_t *gather_grid = nullptr;
 

@@ -3809,9 +3809,9 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
   mark(2, 0);
   const C *eval_src = phi;
   if (!e.fourier && e.n_gather > 0) {
-    if (D == 3 && sizeof(R) == 8 && e.tc64 && e.grid_sparse && e.gather_sym && e.gather_grid != nullptr &&
+    if (D == 3 && sizeof(R) == 8 && e.tc64 && e.grid_lines && e.gather_sym && e.gather_grid != nullptr &&
         e.psi_pitch == 0 && (e.grid_nb == 4 || e.grid_nb == 8 || e.grid_nb == 16)) {
-      // FP64-TC, a cutoff grid with empty boxes: the in-place line stencil over the whole grid
+      // FP64-TC: the in-place line stencil over the whole grid (empty boxes as zero)
       const int nb = e.grid_nb, mt = nb == 4 ? 176 : nb == 8 ? 24 : 3;
       auto gk = nb == 4 ? gathergrid_df_kernel<4, 176> : nb == 8 ? gathergrid_df_kernel<8, 24>
                                                                  : gathergrid_df_kernel<16, 3>;
@@ -3822,7 +3822,7 @@ static cudaError_t run_typed(const ExecDesc &e, const double *sigma, double *u, 
       gk<<<(unsigned)((ss + mt - 1) / mt), kGridThreads, gsm, st>>>(
           e.gather_grid, reinterpret_cast<const double2 *>(e.Pf), reinterpret_cast<const double2 *>(e.Ph),
           reinterpret_cast<const double2 *>(phi), reinterpret_cast<double2 *>(psi), n1, nh, ss, e.grid_periodic);
-    } else if (D == 3 && sizeof(R) == 8 && (e.grid_nb == 4 || e.grid_nb == 8) && !e.grid_sparse &&
+    } else if (D == 3 && sizeof(R) == 8 && (e.grid_nb == 4 || e.grid_nb == 8) && !e.grid_lines &&
                e.gather_grid != nullptr && e.psi_pitch == 0) {
       // FP64, every box of the cutoff level an anchor: the stencil form, axis by axis
       const int nb = e.grid_nb, mt = gather3_mt(nb);

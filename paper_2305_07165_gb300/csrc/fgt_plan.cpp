@@ -1243,10 +1243,11 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
   ex.grid_nb = 0;
   ex.grid_periodic = per ? 1 : 0;
   // FP64-TC plans also take the cutoff grids with empty boxes (4, 8 or 16 boxes a side): the line
-  // stencil over the whole grid reads every slot once per mode
-  ex.grid_sparse = 0;
-  const bool sparse_ok = P.prec == FGT_PREC_FP64_TC && (P.lc >= 2 && P.lc <= 4);
-  if (d == 3 && !P.fourier && P.gather3 && !P.f32() && !hier && ((P.lc == 2 || P.lc == 3) || sparse_ok) &&
+  // stencil over the whole grid reads every slot once per mode (on full grids it measured slower
+  // than gather3: 0.304 against 0.255 ms on the 16.8M-point periodic workload at tol 1e-10)
+  ex.grid_lines = 0;
+  const bool lines_ok = P.prec == FGT_PREC_FP64_TC && (P.lc >= 2 && P.lc <= 4);
+  if (d == 3 && !P.fourier && P.gather3 && !P.f32() && !hier && ((P.lc == 2 || P.lc == 3) || lines_ok) &&
       !anchors.empty()) {
     const int nb = 1 << P.lc;
     ggrid.assign((size_t)nb * nb * nb, -1);
@@ -1258,9 +1259,9 @@ fgt_status prepare_typed(fgt_plan &P, bool upload) {
     for (int32_t v : ggrid) full = full && v >= 0;
     if (full && P.lc <= 3) {
       ex.grid_nb = nb;
-    } else if (sparse_ok) {
+    } else if (lines_ok) {
       ex.grid_nb = nb;
-      ex.grid_sparse = 1;
+      ex.grid_lines = 1;
     } else {
       ggrid.clear();
     }
