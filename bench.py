@@ -73,26 +73,34 @@ def workload(name="adaptive3d"):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms while active."""
+    """nvidia-smi clocks / throttle reasons sampled every 20 ms while active.  Entering waits (up to
+    5 s) for nvidia-smi's first line, so that sampling is live before the caller's region starts;
+    that line (taken before the region) is left out of the summary unless it is the only one."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 20
 
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.first = None
 
     def __enter__(self):
+        import select
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            ready, _, _ = select.select([self.proc.stdout], [], [], 5.0)
+            if ready:
+                self.first = self.proc.stdout.readline()
         except Exception:
             self.proc = None
         return self
 
     def __exit__(self, *a):
-        self.rows = []
+        self.rows, self.pre = [], []
         if self.proc is None:
             return
         self.proc.terminate()
@@ -105,17 +113,28 @@ class ClockSampler:
             f = [x.strip() for x in line.split(",")]
             if len(f) >= 9:
                 self.rows.append(f)
+        if self.first:
+            f = [x.strip() for x in self.first.split(",")]
+            if len(f) >= 9:
+                self.pre.append(f)
 
     def summary(self):
         rows = getattr(self, "rows", [])
+        pre = getattr(self, "pre", [])
+        note = None
+        if not rows and pre:
+            rows, note = pre, "only the sample taken before the timed region"
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": reasons, "samples": len(rows)}
+        out = {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+               "reasons": reasons, "samples": len(rows), "interval_ms": self.INTERVAL_MS}
+        if note:
+            out["note"] = note
+        return out
 
 
 # DRAM bytes (read + write) per step of a phase's launches, measured by ncu on this workload

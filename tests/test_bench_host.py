@@ -112,6 +112,33 @@ def test_derived_alu_peaks(bench):
     assert abs(bench.FP32_PEAK_TFLOPS - 80.54784) < 1e-9
 
 
+def test_clock_sampler_is_live_before_the_region(bench, tmp_path, monkeypatch):
+    # a stand-in nvidia-smi: one idle line at once, then a line every 10 ms at 2070 MHz
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "echo '0, 1200, 2070, 150.0, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "while true; do sleep 0.01; "
+                    "echo '0, 2070, 2070, 900.0, 0x4, Not Active, Not Active, Not Active, Active'; done\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}:{os.environ['PATH']}")
+    import time
+    with bench.ClockSampler(0) as cs:
+        assert cs.first and cs.first.startswith("0, 1200")   # sampling was live before the region
+        time.sleep(0.2)
+    sm = cs.summary()
+    assert sm["sm_mhz"] == 2070.0 and sm["sm_max_mhz"] == 2070.0 and sm["samples"] >= 3
+    assert sm["reasons"] == ["sw_power_cap"] and "note" not in sm
+    # only the pre-region line: reported as such
+    cs.rows = []
+    sm1 = cs.summary()
+    assert sm1["sm_mhz"] == 1200.0 and sm1["samples"] == 1 and "before" in sm1["note"]
+    # no nvidia-smi at all
+    monkeypatch.setenv("PATH", str(tmp_path / "empty"))
+    with bench.ClockSampler(0) as cs0:
+        pass
+    assert cs0.summary()["reasons"] == ["unavailable"]
+
+
 def test_hbm_peak_lookup(bench, tmp_path, monkeypatch):
     f = tmp_path / "peaks.json"
     f.write_text('{"hbm_gbs": 6000.5}')
