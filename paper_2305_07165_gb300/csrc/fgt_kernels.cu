@@ -3108,8 +3108,8 @@ __global__ void __launch_bounds__(kGridThreads, 1) gathergrid_df_kernel(const in
 // The run form (gather2) for FP64 expansions with double-float products (FP64-TC plans, 3D): the
 // phases of each line (o_2, o_3) formed in FP64, every factor and source split into FP32 pairs with
 // integer operations, the 9 (W + 2) + 3 W complex products on the FP32 pipes (about 2^-47 each), the
-// result rounded back to FP64.  Used where the stencil form does not apply (the cutoff grid not
-// full, or more than 8 boxes a side).
+// result rounded back to FP64.  Used where neither stencil form applies (cutoff grids of more than
+// 16 boxes a side, or phases without the exact symmetry the line stencil relies on).
 template <int W>
 __global__ void __launch_bounds__(256) gather2df_kernel(const GatherSeg *__restrict__ segs,
                                                         const double2 *__restrict__ Pf, const double2 *__restrict__ Ph,
