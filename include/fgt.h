@@ -125,7 +125,17 @@ typedef struct {
 
 /* Build a plan: validate the tree, choose l_c, n_f (or n_p), build the lists
  * and the FP64 1D tables (Section 4.1), upload them, size the workspace.
- * delta > 0; tol in [1e-14, 1e-1].  Returns FGT_ERR_TREE for invalid trees. */
+ * delta > 0; tol in [1e-14, 1e-1].  Returns FGT_ERR_TREE for invalid trees.
+ *
+ * Kernel choices are read from the environment when a plan is created (every choice computes the
+ * same transform; the defaults are the measured fastest):
+ *   FGT_OZAKI=0         FP64_TC, 3D: DMMA kernels instead of the sliced BF16 tensor-core stages
+ *   FGT_FORM7=0 / =1    split, 3D: no form on tcgen05 / the tcgen05 form for K = 8 blocks too
+ *   FGT_EVAL7=0         split, 3D: the CUDA-core evaluation instead of the tcgen05 one
+ *   FGT_EVAL5=0 / =1    the evaluation order with the half-range axis last: off in FP64 / on in split
+ *   FGT_GATHER2=0       FP64: the per-anchor gather instead of the run form
+ *   FGT_GATHER3=0       3D: the run-form gather instead of the stencil forms over the cutoff grid
+ *   FGT_TC_EVAL=1, FGT_TC_EVAL4=1, FGT_TC_EVAL6=1   earlier split-precision evaluation variants */
 fgt_status fgt_plan_create(int d, double delta, double tol, int bc, const fgt_tree *tree, fgt_plan **out);
 
 /* Same, with the plane-wave epsilon given explicitly (eps_pw <= 0 means tol). */
