@@ -151,3 +151,11 @@ def test_hbm_peak_lookup(bench, tmp_path, monkeypatch):
 def test_whole_job_rate_of_replicas(bench):
     # weak scaling: every rank transforms its own copy each step
     assert bench.whole_job_rate(1000, 10, 4, 2.0) == 4 * 1000 * 10 / 2.0
+
+
+def test_adaptive_delta_workload_is_the_same_tree(bench):
+    # the delta 1e-4 benchmark workload: the adaptive tree and density unchanged, only delta differs
+    a, b = bench.workload("adaptive3d"), bench.workload("adaptive3d_d1e-4")
+    assert a.delta == 1e-3 and b.delta == 1e-4
+    assert (a.tree.level == b.tree.level).all() and (a.tree.coord == b.tree.coord).all()
+    assert (a.sigma == b.sigma).all() and a.n_points == b.n_points
