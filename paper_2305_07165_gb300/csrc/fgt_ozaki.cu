@@ -393,6 +393,9 @@ __global__ void __launch_bounds__(kThreads, 1) oz_mma_kernel(const OzArgs a, con
         if (li >= 2 && !mbar_wait(smem_addr(tempty + b), (uint32_t)((li / 2 - 1) & 1))) {
           *abort_flag = 1;
           atomicMax(&g_oz_status, 1);
+          // the epilogue may stop before the previous job's commit: its products (the commit covers
+          // every earlier MMA of this thread) finish before the CTA frees tensor memory
+          if (!mbar_wait(smem_addr(tfull + (b ^ 1)), (uint32_t)(((li - 1) / 2) & 1))) atomicMax(&g_oz_status, 2);
           break;
         }
         tc_fence_after();
@@ -420,7 +423,11 @@ __global__ void __launch_bounds__(kThreads, 1) oz_mma_kernel(const OzArgs a, con
           atomicMax(&g_oz_status, 1);
         }
         umma_commit(smem_addr(tfull + b));  // this job's accumulators are complete (or abandoned)
-        if (!ok) break;
+        if (!ok) {
+          // the abandoned job's products finish before the CTA frees tensor memory
+          if (!mbar_wait(smem_addr(tfull + b), (uint32_t)((li / 2) & 1))) atomicMax(&g_oz_status, 2);
+          break;
+        }
       }
     }
   } else {
