@@ -150,3 +150,75 @@ def test_sliced_digit_tables(name, k, delta, tol, bc):
         total += len(jobs)
     assert total == info["n_sliced_jobs"]
     hp.close()
+
+
+def slice_rows(A, e):
+    """Six balanced base-256 digits of each entry of A against its row exponent e (the largest
+    entry of row r lies in [2^(e_r - 1), 2^e_r)): A ~ 2^e_r sum_s d_s 2^(-7 - 8 s), |d_s| <= 128."""
+    N = np.rint(np.ldexp(A, (47 - e)[:, None])).astype(np.int64)   # |N| <= 2^47
+    d = []
+    for _ in range(S - 1):
+        lo = ((N + 128) % 256) - 128
+        d.append(lo)
+        N = (N - lo) // 256
+    d.append(N)
+    return np.stack(d[::-1])                                           # d[0] the leading digit
+
+
+@pytest.mark.parametrize("kind", [1, 4])
+def test_sliced_products_meet_their_bound(kind):
+    """The scheme end to end on one job's real table: a seeded operand A (rows spanning 2^-20 .. 2^20,
+    a zero row, ragged magnitudes) sliced by rows, the 21 digit-pair products with s + t <= 5 summed
+    per diagonal D = s + t (each partial sum below 2^24: exact in FP32), recombined as
+    V = sum_D P_D 2^(8 (5 - D)) (|V| < 2^62) and scaled by 2^(e_r + f_n - 54).  The result meets the
+    bound of the two 47-bit roundings and the dropped pairs, a few units of 2^(e_r + f_n - 47) per
+    term of the contraction, and lies far inside tol 1e-10."""
+    tr = W.random_balanced_tree(3, 21, max_level=4, min_level=2, split_prob=0.25)
+    k = 4
+    hp = F.HostPlan(3, k, 1e-3, 1e-10, tr.level, tr.coord, bc=0, prec=F.PREC_FP64_TC)
+    info = hp.info()
+    n1, nh = info["modes_1d"], info["modes_half"]
+    tab = {nm: hp.array(nm, np.complex128) for nm in ("Ff", "Fh", "Ef", "Eh")}
+    btab = hp.array("oz_btab", np.uint16)
+    bexp = hp.array("oz_bexp", np.int32)
+    blocks = hp.array("blocks" if kind < 3 else "eval_blocks", BLOCK)
+    jobs = hp.array(f"oz_jobs{kind}", JOB)
+    j = jobs[int(np.argmax([int(blocks[x["blk"]]["K"]) for x in jobs]))]   # a job of the largest block
+    b = blocks[j["blk"]]
+    R, Q, N, P, Nc, Np, nks = dims(kind, int(b["K"]), n1, nh)
+    # B's digits and column exponents as the products read them
+    f = bexp[j["eoff"]: j["eoff"] + Np].astype(np.int64)
+    q = np.arange(nks * 16)[:, None]
+    nl = np.arange(Np)[None, :]
+    off = ((q // 16) * S * Np * 16 + (nl >> 3) * 128 + ((q % 16) >> 3) * 64 + (nl & 7) * 8 + (q % 16 & 7))
+    bd = np.stack([bf16_to_float(btab[int(j["boff"]) // 2 + off + s * Np * 16]) for s in range(S)]).astype(np.int64)
+    Bt = real_form(kind, b, k, n1, nh, tab)
+    c = int(j["part"]) * Nc + np.arange(Np)
+    live = (np.arange(Np) < Nc) & (c < N)
+    Bp = np.zeros((nks * 16, Np))
+    Bp[:Q, live] = Bt[:, c[live]]
+    # a seeded operand tile: 128 rows, the contraction padded to whole 16-deep steps with zeros
+    rng = np.random.default_rng(11)
+    A = np.zeros((128, nks * 16))
+    A[:, :Q] = rng.standard_normal((128, Q)) * np.ldexp(1.0, rng.integers(-20, 21, 128))[:, None]
+    A[5] = 0.0
+    A[7, :Q] *= np.ldexp(1.0, -rng.integers(0, 40, Q))                      # ragged within a row
+    amax = np.abs(A).max(axis=1)
+    e = np.where(amax > 0, np.frexp(np.where(amax > 0, amax, 1.0))[1], 0).astype(np.int64)
+    ad = slice_rows(A, e)
+    assert np.abs(ad).max() <= 128 and np.abs(bd).max() <= 128
+    Pd = np.zeros((S, 128, Np), dtype=np.int64)
+    for s in range(S):
+        for t in range(S - s):
+            Pd[s + t] += ad[s] @ bd[t]
+    assert np.abs(Pd).max() < 2 ** 24                                        # exact FP32 accumulation
+    V = sum(Pd[D] << (8 * (S - 1 - D)) for D in range(S))
+    assert np.abs(V).max() < 2 ** 62
+    C = np.ldexp(V.astype(np.float64), e[:, None] + f[None, :] - 54)
+    ref = A @ Bp
+    err = np.abs(C - ref)[:, live]
+    scale = np.ldexp(1.0, e[:, None] + f[None, :])[:, live]
+    assert np.all(err <= 8 * Q * scale * 2.0 ** -47), (err / scale).max()
+    assert np.all(C[5] == 0)
+    assert (err / np.maximum(np.abs(A) @ np.abs(Bp), 1e-300)[:, live]).max() < 1e-12
+    hp.close()
