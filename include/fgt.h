@@ -64,7 +64,8 @@ typedef enum { FGT_BC_FREE = 0, FGT_BC_PERIODIC = 1 } fgt_bc;
  *   pweval) on the BF16 tensor pipe: each FP64 operand is rounded to 47 bits
  *   against its row's (column's) largest exponent and cut into six 8-bit
  *   digits, the digit products are summed exactly in FP32 and recombined in
- *   64-bit integers (error about 2^-46 of the sum of |products|); the out->in
+ *   64-bit integers (error a few units of 2^-47 times the row's and column's
+ *   largest entries per term of the contraction); the out->in
  *   phases and the near field run in double-float arithmetic (FP32 pairs,
  *   about 2^-47 per operation), expansions and u stay FP64.  FGT_OZAKI=0 in the environment at plan
  *   creation, and the allocation-free call, use the FP64 tensor cores (DMMA)

@@ -15,9 +15,10 @@
 //     6 x 160 products of magnitude <= 2^14 sum to less than 2^24, so every P_D is exact;
 //   - C[r][n] = 2^(e_r + f_n - 14) sum_D 2^(-8 D) P_D is recombined in a 64-bit integer and
 //     rounded to FP64 once.
-// The products dropped (s + t >= 6) and the two 47-bit roundings bound the error of C[r][n] by
-// about 2^-46 sum_q |A[r][q]| |B[q][n]| -- FP64 quality for a contraction, for 21 BF16 products per
-// FP64 product where a 3xTF32 product needs 3 TF32 ones.
+// The products dropped (s + t >= 6) and the two 47-bit roundings bound the error of C[r][n] by a
+// few units of 2^(e_r + f_n - 47) per term of the contraction (the roundings are relative to the
+// row's and the column's largest entries) -- FP64 quality for a contraction, for 21 BF16 products
+// per FP64 product where a 3xTF32 product needs 3 TF32 ones.
 //
 // Each stage is one contraction of the block's separable product (form: x3, x2, x1; evaluation:
 // m1, m2, m3, the last one keeping the real part) and takes two launches:
